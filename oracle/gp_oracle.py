@@ -1,0 +1,529 @@
+"""Plain FP64 CPU oracle for the generalized-Poisson hot path.
+
+TEST INFRASTRUCTURE ONLY. Nothing on the product path imports this module:
+only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+leg of ``bench.py`` may call it. It shares no code with the CUDA library.
+
+Every function restates, in plain and slow NumPy, a definition from
+Sanchez, Sued & Scherlis, "First-principles molecular dynamics simulations at
+solid-liquid interfaces with a continuum solvent" (arXiv:0904.4887):
+
+  * Eq. 3   generalized Poisson equation  div(eps grad phi) = -4 pi rho
+  * Eq. 4   Hartree energy  E = 1/2 int rho phi = 1/(8 pi) int eps |grad phi|^2
+  * Eq. 11  dE/dR_I = -1/(8 pi) int (d eps/d R_I)|grad phi|^2 + int phi d rho/d R_I
+            (Appendix B, Eq. 26-31)
+  * Eq. 15  FFT Poisson solve in vacuum
+  * Sec. II.C, Scheme 1   dry/wet split: FFT on the whole box, multigrid on the
+            wet sub-domain with Dirichlet values from the FFT solution,
+            combined self-consistently (abstract; Sec. I)
+
+Readings of points where the paper is silent (the dielectric form, the
+stencil, the charge model, the split's self-consistent loop) are listed in the
+repository's design notes; each function states the one it uses.
+
+Array layout: fields are float64 arrays of shape (nz, ny, nx) in C order, so
+the flat index is i + nx*(j + ny*k): x fastest, z-planes contiguous.
+Units: Angstrom and elementary charge, Gaussian electrostatics (k = 1).
+
+Parity status: every function below is pinned by a ``-m "not gpu"`` test in
+``tests/test_oracle_pins.py`` (closed forms, invariants, brute force).
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+import math
+
+import numpy as np
+from scipy.special import erf
+
+FOUR_PI = 4.0 * math.pi
+# numpy axis of each Cartesian direction for (nz, ny, nx) arrays
+AX = {0: 2, 1: 1, 2: 0}
+
+
+@dataclasses.dataclass(frozen=True)
+class DielectricParams:
+    """eps(r) = 1 + (eps0 - 1) * prod_a s(|r - R_a|),  s(d) = (1 + erf((d - r0)/w))/2.
+
+    Position-dependent dielectric built from the atomic coordinates, the idea of
+    Sec. II.B (Eq. 9-10) with the erf switching function of the workloads; the
+    product runs over atoms and their periodic images with d < rcut (s = 1
+    beyond: 1 - s(6 A) is about 1e-23).
+    """
+    eps0: float = 78.36
+    r0: float = 2.5
+    w: float = 0.5
+    rcut: float = 6.0
+
+
+GAUSS_CUT_SIGMAS = 8.0   # Gaussians truncated at 8 sigma: exp(-32) ~ 1e-14 of the peak
+
+
+def spacing(grid, cell):
+    return tuple(float(cell[a]) / int(grid[a]) for a in range(3))
+
+
+def cell_volume_element(grid, cell):
+    hx, hy, hz = spacing(grid, cell)
+    return hx * hy * hz
+
+
+# ----------------------------------------------------------------------------
+# periodic images: sub-boxes of grid points within `radius` of each image
+# ----------------------------------------------------------------------------
+
+def _image_boxes(center, grid, cell, radius):
+    """Yield (slices, (dz, dy, dx)) for every periodic image of `center` that
+    has grid points within `radius`; d* are broadcastable displacement arrays
+    r - (center + n L) over the sub-box. Images beyond +-1 cell cannot reach
+    the grid when radius <= L (each point and the centre lie in [0, L))."""
+    h = spacing(grid, cell)
+    for a in range(3):
+        assert radius <= cell[a], "cut-off radius must not exceed the cell"
+    for n in itertools.product((-1, 0, 1), repeat=3):
+        c = [center[a] + n[a] * cell[a] for a in range(3)]
+        lo = [max(int(math.ceil((c[a] - radius) / h[a])), 0) for a in range(3)]
+        hi = [min(int(math.floor((c[a] + radius) / h[a])), grid[a] - 1) for a in range(3)]
+        if any(lo[a] > hi[a] for a in range(3)):
+            continue
+        dx = np.arange(lo[0], hi[0] + 1) * h[0] - c[0]
+        dy = np.arange(lo[1], hi[1] + 1) * h[1] - c[1]
+        dz = np.arange(lo[2], hi[2] + 1) * h[2] - c[2]
+        sl = (slice(lo[2], hi[2] + 1), slice(lo[1], hi[1] + 1), slice(lo[0], hi[0] + 1))
+        yield sl, (dz[:, None, None], dy[None, :, None], dx[None, None, :])
+
+
+# ----------------------------------------------------------------------------
+# dielectric eps(R) and its atomic derivative
+# ----------------------------------------------------------------------------
+
+def switching(d, p: DielectricParams):
+    return 0.5 * (1.0 + erf((d - p.r0) / p.w))
+
+
+def switching_derivative(d, p: DielectricParams):
+    """ds/dd = exp(-((d - r0)/w)^2) / (w sqrt(pi))."""
+    return np.exp(-((d - p.r0) / p.w) ** 2) / (p.w * math.sqrt(math.pi))
+
+
+def dielectric_product(grid, cell, pos, p: DielectricParams = DielectricParams()):
+    """P = prod over atoms and images within rcut of s(d); eps = 1 + (eps0-1) P."""
+    P = np.ones((grid[2], grid[1], grid[0]))
+    for R in pos:
+        for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, p.rcut):
+            d = np.sqrt(dx * dx + dy * dy + dz * dz)
+            f = np.where(d < p.rcut, switching(d, p), 1.0)
+            P[sl] *= f
+    return P
+
+
+def dielectric(grid, cell, pos, p: DielectricParams = DielectricParams()):
+    """eps on the grid (position-dependent dielectric, Sec. II.B)."""
+    return 1.0 + (p.eps0 - 1.0) * dielectric_product(grid, cell, pos, p)
+
+
+def dielectric_points(points, cell, pos, p: DielectricParams = DielectricParams()):
+    """eps at arbitrary points (M, 3), one by one over atoms and all 27 images."""
+    points = np.asarray(points, dtype=np.float64)
+    cell = np.asarray(cell, dtype=np.float64)
+    P = np.ones(len(points))
+    for R in pos:
+        for n in itertools.product((-1, 0, 1), repeat=3):
+            d = np.linalg.norm(points - (R + np.asarray(n) * cell), axis=1)
+            P *= np.where(d < p.rcut, switching(d, p), 1.0)
+    return 1.0 + (p.eps0 - 1.0) * P
+
+
+def dielectric_gradient_atom(a, grid, cell, pos, P, p: DielectricParams = DielectricParams()):
+    """d eps_i / d R_a on the grid, as three arrays (x, y, z components).
+
+    Product rule over the factors that belong to atom a (one per image within
+    rcut): d eps/dR_a = (eps0-1) sum_images [P / s(d)] s'(d) dd/dR_a, with
+    dd/dR_a = -(r - R_a)/d. P / s(d) is the product of all other factors;
+    every factor is at least erfc(r0/w)/2 > 0, so the division is exact up to
+    rounding.
+    """
+    out = [np.zeros_like(P) for _ in range(3)]
+    for sl, (dz, dy, dx) in _image_boxes(pos[a], grid, cell, p.rcut):
+        d = np.sqrt(dx * dx + dy * dy + dz * dz)
+        inside = d < p.rcut
+        dsafe = np.where(d > 0, d, 1.0)
+        coef = np.where(inside, (p.eps0 - 1.0) * P[sl] / switching(d, p)
+                        * switching_derivative(d, p) / dsafe, 0.0)
+        coef = np.where(d > 0, coef, 0.0)
+        out[0][sl] += -coef * dx
+        out[1][sl] += -coef * dy
+        out[2][sl] += -coef * dz
+    return out
+
+
+# ----------------------------------------------------------------------------
+# charge density: +Z core and -Z cloud Gaussians per atom (Sec. II.A)
+# ----------------------------------------------------------------------------
+
+def gaussian(d2, sigma):
+    """Normalised 3D Gaussian of standard deviation sigma at squared distance d2."""
+    return np.exp(-d2 / (2.0 * sigma * sigma)) / (2.0 * math.pi * sigma * sigma) ** 1.5
+
+
+def charge_density_raw(grid, cell, pos, Z, sigma_core, sigma_cloud, cut=GAUSS_CUT_SIGMAS):
+    """rho~_i = sum_a Z_a [g(d; sigma_core,a) - g(d; sigma_cloud,a)], images within cut*sigma."""
+    rho = np.zeros((grid[2], grid[1], grid[0]))
+    for a, R in enumerate(pos):
+        for sign, sig in ((1.0, sigma_core[a]), (-1.0, sigma_cloud[a])):
+            rad = cut * sig
+            for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, rad):
+                d2 = dx * dx + dy * dy + dz * dz
+                rho[sl] += np.where(d2 < rad * rad, sign * Z[a] * gaussian(d2, sig), 0.0)
+    return rho
+
+
+def charge_density(grid, cell, pos, Z, sigma_core, sigma_cloud, cut=GAUSS_CUT_SIGMAS):
+    """Neutral rho: the raw Gaussian sum minus its grid mean (discrete neutrality)."""
+    raw = charge_density_raw(grid, cell, pos, Z, sigma_core, sigma_cloud, cut)
+    return raw - raw.mean()
+
+
+def charge_density_points(points, cell, pos, Z, sigma_core, sigma_cloud, cut=GAUSS_CUT_SIGMAS):
+    """rho~ (before mean removal) at arbitrary points, one by one."""
+    points = np.asarray(points, dtype=np.float64)
+    cell = np.asarray(cell, dtype=np.float64)
+    out = np.zeros(len(points))
+    for a, R in enumerate(pos):
+        for n in itertools.product((-1, 0, 1), repeat=3):
+            d2 = np.sum((points - (R + np.asarray(n) * cell)) ** 2, axis=1)
+            for sign, sig in ((1.0, sigma_core[a]), (-1.0, sigma_cloud[a])):
+                rad = cut * sig
+                out += np.where(d2 < rad * rad, sign * Z[a] * gaussian(d2, sig), 0.0)
+    return out
+
+
+def charge_density_gradient_atom(a, grid, cell, pos, Z, sigma_core, sigma_cloud,
+                                 cut=GAUSS_CUT_SIGMAS):
+    """d rho~_i / d R_a (x, y, z arrays): d g/dR = g (r - R)/sigma^2."""
+    out = [np.zeros((grid[2], grid[1], grid[0])) for _ in range(3)]
+    for sign, sig in ((1.0, sigma_core[a]), (-1.0, sigma_cloud[a])):
+        rad = cut * sig
+        for sl, (dz, dy, dx) in _image_boxes(pos[a], grid, cell, rad):
+            d2 = dx * dx + dy * dy + dz * dz
+            c = np.where(d2 < rad * rad, sign * Z[a] * gaussian(d2, sig) / (sig * sig), 0.0)
+            out[0][sl] += c * dx
+            out[1][sl] += c * dy
+            out[2][sl] += c * dz
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the operator of Eq. 3 and the FFT solve of Eq. 15
+# ----------------------------------------------------------------------------
+
+def face_mean(eps, axis):
+    """eps on the face between i and i+1 along `axis`: the arithmetic mean."""
+    return 0.5 * (eps + np.roll(eps, -1, axis=axis))
+
+
+def apply_A(phi, eps, h):
+    """(A phi)_i = sum_axes [eps_{i+1/2}(phi_{i+1}-phi_i) - eps_{i-1/2}(phi_i-phi_{i-1})]/h^2.
+
+    The conservative 7-point discretisation of div(eps grad phi) (Eq. 3),
+    periodic in all three directions.
+    """
+    out = np.zeros_like(phi)
+    for c in range(3):
+        ax = AX[c]
+        flux = face_mean(eps, ax) * (np.roll(phi, -1, axis=ax) - phi) / (h[c] * h[c])
+        out += flux - np.roll(flux, 1, axis=ax)
+    return out
+
+
+def apply_L(phi, h):
+    """The same 7-point operator with eps = 1 (the vacuum Laplacian of Eq. 2)."""
+    return apply_A(phi, np.ones_like(phi), h)
+
+
+def polarisation_term(phi, eps, h):
+    """div((eps-1) grad phi) on the grid: the charge 4 pi rho_pol that the
+    dielectric adds to the vacuum problem, so that A phi = L phi + this."""
+    return apply_A(phi, eps - 1.0, h)
+
+
+def laplacian_symbol(grid, h):
+    """Eigenvalues of the 7-point Laplacian on the periodic grid,
+    lambda(k) = sum_axes (2 cos(2 pi k_a / N_a) - 2)/h_a^2, as an (nz, ny, nx//2+1)
+    array matching numpy's rfftn layout."""
+    nx, ny, nz = grid
+    lx = (2.0 * np.cos(2.0 * np.pi * np.arange(nx // 2 + 1) / nx) - 2.0) / h[0] ** 2
+    ly = (2.0 * np.cos(2.0 * np.pi * np.fft.fftfreq(ny) ) - 2.0) / h[1] ** 2
+    lz = (2.0 * np.cos(2.0 * np.pi * np.fft.fftfreq(nz)) - 2.0) / h[2] ** 2
+    return lz[:, None, None] + ly[None, :, None] + lx[None, None, :]
+
+
+def fft_poisson(src, h):
+    """Solve L phi = src on the periodic grid (Eq. 15 with the symbol of the
+    discrete operator, so that the result satisfies the 7-point equation to
+    rounding). The k = 0 mode is set to zero: phi has mean zero."""
+    grid = (src.shape[2], src.shape[1], src.shape[0])
+    lam = laplacian_symbol(grid, h)
+    s = np.fft.rfftn(src)
+    lam[0, 0, 0] = 1.0
+    s = s / lam
+    s[0, 0, 0] = 0.0
+    return np.fft.irfftn(s, s=src.shape, axes=(0, 1, 2))
+
+
+def vacuum_potential(rho, h):
+    """phi solving the vacuum equation L phi = -4 pi rho (Eq. 2, 15)."""
+    return fft_poisson(-FOUR_PI * rho, h)
+
+
+# ----------------------------------------------------------------------------
+# the generalized Poisson solve, to near machine precision
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class SolveInfo:
+    iterations: int
+    residual: float      # ||b - A phi|| / ||b|| of the returned phi
+
+
+def residual_norm(phi, rho, eps, h):
+    """||b - A phi||_2 / ||b||_2 with b = -4 pi rho, all in FP64."""
+    b = -FOUR_PI * rho
+    r = b - apply_A(phi, eps, h)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(r) / nb) if nb > 0 else float(np.linalg.norm(r))
+
+
+def solve(rho, eps, h, tol=1e-14, maxiter=3000, phi0=None):
+    """phi with A phi = -4 pi rho and mean(phi) = 0.
+
+    Conjugate gradients on -A (symmetric, positive definite on mean-zero
+    vectors), preconditioned by the inverse vacuum Laplacian (the FFT solve).
+    Any convergent method reaches the same discrete solution; this one is
+    textbook PCG. Stops when the recursively updated relative residual is
+    below `tol` or stagnates.
+    """
+    b = -FOUR_PI * (rho - rho.mean())
+    nb = np.linalg.norm(b)
+    phi = np.zeros_like(rho) if phi0 is None else phi0 - phi0.mean()
+    if nb == 0:
+        return np.zeros_like(rho), SolveInfo(0, 0.0)
+    # M = -A, preconditioner P^-1 r = -(L^-1) r
+    r = -(b - apply_A(phi, eps, h))          # residual of M phi = -b
+    r -= r.mean()
+    z = -fft_poisson(r, h)
+    p = z.copy()
+    rz = float(np.vdot(r, z))
+    best = np.inf
+    stall = 0
+    it = 0
+    for it in range(1, maxiter + 1):
+        q = -apply_A(p, eps, h)
+        alpha = rz / float(np.vdot(p, q))
+        phi += alpha * p
+        r -= alpha * q
+        rn = np.linalg.norm(r) / nb
+        if rn < tol:
+            break
+        if rn < 0.5 * best:
+            best = rn
+            stall = 0
+        else:
+            stall += 1
+            if stall > 50:
+                break
+        z = -fft_poisson(r, h)
+        rz_new = float(np.vdot(r, z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    phi -= phi.mean()
+    return phi, SolveInfo(it, residual_norm(phi, rho - rho.mean(), eps, h))
+
+
+# ----------------------------------------------------------------------------
+# energy (Eq. 4) and forces (Eq. 11, Appendix B)
+# ----------------------------------------------------------------------------
+
+def energy(rho, phi, grid, cell):
+    """E = 1/2 h^3 sum rho phi (Eq. 4, first form)."""
+    return 0.5 * cell_volume_element(grid, cell) * float(np.sum(rho * phi))
+
+
+def field_energy(phi, eps, grid, cell):
+    """E' = h^3/(8 pi) sum_faces eps_f (Delta_f phi / h)^2 (Eq. 4, second form)."""
+    h = spacing(grid, cell)
+    tot = 0.0
+    for c in range(3):
+        ax = AX[c]
+        g = (np.roll(phi, -1, axis=ax) - phi) / h[c]
+        tot += float(np.sum(face_mean(eps, ax) * g * g))
+    return cell_volume_element(grid, cell) * tot / (8.0 * math.pi)
+
+
+def variational_energy(rho, phi, eps, grid, cell):
+    """J(phi) = h^3 rho.phi + h^3/(8 pi) phi.A phi; equals E at the solution,
+    with an error quadratic in the error of phi."""
+    h = spacing(grid, cell)
+    dv = cell_volume_element(grid, cell)
+    return dv * float(np.sum(rho * phi)) + dv / (8.0 * math.pi) * float(np.sum(phi * apply_A(phi, eps, h)))
+
+
+def energy_gradient(phi, grid, cell, pos, Z, sigma_core, sigma_cloud,
+                    p: DielectricParams = DielectricParams(), atoms=None, rho_moves=True):
+    """G_a = dE/dR_a = G^eps_a + G^rho_a, the discrete Eq. 11.
+
+    G^eps_a = -h^3/(8 pi) sum_faces (d eps_f/dR_a)(Delta_f phi/h)^2, with
+              d eps_f = (d eps_i + d eps_{i+1})/2 (the face mean of Eq. 3)
+    G^rho_a = h^3 sum_i phi_i d rho_i/dR_a, with rho = rho~ - mean(rho~)
+
+    Returns (G_eps, G_rho), each (n_atoms, 3); rows of atoms not in `atoms` are
+    zero. `phi` must be the solution for this geometry: because A is symmetric
+    it is its own adjoint (Appendix B), so no further solve is needed.
+    """
+    h = spacing(grid, cell)
+    dv = cell_volume_element(grid, cell)
+    n = len(pos)
+    atoms = range(n) if atoms is None else atoms
+    P = dielectric_product(grid, cell, pos, p)
+    grads2 = []
+    for c in range(3):
+        ax = AX[c]
+        g = (np.roll(phi, -1, axis=ax) - phi) / h[c]
+        grads2.append((ax, g * g))
+    Ge = np.zeros((n, 3))
+    Gr = np.zeros((n, 3))
+    for a in atoms:
+        de = dielectric_gradient_atom(a, grid, cell, pos, P, p)
+        for comp in range(3):
+            s = 0.0
+            for ax, g2 in grads2:
+                s += float(np.sum(face_mean(de[comp], ax) * g2))
+            Ge[a, comp] = -dv / (8.0 * math.pi) * s
+        if rho_moves:
+            dr = charge_density_gradient_atom(a, grid, cell, pos, Z, sigma_core, sigma_cloud)
+            for comp in range(3):
+                Gr[a, comp] = dv * float(np.sum(phi * (dr[comp] - dr[comp].mean())))
+    return Ge, Gr
+
+
+# ----------------------------------------------------------------------------
+# dry/wet split (Sec. II.C, Scheme 1) made self-consistent
+# ----------------------------------------------------------------------------
+
+def dry_planes(eps, thresh=1e-3):
+    """z-planes on which eps - 1 < thresh everywhere ("dry": eps is 1 there)."""
+    return (eps - 1.0).max(axis=(1, 2)) < thresh
+
+
+def plan_band(dry, levels, n_dirichlet=1):
+    """Choose the wet band Omega_1 (a periodic run of z-planes) and its
+    Dirichlet planes, from the per-plane dry flags.
+
+    Reading: the Dirichlet planes sit in the middle of the longest periodic run
+    of dry planes; there are n_dirichlet of them (0 = as many as the run holds),
+    reduced to the form 1 + m 2^(levels-1) so that the band (all other planes,
+    nz - n_dirichlet interior planes between Dirichlet walls) coarsens
+    `levels - 1` times. Returns (first_dirichlet_plane, n_dirichlet) or None
+    when no plane is dry.
+    """
+    nz = len(dry)
+    if not np.any(dry):
+        return None
+    if np.all(dry):
+        run_start, run_len = 0, nz
+    else:
+        # start scanning just after a wet plane so that runs do not wrap mid-way
+        k0 = int(np.argmin(dry))
+        run_start, run_len, cur_start, cur_len = 0, 0, None, 0
+        for t in range(1, nz + 1):
+            k = (k0 + t) % nz
+            if dry[k]:
+                if cur_len == 0:
+                    cur_start = k
+                cur_len += 1
+                if cur_len > run_len:
+                    run_start, run_len = cur_start, cur_len
+            else:
+                cur_len = 0
+    step = 2 ** (levels - 1)
+    want = run_len if n_dirichlet <= 0 else min(n_dirichlet, run_len)
+    nd = 1 + ((want - 1) // step) * step
+    if nd >= nz:
+        nd = 1
+    first = (run_start + (run_len - nd) // 2) % nz
+    return first, nd
+
+
+def band_planes(nz, first, nd):
+    """Interior planes of the band, in order: the nz - nd planes after the
+    Dirichlet block (periodic)."""
+    return [(first + nd + t) % nz for t in range(nz - nd)]
+
+
+def assemble_A(eps, h):
+    """A as a scipy sparse matrix (same definition as apply_A), flat x-fastest."""
+    import scipy.sparse as sp
+    nz, ny, nx = eps.shape
+    n = eps.size
+    idx = np.arange(n).reshape(eps.shape)
+    rows, cols, vals = [], [], []
+    diag = np.zeros(eps.shape)
+    for c in range(3):
+        ax = AX[c]
+        ef = face_mean(eps, ax) / (h[c] * h[c])
+        nb = np.roll(idx, -1, axis=ax)
+        rows += [idx.ravel(), nb.ravel()]
+        cols += [nb.ravel(), idx.ravel()]
+        vals += [ef.ravel(), ef.ravel()]
+        diag -= ef + np.roll(ef, 1, axis=ax)
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    vals.append(diag.ravel())
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(n, n))
+
+
+def split_solve(rho, eps, h, band, tol=1e-13, maxit=200):
+    """Scheme 1 iterated to self-consistency (reading of Sec. II.C):
+
+      phi^0 = vacuum FFT solution on the whole box Omega;
+      repeat:  solve A phi = b on the wet band Omega_1 with Dirichlet values
+               phi^k on the planes outside it (keep phi^k there);
+               4 pi rho_pol = div((eps - 1) grad phi) on Omega;
+               phi^{k+1} = FFT solution of L phi = b - 4 pi rho_pol.
+
+    The fixed point satisfies L phi + div((eps-1) grad phi) = A phi = b, the
+    full-box equation. `band` = (first_dirichlet_plane, n_dirichlet).
+    Band solves are exact (sparse LU), so use small grids.
+    Returns (phi, history of the relative change per iteration).
+    """
+    import scipy.sparse.linalg as spl
+    nz, ny, nx = rho.shape
+    first, nd = band
+    planes = band_planes(nz, first, nd)
+    wet = np.zeros(nz, dtype=bool)
+    wet[planes] = True
+    wmask = np.broadcast_to(wet[:, None, None], rho.shape).ravel()
+    widx = np.nonzero(wmask)[0]
+    bidx = np.nonzero(~wmask)[0]
+    A = assemble_A(eps, h)
+    Aww = A[widx][:, widx].tocsc()
+    Awb = A[widx][:, bidx]
+    lu = spl.splu(Aww)
+    b = (-FOUR_PI * rho).ravel()
+    phi = fft_poisson(b.reshape(rho.shape), h)
+    hist = []
+    combined = phi
+    for _ in range(maxit):
+        p = phi.ravel().copy()
+        p[widx] = lu.solve(b[widx] - Awb @ p[bidx])
+        combined = p.reshape(rho.shape)
+        pol = polarisation_term(combined, eps, h)
+        new = fft_poisson(b.reshape(rho.shape) - pol, h)
+        change = np.linalg.norm(new - phi) / max(np.linalg.norm(new), 1e-300)
+        hist.append(change)
+        phi = new
+        if change < tol:
+            break
+    return combined - combined.mean(), hist
