@@ -1,0 +1,173 @@
+/*
+ * gp.h - C ABI of the GB300 generalized-Poisson solver.
+ *
+ * Solves the generalized Poisson equation of Sanchez, Sued & Scherlis
+ * (arXiv:0904.4887), Eq. 3,
+ *
+ *        div( eps(r) grad phi(r) ) = -4 pi rho(r),
+ *
+ * on a periodic orthorhombic grid, with eps built from atomic coordinates
+ * (the position-dependent dielectric of Sec. II.B), optionally splitting the
+ * box into a "dry" part solved by FFT and a "wet" band solved by multigrid
+ * and coupling the two self-consistently (Sec. II.C, Scheme 1). Energy is
+ * Eq. 4 and forces are Eq. 11 (Appendix B).
+ *
+ * Conventions shared by every call:
+ *   - Fields are contiguous float64 arrays in DEVICE memory, x fastest:
+ *     value (i, j, k) at offset i + nx*(j + ny*k). Grid point (i,j,k) sits at
+ *     r = (i*hx, j*hy, k*hz), h = L/N.
+ *   - Atoms are DEVICE arrays: positions double[n][3] in Angstrom (any value;
+ *     wrapped into the cell internally), and Gaussian parameters
+ *     double[n][3] = (Z, sigma_core, sigma_cloud) in e and Angstrom.
+ *   - Units: Angstrom and elementary charge, Gaussian electrostatics (k = 1):
+ *     phi in e/A, energies in e^2/A.
+ *   - The caller owns every pointer it passes; the library owns its
+ *     workspaces (allocated in gp_create / gp_set_dielectric, freed in
+ *     gp_destroy). All work is ordered on the stream given to gp_create;
+ *     calls return after the results are complete on that stream unless
+ *     stated otherwise.
+ *   - Every call returns a gp_status; on failure gp_last_error() describes
+ *     it. A CUDA error leaves the context unusable (GP_ERR_CUDA).
+ */
+#ifndef GP_GB300_H
+#define GP_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gp_ctx gp_ctx;
+
+typedef enum {
+    GP_OK = 0,
+    GP_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported option */
+    GP_ERR_NOT_NEUTRAL = 2,   /* |sum rho| h^3 > 1e-10 sum|rho| h^3 */
+    GP_ERR_NOT_CONVERGED = 3, /* max_outer reached; phi holds the last iterate */
+    GP_ERR_DIVERGED = 4,      /* residual grew 1e3-fold or became non-finite */
+    GP_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    GP_ERR_CUDA = 6,          /* CUDA runtime error */
+    GP_ERR_OOM = 7,           /* device allocation failed */
+    GP_ERR_STATE = 8          /* call out of order (e.g. solve before set_dielectric) */
+} gp_status;
+
+/* Grid: each extent a power of two, or three times one, and >= 8; nx even. */
+typedef struct { int nx, ny, nz; } gp_grid;
+/* Orthorhombic periodic cell, Angstrom; every side > rcut of the dielectric. */
+typedef struct { double lx, ly, lz; } gp_cell;
+
+/* Solver and dielectric parameters; gp_default_params() fills the defaults. */
+typedef struct {
+    /* dielectric eps = 1 + (eps0-1) prod_a s(|r-R_a|), s(d) = (1+erf((d-r0)/w))/2,
+       product over atoms and periodic images with d < rcut (Sec. II.B). */
+    double eps0;          /* 78.36 */
+    double r0;            /* 2.5 A */
+    double w;             /* 0.5 A */
+    double rcut;          /* 6.0 A */
+    double dry_thresh;    /* 1e-3: a z-plane is dry when max(eps-1) < dry_thresh */
+    int split;            /* 0: multigrid on the whole box; 1: dry/wet split (Scheme 1) */
+    int n_dirichlet;      /* split: Dirichlet planes in the dry band (1 default; 0 = all the run allows) */
+    int precision;        /* 0: FP64 throughout; 1: FP32 multigrid inside FP64 defect correction */
+    int nu1, nu2;         /* red-black Gauss-Seidel sweeps before / after the coarse correction (2, 2) */
+    int levels;           /* multigrid levels; 0 = coarsen until the coarsest grid has <= 512 points */
+    int inner;            /* multigrid-preconditioned CG iterations per outer FP64 correction */
+    int max_outer;        /* outer FP64 corrections before GP_ERR_NOT_CONVERGED */
+} gp_params;
+
+#define GP_HISTORY 64
+typedef struct {
+    int outer_iterations;       /* FP64 residual evaluations in the last solve */
+    int inner_iterations;       /* preconditioned CG iterations in the last solve */
+    int vcycles;                /* V-cycles in the last solve */
+    int levels;                 /* multigrid levels in use */
+    int split_active;           /* 1 when the last solve used the dry/wet split */
+    int band_first;             /* first Dirichlet plane (split) */
+    int band_dirichlet;         /* number of Dirichlet planes (split) */
+    int dry_planes;             /* z-planes with max(eps-1) < dry_thresh */
+    double wet_fraction;        /* grid points handed to multigrid / all points */
+    double b_norm;              /* ||4 pi rho||_2 */
+    double residual;            /* final ||b - A phi|| / ||b|| (FP64) */
+    int history_len;
+    double history[GP_HISTORY]; /* relative residual after each outer step */
+} gp_stats;
+
+/* Fill *p with the defaults listed beside each field. */
+void gp_default_params(gp_params* p);
+
+/* Create a solver for `grid` and `cell`. `cuda_stream` is a cudaStream_t (or
+ * NULL for the legacy default stream) on the current device; all work of this
+ * context is ordered on it. Allocates the grid-sized workspaces.
+ * Errors: GP_ERR_INVALID_ARG (sizes), GP_ERR_OOM, GP_ERR_CUDA. */
+gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out);
+
+/* Build eps(R) on the grid from n_atoms positions (device double[n][3]),
+ * the per-level multigrid coefficients, the dry-plane flags and the wet band
+ * (Sec. II.B Eq. 9-10 idea with the erf switching function; Sec. II.C for the
+ * band). Must precede gp_solve and gp_energy_forces; call again whenever the
+ * atoms move. `params` is copied. Errors: GP_ERR_INVALID_ARG, GP_ERR_CUDA. */
+gp_status gp_set_dielectric(gp_ctx* ctx, const double* atoms_dev, int n_atoms,
+                            const gp_params* params);
+
+/* rho(r) = sum_a Z_a [g(r; sigma_core,a) - g(r; sigma_cloud,a)] - mean, with
+ * g the normalised Gaussian of standard deviation sigma, each truncated to
+ * |dx|,|dy|,|dz| < 8 sigma and summed over periodic images (the Gaussian
+ * ionic densities of Sec. II.A). Writes rho_dev (grid-sized). Independent of
+ * gp_set_dielectric. Errors: GP_ERR_INVALID_ARG (a 8 sigma window wider than
+ * the cell), GP_ERR_CUDA. */
+gp_status gp_build_rho(gp_ctx* ctx, const double* atoms_dev, const double* gauss_dev,
+                       int n_atoms, double* rho_dev);
+
+/* Solve A phi = -4 pi rho (Eq. 3, 7-point conservative discretisation with
+ * arithmetic face means) to ||b - A phi||_2 <= tol ||b||_2, b = -4 pi rho.
+ * phi_dev is read as the starting guess (warm start) and overwritten with the
+ * solution, returned with mean zero. rho must be neutral (its caller removes
+ * the mean). Errors: GP_ERR_STATE (no dielectric), GP_ERR_NOT_NEUTRAL,
+ * GP_ERR_NOT_CONVERGED / GP_ERR_DIVERGED (phi holds the last iterate and
+ * gp_get_stats the residuals), GP_ERR_INVALID_ARG (tol <= 0), GP_ERR_CUDA. */
+gp_status gp_solve(gp_ctx* ctx, const double* rho_dev, double* phi_dev, double tol);
+
+/* Energy and forces for the atoms of the last gp_set_dielectric, given the
+ * solution phi of gp_solve for rho:
+ *   energy_host[0] = E  = h^3/2 sum rho phi                       (Eq. 4)
+ *   energy_host[1] = E' = h^3/(8 pi) sum_faces eps_f (grad_f phi)^2 (Eq. 4)
+ *   forces_dev[a]  = -(G_eps_a + G_rho_a)  (device double[n][3], may be NULL)
+ * with G_eps_a = -h^3/(8 pi) sum_faces (d eps_f / d R_a)(grad_f phi)^2 and
+ * G_rho_a = h^3 sum_i phi_i d rho_i / d R_a (Eq. 11, Appendix B). gauss_dev
+ * (as in gp_build_rho) may be NULL, then G_rho is omitted (rho held fixed).
+ * Because the operator is symmetric, phi is its own adjoint: no extra solve.
+ * energy_host may be NULL. Errors: GP_ERR_STATE, GP_ERR_CUDA. */
+gp_status gp_energy_forces(gp_ctx* ctx, const double* phi_dev, const double* rho_dev,
+                           const double* gauss_dev, double* energy_host, double* forces_dev);
+
+/* Residual r = b - A phi (b = -4 pi rho) in FP64 into r_dev (grid-sized,
+ * device), and ||r||_2 / ||b||_2 into *rel_host (may be NULL). Uses the eps of
+ * the last gp_set_dielectric. Errors: GP_ERR_STATE, GP_ERR_CUDA. */
+gp_status gp_residual(gp_ctx* ctx, const double* rho_dev, const double* phi_dev,
+                      double* r_dev, double* rel_host);
+
+/* Vacuum solve L phi = src with the 7-point Laplacian (eps = 1), by the
+ * hand-written FFT (Eq. 15 with the symbol of the discrete operator); the
+ * k = 0 mode is dropped so phi has mean zero. src_dev, phi_dev grid-sized
+ * device arrays (may alias). Errors: GP_ERR_CUDA. */
+gp_status gp_fft_poisson(gp_ctx* ctx, const double* src_dev, double* phi_dev);
+
+/* Copy eps (FP64, grid-sized) of the last gp_set_dielectric into eps_dev. */
+gp_status gp_get_eps(gp_ctx* ctx, double* eps_dev);
+
+/* Per-plane max_xy(eps - 1) into plane_max_host[nz] (host memory). */
+gp_status gp_get_plane_max(gp_ctx* ctx, double* plane_max_host);
+
+/* Statistics of the last gp_set_dielectric / gp_solve. */
+gp_status gp_get_stats(const gp_ctx* ctx, gp_stats* out);
+
+/* Message describing the last error of this context ("" if none). */
+const char* gp_last_error(const gp_ctx* ctx);
+
+/* Free every workspace and the context. Accepts NULL. */
+void gp_destroy(gp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_GB300_H */

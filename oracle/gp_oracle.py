@@ -57,7 +57,7 @@ class DielectricParams:
     rcut: float = 6.0
 
 
-GAUSS_CUT_SIGMAS = 8.0   # Gaussians truncated at 8 sigma: exp(-32) ~ 1e-14 of the peak
+GAUSS_CUT_SIGMAS = 8.0   # Gaussian window half-width in sigmas: exp(-32) ~ 1e-14 of the peak
 
 
 def spacing(grid, cell):
@@ -167,15 +167,23 @@ def gaussian(d2, sigma):
     return np.exp(-d2 / (2.0 * sigma * sigma)) / (2.0 * math.pi * sigma * sigma) ** 1.5
 
 
+def _in_window(dx, dy, dz, rad):
+    """Truncation window of a Gaussian: |dx|, |dy|, |dz| all below cut*sigma
+    (a cube; the paper gives no truncation, and beyond 8 sigma the Gaussian
+    is below 1.3e-14 of its peak)."""
+    return (np.abs(dx) < rad) & (np.abs(dy) < rad) & (np.abs(dz) < rad)
+
+
 def charge_density_raw(grid, cell, pos, Z, sigma_core, sigma_cloud, cut=GAUSS_CUT_SIGMAS):
-    """rho~_i = sum_a Z_a [g(d; sigma_core,a) - g(d; sigma_cloud,a)], images within cut*sigma."""
+    """rho~_i = sum_a Z_a [g(d; sigma_core,a) - g(d; sigma_cloud,a)] over periodic
+    images, each Gaussian truncated to its window (_in_window)."""
     rho = np.zeros((grid[2], grid[1], grid[0]))
     for a, R in enumerate(pos):
         for sign, sig in ((1.0, sigma_core[a]), (-1.0, sigma_cloud[a])):
             rad = cut * sig
             for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, rad):
                 d2 = dx * dx + dy * dy + dz * dz
-                rho[sl] += np.where(d2 < rad * rad, sign * Z[a] * gaussian(d2, sig), 0.0)
+                rho[sl] += np.where(_in_window(dx, dy, dz, rad), sign * Z[a] * gaussian(d2, sig), 0.0)
     return rho
 
 
@@ -192,10 +200,12 @@ def charge_density_points(points, cell, pos, Z, sigma_core, sigma_cloud, cut=GAU
     out = np.zeros(len(points))
     for a, R in enumerate(pos):
         for n in itertools.product((-1, 0, 1), repeat=3):
-            d2 = np.sum((points - (R + np.asarray(n) * cell)) ** 2, axis=1)
+            dd = points - (R + np.asarray(n) * cell)
+            d2 = np.sum(dd ** 2, axis=1)
             for sign, sig in ((1.0, sigma_core[a]), (-1.0, sigma_cloud[a])):
                 rad = cut * sig
-                out += np.where(d2 < rad * rad, sign * Z[a] * gaussian(d2, sig), 0.0)
+                inside = _in_window(dd[:, 0], dd[:, 1], dd[:, 2], rad)
+                out += np.where(inside, sign * Z[a] * gaussian(d2, sig), 0.0)
     return out
 
 
@@ -207,7 +217,7 @@ def charge_density_gradient_atom(a, grid, cell, pos, Z, sigma_core, sigma_cloud,
         rad = cut * sig
         for sl, (dz, dy, dx) in _image_boxes(pos[a], grid, cell, rad):
             d2 = dx * dx + dy * dy + dz * dz
-            c = np.where(d2 < rad * rad, sign * Z[a] * gaussian(d2, sig) / (sig * sig), 0.0)
+            c = np.where(_in_window(dx, dy, dz, rad), sign * Z[a] * gaussian(d2, sig) / (sig * sig), 0.0)
             out[0][sl] += c * dx
             out[1][sl] += c * dy
             out[2][sl] += c * dz
