@@ -158,6 +158,21 @@ gp_status gp_get_eps(gp_ctx* ctx, double* eps_dev);
 /* Per-plane max_xy(eps - 1) into plane_max_host[nz] (host memory). */
 gp_status gp_get_plane_max(gp_ctx* ctx, double* plane_max_host);
 
+/* Host-only planner of the wet band (Sec. II.C reading): from per-plane dry
+ * flags dry[nz] (1 = dry), put the Dirichlet planes in the middle of the
+ * longest periodic run of dry planes, n_dirichlet of them (0 = as many as the
+ * run holds), reduced to 1 + m 2^(levels-1) so that the band of the other
+ * nz - nd planes coarsens levels-1 times. Writes *first (first Dirichlet
+ * plane) and *nd. Returns 1 if a band exists, 0 if no plane is dry, -1 on bad
+ * arguments. Needs no GPU. */
+int gp_plan_band(const int* dry, int nz, int levels, int n_dirichlet, int* first, int* nd);
+
+/* Host-only: multigrid levels for a grid (zper = 1 periodic z with nz planes,
+ * 0 Dirichlet z with nz interior planes): `requested` if the grid coarsens that
+ * far with <= 512 coarsest points, else (requested = 0) the fewest levels >= 2
+ * reaching <= 512 points. Returns -1 if impossible. Needs no GPU. */
+int gp_plan_levels(int nx, int ny, int nz, int zper, int requested);
+
 /* Statistics of the last gp_set_dielectric / gp_solve. */
 gp_status gp_get_stats(const gp_ctx* ctx, gp_stats* out);
 

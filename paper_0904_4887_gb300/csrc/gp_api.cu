@@ -1,0 +1,768 @@
+// C ABI of the solver (declared in include/gp.h) and its host-side driver:
+// workspace ownership, the multigrid hierarchy, the wet-band planner, the
+// V-cycle, the preconditioned CG inner solve and the FP64 outer defect
+// correction that couples the dry FFT solution to the wet multigrid band.
+#include "gp_common.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace gp;
+
+namespace {
+
+// ---------------------------------------------------------------- helpers
+struct Err {
+    gp_status st;
+    std::string msg;
+};
+
+#define GP_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t _e = (call);                                                           \
+        if (_e != cudaSuccess) throw Err{GP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)}; \
+    } while (0)
+
+#define GP_CHECK_LAUNCH() GP_CUDA(cudaGetLastError())
+
+template <typename T>
+struct Hier {
+    int L = 0;
+    int nx = 0, ny = 0, nz = 0, zper = 1;      // level-0 interior dims
+    LV<T> lv[16];
+    T* u[16] = {};
+    T* f[16] = {};
+    T* res[16] = {};
+    T* cx[16] = {};
+    T* cy[16] = {};
+    T* cz[16] = {};
+    T* eps0 = nullptr;                          // owned level-0 cell eps (band only)
+    T* x = nullptr; T* r = nullptr; T* p = nullptr; T* q = nullptr; T* z = nullptr;   // PCG, level 0
+    T* minv = nullptr;
+    int nc = 0;
+    std::vector<void*> allocs;
+    bool ready = false;
+};
+
+template <typename T>
+T* alloc_level(Hier<T>& H, int nx, int ny, int nz) {
+    const size_t pl = (size_t)nx * ny;
+    void* ptr = nullptr;
+    const size_t bytes = pl * (nz + 2) * sizeof(T);
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc of a multigrid level failed"};
+    H.allocs.push_back(ptr);
+    GP_CUDA(cudaMemset(ptr, 0, bytes));
+    return reinterpret_cast<T*>(ptr) + pl;
+}
+
+template <typename T>
+void free_hier(Hier<T>& H) {
+    for (void* p : H.allocs) cudaFree(p);
+    H = Hier<T>();
+}
+
+template <typename T>
+size_t level_bytes(const LV<T>& L) { return (size_t)L.nx * L.ny * (L.nz + 2) * sizeof(T); }
+
+template <typename T>
+T* lbase(const LV<T>& L, T* p) { return p - (size_t)L.nx * L.ny; }
+
+// level plan: number of levels such that the coarsest grid has <= kMaxCoarse points
+int plan_levels(int nx, int ny, int nz, int zper, int requested, std::string& why) {
+    auto dims_ok = [&](int l, long& pts) {
+        const int m = 1 << l;
+        if (nx % m || ny % m) return false;
+        const int cx = nx / m, cy = ny / m;
+        int cz;
+        if (zper) {
+            if (nz % m) return false;
+            cz = nz / m;
+            if (cz < 2) return false;
+        } else {
+            if ((nz + 1) % m) return false;
+            cz = (nz + 1) / m - 1;
+            if (cz < 1) return false;
+        }
+        if (cx < 2 || cy < 2) return false;
+        pts = (long)cx * cy * cz;
+        return true;
+    };
+    if (requested > 0) {
+        long pts = 0;
+        if (requested > 16 || !dims_ok(requested - 1, pts)) { why = "grid does not coarsen to the requested levels"; return -1; }
+        if (pts > kMaxCoarse) { why = "coarsest grid of the requested levels exceeds 512 points"; return -1; }
+        return requested;
+    }
+    for (int l = 1; l < 16; ++l) {
+        long pts = 0;
+        if (!dims_ok(l, pts)) break;
+        if (pts <= kMaxCoarse) return l + 1;
+    }
+    why = "grid cannot be coarsened to <= 512 points";
+    return -1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- context
+struct gp_ctx {
+    Geo g{};
+    long n = 0;
+    cudaStream_t s = nullptr;
+    gp_params prm{};
+    bool have_eps = false;
+    std::string err;
+    gp_stats stats{};
+
+    // device fields
+    double* eps64 = nullptr;
+    double* pe64 = nullptr;
+    float* eps32 = nullptr;
+    double* plane_max = nullptr;
+    double* atoms = nullptr;       // copy of the positions of the last set_dielectric
+    int n_atoms = 0;
+    int atoms_cap = 0;
+    double* partial = nullptr;     // kReduceBlocks * 4
+    double* scal = nullptr;        // device scalars
+    int* dstatus = nullptr;
+    double* forces_S = nullptr;
+    double* forces_T = nullptr;
+    int forces_cap = 0;
+    double* gmat = nullptr;        // Gauss-Jordan workspace (2 * 512^2)
+
+    // solver state
+    Hier<float> fullF, bandF;
+    Hier<double> fullD, bandD;
+    FFTPlan* fft = nullptr;
+    void* fft_work = nullptr;
+    size_t fft_work_bytes = 0;
+    void* rfull = nullptr;         // full-box residual in the working precision (split)
+    void* evac = nullptr;          // full-box vacuum correction (split)
+    int full_levels = 0;
+    int band_first = -1, band_nd = 0, band_nz = 0, band_first_interior = 0;
+    bool split_ok = false;
+    std::vector<void*> misc;
+};
+
+namespace {
+
+void* dalloc(gp_ctx* c, size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+    c->misc.push_back(p);
+    GP_CUDA(cudaMemset(p, 0, bytes));
+    return p;
+}
+
+double sum_host(gp_ctx* c, int ncomp, double* out) {
+    launch_finalize(c->partial, kReduceBlocks, ncomp, c->scal + 8, c->s);
+    GP_CHECK_LAUNCH();
+    GP_CUDA(cudaMemcpyAsync(out, c->scal + 8, sizeof(double) * ncomp, cudaMemcpyDeviceToHost, c->s));
+    GP_CUDA(cudaStreamSynchronize(c->s));
+    return out[0];
+}
+
+// ------------------------------------------------------------ hierarchy setup
+template <typename T>
+void alloc_hier(gp_ctx* c, Hier<T>& H, int nx, int ny, int nz, int zper, int levels, const T* eps_level0,
+                bool own_eps) {
+    const bool realloc = !H.ready || H.nx != nx || H.ny != ny || H.nz != nz || H.zper != zper || H.L != levels;
+    if (realloc) {
+        free_hier(H);
+        H.nx = nx; H.ny = ny; H.nz = nz; H.zper = zper; H.L = levels;
+        int lx = nx, ly = ny, lz = nz;
+        double hx = c->g.hx, hy = c->g.hy, hz = c->g.hz;
+        for (int l = 0; l < levels; ++l) {
+            LV<T>& L = H.lv[l];
+            L.nx = lx; L.ny = ly; L.nz = lz; L.zper = zper;
+            L.ihx2 = (T)(1.0 / (hx * hx)); L.ihy2 = (T)(1.0 / (hy * hy)); L.ihz2 = (T)(1.0 / (hz * hz));
+            L.cell = (l == 0);
+            L.eps = nullptr; L.cx = L.cy = L.cz = nullptr;
+            if (l > 0) {
+                H.cx[l] = alloc_level(H, lx, ly, lz);
+                H.cy[l] = alloc_level(H, lx, ly, lz);
+                H.cz[l] = alloc_level(H, lx, ly, lz);
+                L.cx = H.cx[l]; L.cy = H.cy[l]; L.cz = H.cz[l];
+                H.u[l] = alloc_level(H, lx, ly, lz);
+                H.f[l] = alloc_level(H, lx, ly, lz);
+            }
+            if (l < levels - 1) H.res[l] = alloc_level(H, lx, ly, lz);
+            lx /= 2; ly /= 2;
+            lz = zper ? lz / 2 : (lz + 1) / 2 - 1;
+            hx *= 2; hy *= 2; hz *= 2;
+        }
+        H.x = alloc_level(H, nx, ny, nz);
+        H.r = alloc_level(H, nx, ny, nz);
+        H.p = alloc_level(H, nx, ny, nz);
+        H.q = alloc_level(H, nx, ny, nz);
+        H.z = alloc_level(H, nx, ny, nz);
+        if (own_eps) H.eps0 = alloc_level(H, nx, ny, nz);
+        const LV<T>& C = H.lv[levels - 1];
+        H.nc = C.nx * C.ny * C.nz;
+        void* m = nullptr;
+        if (cudaMalloc(&m, sizeof(T) * (size_t)H.nc * H.nc) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+        H.allocs.push_back(m);
+        H.minv = reinterpret_cast<T*>(m);
+        H.ready = true;
+    }
+    H.lv[0].eps = own_eps ? H.eps0 : eps_level0;
+}
+
+// coarse-level face coefficients and the dense coarsest inverse, from level 0's eps
+template <typename T>
+void coarse_coeffs(gp_ctx* c, Hier<T>& H) {
+    const int levels = H.L;
+    // coefficients of every coarse level from the level above
+    for (int l = 1; l < levels; ++l) {
+        const LV<T>& F = H.lv[l - 1];
+        LV<T>& C = H.lv[l];
+        launch_coarsen_faces<T>(F, C.nx, C.ny, C.nz, H.cx[l], H.cy[l], H.cz[l], c->s);
+        GP_CHECK_LAUNCH();
+    }
+    // dense inverse of the coarsest operator
+    const LV<T>& C = H.lv[levels - 1];
+    if (levels == 1) throw Err{GP_ERR_INVALID_ARG, "multigrid needs at least two levels"};
+    launch_coarse_matrix<T>(C, c->gmat, c->s);
+    GP_CHECK_LAUNCH();
+    launch_gauss_jordan(c->gmat, H.nc, c->dstatus, c->s);
+    GP_CHECK_LAUNCH();
+    int st = 0;
+    GP_CUDA(cudaMemcpyAsync(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    GP_CUDA(cudaStreamSynchronize(c->s));
+    if (st != 0) throw Err{GP_ERR_INVALID_ARG, "coarsest multigrid operator is singular"};
+    launch_store_inverse<T>(c->gmat + (size_t)H.nc * H.nc, H.nc, H.minv, c->s);
+    GP_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------ V-cycle and PCG
+template <typename T>
+void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
+    const int L = H.L;
+    for (int l = 0; l < L - 1; ++l) {
+        const LV<T>& V = H.lv[l];
+        T* u = l == 0 ? u0 : H.u[l];
+        const T* f = l == 0 ? f0 : H.f[l];
+        GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
+        for (int it = 0; it < c->prm.nu1; ++it) {
+            launch_rbgs<T>(V, u, f, 0, c->s);
+            launch_rbgs<T>(V, u, f, 1, c->s);
+        }
+        launch_residual<T>(V, u, f, H.res[l], c->s);
+        launch_restrict<T>(V, H.res[l], H.lv[l + 1], H.f[l + 1], c->s);
+    }
+    launch_coarse_solve<T>(H.lv[L - 1], H.minv, H.nc, H.f[L - 1], H.u[L - 1], c->s);
+    for (int l = L - 2; l >= 0; --l) {
+        const LV<T>& V = H.lv[l];
+        T* u = l == 0 ? u0 : H.u[l];
+        const T* f = l == 0 ? f0 : H.f[l];
+        launch_prolong_add<T>(V, u, H.lv[l + 1], H.u[l + 1], c->s);
+        for (int it = 0; it < c->prm.nu2; ++it) {
+            launch_rbgs<T>(V, u, f, 1, c->s);
+            launch_rbgs<T>(V, u, f, 0, c->s);
+        }
+    }
+    GP_CHECK_LAUNCH();
+    c->stats.vcycles++;
+}
+
+// x ~ A^-1 r by `iters` multigrid-preconditioned CG steps from x = 0; r is overwritten
+template <typename T>
+void pcg(gp_ctx* c, Hier<T>& H, int iters) {
+    const LV<T>& V = H.lv[0];
+    GP_CUDA(cudaMemsetAsync(lbase(V, H.x), 0, level_bytes(V), c->s));
+    vcycle(c, H, H.z, H.r);
+    int cur = 0;
+    launch_dot<T>(V, H.r, H.z, c->partial, c->s);
+    launch_finalize(c->partial, kReduceBlocks, 1, c->scal + cur, c->s);
+    launch_copy_level<T>(V, H.p, H.z, c->s);
+    for (int it = 0; it < iters; ++it) {
+        launch_applyA_dot<T>(V, H.p, H.q, c->partial, c->s);
+        launch_finalize(c->partial, kReduceBlocks, 1, c->scal + 1, c->s);
+        launch_update_xr<T>(V, H.x, H.r, H.p, H.q, c->scal, cur, 1, c->s);
+        c->stats.inner_iterations++;
+        if (it == iters - 1) break;
+        vcycle(c, H, H.z, H.r);
+        const int nxt = 2 - cur;
+        launch_dot<T>(V, H.r, H.z, c->partial, c->s);
+        launch_finalize(c->partial, kReduceBlocks, 1, c->scal + nxt, c->s);
+        launch_update_p<T>(V, H.p, H.z, c->scal, nxt, cur, c->s);
+        cur = nxt;
+    }
+    GP_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------ wet band planner
+// Longest periodic run of dry planes; n_dirichlet planes centred in it, reduced
+// to 1 + m 2^(levels-1) so the band (the other planes) coarsens levels-1 times.
+bool plan_band(const std::vector<int>& dry, int levels, int n_dirichlet, int& first, int& nd) {
+    const int nz = (int)dry.size();
+    int ndry = 0;
+    for (int v : dry) ndry += v;
+    if (ndry == 0) return false;
+    int run_start = 0, run_len = 0;
+    if (ndry == nz) {
+        run_start = 0; run_len = nz;
+    } else {
+        int k0 = 0;
+        while (dry[k0]) ++k0;                       // a wet plane: runs cannot wrap past it
+        int cur_start = -1, cur_len = 0;
+        for (int t = 1; t <= nz; ++t) {
+            const int k = (k0 + t) % nz;
+            if (dry[k]) {
+                if (cur_len == 0) cur_start = k;
+                ++cur_len;
+                if (cur_len > run_len) { run_len = cur_len; run_start = cur_start; }
+            } else {
+                cur_len = 0;
+            }
+        }
+    }
+    const int step = 1 << (levels - 1);
+    const int want = n_dirichlet <= 0 ? run_len : std::min(n_dirichlet, run_len);
+    nd = 1 + ((want - 1) / step) * step;
+    if (nd >= nz) nd = 1;
+    first = (run_start + (run_len - nd) / 2) % nz;
+    return true;
+}
+
+// ------------------------------------------------------------ outer solve
+template <typename T>
+Hier<T>& full_hier(gp_ctx* c);
+template <> Hier<float>& full_hier<float>(gp_ctx* c) { return c->fullF; }
+template <> Hier<double>& full_hier<double>(gp_ctx* c) { return c->fullD; }
+template <typename T>
+Hier<T>& band_hier(gp_ctx* c);
+template <> Hier<float>& band_hier<float>(gp_ctx* c) { return c->bandF; }
+template <> Hier<double>& band_hier<double>(gp_ctx* c) { return c->bandD; }
+
+template <typename T>
+const T* eps_T(gp_ctx* c);
+template <> const float* eps_T<float>(gp_ctx* c) { return c->eps32; }
+template <> const double* eps_T<double>(gp_ctx* c) { return c->eps64; }
+
+template <typename T>
+void setup_solver(gp_ctx* c) {
+    Hier<T>& F = full_hier<T>(c);
+    alloc_hier<T>(c, F, c->g.nx, c->g.ny, c->g.nz, 1, c->full_levels, eps_T<T>(c), false);
+    coarse_coeffs<T>(c, F);
+    c->split_ok = false;
+    c->stats.wet_fraction = 1.0;
+    if (c->prm.split) {
+        std::vector<double> pm(c->g.nz);
+        GP_CUDA(cudaMemcpyAsync(pm.data(), c->plane_max, sizeof(double) * c->g.nz, cudaMemcpyDeviceToHost, c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        std::vector<int> dry(c->g.nz);
+        for (int k = 0; k < c->g.nz; ++k) dry[k] = pm[k] < c->prm.dry_thresh ? 1 : 0;
+        int first = -1, nd = 0;
+        if (plan_band(dry, c->full_levels, c->prm.n_dirichlet, first, nd)) {
+            c->band_first = first;
+            c->band_nd = nd;
+            c->band_nz = c->g.nz - nd;
+            c->band_first_interior = (first + nd) % c->g.nz;
+            Hier<T>& B = band_hier<T>(c);
+            alloc_hier<T>(c, B, c->g.nx, c->g.ny, c->band_nz, 0, c->full_levels, nullptr, true);
+            // the band's level-0 eps, walls included, then its coarse levels
+            launch_band_eps<T>(c->g, eps_T<T>(c), c->band_first_interior, c->band_nz, B.eps0, c->s);
+            GP_CHECK_LAUNCH();
+            coarse_coeffs<T>(c, B);
+            if (!c->rfull) c->rfull = dalloc(c, (size_t)c->n * sizeof(double));
+            if (!c->evac) c->evac = dalloc(c, (size_t)c->n * sizeof(double));
+            if (!c->fft) {
+                c->fft = fft_create(c->g, c->s);
+                if (!c->fft) throw Err{GP_ERR_INVALID_ARG, "grid extents must be 2^a 3^b for the FFT"};
+            }
+            const size_t wb = fft_workspace_bytes(c->g, true);
+            if (!c->fft_work) { c->fft_work = dalloc(c, wb); c->fft_work_bytes = wb; }
+            c->split_ok = true;
+            c->stats.wet_fraction = (double)c->band_nz / c->g.nz;
+        }
+    }
+    c->stats.split_active = c->split_ok ? 1 : 0;
+    c->stats.band_first = c->split_ok ? c->band_first : -1;
+    c->stats.band_dirichlet = c->split_ok ? c->band_nd : 0;
+}
+
+template <typename T>
+gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
+    Hier<T>& F = full_hier<T>(c);
+    Hier<T>& B = band_hier<T>(c);
+    const bool split = c->split_ok;
+    gp_stats& st = c->stats;
+    st.outer_iterations = 0; st.inner_iterations = 0; st.vcycles = 0; st.history_len = 0;
+    st.residual = NAN;
+    double h3[4];
+    launch_rho_stats(c->n, rho, c->partial, c->s);
+    GP_CHECK_LAUNCH();
+    launch_finalize(c->partial, kReduceBlocks, 3, c->scal + 8, c->s);
+    GP_CUDA(cudaMemcpyAsync(h3, c->scal + 8, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->s));
+    GP_CUDA(cudaStreamSynchronize(c->s));
+    if (!(std::fabs(h3[0]) <= 1e-10 * h3[1])) {
+        if (!std::isfinite(h3[0])) throw Err{GP_ERR_INVALID_ARG, "rho is not finite"};
+        throw Err{GP_ERR_NOT_NEUTRAL, "rho is not neutral: |sum rho| > 1e-10 sum |rho|"};
+    }
+    const double nb = 4.0 * kPi * std::sqrt(h3[2]);
+    st.b_norm = nb;
+    if (nb == 0.0) {
+        GP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->n, c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        st.residual = 0.0;
+        return GP_OK;
+    }
+    T* rT = split ? reinterpret_cast<T*>(c->rfull) : F.r;
+    T* ev = reinterpret_cast<T*>(c->evac);
+    double best = INFINITY;
+    gp_status result = GP_ERR_NOT_CONVERGED;
+    for (int it = 0; it < c->prm.max_outer; ++it) {
+        if (it > 0) {
+            if (split) launch_update_phi<T>(c->g, phi, ev, B.x, c->band_first_interior, c->band_nz, c->s);
+            else launch_update_phi<T>(c->g, phi, F.x, (const T*)nullptr, 0, 0, c->s);
+            GP_CHECK_LAUNCH();
+        }
+        launch_residual64<T>(c->g, phi, rho, c->eps64, rT, c->partial, c->s);
+        GP_CHECK_LAUNCH();
+        double s2[2];
+        sum_host(c, 2, s2);
+        const double rn = std::sqrt(s2[0]) / nb;
+        st.outer_iterations++;
+        if (st.history_len < GP_HISTORY) st.history[st.history_len++] = rn;
+        st.residual = rn;
+        if (!std::isfinite(rn) || (it > 0 && rn > 1e3 * best)) { result = GP_ERR_DIVERGED; break; }
+        best = std::min(best, rn);
+        if (rn <= tol) { result = GP_OK; break; }
+        if (it == c->prm.max_outer - 1) break;
+        if (split) {
+            fft_poisson<T>(c->fft, rT, ev, c->fft_work, c->s);
+            GP_CHECK_LAUNCH();
+            launch_band_rhs<T>(c->g, eps_T<T>(c), rT, ev, c->band_first_interior, c->band_nz, B.r, c->s);
+            GP_CHECK_LAUNCH();
+            pcg<T>(c, B, c->prm.inner);
+        } else {
+            pcg<T>(c, F, c->prm.inner);
+        }
+    }
+    // gauge: the last residual pass summed phi into scal[9]
+    launch_sub_mean(c->n, phi, c->scal + 9, 1.0 / (double)c->n, c->s);
+    GP_CHECK_LAUNCH();
+    GP_CUDA(cudaStreamSynchronize(c->s));
+    if (result == GP_ERR_NOT_CONVERGED) c->err = "not converged within max_outer";
+    if (result == GP_ERR_DIVERGED) c->err = "residual diverged";
+    return result;
+}
+
+gp_status fail(gp_ctx* c, const Err& e) {
+    if (c) c->err = e.msg;
+    return e.st;
+}
+
+bool good_extent(int n) {
+    if (n < 8) return false;
+    while (n % 2 == 0) n /= 2;
+    if (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+void gp_default_params(gp_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->eps0 = 78.36;
+    p->r0 = 2.5;
+    p->w = 0.5;
+    p->rcut = 6.0;
+    p->dry_thresh = 1e-3;
+    p->split = 0;
+    p->n_dirichlet = 1;
+    p->precision = 1;
+    p->nu1 = 2;
+    p->nu2 = 2;
+    p->levels = 0;
+    p->inner = 4;
+    p->max_outer = 60;
+}
+
+gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out) {
+    if (!out) return GP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!good_extent(grid.nx) || !good_extent(grid.ny) || !good_extent(grid.nz) || grid.nx % 2)
+        return GP_ERR_INVALID_ARG;
+    if (!(cell.lx > 0 && cell.ly > 0 && cell.lz > 0)) return GP_ERR_INVALID_ARG;
+    gp_ctx* c = new gp_ctx();
+    try {
+        c->g.nx = grid.nx; c->g.ny = grid.ny; c->g.nz = grid.nz;
+        c->g.lx = cell.lx; c->g.ly = cell.ly; c->g.lz = cell.lz;
+        c->g.hx = cell.lx / grid.nx; c->g.hy = cell.ly / grid.ny; c->g.hz = cell.lz / grid.nz;
+        c->n = (long)grid.nx * grid.ny * grid.nz;
+        c->s = reinterpret_cast<cudaStream_t>(cuda_stream);
+        gp_default_params(&c->prm);
+        c->eps64 = (double*)dalloc(c, sizeof(double) * c->n);
+        c->pe64 = (double*)dalloc(c, sizeof(double) * c->n);
+        c->eps32 = (float*)dalloc(c, sizeof(float) * c->n);
+        c->plane_max = (double*)dalloc(c, sizeof(double) * grid.nz);
+        c->partial = (double*)dalloc(c, sizeof(double) * kReduceBlocks * 4);
+        c->scal = (double*)dalloc(c, sizeof(double) * 32);
+        c->dstatus = (int*)dalloc(c, sizeof(int) * 4);
+        c->gmat = (double*)dalloc(c, sizeof(double) * 2 * kMaxCoarse * kMaxCoarse);
+    } catch (const Err& e) {
+        gp_destroy(c);
+        return e.st;
+    }
+    *out = c;
+    return GP_OK;
+}
+
+gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, const gp_params* params) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!params || n_atoms < 0 || (n_atoms > 0 && !atoms_dev)) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        gp_params p = *params;
+        if (!(p.rcut > 0 && p.rcut <= c->g.lx && p.rcut <= c->g.ly && p.rcut <= c->g.lz))
+            throw Err{GP_ERR_INVALID_ARG, "rcut must be positive and not exceed the cell"};
+        if (!(p.w > 0) || !(p.eps0 >= 1.0)) throw Err{GP_ERR_INVALID_ARG, "need w > 0 and eps0 >= 1"};
+        if (p.precision != 0 && p.precision != 1) throw Err{GP_ERR_INVALID_ARG, "precision must be 0 or 1"};
+        if (p.nu1 < 0 || p.nu2 < 0 || p.nu1 + p.nu2 == 0 || p.inner < 1 || p.max_outer < 1)
+            throw Err{GP_ERR_INVALID_ARG, "need nu1+nu2 >= 1, inner >= 1, max_outer >= 1"};
+        std::string why;
+        const int L = plan_levels(c->g.nx, c->g.ny, c->g.nz, 1, p.levels, why);
+        if (L < 2) throw Err{GP_ERR_INVALID_ARG, why.empty() ? "grid too small for multigrid" : why};
+        c->prm = p;
+        c->full_levels = L;
+        if (n_atoms > c->atoms_cap) {
+            void* a = nullptr;
+            if (cudaMalloc(&a, sizeof(double) * 3 * n_atoms) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+            if (c->atoms) cudaFree(c->atoms);
+            c->atoms = (double*)a;
+            c->atoms_cap = n_atoms;
+        }
+        c->n_atoms = n_atoms;
+        if (n_atoms > 0)
+            GP_CUDA(cudaMemcpyAsync(c->atoms, atoms_dev, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToDevice, c->s));
+        Atoms at{c->atoms, nullptr, n_atoms};
+        DielParams dp{p.eps0, p.r0, p.w, p.rcut};
+        launch_build_eps(c->g, at, dp, c->eps64, c->pe64, c->eps32, c->s);
+        GP_CHECK_LAUNCH();
+        launch_plane_max(c->g, c->eps64, c->plane_max, c->s);
+        GP_CHECK_LAUNCH();
+        if (p.precision == 1) setup_solver<float>(c);
+        else setup_solver<double>(c);
+        std::vector<double> pm(c->g.nz);
+        GP_CUDA(cudaMemcpyAsync(pm.data(), c->plane_max, sizeof(double) * c->g.nz, cudaMemcpyDeviceToHost, c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        int nd = 0;
+        for (double v : pm) nd += v < p.dry_thresh;
+        c->stats.dry_planes = nd;
+        c->stats.levels = L;
+        c->have_eps = true;
+        c->err.clear();
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_build_rho(gp_ctx* c, const double* atoms_dev, const double* gauss_dev, int n_atoms, double* rho_dev) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!rho_dev || n_atoms < 0 || (n_atoms > 0 && (!atoms_dev || !gauss_dev)))
+            throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        const double cut = 8.0;
+        if (n_atoms > 0) {
+            std::vector<double> gh(3 * (size_t)n_atoms);
+            GP_CUDA(cudaMemcpyAsync(gh.data(), gauss_dev, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToHost, c->s));
+            GP_CUDA(cudaStreamSynchronize(c->s));
+            const double lmin = std::min(c->g.lx, std::min(c->g.ly, c->g.lz));
+            for (int a = 0; a < n_atoms; ++a)
+                for (int w = 1; w <= 2; ++w)
+                    if (!(gh[3 * a + w] > 0) || cut * gh[3 * a + w] > lmin)
+                        throw Err{GP_ERR_INVALID_ARG, "Gaussian width must be positive with 8 sigma <= the cell"};
+        }
+        Atoms at{atoms_dev, gauss_dev, n_atoms};
+        launch_build_rho_raw(c->g, at, cut, rho_dev, c->s);
+        GP_CHECK_LAUNCH();
+        launch_rho_stats(c->n, rho_dev, c->partial, c->s);
+        launch_finalize(c->partial, kReduceBlocks, 3, c->scal + 12, c->s);
+        launch_sub_mean(c->n, rho_dev, c->scal + 12, 1.0 / (double)c->n, c->s);
+        GP_CHECK_LAUNCH();
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_solve(gp_ctx* c, const double* rho_dev, double* phi_dev, double tol) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!rho_dev || !phi_dev || !(tol > 0)) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_solve"};
+        return c->prm.precision == 1 ? solve_impl<float>(c, rho_dev, phi_dev, tol)
+                                     : solve_impl<double>(c, rho_dev, phi_dev, tol);
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_dev, const double* gauss_dev,
+                           double* energy_host, double* forces_dev) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!phi_dev || !rho_dev) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_energy_forces"};
+        const double dv = c->g.hx * c->g.hy * c->g.hz;
+        if (energy_host) {
+            launch_energy(c->g, rho_dev, phi_dev, c->eps64, c->partial, c->s);
+            GP_CHECK_LAUNCH();
+            double e2[2];
+            sum_host(c, 2, e2);
+            energy_host[0] = 0.5 * dv * e2[0];
+            energy_host[1] = dv / (8.0 * kPi) * e2[1];
+        }
+        if (forces_dev && c->n_atoms > 0) {
+            const int n = c->n_atoms;
+            if (n > c->forces_cap) {
+                if (c->forces_S) cudaFree(c->forces_S);
+                if (c->forces_T) cudaFree(c->forces_T);
+                c->forces_S = nullptr; c->forces_T = nullptr;
+                if (cudaMalloc(&c->forces_S, sizeof(double) * 3 * n) != cudaSuccess ||
+                    cudaMalloc(&c->forces_T, sizeof(double) * 3 * n) != cudaSuccess)
+                    throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+                c->forces_cap = n;
+            }
+            GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
+            GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->s));
+            Atoms at{c->atoms, gauss_dev, n};
+            DielParams dp{c->prm.eps0, c->prm.r0, c->prm.w, c->prm.rcut};
+            launch_forces_eps(c->g, at, dp, phi_dev, c->pe64, c->forces_S, c->s);
+            GP_CHECK_LAUNCH();
+            if (gauss_dev) {
+                launch_forces_rho(c->g, at, 8.0, phi_dev, c->forces_T, c->s);
+                GP_CHECK_LAUNCH();
+            }
+            launch_forces_finish(c->forces_S, gauss_dev ? c->forces_T : nullptr, n, -dv / (8.0 * kPi), dv,
+                                 forces_dev, c->s);
+            GP_CHECK_LAUNCH();
+        }
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_residual(gp_ctx* c, const double* rho_dev, const double* phi_dev, double* r_dev, double* rel_host) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!rho_dev || !phi_dev || !r_dev) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_residual"};
+        launch_residual64<double>(c->g, phi_dev, rho_dev, c->eps64, r_dev, c->partial, c->s);
+        GP_CHECK_LAUNCH();
+        double s2[2];
+        sum_host(c, 2, s2);
+        if (rel_host) {
+            launch_rho_stats(c->n, rho_dev, c->partial, c->s);
+            GP_CHECK_LAUNCH();
+            double h3[3];
+            sum_host(c, 3, h3);
+            const double nb = 4.0 * kPi * std::sqrt(h3[2]);
+            *rel_host = nb > 0 ? std::sqrt(s2[0]) / nb : std::sqrt(s2[0]);
+        }
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_fft_poisson(gp_ctx* c, const double* src_dev, double* phi_dev) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!src_dev || !phi_dev) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        if (!c->fft) {
+            c->fft = fft_create(c->g, c->s);
+            if (!c->fft) throw Err{GP_ERR_INVALID_ARG, "grid extents must be 2^a 3^b for the FFT"};
+        }
+        if (!c->fft_work) {
+            const size_t wb = fft_workspace_bytes(c->g, true);
+            c->fft_work = dalloc(c, wb);
+            c->fft_work_bytes = wb;
+        }
+        fft_poisson<double>(c->fft, src_dev, phi_dev, c->fft_work, c->s);
+        GP_CHECK_LAUNCH();
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_get_eps(gp_ctx* c, double* eps_dev) {
+    if (!c || !eps_dev) return GP_ERR_INVALID_ARG;
+    if (!c->have_eps) { c->err = "no dielectric"; return GP_ERR_STATE; }
+    try {
+        GP_CUDA(cudaMemcpyAsync(eps_dev, c->eps64, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_get_plane_max(gp_ctx* c, double* out) {
+    if (!c || !out) return GP_ERR_INVALID_ARG;
+    if (!c->have_eps) { c->err = "no dielectric"; return GP_ERR_STATE; }
+    try {
+        GP_CUDA(cudaMemcpyAsync(out, c->plane_max, sizeof(double) * c->g.nz, cudaMemcpyDeviceToHost, c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_get_stats(const gp_ctx* c, gp_stats* out) {
+    if (!c || !out) return GP_ERR_INVALID_ARG;
+    *out = c->stats;
+    return GP_OK;
+}
+
+const char* gp_last_error(const gp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int gp_plan_band(const int* dry, int nz, int levels, int n_dirichlet, int* first, int* nd) {
+    if (!dry || nz < 1 || levels < 1 || levels > 16 || !first || !nd) return -1;
+    std::vector<int> d(dry, dry + nz);
+    for (int& v : d) v = v ? 1 : 0;
+    int f = -1, n = 0;
+    const bool ok = plan_band(d, levels, n_dirichlet, f, n);
+    *first = ok ? f : -1;
+    *nd = ok ? n : 0;
+    return ok ? 1 : 0;
+}
+
+int gp_plan_levels(int nx, int ny, int nz, int zper, int requested) {
+    if (nx < 1 || ny < 1 || nz < 1) return -1;
+    std::string why;
+    return plan_levels(nx, ny, nz, zper ? 1 : 0, requested, why);
+}
+
+void gp_destroy(gp_ctx* c) {
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    free_hier(c->fullF);
+    free_hier(c->bandF);
+    free_hier(c->fullD);
+    free_hier(c->bandD);
+    if (c->fft) fft_destroy(c->fft);
+    for (void* p : c->misc) cudaFree(p);
+    if (c->atoms) cudaFree(c->atoms);
+    if (c->forces_S) cudaFree(c->forces_S);
+    if (c->forces_T) cudaFree(c->forces_T);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal declarations shared by the CUDA translation units of the solver.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "gp.h"
+
+namespace gp {
+
+constexpr int kReduceBlocks = 608;      // 4 x 152 SMs: fixed partial count, deterministic sums
+constexpr int kReduceThreads = 256;
+constexpr int kMaxCoarse = 512;         // largest coarsest grid solved by a dense inverse
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- level view
+// One multigrid level. Arrays are addressed with a base pointer at plane 0 and
+// own one halo plane below (k = -1) and one above (k = nz): for Dirichlet
+// levels (zper == 0) the halos hold the boundary values; for periodic levels
+// they are unused and k wraps.
+template <typename T>
+struct LV {
+    int nx, ny, nz, zper;
+    T ihx2, ihy2, ihz2;           // 1/h^2 per axis
+    const T* eps;                 // cell eps (cell == 1): face = (e_i + e_j)/2 * ih2
+    const T* cx;                  // face coefficients incl. 1/h^2 (cell == 0);
+    const T* cy;                  //   c?[i] is the face between i and i+1 along ?
+    const T* cz;                  //   cz valid for k = -1 .. nz-1
+    int cell;
+};
+
+struct Atoms {
+    const double* pos;     // [n][3]
+    const double* gauss;   // [n][3] = Z, sigma_core, sigma_cloud (may be null)
+    int n;
+};
+
+struct Geo {
+    int nx, ny, nz;
+    double hx, hy, hz;
+    double lx, ly, lz;
+};
+
+struct DielParams {
+    double eps0, r0, w, rcut;
+};
+
+__host__ __device__ inline long plane_of(int nx, int ny) { return (long)nx * ny; }
+
+// ---------------------------------------------------------------- launchers
+// fields (k_fields.cu)
+void launch_build_eps(const Geo& g, Atoms at, DielParams p, double* eps64, double* pe64,
+                      float* eps32, cudaStream_t s);
+void launch_build_rho_raw(const Geo& g, Atoms at, double cut_sigmas, double* rho, cudaStream_t s);
+void launch_plane_max(const Geo& g, const double* eps64, double* plane_max, cudaStream_t s);
+void launch_energy(const Geo& g, const double* rho, const double* phi, const double* eps64,
+                   double* partial, cudaStream_t s);
+void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const double* phi,
+                       const double* pe64, double* G, cudaStream_t s);
+void launch_forces_rho(const Geo& g, Atoms at, double cut_sigmas, const double* phi,
+                       double* G, cudaStream_t s);
+void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,
+                          cudaStream_t s);
+
+// reductions and FP64 full-box passes (k_mg.cu)
+void launch_finalize(const double* partial, int nparts, int ncomp, double* out, cudaStream_t s);
+void launch_rho_stats(long n, const double* rho, double* partial, cudaStream_t s);
+void launch_sub_mean(long n, double* x, const double* sum_slot, double scale, cudaStream_t s);
+template <typename T>
+void launch_residual64(const Geo& g, const double* phi, const double* rho, const double* eps64,
+                       T* r_out, double* partial, cudaStream_t s);
+template <typename T>
+void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_band,
+                       int band_first, int band_nz, cudaStream_t s);
+
+// multigrid (k_mg.cu)
+template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s);
+template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* f, T* r, cudaStream_t s);
+template <typename T> void launch_restrict(const LV<T>& F, const T* r, const LV<T>& C, T* fc, cudaStream_t s);
+template <typename T> void launch_prolong_add(const LV<T>& F, T* u, const LV<T>& C, const T* uc, cudaStream_t s);
+template <typename T> void launch_coarsen_faces(const LV<T>& F, int nxc, int nyc, int nzc,
+                                                T* cx, T* cy, T* cz, cudaStream_t s);
+template <typename T> void launch_coarse_matrix(const LV<T>& C, double* M, cudaStream_t s);
+void launch_gauss_jordan(double* M, int n, int* status, cudaStream_t s);
+template <typename T> void launch_store_inverse(const double* M, int n, T* inv, cudaStream_t s);
+template <typename T> void launch_coarse_solve(const LV<T>& C, const T* inv, int n, const T* f, T* u,
+                                               cudaStream_t s);
+template <typename T> void launch_applyA_dot(const LV<T>& L, const T* p, T* q, double* partial,
+                                             cudaStream_t s);
+template <typename T> void launch_dot(const LV<T>& L, const T* a, const T* b, double* partial,
+                                      cudaStream_t s);
+template <typename T> void launch_update_xr(const LV<T>& L, T* x, T* r, const T* p, const T* q,
+                                            const double* scal, int num, int den, cudaStream_t s);
+template <typename T> void launch_update_p(const LV<T>& L, T* p, const T* z, const double* scal,
+                                           int num, int den, cudaStream_t s);
+template <typename T> void launch_copy_level(const LV<T>& L, T* dst, const T* src, cudaStream_t s);
+
+// dry/wet band (k_mg.cu)
+template <typename T> void launch_cast_eps(long n, const double* e64, T* eT, cudaStream_t s);
+template <typename T> void launch_band_eps(const Geo& g, const T* epsT, int first_interior, int band_nz,
+                                           T* band_eps, cudaStream_t s);
+template <typename T> void launch_band_rhs(const Geo& g, const T* epsT, const T* r, const T* evac,
+                                           int first_interior, int band_nz, T* fband, cudaStream_t s);
+
+// FFT (k_fft.cu)
+struct FFTPlan;
+FFTPlan* fft_create(const Geo& g, cudaStream_t s);
+void fft_destroy(FFTPlan* p);
+size_t fft_workspace_bytes(const Geo& g, bool dbl);
+// Solve L out = src (7-point Laplacian, periodic), k = 0 mode dropped.
+template <typename T> void fft_poisson(FFTPlan* p, const T* src, T* out, void* work, cudaStream_t s);
+
+}  // namespace gp

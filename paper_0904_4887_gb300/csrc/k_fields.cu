@@ -1,0 +1,445 @@
+// Fields built from the atoms: the dielectric eps(R) (Sec. II.B), the Gaussian
+// charge density (Sec. II.A), the dry-plane test (Sec. II.C), the energy
+// (Eq. 4) and the forces (Eq. 11, Appendix B).
+//
+// Every kernel here works on 32 x 4 x 4 tiles of grid points, one thread per
+// point. A tile first culls the periodic images of a chunk of atoms against
+// its bounding box (in FP32, with a safety margin), keeps the survivors in
+// shared memory, and then every thread runs over that short list in FP64.
+#include "gp_common.cuh"
+
+namespace gp {
+namespace {
+
+constexpr int TX = 32, TY = 4, TZ = 4, TT = TX * TY * TZ;
+constexpr int ACH = 32;                // atoms per culling chunk
+constexpr int MAXE = ACH * 27;         // (atom, image) entries per chunk
+constexpr float kMargin = 1e-3f;       // FP32 culling slack, Angstrom
+
+__device__ __forceinline__ double wrap_pos(double x, double L) { return x - L * floor(x / L); }
+
+struct Tile {
+    int i0, j0, k0, i1, j1, k1;        // first and last grid index in the tile
+    float bx0, bx1, by0, by1, bz0, bz1;
+};
+
+__device__ __forceinline__ Tile make_tile(const Geo& g) {
+    Tile t;
+    t.i0 = blockIdx.x * TX; t.j0 = blockIdx.y * TY; t.k0 = blockIdx.z * TZ;
+    t.i1 = min(t.i0 + TX, g.nx) - 1; t.j1 = min(t.j0 + TY, g.ny) - 1; t.k1 = min(t.k0 + TZ, g.nz) - 1;
+    t.bx0 = (float)(t.i0 * g.hx); t.bx1 = (float)(t.i1 * g.hx);
+    t.by0 = (float)(t.j0 * g.hy); t.by1 = (float)(t.j1 * g.hy);
+    t.bz0 = (float)(t.k0 * g.hz); t.bz1 = (float)(t.k1 * g.hz);
+    return t;
+}
+
+// squared distance from point c to the tile box (FP32)
+__device__ __forceinline__ float box_d2(const Tile& t, float cx, float cy, float cz) {
+    float dx = fmaxf(fmaxf(t.bx0 - cx, cx - t.bx1), 0.f);
+    float dy = fmaxf(fmaxf(t.by0 - cy, cy - t.by1), 0.f);
+    float dz = fmaxf(fmaxf(t.bz0 - cz, cz - t.bz1), 0.f);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// largest per-axis distance from c to the box (FP32)
+__device__ __forceinline__ float box_dmax(const Tile& t, float cx, float cy, float cz) {
+    float dx = fmaxf(fmaxf(t.bx0 - cx, cx - t.bx1), 0.f);
+    float dy = fmaxf(fmaxf(t.by0 - cy, cy - t.by1), 0.f);
+    float dz = fmaxf(fmaxf(t.bz0 - cz, cz - t.bz1), 0.f);
+    return fmaxf(dx, fmaxf(dy, dz));
+}
+
+// ----------------------------------------------------------------- eps
+// eps = 1 + (eps0 - 1) prod s(d), s(d) = erfc((r0 - d)/w)/2 = (1 + erf((d - r0)/w))/2
+__global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p, double* eps64,
+                                                  double* pe64, float* eps32) {
+    __shared__ double ec[MAXE][3];
+    __shared__ int ne;
+    const Tile t = make_tile(g);
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+    const bool valid = i < g.nx && j < g.ny && k < g.nz;
+    const double x = i * g.hx, y = j * g.hy, z = k * g.hz;
+    const double rc2 = p.rcut * p.rcut;
+    const double iw = 1.0 / p.w;
+    const float rcf = (float)p.rcut + kMargin;
+    double P = 1.0;
+    for (int a0 = 0; a0 < at.n; a0 += ACH) {
+        if (threadIdx.x == 0) ne = 0;
+        __syncthreads();
+        const int na = min(ACH, at.n - a0);
+        for (int q = threadIdx.x; q < na * 27; q += TT) {
+            const int a = a0 + q / 27, im = q % 27;
+            const double cx = wrap_pos(at.pos[3 * a + 0], g.lx) + (im % 3 - 1) * g.lx;
+            const double cy = wrap_pos(at.pos[3 * a + 1], g.ly) + ((im / 3) % 3 - 1) * g.ly;
+            const double cz = wrap_pos(at.pos[3 * a + 2], g.lz) + (im / 9 - 1) * g.lz;
+            if (box_d2(t, (float)cx, (float)cy, (float)cz) < rcf * rcf) {
+                const int s = atomicAdd(&ne, 1);
+                ec[s][0] = cx; ec[s][1] = cy; ec[s][2] = cz;
+            }
+        }
+        __syncthreads();
+        const int m = ne;
+        if (valid) {
+            for (int e = 0; e < m; ++e) {
+                const double dx = x - ec[e][0], dy = y - ec[e][1], dz = z - ec[e][2];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 < rc2) P *= 0.5 * erfc((p.r0 - sqrt(d2)) * iw);
+            }
+        }
+        __syncthreads();
+    }
+    if (valid) {
+        const long idx = i + (long)g.nx * (j + (long)g.ny * k);
+        const double pe = (p.eps0 - 1.0) * P;
+        const double e = 1.0 + pe;
+        eps64[idx] = e;
+        if (pe64) pe64[idx] = pe;
+        if (eps32) eps32[idx] = (float)e;
+    }
+}
+
+// ----------------------------------------------------------------- rho
+// Separable Gaussians: g(r) = N exp(-dx^2/2s^2) exp(-dy^2/2s^2) exp(-dz^2/2s^2),
+// each factor zero outside |d| < cut*s. A tile tabulates the three 1D factors
+// per (atom, image, Gaussian) entry and every point then costs two products.
+constexpr int RCH = 8;                  // atoms per chunk
+constexpr int RMAX = RCH * 27 * 2;      // entries per chunk
+constexpr int RSUB = 32;                // entries tabulated at a time
+
+__global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, double* rho) {
+    __shared__ double en[RMAX][5];      // cx, cy, cz, sigma, coefficient
+    __shared__ double gx[RSUB][TX];
+    __shared__ double gy[RSUB][TY];
+    __shared__ double gz[RSUB][TZ];
+    __shared__ int ne;
+    const Tile t = make_tile(g);
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+    const bool valid = i < g.nx && j < g.ny && k < g.nz;
+    double acc = 0.0;
+    for (int a0 = 0; a0 < at.n; a0 += RCH) {
+        if (threadIdx.x == 0) ne = 0;
+        __syncthreads();
+        const int na = min(RCH, at.n - a0);
+        for (int q = threadIdx.x; q < na * 54; q += TT) {
+            const int a = a0 + q / 54, r = q % 54, im = r % 27, which = r / 27;
+            const double Z = at.gauss[3 * a + 0];
+            const double sg = at.gauss[3 * a + 1 + which];
+            const double cx = wrap_pos(at.pos[3 * a + 0], g.lx) + (im % 3 - 1) * g.lx;
+            const double cy = wrap_pos(at.pos[3 * a + 1], g.ly) + ((im / 3) % 3 - 1) * g.ly;
+            const double cz = wrap_pos(at.pos[3 * a + 2], g.lz) + (im / 9 - 1) * g.lz;
+            const float rad = (float)(cut * sg) + kMargin;
+            if (box_dmax(t, (float)cx, (float)cy, (float)cz) < rad) {
+                const int s = atomicAdd(&ne, 1);
+                en[s][0] = cx; en[s][1] = cy; en[s][2] = cz; en[s][3] = sg;
+                const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
+                en[s][4] = (which == 0 ? Z : -Z) * norm;
+            }
+        }
+        __syncthreads();
+        const int m = ne;
+        for (int e0 = 0; e0 < m; e0 += RSUB) {
+            const int ms = min(RSUB, m - e0);
+            for (int q = threadIdx.x; q < ms * (TX + TY + TZ); q += TT) {
+                const int e = q / (TX + TY + TZ), r = q % (TX + TY + TZ);
+                const double sg = en[e0 + e][3];
+                const double rad = cut * sg;
+                const double i2s = 1.0 / (2.0 * sg * sg);
+                if (r < TX) {
+                    const double d = (t.i0 + r) * g.hx - en[e0 + e][0];
+                    gx[e][r] = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
+                } else if (r < TX + TY) {
+                    const int rr = r - TX;
+                    const double d = (t.j0 + rr) * g.hy - en[e0 + e][1];
+                    gy[e][rr] = (fabs(d) < rad) ? en[e0 + e][4] * exp(-d * d * i2s) : 0.0;
+                } else {
+                    const int rr = r - TX - TY;
+                    const double d = (t.k0 + rr) * g.hz - en[e0 + e][2];
+                    gz[e][rr] = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
+                }
+            }
+            __syncthreads();
+            if (valid) {
+                for (int e = 0; e < ms; ++e) acc = fma(gx[e][tx] * gy[e][ty], gz[e][tz], acc);
+            }
+            __syncthreads();
+        }
+    }
+    if (valid) rho[i + (long)g.nx * (j + (long)g.ny * k)] = acc;
+}
+
+// ----------------------------------------------------------------- dry planes
+__global__ void k_plane_max(Geo g, const double* eps64, double* out) {
+    __shared__ double red[256];
+    const int k = blockIdx.x;
+    const long pl = plane_of(g.nx, g.ny);
+    double m = 0.0;
+    for (long q = threadIdx.x; q < pl; q += blockDim.x) m = fmax(m, eps64[k * pl + q] - 1.0);
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = red[0];
+}
+
+// ----------------------------------------------------------------- energy
+// partial[2b] = sum rho phi, partial[2b+1] = sum_f eps_f (grad_f phi)^2 over block b
+__global__ void __launch_bounds__(kReduceThreads) k_energy(Geo g, const double* rho, const double* phi,
+                                                           const double* eps, double* partial) {
+    __shared__ double red[2][kReduceThreads];
+    const long n = (long)g.nx * g.ny * g.nz;
+    const long pl = plane_of(g.nx, g.ny);
+    const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, ihz = 1.0 / g.hz;
+    double s0 = 0.0, s1 = 0.0;
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % g.nx);
+        const int j = (int)((c / g.nx) % g.ny);
+        const int k = (int)(c / pl);
+        const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1);
+        const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
+        const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
+        const double p0 = phi[c], e0 = eps[c];
+        s0 += rho[c] * p0;
+        double gx = (phi[xp] - p0) * ihx, gy = (phi[yp] - p0) * ihy, gz = (phi[zp] - p0) * ihz;
+        s1 += 0.5 * ((e0 + eps[xp]) * gx * gx + (e0 + eps[yp]) * gy * gy + (e0 + eps[zp]) * gz * gz);
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = red[0][0];
+        partial[2 * blockIdx.x + 1] = red[1][0];
+    }
+}
+
+// ----------------------------------------------------------------- forces
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// dielectric part: S_a = sum_i w_i pe_i sum_images q(d) (-(r_i - c)/d), with
+// w_i = (1/2) sum over the six faces of i of (grad_f phi)^2, pe = eps - 1,
+// q = s'/s. G_eps_a = -h^3/(8 pi) S_a (applied in k_forces_finish).
+__global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p, const double* phi,
+                                                   const double* pe64, double* S) {
+    __shared__ double ec[MAXE][3];
+    __shared__ int eatom[MAXE];
+    __shared__ double eacc[MAXE][3];
+    __shared__ int ne;
+    const Tile t = make_tile(g);
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+    const bool valid = i < g.nx && j < g.ny && k < g.nz;
+    const double x = i * g.hx, y = j * g.hy, z = k * g.hz;
+    double W = 0.0;
+    if (valid) {
+        const long pl = plane_of(g.nx, g.ny);
+        const long c = i + (long)g.nx * (j + (long)g.ny * k);
+        const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
+        const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
+        const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
+        const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
+        const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
+        const double p0 = phi[c];
+        const double ax = (phi[xp] - p0) / g.hx, bx = (p0 - phi[xm]) / g.hx;
+        const double ay = (phi[yp] - p0) / g.hy, by = (p0 - phi[ym]) / g.hy;
+        const double az = (phi[zp] - p0) / g.hz, bz = (p0 - phi[zm]) / g.hz;
+        W = 0.5 * (ax * ax + bx * bx + ay * ay + by * by + az * az + bz * bz) * pe64[c];
+    }
+    const double rc2 = p.rcut * p.rcut;
+    const double iw = 1.0 / p.w;
+    const double sp_norm = 1.0 / (p.w * sqrt(kPi));
+    const float rcf = (float)p.rcut + kMargin;
+    const int lane = threadIdx.x & 31;
+    for (int a0 = 0; a0 < at.n; a0 += ACH) {
+        if (threadIdx.x == 0) ne = 0;
+        __syncthreads();
+        const int na = min(ACH, at.n - a0);
+        for (int q = threadIdx.x; q < na * 27; q += TT) {
+            const int a = a0 + q / 27, im = q % 27;
+            const double cx = wrap_pos(at.pos[3 * a + 0], g.lx) + (im % 3 - 1) * g.lx;
+            const double cy = wrap_pos(at.pos[3 * a + 1], g.ly) + ((im / 3) % 3 - 1) * g.ly;
+            const double cz = wrap_pos(at.pos[3 * a + 2], g.lz) + (im / 9 - 1) * g.lz;
+            if (box_d2(t, (float)cx, (float)cy, (float)cz) < rcf * rcf) {
+                const int s = atomicAdd(&ne, 1);
+                ec[s][0] = cx; ec[s][1] = cy; ec[s][2] = cz; eatom[s] = a;
+                eacc[s][0] = 0.0; eacc[s][1] = 0.0; eacc[s][2] = 0.0;
+            }
+        }
+        __syncthreads();
+        const int m = ne;
+        for (int e = 0; e < m; ++e) {
+            double fx = 0.0, fy = 0.0, fz = 0.0;
+            if (valid) {
+                const double dx = x - ec[e][0], dy = y - ec[e][1], dz = z - ec[e][2];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 < rc2 && d2 > 0.0) {
+                    const double d = sqrt(d2);
+                    const double u = (d - p.r0) * iw;
+                    const double s = 0.5 * erfc(-u);
+                    const double sp = sp_norm * exp(-u * u);
+                    const double c = -W * sp / (s * d);
+                    fx = c * dx; fy = c * dy; fz = c * dz;
+                }
+            }
+            fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+            if (lane == 0 && (fx != 0.0 || fy != 0.0 || fz != 0.0)) {
+                atomicAdd(&eacc[e][0], fx); atomicAdd(&eacc[e][1], fy); atomicAdd(&eacc[e][2], fz);
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < m; e += TT) {
+            const int a = eatom[e];
+            if (eacc[e][0] != 0.0) atomicAdd(&S[3 * a + 0], eacc[e][0]);
+            if (eacc[e][1] != 0.0) atomicAdd(&S[3 * a + 1], eacc[e][1]);
+            if (eacc[e][2] != 0.0) atomicAdd(&S[3 * a + 2], eacc[e][2]);
+        }
+        __syncthreads();
+    }
+}
+
+// charge part: T_a = sum_i phi_i d rho~_i / d R_a with d g / d R = g (r - c)/sigma^2,
+// tabulated per tile like k_build_rho. G_rho_a = h^3 T_a.
+__global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, const double* phi,
+                                                   double* T) {
+    __shared__ double en[RMAX][5];
+    __shared__ int eatom[RMAX];
+    __shared__ double gx[RSUB][TX], dxs[RSUB][TX];
+    __shared__ double gy[RSUB][TY], dys[RSUB][TY];
+    __shared__ double gz[RSUB][TZ], dzs[RSUB][TZ];
+    __shared__ double eacc[RSUB][3];
+    __shared__ int ne;
+    const Tile t = make_tile(g);
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+    const bool valid = i < g.nx && j < g.ny && k < g.nz;
+    const double ph = valid ? phi[i + (long)g.nx * (j + (long)g.ny * k)] : 0.0;
+    const int lane = threadIdx.x & 31;
+    for (int a0 = 0; a0 < at.n; a0 += RCH) {
+        if (threadIdx.x == 0) ne = 0;
+        __syncthreads();
+        const int na = min(RCH, at.n - a0);
+        for (int q = threadIdx.x; q < na * 54; q += TT) {
+            const int a = a0 + q / 54, r = q % 54, im = r % 27, which = r / 27;
+            const double Z = at.gauss[3 * a + 0];
+            const double sg = at.gauss[3 * a + 1 + which];
+            const double cx = wrap_pos(at.pos[3 * a + 0], g.lx) + (im % 3 - 1) * g.lx;
+            const double cy = wrap_pos(at.pos[3 * a + 1], g.ly) + ((im / 3) % 3 - 1) * g.ly;
+            const double cz = wrap_pos(at.pos[3 * a + 2], g.lz) + (im / 9 - 1) * g.lz;
+            const float rad = (float)(cut * sg) + kMargin;
+            if (box_dmax(t, (float)cx, (float)cy, (float)cz) < rad) {
+                const int s = atomicAdd(&ne, 1);
+                en[s][0] = cx; en[s][1] = cy; en[s][2] = cz; en[s][3] = sg;
+                const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
+                en[s][4] = (which == 0 ? Z : -Z) * norm / (sg * sg);
+                eatom[s] = a;
+            }
+        }
+        __syncthreads();
+        const int m = ne;
+        for (int e0 = 0; e0 < m; e0 += RSUB) {
+            const int ms = min(RSUB, m - e0);
+            for (int q = threadIdx.x; q < ms * (TX + TY + TZ); q += TT) {
+                const int e = q / (TX + TY + TZ), r = q % (TX + TY + TZ);
+                const double sg = en[e0 + e][3];
+                const double rad = cut * sg;
+                const double i2s = 1.0 / (2.0 * sg * sg);
+                if (r < TX) {
+                    const double d = (t.i0 + r) * g.hx - en[e0 + e][0];
+                    const double v = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
+                    gx[e][r] = v; dxs[e][r] = v * d;
+                } else if (r < TX + TY) {
+                    const int rr = r - TX;
+                    const double d = (t.j0 + rr) * g.hy - en[e0 + e][1];
+                    const double v = (fabs(d) < rad) ? en[e0 + e][4] * exp(-d * d * i2s) : 0.0;
+                    gy[e][rr] = v; dys[e][rr] = v * d;
+                } else {
+                    const int rr = r - TX - TY;
+                    const double d = (t.k0 + rr) * g.hz - en[e0 + e][2];
+                    const double v = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
+                    gz[e][rr] = v; dzs[e][rr] = v * d;
+                }
+                if (r == 0) { eacc[e][0] = 0.0; eacc[e][1] = 0.0; eacc[e][2] = 0.0; }
+            }
+            __syncthreads();
+            for (int e = 0; e < ms; ++e) {
+                double fx = 0.0, fy = 0.0, fz = 0.0;
+                if (valid) {
+                    const double gyz = gy[e][ty] * gz[e][tz];
+                    fx = ph * dxs[e][tx] * gyz;
+                    fy = ph * gx[e][tx] * dys[e][ty] * gz[e][tz];
+                    fz = ph * gx[e][tx] * gy[e][ty] * dzs[e][tz];
+                }
+                fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+                if (lane == 0 && (fx != 0.0 || fy != 0.0 || fz != 0.0)) {
+                    atomicAdd(&eacc[e][0], fx); atomicAdd(&eacc[e][1], fy); atomicAdd(&eacc[e][2], fz);
+                }
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < ms; e += TT) {
+                const int a = eatom[e0 + e];
+                if (eacc[e][0] != 0.0) atomicAdd(&T[3 * a + 0], eacc[e][0]);
+                if (eacc[e][1] != 0.0) atomicAdd(&T[3 * a + 1], eacc[e][1]);
+                if (eacc[e][2] != 0.0) atomicAdd(&T[3 * a + 2], eacc[e][2]);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// F = -(G_eps + G_rho) with G_eps = ce * S and G_rho = cr * T
+__global__ void k_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < 3 * n) F[q] = -(ce * S[q] + (T ? cr * T[q] : 0.0));
+}
+
+dim3 tile_grid(const Geo& g) {
+    return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
+}
+
+}  // namespace
+
+void launch_build_eps(const Geo& g, Atoms at, DielParams p, double* eps64, double* pe64, float* eps32,
+                      cudaStream_t s) {
+    k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, eps64, pe64, eps32);
+}
+
+void launch_build_rho_raw(const Geo& g, Atoms at, double cut, double* rho, cudaStream_t s) {
+    k_build_rho<<<tile_grid(g), TT, 0, s>>>(g, at, cut, rho);
+}
+
+void launch_plane_max(const Geo& g, const double* eps64, double* out, cudaStream_t s) {
+    k_plane_max<<<g.nz, 256, 0, s>>>(g, eps64, out);
+}
+
+void launch_energy(const Geo& g, const double* rho, const double* phi, const double* eps64,
+                   double* partial, cudaStream_t s) {
+    k_energy<<<kReduceBlocks, kReduceThreads, 0, s>>>(g, rho, phi, eps64, partial);
+}
+
+void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const double* phi, const double* pe64,
+                       double* S, cudaStream_t s) {
+    k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, phi, pe64, S);
+}
+
+void launch_forces_rho(const Geo& g, Atoms at, double cut, const double* phi, double* T, cudaStream_t s) {
+    k_forces_rho<<<tile_grid(g), TT, 0, s>>>(g, at, cut, phi, T);
+}
+
+void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,
+                          cudaStream_t s) {
+    k_forces_finish<<<(3 * n + 255) / 256, 256, 0, s>>>(S, T, n, ce, cr, F);
+}
+
+}  // namespace gp

@@ -1,0 +1,656 @@
+// Multigrid and Krylov kernels for the 7-point conservative operator
+//   (A u)_i = sum_axes [c_{i+1/2}(u_{i+1} - u_i) - c_{i-1/2}(u_i - u_{i-1})],
+// the discretisation of div(eps grad u) of Eq. 3 (c = eps_face / h^2), plus
+// the FP64 full-box passes of the outer defect correction and the kernels
+// that couple the dry FFT solution to the wet multigrid band (Sec. II.C).
+//
+// Levels are vertex-centred: coarse point I sits on fine point 2I (periodic
+// axes) or 2I+1 (Dirichlet z, counting interior planes). Level 0 reads the
+// cell dielectric and forms face means on the fly; coarse levels store face
+// coefficients, obtained from the fine faces by a harmonic mean along the
+// face normal (two faces in series) and full weighting across it.
+#include "gp_common.cuh"
+
+namespace gp {
+namespace {
+
+template <typename T> struct Co { T xm, xp, ym, yp, zm, zp; };
+
+struct Nb { long c, xm, xp, ym, yp, zm, zp; };
+
+__device__ __forceinline__ Nb neighbours(int nx, int ny, int nz, int zper, int i, int j, int k) {
+    Nb n;
+    const long pl = (long)nx * ny;
+    n.c = i + (long)nx * (j + (long)ny * k);
+    n.xm = n.c + (i == 0 ? nx - 1 : -1);
+    n.xp = n.c + (i == nx - 1 ? 1 - nx : 1);
+    n.ym = n.c + (j == 0 ? (long)(ny - 1) * nx : -(long)nx);
+    n.yp = n.c + (j == ny - 1 ? -(long)(ny - 1) * nx : (long)nx);
+    n.zm = n.c + ((k == 0 && zper) ? (long)(nz - 1) * pl : -pl);
+    n.zp = n.c + ((k == nz - 1 && zper) ? -(long)(nz - 1) * pl : pl);
+    return n;
+}
+
+template <typename T>
+__device__ __forceinline__ Co<T> coefs(const LV<T>& L, const Nb& n) {
+    Co<T> o;
+    if (L.cell) {
+        const T e = L.eps[n.c];
+        const T hx = (T)0.5 * L.ihx2, hy = (T)0.5 * L.ihy2, hz = (T)0.5 * L.ihz2;
+        o.xm = (e + L.eps[n.xm]) * hx; o.xp = (e + L.eps[n.xp]) * hx;
+        o.ym = (e + L.eps[n.ym]) * hy; o.yp = (e + L.eps[n.yp]) * hy;
+        o.zm = (e + L.eps[n.zm]) * hz; o.zp = (e + L.eps[n.zp]) * hz;
+    } else {
+        o.xm = L.cx[n.xm]; o.xp = L.cx[n.c];
+        o.ym = L.cy[n.ym]; o.yp = L.cy[n.c];
+        o.zm = L.cz[n.zm]; o.zp = L.cz[n.c];
+    }
+    return o;
+}
+
+// A u at one point
+template <typename T>
+__device__ __forceinline__ T apply_at(const Co<T>& o, const Nb& n, const T* u) {
+    const T u0 = u[n.c];
+    return o.xp * (u[n.xp] - u0) - o.xm * (u0 - u[n.xm]) + o.yp * (u[n.yp] - u0) - o.ym * (u0 - u[n.ym]) +
+           o.zp * (u[n.zp] - u0) - o.zm * (u0 - u[n.zm]);
+}
+
+__device__ __forceinline__ void split3(long t, int nx, int ny, int& i, int& j, int& k) {
+    i = (int)(t % nx);
+    const long r = t / nx;
+    j = (int)(r % ny);
+    k = (int)(r / ny);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    return s;   // valid in thread 0
+}
+
+int grid_for(long n, int threads) {
+    long b = (n + threads - 1) / threads;
+    return (int)(b < 152L * 16 ? (b < 1 ? 1 : b) : 152L * 16);
+}
+
+// ------------------------------------------------------------ smoothing
+// Red-black Gauss-Seidel half sweep for A u = f: u_i = (sum c u_nb - f_i) / sum c.
+// One thread per x-pair; it updates the member of the pair with the colour.
+template <typename T>
+__global__ void k_rbgs(LV<T> L, T* u, const T* f, int color) {
+    const int hx = L.nx >> 1;
+    const long np = (long)hx * L.ny * L.nz;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < np; t += (long)gridDim.x * blockDim.x) {
+        int i2, j, k;
+        split3(t, hx, L.ny, i2, j, k);
+        const int i = 2 * i2 + ((j + k + color) & 1);
+        const Nb n = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
+        const Co<T> o = coefs(L, n);
+        const T s = o.xp * u[n.xp] + o.xm * u[n.xm] + o.yp * u[n.yp] + o.ym * u[n.ym] + o.zp * u[n.zp] +
+                    o.zm * u[n.zm];
+        const T d = o.xp + o.xm + o.yp + o.ym + o.zp + o.zm;
+        u[n.c] = (s - f[n.c]) / d;
+    }
+}
+
+template <typename T>
+__global__ void k_residual(LV<T> L, const T* u, const T* f, T* r) {
+    const long n = (long)L.nx * L.ny * L.nz;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        split3(t, L.nx, L.ny, i, j, k);
+        const Nb nb = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
+        r[nb.c] = f[nb.c] - apply_at(coefs(L, nb), nb, u);
+    }
+}
+
+// full weighting (1/4, 1/2, 1/4) per axis
+template <typename T>
+__global__ void k_restrict(LV<T> F, const T* r, LV<T> C, T* fc) {
+    const long n = (long)C.nx * C.ny * C.nz;
+    const int zoff = F.zper ? 0 : 1;
+    const long pl = (long)F.nx * F.ny;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        int I, J, K;
+        split3(t, C.nx, C.ny, I, J, K);
+        const int kf = 2 * K + zoff;
+        T acc = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            int kk = kf + dz;
+            if (F.zper) kk = (kk + F.nz) % F.nz;
+            const T wz = dz == 0 ? (T)0.5 : (T)0.25;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int jj = (2 * J + dy + F.ny) % F.ny;
+                const T wy = dy == 0 ? (T)0.5 : (T)0.25;
+                const long base = kk * pl + (long)jj * F.nx;
+                const int ic = 2 * I;
+                const int im = ic == 0 ? F.nx - 1 : ic - 1;
+                const int ip = ic == F.nx - 1 ? 0 : ic + 1;
+                acc += wz * wy * ((T)0.25 * r[base + im] + (T)0.5 * r[base + ic] + (T)0.25 * r[base + ip]);
+            }
+        }
+        fc[I + (long)C.nx * (J + (long)C.ny * K)] = acc;
+    }
+}
+
+// trilinear interpolation of the coarse correction, added to u
+template <typename T>
+__global__ void k_prolong_add(LV<T> F, T* u, LV<T> C, const T* uc) {
+    const long n = (long)F.nx * F.ny * F.nz;
+    const int zoff = F.zper ? 0 : 1;
+    const long cpl = (long)C.nx * C.ny;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        split3(t, F.nx, F.ny, i, j, k);
+        int xi[2], yi[2], zi[2];
+        T xw[2], yw[2], zw[2];
+        int nxp, nyp, nzp;
+        if (i & 1) { xi[0] = i >> 1; xi[1] = (xi[0] + 1) % C.nx; xw[0] = xw[1] = (T)0.5; nxp = 2; }
+        else { xi[0] = i >> 1; xw[0] = 1; nxp = 1; }
+        if (j & 1) { yi[0] = j >> 1; yi[1] = (yi[0] + 1) % C.ny; yw[0] = yw[1] = (T)0.5; nyp = 2; }
+        else { yi[0] = j >> 1; yw[0] = 1; nyp = 1; }
+        const int kk = k - zoff;                 // -1 .. for Dirichlet
+        if (kk & 1) {
+            zi[0] = (kk - 1) >> 1;               // floor division: -1 -> -1 (the lower wall)
+            zi[1] = zi[0] + 1;
+            if (C.zper && zi[1] == C.nz) zi[1] = 0;
+            zw[0] = zw[1] = (T)0.5;
+            nzp = 2;
+        } else { zi[0] = kk >> 1; zw[0] = 1; nzp = 1; }
+        T acc = 0;
+        for (int c = 0; c < nzp; ++c)
+            for (int b = 0; b < nyp; ++b)
+                for (int a = 0; a < nxp; ++a)
+                    acc += zw[c] * yw[b] * xw[a] * uc[xi[a] + (long)C.nx * yi[b] + cpl * zi[c]];
+        u[i + (long)F.nx * (j + (long)F.ny * k)] += acc;
+    }
+}
+
+// fine face coefficient along `axis` between (i,j,k) and its + neighbour; k may be -1 (wall face)
+template <typename T>
+__device__ __forceinline__ T fine_face(const LV<T>& F, int axis, int i, int j, int k) {
+    const long pl = (long)F.nx * F.ny;
+    i = (i % F.nx + F.nx) % F.nx;
+    j = (j % F.ny + F.ny) % F.ny;
+    if (F.zper) k = (k % F.nz + F.nz) % F.nz;
+    const long c = i + (long)F.nx * j + pl * k;
+    if (!F.cell) return axis == 0 ? F.cx[c] : (axis == 1 ? F.cy[c] : F.cz[c]);
+    long o;
+    T ih;
+    if (axis == 0) { o = c + (i == F.nx - 1 ? 1 - F.nx : 1); ih = F.ihx2; }
+    else if (axis == 1) { o = c + (j == F.ny - 1 ? -(long)(F.ny - 1) * F.nx : (long)F.nx); ih = F.ihy2; }
+    else { o = c + ((k == F.nz - 1 && F.zper) ? -(long)(F.nz - 1) * pl : pl); ih = F.ihz2; }
+    return (F.eps[c] + F.eps[o]) * (T)0.5 * ih;
+}
+
+template <typename T>
+__device__ __forceinline__ T series_quarter(T a, T b) {
+    // two faces of spacing h in series, re-expressed for spacing 2h: harmonic mean / 4
+    return (a * b) / ((a + b) * (T)2);
+}
+
+template <typename T>
+__global__ void k_coarsen_faces(LV<T> F, int nxc, int nyc, int nzc, T* cx, T* cy, T* cz) {
+    const int zoff = F.zper ? 0 : 1;
+    const int nk = F.zper ? nzc : nzc + 1;      // Dirichlet: also the lower wall face K = -1
+    const long n = (long)nxc * nyc * nk;
+    const long cpl = (long)nxc * nyc;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        int I, J, kk;
+        split3(t, nxc, nyc, I, J, kk);
+        const int K = F.zper ? kk : kk - 1;
+        const int kf = 2 * K + zoff;
+        const long o = I + (long)nxc * J + cpl * K;
+        if (K >= 0) {
+            T ax = 0, ay = 0;
+            for (int dz = -1; dz <= 1; ++dz) {
+                const T wz = dz == 0 ? (T)0.5 : (T)0.25;
+                for (int d = -1; d <= 1; ++d) {
+                    const T wd = d == 0 ? (T)0.5 : (T)0.25;
+                    ax += wz * wd * series_quarter(fine_face(F, 0, 2 * I, 2 * J + d, kf + dz),
+                                                   fine_face(F, 0, 2 * I + 1, 2 * J + d, kf + dz));
+                    ay += wz * wd * series_quarter(fine_face(F, 1, 2 * I + d, 2 * J, kf + dz),
+                                                   fine_face(F, 1, 2 * I + d, 2 * J + 1, kf + dz));
+                }
+            }
+            cx[o] = ax;
+            cy[o] = ay;
+        }
+        T az = 0;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const T wy = dy == 0 ? (T)0.5 : (T)0.25;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const T wx = dx == 0 ? (T)0.5 : (T)0.25;
+                az += wy * wx * series_quarter(fine_face(F, 2, 2 * I + dx, 2 * J + dy, kf),
+                                               fine_face(F, 2, 2 * I + dx, 2 * J + dy, kf + 1));
+            }
+        }
+        cz[o] = az;
+    }
+}
+
+// dense matrix of the coarsest operator (row p = point p), periodic levels
+// regularised by -(max|diag|/n) 1 1^T so that mean-zero data give the
+// mean-zero solution
+template <typename T>
+__global__ void k_coarse_matrix(LV<T> C, double* M) {
+    const int n = C.nx * C.ny * C.nz;
+    __shared__ double dmax;
+    if (threadIdx.x == 0) dmax = 0.0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        for (int q = 0; q < n; ++q) M[(long)p * n + q] = 0.0;
+        int i, j, k;
+        split3(p, C.nx, C.ny, i, j, k);
+        const Nb nb = neighbours(C.nx, C.ny, C.nz, C.zper, i, j, k);
+        const Co<T> o = coefs(C, nb);
+        const long nbr[6] = {nb.xm, nb.xp, nb.ym, nb.yp, nb.zm, nb.zp};
+        const double cf[6] = {(double)o.xm, (double)o.xp, (double)o.ym, (double)o.yp, (double)o.zm,
+                              (double)o.zp};
+        double d = 0.0;
+        for (int s = 0; s < 6; ++s) {
+            d += cf[s];
+            const long q = nbr[s];
+            if (q >= 0 && q < n) M[(long)p * n + q] += cf[s];   // outside: Dirichlet wall (zero)
+        }
+        M[(long)p * n + p] -= d;
+        atomicMax((unsigned long long*)&dmax, __double_as_longlong(d));   // d > 0
+    }
+    __syncthreads();
+    if (C.zper) {
+        const double s = dmax / n;
+        for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) M[e] -= s;
+    }
+}
+
+// in-place inverse by Gauss-Jordan elimination with partial pivoting (one CTA);
+// M is n x n, W (second n x n block after M) receives the inverse
+__global__ void k_gauss_jordan(double* M, int n, int* status) {
+    double* W = M + (long)n * n;
+    __shared__ double fcol[kMaxCoarse];
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) W[e] = (e / n == e % n) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int col = 0; col < n; ++col) {
+        double best = -1.0;
+        int bidx = col;
+        for (int r = col + threadIdx.x; r < n; r += blockDim.x) {
+            const double v = fabs(M[(long)r * n + col]);
+            if (v > best) { best = v; bidx = r; }
+        }
+        bv[threadIdx.x] = best;
+        bi[threadIdx.x] = bidx;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s && bv[threadIdx.x + s] > bv[threadIdx.x]) {
+                bv[threadIdx.x] = bv[threadIdx.x + s];
+                bi[threadIdx.x] = bi[threadIdx.x + s];
+            }
+            __syncthreads();
+        }
+        const int piv = bi[0];
+        if (bv[0] <= 1e-300) {
+            if (threadIdx.x == 0) *status = 1;
+            return;
+        }
+        if (piv != col) {
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                double a = M[(long)col * n + q]; M[(long)col * n + q] = M[(long)piv * n + q]; M[(long)piv * n + q] = a;
+                double b = W[(long)col * n + q]; W[(long)col * n + q] = W[(long)piv * n + q]; W[(long)piv * n + q] = b;
+            }
+        }
+        __syncthreads();
+        const double pv = M[(long)col * n + col];
+        __syncthreads();
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            M[(long)col * n + q] /= pv;
+            W[(long)col * n + q] /= pv;
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x) fcol[r] = M[(long)r * n + col];
+        __syncthreads();
+        for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
+            const int r = (int)(e / n), q = (int)(e % n);
+            if (r == col) continue;
+            const double f = fcol[r];
+            if (f != 0.0) {
+                M[e] -= f * M[(long)col * n + q];
+                W[e] -= f * W[(long)col * n + q];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *status = 0;
+}
+
+template <typename T>
+__global__ void k_store_inverse(const double* W, long nn, T* inv) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x)
+        inv[e] = (T)W[e];
+}
+
+// u = inv * f on the coarsest level (periodic: f projected to mean zero first)
+template <typename T>
+__global__ void k_coarse_solve(LV<T> C, const T* inv, int n, const T* f, T* u) {
+    __shared__ T fs[kMaxCoarse];
+    __shared__ double red[32];
+    double loc = 0.0;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        fs[p] = f[p];
+        loc += (double)f[p];
+    }
+    const double tot = block_sum(loc, red);
+    __shared__ double mean;
+    if (threadIdx.x == 0) mean = C.zper ? tot / n : 0.0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += blockDim.x) fs[p] -= (T)mean;
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        T acc = 0;
+        const T* row = inv + (long)p * n;
+        for (int q = 0; q < n; ++q) acc += row[q] * fs[q];
+        u[p] = acc;
+    }
+}
+
+// ------------------------------------------------------------ Krylov helpers
+template <typename T>
+__global__ void k_applyA_dot(LV<T> L, const T* p, T* q, double* partial) {
+    __shared__ double red[32];
+    const long n = (long)L.nx * L.ny * L.nz;
+    double loc = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        split3(t, L.nx, L.ny, i, j, k);
+        const Nb nb = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
+        const T v = apply_at(coefs(L, nb), nb, p);
+        q[nb.c] = v;
+        loc += (double)p[nb.c] * (double)v;
+    }
+    const double s = block_sum(loc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void k_dot(long n, const T* a, const T* b, double* partial) {
+    __shared__ double red[32];
+    double loc = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        loc += (double)a[t] * (double)b[t];
+    const double s = block_sum(loc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void k_update_xr(long n, T* x, T* r, const T* p, const T* q, const double* scal, int num, int den) {
+    const T alpha = (T)(scal[num] / scal[den]);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        x[t] += alpha * p[t];
+        r[t] -= alpha * q[t];
+    }
+}
+
+template <typename T>
+__global__ void k_update_p(long n, T* p, const T* z, const double* scal, int num, int den) {
+    const T beta = (T)(scal[num] / scal[den]);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        p[t] = z[t] + beta * p[t];
+}
+
+template <typename T>
+__global__ void k_copy(long n, T* dst, const T* src) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        dst[t] = src[t];
+}
+
+// ------------------------------------------------------------ reductions
+// out[c] = sum_b partial[b * ncomp + c], in a fixed order
+__global__ void k_finalize(const double* partial, int nparts, int ncomp, double* out) {
+    __shared__ double red[32];
+    for (int c = 0; c < ncomp; ++c) {
+        double loc = 0.0;
+        for (int b = threadIdx.x; b < nparts; b += blockDim.x) loc += partial[(long)b * ncomp + c];
+        const double s = block_sum(loc, red);
+        if (threadIdx.x == 0) out[c] = s;
+        __syncthreads();
+    }
+}
+
+// partial[3b..3b+2] = sum rho, sum |rho|, sum rho^2
+__global__ void k_rho_stats(long n, const double* rho, double* partial) {
+    __shared__ double red[32];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const double v = rho[t];
+        a += v; b += fabs(v); c += v * v;
+    }
+    double s = block_sum(a, red);
+    if (threadIdx.x == 0) partial[3 * blockIdx.x] = s;
+    s = block_sum(b, red);
+    if (threadIdx.x == 0) partial[3 * blockIdx.x + 1] = s;
+    s = block_sum(c, red);
+    if (threadIdx.x == 0) partial[3 * blockIdx.x + 2] = s;
+}
+
+__global__ void k_sub_mean(long n, double* x, const double* sum_slot, double scale) {
+    const double m = sum_slot[0] * scale;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        x[t] -= m;
+}
+
+// ------------------------------------------------------------ FP64 full box
+// r = -4 pi rho - A phi (periodic, cell eps, FP64); partial[2b] = sum r^2,
+// partial[2b+1] = sum phi
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads) k_residual64(Geo g, const double* phi, const double* rho,
+                                                               const double* eps, T* r_out, double* partial) {
+    __shared__ double red[32];
+    const long n = (long)g.nx * g.ny * g.nz;
+    const double hx = 0.5 / (g.hx * g.hx), hy = 0.5 / (g.hy * g.hy), hz = 0.5 / (g.hz * g.hz);
+    const double fpi = 4.0 * kPi;
+    double s2 = 0.0, sp = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        split3(t, g.nx, g.ny, i, j, k);
+        const Nb nb = neighbours(g.nx, g.ny, g.nz, 1, i, j, k);
+        const double e0 = eps[nb.c], p0 = phi[nb.c];
+        const double ax = (e0 + eps[nb.xp]) * (phi[nb.xp] - p0) - (e0 + eps[nb.xm]) * (p0 - phi[nb.xm]);
+        const double ay = (e0 + eps[nb.yp]) * (phi[nb.yp] - p0) - (e0 + eps[nb.ym]) * (p0 - phi[nb.ym]);
+        const double az = (e0 + eps[nb.zp]) * (phi[nb.zp] - p0) - (e0 + eps[nb.zm]) * (p0 - phi[nb.zm]);
+        const double r = -fpi * rho[nb.c] - (hx * ax + hy * ay + hz * az);
+        r_out[nb.c] = (T)r;
+        s2 += r * r;
+        sp += p0;
+    }
+    double s = block_sum(s2, red);
+    if (threadIdx.x == 0) partial[2 * blockIdx.x] = s;
+    s = block_sum(sp, red);
+    if (threadIdx.x == 0) partial[2 * blockIdx.x + 1] = s;
+}
+
+// phi += e_full (+ e_band on the band planes); band plane kb <-> global plane
+// (band_first + kb) mod nz, kb < band_nz
+template <typename T>
+__global__ void k_update_phi(Geo g, double* phi, const T* e_full, const T* e_band, int band_first, int band_nz) {
+    const long n = (long)g.nx * g.ny * g.nz;
+    const long pl = plane_of(g.nx, g.ny);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        double v = e_full ? (double)e_full[t] : 0.0;
+        if (e_band) {
+            const int k = (int)(t / pl);
+            int kb = k - band_first;
+            if (kb < 0) kb += g.nz;
+            if (kb < band_nz) v += (double)e_band[t - k * pl + kb * pl];
+        }
+        phi[t] += v;
+    }
+}
+
+// ------------------------------------------------------------ band coupling
+template <typename T>
+__global__ void k_cast(long n, const double* a, T* b) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        b[t] = (T)a[t];
+}
+
+// band eps planes kb = -1 .. band_nz (walls included) from the full-box eps
+template <typename T>
+__global__ void k_band_eps(Geo g, const T* eps, int first, int band_nz, T* beps) {
+    const long pl = plane_of(g.nx, g.ny);
+    const long n = pl * (band_nz + 2);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const int kb = (int)(t / pl) - 1;
+        const int k = ((first + kb) % g.nz + g.nz) % g.nz;
+        beps[t - pl] = eps[(t % pl) + k * pl];
+    }
+}
+
+// f_band = r - A e_vac on the band's interior planes (full-box operator, periodic)
+template <typename T>
+__global__ void k_band_rhs(Geo g, const T* eps, const T* r, const T* ev, int first, int band_nz, T* fb) {
+    const long pl = plane_of(g.nx, g.ny);
+    const long n = pl * band_nz;
+    const T hx = (T)(0.5 / (g.hx * g.hx)), hy = (T)(0.5 / (g.hy * g.hy)), hz = (T)(0.5 / (g.hz * g.hz));
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const int kb = (int)(t / pl);
+        const long q = t % pl;
+        const int k = (first + kb) % g.nz;
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const Nb nb = neighbours(g.nx, g.ny, g.nz, 1, i, j, k);
+        const T e0 = eps[nb.c], p0 = ev[nb.c];
+        const T ax = (e0 + eps[nb.xp]) * (ev[nb.xp] - p0) - (e0 + eps[nb.xm]) * (p0 - ev[nb.xm]);
+        const T ay = (e0 + eps[nb.yp]) * (ev[nb.yp] - p0) - (e0 + eps[nb.ym]) * (p0 - ev[nb.ym]);
+        const T az = (e0 + eps[nb.zp]) * (ev[nb.zp] - p0) - (e0 + eps[nb.zm]) * (p0 - ev[nb.zm]);
+        fb[t] = r[nb.c] - (hx * ax + hy * ay + hz * az);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+void launch_finalize(const double* partial, int nparts, int ncomp, double* out, cudaStream_t s) {
+    k_finalize<<<1, 1024, 0, s>>>(partial, nparts, ncomp, out);
+}
+void launch_rho_stats(long n, const double* rho, double* partial, cudaStream_t s) {
+    k_rho_stats<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, rho, partial);
+}
+void launch_sub_mean(long n, double* x, const double* sum_slot, double scale, cudaStream_t s) {
+    k_sub_mean<<<grid_for(n, 256), 256, 0, s>>>(n, x, sum_slot, scale);
+}
+template <typename T>
+void launch_residual64(const Geo& g, const double* phi, const double* rho, const double* eps64, T* r_out,
+                       double* partial, cudaStream_t s) {
+    k_residual64<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(g, phi, rho, eps64, r_out, partial);
+}
+template <typename T>
+void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_band, int band_first, int band_nz,
+                       cudaStream_t s) {
+    const long n = (long)g.nx * g.ny * g.nz;
+    k_update_phi<T><<<grid_for(n, 256), 256, 0, s>>>(g, phi, e_full, e_band, band_first, band_nz);
+}
+template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s) {
+    const long n = (long)(L.nx / 2) * L.ny * L.nz;
+    k_rbgs<T><<<grid_for(n, 256), 256, 0, s>>>(L, u, f, color);
+}
+template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* f, T* r, cudaStream_t s) {
+    const long n = (long)L.nx * L.ny * L.nz;
+    k_residual<T><<<grid_for(n, 256), 256, 0, s>>>(L, u, f, r);
+}
+template <typename T> void launch_restrict(const LV<T>& F, const T* r, const LV<T>& C, T* fc, cudaStream_t s) {
+    const long n = (long)C.nx * C.ny * C.nz;
+    k_restrict<T><<<grid_for(n, 256), 256, 0, s>>>(F, r, C, fc);
+}
+template <typename T> void launch_prolong_add(const LV<T>& F, T* u, const LV<T>& C, const T* uc, cudaStream_t s) {
+    const long n = (long)F.nx * F.ny * F.nz;
+    k_prolong_add<T><<<grid_for(n, 256), 256, 0, s>>>(F, u, C, uc);
+}
+template <typename T> void launch_coarsen_faces(const LV<T>& F, int nxc, int nyc, int nzc, T* cx, T* cy, T* cz,
+                                                cudaStream_t s) {
+    const long n = (long)nxc * nyc * (nzc + 1);
+    k_coarsen_faces<T><<<grid_for(n, 256), 256, 0, s>>>(F, nxc, nyc, nzc, cx, cy, cz);
+}
+template <typename T> void launch_coarse_matrix(const LV<T>& C, double* M, cudaStream_t s) {
+    k_coarse_matrix<T><<<1, 512, 0, s>>>(C, M);
+}
+void launch_gauss_jordan(double* M, int n, int* status, cudaStream_t s) {
+    k_gauss_jordan<<<1, 1024, 0, s>>>(M, n, status);
+}
+template <typename T> void launch_store_inverse(const double* W, int n, T* inv, cudaStream_t s) {
+    const long nn = (long)n * n;
+    k_store_inverse<T><<<grid_for(nn, 256), 256, 0, s>>>(W, nn, inv);
+}
+template <typename T> void launch_coarse_solve(const LV<T>& C, const T* inv, int n, const T* f, T* u,
+                                               cudaStream_t s) {
+    k_coarse_solve<T><<<1, 512, 0, s>>>(C, inv, n, f, u);
+}
+template <typename T> void launch_applyA_dot(const LV<T>& L, const T* p, T* q, double* partial, cudaStream_t s) {
+    k_applyA_dot<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(L, p, q, partial);
+}
+template <typename T> void launch_dot(const LV<T>& L, const T* a, const T* b, double* partial, cudaStream_t s) {
+    const long n = (long)L.nx * L.ny * L.nz;
+    k_dot<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, a, b, partial);
+}
+template <typename T> void launch_update_xr(const LV<T>& L, T* x, T* r, const T* p, const T* q, const double* scal,
+                                            int num, int den, cudaStream_t s) {
+    const long n = (long)L.nx * L.ny * L.nz;
+    k_update_xr<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, r, p, q, scal, num, den);
+}
+template <typename T> void launch_update_p(const LV<T>& L, T* p, const T* z, const double* scal, int num, int den,
+                                           cudaStream_t s) {
+    const long n = (long)L.nx * L.ny * L.nz;
+    k_update_p<T><<<grid_for(n, 256), 256, 0, s>>>(n, p, z, scal, num, den);
+}
+template <typename T> void launch_copy_level(const LV<T>& L, T* dst, const T* src, cudaStream_t s) {
+    const long n = (long)L.nx * L.ny * L.nz;
+    k_copy<T><<<grid_for(n, 256), 256, 0, s>>>(n, dst, src);
+}
+template <typename T> void launch_cast_eps(long n, const double* e64, T* eT, cudaStream_t s) {
+    k_cast<T><<<grid_for(n, 256), 256, 0, s>>>(n, e64, eT);
+}
+template <typename T> void launch_band_eps(const Geo& g, const T* epsT, int first, int band_nz, T* beps,
+                                           cudaStream_t s) {
+    const long n = plane_of(g.nx, g.ny) * (band_nz + 2);
+    k_band_eps<T><<<grid_for(n, 256), 256, 0, s>>>(g, epsT, first, band_nz, beps);
+}
+template <typename T> void launch_band_rhs(const Geo& g, const T* epsT, const T* r, const T* ev, int first,
+                                           int band_nz, T* fb, cudaStream_t s) {
+    const long n = plane_of(g.nx, g.ny) * band_nz;
+    k_band_rhs<T><<<grid_for(n, 256), 256, 0, s>>>(g, epsT, r, ev, first, band_nz, fb);
+}
+
+#define GP_INST(T)                                                                                           \
+    template void launch_residual64<T>(const Geo&, const double*, const double*, const double*, T*, double*, \
+                                       cudaStream_t);                                                        \
+    template void launch_update_phi<T>(const Geo&, double*, const T*, const T*, int, int, cudaStream_t);     \
+    template void launch_rbgs<T>(const LV<T>&, T*, const T*, int, cudaStream_t);                             \
+    template void launch_residual<T>(const LV<T>&, const T*, const T*, T*, cudaStream_t);                    \
+    template void launch_restrict<T>(const LV<T>&, const T*, const LV<T>&, T*, cudaStream_t);                \
+    template void launch_prolong_add<T>(const LV<T>&, T*, const LV<T>&, const T*, cudaStream_t);             \
+    template void launch_coarsen_faces<T>(const LV<T>&, int, int, int, T*, T*, T*, cudaStream_t);            \
+    template void launch_coarse_matrix<T>(const LV<T>&, double*, cudaStream_t);                              \
+    template void launch_store_inverse<T>(const double*, int, T*, cudaStream_t);                             \
+    template void launch_coarse_solve<T>(const LV<T>&, const T*, int, const T*, T*, cudaStream_t);           \
+    template void launch_applyA_dot<T>(const LV<T>&, const T*, T*, double*, cudaStream_t);                   \
+    template void launch_dot<T>(const LV<T>&, const T*, const T*, double*, cudaStream_t);                    \
+    template void launch_update_xr<T>(const LV<T>&, T*, T*, const T*, const T*, const double*, int, int,     \
+                                      cudaStream_t);                                                         \
+    template void launch_update_p<T>(const LV<T>&, T*, const T*, const double*, int, int, cudaStream_t);     \
+    template void launch_copy_level<T>(const LV<T>&, T*, const T*, cudaStream_t);                            \
+    template void launch_cast_eps<T>(long, const double*, T*, cudaStream_t);                                 \
+    template void launch_band_eps<T>(const Geo&, const T*, int, int, T*, cudaStream_t);                      \
+    template void launch_band_rhs<T>(const Geo&, const T*, const T*, const T*, int, int, T*, cudaStream_t);
+
+GP_INST(float)
+GP_INST(double)
+
+}  // namespace gp

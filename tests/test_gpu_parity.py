@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle.
+
+Small cases compare element by element; the full-size workloads compare
+sampled outputs the oracle computes one by one, and properties that hold at
+any size (the FP64 residual measured by the oracle's own operator, the energy
+identity). Tolerances: FP64 path 1e-10 relative for phi and E; mixed precision
+1e-8 for E and phi, 1e-6 for forces.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W
+from oracle import gp_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0904_4887_gb300 import GPSolver
+    return GPSolver
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _gauss(at):
+    return np.stack([at.Z, at.sigma_core, at.sigma_cloud], axis=1)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _case(grid, cell, n, layers, seed=0):
+    at = W.slab_atoms(cell, n, layers, seed=seed)
+    h = O.spacing(grid, cell)
+    eps = O.dielectric(grid, cell, at.pos)
+    rho = O.charge_density(grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud)
+    return at, h, eps, rho
+
+
+SMALL = [((32, 32, 64), (10.0, 10.0, 20.0), 2, 3),       # the 32x32x64 full-box workload
+         ((24, 24, 48), (10.0, 10.0, 20.0), 2, 3),       # 3 * 2^k extents, ragged 32-wide tiles
+         ((16, 8, 24), (7.0, 6.5, 12.0), 1, 2)]          # anisotropic, tiny
+
+
+@pytest.fixture(scope="module")
+def small_cases():
+    return [(_case(g, c, n, l), g, c) for g, c, n, l in SMALL]
+
+
+# ------------------------------------------------------------------ fields
+
+@pytest.mark.parametrize("k", range(len(SMALL)))
+def test_dielectric_matches_oracle(small_cases, k):
+    GPSolver = _gpu()
+    (at, h, eps, rho), grid, cell = small_cases[k]
+    s = GPSolver(grid, cell)
+    s.set_atoms(_t(at.pos))
+    e = s.eps().cpu().numpy()
+    assert _rel(e, eps) < 1e-13
+    pm = s.plane_max()
+    assert np.array_equal(pm < 1e-3, O.dry_planes(eps))
+
+
+@pytest.mark.parametrize("k", range(len(SMALL)))
+def test_charge_density_matches_oracle(small_cases, k):
+    GPSolver = _gpu()
+    (at, h, eps, rho), grid, cell = small_cases[k]
+    s = GPSolver(grid, cell)
+    r = s.build_rho(_t(at.pos), _t(_gauss(at))).cpu().numpy()
+    assert np.max(np.abs(r - rho)) < 1e-12 * np.max(np.abs(rho))
+
+
+def test_empty_atom_list_gives_uniform_eps():
+    GPSolver = _gpu()
+    s = GPSolver((16, 16, 16), (8.0, 8.0, 8.0))
+    s.set_atoms(torch.zeros((0, 3), dtype=torch.float64, device=DEV))
+    assert torch.all(s.eps() == 78.36)
+
+
+# ------------------------------------------------------------------ operators
+
+@pytest.mark.parametrize("k", range(len(SMALL)))
+def test_fft_poisson_matches_oracle(small_cases, k):
+    GPSolver = _gpu()
+    (at, h, eps, rho), grid, cell = small_cases[k]
+    s = GPSolver(grid, cell)
+    src = W.random_field(eps.shape, seed=k)
+    got = s.fft_poisson(_t(src)).cpu().numpy()
+    ref = O.fft_poisson(src, h)
+    assert _rel(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("k", range(len(SMALL)))
+def test_fp64_residual_matches_oracle(small_cases, k):
+    GPSolver = _gpu()
+    (at, h, eps, rho), grid, cell = small_cases[k]
+    s = GPSolver(grid, cell)
+    s.set_atoms(_t(at.pos))
+    phi = W.random_field(eps.shape, seed=10 + k)
+    r, rel = s.residual(_t(rho), _t(phi))
+    ref = -4 * math.pi * rho - O.apply_A(phi, eps, h)
+    assert _rel(r.cpu().numpy(), ref) < 1e-13
+    assert abs(rel - np.linalg.norm(ref) / np.linalg.norm(4 * math.pi * rho)) < 1e-12 * rel
+
+
+# ------------------------------------------------------------------ solves
+
+def _solve_case(small_cases, k, **params):
+    GPSolver = _gpu()
+    (at, h, eps, rho), grid, cell = small_cases[k]
+    s = GPSolver(grid, cell, **params)
+    s.set_atoms(_t(at.pos))
+    rho_t = _t(rho)
+    phi = s.solve(rho_t, tol=1e-13 if params.get("precision", 1) == 0 else 1e-12)
+    ref, info = O.solve(rho, eps, h, tol=1e-14)
+    return s, phi.cpu().numpy(), ref, rho, grid, cell, eps
+
+
+@pytest.mark.parametrize("k", range(len(SMALL)))
+@pytest.mark.parametrize("split", [0, 1])
+def test_fp64_solve_matches_oracle(small_cases, k, split):
+    s, phi, ref, rho, grid, cell, eps = _solve_case(small_cases, k, precision=0, split=split, inner=6)
+    assert _rel(phi, ref) < 1e-10
+    E = O.energy(rho, phi, grid, cell)
+    E0 = O.energy(rho, ref, grid, cell)
+    assert abs(E - E0) < 1e-10 * abs(E0)
+    st = s.stats()
+    assert st.residual < 1e-13
+
+
+@pytest.mark.parametrize("k", range(len(SMALL)))
+@pytest.mark.parametrize("split", [0, 1])
+def test_mixed_solve_matches_oracle(small_cases, k, split):
+    s, phi, ref, rho, grid, cell, eps = _solve_case(small_cases, k, precision=1, split=split)
+    assert _rel(phi, ref) < 1e-8
+    E = O.energy(rho, phi, grid, cell)
+    E0 = O.energy(rho, ref, grid, cell)
+    assert abs(E - E0) < 1e-8 * abs(E0)
+
+
+def test_split_band_matches_oracle_planner(small_cases):
+    GPSolver = _gpu()
+    (at, h, eps, rho), grid, cell = small_cases[0]
+    s = GPSolver(grid, cell, split=1, precision=0)
+    s.set_atoms(_t(at.pos))
+    st = s.stats()
+    levels = st.levels
+    expect = O.plan_band(O.dry_planes(eps), levels, 1)
+    assert expect is not None and st.split_active == 1
+    assert (st.band_first, st.band_dirichlet) == expect
+    assert st.dry_planes == int(O.dry_planes(eps).sum())
+
+
+def test_uniform_eps_is_vacuum_over_eps0():
+    """No atoms: eps = eps0 everywhere and phi = phi_vac / eps0 (a closed form)."""
+    GPSolver = _gpu()
+    grid, cell = (32, 32, 32), (10.0, 10.0, 10.0)
+    h = O.spacing(grid, cell)
+    rho = W.random_field((32, 32, 32), seed=3)
+    s = GPSolver(grid, cell, precision=0)
+    s.set_atoms(torch.zeros((0, 3), dtype=torch.float64, device=DEV))
+    phi = s.solve(_t(rho), tol=1e-13).cpu().numpy()
+    ref = O.vacuum_potential(rho, h) / 78.36
+    assert _rel(phi, ref) < 1e-10
+
+
+# ------------------------------------------------------------------ energy, forces
+
+def test_energy_and_forces_match_oracle():
+    GPSolver = _gpu()
+    grid, cell = (32, 32, 48), (10.0, 10.0, 15.0)
+    at, h, eps, rho = _case(grid, cell, 2, 3, seed=2)
+    s = GPSolver(grid, cell, precision=0)
+    pos = _t(at.pos)
+    s.set_atoms(pos)
+    phi = s.solve(_t(rho), tol=1e-13)
+    E, E2, F = s.energy_forces(phi, _t(rho), _t(_gauss(at)))
+    p = phi.cpu().numpy()
+    Ge, Gr = O.energy_gradient(p, grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud)
+    Fo = -(Ge + Gr)
+    assert _rel(F.cpu().numpy(), Fo) < 1e-10
+    Eo = O.energy(rho, p, grid, cell)
+    assert abs(E - Eo) < 1e-12 * abs(Eo)
+    assert abs(E2 - O.field_energy(p, eps, grid, cell)) < 1e-12 * abs(Eo)
+    assert abs(E - E2) < 1e-10 * abs(E)          # Eq. 4 identity at convergence
+    # solvent (eps) part alone
+    _, _, Fe = s.energy_forces(phi, _t(rho), None)
+    assert _rel(Fe.cpu().numpy(), -Ge) < 1e-10
+
+
+def test_autograd_forces_match_central_differences():
+    """dE/dR from the hand-written backward against central differences of E
+    (h = 1e-4 A) on 6 seeded atoms, rho moving with its atoms."""
+    GPSolver = _gpu()
+    from paper_0904_4887_gb300 import poisson_energy
+    grid, cell = (32, 32, 64), (10.0, 10.0, 20.0)
+    at = W.slab_atoms(cell, 2, 3, seed=4)
+    s = GPSolver(grid, cell, precision=0)
+    gauss = _t(_gauss(at))
+
+    def energy(p):
+        pt = _t(p)
+        rho = s.build_rho(pt, gauss)
+        E, _ = poisson_energy(pt, rho, s, tol=1e-13, gauss=gauss)
+        return float(E)
+
+    pos = _t(at.pos).requires_grad_(True)
+    rho = s.build_rho(pos.detach(), gauss)
+    E, phi = poisson_energy(pos, rho, s, tol=1e-13, gauss=gauss)
+    E.backward()
+    G = pos.grad.cpu().numpy()
+    idx = W.fd_atom_indices(len(at.Z), 6, seed=0)
+    d = 1e-4
+    fd = np.zeros((len(idx), 3))
+    for t, a in enumerate(idx):
+        for c in range(3):
+            pp = at.pos.copy(); pp[a, c] += d
+            pm = at.pos.copy(); pm[a, c] -= d
+            fd[t, c] = (energy(pp) - energy(pm)) / (2 * d)
+    err = np.max(np.abs(fd - G[idx])) / np.max(np.abs(fd))
+    assert err < 1e-6, err
+
+
+def test_grad_rho_is_h3_phi():
+    GPSolver = _gpu()
+    from paper_0904_4887_gb300 import poisson_energy
+    grid, cell = (16, 16, 32), (10.0, 10.0, 20.0)
+    at, h, eps, rho = _case(grid, cell, 2, 2)
+    s = GPSolver(grid, cell, precision=0)
+    rho_t = _t(rho).requires_grad_(True)
+    E, phi = poisson_energy(_t(at.pos), rho_t, s, tol=1e-13)
+    E.backward()
+    assert torch.allclose(rho_t.grad, phi * s.dv, rtol=0, atol=0)
+
+
+# ------------------------------------------------------------------ errors
+
+def test_error_paths():
+    GPSolver = _gpu()
+    from paper_0904_4887_gb300 import GPError
+    grid, cell = (16, 16, 16), (8.0, 8.0, 8.0)
+    s = GPSolver(grid, cell)
+    rho = torch.ones((16, 16, 16), dtype=torch.float64, device=DEV)
+    with pytest.raises(GPError) as e:
+        s.solve(rho - rho.mean(), tol=1e-8)
+    assert e.value.status == 8                      # no dielectric yet
+    s.set_atoms(torch.zeros((0, 3), dtype=torch.float64, device=DEV))
+    with pytest.raises(GPError) as e:
+        s.solve(rho, tol=1e-8)                      # not neutral
+    assert e.value.status == 2
+    with pytest.raises(GPError) as e:
+        s.solve(rho - rho.mean(), tol=0.0)
+    assert e.value.status == 1
+    z = s.solve(torch.zeros_like(rho), tol=1e-8)
+    assert torch.count_nonzero(z) == 0
+    with pytest.raises(GPError):
+        GPSolver((10, 16, 16), cell)                # 10 is not 2^a 3^b
