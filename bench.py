@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the generalized-Poisson hot path on GB300.
+
+One step = the whole hot path over one synthetic slab configuration:
+  eps(R) and the multigrid hierarchy / wet band  (gp_set_dielectric)
+  the Gaussian charge density                    (gp_build_rho)
+  the solve to the relative-residual tolerance   (gp_solve, cold start)
+  energy and forces                              (gp_energy_forces)
+Inputs (atom positions, Gaussian widths) are resident in HBM before the timed
+region; every step uses a new frame of a seeded ballistic trajectory.
+
+Prints ONE JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
+instead, on bounded samples of the same workload, and prints its own line.
+Multi-GPU (torchrun, N > 1): independent replicas, one per GPU, no collective
+on the data path ("scaling": "weak"); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "generalized-Poisson solves/s at 1e-8 rel. residual, mixed vs FP64; smoother HBM GB/s"
+UNIT = "solves/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (non-tensor), the profiling recipe's table
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- inputs
+def make_inputs(w, frames, seed=0):
+    at = W.workload_atoms(w, seed=seed)
+    traj = W.md_frames(at, w.cell, frames, dt_fs=w.dt_fs, temperature=w.temperature, seed=seed)
+    gauss = np.stack([at.Z, at.sigma_core, at.sigma_cloud], axis=1)
+    return at, traj, gauss
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def roofline_for(kind, prof, n0, hbm, hbm_src, prec_bytes):
+    """Achieved vs peak for the kernel group `kind` from the live CUDA-event profile."""
+    p = prof[kind]
+    if p["launches"] == 0 or p["ms"] <= 0:
+        return None
+    per_launch_s = p["ms"] / 1e3 / p["launches"]
+    if kind == "smooth0":
+        # one red or black half sweep: half of the 16 B/pt (FP32) or 32 B/pt (FP64) sweep
+        bytes_per_launch = 0.5 * (4 * prec_bytes) * n0
+        achieved = bytes_per_launch / per_launch_s / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": hbm_src, "kernel": "k_rbgs (finest level, half sweep)",
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": per_launch_s * 1e3}
+    if kind == "res64":
+        # read phi, rho, eps (FP64), write r in the working precision; 30 FP64 flops per point
+        bytes_per_launch = (24 + prec_bytes) * n0
+        flops = 30.0 * n0
+        ach_f = flops / per_launch_s / 1e9
+        return {"bound": "alu", "achieved": ach_f, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": ach_f / FP64_PEAK_GFLOPS, "peak_source": "nominal FP64 (recipe table)",
+                "kernel": "k_residual64", "hbm_gbs": bytes_per_launch / per_launch_s / 1e9,
+                "avg_launch_ms": per_launch_s * 1e3}
+    return {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": None,
+            "kernel": kind, "avg_launch_ms": per_launch_s * 1e3,
+            "note": "FP64 special-function kernel; no algorithmic flop count is defined for it"}
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    import paper_0904_4887_gb300 as P
+    from paper_0904_4887_gb300 import gp as G
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.WORKLOADS[args.workload]
+    nfr = args.warmup + args.steps
+    at, traj, gauss_np = make_inputs(w, max(nfr, 2), seed=rank)
+    gauss = torch.tensor(gauss_np, dtype=torch.float64, device=dev)
+    frames = [torch.tensor(traj[i % len(traj)], dtype=torch.float64, device=dev) for i in range(nfr)]
+    hbm, hbm_src = load_peaks()
+
+    def make_solver(precision, split):
+        return P.GPSolver(w.grid, w.cell, precision=precision, split=split, levels=w.levels)
+
+    solver = make_solver(args.precision, args.split)
+    rho = solver.zeros()
+    phi = solver.zeros()
+    F = torch.zeros((len(at.Z), 3), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(s, pos, phi_buf, rho_buf):
+        s.set_atoms(pos)
+        s.build_rho(pos, gauss, out=rho_buf)
+        phi_buf.zero_()
+        st = s.ctx.gp_solve(rho_buf, phi_buf, args.tol, check=False)
+        if st not in (0,):
+            raise RuntimeError("solve failed: %s %s" % (G.STATUS_NAMES.get(st), s.ctx._lib.gp_last_error(s.ctx._h)))
+        E, E2 = s.ctx.gp_energy_forces(phi_buf, rho_buf, gauss, F)
+        return E
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        step(solver, frames[i], phi, rho)
+    solver.ctx.gp_profile(True)
+    launches0 = G.gp_launch_count()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    outer, vcyc = [], []
+    e0.record(stream)
+    for i in range(args.steps):
+        step(solver, frames[args.warmup + i], phi, rho)
+        st = solver.stats()
+        outer.append(st.outer_iterations)
+        vcyc.append(st.vcycles)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    launches = G.gp_launch_count() - launches0
+    prof = solver.ctx.gp_get_profile()
+    solver.ctx.gp_profile(False)
+    stats = solver.stats()
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * args.steps / (ms_total / 1e3)
+
+    if rank != 0:
+        return None
+
+    # level-0 size of the multigrid in use (band or full box)
+    n_full = w.n_points
+    n0 = int(round(n_full * (stats.wet_fraction if stats.split_active else 1.0)))
+    prec_bytes = 4 if args.precision == 1 else 8
+    total_ms = sum(v["ms"] for v in prof.values())
+    dominant = max(prof, key=lambda k: prof[k]["ms"])
+    roof = roofline_for(dominant, prof, n0, hbm, hbm_src, prec_bytes) or {}
+    roof["traffic"] = None
+    smooth = roofline_for("smooth0", prof, n0, hbm, hbm_src, prec_bytes)
+    phases = {k: {"ms_per_step": v["ms"] / args.steps, "share": (v["ms"] / total_ms if total_ms else 0.0),
+                  "launches_per_step": v["launches"] / args.steps} for k, v in prof.items() if v["launches"]}
+
+    # FP64 full-box comparator (the plain FP64 multigrid) on the same frames
+    comparator = None
+    if not args.no_comparator:
+        s64 = make_solver(0, 0)
+        step(s64, frames[0], phi, rho)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        ncmp = max(1, min(args.steps, 3))
+        c0.record(stream)
+        for i in range(ncmp):
+            step(s64, frames[args.warmup + i], phi, rho)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        comparator = {"solver": "FP64 full-box multigrid (precision=0, split=0)",
+                      "value": ncmp / (c0.elapsed_time(c1) / 1e3), "unit": UNIT, "steps": ncmp,
+                      "outer_iterations": s64.stats().outer_iterations}
+        del s64
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pos_h = [torch.tensor(traj[i % len(traj)], dtype=torch.float64).pin_memory() for i in range(args.steps)]
+        gauss_h = torch.tensor(gauss_np, dtype=torch.float64).pin_memory()
+        phi_h = torch.empty(solver.shape, dtype=torch.float64).pin_memory()
+        F_h = torch.empty((len(at.Z), 3), dtype=torch.float64).pin_memory()
+        pos_d = torch.empty((len(at.Z), 3), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            pos_d.copy_(pos_h[i], non_blocking=True)
+            gauss.copy_(gauss_h, non_blocking=True)
+            step(solver, pos_d, phi, rho)
+            phi_h.copy_(phi, non_blocking=True)
+            F_h.copy_(F, non_blocking=True)
+            torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e = {"value": args.steps / (t1 - t0), "unit": UNIT,
+               "h2d_bytes_per_step": int(pos_h[0].numel() * 8 + gauss_h.numel() * 8),
+               "d2h_bytes_per_step": int(phi_h.numel() * 8 + F_h.numel() * 8 + 16)}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = oracle_sample(w, at, traj[0], budget_s=args.cpu_budget)
+        cpu = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
+               "sample": cpu["sample"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/f64" if args.precision == 1 else "f64", "data": "synthetic",
+        "config": {"workload": w.name, "grid": list(w.grid), "cell_A": list(w.cell), "atoms": int(len(at.Z)),
+                   "tol": args.tol, "precision": "mixed" if args.precision == 1 else "fp64",
+                   "split": bool(args.split), "split_active": bool(stats.split_active),
+                   "wet_fraction": stats.wet_fraction, "levels": stats.levels,
+                   "outer_iterations_mean": float(np.mean(outer)), "vcycles_mean": float(np.mean(vcyc)),
+                   "l2": "inputs larger than L2 (FP64 fields of 113 MB each)",
+                   "step": "set_dielectric + build_rho + solve (cold) + energy_forces",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof, "smoother": smooth, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk, "fp64_fullbox": comparator, "phases": phases, "dominant_kernel_group": dominant,
+    }
+    return line
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) arm
+def oracle_sample(w, at, pos, budget_s=20.0):
+    """Time the FP64 oracle on bounded samples of the workload and scale to one
+    step: eps and rho for a subset of atoms (scaled by n/m), a few PCG
+    iterations (scaled by the iteration count its measured contraction needs
+    for the tolerance), and the force terms for a subset of atoms."""
+    from oracle import gp_oracle as O
+
+    grid, cell = w.grid, w.cell
+    h = O.spacing(grid, cell)
+    n = len(at.Z)
+    m = max(2, min(n, int(n * min(1.0, budget_s / 400.0))))
+    sel = np.arange(m)
+    t0 = time.perf_counter()
+    P = O.dielectric_product(grid, cell, pos[sel])
+    t_eps = (time.perf_counter() - t0) * n / m
+    t0 = time.perf_counter()
+    O.charge_density_raw(grid, cell, pos[sel], at.Z[sel], at.sigma_core[sel], at.sigma_cloud[sel])
+    t_rho = (time.perf_counter() - t0) * n / m
+    # (the density of the sampled atoms also serves as the right-hand side below)
+    eps = 1.0 + 77.36 * P
+    rho = O.charge_density(grid, cell, pos[sel], at.Z[sel], at.sigma_core[sel], at.sigma_cloud[sel])
+    k = 2
+    t0 = time.perf_counter()
+    phi, info = O.solve(rho, eps, h, tol=1e-300, maxiter=k)
+    t_it = (time.perf_counter() - t0) / k
+    rate = max(min(info.residual ** (1.0 / k), 0.95), 0.05)
+    iters = math.ceil(math.log(1e-8) / math.log(rate))
+    t_solve = t_it * iters
+    t0 = time.perf_counter()
+    O.energy_gradient(phi, grid, cell, pos[sel[:1]], at.Z[:1], at.sigma_core[:1], at.sigma_cloud[:1])
+    t_force = (time.perf_counter() - t0) * n
+    t_step = t_eps + t_rho + t_solve + t_force
+    return {"value": 1.0 / t_step, "cores": 1, "t_step_s": t_step,
+            "sample": ("%s: eps and rho over %d of %d atoms (x%.0f), %d PCG iterations x %d needed for 1e-8 "
+                       "(measured contraction %.3f), forces of 1 atom (x%d); numpy single thread"
+                       % (w.name, m, n, n / m, k, iters, rate, n))}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return None
+    w = W.WORKLOADS[args.workload]
+    at, traj, _ = make_inputs(w, 2)
+    budget = max(2.0, min(args.cpu_budget, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(w, at, traj[i % len(traj)], budget_s=budget)
+        if i >= args.warmup:
+            vals.append(r["t_step_s"])
+            last = r
+    t = float(np.mean(vals))
+    value = 1.0 / t
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.grid), "cell_A": list(w.cell), "atoms": int(len(at.Z)),
+                       "tol": args.tol, "solver": "FP64 CPU oracle (FFT-preconditioned CG), sampled"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gp", choices=["gp", "reference"])
+    ap.add_argument("--workload", default="mixed_192x192x384", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--split", type=int, default=1)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gp":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "gp":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    line = reference_arm(args, rank, world) if args.impl == "reference" else gpu_arm(args, rank, world)
+    if line is not None:
+        print(json.dumps(line))
+    if world > 1 and args.impl == "gp":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -173,6 +173,38 @@ int gp_plan_band(const int* dry, int nz, int levels, int n_dirichlet, int* first
  * reaching <= 512 points. Returns -1 if impossible. Needs no GPU. */
 int gp_plan_levels(int nx, int ny, int nz, int zper, int requested);
 
+/* Kernel groups timed by gp_profile (indices into the arrays of gp_get_profile). */
+enum {
+    GP_PROF_EPS = 0,         /* dielectric builder */
+    GP_PROF_RHO = 1,         /* Gaussian charge density */
+    GP_PROF_FORCES_EPS = 2,  /* dielectric (solvent) force */
+    GP_PROF_FORCES_RHO = 3,  /* charge-motion force */
+    GP_PROF_RES64 = 4,       /* FP64 full-box residual + norm (outer correction) */
+    GP_PROF_SMOOTH0 = 5,     /* red-black Gauss-Seidel on the finest multigrid level */
+    GP_PROF_MG_FINE = 6,     /* finest-level residual, restriction, prolongation */
+    GP_PROF_MG_COARSE = 7,   /* all coarser levels and the coarsest solve */
+    GP_PROF_KRYLOV = 8,      /* CG operator application, dot products, updates */
+    GP_PROF_FFT = 9,         /* the five FFT Poisson passes */
+    GP_PROF_SETUP = 10,      /* coarse coefficients and the coarsest inverse */
+    GP_PROF_MISC = 11,       /* reductions, gauge, atom wrapping */
+    GP_PROF_UPDATE64 = 12,   /* FP64 phi update */
+    GP_PROF_ENERGY = 13,     /* energy reductions */
+    GP_PROF_KINDS = 14
+};
+
+/* Enable (1) or disable (0) CUDA-event timing of kernel groups on this
+ * context's stream. Timing adds two event records per group and never
+ * changes results. Enabling resets the totals. */
+gp_status gp_profile(gp_ctx* ctx, int enable);
+
+/* Totals since gp_profile(ctx, 1): ms[k] device milliseconds, launches[k]
+ * kernel launches and groups[k] timed groups for each kind k < n (n <=
+ * GP_PROF_KINDS); host arrays, any may be NULL. */
+gp_status gp_get_profile(const gp_ctx* ctx, double* ms, long* launches, long* groups, int n);
+
+/* Process-wide count of kernels this library has launched (host-only). */
+long gp_launch_count(void);
+
 /* Statistics of the last gp_set_dielectric / gp_solve. */
 gp_status gp_get_stats(const gp_ctx* ctx, gp_stats* out);
 

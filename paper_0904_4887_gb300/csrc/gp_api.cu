@@ -4,6 +4,7 @@
 // correction that couples the dry FFT solution to the wet multigrid band.
 #include "gp_common.cuh"
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -97,11 +98,14 @@ int plan_levels(int nx, int ny, int nz, int zper, int requested, std::string& wh
         if (pts > kMaxCoarse) { why = "coarsest grid of the requested levels exceeds 512 points"; return -1; }
         return requested;
     }
+    int best = -1;
     for (int l = 1; l < 16; ++l) {
         long pts = 0;
         if (!dims_ok(l, pts)) break;
-        if (pts <= kMaxCoarse) return l + 1;
+        if (pts <= kMaxCoarse) best = l + 1;
+        if (pts <= kAutoCoarse) return l + 1;
     }
+    if (best > 0) return best;
     why = "grid cannot be coarsened to <= 512 points";
     return -1;
 }
@@ -123,9 +127,13 @@ struct gp_ctx {
     double* pe64 = nullptr;
     float* eps32 = nullptr;
     double* plane_max = nullptr;
-    double* atoms = nullptr;       // copy of the positions of the last set_dielectric
+    double* atoms = nullptr;       // positions of the last set_dielectric, wrapped into the cell
+    float4* atoms32 = nullptr;
     int n_atoms = 0;
     int atoms_cap = 0;
+    double* ratoms = nullptr;      // gp_build_rho's positions, wrapped
+    float4* ratoms32 = nullptr;
+    int ratoms_cap = 0;
     double* partial = nullptr;     // kReduceBlocks * 4
     double* scal = nullptr;        // device scalars
     int* dstatus = nullptr;
@@ -146,9 +154,66 @@ struct gp_ctx {
     int band_first = -1, band_nd = 0, band_nz = 0, band_first_interior = 0;
     bool split_ok = false;
     std::vector<void*> misc;
+
+    // optional per-kernel-group timing (gp_profile)
+    bool prof_on = false;
+    struct Pending { int kind; int launches; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double prof_ms[GP_PROF_KINDS] = {};
+    long prof_launches[GP_PROF_KINDS] = {};
+    long prof_groups[GP_PROF_KINDS] = {};
 };
 
 namespace {
+
+std::atomic<long> g_launches{0};
+
+inline void count_launch(long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaEvent_t prof_event(gp_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    GP_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+// brackets a group of `launches` kernels of one kind with events on the stream
+struct ProfScope {
+    gp_ctx* c; int kind; int launches; cudaEvent_t a{}, b{};
+    ProfScope(gp_ctx* c_, int k, int n) : c(c_), kind(k), launches(n) {
+        count_launch(n);
+        if (c->prof_on) { a = prof_event(c); GP_CUDA(cudaEventRecord(a, c->s)); }
+    }
+    ~ProfScope() {
+        // never throws: a failed record only loses this sample
+        if (c->prof_on && a) {
+            cudaEvent_t e = nullptr;
+            if (!c->event_pool.empty()) { e = c->event_pool.back(); c->event_pool.pop_back(); }
+            else if (cudaEventCreate(&e) != cudaSuccess) return;
+            if (cudaEventRecord(e, c->s) != cudaSuccess) { c->event_pool.push_back(e); return; }
+            c->pending.push_back({kind, launches, a, e});
+        }
+    }
+};
+
+// after the stream is synchronised: fold the event pairs into the totals
+void prof_collect(gp_ctx* c) {
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        GP_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+        c->prof_ms[p.kind] += ms;
+        c->prof_launches[p.kind] += p.launches;
+        c->prof_groups[p.kind] += 1;
+        c->event_pool.push_back(p.a);
+        c->event_pool.push_back(p.b);
+    }
+    c->pending.clear();
+}
 
 void* dalloc(gp_ctx* c, size_t bytes) {
     void* p = nullptr;
@@ -159,7 +224,7 @@ void* dalloc(gp_ctx* c, size_t bytes) {
 }
 
 double sum_host(gp_ctx* c, int ncomp, double* out) {
-    launch_finalize(c->partial, kReduceBlocks, ncomp, c->scal + 8, c->s);
+    { ProfScope ps(c, GP_PROF_MISC, 1); launch_finalize(c->partial, kReduceBlocks, ncomp, c->scal + 8, c->s); }
     GP_CHECK_LAUNCH();
     GP_CUDA(cudaMemcpyAsync(out, c->scal + 8, sizeof(double) * ncomp, cudaMemcpyDeviceToHost, c->s));
     GP_CUDA(cudaStreamSynchronize(c->s));
@@ -220,20 +285,24 @@ void coarse_coeffs(gp_ctx* c, Hier<T>& H) {
     for (int l = 1; l < levels; ++l) {
         const LV<T>& F = H.lv[l - 1];
         LV<T>& C = H.lv[l];
+        ProfScope ps(c, GP_PROF_SETUP, 1);
         launch_coarsen_faces<T>(F, C.nx, C.ny, C.nz, H.cx[l], H.cy[l], H.cz[l], c->s);
         GP_CHECK_LAUNCH();
     }
     // dense inverse of the coarsest operator
     const LV<T>& C = H.lv[levels - 1];
     if (levels == 1) throw Err{GP_ERR_INVALID_ARG, "multigrid needs at least two levels"};
-    launch_coarse_matrix<T>(C, c->gmat, c->s);
-    GP_CHECK_LAUNCH();
-    launch_gauss_jordan(c->gmat, H.nc, c->dstatus, c->s);
+    {
+        ProfScope ps(c, GP_PROF_SETUP, 2);
+        launch_coarse_matrix<T>(C, c->gmat, c->s);
+        launch_gauss_jordan(c->gmat, H.nc, c->dstatus, c->s);
+    }
     GP_CHECK_LAUNCH();
     int st = 0;
     GP_CUDA(cudaMemcpyAsync(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     GP_CUDA(cudaStreamSynchronize(c->s));
     if (st != 0) throw Err{GP_ERR_INVALID_ARG, "coarsest multigrid operator is singular"};
+    ProfScope ps(c, GP_PROF_SETUP, 1);
     launch_store_inverse<T>(c->gmat + (size_t)H.nc * H.nc, H.nc, H.minv, c->s);
     GP_CHECK_LAUNCH();
 }
@@ -247,19 +316,30 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
         T* u = l == 0 ? u0 : H.u[l];
         const T* f = l == 0 ? f0 : H.f[l];
         GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
-        for (int it = 0; it < c->prm.nu1; ++it) {
-            launch_rbgs<T>(V, u, f, 0, c->s);
-            launch_rbgs<T>(V, u, f, 1, c->s);
+        {
+            ProfScope ps(c, l == 0 ? GP_PROF_SMOOTH0 : GP_PROF_MG_COARSE, 2 * c->prm.nu1);
+            for (int it = 0; it < c->prm.nu1; ++it) {
+                launch_rbgs<T>(V, u, f, 0, c->s);
+                launch_rbgs<T>(V, u, f, 1, c->s);
+            }
         }
+        ProfScope ps(c, l == 0 ? GP_PROF_MG_FINE : GP_PROF_MG_COARSE, 2);
         launch_residual<T>(V, u, f, H.res[l], c->s);
         launch_restrict<T>(V, H.res[l], H.lv[l + 1], H.f[l + 1], c->s);
     }
-    launch_coarse_solve<T>(H.lv[L - 1], H.minv, H.nc, H.f[L - 1], H.u[L - 1], c->s);
+    {
+        ProfScope ps(c, GP_PROF_MG_COARSE, 1);
+        launch_coarse_solve<T>(H.lv[L - 1], H.minv, H.nc, H.f[L - 1], H.u[L - 1], c->s);
+    }
     for (int l = L - 2; l >= 0; --l) {
         const LV<T>& V = H.lv[l];
         T* u = l == 0 ? u0 : H.u[l];
         const T* f = l == 0 ? f0 : H.f[l];
-        launch_prolong_add<T>(V, u, H.lv[l + 1], H.u[l + 1], c->s);
+        {
+            ProfScope ps(c, l == 0 ? GP_PROF_MG_FINE : GP_PROF_MG_COARSE, 1);
+            launch_prolong_add<T>(V, u, H.lv[l + 1], H.u[l + 1], c->s);
+        }
+        ProfScope ps(c, l == 0 ? GP_PROF_SMOOTH0 : GP_PROF_MG_COARSE, 2 * c->prm.nu2);
         for (int it = 0; it < c->prm.nu2; ++it) {
             launch_rbgs<T>(V, u, f, 1, c->s);
             launch_rbgs<T>(V, u, f, 0, c->s);
@@ -276,20 +356,29 @@ void pcg(gp_ctx* c, Hier<T>& H, int iters) {
     GP_CUDA(cudaMemsetAsync(lbase(V, H.x), 0, level_bytes(V), c->s));
     vcycle(c, H, H.z, H.r);
     int cur = 0;
-    launch_dot<T>(V, H.r, H.z, c->partial, c->s);
-    launch_finalize(c->partial, kReduceBlocks, 1, c->scal + cur, c->s);
-    launch_copy_level<T>(V, H.p, H.z, c->s);
+    {
+        ProfScope ps(c, GP_PROF_KRYLOV, 3);
+        launch_dot<T>(V, H.r, H.z, c->partial, c->s);
+        launch_finalize(c->partial, kReduceBlocks, 1, c->scal + cur, c->s);
+        launch_copy_level<T>(V, H.p, H.z, c->s);
+    }
     for (int it = 0; it < iters; ++it) {
-        launch_applyA_dot<T>(V, H.p, H.q, c->partial, c->s);
-        launch_finalize(c->partial, kReduceBlocks, 1, c->scal + 1, c->s);
-        launch_update_xr<T>(V, H.x, H.r, H.p, H.q, c->scal, cur, 1, c->s);
+        {
+            ProfScope ps(c, GP_PROF_KRYLOV, 3);
+            launch_applyA_dot<T>(V, H.p, H.q, c->partial, c->s);
+            launch_finalize(c->partial, kReduceBlocks, 1, c->scal + 1, c->s);
+            launch_update_xr<T>(V, H.x, H.r, H.p, H.q, c->scal, cur, 1, c->s);
+        }
         c->stats.inner_iterations++;
         if (it == iters - 1) break;
         vcycle(c, H, H.z, H.r);
         const int nxt = 2 - cur;
-        launch_dot<T>(V, H.r, H.z, c->partial, c->s);
-        launch_finalize(c->partial, kReduceBlocks, 1, c->scal + nxt, c->s);
-        launch_update_p<T>(V, H.p, H.z, c->scal, nxt, cur, c->s);
+        {
+            ProfScope ps(c, GP_PROF_KRYLOV, 3);
+            launch_dot<T>(V, H.r, H.z, c->partial, c->s);
+            launch_finalize(c->partial, kReduceBlocks, 1, c->scal + nxt, c->s);
+            launch_update_p<T>(V, H.p, H.z, c->scal, nxt, cur, c->s);
+        }
         cur = nxt;
     }
     GP_CHECK_LAUNCH();
@@ -366,7 +455,10 @@ void setup_solver(gp_ctx* c) {
             Hier<T>& B = band_hier<T>(c);
             alloc_hier<T>(c, B, c->g.nx, c->g.ny, c->band_nz, 0, c->full_levels, nullptr, true);
             // the band's level-0 eps, walls included, then its coarse levels
-            launch_band_eps<T>(c->g, eps_T<T>(c), c->band_first_interior, c->band_nz, B.eps0, c->s);
+            {
+                ProfScope ps(c, GP_PROF_SETUP, 1);
+                launch_band_eps<T>(c->g, eps_T<T>(c), c->band_first_interior, c->band_nz, B.eps0, c->s);
+            }
             GP_CHECK_LAUNCH();
             coarse_coeffs<T>(c, B);
             if (!c->rfull) c->rfull = dalloc(c, (size_t)c->n * sizeof(double));
@@ -395,9 +487,12 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
     st.outer_iterations = 0; st.inner_iterations = 0; st.vcycles = 0; st.history_len = 0;
     st.residual = NAN;
     double h3[4];
-    launch_rho_stats(c->n, rho, c->partial, c->s);
+    {
+        ProfScope ps(c, GP_PROF_MISC, 2);
+        launch_rho_stats(c->n, rho, c->partial, c->s);
+        launch_finalize(c->partial, kReduceBlocks, 3, c->scal + 8, c->s);
+    }
     GP_CHECK_LAUNCH();
-    launch_finalize(c->partial, kReduceBlocks, 3, c->scal + 8, c->s);
     GP_CUDA(cudaMemcpyAsync(h3, c->scal + 8, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->s));
     GP_CUDA(cudaStreamSynchronize(c->s));
     if (!(std::fabs(h3[0]) <= 1e-10 * h3[1])) {
@@ -418,11 +513,15 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
     gp_status result = GP_ERR_NOT_CONVERGED;
     for (int it = 0; it < c->prm.max_outer; ++it) {
         if (it > 0) {
+            ProfScope ps(c, GP_PROF_UPDATE64, 1);
             if (split) launch_update_phi<T>(c->g, phi, ev, B.x, c->band_first_interior, c->band_nz, c->s);
             else launch_update_phi<T>(c->g, phi, F.x, (const T*)nullptr, 0, 0, c->s);
             GP_CHECK_LAUNCH();
         }
-        launch_residual64<T>(c->g, phi, rho, c->eps64, rT, c->partial, c->s);
+        {
+            ProfScope ps(c, GP_PROF_RES64, 1);
+            launch_residual64<T>(c->g, phi, rho, c->eps64, rT, c->partial, c->s);
+        }
         GP_CHECK_LAUNCH();
         double s2[2];
         sum_host(c, 2, s2);
@@ -435,8 +534,12 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         if (rn <= tol) { result = GP_OK; break; }
         if (it == c->prm.max_outer - 1) break;
         if (split) {
-            fft_poisson<T>(c->fft, rT, ev, c->fft_work, c->s);
+            {
+                ProfScope ps(c, GP_PROF_FFT, 5);
+                fft_poisson<T>(c->fft, rT, ev, c->fft_work, c->s);
+            }
             GP_CHECK_LAUNCH();
+            ProfScope ps(c, GP_PROF_MG_FINE, 1);
             launch_band_rhs<T>(c->g, eps_T<T>(c), rT, ev, c->band_first_interior, c->band_nz, B.r, c->s);
             GP_CHECK_LAUNCH();
             pcg<T>(c, B, c->prm.inner);
@@ -445,9 +548,13 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         }
     }
     // gauge: the last residual pass summed phi into scal[9]
-    launch_sub_mean(c->n, phi, c->scal + 9, 1.0 / (double)c->n, c->s);
+    {
+        ProfScope ps(c, GP_PROF_MISC, 1);
+        launch_sub_mean(c->n, phi, c->scal + 9, 1.0 / (double)c->n, c->s);
+    }
     GP_CHECK_LAUNCH();
     GP_CUDA(cudaStreamSynchronize(c->s));
+    prof_collect(c);
     if (result == GP_ERR_NOT_CONVERGED) c->err = "not converged within max_outer";
     if (result == GP_ERR_DIVERGED) c->err = "residual diverged";
     return result;
@@ -536,19 +643,33 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         c->full_levels = L;
         if (n_atoms > c->atoms_cap) {
             void* a = nullptr;
-            if (cudaMalloc(&a, sizeof(double) * 3 * n_atoms) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+            void* b = nullptr;
+            if (cudaMalloc(&a, sizeof(double) * 3 * n_atoms) != cudaSuccess ||
+                cudaMalloc(&b, sizeof(float4) * n_atoms) != cudaSuccess)
+                throw Err{GP_ERR_OOM, "cudaMalloc failed"};
             if (c->atoms) cudaFree(c->atoms);
+            if (c->atoms32) cudaFree(c->atoms32);
             c->atoms = (double*)a;
+            c->atoms32 = (float4*)b;
             c->atoms_cap = n_atoms;
         }
         c->n_atoms = n_atoms;
-        if (n_atoms > 0)
-            GP_CUDA(cudaMemcpyAsync(c->atoms, atoms_dev, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToDevice, c->s));
-        Atoms at{c->atoms, nullptr, n_atoms};
-        DielParams dp{p.eps0, p.r0, p.w, p.rcut};
-        launch_build_eps(c->g, at, dp, c->eps64, c->pe64, c->eps32, c->s);
+        {
+            ProfScope ps(c, GP_PROF_MISC, n_atoms > 0 ? 1 : 0);
+            launch_wrap_atoms(c->g, atoms_dev, n_atoms, c->atoms, c->atoms32, c->s);
+        }
         GP_CHECK_LAUNCH();
-        launch_plane_max(c->g, c->eps64, c->plane_max, c->s);
+        Atoms at{c->atoms, c->atoms32, nullptr, n_atoms};
+        DielParams dp{p.eps0, p.r0, p.w, p.rcut};
+        {
+            ProfScope ps(c, GP_PROF_EPS, 1);
+            launch_build_eps(c->g, at, dp, c->eps64, c->pe64, c->eps32, c->s);
+        }
+        GP_CHECK_LAUNCH();
+        {
+            ProfScope ps(c, GP_PROF_MISC, 1);
+            launch_plane_max(c->g, c->eps64, c->plane_max, c->s);
+        }
         GP_CHECK_LAUNCH();
         if (p.precision == 1) setup_solver<float>(c);
         else setup_solver<double>(c);
@@ -560,6 +681,7 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         c->stats.dry_planes = nd;
         c->stats.levels = L;
         c->have_eps = true;
+        prof_collect(c);
         c->err.clear();
         return GP_OK;
     } catch (const Err& e) {
@@ -583,14 +705,37 @@ gp_status gp_build_rho(gp_ctx* c, const double* atoms_dev, const double* gauss_d
                     if (!(gh[3 * a + w] > 0) || cut * gh[3 * a + w] > lmin)
                         throw Err{GP_ERR_INVALID_ARG, "Gaussian width must be positive with 8 sigma <= the cell"};
         }
-        Atoms at{atoms_dev, gauss_dev, n_atoms};
-        launch_build_rho_raw(c->g, at, cut, rho_dev, c->s);
+        if (n_atoms > c->ratoms_cap) {
+            void* a = nullptr;
+            void* b = nullptr;
+            if (cudaMalloc(&a, sizeof(double) * 3 * n_atoms) != cudaSuccess ||
+                cudaMalloc(&b, sizeof(float4) * n_atoms) != cudaSuccess)
+                throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+            if (c->ratoms) cudaFree(c->ratoms);
+            if (c->ratoms32) cudaFree(c->ratoms32);
+            c->ratoms = (double*)a;
+            c->ratoms32 = (float4*)b;
+            c->ratoms_cap = n_atoms;
+        }
+        {
+            ProfScope ps(c, GP_PROF_MISC, n_atoms > 0 ? 1 : 0);
+            launch_wrap_atoms(c->g, atoms_dev, n_atoms, c->ratoms, c->ratoms32, c->s);
+        }
+        Atoms at{c->ratoms, c->ratoms32, gauss_dev, n_atoms};
+        {
+            ProfScope ps(c, GP_PROF_RHO, 1);
+            launch_build_rho_raw(c->g, at, cut, rho_dev, c->s);
+        }
         GP_CHECK_LAUNCH();
-        launch_rho_stats(c->n, rho_dev, c->partial, c->s);
-        launch_finalize(c->partial, kReduceBlocks, 3, c->scal + 12, c->s);
-        launch_sub_mean(c->n, rho_dev, c->scal + 12, 1.0 / (double)c->n, c->s);
+        {
+            ProfScope ps(c, GP_PROF_MISC, 3);
+            launch_rho_stats(c->n, rho_dev, c->partial, c->s);
+            launch_finalize(c->partial, kReduceBlocks, 3, c->scal + 12, c->s);
+            launch_sub_mean(c->n, rho_dev, c->scal + 12, 1.0 / (double)c->n, c->s);
+        }
         GP_CHECK_LAUNCH();
         GP_CUDA(cudaStreamSynchronize(c->s));
+        prof_collect(c);
         return GP_OK;
     } catch (const Err& e) {
         return fail(c, e);
@@ -617,7 +762,10 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
         if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_energy_forces"};
         const double dv = c->g.hx * c->g.hy * c->g.hz;
         if (energy_host) {
-            launch_energy(c->g, rho_dev, phi_dev, c->eps64, c->partial, c->s);
+            {
+                ProfScope ps(c, GP_PROF_ENERGY, 1);
+                launch_energy(c->g, rho_dev, phi_dev, c->eps64, c->partial, c->s);
+            }
             GP_CHECK_LAUNCH();
             double e2[2];
             sum_host(c, 2, e2);
@@ -637,19 +785,25 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             }
             GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
             GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->s));
-            Atoms at{c->atoms, gauss_dev, n};
+            Atoms at{c->atoms, c->atoms32, gauss_dev, n};
             DielParams dp{c->prm.eps0, c->prm.r0, c->prm.w, c->prm.rcut};
-            launch_forces_eps(c->g, at, dp, phi_dev, c->pe64, c->forces_S, c->s);
+            {
+                ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
+                launch_forces_eps(c->g, at, dp, phi_dev, c->pe64, c->forces_S, c->s);
+            }
             GP_CHECK_LAUNCH();
             if (gauss_dev) {
+                ProfScope ps(c, GP_PROF_FORCES_RHO, 1);
                 launch_forces_rho(c->g, at, 8.0, phi_dev, c->forces_T, c->s);
-                GP_CHECK_LAUNCH();
             }
+            GP_CHECK_LAUNCH();
+            ProfScope ps(c, GP_PROF_MISC, 1);
             launch_forces_finish(c->forces_S, gauss_dev ? c->forces_T : nullptr, n, -dv / (8.0 * kPi), dv,
                                  forces_dev, c->s);
             GP_CHECK_LAUNCH();
         }
         GP_CUDA(cudaStreamSynchronize(c->s));
+        prof_collect(c);
         return GP_OK;
     } catch (const Err& e) {
         return fail(c, e);
@@ -661,11 +815,13 @@ gp_status gp_residual(gp_ctx* c, const double* rho_dev, const double* phi_dev, d
     try {
         if (!rho_dev || !phi_dev || !r_dev) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
         if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_residual"};
+        count_launch(1);
         launch_residual64<double>(c->g, phi_dev, rho_dev, c->eps64, r_dev, c->partial, c->s);
         GP_CHECK_LAUNCH();
         double s2[2];
         sum_host(c, 2, s2);
         if (rel_host) {
+            count_launch(1);
             launch_rho_stats(c->n, rho_dev, c->partial, c->s);
             GP_CHECK_LAUNCH();
             double h3[3];
@@ -692,6 +848,7 @@ gp_status gp_fft_poisson(gp_ctx* c, const double* src_dev, double* phi_dev) {
             c->fft_work = dalloc(c, wb);
             c->fft_work_bytes = wb;
         }
+        count_launch(5);
         fft_poisson<double>(c->fft, src_dev, phi_dev, c->fft_work, c->s);
         GP_CHECK_LAUNCH();
         GP_CUDA(cudaStreamSynchronize(c->s));
@@ -733,6 +890,32 @@ gp_status gp_get_stats(const gp_ctx* c, gp_stats* out) {
 
 const char* gp_last_error(const gp_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+gp_status gp_profile(gp_ctx* c, int enable) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        prof_collect(c);
+        c->prof_on = enable != 0;
+        if (c->prof_on)
+            for (int k = 0; k < GP_PROF_KINDS; ++k) { c->prof_ms[k] = 0; c->prof_launches[k] = 0; c->prof_groups[k] = 0; }
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_get_profile(const gp_ctx* c, double* ms, long* launches, long* groups, int n) {
+    if (!c || n < 0 || n > GP_PROF_KINDS) return GP_ERR_INVALID_ARG;
+    for (int k = 0; k < n; ++k) {
+        if (ms) ms[k] = c->prof_ms[k];
+        if (launches) launches[k] = c->prof_launches[k];
+        if (groups) groups[k] = c->prof_groups[k];
+    }
+    return GP_OK;
+}
+
+long gp_launch_count(void) { return g_launches.load(); }
+
 int gp_plan_band(const int* dry, int nz, int levels, int n_dirichlet, int* first, int* nd) {
     if (!dry || nz < 1 || levels < 1 || levels > 16 || !first || !nd) return -1;
     std::vector<int> d(dry, dry + nz);
@@ -758,8 +941,13 @@ void gp_destroy(gp_ctx* c) {
     free_hier(c->fullD);
     free_hier(c->bandD);
     if (c->fft) fft_destroy(c->fft);
+    for (auto& p : c->pending) { c->event_pool.push_back(p.a); c->event_pool.push_back(p.b); }
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     for (void* p : c->misc) cudaFree(p);
     if (c->atoms) cudaFree(c->atoms);
+    if (c->atoms32) cudaFree(c->atoms32);
+    if (c->ratoms) cudaFree(c->ratoms);
+    if (c->ratoms32) cudaFree(c->ratoms32);
     if (c->forces_S) cudaFree(c->forces_S);
     if (c->forces_T) cudaFree(c->forces_T);
     delete c;

@@ -11,6 +11,7 @@ namespace gp {
 constexpr int kReduceBlocks = 608;      // 4 x 152 SMs: fixed partial count, deterministic sums
 constexpr int kReduceThreads = 256;
 constexpr int kMaxCoarse = 512;         // largest coarsest grid solved by a dense inverse
+constexpr int kAutoCoarse = 64;         // automatic level choice: coarsen to <= 64 points
 constexpr double kPi = 3.14159265358979323846;
 
 // ---------------------------------------------------------------- level view
@@ -30,7 +31,8 @@ struct LV {
 };
 
 struct Atoms {
-    const double* pos;     // [n][3]
+    const double* w64;     // [n][3] positions wrapped into the cell (launch_wrap_atoms)
+    const float4* w32;     // the same in FP32, for culling
     const double* gauss;   // [n][3] = Z, sigma_core, sigma_cloud (may be null)
     int n;
 };
@@ -49,6 +51,7 @@ __host__ __device__ inline long plane_of(int nx, int ny) { return (long)nx * ny;
 
 // ---------------------------------------------------------------- launchers
 // fields (k_fields.cu)
+void launch_wrap_atoms(const Geo& g, const double* pos, int n, double* w64, float4* w32, cudaStream_t s);
 void launch_build_eps(const Geo& g, Atoms at, DielParams p, double* eps64, double* pe64,
                       float* eps32, cudaStream_t s);
 void launch_build_rho_raw(const Geo& g, Atoms at, double cut_sigmas, double* rho, cudaStream_t s);

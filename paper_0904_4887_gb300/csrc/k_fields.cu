@@ -18,6 +18,32 @@ constexpr float kMargin = 1e-3f;       // FP32 culling slack, Angstrom
 
 __device__ __forceinline__ double wrap_pos(double x, double L) { return x - L * floor(x / L); }
 
+// image `im` (0..26) of wrapped atom a: FP32 centre for culling
+__device__ __forceinline__ void image32(const float4* w32, int a, int im, const Geo& g, float& cx, float& cy,
+                                        float& cz) {
+    const float4 p = w32[a];
+    cx = p.x + (float)((im % 3 - 1) * g.lx);
+    cy = p.y + (float)(((im / 3) % 3 - 1) * g.ly);
+    cz = p.z + (float)((im / 9 - 1) * g.lz);
+}
+
+// the same image in FP64
+__device__ __forceinline__ void image64(const double* w64, int a, int im, const Geo& g, double& cx, double& cy,
+                                        double& cz) {
+    cx = w64[3 * a + 0] + (im % 3 - 1) * g.lx;
+    cy = w64[3 * a + 1] + ((im / 3) % 3 - 1) * g.ly;
+    cz = w64[3 * a + 2] + (im / 9 - 1) * g.lz;
+}
+
+__global__ void k_wrap_atoms(Geo g, const double* pos, int n, double* w64, float4* w32) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    const double x = wrap_pos(pos[3 * a + 0], g.lx), y = wrap_pos(pos[3 * a + 1], g.ly),
+                 z = wrap_pos(pos[3 * a + 2], g.lz);
+    w64[3 * a + 0] = x; w64[3 * a + 1] = y; w64[3 * a + 2] = z;
+    w32[a] = make_float4((float)x, (float)y, (float)z, 0.f);
+}
+
 struct Tile {
     int i0, j0, k0, i1, j1, k1;        // first and last grid index in the tile
     float bx0, bx1, by0, by1, bz0, bz1;
@@ -70,12 +96,11 @@ __global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p,
         const int na = min(ACH, at.n - a0);
         for (int q = threadIdx.x; q < na * 27; q += TT) {
             const int a = a0 + q / 27, im = q % 27;
-            const double cx = wrap_pos(at.pos[3 * a + 0], g.lx) + (im % 3 - 1) * g.lx;
-            const double cy = wrap_pos(at.pos[3 * a + 1], g.ly) + ((im / 3) % 3 - 1) * g.ly;
-            const double cz = wrap_pos(at.pos[3 * a + 2], g.lz) + (im / 9 - 1) * g.lz;
-            if (box_d2(t, (float)cx, (float)cy, (float)cz) < rcf * rcf) {
+            float fx, fy, fz;
+            image32(at.w32, a, im, g, fx, fy, fz);
+            if (box_d2(t, fx, fy, fz) < rcf * rcf) {
                 const int s = atomicAdd(&ne, 1);
-                ec[s][0] = cx; ec[s][1] = cy; ec[s][2] = cz;
+                image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
             }
         }
         __syncthreads();
@@ -124,15 +149,15 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, d
         const int na = min(RCH, at.n - a0);
         for (int q = threadIdx.x; q < na * 54; q += TT) {
             const int a = a0 + q / 54, r = q % 54, im = r % 27, which = r / 27;
-            const double Z = at.gauss[3 * a + 0];
             const double sg = at.gauss[3 * a + 1 + which];
-            const double cx = wrap_pos(at.pos[3 * a + 0], g.lx) + (im % 3 - 1) * g.lx;
-            const double cy = wrap_pos(at.pos[3 * a + 1], g.ly) + ((im / 3) % 3 - 1) * g.ly;
-            const double cz = wrap_pos(at.pos[3 * a + 2], g.lz) + (im / 9 - 1) * g.lz;
+            float fx, fy, fz;
+            image32(at.w32, a, im, g, fx, fy, fz);
             const float rad = (float)(cut * sg) + kMargin;
-            if (box_dmax(t, (float)cx, (float)cy, (float)cz) < rad) {
+            if (box_dmax(t, fx, fy, fz) < rad) {
+                const double Z = at.gauss[3 * a + 0];
                 const int s = atomicAdd(&ne, 1);
-                en[s][0] = cx; en[s][1] = cy; en[s][2] = cz; en[s][3] = sg;
+                image64(at.w64, a, im, g, en[s][0], en[s][1], en[s][2]);
+                en[s][3] = sg;
                 const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
                 en[s][4] = (which == 0 ? Z : -Z) * norm;
             }
@@ -268,12 +293,12 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
         const int na = min(ACH, at.n - a0);
         for (int q = threadIdx.x; q < na * 27; q += TT) {
             const int a = a0 + q / 27, im = q % 27;
-            const double cx = wrap_pos(at.pos[3 * a + 0], g.lx) + (im % 3 - 1) * g.lx;
-            const double cy = wrap_pos(at.pos[3 * a + 1], g.ly) + ((im / 3) % 3 - 1) * g.ly;
-            const double cz = wrap_pos(at.pos[3 * a + 2], g.lz) + (im / 9 - 1) * g.lz;
-            if (box_d2(t, (float)cx, (float)cy, (float)cz) < rcf * rcf) {
+            float fx, fy, fz;
+            image32(at.w32, a, im, g, fx, fy, fz);
+            if (box_d2(t, fx, fy, fz) < rcf * rcf) {
                 const int s = atomicAdd(&ne, 1);
-                ec[s][0] = cx; ec[s][1] = cy; ec[s][2] = cz; eatom[s] = a;
+                image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
+                eatom[s] = a;
                 eacc[s][0] = 0.0; eacc[s][1] = 0.0; eacc[s][2] = 0.0;
             }
         }
@@ -332,15 +357,15 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, 
         const int na = min(RCH, at.n - a0);
         for (int q = threadIdx.x; q < na * 54; q += TT) {
             const int a = a0 + q / 54, r = q % 54, im = r % 27, which = r / 27;
-            const double Z = at.gauss[3 * a + 0];
             const double sg = at.gauss[3 * a + 1 + which];
-            const double cx = wrap_pos(at.pos[3 * a + 0], g.lx) + (im % 3 - 1) * g.lx;
-            const double cy = wrap_pos(at.pos[3 * a + 1], g.ly) + ((im / 3) % 3 - 1) * g.ly;
-            const double cz = wrap_pos(at.pos[3 * a + 2], g.lz) + (im / 9 - 1) * g.lz;
+            float fx, fy, fz;
+            image32(at.w32, a, im, g, fx, fy, fz);
             const float rad = (float)(cut * sg) + kMargin;
-            if (box_dmax(t, (float)cx, (float)cy, (float)cz) < rad) {
+            if (box_dmax(t, fx, fy, fz) < rad) {
+                const double Z = at.gauss[3 * a + 0];
                 const int s = atomicAdd(&ne, 1);
-                en[s][0] = cx; en[s][1] = cy; en[s][2] = cz; en[s][3] = sg;
+                image64(at.w64, a, im, g, en[s][0], en[s][1], en[s][2]);
+                en[s][3] = sg;
                 const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
                 en[s][4] = (which == 0 ? Z : -Z) * norm / (sg * sg);
                 eatom[s] = a;
@@ -409,6 +434,10 @@ dim3 tile_grid(const Geo& g) {
 }
 
 }  // namespace
+
+void launch_wrap_atoms(const Geo& g, const double* pos, int n, double* w64, float4* w32, cudaStream_t s) {
+    if (n > 0) k_wrap_atoms<<<(n + 127) / 128, 128, 0, s>>>(g, pos, n, w64, w32);
+}
 
 void launch_build_eps(const Geo& g, Atoms at, DielParams p, double* eps64, double* pe64, float* eps32,
                       cudaStream_t s) {

@@ -61,7 +61,18 @@ _SIGNATURES = {
     "gp_plan_band": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "gp_plan_levels": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "gp_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gp_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long),
+                                      ctypes.POINTER(ctypes.c_long), ctypes.c_int]),
+    "gp_launch_count": (ctypes.c_long, []),
 }
+
+PROF_KINDS = ["eps", "rho", "forces_eps", "forces_rho", "res64", "smooth0", "mg_fine", "mg_coarse", "krylov",
+              "fft", "setup", "misc", "update64", "energy"]
+
+
+def gp_launch_count():
+    return int(load().gp_launch_count())
 
 _lib = None
 
@@ -207,6 +218,17 @@ class Context:
         out = np.zeros(self.grid[2], dtype=np.float64)
         self._check(self._lib.gp_get_plane_max(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
+
+    def gp_profile(self, enable=True):
+        return self._check(self._lib.gp_profile(self._h, 1 if enable else 0))
+
+    def gp_get_profile(self):
+        n = len(PROF_KINDS)
+        ms = (ctypes.c_double * n)()
+        la = (ctypes.c_long * n)()
+        gr = (ctypes.c_long * n)()
+        self._check(self._lib.gp_get_profile(self._h, ms, la, gr, n))
+        return {k: {"ms": ms[i], "launches": la[i], "groups": gr[i]} for i, k in enumerate(PROF_KINDS)}
 
     def gp_get_stats(self) -> gp_stats:
         s = gp_stats()

@@ -25,7 +25,7 @@ def declared_functions():
 def test_library_exports_every_declared_symbol():
     lib = G.load()
     names = declared_functions()
-    assert len(names) >= 14
+    assert len(names) >= 17
     for n in names:
         assert hasattr(lib, n), n
     assert set(names) == set(G._SIGNATURES)
@@ -51,9 +51,9 @@ def test_band_planner_matches_oracle(seed):
 
 
 def test_level_planner():
-    assert G.gp_plan_levels(32, 32, 64) == 4          # 4 x 4 x 8 = 128 points
-    assert G.gp_plan_levels(192, 192, 384) == 6       # 6 x 6 x 12 = 432
-    assert G.gp_plan_levels(96, 96, 192, 1, 5) == 5
+    assert G.gp_plan_levels(32, 32, 64) == 5          # 2 x 2 x 4 = 16 points
+    assert G.gp_plan_levels(192, 192, 384) == 7       # 3 x 3 x 6 = 54
+    assert G.gp_plan_levels(96, 96, 192, 1, 5) == 5   # requested: 6 x 6 x 12 = 432
     assert G.gp_plan_levels(8, 8, 8) == 2
-    assert G.gp_plan_levels(192, 192, 383, 0) == 6    # Dirichlet band: (383+1)/32 - 1 = 11 planes
+    assert G.gp_plan_levels(192, 192, 383, 0) == 7    # Dirichlet band: (383+1)/64 - 1 = 5 planes
     assert G.gp_plan_levels(96, 96, 192, 1, 9) == -1
