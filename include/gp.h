@@ -73,6 +73,9 @@ typedef struct {
     int levels;           /* multigrid levels; 0 = coarsen until the coarsest grid has <= 512 points */
     int inner;            /* multigrid-preconditioned CG iterations per outer FP64 correction */
     int max_outer;        /* outer FP64 corrections before GP_ERR_NOT_CONVERGED */
+    int accel;            /* split: 1 = accelerate the self-consistent coupling with FP64 flexible
+                             GMRES (same fixed point); 0 = plain coupling iteration */
+    int restart;          /* split with accel: Krylov vectors kept before a restart (10, <= 15) */
 } gp_params;
 
 #define GP_HISTORY 64

@@ -134,7 +134,7 @@ struct gp_ctx {
     double* ratoms = nullptr;      // gp_build_rho's positions, wrapped
     float4* ratoms32 = nullptr;
     int ratoms_cap = 0;
-    double* partial = nullptr;     // kReduceBlocks * 4
+    double* partial = nullptr;     // kReduceBlocks * (kMaxKrylov + 1)
     double* scal = nullptr;        // device scalars
     int* dstatus = nullptr;
     double* forces_S = nullptr;
@@ -153,6 +153,13 @@ struct gp_ctx {
     int full_levels = 0;
     int band_first = -1, band_nd = 0, band_nz = 0, band_first_interior = 0;
     bool split_ok = false;
+    // FGMRES storage (split with accel): V[0..m] FP64, Z[0..m-1] and vT in the working precision
+    std::vector<double*> kV;
+    std::vector<void*> kZ;
+    void* kvT = nullptr;
+    double* kY = nullptr;
+    int k_m = 0;
+    int k_bytes = 0;
     std::vector<void*> misc;
 
     // optional per-kernel-group timing (gp_profile)
@@ -479,6 +486,146 @@ void setup_solver(gp_ctx* c) {
 }
 
 template <typename T>
+void ensure_krylov(gp_ctx* c, int m) {
+    if (c->k_m >= m && c->k_bytes == (int)sizeof(T)) return;
+    for (double* v : c->kV) cudaFree(v);
+    for (void* z : c->kZ) cudaFree(z);
+    if (c->kvT) cudaFree(c->kvT);
+    if (c->kY) cudaFree(c->kY);
+    c->kV.clear(); c->kZ.clear(); c->kvT = nullptr; c->kY = nullptr; c->k_m = 0;
+    for (int j = 0; j <= m; ++j) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, sizeof(double) * c->n) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+        c->kV.push_back((double*)p);
+    }
+    for (int j = 0; j < m; ++j) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, sizeof(T) * c->n) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+        c->kZ.push_back(p);
+    }
+    if (cudaMalloc(&c->kvT, sizeof(T) * c->n) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+    if (cudaMalloc(&c->kY, sizeof(double) * kMaxKrylov) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+    c->k_m = m;
+    c->k_bytes = (int)sizeof(T);
+}
+
+// z = M v: the dry/wet split applied to a residual-like vector v (in T):
+// z = L^-1 v on the whole box (FFT), plus the band correction solving
+// A e = v - A L^-1 v on the wet band with e = 0 on the Dirichlet planes.
+template <typename T>
+void split_precondition(gp_ctx* c, const T* v, T* z) {
+    Hier<T>& B = band_hier<T>(c);
+    T* ev = reinterpret_cast<T*>(c->evac);
+    {
+        ProfScope ps(c, GP_PROF_FFT, 5);
+        fft_poisson<T>(c->fft, v, ev, c->fft_work, c->s);
+    }
+    {
+        ProfScope ps(c, GP_PROF_MG_FINE, 1);
+        launch_band_rhs<T>(c->g, eps_T<T>(c), v, ev, c->band_first_interior, c->band_nz, B.r, c->s);
+    }
+    GP_CHECK_LAUNCH();
+    pcg<T>(c, B, c->prm.inner);
+    if (z) {
+        ProfScope ps(c, GP_PROF_MG_FINE, 1);
+        launch_combine<T>(c->g, ev, B.x, c->band_first_interior, c->band_nz, z, c->s);
+    }
+    GP_CHECK_LAUNCH();
+}
+
+// FP64 flexible GMRES(m) on A phi = b, right-preconditioned by the split.
+template <typename T>
+gp_status fgmres_split(gp_ctx* c, const double* rho, double* phi, double tol, double nb) {
+    const int m = c->prm.restart;
+    ensure_krylov<T>(c, m);
+    gp_stats& st = c->stats;
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m), hv(m + 2);
+    auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+    T* vT = reinterpret_cast<T*>(c->kvT);
+    double best = INFINITY;
+    while (true) {
+        {
+            ProfScope ps(c, GP_PROF_RES64, 1);
+            launch_residual64<double>(c->g, phi, rho, c->eps64, c->kV[0], c->partial, c->s);
+        }
+        GP_CHECK_LAUNCH();
+        double s2[2];
+        sum_host(c, 2, s2);
+        const double beta = std::sqrt(s2[0]);
+        const double rn = beta / nb;
+        st.outer_iterations++;
+        if (st.history_len < GP_HISTORY) st.history[st.history_len++] = rn;
+        st.residual = rn;
+        if (!std::isfinite(rn) || rn > 1e3 * best) return GP_ERR_DIVERGED;
+        best = std::min(best, rn);
+        if (rn <= tol) return GP_OK;
+        if (st.outer_iterations >= c->prm.max_outer) return GP_ERR_NOT_CONVERGED;
+        {
+            ProfScope ps(c, GP_PROF_KRYLOV, 1);
+            launch_scale_by_norm(c->n, c->kV[0], c->scal + 8, c->s);
+        }
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int used = 0;
+        for (int j = 0; j < m; ++j) {
+            T* zj = reinterpret_cast<T*>(c->kZ[j]);
+            {
+                ProfScope ps(c, GP_PROF_KRYLOV, 1);
+                launch_cast_eps<T>(c->n, c->kV[j], vT, c->s);
+            }
+            split_precondition<T>(c, vT, zj);
+            VecList V;
+            V.n = j + 1;
+            for (int i = 0; i <= j; ++i) V.v[i] = c->kV[i];
+            {
+                ProfScope ps(c, GP_PROF_KRYLOV, 6);
+                launch_applyA64<T>(c->g, c->eps64, zj, c->kV[j + 1], c->s);
+                launch_multidot(c->n, c->kV[j + 1], V, c->partial, c->s);
+                launch_finalize(c->partial, kReduceBlocks, j + 1, c->scal + 16, c->s);
+                launch_multiaxpy_norm(c->n, c->kV[j + 1], V, c->scal + 16, c->partial, c->s);
+                launch_finalize(c->partial, kReduceBlocks, 1, c->scal + 15, c->s);
+                launch_scale_by_norm(c->n, c->kV[j + 1], c->scal + 15, c->s);
+            }
+            GP_CHECK_LAUNCH();
+            GP_CUDA(cudaMemcpyAsync(hv.data(), c->scal + 15, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, c->s));
+            GP_CUDA(cudaStreamSynchronize(c->s));
+            for (int i = 0; i <= j; ++i) Hij(i, j) = hv[1 + i];
+            Hij(j + 1, j) = std::sqrt(hv[0]);
+            for (int i = 0; i < j; ++i) {
+                const double a = Hij(i, j), b = Hij(i + 1, j);
+                Hij(i, j) = cs[i] * a + sn[i] * b;
+                Hij(i + 1, j) = -sn[i] * a + cs[i] * b;
+            }
+            const double a = Hij(j, j), b = Hij(j + 1, j);
+            const double r = std::hypot(a, b);
+            cs[j] = r > 0 ? a / r : 1.0;
+            sn[j] = r > 0 ? b / r : 0.0;
+            Hij(j, j) = r;
+            Hij(j + 1, j) = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            used = j + 1;
+            st.inner_iterations++;
+            if (std::fabs(g[j + 1]) <= 0.5 * tol * nb || hv[0] <= 0.0) break;
+        }
+        for (int i = used - 1; i >= 0; --i) {
+            double acc = g[i];
+            for (int k = i + 1; k < used; ++k) acc -= Hij(i, k) * y[k];
+            y[i] = acc / Hij(i, i);
+        }
+        GP_CUDA(cudaMemcpyAsync(c->kY, y.data(), sizeof(double) * used, cudaMemcpyHostToDevice, c->s));
+        TVecList<T> Z;
+        Z.n = used;
+        for (int j = 0; j < used; ++j) Z.v[j] = reinterpret_cast<const T*>(c->kZ[j]);
+        {
+            ProfScope ps(c, GP_PROF_UPDATE64, 1);
+            launch_update_krylov<T>(c->n, phi, Z, c->kY, c->s);
+        }
+        GP_CHECK_LAUNCH();
+    }
+}
+
+template <typename T>
 gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
     Hier<T>& F = full_hier<T>(c);
     Hier<T>& B = band_hier<T>(c);
@@ -511,6 +658,9 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
     T* ev = reinterpret_cast<T*>(c->evac);
     double best = INFINITY;
     gp_status result = GP_ERR_NOT_CONVERGED;
+    if (split && c->prm.accel) {
+        result = fgmres_split<T>(c, rho, phi, tol, nb);
+    } else
     for (int it = 0; it < c->prm.max_outer; ++it) {
         if (it > 0) {
             ProfScope ps(c, GP_PROF_UPDATE64, 1);
@@ -593,6 +743,8 @@ void gp_default_params(gp_params* p) {
     p->levels = 0;
     p->inner = 4;
     p->max_outer = 60;
+    p->accel = 1;
+    p->restart = 10;
 }
 
 gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out) {
@@ -613,7 +765,7 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
         c->pe64 = (double*)dalloc(c, sizeof(double) * c->n);
         c->eps32 = (float*)dalloc(c, sizeof(float) * c->n);
         c->plane_max = (double*)dalloc(c, sizeof(double) * grid.nz);
-        c->partial = (double*)dalloc(c, sizeof(double) * kReduceBlocks * 4);
+        c->partial = (double*)dalloc(c, sizeof(double) * kReduceBlocks * (kMaxKrylov + 1));
         c->scal = (double*)dalloc(c, sizeof(double) * 32);
         c->dstatus = (int*)dalloc(c, sizeof(int) * 4);
         c->gmat = (double*)dalloc(c, sizeof(double) * 2 * kMaxCoarse * kMaxCoarse);
@@ -636,6 +788,8 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         if (p.precision != 0 && p.precision != 1) throw Err{GP_ERR_INVALID_ARG, "precision must be 0 or 1"};
         if (p.nu1 < 0 || p.nu2 < 0 || p.nu1 + p.nu2 == 0 || p.inner < 1 || p.max_outer < 1)
             throw Err{GP_ERR_INVALID_ARG, "need nu1+nu2 >= 1, inner >= 1, max_outer >= 1"};
+        if (p.accel && (p.restart < 1 || p.restart > kMaxKrylov - 1))
+            throw Err{GP_ERR_INVALID_ARG, "restart must be in 1..15"};
         std::string why;
         const int L = plan_levels(c->g.nx, c->g.ny, c->g.nz, 1, p.levels, why);
         if (L < 2) throw Err{GP_ERR_INVALID_ARG, why.empty() ? "grid too small for multigrid" : why};
@@ -941,6 +1095,10 @@ void gp_destroy(gp_ctx* c) {
     free_hier(c->fullD);
     free_hier(c->bandD);
     if (c->fft) fft_destroy(c->fft);
+    for (double* v : c->kV) cudaFree(v);
+    for (void* z : c->kZ) cudaFree(z);
+    if (c->kvT) cudaFree(c->kvT);
+    if (c->kY) cudaFree(c->kY);
     for (auto& p : c->pending) { c->event_pool.push_back(p.a); c->event_pool.push_back(p.b); }
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     for (void* p : c->misc) cudaFree(p);

@@ -535,9 +535,122 @@ __global__ void k_band_rhs(Geo g, const T* eps, const T* r, const T* ev, int fir
     }
 }
 
+// ------------------------------------------------------------ FGMRES (FP64 outer Krylov)
+// w = A z with the FP64 operator (cell eps, periodic) applied to a T vector
+template <typename T>
+__global__ void k_applyA64(Geo g, const double* eps, const T* z, double* w) {
+    const long n = (long)g.nx * g.ny * g.nz;
+    const double hx = 0.5 / (g.hx * g.hx), hy = 0.5 / (g.hy * g.hy), hz = 0.5 / (g.hz * g.hz);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        split3(t, g.nx, g.ny, i, j, k);
+        const Nb nb = neighbours(g.nx, g.ny, g.nz, 1, i, j, k);
+        const double e0 = eps[nb.c], p0 = (double)z[nb.c];
+        const double ax = (e0 + eps[nb.xp]) * ((double)z[nb.xp] - p0) - (e0 + eps[nb.xm]) * (p0 - (double)z[nb.xm]);
+        const double ay = (e0 + eps[nb.yp]) * ((double)z[nb.yp] - p0) - (e0 + eps[nb.ym]) * (p0 - (double)z[nb.ym]);
+        const double az = (e0 + eps[nb.zp]) * ((double)z[nb.zp] - p0) - (e0 + eps[nb.zm]) * (p0 - (double)z[nb.zm]);
+        w[t] = hx * ax + hy * ay + hz * az;
+    }
+}
+
+// partial[b * nv + i] = block b's share of w . v_i
+__global__ void __launch_bounds__(kReduceThreads) k_multidot(long n, const double* w, VecList V, double* partial) {
+    __shared__ double red[32];
+    double loc[kMaxKrylov + 1];
+    for (int i = 0; i < V.n; ++i) loc[i] = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const double wv = w[t];
+        for (int i = 0; i < V.n; ++i) loc[i] += wv * V.v[i][t];
+    }
+    for (int i = 0; i < V.n; ++i) {
+        const double s = block_sum(loc[i], red);
+        if (threadIdx.x == 0) partial[(long)blockIdx.x * V.n + i] = s;
+    }
+}
+
+// w -= sum_i h[i] v_i; partial[b] = block share of |w|^2
+__global__ void __launch_bounds__(kReduceThreads) k_multiaxpy_norm(long n, double* w, VecList V, const double* h,
+                                                                   double* partial) {
+    __shared__ double red[32];
+    __shared__ double hs[kMaxKrylov + 1];
+    if (threadIdx.x < V.n) hs[threadIdx.x] = h[threadIdx.x];
+    __syncthreads();
+    double loc = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        double x = w[t];
+        for (int i = 0; i < V.n; ++i) x -= hs[i] * V.v[i][t];
+        w[t] = x;
+        loc += x * x;
+    }
+    const double s = block_sum(loc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// v = w / sqrt(*sq)
+__global__ void k_scale_by_norm(long n, double* v, const double* sq) {
+    const double f = 1.0 / sqrt(sq[0]);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) v[t] *= f;
+}
+
+// z = e_vac, plus the band correction on the band planes
+template <typename T>
+__global__ void k_combine(Geo g, const T* ev, const T* eb, int first, int band_nz, T* z) {
+    const long n = (long)g.nx * g.ny * g.nz;
+    const long pl = plane_of(g.nx, g.ny);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        T v = ev[t];
+        const int k = (int)(t / pl);
+        int kb = k - first;
+        if (kb < 0) kb += g.nz;
+        if (kb < band_nz) v += eb[t - k * pl + kb * pl];
+        z[t] = v;
+    }
+}
+
+// x += sum_j y[j] z_j (z in T, x and y FP64)
+template <typename T>
+__global__ void k_update_krylov(long n, double* x, TVecList<T> Z, const double* y) {
+    __shared__ double ys[kMaxKrylov];
+    if (threadIdx.x < Z.n) ys[threadIdx.x] = y[threadIdx.x];
+    __syncthreads();
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        double acc = x[t];
+        for (int j = 0; j < Z.n; ++j) acc += ys[j] * (double)Z.v[j][t];
+        x[t] = acc;
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ launchers
+template <typename T> void launch_applyA64(const Geo& g, const double* eps, const T* z, double* w, cudaStream_t s) {
+    const long n = (long)g.nx * g.ny * g.nz;
+    k_applyA64<T><<<grid_for(n, 256), 256, 0, s>>>(g, eps, z, w);
+}
+void launch_multidot(long n, const double* w, const VecList& V, double* partial, cudaStream_t s) {
+    k_multidot<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, w, V, partial);
+}
+void launch_multiaxpy_norm(long n, double* w, const VecList& V, const double* h, double* partial, cudaStream_t s) {
+    k_multiaxpy_norm<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, w, V, h, partial);
+}
+void launch_scale_by_norm(long n, double* v, const double* sq, cudaStream_t s) {
+    k_scale_by_norm<<<grid_for(n, 256), 256, 0, s>>>(n, v, sq);
+}
+template <typename T> void launch_combine(const Geo& g, const T* ev, const T* eb, int first, int band_nz, T* z,
+                                          cudaStream_t s) {
+    const long n = (long)g.nx * g.ny * g.nz;
+    k_combine<T><<<grid_for(n, 256), 256, 0, s>>>(g, ev, eb, first, band_nz, z);
+}
+template <typename T> void launch_update_krylov(long n, double* x, const TVecList<T>& Z, const double* y,
+                                                cudaStream_t s) {
+    k_update_krylov<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, Z, y);
+}
+template void launch_applyA64<float>(const Geo&, const double*, const float*, double*, cudaStream_t);
+template void launch_applyA64<double>(const Geo&, const double*, const double*, double*, cudaStream_t);
+template void launch_combine<float>(const Geo&, const float*, const float*, int, int, float*, cudaStream_t);
+template void launch_combine<double>(const Geo&, const double*, const double*, int, int, double*, cudaStream_t);
+template void launch_update_krylov<float>(long, double*, const TVecList<float>&, const double*, cudaStream_t);
+template void launch_update_krylov<double>(long, double*, const TVecList<double>&, const double*, cudaStream_t);
 void launch_finalize(const double* partial, int nparts, int ncomp, double* out, cudaStream_t s) {
     k_finalize<<<1, 1024, 0, s>>>(partial, nparts, ncomp, out);
 }

@@ -128,9 +128,9 @@ def _solve_case(small_cases, k, **params):
 
 
 @pytest.mark.parametrize("k", range(len(SMALL)))
-@pytest.mark.parametrize("split", [0, 1])
-def test_fp64_solve_matches_oracle(small_cases, k, split):
-    s, phi, ref, rho, grid, cell, eps = _solve_case(small_cases, k, precision=0, split=split, inner=6)
+@pytest.mark.parametrize("split,accel", [(0, 1), (1, 1), (1, 0)])
+def test_fp64_solve_matches_oracle(small_cases, k, split, accel):
+    s, phi, ref, rho, grid, cell, eps = _solve_case(small_cases, k, precision=0, split=split, inner=6, accel=accel)
     assert _rel(phi, ref) < 1e-10
     E = O.energy(rho, phi, grid, cell)
     E0 = O.energy(rho, ref, grid, cell)
@@ -140,9 +140,9 @@ def test_fp64_solve_matches_oracle(small_cases, k, split):
 
 
 @pytest.mark.parametrize("k", range(len(SMALL)))
-@pytest.mark.parametrize("split", [0, 1])
-def test_mixed_solve_matches_oracle(small_cases, k, split):
-    s, phi, ref, rho, grid, cell, eps = _solve_case(small_cases, k, precision=1, split=split)
+@pytest.mark.parametrize("split,accel", [(0, 1), (1, 1), (1, 0)])
+def test_mixed_solve_matches_oracle(small_cases, k, split, accel):
+    s, phi, ref, rho, grid, cell, eps = _solve_case(small_cases, k, precision=1, split=split, accel=accel)
     assert _rel(phi, ref) < 1e-8
     E = O.energy(rho, phi, grid, cell)
     E0 = O.energy(rho, ref, grid, cell)
