@@ -176,6 +176,39 @@ int gp_plan_band(const int* dry, int nz, int levels, int n_dirichlet, int* first
  * reaching <= 512 points. Returns -1 if impossible. Needs no GPU. */
 int gp_plan_levels(int nx, int ny, int nz, int zper, int requested);
 
+/* Largest nz accepted by gp_residual_noalloc: its scratch holds two partial
+ * sums per z-plane, 2 * 4096 doubles (64 KiB) per GPU. */
+#define GP_NOALLOC_MAX_PLANES 4096
+
+/* gp_residual_noalloc: the FP64 residual of gp_residual, for callers that
+ * cannot allocate device memory (no cudaMalloc: for example code running
+ * where the allocator is owned by someone else, inside a memory pool that
+ * must not grow, or in a plug-in that may not create a solver context). The
+ * paper has no counterpart; this is a deployment entry point.
+ *
+ *   r = -4 pi rho - A phi  (Eq. 3 operator, FP64, eps given by the caller)
+ *   rel_dev[0] = ||r||_2 / ||4 pi rho||_2
+ *
+ * Arguments: grid and cell as for gp_create; eps_dev, rho_dev, phi_dev and
+ * r_dev are grid-sized float64 device arrays (x fastest); rel_dev is one
+ * device double; cuda_stream is a cudaStream_t (NULL = legacy stream). The
+ * call only enqueues work on that stream and returns; nothing is allocated or
+ * freed, and no context is needed.
+ *
+ * Scratch: a file-scope device array of 2 * GP_NOALLOC_MAX_PLANES doubles,
+ * present on every GPU that loads the library until the process exits.
+ * Every call overwrites the slots it reads, but all calls share the one
+ * array: calls that overlap on the GPU (different streams, or threads) race
+ * and give wrong sums; serialise them. The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it, so make
+ * that first call outside any CUDA stream capture.
+ *
+ * Errors: GP_ERR_INVALID_ARG for a null pointer, an extent below 2, a
+ * non-positive cell side, or nz > GP_NOALLOC_MAX_PLANES; GP_ERR_CUDA if the
+ * address lookup or a launch fails. */
+gp_status gp_residual_noalloc(gp_grid grid, gp_cell cell, const double* eps_dev, const double* rho_dev,
+                              const double* phi_dev, double* r_dev, double* rel_dev, void* cuda_stream);
+
 /* Kernel groups timed by gp_profile (indices into the arrays of gp_get_profile). */
 enum {
     GP_PROF_EPS = 0,         /* dielectric builder */

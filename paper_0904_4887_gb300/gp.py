@@ -65,6 +65,7 @@ _SIGNATURES = {
     "gp_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long),
                                       ctypes.POINTER(ctypes.c_long), ctypes.c_int]),
     "gp_launch_count": (ctypes.c_long, []),
+    "gp_residual_noalloc": (ctypes.c_int, [gp_grid, gp_cell, _P, _P, _P, _P, _P, _P]),
 }
 
 PROF_KINDS = ["eps", "rho", "forces_eps", "forces_rho", "res64", "smooth0", "mg_fine", "mg_coarse", "krylov",
@@ -110,6 +111,14 @@ def gp_plan_band(dry, levels, n_dirichlet=1):
 
 def gp_plan_levels(nx, ny, nz, zper=1, requested=0):
     return load().gp_plan_levels(int(nx), int(ny), int(nz), int(zper), int(requested))
+
+
+def gp_residual_noalloc(grid, cell, eps, rho, phi, r, rel, stream=None):
+    """Allocation-free FP64 residual (no context); rel is a 1-element device tensor."""
+    import torch
+    st = torch.cuda.current_stream() if stream is None else stream
+    return load().gp_residual_noalloc(gp_grid(*grid), gp_cell(*cell), _ptr(eps), _ptr(rho), _ptr(phi), _ptr(r),
+                                      _ptr(rel), ctypes.c_void_p(st.cuda_stream))
 
 
 class GPError(RuntimeError):
