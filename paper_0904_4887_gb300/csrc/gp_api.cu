@@ -43,10 +43,18 @@ struct Hier {
     T* cz[16] = {};
     T* eps0 = nullptr;                          // owned level-0 cell eps (band only)
     T* x = nullptr; T* r = nullptr; T* p = nullptr; T* q = nullptr; T* z = nullptr;   // PCG, level 0
+    T* tmp = nullptr;                           // level-0 ping-pong buffer of the fused sweep
     T* minv = nullptr;
     int nc = 0;
     std::vector<void*> allocs;
     bool ready = false;
+    // captured CUDA graph of pcg(iters) on this hierarchy
+    cudaGraphExec_t pcg_exec = nullptr;
+    long pcg_key = -1;
+    long pcg_launches = 0;
+    int pcg_vcycles = 0, pcg_inner = 0;
+    std::vector<int> pcg_kinds, pcg_nlaunch;
+    std::vector<cudaEvent_t> pcg_ev;          // event pairs recorded inside the graph (profiling)
 };
 
 template <typename T>
@@ -62,6 +70,8 @@ T* alloc_level(Hier<T>& H, int nx, int ny, int nz) {
 
 template <typename T>
 void free_hier(Hier<T>& H) {
+    if (H.pcg_exec) cudaGraphExecDestroy(H.pcg_exec);
+    for (cudaEvent_t e : H.pcg_ev) cudaEventDestroy(e);
     for (void* p : H.allocs) cudaFree(p);
     H = Hier<T>();
 }
@@ -162,11 +172,17 @@ struct gp_ctx {
     int k_bytes = 0;
     std::vector<void*> misc;
 
+    // CUDA graphs: captured on a library stream that is ordered after / before the user's stream
+    bool use_graphs = true;
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+
     // optional per-kernel-group timing (gp_profile)
     bool prof_on = false;
     struct Pending { int kind; int launches; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
+    long prm_on_key() const { return prof_on ? 1 : 0; }
     double prof_ms[GP_PROF_KINDS] = {};
     long prof_launches[GP_PROF_KINDS] = {};
     long prof_groups[GP_PROF_KINDS] = {};
@@ -272,6 +288,7 @@ void alloc_hier(gp_ctx* c, Hier<T>& H, int nx, int ny, int nz, int zper, int lev
         H.p = alloc_level(H, nx, ny, nz);
         H.q = alloc_level(H, nx, ny, nz);
         H.z = alloc_level(H, nx, ny, nz);
+        H.tmp = alloc_level(H, nx, ny, nz);
         if (own_eps) H.eps0 = alloc_level(H, nx, ny, nz);
         const LV<T>& C = H.lv[levels - 1];
         H.nc = C.nx * C.ny * C.nz;
@@ -315,6 +332,27 @@ void coarse_coeffs(gp_ctx* c, Hier<T>& H) {
 }
 
 // ------------------------------------------------------------ V-cycle and PCG
+// nu fused red-black sweeps of the finest level, colour `first` first; the
+// result ends in u (ping-pong through H.tmp)
+template <typename T>
+void smooth_fine(gp_ctx* c, Hier<T>& H, T* u, const T* f, int nu, int first) {
+    if (nu <= 0) return;
+    const LV<T>& V = H.lv[0];
+    T* a = u;
+    T* b = H.tmp;
+    {
+        ProfScope ps(c, GP_PROF_SMOOTH0, nu);
+        for (int it = 0; it < nu; ++it) {
+            launch_rb_sweep<T>(V, a, f, b, first, c->s);
+            T* t = a; a = b; b = t;
+        }
+    }
+    if (a != u) {
+        ProfScope ps(c, GP_PROF_MG_FINE, 1);
+        launch_copy_level<T>(V, u, a, c->s);
+    }
+}
+
 template <typename T>
 void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
     const int L = H.L;
@@ -323,8 +361,10 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
         T* u = l == 0 ? u0 : H.u[l];
         const T* f = l == 0 ? f0 : H.f[l];
         GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
-        {
-            ProfScope ps(c, l == 0 ? GP_PROF_SMOOTH0 : GP_PROF_MG_COARSE, 2 * c->prm.nu1);
+        if (l == 0) {
+            smooth_fine(c, H, u, f, c->prm.nu1, 0);
+        } else {
+            ProfScope ps(c, GP_PROF_MG_COARSE, 2 * c->prm.nu1);
             for (int it = 0; it < c->prm.nu1; ++it) {
                 launch_rbgs<T>(V, u, f, 0, c->s);
                 launch_rbgs<T>(V, u, f, 1, c->s);
@@ -346,7 +386,11 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
             ProfScope ps(c, l == 0 ? GP_PROF_MG_FINE : GP_PROF_MG_COARSE, 1);
             launch_prolong_add<T>(V, u, H.lv[l + 1], H.u[l + 1], c->s);
         }
-        ProfScope ps(c, l == 0 ? GP_PROF_SMOOTH0 : GP_PROF_MG_COARSE, 2 * c->prm.nu2);
+        if (l == 0) {
+            smooth_fine(c, H, u, f, c->prm.nu2, 1);
+            continue;
+        }
+        ProfScope ps(c, GP_PROF_MG_COARSE, 2 * c->prm.nu2);
         for (int it = 0; it < c->prm.nu2; ++it) {
             launch_rbgs<T>(V, u, f, 1, c->s);
             launch_rbgs<T>(V, u, f, 0, c->s);
@@ -356,9 +400,86 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
     c->stats.vcycles++;
 }
 
-// x ~ A^-1 r by `iters` multigrid-preconditioned CG steps from x = 0; r is overwritten
+template <typename T>
+void pcg_body(gp_ctx* c, Hier<T>& H, int iters);
+
+// x ~ A^-1 r by `iters` multigrid-preconditioned CG steps from x = 0; r is
+// overwritten. The whole sequence (V-cycles, dot products, updates: no host
+// round trip) is captured once per hierarchy into a CUDA graph and replayed.
 template <typename T>
 void pcg(gp_ctx* c, Hier<T>& H, int iters) {
+    if (!c->use_graphs) {
+        pcg_body(c, H, iters);
+        return;
+    }
+    const long key = ((long)iters << 20) | ((long)c->prm.nu1 << 12) | ((long)c->prm.nu2 << 4) | (c->prm_on_key());
+    if (!H.pcg_exec || H.pcg_key != key) {
+        if (H.pcg_exec) { cudaGraphExecDestroy(H.pcg_exec); H.pcg_exec = nullptr; }
+        for (cudaEvent_t e : H.pcg_ev) cudaEventDestroy(e);
+        H.pcg_ev.clear(); H.pcg_kinds.clear(); H.pcg_nlaunch.clear();
+        cudaStream_t user = c->s;
+        c->s = c->gs;
+        const long l0 = g_launches.load();
+        const int v0 = c->stats.vcycles, i0 = c->stats.inner_iterations;
+        std::vector<gp_ctx::Pending> saved;
+        saved.swap(c->pending);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e1 = cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal);
+        if (e1 == cudaSuccess) {
+            try {
+                pcg_body(c, H, iters);
+            } catch (...) {
+                cudaStreamEndCapture(c->gs, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                c->s = user;
+                throw;
+            }
+            e1 = cudaStreamEndCapture(c->gs, &graph);
+        }
+        c->s = user;
+        if (e1 != cudaSuccess) throw Err{GP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1)};
+        cudaError_t e2 = cudaGraphInstantiate(&H.pcg_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e2 != cudaSuccess) throw Err{GP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2)};
+        H.pcg_launches = g_launches.load() - l0;
+        H.pcg_vcycles = c->stats.vcycles - v0;
+        H.pcg_inner = c->stats.inner_iterations - i0;
+        c->stats.vcycles = v0;
+        c->stats.inner_iterations = i0;
+        g_launches.fetch_sub(H.pcg_launches);
+        for (auto& p : c->pending) {
+            H.pcg_kinds.push_back(p.kind);
+            H.pcg_nlaunch.push_back(p.launches);
+            H.pcg_ev.push_back(p.a);
+            H.pcg_ev.push_back(p.b);
+        }
+        c->pending.swap(saved);
+        H.pcg_key = key;
+    }
+    GP_CUDA(cudaEventRecord(c->ev_in, c->s));
+    GP_CUDA(cudaStreamWaitEvent(c->gs, c->ev_in, 0));
+    GP_CUDA(cudaGraphLaunch(H.pcg_exec, c->gs));
+    GP_CUDA(cudaEventRecord(c->ev_out, c->gs));
+    GP_CUDA(cudaStreamWaitEvent(c->s, c->ev_out, 0));
+    count_launch(H.pcg_launches);
+    c->stats.vcycles += H.pcg_vcycles;
+    c->stats.inner_iterations += H.pcg_inner;
+    if (c->prof_on) {
+        // the graph's event pairs hold this replay's times until the next replay;
+        // every caller synchronises (and collects) before replaying again
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        for (size_t k = 0; k < H.pcg_kinds.size(); ++k) {
+            float ms = 0.f;
+            GP_CUDA(cudaEventElapsedTime(&ms, H.pcg_ev[2 * k], H.pcg_ev[2 * k + 1]));
+            c->prof_ms[H.pcg_kinds[k]] += ms;
+            c->prof_launches[H.pcg_kinds[k]] += H.pcg_nlaunch[k];
+            c->prof_groups[H.pcg_kinds[k]] += 1;
+        }
+    }
+}
+
+template <typename T>
+void pcg_body(gp_ctx* c, Hier<T>& H, int iters) {
     const LV<T>& V = H.lv[0];
     GP_CUDA(cudaMemsetAsync(lbase(V, H.x), 0, level_bytes(V), c->s));
     vcycle(c, H, H.z, H.r);
@@ -769,6 +890,12 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
         c->scal = (double*)dalloc(c, sizeof(double) * 32);
         c->dstatus = (int*)dalloc(c, sizeof(int) * 4);
         c->gmat = (double*)dalloc(c, sizeof(double) * 2 * kMaxCoarse * kMaxCoarse);
+        rb_sweep_init();
+        GP_CUDA(cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking));
+        GP_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+        GP_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+        const char* ev = std::getenv("GP_NO_GRAPHS");
+        c->use_graphs = !(ev && ev[0] == '1');
     } catch (const Err& e) {
         gp_destroy(c);
         return e.st;
@@ -1090,6 +1217,7 @@ int gp_plan_levels(int nx, int ny, int nz, int zper, int requested) {
 void gp_destroy(gp_ctx* c) {
     if (!c) return;
     if (c->s) cudaStreamSynchronize(c->s);
+    if (c->gs) cudaStreamSynchronize(c->gs);
     free_hier(c->fullF);
     free_hier(c->bandF);
     free_hier(c->fullD);
@@ -1101,6 +1229,9 @@ void gp_destroy(gp_ctx* c) {
     if (c->kY) cudaFree(c->kY);
     for (auto& p : c->pending) { c->event_pool.push_back(p.a); c->event_pool.push_back(p.b); }
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->gs) cudaStreamDestroy(c->gs);
     for (void* p : c->misc) cudaFree(p);
     if (c->atoms) cudaFree(c->atoms);
     if (c->atoms32) cudaFree(c->atoms32);

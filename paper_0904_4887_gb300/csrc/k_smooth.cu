@@ -1,0 +1,150 @@
+// One full red-black Gauss-Seidel sweep of the finest multigrid level in a
+// single pass over memory.
+//
+// A sweep updates the points of the first colour from the old values of the
+// other colour, then the points of the second colour from the new values of
+// the first. Two launches would stream u and eps twice; here each CTA owns an
+// x-y tile and a chunk of z-planes and marches through them with a ring of
+// four planes in shared memory:
+//
+//   load plane q+1 (u_old, eps, f with a 2-point x-y halo)
+//   first colour, new values, at plane q on the tile plus a 1-point halo
+//   second colour at plane q-1 on the tile, from those new values
+//   write plane q-1 of u_new (both colours)
+//
+// The halo values of the first colour are recomputed by every CTA that needs
+// them from u_old, which nobody writes during the sweep (u_new is a separate
+// buffer), so the result is identical to the two-launch sweep. Algorithmic
+// traffic: read u_old, eps, f and write u_new, 16 bytes per point in FP32.
+#include "gp_common.cuh"
+
+namespace gp {
+namespace {
+
+constexpr int SX = 64, SY = 8, SZ = 32;           // output tile per CTA
+constexpr int HX = SX + 4, HY = SY + 4;           // with a 2-point halo
+constexpr int HP = HX * HY;
+constexpr int NT = 256;
+
+template <typename T>
+struct Ring {
+    T u[4][HP];
+    T e[4][HP];
+    T f[4][HP];
+    T r[4][HP];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ u_old, const T* __restrict__ f,
+                                                 T* __restrict__ u_new, int first) {
+    extern __shared__ unsigned char smem_raw[];
+    Ring<T>& R = *reinterpret_cast<Ring<T>*>(smem_raw);
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const long pl = (long)nx * ny;
+    const int i0 = blockIdx.x * SX, j0 = blockIdx.y * SY;
+    const int z0 = blockIdx.z * SZ;
+    const int z1 = min(z0 + SZ, nz);
+    const T cx = (T)0.5 * L.ihx2, cy = (T)0.5 * L.ihy2, cz = (T)0.5 * L.ihz2;
+
+    // smem index of (dx, dy) with dx in [-2, SX+2), dy in [-2, SY+2)
+    auto sidx = [](int dx, int dy) { return (dy + 2) * HX + (dx + 2); };
+
+    // global plane index of march plane q, or -99 when it does not exist (Dirichlet beyond the walls)
+    auto gplane = [&](int q) -> int {
+        if (L.zper) return ((q % nz) + nz) % nz;
+        return (q < -1 || q > nz) ? -99 : q;
+    };
+
+    auto load_plane = [&](int q) {
+        const int slot = (q + 8) & 3;
+        const int kg = gplane(q);
+        for (int t = threadIdx.x; t < HP; t += NT) {
+            const int dy = t / HX - 2, dx = t % HX - 2;
+            const int i = ((i0 + dx) % nx + nx) % nx, j = ((j0 + dy) % ny + ny) % ny;
+            T uv = 0, ev = 1, fv = 0;
+            if (kg != -99) {
+                const long g = (long)kg * pl + (long)j * nx + i;
+                uv = u_old[g];
+                ev = L.eps[g];
+                if (kg >= 0 && kg < nz) fv = f[g];
+            }
+            R.u[slot][t] = uv;
+            R.e[slot][t] = ev;
+            R.f[slot][t] = fv;
+        }
+    };
+
+    // Gauss-Seidel value at (dx, dy) of plane q from the values in `src` for
+    // the in-plane neighbours and srcm / srcp for the planes below / above
+    auto gs_update = [&](int q, int dx, int dy, const T* srcm, const T* src, const T* srcp) -> T {
+        const int s0 = (q + 8) & 3, sm = (q + 7) & 3, sp = (q + 9) & 3;
+        const int c = sidx(dx, dy);
+        const T e0 = R.e[s0][c];
+        const T axm = (e0 + R.e[s0][c - 1]) * cx, axp = (e0 + R.e[s0][c + 1]) * cx;
+        const T aym = (e0 + R.e[s0][c - HX]) * cy, ayp = (e0 + R.e[s0][c + HX]) * cy;
+        const T azm = (e0 + R.e[sm][c]) * cz, azp = (e0 + R.e[sp][c]) * cz;
+        const T s = axm * src[c - 1] + axp * src[c + 1] + aym * src[c - HX] + ayp * src[c + HX] + azm * srcm[c] +
+                    azp * srcp[c];
+        return (s - R.f[s0][c]) / (axm + axp + aym + ayp + azm + azp);
+    };
+
+    const int qbeg = z0 - 2, qend = z1 + 1;         // planes loaded
+    for (int q = qbeg; q <= qend; ++q) {
+        __syncthreads();                           // the slot of q+1 mod 4 == q-3 is free
+        load_plane(q);
+        __syncthreads();
+        const int qf = q - 1;                      // first colour at plane qf
+        if (qf >= z0 - 1 && qf <= z1) {
+            const int s0 = (qf + 8) & 3, sm = (qf + 7) & 3, sp = (qf + 9) & 3;
+            const int kg = gplane(qf);
+            const bool wall = !L.zper && (kg == -1 || kg == nz);
+            for (int t = threadIdx.x; t < (SX + 2) * (SY + 2); t += NT) {
+                const int dy = t / (SX + 2) - 1, dx = t % (SX + 2) - 1;
+                const int c = sidx(dx, dy);
+                // colour of the global point (periodic extents are even, so wrapping keeps parity)
+                const int par = ((i0 + dx) + (j0 + dy) + qf) & 1;
+                T v = R.u[s0][c];
+                if (!wall && kg != -99 && par == first) v = gs_update(qf, dx, dy, R.u[sm], R.u[s0], R.u[sp]);
+                R.r[s0][c] = v;
+            }
+        }
+        __syncthreads();
+        const int qs = q - 2;                      // second colour and output at plane qs
+        if (qs >= z0 && qs < z1) {
+            const int s0 = (qs + 8) & 3, sm = (qs + 7) & 3, sp = (qs + 9) & 3;
+            for (int t = threadIdx.x; t < SX * SY; t += NT) {
+                const int dy = t / SX, dx = t % SX;
+                const int i = i0 + dx, j = j0 + dy;
+                if (i >= nx || j >= ny) continue;
+                const int c = sidx(dx, dy);
+                const int par = (i + j + qs) & 1;
+                T v = R.r[s0][c];
+                if (par != first) v = gs_update(qs, dx, dy, R.r[sm], R.r[s0], R.r[sp]);
+                u_new[(long)qs * pl + (long)j * nx + i] = v;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+size_t rb_sweep_smem() { return sizeof(Ring<T>); }
+
+// allow the dynamic shared memory of the sweep (called before any capture)
+void rb_sweep_init() {
+    cudaFuncSetAttribute(k_rb_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Ring<float>));
+    cudaFuncSetAttribute(k_rb_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Ring<double>));
+}
+
+template <typename T>
+void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s) {
+    const size_t sm = sizeof(Ring<T>);
+    dim3 grid((L.nx + SX - 1) / SX, (L.ny + SY - 1) / SY, (L.nz + SZ - 1) / SZ);
+    k_rb_sweep<T><<<grid, NT, sm, s>>>(L, u_old, f, u_new, first);
+}
+
+template void launch_rb_sweep<float>(const LV<float>&, const float*, const float*, float*, int, cudaStream_t);
+template void launch_rb_sweep<double>(const LV<double>&, const double*, const double*, double*, int, cudaStream_t);
+
+}  // namespace gp
