@@ -117,11 +117,12 @@ def roofline_for(kind, prof, n0, hbm, hbm_src, prec_bytes):
         return None
     per_launch_s = p["ms"] / 1e3 / p["launches"]
     if kind == "smooth0":
-        # one red or black half sweep: half of the 16 B/pt (FP32) or 32 B/pt (FP64) sweep
-        bytes_per_launch = 0.5 * (4 * prec_bytes) * n0
+        # FP32: one launch = one fused red-black sweep, 16 B/pt (read u, f, eps; write u);
+        # FP64: one launch = one colour of a sweep, half of 32 B/pt
+        bytes_per_launch = 16.0 * n0
         achieved = bytes_per_launch / per_launch_s / 1e9
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_source": hbm_src, "kernel": "k_rbgs (finest level, half sweep)",
+                "peak_source": hbm_src, "kernel": "k_rb_sweep (finest level, fused red-black sweep)" if prec_bytes == 4 else "k_rbgs (finest level, one colour)",
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": per_launch_s * 1e3}
     if kind == "res64":
         # read phi, rho, eps (FP64), write r in the working precision; 30 FP64 flops per point

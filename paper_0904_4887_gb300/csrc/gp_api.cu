@@ -174,6 +174,7 @@ struct gp_ctx {
 
     // CUDA graphs: captured on a library stream that is ordered after / before the user's stream
     bool use_graphs = true;
+    bool capturing = false;
     cudaStream_t gs = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
@@ -210,7 +211,10 @@ struct ProfScope {
     gp_ctx* c; int kind; int launches; cudaEvent_t a{}, b{};
     ProfScope(gp_ctx* c_, int k, int n) : c(c_), kind(k), launches(n) {
         count_launch(n);
-        if (c->prof_on) { a = prof_event(c); GP_CUDA(cudaEventRecord(a, c->s)); }
+        if (c->prof_on) {
+            a = prof_event(c);
+            GP_CUDA(cudaEventRecordWithFlags(a, c->s, c->capturing ? cudaEventRecordExternal : 0));
+        }
     }
     ~ProfScope() {
         // never throws: a failed record only loses this sample
@@ -218,7 +222,10 @@ struct ProfScope {
             cudaEvent_t e = nullptr;
             if (!c->event_pool.empty()) { e = c->event_pool.back(); c->event_pool.pop_back(); }
             else if (cudaEventCreate(&e) != cudaSuccess) return;
-            if (cudaEventRecord(e, c->s) != cudaSuccess) { c->event_pool.push_back(e); return; }
+            if (cudaEventRecordWithFlags(e, c->s, c->capturing ? cudaEventRecordExternal : 0) != cudaSuccess) {
+                c->event_pool.push_back(e);
+                return;
+            }
             c->pending.push_back({kind, launches, a, e});
         }
     }
@@ -338,6 +345,15 @@ template <typename T>
 void smooth_fine(gp_ctx* c, Hier<T>& H, T* u, const T* f, int nu, int first) {
     if (nu <= 0) return;
     const LV<T>& V = H.lv[0];
+    if (sizeof(T) == 8) {
+        // FP64 is bound by the FP64 pipe: the two-launch sweep issues no redundant work
+        ProfScope ps(c, GP_PROF_SMOOTH0, 2 * nu);
+        for (int it = 0; it < nu; ++it) {
+            launch_rbgs<T>(V, u, f, first, c->s);
+            launch_rbgs<T>(V, u, f, 1 - first, c->s);
+        }
+        return;
+    }
     T* a = u;
     T* b = H.tmp;
     {
@@ -426,14 +442,17 @@ void pcg(gp_ctx* c, Hier<T>& H, int iters) {
         cudaGraph_t graph = nullptr;
         cudaError_t e1 = cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal);
         if (e1 == cudaSuccess) {
+            c->capturing = true;
             try {
                 pcg_body(c, H, iters);
             } catch (...) {
+                c->capturing = false;
                 cudaStreamEndCapture(c->gs, &graph);
                 if (graph) cudaGraphDestroy(graph);
                 c->s = user;
                 throw;
             }
+            c->capturing = false;
             e1 = cudaStreamEndCapture(c->gs, &graph);
         }
         c->s = user;
