@@ -76,18 +76,39 @@ __device__ __forceinline__ float box_dmax(const Tile& t, float cx, float cy, flo
 }
 
 // ----------------------------------------------------------------- eps
-// eps = 1 + (eps0 - 1) prod s(d), s(d) = erfc((r0 - d)/w)/2 = (1 + erf((d - r0)/w))/2
+// compact 8 x 2 x 2 block of the tile for warp w, lane l (spatially close points
+// take the same branches below)
+__device__ __forceinline__ void compact_point(int w, int l, int& tx, int& ty, int& tz) {
+    tx = (w & 3) * 8 + (l & 7);
+    ty = ((w >> 2) & 1) * 2 + ((l >> 3) & 1);
+    tz = (w >> 3) * 2 + (l >> 4);
+}
+
+// s(d) = erfc((r0 - d)/w)/2 with u = (d - r0)/w. Far from the switching
+// radius (|u| > 4) the factor is 1 - t or t with t = erfc(|u|)/2 < 7.7e-9:
+// FP32 erfc gives t to a few ulp, i.e. s to 1e-15 absolute (u > 4) or to
+// 1e-7 relative of a factor below 7.7e-9 (u < -4); otherwise FP64.
+__device__ __forceinline__ double switch_s(double u) {
+    if (u > 4.0) return 1.0 - 0.5 * (double)erfcf((float)u);
+    if (u < -4.0) return 0.5 * (double)erfcf((float)(-u));
+    return 0.5 * erfc(-u);
+}
+
+// eps = 1 + (eps0 - 1) prod s(d). Once (eps0-1) P < 2^-54 further factors
+// (all <= 1) cannot move 1 + (eps0-1) P away from 1.0, so the product stops.
 __global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p, double* eps64,
                                                   double* pe64, float* eps32) {
     __shared__ double ec[MAXE][3];
     __shared__ int ne;
     const Tile t = make_tile(g);
-    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    int tx, ty, tz;
+    compact_point(threadIdx.x >> 5, threadIdx.x & 31, tx, ty, tz);
     const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
     const bool valid = i < g.nx && j < g.ny && k < g.nz;
     const double x = i * g.hx, y = j * g.hy, z = k * g.hz;
     const double rc2 = p.rcut * p.rcut;
     const double iw = 1.0 / p.w;
+    const double tiny = 5.5e-17 / (p.eps0 - 1.0 > 0.0 ? p.eps0 - 1.0 : 1.0);
     const float rcf = (float)p.rcut + kMargin;
     double P = 1.0;
     for (int a0 = 0; a0 < at.n; a0 += ACH) {
@@ -105,11 +126,14 @@ __global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p,
         }
         __syncthreads();
         const int m = ne;
-        if (valid) {
+        if (valid && P >= tiny) {
             for (int e = 0; e < m; ++e) {
                 const double dx = x - ec[e][0], dy = y - ec[e][1], dz = z - ec[e][2];
                 const double d2 = dx * dx + dy * dy + dz * dz;
-                if (d2 < rc2) P *= 0.5 * erfc((p.r0 - sqrt(d2)) * iw);
+                if (d2 < rc2) {
+                    P *= switch_s((sqrt(d2) - p.r0) * iw);
+                    if (P < tiny) break;
+                }
             }
         }
         __syncthreads();
@@ -128,23 +152,40 @@ __global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p,
 // Separable Gaussians: g(r) = N exp(-dx^2/2s^2) exp(-dy^2/2s^2) exp(-dz^2/2s^2),
 // each factor zero outside |d| < cut*s. A tile tabulates the three 1D factors
 // per (atom, image, Gaussian) entry and every point then costs two products.
+// Entries whose largest value on the tile is below 1e-8 of their peak are
+// tabulated and summed in FP32 (their sum is far below FP64 rounding of the
+// total); the others in FP64.
 constexpr int RCH = 8;                  // atoms per chunk
 constexpr int RMAX = RCH * 27 * 2;      // entries per chunk
 constexpr int RSUB = 32;                // entries tabulated at a time
+constexpr double kTail = 1e-8;
+
+// largest exp(-d^2/2s^2) of a Gaussian centred at c over the tile box
+__device__ __forceinline__ double tile_peak(const Tile& t, const Geo& g, double cx, double cy, double cz, double sg) {
+    const double dx = fmax(fmax(t.i0 * g.hx - cx, cx - t.i1 * g.hx), 0.0);
+    const double dy = fmax(fmax(t.j0 * g.hy - cy, cy - t.j1 * g.hy), 0.0);
+    const double dz = fmax(fmax(t.k0 * g.hz - cz, cz - t.k1 * g.hz), 0.0);
+    return exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sg * sg));
+}
 
 __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, double* rho) {
-    __shared__ double en[RMAX][5];      // cx, cy, cz, sigma, coefficient
+    __shared__ double en[RMAX][5];      // cx, cy, cz, sigma, coefficient (FP64 entries from the front,
+                                        //  FP32 entries from the back)
     __shared__ double gx[RSUB][TX];
     __shared__ double gy[RSUB][TY];
     __shared__ double gz[RSUB][TZ];
-    __shared__ int ne;
+    __shared__ float fx32[RSUB][TX];
+    __shared__ float fy32[RSUB][TY];
+    __shared__ float fz32[RSUB][TZ];
+    __shared__ int n64, n32;
     const Tile t = make_tile(g);
     const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
     const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
     const bool valid = i < g.nx && j < g.ny && k < g.nz;
     double acc = 0.0;
+    float acc32 = 0.f;
     for (int a0 = 0; a0 < at.n; a0 += RCH) {
-        if (threadIdx.x == 0) ne = 0;
+        if (threadIdx.x == 0) { n64 = 0; n32 = 0; }
         __syncthreads();
         const int na = min(RCH, at.n - a0);
         for (int q = threadIdx.x; q < na * 54; q += TT) {
@@ -155,32 +196,34 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, d
             const float rad = (float)(cut * sg) + kMargin;
             if (box_dmax(t, fx, fy, fz) < rad) {
                 const double Z = at.gauss[3 * a + 0];
-                const int s = atomicAdd(&ne, 1);
-                image64(at.w64, a, im, g, en[s][0], en[s][1], en[s][2]);
-                en[s][3] = sg;
+                double cx, cy, cz;
+                image64(at.w64, a, im, g, cx, cy, cz);
+                const bool tail = tile_peak(t, g, cx, cy, cz, sg) < kTail;
+                const int s = tail ? RMAX - 1 - atomicAdd(&n32, 1) : atomicAdd(&n64, 1);
+                en[s][0] = cx; en[s][1] = cy; en[s][2] = cz; en[s][3] = sg;
                 const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
                 en[s][4] = (which == 0 ? Z : -Z) * norm;
             }
         }
         __syncthreads();
-        const int m = ne;
-        for (int e0 = 0; e0 < m; e0 += RSUB) {
-            const int ms = min(RSUB, m - e0);
+        const int m64 = n64, m32 = n32;
+        for (int e0 = 0; e0 < m64; e0 += RSUB) {
+            const int ms = min(RSUB, m64 - e0);
             for (int q = threadIdx.x; q < ms * (TX + TY + TZ); q += TT) {
                 const int e = q / (TX + TY + TZ), r = q % (TX + TY + TZ);
-                const double sg = en[e0 + e][3];
-                const double rad = cut * sg;
-                const double i2s = 1.0 / (2.0 * sg * sg);
+                const double* E = en[e0 + e];
+                const double rad = cut * E[3];
+                const double i2s = 1.0 / (2.0 * E[3] * E[3]);
                 if (r < TX) {
-                    const double d = (t.i0 + r) * g.hx - en[e0 + e][0];
+                    const double d = (t.i0 + r) * g.hx - E[0];
                     gx[e][r] = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
                 } else if (r < TX + TY) {
                     const int rr = r - TX;
-                    const double d = (t.j0 + rr) * g.hy - en[e0 + e][1];
-                    gy[e][rr] = (fabs(d) < rad) ? en[e0 + e][4] * exp(-d * d * i2s) : 0.0;
+                    const double d = (t.j0 + rr) * g.hy - E[1];
+                    gy[e][rr] = (fabs(d) < rad) ? E[4] * exp(-d * d * i2s) : 0.0;
                 } else {
                     const int rr = r - TX - TY;
-                    const double d = (t.k0 + rr) * g.hz - en[e0 + e][2];
+                    const double d = (t.k0 + rr) * g.hz - E[2];
                     gz[e][rr] = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
                 }
             }
@@ -190,8 +233,34 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, d
             }
             __syncthreads();
         }
+        for (int e0 = 0; e0 < m32; e0 += RSUB) {
+            const int ms = min(RSUB, m32 - e0);
+            for (int q = threadIdx.x; q < ms * (TX + TY + TZ); q += TT) {
+                const int e = q / (TX + TY + TZ), r = q % (TX + TY + TZ);
+                const double* E = en[RMAX - 1 - (e0 + e)];
+                const float rad = (float)(cut * E[3]);
+                const float i2s = (float)(1.0 / (2.0 * E[3] * E[3]));
+                if (r < TX) {
+                    const float d = (float)((t.i0 + r) * g.hx - E[0]);
+                    fx32[e][r] = (fabsf(d) < rad) ? expf(-d * d * i2s) : 0.f;
+                } else if (r < TX + TY) {
+                    const int rr = r - TX;
+                    const float d = (float)((t.j0 + rr) * g.hy - E[1]);
+                    fy32[e][rr] = (fabsf(d) < rad) ? (float)E[4] * expf(-d * d * i2s) : 0.f;
+                } else {
+                    const int rr = r - TX - TY;
+                    const float d = (float)((t.k0 + rr) * g.hz - E[2]);
+                    fz32[e][rr] = (fabsf(d) < rad) ? expf(-d * d * i2s) : 0.f;
+                }
+            }
+            __syncthreads();
+            if (valid) {
+                for (int e = 0; e < ms; ++e) acc32 = fmaf(fx32[e][tx] * fy32[e][ty], fz32[e][tz], acc32);
+            }
+            __syncthreads();
+        }
     }
-    if (valid) rho[i + (long)g.nx * (j + (long)g.ny * k)] = acc;
+    if (valid) rho[i + (long)g.nx * (j + (long)g.ny * k)] = acc + (double)acc32;
 }
 
 // ----------------------------------------------------------------- dry planes
@@ -253,40 +322,44 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// dielectric part: S_a = sum_i w_i pe_i sum_images q(d) (-(r_i - c)/d), with
-// w_i = (1/2) sum over the six faces of i of (grad_f phi)^2, pe = eps - 1,
+// dielectric part: S_a = sum_i W_i sum_images q(d) (-(r_i - c)/d), with
+// W_i = (1/2) sum over the six faces of i of (grad_f phi)^2 times pe_i = eps_i - 1,
 // q = s'/s. G_eps_a = -h^3/(8 pi) S_a (applied in k_forces_finish).
+// One warp per (atom, image) entry runs over the tile's 512 points in compact
+// 8 x 2 x 2 blocks. Pairs with |u| > 3.5 contribute at most 5e-6 of a pair at
+// the switching radius; their s and s' are taken in FP32.
 __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p, const double* phi,
                                                    const double* pe64, double* S) {
     __shared__ double ec[MAXE][3];
     __shared__ int eatom[MAXE];
-    __shared__ double eacc[MAXE][3];
+    __shared__ double Ws[TT];
     __shared__ int ne;
     const Tile t = make_tile(g);
-    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
-    const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
-    const bool valid = i < g.nx && j < g.ny && k < g.nz;
-    const double x = i * g.hx, y = j * g.hy, z = k * g.hz;
-    double W = 0.0;
-    if (valid) {
-        const long pl = plane_of(g.nx, g.ny);
-        const long c = i + (long)g.nx * (j + (long)g.ny * k);
-        const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
-        const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
-        const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
-        const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
-        const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
-        const double p0 = phi[c];
-        const double ax = (phi[xp] - p0) / g.hx, bx = (p0 - phi[xm]) / g.hx;
-        const double ay = (phi[yp] - p0) / g.hy, by = (p0 - phi[ym]) / g.hy;
-        const double az = (phi[zp] - p0) / g.hz, bz = (p0 - phi[zm]) / g.hz;
-        W = 0.5 * (ax * ax + bx * bx + ay * ay + by * by + az * az + bz * bz) * pe64[c];
+    {
+        const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+        const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+        double W = 0.0;
+        if (i < g.nx && j < g.ny && k < g.nz) {
+            const long pl = plane_of(g.nx, g.ny);
+            const long c = i + (long)g.nx * (j + (long)g.ny * k);
+            const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
+            const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
+            const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
+            const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
+            const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
+            const double p0 = phi[c];
+            const double ax = (phi[xp] - p0) / g.hx, bx = (p0 - phi[xm]) / g.hx;
+            const double ay = (phi[yp] - p0) / g.hy, by = (p0 - phi[ym]) / g.hy;
+            const double az = (phi[zp] - p0) / g.hz, bz = (p0 - phi[zm]) / g.hz;
+            W = 0.5 * (ax * ax + bx * bx + ay * ay + by * by + az * az + bz * bz) * pe64[c];
+        }
+        Ws[threadIdx.x] = W;   // index tx + TX (ty + TY tz)
     }
     const double rc2 = p.rcut * p.rcut;
     const double iw = 1.0 / p.w;
     const double sp_norm = 1.0 / (p.w * sqrt(kPi));
     const float rcf = (float)p.rcut + kMargin;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int a0 = 0; a0 < at.n; a0 += ACH) {
         if (threadIdx.x == 0) ne = 0;
         __syncthreads();
@@ -299,58 +372,67 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
                 const int s = atomicAdd(&ne, 1);
                 image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
                 eatom[s] = a;
-                eacc[s][0] = 0.0; eacc[s][1] = 0.0; eacc[s][2] = 0.0;
             }
         }
         __syncthreads();
         const int m = ne;
-        for (int e = 0; e < m; ++e) {
+        for (int e = warp; e < m; e += TT / 32) {
+            const double cx = ec[e][0], cy = ec[e][1], cz = ec[e][2];
             double fx = 0.0, fy = 0.0, fz = 0.0;
-            if (valid) {
-                const double dx = x - ec[e][0], dy = y - ec[e][1], dz = z - ec[e][2];
+            for (int blk = 0; blk < 16; ++blk) {
+                int tx, ty, tz;
+                compact_point(blk, lane, tx, ty, tz);
+                const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+                if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
+                const double dx = i * g.hx - cx, dy = j * g.hy - cy, dz = k * g.hz - cz;
                 const double d2 = dx * dx + dy * dy + dz * dz;
-                if (d2 < rc2 && d2 > 0.0) {
-                    const double d = sqrt(d2);
-                    const double u = (d - p.r0) * iw;
-                    const double s = 0.5 * erfc(-u);
-                    const double sp = sp_norm * exp(-u * u);
-                    const double c = -W * sp / (s * d);
-                    fx = c * dx; fy = c * dy; fz = c * dz;
+                if (!(d2 < rc2 && d2 > 0.0)) continue;
+                const double W = Ws[tx + TX * (ty + TY * tz)];
+                const double d = sqrt(d2);
+                const double u = (d - p.r0) * iw;
+                double ratio;   // s'(d) / (s(d) d)
+                if (fabs(u) > 3.5) {
+                    const float uf = (float)u;
+                    const float sf = 0.5f * erfcf(-uf);
+                    const float spf = (float)sp_norm * expf(-uf * uf);
+                    ratio = (double)(spf / (sf * (float)d));
+                } else {
+                    ratio = sp_norm * exp(-u * u) / (0.5 * erfc(-u) * d);
                 }
+                const double c = -W * ratio;
+                fx += c * dx; fy += c * dy; fz += c * dz;
             }
             fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
-            if (lane == 0 && (fx != 0.0 || fy != 0.0 || fz != 0.0)) {
-                atomicAdd(&eacc[e][0], fx); atomicAdd(&eacc[e][1], fy); atomicAdd(&eacc[e][2], fz);
+            if (lane == 0) {
+                const int a = eatom[e];
+                if (fx != 0.0) atomicAdd(&S[3 * a + 0], fx);
+                if (fy != 0.0) atomicAdd(&S[3 * a + 1], fy);
+                if (fz != 0.0) atomicAdd(&S[3 * a + 2], fz);
             }
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < m; e += TT) {
-            const int a = eatom[e];
-            if (eacc[e][0] != 0.0) atomicAdd(&S[3 * a + 0], eacc[e][0]);
-            if (eacc[e][1] != 0.0) atomicAdd(&S[3 * a + 1], eacc[e][1]);
-            if (eacc[e][2] != 0.0) atomicAdd(&S[3 * a + 2], eacc[e][2]);
         }
         __syncthreads();
     }
 }
 
-// charge part: T_a = sum_i phi_i d rho~_i / d R_a with d g / d R = g (r - c)/sigma^2,
-// tabulated per tile like k_build_rho. G_rho_a = h^3 T_a.
+// charge part: T_a = sum_i phi_i d rho~_i / d R_a with d g / d R = g (r - c)/sigma^2.
+// One warp per (atom, image, Gaussian) entry, lanes along x; the y and z
+// factors are separable, so each lane first sums its column over the 16
+// (y, z) rows. Entries below 1e-8 of their peak on the tile run in FP32.
 __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, const double* phi,
                                                    double* T) {
     __shared__ double en[RMAX][5];
     __shared__ int eatom[RMAX];
-    __shared__ double gx[RSUB][TX], dxs[RSUB][TX];
-    __shared__ double gy[RSUB][TY], dys[RSUB][TY];
-    __shared__ double gz[RSUB][TZ], dzs[RSUB][TZ];
-    __shared__ double eacc[RSUB][3];
+    __shared__ double ph[TT];
     __shared__ int ne;
     const Tile t = make_tile(g);
-    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
-    const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
-    const bool valid = i < g.nx && j < g.ny && k < g.nz;
-    const double ph = valid ? phi[i + (long)g.nx * (j + (long)g.ny * k)] : 0.0;
-    const int lane = threadIdx.x & 31;
+    {
+        const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+        const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+        ph[threadIdx.x] = (i < g.nx && j < g.ny && k < g.nz) ? phi[i + (long)g.nx * (j + (long)g.ny * k)] : 0.0;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = t.i0 + lane;
+    const bool lane_ok = i < g.nx;
     for (int a0 = 0; a0 < at.n; a0 += RCH) {
         if (threadIdx.x == 0) ne = 0;
         __syncthreads();
@@ -373,57 +455,79 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, 
         }
         __syncthreads();
         const int m = ne;
-        for (int e0 = 0; e0 < m; e0 += RSUB) {
-            const int ms = min(RSUB, m - e0);
-            for (int q = threadIdx.x; q < ms * (TX + TY + TZ); q += TT) {
-                const int e = q / (TX + TY + TZ), r = q % (TX + TY + TZ);
-                const double sg = en[e0 + e][3];
-                const double rad = cut * sg;
-                const double i2s = 1.0 / (2.0 * sg * sg);
-                if (r < TX) {
-                    const double d = (t.i0 + r) * g.hx - en[e0 + e][0];
-                    const double v = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
-                    gx[e][r] = v; dxs[e][r] = v * d;
-                } else if (r < TX + TY) {
-                    const int rr = r - TX;
-                    const double d = (t.j0 + rr) * g.hy - en[e0 + e][1];
-                    const double v = (fabs(d) < rad) ? en[e0 + e][4] * exp(-d * d * i2s) : 0.0;
-                    gy[e][rr] = v; dys[e][rr] = v * d;
-                } else {
-                    const int rr = r - TX - TY;
-                    const double d = (t.k0 + rr) * g.hz - en[e0 + e][2];
-                    const double v = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
-                    gz[e][rr] = v; dzs[e][rr] = v * d;
+        for (int e = warp; e < m; e += TT / 32) {
+            const double cx = en[e][0], cy = en[e][1], cz = en[e][2], sg = en[e][3], coef = en[e][4];
+            const double rad = cut * sg;
+            const double i2s = 1.0 / (2.0 * sg * sg);
+            double fx = 0.0, fy = 0.0, fz = 0.0;
+            if (tile_peak(t, g, cx, cy, cz, sg) < kTail) {
+                // FP32: lane < 8 tabulates one y or z factor, shared by shuffles
+                float gyz_v = 0.f, d_v = 0.f;
+                if (lane < TY) {
+                    const float d = (float)((t.j0 + lane) * g.hy - cy);
+                    d_v = d;
+                    gyz_v = (fabsf(d) < (float)rad) ? expf(-d * d * (float)i2s) : 0.f;
+                } else if (lane < TY + TZ) {
+                    const float d = (float)((t.k0 + lane - TY) * g.hz - cz);
+                    d_v = d;
+                    gyz_v = (fabsf(d) < (float)rad) ? expf(-d * d * (float)i2s) : 0.f;
                 }
-                if (r == 0) { eacc[e][0] = 0.0; eacc[e][1] = 0.0; eacc[e][2] = 0.0; }
-            }
-            __syncthreads();
-            for (int e = 0; e < ms; ++e) {
-                double fx = 0.0, fy = 0.0, fz = 0.0;
-                if (valid) {
-                    const double gyz = gy[e][ty] * gz[e][tz];
-                    fx = ph * dxs[e][tx] * gyz;
-                    fy = ph * gx[e][tx] * dys[e][ty] * gz[e][tz];
-                    fz = ph * gx[e][tx] * gy[e][ty] * dzs[e][tz];
+                const float dxf = (float)(i * g.hx - cx);
+                const float gxf = (lane_ok && fabsf(dxf) < (float)rad) ? expf(-dxf * dxf * (float)i2s) : 0.f;
+                float s0 = 0.f, sy = 0.f, sz = 0.f;
+                for (int tz = 0; tz < TZ; ++tz) {
+                    const float gz = __shfl_sync(0xffffffffu, gyz_v, TY + tz);
+                    const float dz = __shfl_sync(0xffffffffu, d_v, TY + tz);
+                    for (int ty = 0; ty < TY; ++ty) {
+                        const float gy = __shfl_sync(0xffffffffu, gyz_v, ty);
+                        const float dy = __shfl_sync(0xffffffffu, d_v, ty);
+                        const float v = (float)ph[lane + TX * (ty + TY * tz)] * gy * gz;
+                        s0 += v; sy += v * dy; sz += v * dz;
+                    }
                 }
-                fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
-                if (lane == 0 && (fx != 0.0 || fy != 0.0 || fz != 0.0)) {
-                    atomicAdd(&eacc[e][0], fx); atomicAdd(&eacc[e][1], fy); atomicAdd(&eacc[e][2], fz);
+                fx = coef * (double)(dxf * gxf * s0);
+                fy = coef * (double)(gxf * sy);
+                fz = coef * (double)(gxf * sz);
+            } else {
+                double gyz_v = 0.0, d_v = 0.0;
+                if (lane < TY) {
+                    const double d = (t.j0 + lane) * g.hy - cy;
+                    d_v = d;
+                    gyz_v = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
+                } else if (lane < TY + TZ) {
+                    const double d = (t.k0 + lane - TY) * g.hz - cz;
+                    d_v = d;
+                    gyz_v = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
                 }
+                const double dx = i * g.hx - cx;
+                const double gx = (lane_ok && fabs(dx) < rad) ? exp(-dx * dx * i2s) : 0.0;
+                double s0 = 0.0, sy = 0.0, sz = 0.0;
+                for (int tz = 0; tz < TZ; ++tz) {
+                    const double gz = __shfl_sync(0xffffffffu, gyz_v, TY + tz);
+                    const double dz = __shfl_sync(0xffffffffu, d_v, TY + tz);
+                    for (int ty = 0; ty < TY; ++ty) {
+                        const double gy = __shfl_sync(0xffffffffu, gyz_v, ty);
+                        const double dy = __shfl_sync(0xffffffffu, d_v, ty);
+                        const double v = ph[lane + TX * (ty + TY * tz)] * gy * gz;
+                        s0 += v; sy += v * dy; sz += v * dz;
+                    }
+                }
+                fx = coef * dx * gx * s0;
+                fy = coef * gx * sy;
+                fz = coef * gx * sz;
             }
-            __syncthreads();
-            for (int e = threadIdx.x; e < ms; e += TT) {
-                const int a = eatom[e0 + e];
-                if (eacc[e][0] != 0.0) atomicAdd(&T[3 * a + 0], eacc[e][0]);
-                if (eacc[e][1] != 0.0) atomicAdd(&T[3 * a + 1], eacc[e][1]);
-                if (eacc[e][2] != 0.0) atomicAdd(&T[3 * a + 2], eacc[e][2]);
+            fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+            if (lane == 0) {
+                const int a = eatom[e];
+                if (fx != 0.0) atomicAdd(&T[3 * a + 0], fx);
+                if (fy != 0.0) atomicAdd(&T[3 * a + 1], fy);
+                if (fz != 0.0) atomicAdd(&T[3 * a + 2], fz);
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
 }
 
-// F = -(G_eps + G_rho) with G_eps = ce * S and G_rho = cr * T
 __global__ void k_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < 3 * n) F[q] = -(ce * S[q] + (T ? cr * T[q] : 0.0));

@@ -45,28 +45,39 @@ __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ 
     const int z0 = blockIdx.z * SZ;
     const int z1 = min(z0 + SZ, nz);
     const T cx = (T)0.5 * L.ihx2, cy = (T)0.5 * L.ihy2, cz = (T)0.5 * L.ihz2;
+    const int second = 1 - first;
+    const int tid = threadIdx.x;
 
-    // smem index of (dx, dy) with dx in [-2, SX+2), dy in [-2, SY+2)
-    auto sidx = [](int dx, int dy) { return (dy + 2) * HX + (dx + 2); };
-
-    // global plane index of march plane q, or -99 when it does not exist (Dirichlet beyond the walls)
-    auto gplane = [&](int q) -> int {
-        if (L.zper) return ((q % nz) + nz) % nz;
-        return (q < -1 || q > nz) ? -99 : q;
-    };
+    // in-plane offsets of this thread's halo-tile elements (periodic wrap), once
+    constexpr int NL = (HP + NT - 1) / NT;
+    int off[NL];
+#pragma unroll
+    for (int r = 0; r < NL; ++r) {
+        const int t = tid + r * NT;
+        off[r] = -1;
+        if (t < HP) {
+            const int dy = t / HX - 2, dx = t % HX - 2;
+            const int i = ((i0 + dx) % nx + nx) % nx, j = ((j0 + dy) % ny + ny) % ny;
+            off[r] = j * nx + i;
+        }
+    }
 
     auto load_plane = [&](int q) {
         const int slot = (q + 8) & 3;
-        const int kg = gplane(q);
-        for (int t = threadIdx.x; t < HP; t += NT) {
-            const int dy = t / HX - 2, dx = t % HX - 2;
-            const int i = ((i0 + dx) % nx + nx) % nx, j = ((j0 + dy) % ny + ny) % ny;
+        int kg;
+        if (L.zper) kg = q < 0 ? q + nz : (q >= nz ? q - nz : q);
+        else kg = (q < -1 || q > nz) ? -99 : q;
+        const bool inner = kg >= 0 && kg < nz;
+        const long base = (long)kg * pl;
+#pragma unroll
+        for (int r = 0; r < NL; ++r) {
+            if (off[r] < 0) continue;
+            const int t = tid + r * NT;
             T uv = 0, ev = 1, fv = 0;
             if (kg != -99) {
-                const long g = (long)kg * pl + (long)j * nx + i;
-                uv = u_old[g];
-                ev = L.eps[g];
-                if (kg >= 0 && kg < nz) fv = f[g];
+                uv = u_old[base + off[r]];
+                ev = L.eps[base + off[r]];
+                if (inner) fv = f[base + off[r]];
             }
             R.u[slot][t] = uv;
             R.e[slot][t] = ev;
@@ -74,53 +85,53 @@ __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ 
         }
     };
 
-    // Gauss-Seidel value at (dx, dy) of plane q from the values in `src` for
-    // the in-plane neighbours and srcm / srcp for the planes below / above
-    auto gs_update = [&](int q, int dx, int dy, const T* srcm, const T* src, const T* srcp) -> T {
-        const int s0 = (q + 8) & 3, sm = (q + 7) & 3, sp = (q + 9) & 3;
-        const int c = sidx(dx, dy);
+    // Gauss-Seidel value at smem cell c of plane slot s0 (neighbour planes sm, sp)
+    auto gs_update = [&](int c, int s0, int sm, int sp, const T* srcm, const T* src, const T* srcp) -> T {
         const T e0 = R.e[s0][c];
         const T axm = (e0 + R.e[s0][c - 1]) * cx, axp = (e0 + R.e[s0][c + 1]) * cx;
         const T aym = (e0 + R.e[s0][c - HX]) * cy, ayp = (e0 + R.e[s0][c + HX]) * cy;
         const T azm = (e0 + R.e[sm][c]) * cz, azp = (e0 + R.e[sp][c]) * cz;
         const T s = axm * src[c - 1] + axp * src[c + 1] + aym * src[c - HX] + ayp * src[c + HX] + azm * srcm[c] +
                     azp * srcp[c];
-        return (s - R.f[s0][c]) / (axm + axp + aym + ayp + azm + azp);
+        const T d = axm + axp + aym + ayp + azm + azp;
+        if constexpr (sizeof(T) == 4) return __fdividef(s - R.f[s0][c], d);
+        else return (s - R.f[s0][c]) / d;
     };
 
-    const int qbeg = z0 - 2, qend = z1 + 1;         // planes loaded
-    for (int q = qbeg; q <= qend; ++q) {
-        __syncthreads();                           // the slot of q+1 mod 4 == q-3 is free
+    constexpr int HALF1 = (SX + 2) / 2;              // first-colour points per halo-1 row
+    constexpr int NF = HALF1 * (SY + 2);             // first-colour points on the halo-1 tile
+    for (int q = z0 - 2; q <= z1 + 1; ++q) {
+        __syncthreads();                             // plane q-4's slot is free
         load_plane(q);
         __syncthreads();
-        const int qf = q - 1;                      // first colour at plane qf
+        const int qf = q - 1;                        // first colour, new values, at plane qf
         if (qf >= z0 - 1 && qf <= z1) {
             const int s0 = (qf + 8) & 3, sm = (qf + 7) & 3, sp = (qf + 9) & 3;
-            const int kg = gplane(qf);
-            const bool wall = !L.zper && (kg == -1 || kg == nz);
-            for (int t = threadIdx.x; t < (SX + 2) * (SY + 2); t += NT) {
-                const int dy = t / (SX + 2) - 1, dx = t % (SX + 2) - 1;
-                const int c = sidx(dx, dy);
-                // colour of the global point (periodic extents are even, so wrapping keeps parity)
-                const int par = ((i0 + dx) + (j0 + dy) + qf) & 1;
-                T v = R.u[s0][c];
-                if (!wall && kg != -99 && par == first) v = gs_update(qf, dx, dy, R.u[sm], R.u[s0], R.u[sp]);
-                R.r[s0][c] = v;
+            const bool wall = !L.zper && (qf == -1 || qf == nz);
+            for (int t = tid; t < NF; t += NT) {
+                const int dy = t / HALF1 - 1, m = t % HALF1;
+                const int p = (first - (i0 - 1 + j0 + dy + qf)) & 1;
+                const int dx = -1 + 2 * m + p;
+                const int c = (dy + 2) * HX + (dx + 2);
+                R.r[s0][c] = wall ? R.u[s0][c] : gs_update(c, s0, sm, sp, R.u[sm], R.u[s0], R.u[sp]);
             }
         }
         __syncthreads();
-        const int qs = q - 2;                      // second colour and output at plane qs
+        const int qs = q - 2;                        // second colour, and the output plane
         if (qs >= z0 && qs < z1) {
             const int s0 = (qs + 8) & 3, sm = (qs + 7) & 3, sp = (qs + 9) & 3;
-            for (int t = threadIdx.x; t < SX * SY; t += NT) {
-                const int dy = t / SX, dx = t % SX;
-                const int i = i0 + dx, j = j0 + dy;
+            for (int t = tid; t < (SX / 2) * SY; t += NT) {
+                const int dy = t / (SX / 2), m = t % (SX / 2);
+                const int i = i0 + 2 * m, j = j0 + dy;
                 if (i >= nx || j >= ny) continue;
-                const int c = sidx(dx, dy);
-                const int par = (i + j + qs) & 1;
-                T v = R.r[s0][c];
-                if (par != first) v = gs_update(qs, dx, dy, R.r[sm], R.r[s0], R.r[sp]);
-                u_new[(long)qs * pl + (long)j * nx + i] = v;
+                const int c0 = (dy + 2) * HX + (2 * m + 2);        // even member of the x pair
+                const int p2 = (second - (i + j + qs)) & 1;        // which member has the second colour
+                const int cs = c0 + p2, cf = c0 + 1 - p2;
+                const T vs = gs_update(cs, s0, sm, sp, R.r[sm], R.r[s0], R.r[sp]);
+                const T vf = R.r[s0][cf];
+                T* out = u_new + (long)qs * pl + (long)j * nx + i;
+                out[0] = p2 ? vf : vs;
+                out[1] = p2 ? vs : vf;
             }
         }
     }
