@@ -21,49 +21,69 @@
 namespace gp {
 namespace {
 
-constexpr int SX = 64, SY = 8, SZ = 32;           // output tile per CTA
+constexpr int SX = 64, SY = 8;                    // output tile per CTA (x, y); z chunk set at launch
 constexpr int HX = SX + 4, HY = SY + 4;           // with a 2-point halo
 constexpr int HP = HX * HY;
 constexpr int NT = 256;
 
+constexpr int NRING = 6;                          // planes q-3 .. q+1 resident, q+2 in flight
+
 template <typename T>
-struct Ring {
-    T u[4][HP];
-    T e[4][HP];
-    T f[4][HP];
-    T r[4][HP];
+struct __align__(16) Ring {
+    T u[NRING][HP];
+    T e[NRING][HP];
+    T f[NRING][HP];
+    T r[4][HP];                                   // first-colour values of planes q-3 .. q-1
 };
+
+// asynchronous copy of two consecutive elements (8 bytes in FP32, 16 in FP64)
+__device__ __forceinline__ void cp_async_pair(float* smem_dst, const float* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_pair(double* smem_dst, const double* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ u_old, const T* __restrict__ f,
-                                                 T* __restrict__ u_new, int first) {
+                                                 T* __restrict__ u_new, int first, int sz) {
     extern __shared__ unsigned char smem_raw[];
     Ring<T>& R = *reinterpret_cast<Ring<T>*>(smem_raw);
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const long pl = (long)nx * ny;
     const int i0 = blockIdx.x * SX, j0 = blockIdx.y * SY;
-    const int z0 = blockIdx.z * SZ;
-    const int z1 = min(z0 + SZ, nz);
+    const int z0 = blockIdx.z * sz;
+    const int z1 = min(z0 + sz, nz);
+    if (z0 >= nz) return;
     const T cx = (T)0.5 * L.ihx2, cy = (T)0.5 * L.ihy2, cz = (T)0.5 * L.ihz2;
     const int second = 1 - first;
     const int tid = threadIdx.x;
 
-    // in-plane offsets of this thread's halo-tile elements (periodic wrap), once
-    constexpr int NL = (HP + NT - 1) / NT;
+    // This thread copies x-pairs of the halo tile: pair p covers cells (2p, 2p+1)
+    // of the tile. Its in-plane global offset (periodic wrap; nx even keeps
+    // pairs whole) is computed once.
+    constexpr int NPAIR = HP / 2;
+    constexpr int NL = (NPAIR + NT - 1) / NT;
     int off[NL];
 #pragma unroll
     for (int r = 0; r < NL; ++r) {
-        const int t = tid + r * NT;
+        const int p = tid + r * NT;
         off[r] = -1;
-        if (t < HP) {
+        if (p < NPAIR) {
+            const int t = 2 * p;
             const int dy = t / HX - 2, dx = t % HX - 2;
             const int i = ((i0 + dx) % nx + nx) % nx, j = ((j0 + dy) % ny + ny) % ny;
             off[r] = j * nx + i;
         }
     }
 
-    auto load_plane = [&](int q) {
-        const int slot = (q + 8) & 3;
+    auto issue_plane = [&](int q) {
+        if (q > z1 + 1) { cp_async_commit(); return; }
+        const int slot = (q + 60) % NRING;
         int kg;
         if (L.zper) kg = q < 0 ? q + nz : (q >= nz ? q - nz : q);
         else kg = (q < -1 || q > nz) ? -99 : q;
@@ -72,17 +92,18 @@ __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ 
 #pragma unroll
         for (int r = 0; r < NL; ++r) {
             if (off[r] < 0) continue;
-            const int t = tid + r * NT;
-            T uv = 0, ev = 1, fv = 0;
+            const int t = 2 * (tid + r * NT);
             if (kg != -99) {
-                uv = u_old[base + off[r]];
-                ev = L.eps[base + off[r]];
-                if (inner) fv = f[base + off[r]];
+                cp_async_pair(&R.u[slot][t], u_old + base + off[r]);
+                cp_async_pair(&R.e[slot][t], L.eps + base + off[r]);
+            } else {
+                R.u[slot][t] = 0; R.u[slot][t + 1] = 0;
+                R.e[slot][t] = 1; R.e[slot][t + 1] = 1;
             }
-            R.u[slot][t] = uv;
-            R.e[slot][t] = ev;
-            R.f[slot][t] = fv;
+            if (inner) cp_async_pair(&R.f[slot][t], f + base + off[r]);
+            else { R.f[slot][t] = 0; R.f[slot][t + 1] = 0; }
         }
+        cp_async_commit();
     };
 
     // Gauss-Seidel value at smem cell c of plane slot s0 (neighbour planes sm, sp)
@@ -100,26 +121,29 @@ __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ 
 
     constexpr int HALF1 = (SX + 2) / 2;              // first-colour points per halo-1 row
     constexpr int NF = HALF1 * (SY + 2);             // first-colour points on the halo-1 tile
+    issue_plane(z0 - 2);
     for (int q = z0 - 2; q <= z1 + 1; ++q) {
-        __syncthreads();                             // plane q-4's slot is free
-        load_plane(q);
-        __syncthreads();
+        issue_plane(q + 1);                          // prefetch the next plane
+        cp_async_wait1();                            // this thread's copies of plane q landed
+        __syncthreads();                             // ... and everyone's
         const int qf = q - 1;                        // first colour, new values, at plane qf
         if (qf >= z0 - 1 && qf <= z1) {
-            const int s0 = (qf + 8) & 3, sm = (qf + 7) & 3, sp = (qf + 9) & 3;
+            const int s0 = (qf + 60) % NRING, sm = (qf + 59) % NRING, sp = (qf + 61) % NRING;
+            const int r0 = (qf + 8) & 3;
             const bool wall = !L.zper && (qf == -1 || qf == nz);
             for (int t = tid; t < NF; t += NT) {
                 const int dy = t / HALF1 - 1, m = t % HALF1;
                 const int p = (first - (i0 - 1 + j0 + dy + qf)) & 1;
                 const int dx = -1 + 2 * m + p;
                 const int c = (dy + 2) * HX + (dx + 2);
-                R.r[s0][c] = wall ? R.u[s0][c] : gs_update(c, s0, sm, sp, R.u[sm], R.u[s0], R.u[sp]);
+                R.r[r0][c] = wall ? R.u[s0][c] : gs_update(c, s0, sm, sp, R.u[sm], R.u[s0], R.u[sp]);
             }
         }
         __syncthreads();
         const int qs = q - 2;                        // second colour, and the output plane
         if (qs >= z0 && qs < z1) {
-            const int s0 = (qs + 8) & 3, sm = (qs + 7) & 3, sp = (qs + 9) & 3;
+            const int s0 = (qs + 60) % NRING, sm = (qs + 59) % NRING, sp = (qs + 61) % NRING;
+            const int r0 = (qs + 8) & 3, rm = (qs + 7) & 3, rp = (qs + 9) & 3;
             for (int t = tid; t < (SX / 2) * SY; t += NT) {
                 const int dy = t / (SX / 2), m = t % (SX / 2);
                 const int i = i0 + 2 * m, j = j0 + dy;
@@ -127,8 +151,8 @@ __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ 
                 const int c0 = (dy + 2) * HX + (2 * m + 2);        // even member of the x pair
                 const int p2 = (second - (i + j + qs)) & 1;        // which member has the second colour
                 const int cs = c0 + p2, cf = c0 + 1 - p2;
-                const T vs = gs_update(cs, s0, sm, sp, R.r[sm], R.r[s0], R.r[sp]);
-                const T vf = R.r[s0][cf];
+                const T vs = gs_update(cs, s0, sm, sp, R.r[rm], R.r[r0], R.r[rp]);
+                const T vf = R.r[r0][cf];
                 T* out = u_new + (long)qs * pl + (long)j * nx + i;
                 out[0] = p2 ? vf : vs;
                 out[1] = p2 ? vs : vf;
@@ -151,8 +175,15 @@ void rb_sweep_init() {
 template <typename T>
 void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s) {
     const size_t sm = sizeof(Ring<T>);
-    dim3 grid((L.nx + SX - 1) / SX, (L.ny + SY - 1) / SY, (L.nz + SZ - 1) / SZ);
-    k_rb_sweep<T><<<grid, NT, sm, s>>>(L, u_old, f, u_new, first);
+    // z chunk: about one wave of resident CTAs (3 per SM fit the shared memory)
+    const int txy = ((L.nx + SX - 1) / SX) * ((L.ny + SY - 1) / SY);
+    const int target = 152 * (sizeof(T) == 4 ? 3 : 1);
+    int chunks = (target + txy - 1) / txy;
+    if (chunks > L.nz) chunks = L.nz;
+    if (chunks < 1) chunks = 1;
+    const int sz = (L.nz + chunks - 1) / chunks;
+    dim3 grid((L.nx + SX - 1) / SX, (L.ny + SY - 1) / SY, (L.nz + sz - 1) / sz);
+    k_rb_sweep<T><<<grid, NT, sm, s>>>(L, u_old, f, u_new, first, sz);
 }
 
 template void launch_rb_sweep<float>(const LV<float>&, const float*, const float*, float*, int, cudaStream_t);
