@@ -73,9 +73,11 @@ typedef struct {
     int levels;           /* multigrid levels; 0 = coarsen until the coarsest grid has <= 512 points */
     int inner;            /* multigrid-preconditioned CG iterations per outer FP64 correction */
     int max_outer;        /* outer FP64 corrections before GP_ERR_NOT_CONVERGED */
-    int accel;            /* split: 1 = accelerate the self-consistent coupling with FP64 flexible
-                             GMRES (same fixed point); 0 = plain coupling iteration */
-    int restart;          /* split with accel: Krylov vectors kept before a restart (10, <= 15) */
+    int accel;            /* split: 1 = each FP64 outer correction is solved by flexible GMRES in the
+                             working precision, preconditioned by the split (same fixed point);
+                             0 = plain self-consistent coupling iteration */
+    int restart;          /* split with accel: GMRES steps per outer correction (12, <= 15) */
+    int band_vcycles;     /* split: V-cycles on the wet band per application of the split (1) */
 } gp_params;
 
 #define GP_HISTORY 64

@@ -30,6 +30,24 @@ struct Err {
 
 #define GP_CHECK_LAUNCH() GP_CUDA(cudaGetLastError())
 
+// A captured CUDA graph and what replaying it adds to the counters: the
+// kernel launches, V-cycles and inner iterations it holds, and (when it was
+// captured with profiling on) its event pairs per kernel group.
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    long key = -1;
+    long launches = 0;
+    int vcycles = 0, inner = 0;
+    std::vector<int> kinds, nlaunch;
+    std::vector<cudaEvent_t> ev;
+};
+
+void clear_slot(GraphSlot& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+    g = GraphSlot();
+}
+
 template <typename T>
 struct Hier {
     int L = 0;
@@ -48,13 +66,8 @@ struct Hier {
     int nc = 0;
     std::vector<void*> allocs;
     bool ready = false;
-    // captured CUDA graph of pcg(iters) on this hierarchy
-    cudaGraphExec_t pcg_exec = nullptr;
-    long pcg_key = -1;
-    long pcg_launches = 0;
-    int pcg_vcycles = 0, pcg_inner = 0;
-    std::vector<int> pcg_kinds, pcg_nlaunch;
-    std::vector<cudaEvent_t> pcg_ev;          // event pairs recorded inside the graph (profiling)
+    GraphSlot pcg_g;                            // pcg(iters) on this hierarchy
+    std::vector<GraphSlot> prec_g;              // split preconditioner into Krylov vector j (band only)
 };
 
 template <typename T>
@@ -70,8 +83,8 @@ T* alloc_level(Hier<T>& H, int nx, int ny, int nz) {
 
 template <typename T>
 void free_hier(Hier<T>& H) {
-    if (H.pcg_exec) cudaGraphExecDestroy(H.pcg_exec);
-    for (cudaEvent_t e : H.pcg_ev) cudaEventDestroy(e);
+    clear_slot(H.pcg_g);
+    for (GraphSlot& g : H.prec_g) clear_slot(g);
     for (void* p : H.allocs) cudaFree(p);
     H = Hier<T>();
 }
@@ -164,9 +177,9 @@ struct gp_ctx {
     int band_first = -1, band_nd = 0, band_nz = 0, band_first_interior = 0;
     bool split_ok = false;
     // FGMRES storage (split with accel): V[0..m] FP64, Z[0..m-1] and vT in the working precision
-    std::vector<double*> kV;
+    std::vector<void*> kV;
     std::vector<void*> kZ;
-    void* kvT = nullptr;
+    void* ekry = nullptr;          // inner FGMRES solution (working precision, full box)
     double* kY = nullptr;
     int k_m = 0;
     int k_bytes = 0;
@@ -416,23 +429,18 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
     c->stats.vcycles++;
 }
 
-template <typename T>
-void pcg_body(gp_ctx* c, Hier<T>& H, int iters);
-
-// x ~ A^-1 r by `iters` multigrid-preconditioned CG steps from x = 0; r is
-// overwritten. The whole sequence (V-cycles, dot products, updates: no host
-// round trip) is captured once per hierarchy into a CUDA graph and replayed.
-template <typename T>
-void pcg(gp_ctx* c, Hier<T>& H, int iters) {
+// Run `body` (stream work only: no host round trip inside) through a CUDA
+// graph: captured once per key on the library stream, then replayed there,
+// ordered after and before the user's stream by events.
+template <typename F>
+void run_graph(gp_ctx* c, GraphSlot& g, long key, F&& body) {
     if (!c->use_graphs) {
-        pcg_body(c, H, iters);
+        body();
         return;
     }
-    const long key = ((long)iters << 20) | ((long)c->prm.nu1 << 12) | ((long)c->prm.nu2 << 4) | (c->prm_on_key());
-    if (!H.pcg_exec || H.pcg_key != key) {
-        if (H.pcg_exec) { cudaGraphExecDestroy(H.pcg_exec); H.pcg_exec = nullptr; }
-        for (cudaEvent_t e : H.pcg_ev) cudaEventDestroy(e);
-        H.pcg_ev.clear(); H.pcg_kinds.clear(); H.pcg_nlaunch.clear();
+    key = key * 2 + (c->prof_on ? 1 : 0);
+    if (!g.exec || g.key != key) {
+        clear_slot(g);
         cudaStream_t user = c->s;
         c->s = c->gs;
         const long l0 = g_launches.load();
@@ -444,57 +452,75 @@ void pcg(gp_ctx* c, Hier<T>& H, int iters) {
         if (e1 == cudaSuccess) {
             c->capturing = true;
             try {
-                pcg_body(c, H, iters);
+                body();
             } catch (...) {
                 c->capturing = false;
                 cudaStreamEndCapture(c->gs, &graph);
                 if (graph) cudaGraphDestroy(graph);
                 c->s = user;
+                c->pending.swap(saved);
                 throw;
             }
             c->capturing = false;
             e1 = cudaStreamEndCapture(c->gs, &graph);
         }
         c->s = user;
-        if (e1 != cudaSuccess) throw Err{GP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1)};
-        cudaError_t e2 = cudaGraphInstantiate(&H.pcg_exec, graph, 0);
+        if (e1 != cudaSuccess) {
+            c->pending.swap(saved);
+            throw Err{GP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1)};
+        }
+        cudaError_t e2 = cudaGraphInstantiate(&g.exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e2 != cudaSuccess) throw Err{GP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2)};
-        H.pcg_launches = g_launches.load() - l0;
-        H.pcg_vcycles = c->stats.vcycles - v0;
-        H.pcg_inner = c->stats.inner_iterations - i0;
+        if (e2 != cudaSuccess) {
+            c->pending.swap(saved);
+            throw Err{GP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2)};
+        }
+        g.launches = g_launches.load() - l0;
+        g.vcycles = c->stats.vcycles - v0;
+        g.inner = c->stats.inner_iterations - i0;
         c->stats.vcycles = v0;
         c->stats.inner_iterations = i0;
-        g_launches.fetch_sub(H.pcg_launches);
+        g_launches.fetch_sub(g.launches);
         for (auto& p : c->pending) {
-            H.pcg_kinds.push_back(p.kind);
-            H.pcg_nlaunch.push_back(p.launches);
-            H.pcg_ev.push_back(p.a);
-            H.pcg_ev.push_back(p.b);
+            g.kinds.push_back(p.kind);
+            g.nlaunch.push_back(p.launches);
+            g.ev.push_back(p.a);
+            g.ev.push_back(p.b);
         }
         c->pending.swap(saved);
-        H.pcg_key = key;
+        g.key = key;
     }
     GP_CUDA(cudaEventRecord(c->ev_in, c->s));
     GP_CUDA(cudaStreamWaitEvent(c->gs, c->ev_in, 0));
-    GP_CUDA(cudaGraphLaunch(H.pcg_exec, c->gs));
+    GP_CUDA(cudaGraphLaunch(g.exec, c->gs));
     GP_CUDA(cudaEventRecord(c->ev_out, c->gs));
     GP_CUDA(cudaStreamWaitEvent(c->s, c->ev_out, 0));
-    count_launch(H.pcg_launches);
-    c->stats.vcycles += H.pcg_vcycles;
-    c->stats.inner_iterations += H.pcg_inner;
-    if (c->prof_on) {
-        // the graph's event pairs hold this replay's times until the next replay;
-        // every caller synchronises (and collects) before replaying again
+    count_launch(g.launches);
+    c->stats.vcycles += g.vcycles;
+    c->stats.inner_iterations += g.inner;
+    if (c->prof_on && !g.kinds.empty()) {
+        // the graph's event pairs hold this replay's times until the next replay
         GP_CUDA(cudaStreamSynchronize(c->s));
-        for (size_t k = 0; k < H.pcg_kinds.size(); ++k) {
+        for (size_t k = 0; k < g.kinds.size(); ++k) {
             float ms = 0.f;
-            GP_CUDA(cudaEventElapsedTime(&ms, H.pcg_ev[2 * k], H.pcg_ev[2 * k + 1]));
-            c->prof_ms[H.pcg_kinds[k]] += ms;
-            c->prof_launches[H.pcg_kinds[k]] += H.pcg_nlaunch[k];
-            c->prof_groups[H.pcg_kinds[k]] += 1;
+            GP_CUDA(cudaEventElapsedTime(&ms, g.ev[2 * k], g.ev[2 * k + 1]));
+            c->prof_ms[g.kinds[k]] += ms;
+            c->prof_launches[g.kinds[k]] += g.nlaunch[k];
+            c->prof_groups[g.kinds[k]] += 1;
         }
     }
+}
+
+template <typename T>
+void pcg_body(gp_ctx* c, Hier<T>& H, int iters);
+
+// x ~ A^-1 r by `iters` multigrid-preconditioned CG steps from x = 0; r is
+// overwritten. The whole sequence (V-cycles, dot products, updates: no host
+// round trip) is one CUDA graph per hierarchy.
+template <typename T>
+void pcg(gp_ctx* c, Hier<T>& H, int iters) {
+    const long key = ((long)iters << 16) | ((long)c->prm.nu1 << 8) | (long)c->prm.nu2;
+    run_graph(c, H.pcg_g, key, [&] { pcg_body(c, H, iters); });
 }
 
 template <typename T>
@@ -610,6 +636,7 @@ void setup_solver(gp_ctx* c) {
             coarse_coeffs<T>(c, B);
             if (!c->rfull) c->rfull = dalloc(c, (size_t)c->n * sizeof(double));
             if (!c->evac) c->evac = dalloc(c, (size_t)c->n * sizeof(double));
+            if (!c->ekry) c->ekry = dalloc(c, (size_t)c->n * sizeof(double));
             if (!c->fft) {
                 c->fft = fft_create(c->g, c->s);
                 if (!c->fft) throw Err{GP_ERR_INVALID_ARG, "grid extents must be 2^a 3^b for the FFT"};
@@ -628,32 +655,32 @@ void setup_solver(gp_ctx* c) {
 template <typename T>
 void ensure_krylov(gp_ctx* c, int m) {
     if (c->k_m >= m && c->k_bytes == (int)sizeof(T)) return;
-    for (double* v : c->kV) cudaFree(v);
+    for (void* v : c->kV) cudaFree(v);
     for (void* z : c->kZ) cudaFree(z);
-    if (c->kvT) cudaFree(c->kvT);
-    if (c->kY) cudaFree(c->kY);
-    c->kV.clear(); c->kZ.clear(); c->kvT = nullptr; c->kY = nullptr; c->k_m = 0;
+    c->kV.clear(); c->kZ.clear(); c->k_m = 0;
+    for (GraphSlot& g : band_hier<T>(c).prec_g) clear_slot(g);   // they bake the old pointers
     for (int j = 0; j <= m; ++j) {
         void* p = nullptr;
-        if (cudaMalloc(&p, sizeof(double) * c->n) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
-        c->kV.push_back((double*)p);
+        if (cudaMalloc(&p, sizeof(T) * c->n) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+        c->kV.push_back(p);
     }
     for (int j = 0; j < m; ++j) {
         void* p = nullptr;
         if (cudaMalloc(&p, sizeof(T) * c->n) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
         c->kZ.push_back(p);
     }
-    if (cudaMalloc(&c->kvT, sizeof(T) * c->n) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
-    if (cudaMalloc(&c->kY, sizeof(double) * kMaxKrylov) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+    if (!c->kY && cudaMalloc(&c->kY, sizeof(double) * kMaxKrylov) != cudaSuccess)
+        throw Err{GP_ERR_OOM, "cudaMalloc failed"};
     c->k_m = m;
     c->k_bytes = (int)sizeof(T);
 }
 
 // z = M v: the dry/wet split applied to a residual-like vector v (in T):
-// z = L^-1 v on the whole box (FFT), plus the band correction solving
-// A e = v - A L^-1 v on the wet band with e = 0 on the Dirichlet planes.
+// z = L^-1 v on the whole box (FFT, Eq. 15), plus the band correction for
+// A e = v - A L^-1 v on the wet band with e = 0 on the Dirichlet planes
+// (band_vcycles V-cycles from zero: a fixed linear map, as FGMRES prefers).
 template <typename T>
-void split_precondition(gp_ctx* c, const T* v, T* z) {
+void split_precondition_body(gp_ctx* c, const T* v, T* z) {
     Hier<T>& B = band_hier<T>(c);
     T* ev = reinterpret_cast<T*>(c->evac);
     {
@@ -664,105 +691,112 @@ void split_precondition(gp_ctx* c, const T* v, T* z) {
         ProfScope ps(c, GP_PROF_MG_FINE, 1);
         launch_band_rhs<T>(c->g, eps_T<T>(c), v, ev, c->band_first_interior, c->band_nz, B.r, c->s);
     }
-    GP_CHECK_LAUNCH();
-    pcg<T>(c, B, c->prm.inner);
-    if (z) {
-        ProfScope ps(c, GP_PROF_MG_FINE, 1);
-        launch_combine<T>(c->g, ev, B.x, c->band_first_interior, c->band_nz, z, c->s);
+    vcycle(c, B, B.x, B.r);
+    for (int it = 1; it < c->prm.band_vcycles; ++it) {
+        {
+            ProfScope ps(c, GP_PROF_MG_FINE, 1);
+            launch_residual<T>(B.lv[0], B.x, B.r, B.q, c->s);
+        }
+        vcycle(c, B, B.z, B.q);
+        ProfScope ps(c, GP_PROF_KRYLOV, 1);
+        launch_axpy1<T>(B.lv[0], B.x, B.z, c->s);
     }
+    ProfScope ps(c, GP_PROF_MG_FINE, 1);
+    launch_combine<T>(c->g, ev, B.x, c->band_first_interior, c->band_nz, z, c->s);
     GP_CHECK_LAUNCH();
 }
 
-// FP64 flexible GMRES(m) on A phi = b, right-preconditioned by the split.
 template <typename T>
-gp_status fgmres_split(gp_ctx* c, const double* rho, double* phi, double tol, double nb) {
-    const int m = c->prm.restart;
+void split_precondition(gp_ctx* c, int j, const T* v, T* z) {
+    Hier<T>& B = band_hier<T>(c);
+    if ((int)B.prec_g.size() <= j) B.prec_g.resize(j + 1);
+    const long key = ((long)c->prm.band_vcycles << 16) | ((long)c->prm.nu1 << 8) | (long)c->prm.nu2;
+    run_graph(c, B.prec_g[j], key, [&] { split_precondition_body<T>(c, v, z); });
+}
+
+// Right-preconditioned flexible GMRES(m) in the working precision T on
+// A x = rhs over the whole box (periodic operator of the finest level),
+// preconditioned by the split. Stops when the Givens estimate of the
+// residual drops below rel_tol |rhs|, after m steps, or on breakdown.
+// x receives the solution (x = 0 start); rhs is not modified.
+template <typename T>
+int fgmres_inner(gp_ctx* c, const T* rhs, T* x, int m, double rel_tol) {
+    Hier<T>& F = full_hier<T>(c);
     ensure_krylov<T>(c, m);
-    gp_stats& st = c->stats;
-    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m), hv(m + 2);
+    const LV<T>& V0 = F.lv[0];
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m), hv(kMaxKrylov + 2);
     auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
-    T* vT = reinterpret_cast<T*>(c->kvT);
-    double best = INFINITY;
-    while (true) {
-        {
-            ProfScope ps(c, GP_PROF_RES64, 1);
-            launch_residual64<double>(c->g, phi, rho, c->eps64, c->kV[0], c->partial, c->s);
-        }
-        GP_CHECK_LAUNCH();
-        double s2[2];
-        sum_host(c, 2, s2);
-        const double beta = std::sqrt(s2[0]);
-        const double rn = beta / nb;
-        st.outer_iterations++;
-        if (st.history_len < GP_HISTORY) st.history[st.history_len++] = rn;
-        st.residual = rn;
-        if (!std::isfinite(rn) || rn > 1e3 * best) return GP_ERR_DIVERGED;
-        best = std::min(best, rn);
-        if (rn <= tol) return GP_OK;
-        if (st.outer_iterations >= c->prm.max_outer) return GP_ERR_NOT_CONVERGED;
-        {
-            ProfScope ps(c, GP_PROF_KRYLOV, 1);
-            launch_scale_by_norm(c->n, c->kV[0], c->scal + 8, c->s);
-        }
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int used = 0;
-        for (int j = 0; j < m; ++j) {
-            T* zj = reinterpret_cast<T*>(c->kZ[j]);
-            {
-                ProfScope ps(c, GP_PROF_KRYLOV, 1);
-                launch_cast_eps<T>(c->n, c->kV[j], vT, c->s);
-            }
-            split_precondition<T>(c, vT, zj);
-            VecList V;
-            V.n = j + 1;
-            for (int i = 0; i <= j; ++i) V.v[i] = c->kV[i];
-            {
-                ProfScope ps(c, GP_PROF_KRYLOV, 6);
-                launch_applyA64<T>(c->g, c->eps64, zj, c->kV[j + 1], c->s);
-                launch_multidot(c->n, c->kV[j + 1], V, c->partial, c->s);
-                launch_finalize(c->partial, kReduceBlocks, j + 1, c->scal + 16, c->s);
-                launch_multiaxpy_norm(c->n, c->kV[j + 1], V, c->scal + 16, c->partial, c->s);
-                launch_finalize(c->partial, kReduceBlocks, 1, c->scal + 15, c->s);
-                launch_scale_by_norm(c->n, c->kV[j + 1], c->scal + 15, c->s);
-            }
-            GP_CHECK_LAUNCH();
-            GP_CUDA(cudaMemcpyAsync(hv.data(), c->scal + 15, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, c->s));
-            GP_CUDA(cudaStreamSynchronize(c->s));
-            for (int i = 0; i <= j; ++i) Hij(i, j) = hv[1 + i];
-            Hij(j + 1, j) = std::sqrt(hv[0]);
-            for (int i = 0; i < j; ++i) {
-                const double a = Hij(i, j), b = Hij(i + 1, j);
-                Hij(i, j) = cs[i] * a + sn[i] * b;
-                Hij(i + 1, j) = -sn[i] * a + cs[i] * b;
-            }
-            const double a = Hij(j, j), b = Hij(j + 1, j);
-            const double r = std::hypot(a, b);
-            cs[j] = r > 0 ? a / r : 1.0;
-            sn[j] = r > 0 ? b / r : 0.0;
-            Hij(j, j) = r;
-            Hij(j + 1, j) = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            used = j + 1;
-            st.inner_iterations++;
-            if (std::fabs(g[j + 1]) <= 0.5 * tol * nb || hv[0] <= 0.0) break;
-        }
-        for (int i = used - 1; i >= 0; --i) {
-            double acc = g[i];
-            for (int k = i + 1; k < used; ++k) acc -= Hij(i, k) * y[k];
-            y[i] = acc / Hij(i, i);
-        }
-        GP_CUDA(cudaMemcpyAsync(c->kY, y.data(), sizeof(double) * used, cudaMemcpyHostToDevice, c->s));
-        TVecList<T> Z;
-        Z.n = used;
-        for (int j = 0; j < used; ++j) Z.v[j] = reinterpret_cast<const T*>(c->kZ[j]);
-        {
-            ProfScope ps(c, GP_PROF_UPDATE64, 1);
-            launch_update_krylov<T>(c->n, phi, Z, c->kY, c->s);
-        }
-        GP_CHECK_LAUNCH();
+    auto Vp = [&](int j) { return reinterpret_cast<T*>(c->kV[j]); };
+    auto Zp = [&](int j) { return reinterpret_cast<T*>(c->kZ[j]); };
+    {
+        ProfScope ps(c, GP_PROF_KRYLOV, 3);
+        launch_dot<T>(V0, rhs, rhs, c->partial, c->s);
+        launch_finalize(c->partial, kReduceBlocks, 1, c->scal + 15, c->s);
+        launch_scale_by_norm<T>(c->n, rhs, Vp(0), c->scal + 15, c->s);
     }
+    GP_CHECK_LAUNCH();
+    GP_CUDA(cudaMemcpyAsync(hv.data(), c->scal + 15, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    GP_CUDA(cudaStreamSynchronize(c->s));
+    const double beta = std::sqrt(hv[0]);
+    if (!(beta > 0)) {
+        GP_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * c->n, c->s));
+        return 0;
+    }
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int used = 0;
+    for (int j = 0; j < m; ++j) {
+        split_precondition<T>(c, j, Vp(j), Zp(j));
+        TVecList<T> V;
+        V.n = j + 1;
+        for (int i = 0; i <= j; ++i) V.v[i] = Vp(i);
+        {
+            ProfScope ps(c, GP_PROF_KRYLOV, 6);
+            launch_applyA_dot<T>(V0, Zp(j), Vp(j + 1), c->partial, c->s);
+            launch_multidot<T>(c->n, Vp(j + 1), V, c->partial, c->s);
+            launch_finalize(c->partial, kReduceBlocks, j + 1, c->scal + 16, c->s);
+            launch_multiaxpy_norm<T>(c->n, Vp(j + 1), V, c->scal + 16, c->partial, c->s);
+            launch_finalize(c->partial, kReduceBlocks, 1, c->scal + 15, c->s);
+            launch_scale_by_norm<T>(c->n, Vp(j + 1), Vp(j + 1), c->scal + 15, c->s);
+        }
+        GP_CHECK_LAUNCH();
+        GP_CUDA(cudaMemcpyAsync(hv.data(), c->scal + 15, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        prof_collect(c);
+        for (int i = 0; i <= j; ++i) Hij(i, j) = hv[1 + i];
+        Hij(j + 1, j) = std::sqrt(hv[0]);
+        for (int i = 0; i < j; ++i) {
+            const double a = Hij(i, j), b = Hij(i + 1, j);
+            Hij(i, j) = cs[i] * a + sn[i] * b;
+            Hij(i + 1, j) = -sn[i] * a + cs[i] * b;
+        }
+        const double a = Hij(j, j), b = Hij(j + 1, j);
+        const double r = std::hypot(a, b);
+        cs[j] = r > 0 ? a / r : 1.0;
+        sn[j] = r > 0 ? b / r : 0.0;
+        Hij(j, j) = r;
+        Hij(j + 1, j) = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        used = j + 1;
+        c->stats.inner_iterations++;
+        if (std::fabs(g[j + 1]) <= rel_tol * beta || !(hv[0] > 0.0)) break;
+    }
+    for (int i = used - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int k = i + 1; k < used; ++k) acc -= Hij(i, k) * y[k];
+        y[i] = acc / Hij(i, i);
+    }
+    GP_CUDA(cudaMemcpyAsync(c->kY, y.data(), sizeof(double) * used, cudaMemcpyHostToDevice, c->s));
+    TVecList<T> Z;
+    Z.n = used;
+    for (int j = 0; j < used; ++j) Z.v[j] = Zp(j);
+    {
+        ProfScope ps(c, GP_PROF_KRYLOV, 1);
+        launch_krylov_combine<T>(c->n, x, Z, c->kY, c->s);
+    }
+    GP_CHECK_LAUNCH();
+    return used;
 }
 
 template <typename T>
@@ -798,13 +832,13 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
     T* ev = reinterpret_cast<T*>(c->evac);
     double best = INFINITY;
     gp_status result = GP_ERR_NOT_CONVERGED;
-    if (split && c->prm.accel) {
-        result = fgmres_split<T>(c, rho, phi, tol, nb);
-    } else
+    const bool krylov = split && c->prm.accel;
+    T* ekry = reinterpret_cast<T*>(c->ekry);
     for (int it = 0; it < c->prm.max_outer; ++it) {
         if (it > 0) {
             ProfScope ps(c, GP_PROF_UPDATE64, 1);
-            if (split) launch_update_phi<T>(c->g, phi, ev, B.x, c->band_first_interior, c->band_nz, c->s);
+            if (krylov) launch_update_phi<T>(c->g, phi, ekry, (const T*)nullptr, 0, 0, c->s);
+            else if (split) launch_update_phi<T>(c->g, phi, ev, B.x, c->band_first_interior, c->band_nz, c->s);
             else launch_update_phi<T>(c->g, phi, F.x, (const T*)nullptr, 0, 0, c->s);
             GP_CHECK_LAUNCH();
         }
@@ -823,7 +857,12 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         best = std::min(best, rn);
         if (rn <= tol) { result = GP_OK; break; }
         if (it == c->prm.max_outer - 1) break;
-        if (split) {
+        if (krylov) {
+            // FP32 (or FP64) flexible GMRES on the correction equation A e = r,
+            // preconditioned by the dry/wet split; the FP64 outer loop couples
+            // the two regions through the full-box residual
+            fgmres_inner<T>(c, rT, ekry, c->prm.restart, sizeof(T) == 4 ? 1e-4 : 1e-7);
+        } else if (split) {
             {
                 ProfScope ps(c, GP_PROF_FFT, 5);
                 fft_poisson<T>(c->fft, rT, ev, c->fft_work, c->s);
@@ -884,7 +923,8 @@ void gp_default_params(gp_params* p) {
     p->inner = 4;
     p->max_outer = 60;
     p->accel = 1;
-    p->restart = 10;
+    p->restart = 12;
+    p->band_vcycles = 1;
 }
 
 gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out) {
@@ -936,6 +976,7 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             throw Err{GP_ERR_INVALID_ARG, "need nu1+nu2 >= 1, inner >= 1, max_outer >= 1"};
         if (p.accel && (p.restart < 1 || p.restart > kMaxKrylov - 1))
             throw Err{GP_ERR_INVALID_ARG, "restart must be in 1..15"};
+        if (p.band_vcycles < 1) throw Err{GP_ERR_INVALID_ARG, "band_vcycles must be >= 1"};
         std::string why;
         const int L = plan_levels(c->g.nx, c->g.ny, c->g.nz, 1, p.levels, why);
         if (L < 2) throw Err{GP_ERR_INVALID_ARG, why.empty() ? "grid too small for multigrid" : why};
@@ -1242,9 +1283,8 @@ void gp_destroy(gp_ctx* c) {
     free_hier(c->fullD);
     free_hier(c->bandD);
     if (c->fft) fft_destroy(c->fft);
-    for (double* v : c->kV) cudaFree(v);
+    for (void* v : c->kV) cudaFree(v);
     for (void* z : c->kZ) cudaFree(z);
-    if (c->kvT) cudaFree(c->kvT);
     if (c->kY) cudaFree(c->kY);
     for (auto& p : c->pending) { c->event_pool.push_back(p.a); c->event_pool.push_back(p.b); }
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);

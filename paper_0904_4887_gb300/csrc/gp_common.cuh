@@ -109,18 +109,17 @@ template <typename T> void launch_band_eps(const Geo& g, const T* epsT, int firs
 template <typename T> void launch_band_rhs(const Geo& g, const T* epsT, const T* r, const T* evac,
                                            int first_interior, int band_nz, T* fband, cudaStream_t s);
 
-// FGMRES outer Krylov (k_mg.cu)
+// FGMRES inner Krylov (k_mg.cu)
 constexpr int kMaxKrylov = 16;
-struct VecList { const double* v[kMaxKrylov + 1]; int n; };
 template <typename T> struct TVecList { const T* v[kMaxKrylov]; int n; };
-template <typename T> void launch_applyA64(const Geo& g, const double* eps, const T* z, double* w, cudaStream_t s);
-void launch_multidot(long n, const double* w, const VecList& V, double* partial, cudaStream_t s);
-void launch_multiaxpy_norm(long n, double* w, const VecList& V, const double* h, double* partial, cudaStream_t s);
-void launch_scale_by_norm(long n, double* v, const double* sq, cudaStream_t s);
+template <typename T> void launch_multidot(long n, const T* w, const TVecList<T>& V, double* partial, cudaStream_t s);
+template <typename T> void launch_multiaxpy_norm(long n, T* w, const TVecList<T>& V, const double* h, double* partial,
+                                                 cudaStream_t s);
+template <typename T> void launch_scale_by_norm(long n, const T* src, T* dst, const double* sq, cudaStream_t s);
 template <typename T> void launch_combine(const Geo& g, const T* ev, const T* eb, int first, int band_nz, T* z,
                                           cudaStream_t s);
-template <typename T> void launch_update_krylov(long n, double* x, const TVecList<T>& Z, const double* y,
-                                                cudaStream_t s);
+template <typename T> void launch_krylov_combine(long n, T* x, const TVecList<T>& Z, const double* y, cudaStream_t s);
+template <typename T> void launch_axpy1(const LV<T>& L, T* x, const T* y, cudaStream_t s);
 
 // FFT (k_fft.cu)
 struct FFTPlan;

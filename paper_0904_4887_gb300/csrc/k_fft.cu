@@ -280,16 +280,24 @@ void run_fft_poisson(FFTPlan* p, const T* src, T* out, void* work, cudaStream_t 
     const int by = ((nxh + my - 1) / my) * g.nz;
     const int bz = ((nxh + mz - 1) / mz) * g.ny;
     const size_t sx = smem_bytes(g.nx, mx, cs), sy = smem_bytes(g.ny, my, cs), sz = smem_bytes(g.nz, mz, cs);
-    cudaFuncSetAttribute(k_fft_x_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
-    cudaFuncSetAttribute(k_fft_x_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
-    cudaFuncSetAttribute(k_fft_y<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy);
-    cudaFuncSetAttribute(k_fft_y<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy);
-    cudaFuncSetAttribute(k_fft_z_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
     k_fft_x_fwd<T><<<bx, 256, sx, s>>>(g, p->ax[0], twx, mx, src, C);
     k_fft_y<T, false><<<by, 256, sy, s>>>(g, p->ax[1], twy, my, C);
     k_fft_z_solve<T><<<bz, 256, sz, s>>>(g, p->ax[2], twz, mz, p->lam[0], p->lam[1], p->lam[2], C);
     k_fft_y<T, true><<<by, 256, sy, s>>>(g, p->ax[1], twy, my, C);
     k_fft_x_inv<T><<<bx, 256, sx, s>>>(g, p->ax[0], twx, mx, C, out);
+}
+
+// allow the dynamic shared memory of every pass (done once, before any capture)
+template <typename T>
+void set_fft_attributes(const Geo& g) {
+    const size_t cs = sizeof(Cx<T>);
+    const int mx = lines_per_cta(g.nx, cs), my = lines_per_cta(g.ny, cs), mz = lines_per_cta(g.nz, cs);
+    const size_t sx = smem_bytes(g.nx, mx, cs), sy = smem_bytes(g.ny, my, cs), sz = smem_bytes(g.nz, mz, cs);
+    cudaFuncSetAttribute(k_fft_x_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
+    cudaFuncSetAttribute(k_fft_x_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
+    cudaFuncSetAttribute(k_fft_y<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy);
+    cudaFuncSetAttribute(k_fft_y<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy);
+    cudaFuncSetAttribute(k_fft_z_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
 }
 
 }  // namespace
@@ -312,6 +320,8 @@ FFTPlan* fft_create(const Geo& g, cudaStream_t s) {
         k_twiddles<<<(n[a] + 127) / 128, 128, 0, s>>>(n[a], p->tw64[a], p->tw32[a]);
         k_symbol<<<(n[a] + 127) / 128, 128, 0, s>>>(n[a], h[a], p->lam[a]);
     }
+    set_fft_attributes<float>(g);
+    set_fft_attributes<double>(g);
     return p;
 }
 

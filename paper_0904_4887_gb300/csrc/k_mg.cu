@@ -535,32 +535,16 @@ __global__ void k_band_rhs(Geo g, const T* eps, const T* r, const T* ev, int fir
     }
 }
 
-// ------------------------------------------------------------ FGMRES (FP64 outer Krylov)
-// w = A z with the FP64 operator (cell eps, periodic) applied to a T vector
+// ------------------------------------------------------------ FGMRES (inner, working precision)
+// partial[b * nv + i] = block b's share of w . v_i (accumulated in FP64)
 template <typename T>
-__global__ void k_applyA64(Geo g, const double* eps, const T* z, double* w) {
-    const long n = (long)g.nx * g.ny * g.nz;
-    const double hx = 0.5 / (g.hx * g.hx), hy = 0.5 / (g.hy * g.hy), hz = 0.5 / (g.hz * g.hz);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        split3(t, g.nx, g.ny, i, j, k);
-        const Nb nb = neighbours(g.nx, g.ny, g.nz, 1, i, j, k);
-        const double e0 = eps[nb.c], p0 = (double)z[nb.c];
-        const double ax = (e0 + eps[nb.xp]) * ((double)z[nb.xp] - p0) - (e0 + eps[nb.xm]) * (p0 - (double)z[nb.xm]);
-        const double ay = (e0 + eps[nb.yp]) * ((double)z[nb.yp] - p0) - (e0 + eps[nb.ym]) * (p0 - (double)z[nb.ym]);
-        const double az = (e0 + eps[nb.zp]) * ((double)z[nb.zp] - p0) - (e0 + eps[nb.zm]) * (p0 - (double)z[nb.zm]);
-        w[t] = hx * ax + hy * ay + hz * az;
-    }
-}
-
-// partial[b * nv + i] = block b's share of w . v_i
-__global__ void __launch_bounds__(kReduceThreads) k_multidot(long n, const double* w, VecList V, double* partial) {
+__global__ void __launch_bounds__(kReduceThreads) k_multidot(long n, const T* w, TVecList<T> V, double* partial) {
     __shared__ double red[32];
-    double loc[kMaxKrylov + 1];
+    double loc[kMaxKrylov];
     for (int i = 0; i < V.n; ++i) loc[i] = 0.0;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        const double wv = w[t];
-        for (int i = 0; i < V.n; ++i) loc[i] += wv * V.v[i][t];
+        const double wv = (double)w[t];
+        for (int i = 0; i < V.n; ++i) loc[i] += wv * (double)V.v[i][t];
     }
     for (int i = 0; i < V.n; ++i) {
         const double s = block_sum(loc[i], red);
@@ -569,27 +553,30 @@ __global__ void __launch_bounds__(kReduceThreads) k_multidot(long n, const doubl
 }
 
 // w -= sum_i h[i] v_i; partial[b] = block share of |w|^2
-__global__ void __launch_bounds__(kReduceThreads) k_multiaxpy_norm(long n, double* w, VecList V, const double* h,
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads) k_multiaxpy_norm(long n, T* w, TVecList<T> V, const double* h,
                                                                    double* partial) {
     __shared__ double red[32];
-    __shared__ double hs[kMaxKrylov + 1];
+    __shared__ double hs[kMaxKrylov];
     if (threadIdx.x < V.n) hs[threadIdx.x] = h[threadIdx.x];
     __syncthreads();
     double loc = 0.0;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        double x = w[t];
-        for (int i = 0; i < V.n; ++i) x -= hs[i] * V.v[i][t];
-        w[t] = x;
+        double x = (double)w[t];
+        for (int i = 0; i < V.n; ++i) x -= hs[i] * (double)V.v[i][t];
+        w[t] = (T)x;
         loc += x * x;
     }
     const double s = block_sum(loc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// v = w / sqrt(*sq)
-__global__ void k_scale_by_norm(long n, double* v, const double* sq) {
+// dst = src / sqrt(*sq)
+template <typename T>
+__global__ void k_scale_by_norm(long n, const T* src, T* dst, const double* sq) {
     const double f = 1.0 / sqrt(sq[0]);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) v[t] *= f;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        dst[t] = (T)((double)src[t] * f);
 }
 
 // z = e_vac, plus the band correction on the band planes
@@ -607,50 +594,59 @@ __global__ void k_combine(Geo g, const T* ev, const T* eb, int first, int band_n
     }
 }
 
-// x += sum_j y[j] z_j (z in T, x and y FP64)
+// x = sum_j y[j] z_j
 template <typename T>
-__global__ void k_update_krylov(long n, double* x, TVecList<T> Z, const double* y) {
+__global__ void k_krylov_combine(long n, T* x, TVecList<T> Z, const double* y) {
     __shared__ double ys[kMaxKrylov];
     if (threadIdx.x < Z.n) ys[threadIdx.x] = y[threadIdx.x];
     __syncthreads();
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        double acc = x[t];
+        double acc = 0.0;
         for (int j = 0; j < Z.n; ++j) acc += ys[j] * (double)Z.v[j][t];
-        x[t] = acc;
+        x[t] = (T)acc;
     }
+}
+
+// x += y
+template <typename T>
+__global__ void k_axpy1(long n, T* x, const T* y) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) x[t] += y[t];
 }
 
 }  // namespace
 
 // ------------------------------------------------------------ launchers
-template <typename T> void launch_applyA64(const Geo& g, const double* eps, const T* z, double* w, cudaStream_t s) {
-    const long n = (long)g.nx * g.ny * g.nz;
-    k_applyA64<T><<<grid_for(n, 256), 256, 0, s>>>(g, eps, z, w);
+template <typename T> void launch_multidot(long n, const T* w, const TVecList<T>& V, double* partial, cudaStream_t s) {
+    k_multidot<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, w, V, partial);
 }
-void launch_multidot(long n, const double* w, const VecList& V, double* partial, cudaStream_t s) {
-    k_multidot<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, w, V, partial);
+template <typename T> void launch_multiaxpy_norm(long n, T* w, const TVecList<T>& V, const double* h, double* partial,
+                                                 cudaStream_t s) {
+    k_multiaxpy_norm<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, w, V, h, partial);
 }
-void launch_multiaxpy_norm(long n, double* w, const VecList& V, const double* h, double* partial, cudaStream_t s) {
-    k_multiaxpy_norm<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, w, V, h, partial);
-}
-void launch_scale_by_norm(long n, double* v, const double* sq, cudaStream_t s) {
-    k_scale_by_norm<<<grid_for(n, 256), 256, 0, s>>>(n, v, sq);
+template <typename T> void launch_scale_by_norm(long n, const T* src, T* dst, const double* sq, cudaStream_t s) {
+    k_scale_by_norm<T><<<grid_for(n, 256), 256, 0, s>>>(n, src, dst, sq);
 }
 template <typename T> void launch_combine(const Geo& g, const T* ev, const T* eb, int first, int band_nz, T* z,
                                           cudaStream_t s) {
     const long n = (long)g.nx * g.ny * g.nz;
     k_combine<T><<<grid_for(n, 256), 256, 0, s>>>(g, ev, eb, first, band_nz, z);
 }
-template <typename T> void launch_update_krylov(long n, double* x, const TVecList<T>& Z, const double* y,
-                                                cudaStream_t s) {
-    k_update_krylov<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, Z, y);
+template <typename T> void launch_krylov_combine(long n, T* x, const TVecList<T>& Z, const double* y, cudaStream_t s) {
+    k_krylov_combine<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, Z, y);
 }
-template void launch_applyA64<float>(const Geo&, const double*, const float*, double*, cudaStream_t);
-template void launch_applyA64<double>(const Geo&, const double*, const double*, double*, cudaStream_t);
-template void launch_combine<float>(const Geo&, const float*, const float*, int, int, float*, cudaStream_t);
-template void launch_combine<double>(const Geo&, const double*, const double*, int, int, double*, cudaStream_t);
-template void launch_update_krylov<float>(long, double*, const TVecList<float>&, const double*, cudaStream_t);
-template void launch_update_krylov<double>(long, double*, const TVecList<double>&, const double*, cudaStream_t);
+template <typename T> void launch_axpy1(const LV<T>& L, T* x, const T* y, cudaStream_t s) {
+    const long n = (long)L.nx * L.ny * L.nz;
+    k_axpy1<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, y);
+}
+#define GP_KINST(T)                                                                                          \
+    template void launch_multidot<T>(long, const T*, const TVecList<T>&, double*, cudaStream_t);             \
+    template void launch_multiaxpy_norm<T>(long, T*, const TVecList<T>&, const double*, double*, cudaStream_t); \
+    template void launch_scale_by_norm<T>(long, const T*, T*, const double*, cudaStream_t);                  \
+    template void launch_combine<T>(const Geo&, const T*, const T*, int, int, T*, cudaStream_t);            \
+    template void launch_krylov_combine<T>(long, T*, const TVecList<T>&, const double*, cudaStream_t);       \
+    template void launch_axpy1<T>(const LV<T>&, T*, const T*, cudaStream_t);
+GP_KINST(float)
+GP_KINST(double)
 void launch_finalize(const double* partial, int nparts, int ncomp, double* out, cudaStream_t s) {
     k_finalize<<<1, 1024, 0, s>>>(partial, nparts, ncomp, out);
 }

@@ -32,7 +32,8 @@ class gp_params(ctypes.Structure):
                 ("rcut", ctypes.c_double), ("dry_thresh", ctypes.c_double), ("split", ctypes.c_int),
                 ("n_dirichlet", ctypes.c_int), ("precision", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("levels", ctypes.c_int), ("inner", ctypes.c_int),
-                ("max_outer", ctypes.c_int), ("accel", ctypes.c_int), ("restart", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("accel", ctypes.c_int), ("restart", ctypes.c_int),
+                ("band_vcycles", ctypes.c_int)]
 
 
 class gp_stats(ctypes.Structure):
