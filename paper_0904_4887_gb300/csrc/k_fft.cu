@@ -264,6 +264,260 @@ int lines_per_cta(int n, size_t csize) {
 
 size_t smem_bytes(int n, int m, size_t csize) { return (size_t)n * csize * (1 + 2 * (size_t)m); }
 
+// ---------------------------------------------------------------------------
+// Compile-time sizes: with N, M and the radix sequence known to the compiler,
+// every index division in the Stockham stages becomes a shift or a multiply.
+__host__ __device__ constexpr int st_count(int n) {
+    int s = 0;
+    while (n % 4 == 0) { n /= 4; ++s; }
+    while (n % 2 == 0) { n /= 2; ++s; }
+    while (n % 3 == 0) { n /= 3; ++s; }
+    return s;
+}
+__host__ __device__ constexpr int st_radix(int n, int st) {
+    int s = 0;
+    while (n % 4 == 0) { if (s == st) return 4; n /= 4; ++s; }
+    while (n % 2 == 0) { if (s == st) return 2; n /= 2; ++s; }
+    while (n % 3 == 0) { if (s == st) return 3; n /= 3; ++s; }
+    return 1;
+}
+__host__ __device__ constexpr int st_before(int n, int st) {
+    int p = 1;
+    for (int i = 0; i < st; ++i) p *= st_radix(n, i);
+    return p;
+}
+
+template <typename T, int N, int M, bool INV, int ST>
+__device__ __forceinline__ Cx<T>* sstage(Cx<T>* A, Cx<T>* B, const Cx<T>* tw) {
+    if constexpr (ST >= st_count(N)) {
+        return A;
+    } else {
+        constexpr int R = st_radix(N, ST), Ns = st_before(N, ST), NR = N / R, tstep = N / (Ns * R);
+        for (int b = threadIdx.x; b < M * NR; b += blockDim.x) {
+            const int l = b % M, j = b / M;
+            const int kk = j % Ns;
+            Cx<T> v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                Cx<T> x = A[(j + r * NR) * M + l];
+                if (r > 0 && kk > 0) {
+                    Cx<T> w = tw[r * kk * tstep];
+                    if (INV) w.im = -w.im;
+                    x = cmul(x, w);
+                }
+                v[r] = x;
+            }
+            Cx<T> o[R];
+            if constexpr (R == 2) {
+                o[0] = cadd(v[0], v[1]);
+                o[1] = csub(v[0], v[1]);
+            } else if constexpr (R == 4) {
+                const Cx<T> a = cadd(v[0], v[2]), bb = csub(v[0], v[2]);
+                const Cx<T> c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+                const Cx<T> mid = INV ? Cx<T>{-d.im, d.re} : Cx<T>{d.im, -d.re};
+                o[0] = cadd(a, c);
+                o[2] = csub(a, c);
+                o[1] = cadd(bb, mid);
+                o[3] = csub(bb, mid);
+            } else {
+                const T c3 = (T)-0.5;
+                const T s3 = INV ? (T)0.86602540378443864676 : (T)-0.86602540378443864676;
+                const Cx<T> t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+                const Cx<T> m = {v[0].re + c3 * t.re, v[0].im + c3 * t.im};
+                const Cx<T> rot = {-s3 * d.im, s3 * d.re};
+                o[0] = cadd(v[0], t);
+                o[1] = cadd(m, rot);
+                o[2] = csub(m, rot);
+            }
+            const int base = (j / Ns) * Ns * R + kk;
+#pragma unroll
+            for (int r = 0; r < R; ++r) B[(base + r * Ns) * M + l] = o[r];
+        }
+        __syncthreads();
+        return sstage<T, N, M, INV, ST + 1>(B, A, tw);
+    }
+}
+
+template <typename T, int N>
+constexpr int lines_static() {
+    int m = 16;
+    while (m > 1 && 2 * N * m * (int)sizeof(Cx<T>) > 96 * 1024) m >>= 1;
+    return m;
+}
+
+template <typename T, int N, int M>
+__global__ void __launch_bounds__(256) ks_x_fwd(Geo g, const T* tw, const T* src, Cx<T>* C) {
+    extern __shared__ unsigned char smem_raw[];
+    Cx<T>* sw = reinterpret_cast<Cx<T>*>(smem_raw);
+    constexpr int nxh = N / 2 + 1;
+    Cx<T>* A = sw + N;
+    Cx<T>* B = A + N * M;
+    load_tw(sw, tw, N);
+    const long rows = (long)g.ny * g.nz;
+    const long row0 = (long)blockIdx.x * M;
+    for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
+        const int l = q / N, e = q % N;
+        const long row = row0 + l;
+        A[e * M + l] = Cx<T>{row < rows ? src[row * N + e] : (T)0, (T)0};
+    }
+    __syncthreads();
+    Cx<T>* R = sstage<T, N, M, false, 0>(A, B, sw);
+    for (int q = threadIdx.x; q < M * nxh; q += blockDim.x) {
+        const int l = q / nxh, e = q % nxh;
+        const long row = row0 + l;
+        if (row < rows) C[row * nxh + e] = R[e * M + l];
+    }
+}
+
+template <typename T, int N, int M>
+__global__ void __launch_bounds__(256) ks_x_inv(Geo g, const T* tw, const Cx<T>* C, T* out) {
+    extern __shared__ unsigned char smem_raw[];
+    Cx<T>* sw = reinterpret_cast<Cx<T>*>(smem_raw);
+    constexpr int nxh = N / 2 + 1;
+    Cx<T>* A = sw + N;
+    Cx<T>* B = A + N * M;
+    load_tw(sw, tw, N);
+    const long rows = (long)g.ny * g.nz;
+    const long row0 = (long)blockIdx.x * M;
+    for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
+        const int l = q / N, e = q % N;
+        const long row = row0 + l;
+        Cx<T> v = {(T)0, (T)0};
+        if (row < rows) {
+            if (e < nxh) v = C[row * nxh + e];
+            else { v = C[row * nxh + (N - e)]; v.im = -v.im; }
+        }
+        A[e * M + l] = v;
+    }
+    __syncthreads();
+    Cx<T>* R = sstage<T, N, M, true, 0>(A, B, sw);
+    for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
+        const int l = q / N, e = q % N;
+        const long row = row0 + l;
+        if (row < rows) out[row * N + e] = R[e * M + l].re;
+    }
+}
+
+template <typename T, int N, int M, bool INV>
+__global__ void __launch_bounds__(256) ks_y(Geo g, const T* tw, Cx<T>* C) {
+    extern __shared__ unsigned char smem_raw[];
+    Cx<T>* sw = reinterpret_cast<Cx<T>*>(smem_raw);
+    const int nxh = g.nx / 2 + 1;
+    Cx<T>* A = sw + N;
+    Cx<T>* B = A + N * M;
+    load_tw(sw, tw, N);
+    const int nchunks = (nxh + M - 1) / M;
+    const int kx0 = (blockIdx.x % nchunks) * M;
+    const long k = blockIdx.x / nchunks;
+    Cx<T>* base = C + k * (long)nxh * N;
+    for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
+        const int e = q / M, l = q % M;
+        A[e * M + l] = (kx0 + l < nxh) ? base[(long)e * nxh + kx0 + l] : Cx<T>{(T)0, (T)0};
+    }
+    __syncthreads();
+    Cx<T>* R = sstage<T, N, M, INV, 0>(A, B, sw);
+    for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
+        const int e = q / M, l = q % M;
+        if (kx0 + l < nxh) base[(long)e * nxh + kx0 + l] = R[e * M + l];
+    }
+}
+
+template <typename T, int N, int M>
+__global__ void __launch_bounds__(256) ks_z_solve(Geo g, const T* tw, const double* lx, const double* ly,
+                                                  const double* lz, Cx<T>* C) {
+    extern __shared__ unsigned char smem_raw[];
+    Cx<T>* sw = reinterpret_cast<Cx<T>*>(smem_raw);
+    const int nxh = g.nx / 2 + 1;
+    Cx<T>* A = sw + N;
+    Cx<T>* B = A + N * M;
+    load_tw(sw, tw, N);
+    const int nchunks = (nxh + M - 1) / M;
+    const int kx0 = (blockIdx.x % nchunks) * M;
+    const int ky = blockIdx.x / nchunks;
+    const long zs = (long)nxh * g.ny;
+    Cx<T>* base = C + (long)ky * nxh;
+    for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
+        const int e = q / M, l = q % M;
+        A[e * M + l] = (kx0 + l < nxh) ? base[e * zs + kx0 + l] : Cx<T>{(T)0, (T)0};
+    }
+    __syncthreads();
+    Cx<T>* R = sstage<T, N, M, false, 0>(A, B, sw);
+    Cx<T>* O = (R == A) ? B : A;
+    const double inv_n = 1.0 / ((double)g.nx * g.ny * g.nz);
+    for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
+        const int e = q / M, l = q % M;
+        const int kx = kx0 + l;
+        Cx<T> v = R[e * M + l];
+        if (kx < nxh) {
+            const double lam = lx[kx] + ly[ky] + lz[e];
+            const T f = (kx == 0 && ky == 0 && e == 0) ? (T)0 : (T)(inv_n / lam);
+            v.re *= f; v.im *= f;
+        } else {
+            v = Cx<T>{(T)0, (T)0};
+        }
+        R[e * M + l] = v;
+    }
+    __syncthreads();
+    Cx<T>* R2 = sstage<T, N, M, true, 0>(R, O, sw);
+    for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
+        const int e = q / M, l = q % M;
+        if (kx0 + l < nxh) base[e * zs + kx0 + l] = R2[e * M + l];
+    }
+}
+
+template <typename T, int N>
+constexpr size_t smem_static() { return (size_t)N * sizeof(Cx<T>) * (1 + 2 * (size_t)lines_static<T, N>()); }
+
+// one pass of axis `axis` (0 x-forward, 1 y-forward, 2 z-solve, 3 y-inverse, 4 x-inverse) with N
+// known at compile time; returns false if N has no static instance
+template <typename T, int N>
+void static_pass(int pass, FFTPlan* p, const T* tw, const T* src, T* out, Cx<T>* C, cudaStream_t s, bool attr) {
+    constexpr int M = lines_static<T, N>();
+    constexpr size_t sm = smem_static<T, N>();
+    const Geo& g = p->g;
+    const int nxh = g.nx / 2 + 1;
+    if (attr) {
+        switch (pass) {
+            case 0: cudaFuncSetAttribute(ks_x_fwd<T, N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+            case 1: cudaFuncSetAttribute(ks_y<T, N, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+            case 2: cudaFuncSetAttribute(ks_z_solve<T, N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+            case 3: cudaFuncSetAttribute(ks_y<T, N, M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+            case 4: cudaFuncSetAttribute(ks_x_inv<T, N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+        }
+        return;
+    }
+    const long rows = (long)g.ny * g.nz;
+    switch (pass) {
+        case 0: ks_x_fwd<T, N, M><<<(int)((rows + M - 1) / M), 256, sm, s>>>(g, tw, src, C); break;
+        case 1: ks_y<T, N, M, false><<<((nxh + M - 1) / M) * g.nz, 256, sm, s>>>(g, tw, C); break;
+        case 2: ks_z_solve<T, N, M><<<((nxh + M - 1) / M) * g.ny, 256, sm, s>>>(g, tw, p->lam[0], p->lam[1],
+                                                                                  p->lam[2], C); break;
+        case 3: ks_y<T, N, M, true><<<((nxh + M - 1) / M) * g.nz, 256, sm, s>>>(g, tw, C); break;
+        case 4: ks_x_inv<T, N, M><<<(int)((rows + M - 1) / M), 256, sm, s>>>(g, tw, C, out); break;
+    }
+}
+
+template <typename T>
+bool dispatch_pass(int n, int pass, FFTPlan* p, const T* tw, const T* src, T* out, Cx<T>* C, cudaStream_t s,
+                   bool attr) {
+    switch (n) {
+        case 8: static_pass<T, 8>(pass, p, tw, src, out, C, s, attr); return true;
+        case 12: static_pass<T, 12>(pass, p, tw, src, out, C, s, attr); return true;
+        case 16: static_pass<T, 16>(pass, p, tw, src, out, C, s, attr); return true;
+        case 24: static_pass<T, 24>(pass, p, tw, src, out, C, s, attr); return true;
+        case 32: static_pass<T, 32>(pass, p, tw, src, out, C, s, attr); return true;
+        case 48: static_pass<T, 48>(pass, p, tw, src, out, C, s, attr); return true;
+        case 64: static_pass<T, 64>(pass, p, tw, src, out, C, s, attr); return true;
+        case 96: static_pass<T, 96>(pass, p, tw, src, out, C, s, attr); return true;
+        case 128: static_pass<T, 128>(pass, p, tw, src, out, C, s, attr); return true;
+        case 192: static_pass<T, 192>(pass, p, tw, src, out, C, s, attr); return true;
+        case 256: static_pass<T, 256>(pass, p, tw, src, out, C, s, attr); return true;
+        case 384: static_pass<T, 384>(pass, p, tw, src, out, C, s, attr); return true;
+        case 512: static_pass<T, 512>(pass, p, tw, src, out, C, s, attr); return true;
+        default: return false;
+    }
+}
+
 template <typename T>
 void run_fft_poisson(FFTPlan* p, const T* src, T* out, void* work, cudaStream_t s) {
     const Geo& g = p->g;
@@ -280,11 +534,17 @@ void run_fft_poisson(FFTPlan* p, const T* src, T* out, void* work, cudaStream_t 
     const int by = ((nxh + my - 1) / my) * g.nz;
     const int bz = ((nxh + mz - 1) / mz) * g.ny;
     const size_t sx = smem_bytes(g.nx, mx, cs), sy = smem_bytes(g.ny, my, cs), sz = smem_bytes(g.nz, mz, cs);
-    k_fft_x_fwd<T><<<bx, 256, sx, s>>>(g, p->ax[0], twx, mx, src, C);
-    k_fft_y<T, false><<<by, 256, sy, s>>>(g, p->ax[1], twy, my, C);
-    k_fft_z_solve<T><<<bz, 256, sz, s>>>(g, p->ax[2], twz, mz, p->lam[0], p->lam[1], p->lam[2], C);
-    k_fft_y<T, true><<<by, 256, sy, s>>>(g, p->ax[1], twy, my, C);
-    k_fft_x_inv<T><<<bx, 256, sx, s>>>(g, p->ax[0], twx, mx, C, out);
+    // each pass: the compile-time-size kernel when there is one, else the generic one
+    if (!dispatch_pass<T>(g.nx, 0, p, twx, src, out, C, s, false))
+        k_fft_x_fwd<T><<<bx, 256, sx, s>>>(g, p->ax[0], twx, mx, src, C);
+    if (!dispatch_pass<T>(g.ny, 1, p, twy, src, out, C, s, false))
+        k_fft_y<T, false><<<by, 256, sy, s>>>(g, p->ax[1], twy, my, C);
+    if (!dispatch_pass<T>(g.nz, 2, p, twz, src, out, C, s, false))
+        k_fft_z_solve<T><<<bz, 256, sz, s>>>(g, p->ax[2], twz, mz, p->lam[0], p->lam[1], p->lam[2], C);
+    if (!dispatch_pass<T>(g.ny, 3, p, twy, src, out, C, s, false))
+        k_fft_y<T, true><<<by, 256, sy, s>>>(g, p->ax[1], twy, my, C);
+    if (!dispatch_pass<T>(g.nx, 4, p, twx, src, out, C, s, false))
+        k_fft_x_inv<T><<<bx, 256, sx, s>>>(g, p->ax[0], twx, mx, C, out);
 }
 
 // allow the dynamic shared memory of every pass (done once, before any capture)
@@ -298,6 +558,9 @@ void set_fft_attributes(const Geo& g) {
     cudaFuncSetAttribute(k_fft_y<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy);
     cudaFuncSetAttribute(k_fft_y<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy);
     cudaFuncSetAttribute(k_fft_z_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
+    const int ns[5] = {g.nx, g.ny, g.nz, g.ny, g.nx};
+    for (int pass = 0; pass < 5; ++pass)
+        dispatch_pass<T>(ns[pass], pass, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, true);
 }
 
 }  // namespace
