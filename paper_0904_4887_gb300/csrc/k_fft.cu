@@ -474,8 +474,6 @@ template <typename T, int N>
 void static_pass(int pass, FFTPlan* p, const T* tw, const T* src, T* out, Cx<T>* C, cudaStream_t s, bool attr) {
     constexpr int M = lines_static<T, N>();
     constexpr size_t sm = smem_static<T, N>();
-    const Geo& g = p->g;
-    const int nxh = g.nx / 2 + 1;
     if (attr) {
         switch (pass) {
             case 0: cudaFuncSetAttribute(ks_x_fwd<T, N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
@@ -486,6 +484,8 @@ void static_pass(int pass, FFTPlan* p, const T* tw, const T* src, T* out, Cx<T>*
         }
         return;
     }
+    const Geo& g = p->g;
+    const int nxh = g.nx / 2 + 1;
     const long rows = (long)g.ny * g.nz;
     switch (pass) {
         case 0: ks_x_fwd<T, N, M><<<(int)((rows + M - 1) / M), 256, sm, s>>>(g, tw, src, C); break;
