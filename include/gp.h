@@ -77,7 +77,7 @@ typedef struct {
                              working precision, preconditioned by the split (same fixed point);
                              0 = plain self-consistent coupling iteration */
     int restart;          /* split with accel: GMRES steps per outer correction (12, <= 15) */
-    int band_vcycles;     /* split: V-cycles on the wet band per application of the split (1) */
+    int band_vcycles;     /* split: V-cycles on the wet band per application of the split (2) */
 } gp_params;
 
 #define GP_HISTORY 64

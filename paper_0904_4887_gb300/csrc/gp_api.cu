@@ -931,7 +931,7 @@ void gp_default_params(gp_params* p) {
     p->max_outer = 60;
     p->accel = 1;
     p->restart = 12;
-    p->band_vcycles = 1;
+    p->band_vcycles = 2;
 }
 
 gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out) {
