@@ -296,6 +296,62 @@ def gpu_arm(args, rank, world):
     return line
 
 
+# ----------------------------------------------------------------------------- MD frames
+def md_arm(args, rank, world):
+    """Consecutive MD frames (seeded 300 K Maxwell velocities, dt 0.5 fs): each
+    frame rebuilds eps and rho, solves warm-started from the previous phi with
+    `graph_outer` corrections captured as one CUDA graph, then energy + forces.
+    Reports frames/s and per-frame p50 / p99 latency (CUDA events)."""
+    import torch
+    import paper_0904_4887_gb300 as P
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.WORKLOADS["md_128x128x256"]
+    frames = args.frames
+    at, traj, gauss_np = make_inputs(w, frames + args.warmup, seed=rank)
+    gauss = torch.tensor(gauss_np, dtype=torch.float64, device=dev)
+    pos = [torch.tensor(traj[i], dtype=torch.float64, device=dev) for i in range(frames + args.warmup)]
+    s = P.GPSolver(w.grid, w.cell, precision=args.precision, split=args.split, graph_outer=args.graph_outer)
+    rho, phi = s.zeros(), s.zeros()
+    F = torch.zeros((len(at.Z), 3), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def frame(p):
+        s.set_atoms(p)
+        s.build_rho(p, gauss, out=rho)
+        st = s.ctx.gp_solve(rho, phi, args.tol, check=False)
+        if st != 0:
+            raise RuntimeError("frame solve failed with status %d" % st)
+        s.ctx.gp_energy_forces(phi, rho, gauss, F)
+
+    for i in range(args.warmup):
+        frame(pos[i])
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(frames + 1)]
+    outer = []
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(frames):
+        frame(pos[args.warmup + i])
+        evs[i + 1].record(stream)
+        outer.append(s.stats().outer_iterations)
+    torch.cuda.synchronize()
+    lat = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(frames)])
+    total = evs[0].elapsed_time(evs[frames])
+    if rank != 0:
+        return None
+    return {"metric": "MD frames/s (warm-started graph-captured solve + forces)", "value": frames / (total / 1e3),
+            "unit": "frames/s", "n_gpus": world, "steps": frames, "warmup": args.warmup,
+            "ms_per_step": total / frames, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/f64" if args.precision == 1 else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.grid), "cell_A": list(w.cell), "atoms": int(len(at.Z)),
+                       "tol": args.tol, "graph_outer": args.graph_outer, "split": bool(args.split),
+                       "outer_iterations_mean": float(np.mean(outer))},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())}}
+
+
 # ----------------------------------------------------------------------------- oracle (CPU) arm
 def oracle_sample(w, at, pos, budget_s=20.0):
     """Time the FP64 oracle on bounded samples of the workload and scale to one
@@ -374,6 +430,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--mode", default="step", choices=["step", "md"])
+    ap.add_argument("--frames", type=int, default=100)
+    ap.add_argument("--graph-outer", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gp":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -385,7 +444,12 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    line = reference_arm(args, rank, world) if args.impl == "reference" else gpu_arm(args, rank, world)
+    if args.impl == "reference":
+        line = reference_arm(args, rank, world)
+    elif args.mode == "md":
+        line = md_arm(args, rank, world)
+    else:
+        line = gpu_arm(args, rank, world)
     if line is not None:
         print(json.dumps(line))
     if world > 1 and args.impl == "gp":

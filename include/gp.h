@@ -78,6 +78,10 @@ typedef struct {
                              0 = plain self-consistent coupling iteration */
     int restart;          /* split with accel: GMRES steps per outer correction (12, <= 15) */
     int band_vcycles;     /* split: V-cycles on the wet band per application of the split (2) */
+    int graph_outer;      /* full box: if > 0, run this many outer corrections as one captured CUDA
+                             graph (no host round trip), check the residual once, and continue with
+                             the checked loop only if it is not yet below tol (warm-started frames);
+                             the graph is kept for the same rho/phi buffers (0 = off, <= 16) */
 } gp_params;
 
 #define GP_HISTORY 64
@@ -95,6 +99,8 @@ typedef struct {
     double residual;            /* final ||b - A phi|| / ||b|| (FP64) */
     int history_len;
     double history[GP_HISTORY]; /* relative residual after each outer step */
+    int sweep_shape;            /* finest-level smoother tile chosen by the autotuner:
+                                   0: 64x8, 1: 32x16, 2: 128x4, 3: 32x8 points (x, y) */
 } gp_stats;
 
 /* Fill *p with the defaults listed beside each field. */

@@ -81,7 +81,8 @@ template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int col
 // one fused red-black sweep of a cell-eps level: u_new from u_old, colour `first` updated first (k_smooth.cu)
 void rb_sweep_init();
 template <typename T> void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first,
-                                           cudaStream_t s);
+                                           cudaStream_t s, int shape);
+template <typename T> int rb_sweep_autotune(const LV<T>& L, const T* u_old, const T* f, T* u_new, cudaStream_t s);
 template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* f, T* r, cudaStream_t s);
 template <typename T> void launch_restrict(const LV<T>& F, const T* r, const LV<T>& C, T* fc, cudaStream_t s);
 template <typename T> void launch_prolong_add(const LV<T>& F, T* u, const LV<T>& C, const T* uc, cudaStream_t s);

@@ -21,15 +21,14 @@
 namespace gp {
 namespace {
 
-constexpr int SX = 64, SY = 8;                    // output tile per CTA (x, y); z chunk set at launch
-constexpr int HX = SX + 4, HY = SY + 4;           // with a 2-point halo
-constexpr int HP = HX * HY;
 constexpr int NT = 256;
 
 constexpr int NRING = 6;                          // planes q-3 .. q+1 resident, q+2 in flight
 
-template <typename T>
+// output tile SX x SY per CTA (z chunk set at launch) with a 2-point x-y halo
+template <typename T, int SX, int SY>
 struct __align__(16) Ring {
+    static constexpr int HX = SX + 4, HY = SY + 4, HP = HX * HY;
     T u[NRING][HP];
     T e[NRING][HP];
     T f[NRING][HP];
@@ -48,11 +47,13 @@ __device__ __forceinline__ void cp_async_pair(double* smem_dst, const double* gs
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
-template <typename T>
+template <typename T, int SX, int SY>
 __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ u_old, const T* __restrict__ f,
                                                  T* __restrict__ u_new, int first, int sz) {
     extern __shared__ unsigned char smem_raw[];
-    Ring<T>& R = *reinterpret_cast<Ring<T>*>(smem_raw);
+    using RingT = Ring<T, SX, SY>;
+    constexpr int HX = RingT::HX, HP = RingT::HP;
+    RingT& R = *reinterpret_cast<RingT*>(smem_raw);
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const long pl = (long)nx * ny;
     const int i0 = blockIdx.x * SX, j0 = blockIdx.y * SY;
@@ -161,32 +162,87 @@ __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ 
     }
 }
 
-}  // namespace
+// tile shapes the autotuner chooses from (x, y)
+#define GP_SWEEP_SHAPES(X) X(0, 64, 8) X(1, 32, 16) X(2, 128, 4) X(3, 32, 8)
+constexpr int kSweepShapes = 4;
 
-template <typename T>
-size_t rb_sweep_smem() { return sizeof(Ring<T>); }
-
-// allow the dynamic shared memory of the sweep (called before any capture)
-void rb_sweep_init() {
-    cudaFuncSetAttribute(k_rb_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Ring<float>));
-    cudaFuncSetAttribute(k_rb_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Ring<double>));
-}
-
-template <typename T>
-void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s) {
-    const size_t sm = sizeof(Ring<T>);
-    // z chunk: about one wave of resident CTAs (3 per SM fit the shared memory)
+template <typename T, int SX, int SY>
+void sweep_shape(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s, bool attr) {
+    const size_t sm = sizeof(Ring<T, SX, SY>);
+    if (attr) {
+        cudaFuncSetAttribute(k_rb_sweep<T, SX, SY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        return;
+    }
+    // z chunk: about one wave of resident CTAs
+    int per_sm = (int)((220 * 1024) / sm);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
     const int txy = ((L.nx + SX - 1) / SX) * ((L.ny + SY - 1) / SY);
-    const int target = 152 * (sizeof(T) == 4 ? 3 : 1);
-    int chunks = (target + txy - 1) / txy;
+    int chunks = (152 * per_sm + txy - 1) / txy;
     if (chunks > L.nz) chunks = L.nz;
     if (chunks < 1) chunks = 1;
     const int sz = (L.nz + chunks - 1) / chunks;
     dim3 grid((L.nx + SX - 1) / SX, (L.ny + SY - 1) / SY, (L.nz + sz - 1) / sz);
-    k_rb_sweep<T><<<grid, NT, sm, s>>>(L, u_old, f, u_new, first, sz);
+    k_rb_sweep<T, SX, SY><<<grid, NT, sm, s>>>(L, u_old, f, u_new, first, sz);
 }
 
-template void launch_rb_sweep<float>(const LV<float>&, const float*, const float*, float*, int, cudaStream_t);
-template void launch_rb_sweep<double>(const LV<double>&, const double*, const double*, double*, int, cudaStream_t);
+template <typename T>
+void sweep_dispatch(int shape, const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s,
+                    bool attr) {
+    switch (shape) {
+#define GP_CASE(I, X, Y) \
+    case I: sweep_shape<T, X, Y>(L, u_old, f, u_new, first, s, attr); break;
+        GP_SWEEP_SHAPES(GP_CASE)
+#undef GP_CASE
+        default: sweep_shape<T, 64, 8>(L, u_old, f, u_new, first, s, attr); break;
+    }
+}
+
+}  // namespace
+
+// allow the dynamic shared memory of every sweep shape (called before any capture)
+void rb_sweep_init() {
+    for (int k = 0; k < kSweepShapes; ++k) {
+        LV<float> lf{};
+        LV<double> ld{};
+        sweep_dispatch<float>(k, lf, nullptr, nullptr, nullptr, 0, nullptr, true);
+        sweep_dispatch<double>(k, ld, nullptr, nullptr, nullptr, 0, nullptr, true);
+    }
+}
+
+template <typename T>
+void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s, int shape) {
+    sweep_dispatch<T>(shape, L, u_old, f, u_new, first, s, false);
+}
+
+// Time every tile shape on this level (three sweeps each, CUDA events on the
+// given stream, inputs as they are) and return the fastest. Uses u_new as
+// scratch output; run outside any stream capture.
+template <typename T>
+int rb_sweep_autotune(const LV<T>& L, const T* u_old, const T* f, T* u_new, cudaStream_t s) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return 0;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 0; }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int k = 0; k < kSweepShapes; ++k) {
+        sweep_dispatch<T>(k, L, u_old, f, u_new, 0, s, false);     // warm-up
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 3; ++r) sweep_dispatch<T>(k, L, u_old, f, u_new, 0, s, false);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) { best_ms = ms; best = k; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+template void launch_rb_sweep<float>(const LV<float>&, const float*, const float*, float*, int, cudaStream_t, int);
+template void launch_rb_sweep<double>(const LV<double>&, const double*, const double*, double*, int, cudaStream_t, int);
+template int rb_sweep_autotune<float>(const LV<float>&, const float*, const float*, float*, cudaStream_t);
+template int rb_sweep_autotune<double>(const LV<double>&, const double*, const double*, double*, cudaStream_t);
 
 }  // namespace gp

@@ -33,7 +33,7 @@ class gp_params(ctypes.Structure):
                 ("n_dirichlet", ctypes.c_int), ("precision", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("levels", ctypes.c_int), ("inner", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("accel", ctypes.c_int), ("restart", ctypes.c_int),
-                ("band_vcycles", ctypes.c_int)]
+                ("band_vcycles", ctypes.c_int), ("graph_outer", ctypes.c_int)]
 
 
 class gp_stats(ctypes.Structure):
@@ -41,7 +41,8 @@ class gp_stats(ctypes.Structure):
                 ("vcycles", ctypes.c_int), ("levels", ctypes.c_int), ("split_active", ctypes.c_int),
                 ("band_first", ctypes.c_int), ("band_dirichlet", ctypes.c_int), ("dry_planes", ctypes.c_int),
                 ("wet_fraction", ctypes.c_double), ("b_norm", ctypes.c_double), ("residual", ctypes.c_double),
-                ("history_len", ctypes.c_int), ("history", ctypes.c_double * GP_HISTORY)]
+                ("history_len", ctypes.c_int), ("history", ctypes.c_double * GP_HISTORY),
+                ("sweep_shape", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

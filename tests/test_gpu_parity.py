@@ -266,3 +266,26 @@ def test_error_paths():
     assert torch.count_nonzero(z) == 0
     with pytest.raises(GPError):
         GPSolver((10, 16, 16), cell)                # 10 is not 2^a 3^b
+
+
+def test_graph_captured_warm_start_frames():
+    """Consecutive frames warm-started from the previous phi with the fixed-count
+    graph-captured solve reach the tolerance and agree with the oracle."""
+    GPSolver = _gpu()
+    grid, cell = (32, 32, 64), (10.0, 10.0, 20.0)
+    at = W.slab_atoms(cell, 2, 3, seed=0)
+    traj = W.md_frames(at, cell, 4, dt_fs=0.5, temperature=300.0, seed=0)
+    gauss = _t(_gauss(at))
+    s = GPSolver(grid, cell, precision=1, graph_outer=2)
+    phi = s.zeros()
+    for f in range(4):
+        pos = _t(traj[f])
+        s.set_atoms(pos)
+        rho = s.build_rho(pos, gauss)
+        s.solve(rho, phi, tol=1e-10)
+        assert s.stats().residual <= 1e-10
+    h = O.spacing(grid, cell)
+    eps = O.dielectric(grid, cell, traj[3])
+    rho_o = O.charge_density(grid, cell, traj[3], at.Z, at.sigma_core, at.sigma_cloud)
+    ref, _ = O.solve(rho_o, eps, h, tol=1e-14)
+    assert _rel(phi.cpu().numpy(), ref) < 1e-7
