@@ -536,34 +536,40 @@ __global__ void k_band_rhs(Geo g, const T* eps, const T* r, const T* ev, int fir
 }
 
 // ------------------------------------------------------------ FGMRES (inner, working precision)
-// partial[b * nv + i] = block b's share of w . v_i (accumulated in FP64)
-template <typename T>
-__global__ void __launch_bounds__(kReduceThreads) k_multidot(long n, const T* w, TVecList<T> V, double* partial) {
+// partial[b * nv + i] = block b's share of w . v_i (accumulated in FP64).
+// The vector count is a template argument so the accumulators stay in registers.
+template <typename T, int NV>
+__global__ void __launch_bounds__(kReduceThreads) k_multidot(long n, const T* __restrict__ w, TVecList<T> V,
+                                                             double* partial) {
     __shared__ double red[32];
-    double loc[kMaxKrylov];
-    for (int i = 0; i < V.n; ++i) loc[i] = 0.0;
+    double loc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) loc[i] = 0.0;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         const double wv = (double)w[t];
-        for (int i = 0; i < V.n; ++i) loc[i] += wv * (double)V.v[i][t];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) loc[i] += wv * (double)V.v[i][t];
     }
-    for (int i = 0; i < V.n; ++i) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
         const double s = block_sum(loc[i], red);
-        if (threadIdx.x == 0) partial[(long)blockIdx.x * V.n + i] = s;
+        if (threadIdx.x == 0) partial[(long)blockIdx.x * NV + i] = s;
     }
 }
 
 // w -= sum_i h[i] v_i; partial[b] = block share of |w|^2
-template <typename T>
-__global__ void __launch_bounds__(kReduceThreads) k_multiaxpy_norm(long n, T* w, TVecList<T> V, const double* h,
-                                                                   double* partial) {
+template <typename T, int NV>
+__global__ void __launch_bounds__(kReduceThreads) k_multiaxpy_norm(long n, T* __restrict__ w, TVecList<T> V,
+                                                                   const double* h, double* partial) {
     __shared__ double red[32];
-    __shared__ double hs[kMaxKrylov];
-    if (threadIdx.x < V.n) hs[threadIdx.x] = h[threadIdx.x];
-    __syncthreads();
+    double hs[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) hs[i] = h[i];
     double loc = 0.0;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         double x = (double)w[t];
-        for (int i = 0; i < V.n; ++i) x -= hs[i] * (double)V.v[i][t];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) x -= hs[i] * (double)V.v[i][t];
         w[t] = (T)x;
         loc += x * x;
     }
@@ -616,12 +622,23 @@ __global__ void k_axpy1(long n, T* x, const T* y) {
 }  // namespace
 
 // ------------------------------------------------------------ launchers
+#define GP_NV_SWITCH(X)                                                                                  \
+    switch (V.n) {                                                                                       \
+        case 1: X(1); break; case 2: X(2); break; case 3: X(3); break; case 4: X(4); break;              \
+        case 5: X(5); break; case 6: X(6); break; case 7: X(7); break; case 8: X(8); break;              \
+        case 9: X(9); break; case 10: X(10); break; case 11: X(11); break; case 12: X(12); break;        \
+        case 13: X(13); break; case 14: X(14); break; case 15: X(15); break; default: X(16); break;      \
+    }
 template <typename T> void launch_multidot(long n, const T* w, const TVecList<T>& V, double* partial, cudaStream_t s) {
-    k_multidot<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, w, V, partial);
+#define GP_MD(N) k_multidot<T, N><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, w, V, partial)
+    GP_NV_SWITCH(GP_MD)
+#undef GP_MD
 }
 template <typename T> void launch_multiaxpy_norm(long n, T* w, const TVecList<T>& V, const double* h, double* partial,
                                                  cudaStream_t s) {
-    k_multiaxpy_norm<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, w, V, h, partial);
+#define GP_MA(N) k_multiaxpy_norm<T, N><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, w, V, h, partial)
+    GP_NV_SWITCH(GP_MA)
+#undef GP_MA
 }
 template <typename T> void launch_scale_by_norm(long n, const T* src, T* dst, const double* sq, cudaStream_t s) {
     k_scale_by_norm<T><<<grid_for(n, 256), 256, 0, s>>>(n, src, dst, sq);
