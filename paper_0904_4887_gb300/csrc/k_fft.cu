@@ -40,6 +40,7 @@ struct FFTPlan {
     double* tw64[3];      // W_N^t = exp(-2 pi i t / N), t < N, as (re, im)
     float* tw32[3];
     double* lam[3];       // 1D symbol per axis
+    float* lam32[3];      // the same in FP32
 };
 
 namespace {
@@ -65,10 +66,11 @@ __global__ void k_twiddles(int n, double* tw64, float* tw32) {
     }
 }
 
-__global__ void k_symbol(int n, double h, double* lam) {
+__global__ void k_symbol(int n, double h, double* lam, float* lam32) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const double s = sinpi((double)t / n);
         lam[t] = -4.0 * s * s / (h * h);
+        lam32[t] = (float)lam[t];
     }
 }
 
@@ -423,8 +425,8 @@ __global__ void __launch_bounds__(256) ks_y(Geo g, const T* tw, Cx<T>* C) {
 }
 
 template <typename T, int N, int M>
-__global__ void __launch_bounds__(256) ks_z_solve(Geo g, const T* tw, const double* lx, const double* ly,
-                                                  const double* lz, Cx<T>* C) {
+__global__ void __launch_bounds__(256) ks_z_solve(Geo g, const T* tw, const T* lx, const T* ly, const T* lz,
+                                                  Cx<T>* C) {
     extern __shared__ unsigned char smem_raw[];
     Cx<T>* sw = reinterpret_cast<Cx<T>*>(smem_raw);
     const int nxh = g.nx / 2 + 1;
@@ -443,14 +445,16 @@ __global__ void __launch_bounds__(256) ks_z_solve(Geo g, const T* tw, const doub
     __syncthreads();
     Cx<T>* R = sstage<T, N, M, false, 0>(A, B, sw);
     Cx<T>* O = (R == A) ? B : A;
-    const double inv_n = 1.0 / ((double)g.nx * g.ny * g.nz);
+    // symbol in the working precision: 1/(lambda N) (no FP64 per element for FP32)
+    const T inv_n = (T)(1.0 / ((double)g.nx * g.ny * g.nz));
+    const T lyv = ly[ky];
     for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
         const int e = q / M, l = q % M;
         const int kx = kx0 + l;
         Cx<T> v = R[e * M + l];
         if (kx < nxh) {
-            const double lam = lx[kx] + ly[ky] + lz[e];
-            const T f = (kx == 0 && ky == 0 && e == 0) ? (T)0 : (T)(inv_n / lam);
+            const T lam = (lx[kx] + lyv + lz[e]) / inv_n;
+            const T f = (kx == 0 && ky == 0 && e == 0) ? (T)0 : (T)1 / lam;
             v.re *= f; v.im *= f;
         } else {
             v = Cx<T>{(T)0, (T)0};
@@ -490,8 +494,13 @@ void static_pass(int pass, FFTPlan* p, const T* tw, const T* src, T* out, Cx<T>*
     switch (pass) {
         case 0: ks_x_fwd<T, N, M><<<(int)((rows + M - 1) / M), 256, sm, s>>>(g, tw, src, C); break;
         case 1: ks_y<T, N, M, false><<<((nxh + M - 1) / M) * g.nz, 256, sm, s>>>(g, tw, C); break;
-        case 2: ks_z_solve<T, N, M><<<((nxh + M - 1) / M) * g.ny, 256, sm, s>>>(g, tw, p->lam[0], p->lam[1],
-                                                                                  p->lam[2], C); break;
+        case 2: {
+            const T* l0 = sizeof(T) == 8 ? (const T*)p->lam[0] : (const T*)p->lam32[0];
+            const T* l1 = sizeof(T) == 8 ? (const T*)p->lam[1] : (const T*)p->lam32[1];
+            const T* l2 = sizeof(T) == 8 ? (const T*)p->lam[2] : (const T*)p->lam32[2];
+            ks_z_solve<T, N, M><<<((nxh + M - 1) / M) * g.ny, 256, sm, s>>>(g, tw, l0, l1, l2, C);
+            break;
+        }
         case 3: ks_y<T, N, M, true><<<((nxh + M - 1) / M) * g.nz, 256, sm, s>>>(g, tw, C); break;
         case 4: ks_x_inv<T, N, M><<<(int)((rows + M - 1) / M), 256, sm, s>>>(g, tw, C, out); break;
     }
@@ -573,15 +582,16 @@ FFTPlan* fft_create(const Geo& g, cudaStream_t s) {
     for (int a = 0; a < 3; ++a) {
         p->ax[a] = make_axis(n[a]);
         if (p->ax[a].nstages < 0) { delete p; return nullptr; }
-        p->tw64[a] = nullptr; p->tw32[a] = nullptr; p->lam[a] = nullptr;
+        p->tw64[a] = nullptr; p->tw32[a] = nullptr; p->lam[a] = nullptr; p->lam32[a] = nullptr;
         if (cudaMalloc(&p->tw64[a], sizeof(double) * 2 * n[a]) != cudaSuccess ||
             cudaMalloc(&p->tw32[a], sizeof(float) * 2 * n[a]) != cudaSuccess ||
-            cudaMalloc(&p->lam[a], sizeof(double) * n[a]) != cudaSuccess) {
+            cudaMalloc(&p->lam[a], sizeof(double) * n[a]) != cudaSuccess ||
+            cudaMalloc(&p->lam32[a], sizeof(float) * n[a]) != cudaSuccess) {
             fft_destroy(p);
             return nullptr;
         }
         k_twiddles<<<(n[a] + 127) / 128, 128, 0, s>>>(n[a], p->tw64[a], p->tw32[a]);
-        k_symbol<<<(n[a] + 127) / 128, 128, 0, s>>>(n[a], h[a], p->lam[a]);
+        k_symbol<<<(n[a] + 127) / 128, 128, 0, s>>>(n[a], h[a], p->lam[a], p->lam32[a]);
     }
     set_fft_attributes<float>(g);
     set_fft_attributes<double>(g);
@@ -594,6 +604,7 @@ void fft_destroy(FFTPlan* p) {
         if (p->tw64[a]) cudaFree(p->tw64[a]);
         if (p->tw32[a]) cudaFree(p->tw32[a]);
         if (p->lam[a]) cudaFree(p->lam[a]);
+        if (p->lam32[a]) cudaFree(p->lam32[a]);
     }
     delete p;
 }

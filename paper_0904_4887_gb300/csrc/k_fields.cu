@@ -148,6 +148,38 @@ __global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p,
     }
 }
 
+// ----------------------------------------------------------------- df64
+// A value carried as an unevaluated sum hi + lo of two FP32 numbers (about 48
+// significant bits; Dekker 1971, Knuth's two-sum). The per-point sums of the
+// density and its force run in this form: a few FP32 instructions replace an
+// FP64 instruction that costs 64 FP32 issue slots on this GPU.
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df df_from(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df df_quick(float s, float e) {   // |s| >= |e|
+    const float t = s + e;
+    return {t, e - (t - s)};
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_quick(p, e);
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    const float s = a.hi + b.hi;
+    const float v = s - a.hi;
+    float e = (a.hi - (s - v)) + (b.hi - v);
+    e += a.lo + b.lo;
+    return df_quick(s, e);
+}
+
 // ----------------------------------------------------------------- rho
 // Separable Gaussians: g(r) = N exp(-dx^2/2s^2) exp(-dy^2/2s^2) exp(-dz^2/2s^2),
 // each factor zero outside |d| < cut*s. A tile tabulates the three 1D factors
@@ -169,11 +201,12 @@ __device__ __forceinline__ double tile_peak(const Tile& t, const Geo& g, double 
 }
 
 __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, double* rho) {
-    __shared__ double en[RMAX][5];      // cx, cy, cz, sigma, coefficient (FP64 entries from the front,
-                                        //  FP32 entries from the back)
-    __shared__ double gx[RSUB][TX];
+    __shared__ double en[RMAX][5];      // cx, cy, cz, sigma, coefficient (near entries from the front,
+                                        //  FP32 tail entries from the back)
+    __shared__ df gx[RSUB][TX];
     __shared__ double gy[RSUB][TY];
     __shared__ double gz[RSUB][TZ];
+    __shared__ df gyz[RSUB][TY * TZ];
     __shared__ float fx32[RSUB][TX];
     __shared__ float fy32[RSUB][TY];
     __shared__ float fz32[RSUB][TZ];
@@ -182,7 +215,7 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, d
     const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
     const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
     const bool valid = i < g.nx && j < g.ny && k < g.nz;
-    double acc = 0.0;
+    df acc = {0.f, 0.f};
     float acc32 = 0.f;
     for (int a0 = 0; a0 < at.n; a0 += RCH) {
         if (threadIdx.x == 0) { n64 = 0; n32 = 0; }
@@ -216,7 +249,7 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, d
                 const double i2s = 1.0 / (2.0 * E[3] * E[3]);
                 if (r < TX) {
                     const double d = (t.i0 + r) * g.hx - E[0];
-                    gx[e][r] = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
+                    gx[e][r] = df_from((fabs(d) < rad) ? exp(-d * d * i2s) : 0.0);
                 } else if (r < TX + TY) {
                     const int rr = r - TX;
                     const double d = (t.j0 + rr) * g.hy - E[1];
@@ -228,8 +261,13 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, d
                 }
             }
             __syncthreads();
+            for (int q = threadIdx.x; q < ms * TY * TZ; q += TT) {
+                const int e = q / (TY * TZ), r = q % (TY * TZ);
+                gyz[e][r] = df_from(gy[e][r / TZ] * gz[e][r % TZ]);
+            }
+            __syncthreads();
             if (valid) {
-                for (int e = 0; e < ms; ++e) acc = fma(gx[e][tx] * gy[e][ty], gz[e][tz], acc);
+                for (int e = 0; e < ms; ++e) acc = df_add(acc, df_mul(gx[e][tx], gyz[e][ty * TZ + tz]));
             }
             __syncthreads();
         }
@@ -260,7 +298,7 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, d
             __syncthreads();
         }
     }
-    if (valid) rho[i + (long)g.nx * (j + (long)g.ny * k)] = acc + (double)acc32;
+    if (valid) rho[i + (long)g.nx * (j + (long)g.ny * k)] = df_to(acc) + (double)acc32;
 }
 
 // ----------------------------------------------------------------- dry planes
@@ -433,6 +471,10 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = t.i0 + lane;
     const bool lane_ok = i < g.nx;
+    __syncthreads();
+    df phd[TY * TZ];                    // this lane's phi column (16 rows) in df64
+#pragma unroll
+    for (int r = 0; r < TY * TZ; ++r) phd[r] = df_from(ph[lane + TX * r]);
     for (int a0 = 0; a0 < at.n; a0 += RCH) {
         if (threadIdx.x == 0) ne = 0;
         __syncthreads();
@@ -501,20 +543,24 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, 
                 }
                 const double dx = i * g.hx - cx;
                 const double gx = (lane_ok && fabs(dx) < rad) ? exp(-dx * dx * i2s) : 0.0;
-                double s0 = 0.0, sy = 0.0, sz = 0.0;
+                // column sums over the 16 (y, z) rows in df64
+                df s0 = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f};
                 for (int tz = 0; tz < TZ; ++tz) {
                     const double gz = __shfl_sync(0xffffffffu, gyz_v, TY + tz);
                     const double dz = __shfl_sync(0xffffffffu, d_v, TY + tz);
+                    const df gzd = df_from(gz), dzd = df_from(dz);
                     for (int ty = 0; ty < TY; ++ty) {
                         const double gy = __shfl_sync(0xffffffffu, gyz_v, ty);
                         const double dy = __shfl_sync(0xffffffffu, d_v, ty);
-                        const double v = ph[lane + TX * (ty + TY * tz)] * gy * gz;
-                        s0 += v; sy += v * dy; sz += v * dz;
+                        const df v = df_mul(phd[ty + TY * tz], df_mul(df_from(gy), gzd));
+                        s0 = df_add(s0, v);
+                        sy = df_add(sy, df_mul(v, df_from(dy)));
+                        sz = df_add(sz, df_mul(v, dzd));
                     }
                 }
-                fx = coef * dx * gx * s0;
-                fy = coef * gx * sy;
-                fz = coef * gx * sz;
+                fx = coef * dx * gx * df_to(s0);
+                fy = coef * gx * df_to(sy);
+                fz = coef * gx * df_to(sz);
             }
             fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
             if (lane == 0) {

@@ -77,6 +77,12 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;   // valid in thread 0
 }
 
+// per-thread accumulator of the working precision: FP32 data is summed in
+// FP32 within a thread (a few hundred terms) and in FP64 across threads, so
+// no FP64 instruction runs per element (GB300's FP64 rate is 1/64 of FP32)
+template <typename T> struct AccT { using type = double; };
+template <> struct AccT<float> { using type = float; };
+
 int grid_for(long n, int threads) {
     long b = (n + threads - 1) / threads;
     return (int)(b < 152L * 16 ? (b < 1 ? 1 : b) : 152L * 16);
@@ -368,26 +374,26 @@ template <typename T>
 __global__ void k_applyA_dot(LV<T> L, const T* p, T* q, double* partial) {
     __shared__ double red[32];
     const long n = (long)L.nx * L.ny * L.nz;
-    double loc = 0.0;
+    typename AccT<T>::type loc = 0;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         int i, j, k;
         split3(t, L.nx, L.ny, i, j, k);
         const Nb nb = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
         const T v = apply_at(coefs(L, nb), nb, p);
         q[nb.c] = v;
-        loc += (double)p[nb.c] * (double)v;
+        loc += p[nb.c] * v;
     }
-    const double s = block_sum(loc, red);
+    const double s = block_sum((double)loc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
 template <typename T>
 __global__ void k_dot(long n, const T* a, const T* b, double* partial) {
     __shared__ double red[32];
-    double loc = 0.0;
+    typename AccT<T>::type loc = 0;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
-        loc += (double)a[t] * (double)b[t];
-    const double s = block_sum(loc, red);
+        loc += a[t] * b[t];
+    const double s = block_sum((double)loc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
@@ -542,17 +548,18 @@ template <typename T, int NV>
 __global__ void __launch_bounds__(kReduceThreads) k_multidot(long n, const T* __restrict__ w, TVecList<T> V,
                                                              double* partial) {
     __shared__ double red[32];
-    double loc[NV];
+    using A = typename AccT<T>::type;
+    A loc[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) loc[i] = 0.0;
+    for (int i = 0; i < NV; ++i) loc[i] = 0;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        const double wv = (double)w[t];
+        const A wv = w[t];
 #pragma unroll
-        for (int i = 0; i < NV; ++i) loc[i] += wv * (double)V.v[i][t];
+        for (int i = 0; i < NV; ++i) loc[i] += wv * V.v[i][t];
     }
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-        const double s = block_sum(loc[i], red);
+        const double s = block_sum((double)loc[i], red);
         if (threadIdx.x == 0) partial[(long)blockIdx.x * NV + i] = s;
     }
 }
@@ -562,27 +569,28 @@ template <typename T, int NV>
 __global__ void __launch_bounds__(kReduceThreads) k_multiaxpy_norm(long n, T* __restrict__ w, TVecList<T> V,
                                                                    const double* h, double* partial) {
     __shared__ double red[32];
-    double hs[NV];
+    using A = typename AccT<T>::type;
+    A hs[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) hs[i] = h[i];
-    double loc = 0.0;
+    for (int i = 0; i < NV; ++i) hs[i] = (A)h[i];
+    A loc = 0;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        double x = (double)w[t];
+        A x = w[t];
 #pragma unroll
-        for (int i = 0; i < NV; ++i) x -= hs[i] * (double)V.v[i][t];
+        for (int i = 0; i < NV; ++i) x -= hs[i] * V.v[i][t];
         w[t] = (T)x;
         loc += x * x;
     }
-    const double s = block_sum(loc, red);
+    const double s = block_sum((double)loc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
 // dst = src / sqrt(*sq)
 template <typename T>
 __global__ void k_scale_by_norm(long n, const T* src, T* dst, const double* sq) {
-    const double f = 1.0 / sqrt(sq[0]);
+    const T f = (T)(1.0 / sqrt(sq[0]));
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
-        dst[t] = (T)((double)src[t] * f);
+        dst[t] = src[t] * f;
 }
 
 // z = e_vac, plus the band correction on the band planes
@@ -606,9 +614,10 @@ __global__ void k_krylov_combine(long n, T* x, TVecList<T> Z, const double* y) {
     __shared__ double ys[kMaxKrylov];
     if (threadIdx.x < Z.n) ys[threadIdx.x] = y[threadIdx.x];
     __syncthreads();
+    using A = typename AccT<T>::type;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int j = 0; j < Z.n; ++j) acc += ys[j] * (double)Z.v[j][t];
+        A acc = 0;
+        for (int j = 0; j < Z.n; ++j) acc += (A)ys[j] * Z.v[j][t];
         x[t] = (T)acc;
     }
 }
