@@ -471,10 +471,6 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = t.i0 + lane;
     const bool lane_ok = i < g.nx;
-    __syncthreads();
-    df phd[TY * TZ];                    // this lane's phi column (16 rows) in df64
-#pragma unroll
-    for (int r = 0; r < TY * TZ; ++r) phd[r] = df_from(ph[lane + TX * r]);
     for (int a0 = 0; a0 < at.n; a0 += RCH) {
         if (threadIdx.x == 0) ne = 0;
         __syncthreads();
@@ -543,24 +539,20 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, 
                 }
                 const double dx = i * g.hx - cx;
                 const double gx = (lane_ok && fabs(dx) < rad) ? exp(-dx * dx * i2s) : 0.0;
-                // column sums over the 16 (y, z) rows in df64
-                df s0 = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f};
+                double s0 = 0.0, sy = 0.0, sz = 0.0;
                 for (int tz = 0; tz < TZ; ++tz) {
                     const double gz = __shfl_sync(0xffffffffu, gyz_v, TY + tz);
                     const double dz = __shfl_sync(0xffffffffu, d_v, TY + tz);
-                    const df gzd = df_from(gz), dzd = df_from(dz);
                     for (int ty = 0; ty < TY; ++ty) {
                         const double gy = __shfl_sync(0xffffffffu, gyz_v, ty);
                         const double dy = __shfl_sync(0xffffffffu, d_v, ty);
-                        const df v = df_mul(phd[ty + TY * tz], df_mul(df_from(gy), gzd));
-                        s0 = df_add(s0, v);
-                        sy = df_add(sy, df_mul(v, df_from(dy)));
-                        sz = df_add(sz, df_mul(v, dzd));
+                        const double v = ph[lane + TX * (ty + TY * tz)] * gy * gz;
+                        s0 += v; sy += v * dy; sz += v * dz;
                     }
                 }
-                fx = coef * dx * gx * df_to(s0);
-                fy = coef * gx * df_to(sy);
-                fz = coef * gx * df_to(sz);
+                fx = coef * dx * gx * s0;
+                fy = coef * gx * sy;
+                fz = coef * gx * sz;
             }
             fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
             if (lane == 0) {

@@ -83,6 +83,20 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 template <typename T> struct AccT { using type = double; };
 template <> struct AccT<float> { using type = float; };
 
+// compensated running sum (Kahan): the FP32 per-thread partial sums keep
+// about FP64 accuracy at four FP32 instructions per term
+template <typename A>
+struct KSum {
+    A s = 0, c = 0;
+    __device__ __forceinline__ void add(A v) {
+        const A y = v - c;
+        const A t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 int grid_for(long n, int threads) {
     long b = (n + threads - 1) / threads;
     return (int)(b < 152L * 16 ? (b < 1 ? 1 : b) : 152L * 16);
@@ -374,26 +388,26 @@ template <typename T>
 __global__ void k_applyA_dot(LV<T> L, const T* p, T* q, double* partial) {
     __shared__ double red[32];
     const long n = (long)L.nx * L.ny * L.nz;
-    typename AccT<T>::type loc = 0;
+    KSum<typename AccT<T>::type> loc;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         int i, j, k;
         split3(t, L.nx, L.ny, i, j, k);
         const Nb nb = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
         const T v = apply_at(coefs(L, nb), nb, p);
         q[nb.c] = v;
-        loc += p[nb.c] * v;
+        loc.add(p[nb.c] * v);
     }
-    const double s = block_sum((double)loc, red);
+    const double s = block_sum(loc.value(), red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
 template <typename T>
 __global__ void k_dot(long n, const T* a, const T* b, double* partial) {
     __shared__ double red[32];
-    typename AccT<T>::type loc = 0;
+    KSum<typename AccT<T>::type> loc;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
-        loc += a[t] * b[t];
-    const double s = block_sum((double)loc, red);
+        loc.add(a[t] * b[t]);
+    const double s = block_sum(loc.value(), red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
@@ -549,17 +563,15 @@ __global__ void __launch_bounds__(kReduceThreads) k_multidot(long n, const T* __
                                                              double* partial) {
     __shared__ double red[32];
     using A = typename AccT<T>::type;
-    A loc[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) loc[i] = 0;
+    KSum<A> loc[NV];
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         const A wv = w[t];
 #pragma unroll
-        for (int i = 0; i < NV; ++i) loc[i] += wv * V.v[i][t];
+        for (int i = 0; i < NV; ++i) loc[i].add(wv * V.v[i][t]);
     }
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-        const double s = block_sum((double)loc[i], red);
+        const double s = block_sum(loc[i].value(), red);
         if (threadIdx.x == 0) partial[(long)blockIdx.x * NV + i] = s;
     }
 }
@@ -573,15 +585,15 @@ __global__ void __launch_bounds__(kReduceThreads) k_multiaxpy_norm(long n, T* __
     A hs[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) hs[i] = (A)h[i];
-    A loc = 0;
+    KSum<A> loc;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         A x = w[t];
 #pragma unroll
         for (int i = 0; i < NV; ++i) x -= hs[i] * V.v[i][t];
         w[t] = (T)x;
-        loc += x * x;
+        loc.add(x * x);
     }
-    const double s = block_sum((double)loc, red);
+    const double s = block_sum(loc.value(), red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
