@@ -168,6 +168,8 @@ struct gp_ctx {
     double* forces_T = nullptr;
     int forces_cap = 0;
     double* gmat = nullptr;        // Gauss-Jordan workspace (2 * 512^2)
+    double* sw_coef = nullptr;     // switching-function tables (2 * kSwNI * (kSwDeg+1))
+    SwTables sw{};
 
     // solver state
     Hier<float> fullF, bandF;
@@ -1019,6 +1021,7 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
         c->scal = (double*)dalloc(c, sizeof(double) * 64);
         c->dstatus = (int*)dalloc(c, sizeof(int) * 4);
         c->gmat = (double*)dalloc(c, sizeof(double) * 2 * kMaxCoarse * kMaxCoarse);
+        c->sw_coef = (double*)dalloc(c, sizeof(double) * 2 * kSwNI * (kSwDeg + 1));
         rb_sweep_init();
         GP_CUDA(cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking));
         GP_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
@@ -1073,9 +1076,24 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         GP_CHECK_LAUNCH();
         Atoms at{c->atoms, c->atoms32, nullptr, n_atoms};
         DielParams dp{p.eps0, p.r0, p.w, p.rcut};
+        // switching-function tables for these r0, w (when the tabulated range is away from d = 0)
+        SwTables tb{};
+        if (p.r0 - 4.0 * p.w > 0.0 && p.r0 + 6.0 * p.w <= p.rcut) {
+            tb.s = c->sw_coef;
+            tb.h = c->sw_coef + (size_t)kSwNI * (kSwDeg + 1);
+            tb.s_qlo = (p.r0 - 4.0 * p.w) * (p.r0 - 4.0 * p.w);
+            tb.s_qhi = (p.r0 + 6.0 * p.w) * (p.r0 + 6.0 * p.w);
+            tb.s_inv_dq = kSwNI / (tb.s_qhi - tb.s_qlo);
+            tb.h_qlo = (p.r0 - 3.5 * p.w) * (p.r0 - 3.5 * p.w);
+            tb.h_qhi = (p.r0 + 3.5 * p.w) * (p.r0 + 3.5 * p.w);
+            tb.h_inv_dq = kSwNI / (tb.h_qhi - tb.h_qlo);
+            ProfScope ps(c, GP_PROF_EPS, 1);
+            launch_switch_tables(dp, tb, c->sw_coef, c->sw_coef + (size_t)kSwNI * (kSwDeg + 1), c->s);
+        }
+        c->sw = tb;
         {
             ProfScope ps(c, GP_PROF_EPS, 1);
-            launch_build_eps(c->g, at, dp, c->eps64, c->pe64, c->eps32, c->s);
+            launch_build_eps(c->g, at, dp, tb, c->eps64, c->pe64, c->eps32, c->s);
         }
         GP_CHECK_LAUNCH();
         {
@@ -1201,7 +1219,7 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             DielParams dp{c->prm.eps0, c->prm.r0, c->prm.w, c->prm.rcut};
             {
                 ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
-                launch_forces_eps(c->g, at, dp, phi_dev, c->pe64, c->forces_S, c->s);
+                launch_forces_eps(c->g, at, dp, c->sw, phi_dev, c->pe64, c->forces_S, c->s);
             }
             GP_CHECK_LAUNCH();
             if (gauss_dev) {

@@ -49,16 +49,26 @@ struct DielParams {
 
 __host__ __device__ inline long plane_of(int nx, int ny) { return (long)nx * ny; }
 
+// switching-function tables (k_fields.cu): s and h = s'/(s d) as polynomials in q = d^2
+constexpr int kSwNI = 256, kSwDeg = 9;
+struct SwTables {
+    const double* s = nullptr;    // kSwNI x (kSwDeg+1) monomial coefficients, or null (use erfc)
+    const double* h = nullptr;
+    double s_qlo = 0, s_qhi = 0, s_inv_dq = 0;
+    double h_qlo = 0, h_qhi = 0, h_inv_dq = 0;
+};
+
 // ---------------------------------------------------------------- launchers
 // fields (k_fields.cu)
 void launch_wrap_atoms(const Geo& g, const double* pos, int n, double* w64, float4* w32, cudaStream_t s);
-void launch_build_eps(const Geo& g, Atoms at, DielParams p, double* eps64, double* pe64,
+void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, double* h_coef, cudaStream_t s);
+void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, double* eps64, double* pe64,
                       float* eps32, cudaStream_t s);
 void launch_build_rho_raw(const Geo& g, Atoms at, double cut_sigmas, double* rho, cudaStream_t s);
 void launch_plane_max(const Geo& g, const double* eps64, double* plane_max, cudaStream_t s);
 void launch_energy(const Geo& g, const double* rho, const double* phi, const double* eps64,
                    double* partial, cudaStream_t s);
-void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const double* phi,
+void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const double* phi,
                        const double* pe64, double* G, cudaStream_t s);
 void launch_forces_rho(const Geo& g, Atoms at, double cut_sigmas, const double* phi,
                        double* G, cudaStream_t s);

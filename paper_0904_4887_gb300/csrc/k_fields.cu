@@ -75,6 +75,68 @@ __device__ __forceinline__ float box_dmax(const Tile& t, float cx, float cy, flo
     return fmaxf(dx, fmaxf(dy, dz));
 }
 
+// ----------------------------------------------------------------- switching-function tables
+// s(d) = erfc((r0 - d)/w)/2 and h(d) = s'(d)/(s(d) d) tabulated as functions
+// of q = d^2 (no square root per pair): kSwNI equal intervals in q, on each a
+// degree-kSwDeg polynomial in the local variable t in [-1, 1], obtained by
+// Chebyshev interpolation (Trefethen, Approximation Theory and Approximation
+// Practice, ch. 3: values at the Chebyshev points of the first kind, discrete
+// cosine transform to Chebyshev coefficients, then to monomials). The FP64
+// values at the nodes come from erfc and exp. Interpolation error is about
+// 5e-15 relative for s on q in [(r0-4w)^2, (r0+6w)^2] and for h on
+// [(r0-3.5w)^2, (r0+3.5w)^2]; outside those ranges the kernels use exact
+// forms (s = 1, or FP32 special functions on terms below 1e-8).
+__global__ void k_switch_tables(DielParams p, SwTables tb, double* s_coef, double* h_coef) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * kSwNI) return;
+    const bool is_h = k >= kSwNI;
+    const int iv = is_h ? k - kSwNI : k;
+    const double qlo = is_h ? tb.h_qlo : tb.s_qlo;
+    const double dq = 1.0 / (is_h ? tb.h_inv_dq : tb.s_inv_dq);
+    constexpr int n = kSwDeg + 1;
+    double fv[n], c[n];
+    for (int j = 0; j < n; ++j) {
+        const double xj = cospi((j + 0.5) / n);
+        const double q = qlo + iv * dq + (xj + 1.0) * 0.5 * dq;
+        const double d = sqrt(q);
+        const double u = (d - p.r0) / p.w;
+        const double sv = 0.5 * erfc(-u);
+        fv[j] = is_h ? exp(-u * u) / (p.w * sqrt(kPi)) / (sv * d) : sv;
+    }
+    for (int m = 0; m < n; ++m) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += fv[j] * cospi(m * (j + 0.5) / n);
+        c[m] = acc * 2.0 / n;
+    }
+    c[0] *= 0.5;
+    // monomial coefficients: T_0 = 1, T_1 = t, T_{m+1} = 2 t T_m - T_{m-1}
+    double Tm1[n], Tm[n], mono[n];
+    for (int e = 0; e < n; ++e) { Tm1[e] = 0.0; Tm[e] = 0.0; mono[e] = 0.0; }
+    Tm1[0] = 1.0;                       // T_0
+    Tm[1] = 1.0;                        // T_1
+    mono[0] += c[0];
+    for (int e = 0; e < n; ++e) mono[e] += c[1] * Tm[e];
+    for (int m = 2; m < n; ++m) {
+        double Tn[n];
+        for (int e = 0; e < n; ++e) Tn[e] = (e > 0 ? 2.0 * Tm[e - 1] : 0.0) - Tm1[e];
+        for (int e = 0; e < n; ++e) { mono[e] += c[m] * Tn[e]; Tm1[e] = Tm[e]; Tm[e] = Tn[e]; }
+    }
+    double* out = (is_h ? h_coef : s_coef) + (long)iv * n;
+    for (int e = 0; e < n; ++e) out[e] = mono[e];
+}
+
+__device__ __forceinline__ double sw_eval(const double* __restrict__ coef, double qlo, double inv_dq, double q) {
+    double x = (q - qlo) * inv_dq;
+    int k = (int)x;
+    k = k < 0 ? 0 : (k >= kSwNI ? kSwNI - 1 : k);
+    const double t = 2.0 * (x - k) - 1.0;
+    const double* c = coef + k * (kSwDeg + 1);
+    double acc = __ldg(c + kSwDeg);
+#pragma unroll
+    for (int e = kSwDeg - 1; e >= 0; --e) acc = fma(acc, t, __ldg(c + e));
+    return acc;
+}
+
 // ----------------------------------------------------------------- eps
 // compact 8 x 2 x 2 block of the tile for warp w, lane l (spatially close points
 // take the same branches below)
@@ -96,7 +158,7 @@ __device__ __forceinline__ double switch_s(double u) {
 
 // eps = 1 + (eps0 - 1) prod s(d). Once (eps0-1) P < 2^-54 further factors
 // (all <= 1) cannot move 1 + (eps0-1) P away from 1.0, so the product stops.
-__global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p, double* eps64,
+__global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p, SwTables tb, double* eps64,
                                                   double* pe64, float* eps32) {
     __shared__ double ec[MAXE][3];
     __shared__ int ne;
@@ -131,7 +193,12 @@ __global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p,
                 const double dx = x - ec[e][0], dy = y - ec[e][1], dz = z - ec[e][2];
                 const double d2 = dx * dx + dy * dy + dz * dz;
                 if (d2 < rc2) {
-                    P *= switch_s((sqrt(d2) - p.r0) * iw);
+                    double sv;
+                    if (!tb.s) sv = switch_s((sqrt(d2) - p.r0) * iw);
+                    else if (d2 >= tb.s_qhi) continue;                 // u >= 6: s == 1 in FP64
+                    else if (d2 > tb.s_qlo) sv = sw_eval(tb.s, tb.s_qlo, tb.s_inv_dq, d2);
+                    else sv = 0.5 * (double)erfcf((float)((p.r0 - sqrt(d2)) * iw));   // u < -4, s < 8e-9
+                    P *= sv;
                     if (P < tiny) break;
                 }
             }
@@ -366,7 +433,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // One warp per (atom, image) entry runs over the tile's 512 points in compact
 // 8 x 2 x 2 blocks. Pairs with |u| > 3.5 contribute at most 5e-6 of a pair at
 // the switching radius; their s and s' are taken in FP32.
-__global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p, const double* phi,
+__global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p, SwTables tb, const double* phi,
                                                    const double* pe64, double* S) {
     __shared__ double ec[MAXE][3];
     __shared__ int eatom[MAXE];
@@ -426,15 +493,18 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
                 const double d2 = dx * dx + dy * dy + dz * dz;
                 if (!(d2 < rc2 && d2 > 0.0)) continue;
                 const double W = Ws[tx + TX * (ty + TY * tz)];
-                const double d = sqrt(d2);
-                const double u = (d - p.r0) * iw;
+                const float df = sqrtf((float)d2);
+                const float uf = (df - (float)p.r0) * (float)iw;
                 double ratio;   // s'(d) / (s(d) d)
-                if (fabs(u) > 3.5) {
-                    const float uf = (float)u;
+                if (fabsf(uf) > 3.45f) {
                     const float sf = 0.5f * erfcf(-uf);
                     const float spf = (float)sp_norm * expf(-uf * uf);
-                    ratio = (double)(spf / (sf * (float)d));
+                    ratio = (double)(spf / (sf * df));
+                } else if (tb.h) {
+                    ratio = sw_eval(tb.h, tb.h_qlo, tb.h_inv_dq, d2);
                 } else {
+                    const double d = sqrt(d2);
+                    const double u = (d - p.r0) * iw;
                     ratio = sp_norm * exp(-u * u) / (0.5 * erfc(-u) * d);
                 }
                 const double c = -W * ratio;
@@ -581,9 +651,13 @@ void launch_wrap_atoms(const Geo& g, const double* pos, int n, double* w64, floa
     if (n > 0) k_wrap_atoms<<<(n + 127) / 128, 128, 0, s>>>(g, pos, n, w64, w32);
 }
 
-void launch_build_eps(const Geo& g, Atoms at, DielParams p, double* eps64, double* pe64, float* eps32,
-                      cudaStream_t s) {
-    k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, eps64, pe64, eps32);
+void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, double* h_coef, cudaStream_t s) {
+    k_switch_tables<<<(2 * kSwNI + 127) / 128, 128, 0, s>>>(p, tb, s_coef, h_coef);
+}
+
+void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, double* eps64, double* pe64,
+                      float* eps32, cudaStream_t s) {
+    k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
 }
 
 void launch_build_rho_raw(const Geo& g, Atoms at, double cut, double* rho, cudaStream_t s) {
@@ -599,9 +673,9 @@ void launch_energy(const Geo& g, const double* rho, const double* phi, const dou
     k_energy<<<kReduceBlocks, kReduceThreads, 0, s>>>(g, rho, phi, eps64, partial);
 }
 
-void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const double* phi, const double* pe64,
-                       double* S, cudaStream_t s) {
-    k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, phi, pe64, S);
+void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const double* phi,
+                       const double* pe64, double* S, cudaStream_t s) {
+    k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
 }
 
 void launch_forces_rho(const Geo& g, Atoms at, double cut, const double* phi, double* T, cudaStream_t s) {
