@@ -4,6 +4,7 @@
 // correction that couples the dry FFT solution to the wet multigrid band.
 #include "gp_common.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -169,6 +170,8 @@ struct gp_ctx {
     int forces_cap = 0;
     double* gmat = nullptr;        // Gauss-Jordan workspace (2 * 512^2)
     double* sw_coef = nullptr;     // switching-function tables (2 * kSwNI * (kSwDeg+1))
+    double* gtab = nullptr;        // Gaussian factor tables [atom][2][3][3][nmax]
+    size_t gtab_cap = 0;
     SwTables sw{};
 
     // solver state
@@ -270,6 +273,18 @@ void* dalloc(gp_ctx* c, size_t bytes) {
     c->misc.push_back(p);
     GP_CUDA(cudaMemset(p, 0, bytes));
     return p;
+}
+
+double* ensure_gtab(gp_ctx* c, int n_atoms, int& nmax) {
+    nmax = std::max(c->g.nx, std::max(c->g.ny, c->g.nz));
+    const size_t need = (size_t)std::max(n_atoms, 1) * 18 * nmax;
+    if (need > c->gtab_cap) {
+        if (c->gtab) cudaFree(c->gtab);
+        c->gtab = nullptr;
+        if (cudaMalloc(&c->gtab, sizeof(double) * need) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+        c->gtab_cap = need;
+    }
+    return c->gtab;
 }
 
 double sum_host(gp_ctx* c, int ncomp, double* out) {
@@ -1152,9 +1167,12 @@ gp_status gp_build_rho(gp_ctx* c, const double* atoms_dev, const double* gauss_d
             launch_wrap_atoms(c->g, atoms_dev, n_atoms, c->ratoms, c->ratoms32, c->s);
         }
         Atoms at{c->ratoms, c->ratoms32, gauss_dev, n_atoms};
+        int nmax = 0;
+        double* tab = ensure_gtab(c, n_atoms, nmax);
         {
-            ProfScope ps(c, GP_PROF_RHO, 1);
-            launch_build_rho_raw(c->g, at, cut, rho_dev, c->s);
+            ProfScope ps(c, GP_PROF_RHO, 2);
+            launch_gauss_tables(c->g, at, cut, nmax, tab, c->s);
+            launch_build_rho_raw(c->g, at, cut, tab, nmax, rho_dev, c->s);
         }
         GP_CHECK_LAUNCH();
         {
@@ -1223,8 +1241,11 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             }
             GP_CHECK_LAUNCH();
             if (gauss_dev) {
-                ProfScope ps(c, GP_PROF_FORCES_RHO, 1);
-                launch_forces_rho(c->g, at, 8.0, phi_dev, c->forces_T, c->s);
+                int nmax = 0;
+                double* tab = ensure_gtab(c, n, nmax);
+                ProfScope ps(c, GP_PROF_FORCES_RHO, 2);
+                launch_gauss_tables(c->g, at, 8.0, nmax, tab, c->s);
+                launch_forces_rho(c->g, at, 8.0, tab, nmax, phi_dev, c->forces_T, c->s);
             }
             GP_CHECK_LAUNCH();
             ProfScope ps(c, GP_PROF_MISC, 1);
@@ -1383,6 +1404,7 @@ void gp_destroy(gp_ctx* c) {
     for (void* p : c->misc) cudaFree(p);
     if (c->atoms) cudaFree(c->atoms);
     if (c->atoms32) cudaFree(c->atoms32);
+    if (c->gtab) cudaFree(c->gtab);
     if (c->ratoms) cudaFree(c->ratoms);
     if (c->ratoms32) cudaFree(c->ratoms32);
     if (c->forces_S) cudaFree(c->forces_S);

@@ -64,13 +64,15 @@ void launch_wrap_atoms(const Geo& g, const double* pos, int n, double* w64, floa
 void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, double* h_coef, cudaStream_t s);
 void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, double* eps64, double* pe64,
                       float* eps32, cudaStream_t s);
-void launch_build_rho_raw(const Geo& g, Atoms at, double cut_sigmas, double* rho, cudaStream_t s);
+void launch_gauss_tables(const Geo& g, Atoms at, double cut_sigmas, int nmax, double* tab, cudaStream_t s);
+void launch_build_rho_raw(const Geo& g, Atoms at, double cut_sigmas, const double* tab, int nmax, double* rho,
+                          cudaStream_t s);
 void launch_plane_max(const Geo& g, const double* eps64, double* plane_max, cudaStream_t s);
 void launch_energy(const Geo& g, const double* rho, const double* phi, const double* eps64,
                    double* partial, cudaStream_t s);
 void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const double* phi,
                        const double* pe64, double* G, cudaStream_t s);
-void launch_forces_rho(const Geo& g, Atoms at, double cut_sigmas, const double* phi,
+void launch_forces_rho(const Geo& g, Atoms at, double cut_sigmas, const double* tab, int nmax, const double* phi,
                        double* G, cudaStream_t s);
 void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,
                           cudaStream_t s);

@@ -247,6 +247,38 @@ __device__ __forceinline__ df df_add(df a, df b) {
     return df_quick(s, e);
 }
 
+// ----------------------------------------------------------------- Gaussian factor tables
+// One-dimensional factors of every Gaussian, exp(-(x_i - c)^2 / 2 sigma^2) with
+// c an image of the atom's coordinate along one axis (shift -L, 0, +L), zero
+// outside the 8 sigma window; indexed [atom][core/cloud][axis][image][i].
+// Tiles then read these instead of evaluating exp per tile.
+__device__ __forceinline__ long gtab_index(int a, int which, int axis, int img, int i, int nmax) {
+    return ((((long)a * 2 + which) * 3 + axis) * 3 + img) * nmax + i;
+}
+
+__global__ void k_gauss_tables(Geo g, Atoms at, double cut, int nmax, double* tab) {
+    const long total = (long)at.n * 2 * 3 * 3 * nmax;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % nmax);
+        long r = q / nmax;
+        const int img = (int)(r % 3); r /= 3;
+        const int axis = (int)(r % 3); r /= 3;
+        const int which = (int)(r % 2);
+        const int a = (int)(r / 2);
+        const int n = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+        double v = 0.0;
+        if (i < n) {
+            const double h = axis == 0 ? g.hx : (axis == 1 ? g.hy : g.hz);
+            const double L = axis == 0 ? g.lx : (axis == 1 ? g.ly : g.lz);
+            const double sg = at.gauss[3 * a + 1 + which];
+            const double c = at.w64[3 * a + axis] + (img - 1) * L;
+            const double d = i * h - c;
+            if (fabs(d) < cut * sg) v = exp(-d * d / (2.0 * sg * sg));
+        }
+        tab[q] = v;
+    }
+}
+
 // ----------------------------------------------------------------- rho
 // Separable Gaussians: g(r) = N exp(-dx^2/2s^2) exp(-dy^2/2s^2) exp(-dz^2/2s^2),
 // each factor zero outside |d| < cut*s. A tile tabulates the three 1D factors
@@ -267,9 +299,11 @@ __device__ __forceinline__ double tile_peak(const Tile& t, const Geo& g, double 
     return exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sg * sg));
 }
 
-__global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, double* rho) {
+__global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, const double* __restrict__ tab,
+                                                  int nmax, double* rho) {
     __shared__ double en[RMAX][5];      // cx, cy, cz, sigma, coefficient (near entries from the front,
                                         //  FP32 tail entries from the back)
+    __shared__ int ekey[RMAX];          // (atom * 2 + which) * 27 + image
     __shared__ df gx[RSUB][TX];
     __shared__ double gy[RSUB][TY];
     __shared__ double gz[RSUB][TZ];
@@ -303,6 +337,7 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, d
                 en[s][0] = cx; en[s][1] = cy; en[s][2] = cz; en[s][3] = sg;
                 const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
                 en[s][4] = (which == 0 ? Z : -Z) * norm;
+                ekey[s] = (a * 2 + which) * 27 + im;
             }
         }
         __syncthreads();
@@ -311,20 +346,18 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, d
             const int ms = min(RSUB, m64 - e0);
             for (int q = threadIdx.x; q < ms * (TX + TY + TZ); q += TT) {
                 const int e = q / (TX + TY + TZ), r = q % (TX + TY + TZ);
-                const double* E = en[e0 + e];
-                const double rad = cut * E[3];
-                const double i2s = 1.0 / (2.0 * E[3] * E[3]);
+                const int key = ekey[e0 + e];
+                const int im = key % 27, aw = key / 27;
+                const int a = aw / 2, which = aw % 2;
                 if (r < TX) {
-                    const double d = (t.i0 + r) * g.hx - E[0];
-                    gx[e][r] = df_from((fabs(d) < rad) ? exp(-d * d * i2s) : 0.0);
+                    const int ii = t.i0 + r;
+                    gx[e][r] = df_from(ii < g.nx ? tab[gtab_index(a, which, 0, im % 3, ii, nmax)] : 0.0);
                 } else if (r < TX + TY) {
-                    const int rr = r - TX;
-                    const double d = (t.j0 + rr) * g.hy - E[1];
-                    gy[e][rr] = (fabs(d) < rad) ? E[4] * exp(-d * d * i2s) : 0.0;
+                    const int rr = r - TX, jj = t.j0 + rr;
+                    gy[e][rr] = jj < g.ny ? en[e0 + e][4] * tab[gtab_index(a, which, 1, (im / 3) % 3, jj, nmax)] : 0.0;
                 } else {
-                    const int rr = r - TX - TY;
-                    const double d = (t.k0 + rr) * g.hz - E[2];
-                    gz[e][rr] = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
+                    const int rr = r - TX - TY, kk = t.k0 + rr;
+                    gz[e][rr] = kk < g.nz ? tab[gtab_index(a, which, 2, im / 9, kk, nmax)] : 0.0;
                 }
             }
             __syncthreads();
@@ -342,20 +375,20 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, d
             const int ms = min(RSUB, m32 - e0);
             for (int q = threadIdx.x; q < ms * (TX + TY + TZ); q += TT) {
                 const int e = q / (TX + TY + TZ), r = q % (TX + TY + TZ);
-                const double* E = en[RMAX - 1 - (e0 + e)];
-                const float rad = (float)(cut * E[3]);
-                const float i2s = (float)(1.0 / (2.0 * E[3] * E[3]));
+                const int slot = RMAX - 1 - (e0 + e);
+                const int key = ekey[slot];
+                const int im = key % 27, aw = key / 27;
+                const int a = aw / 2, which = aw % 2;
                 if (r < TX) {
-                    const float d = (float)((t.i0 + r) * g.hx - E[0]);
-                    fx32[e][r] = (fabsf(d) < rad) ? expf(-d * d * i2s) : 0.f;
+                    const int ii = t.i0 + r;
+                    fx32[e][r] = ii < g.nx ? (float)tab[gtab_index(a, which, 0, im % 3, ii, nmax)] : 0.f;
                 } else if (r < TX + TY) {
-                    const int rr = r - TX;
-                    const float d = (float)((t.j0 + rr) * g.hy - E[1]);
-                    fy32[e][rr] = (fabsf(d) < rad) ? (float)E[4] * expf(-d * d * i2s) : 0.f;
+                    const int rr = r - TX, jj = t.j0 + rr;
+                    fy32[e][rr] = jj < g.ny ? (float)(en[slot][4] * tab[gtab_index(a, which, 1, (im / 3) % 3, jj, nmax)])
+                                            : 0.f;
                 } else {
-                    const int rr = r - TX - TY;
-                    const float d = (float)((t.k0 + rr) * g.hz - E[2]);
-                    fz32[e][rr] = (fabsf(d) < rad) ? expf(-d * d * i2s) : 0.f;
+                    const int rr = r - TX - TY, kk = t.k0 + rr;
+                    fz32[e][rr] = kk < g.nz ? (float)tab[gtab_index(a, which, 2, im / 9, kk, nmax)] : 0.f;
                 }
             }
             __syncthreads();
@@ -526,10 +559,11 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
 // One warp per (atom, image, Gaussian) entry, lanes along x; the y and z
 // factors are separable, so each lane first sums its column over the 16
 // (y, z) rows. Entries below 1e-8 of their peak on the tile run in FP32.
-__global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, const double* phi,
-                                                   double* T) {
+__global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, const double* __restrict__ tab,
+                                                   int nmax, const double* phi, double* T) {
     __shared__ double en[RMAX][5];
     __shared__ int eatom[RMAX];
+    __shared__ int ekey[RMAX];
     __shared__ double ph[TT];
     __shared__ int ne;
     const Tile t = make_tile(g);
@@ -559,6 +593,7 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, 
                 const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
                 en[s][4] = (which == 0 ? Z : -Z) * norm / (sg * sg);
                 eatom[s] = a;
+                ekey[s] = (a * 2 + which) * 27 + im;
             }
         }
         __syncthreads();
@@ -567,21 +602,23 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, 
             const double cx = en[e][0], cy = en[e][1], cz = en[e][2], sg = en[e][3], coef = en[e][4];
             const double rad = cut * sg;
             const double i2s = 1.0 / (2.0 * sg * sg);
+            const int key = ekey[e], im = key % 27, aw = key / 27, ea = aw / 2, ew = aw % 2;
+            // this lane's x factor and the 8 y / z factors, from the tables
+            const double gxt = lane_ok ? tab[gtab_index(ea, ew, 0, im % 3, i, nmax)] : 0.0;
+            double gyz_t = 0.0;
+            if (lane < TY && t.j0 + lane < g.ny) gyz_t = tab[gtab_index(ea, ew, 1, (im / 3) % 3, t.j0 + lane, nmax)];
+            else if (lane >= TY && lane < TY + TZ && t.k0 + lane - TY < g.nz)
+                gyz_t = tab[gtab_index(ea, ew, 2, im / 9, t.k0 + lane - TY, nmax)];
+            (void)rad; (void)i2s;
             double fx = 0.0, fy = 0.0, fz = 0.0;
             if (tile_peak(t, g, cx, cy, cz, sg) < kTail) {
                 // FP32: lane < 8 tabulates one y or z factor, shared by shuffles
-                float gyz_v = 0.f, d_v = 0.f;
-                if (lane < TY) {
-                    const float d = (float)((t.j0 + lane) * g.hy - cy);
-                    d_v = d;
-                    gyz_v = (fabsf(d) < (float)rad) ? expf(-d * d * (float)i2s) : 0.f;
-                } else if (lane < TY + TZ) {
-                    const float d = (float)((t.k0 + lane - TY) * g.hz - cz);
-                    d_v = d;
-                    gyz_v = (fabsf(d) < (float)rad) ? expf(-d * d * (float)i2s) : 0.f;
-                }
+                float d_v = 0.f;
+                if (lane < TY) d_v = (float)((t.j0 + lane) * g.hy - cy);
+                else if (lane < TY + TZ) d_v = (float)((t.k0 + lane - TY) * g.hz - cz);
+                const float gyz_v = (float)gyz_t;
                 const float dxf = (float)(i * g.hx - cx);
-                const float gxf = (lane_ok && fabsf(dxf) < (float)rad) ? expf(-dxf * dxf * (float)i2s) : 0.f;
+                const float gxf = (float)gxt;
                 float s0 = 0.f, sy = 0.f, sz = 0.f;
                 for (int tz = 0; tz < TZ; ++tz) {
                     const float gz = __shfl_sync(0xffffffffu, gyz_v, TY + tz);
@@ -597,18 +634,12 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, 
                 fy = coef * (double)(gxf * sy);
                 fz = coef * (double)(gxf * sz);
             } else {
-                double gyz_v = 0.0, d_v = 0.0;
-                if (lane < TY) {
-                    const double d = (t.j0 + lane) * g.hy - cy;
-                    d_v = d;
-                    gyz_v = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
-                } else if (lane < TY + TZ) {
-                    const double d = (t.k0 + lane - TY) * g.hz - cz;
-                    d_v = d;
-                    gyz_v = (fabs(d) < rad) ? exp(-d * d * i2s) : 0.0;
-                }
+                double d_v = 0.0;
+                if (lane < TY) d_v = (t.j0 + lane) * g.hy - cy;
+                else if (lane < TY + TZ) d_v = (t.k0 + lane - TY) * g.hz - cz;
+                const double gyz_v = gyz_t;
                 const double dx = i * g.hx - cx;
-                const double gx = (lane_ok && fabs(dx) < rad) ? exp(-dx * dx * i2s) : 0.0;
+                const double gx = gxt;
                 double s0 = 0.0, sy = 0.0, sz = 0.0;
                 for (int tz = 0; tz < TZ; ++tz) {
                     const double gz = __shfl_sync(0xffffffffu, gyz_v, TY + tz);
@@ -660,8 +691,15 @@ void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, 
     k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
 }
 
-void launch_build_rho_raw(const Geo& g, Atoms at, double cut, double* rho, cudaStream_t s) {
-    k_build_rho<<<tile_grid(g), TT, 0, s>>>(g, at, cut, rho);
+void launch_gauss_tables(const Geo& g, Atoms at, double cut, int nmax, double* tab, cudaStream_t s) {
+    const long total = (long)at.n * 18 * nmax;
+    if (total > 0) k_gauss_tables<<<(int)((total + 255) / 256 < 152L * 64 ? (total + 255) / 256 : 152L * 64), 256, 0, s>>>(
+        g, at, cut, nmax, tab);
+}
+
+void launch_build_rho_raw(const Geo& g, Atoms at, double cut, const double* tab, int nmax, double* rho,
+                          cudaStream_t s) {
+    k_build_rho<<<tile_grid(g), TT, 0, s>>>(g, at, cut, tab, nmax, rho);
 }
 
 void launch_plane_max(const Geo& g, const double* eps64, double* out, cudaStream_t s) {
@@ -678,8 +716,9 @@ void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb,
     k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
 }
 
-void launch_forces_rho(const Geo& g, Atoms at, double cut, const double* phi, double* T, cudaStream_t s) {
-    k_forces_rho<<<tile_grid(g), TT, 0, s>>>(g, at, cut, phi, T);
+void launch_forces_rho(const Geo& g, Atoms at, double cut, const double* tab, int nmax, const double* phi,
+                       double* T, cudaStream_t s) {
+    k_forces_rho<<<tile_grid(g), TT, 0, s>>>(g, at, cut, tab, nmax, phi, T);
 }
 
 void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,
