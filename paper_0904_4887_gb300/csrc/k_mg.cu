@@ -108,10 +108,10 @@ int grid_for(long n, int threads) {
 template <typename T>
 __global__ void k_rbgs(LV<T> L, T* u, const T* f, int color) {
     const int hx = L.nx >> 1;
-    const long np = (long)hx * L.ny * L.nz;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < np; t += (long)gridDim.x * blockDim.x) {
-        int i2, j, k;
-        split3(t, hx, L.ny, i2, j, k);
+    const long rows = (long)L.ny * L.nz;
+    for (long row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int i2 = threadIdx.x; i2 < hx; i2 += blockDim.x) {
+        const int j = (int)(row % L.ny), k = (int)(row / L.ny);
         const int i = 2 * i2 + ((j + k + color) & 1);
         const Nb n = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
         const Co<T> o = coefs(L, n);
@@ -124,10 +124,10 @@ __global__ void k_rbgs(LV<T> L, T* u, const T* f, int color) {
 
 template <typename T>
 __global__ void k_residual(LV<T> L, const T* u, const T* f, T* r) {
-    const long n = (long)L.nx * L.ny * L.nz;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        split3(t, L.nx, L.ny, i, j, k);
+    const long rows = (long)L.ny * L.nz;
+    for (long row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int i = threadIdx.x; i < L.nx; i += blockDim.x) {
+        const int j = (int)(row % L.ny), k = (int)(row / L.ny);
         const Nb nb = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
         r[nb.c] = f[nb.c] - apply_at(coefs(L, nb), nb, u);
     }
@@ -136,12 +136,12 @@ __global__ void k_residual(LV<T> L, const T* u, const T* f, T* r) {
 // full weighting (1/4, 1/2, 1/4) per axis
 template <typename T>
 __global__ void k_restrict(LV<T> F, const T* r, LV<T> C, T* fc) {
-    const long n = (long)C.nx * C.ny * C.nz;
+    const long rows = (long)C.ny * C.nz;
     const int zoff = F.zper ? 0 : 1;
     const long pl = (long)F.nx * F.ny;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        int I, J, K;
-        split3(t, C.nx, C.ny, I, J, K);
+    for (long row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int I = threadIdx.x; I < C.nx; I += blockDim.x) {
+        const int J = (int)(row % C.ny), K = (int)(row / C.ny);
         const int kf = 2 * K + zoff;
         T acc = 0;
         for (int dz = -1; dz <= 1; ++dz) {
@@ -165,12 +165,12 @@ __global__ void k_restrict(LV<T> F, const T* r, LV<T> C, T* fc) {
 // trilinear interpolation of the coarse correction, added to u
 template <typename T>
 __global__ void k_prolong_add(LV<T> F, T* u, LV<T> C, const T* uc) {
-    const long n = (long)F.nx * F.ny * F.nz;
+    const long rows = (long)F.ny * F.nz;
     const int zoff = F.zper ? 0 : 1;
     const long cpl = (long)C.nx * C.ny;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        split3(t, F.nx, F.ny, i, j, k);
+    for (long row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int i = threadIdx.x; i < F.nx; i += blockDim.x) {
+        const int j = (int)(row % F.ny), k = (int)(row / F.ny);
         int xi[2], yi[2], zi[2];
         T xw[2], yw[2], zw[2];
         int nxp, nyp, nzp;
@@ -387,11 +387,11 @@ __global__ void k_coarse_solve(LV<T> C, const T* inv, int n, const T* f, T* u) {
 template <typename T>
 __global__ void k_applyA_dot(LV<T> L, const T* p, T* q, double* partial) {
     __shared__ double red[32];
-    const long n = (long)L.nx * L.ny * L.nz;
+    const long rows = (long)L.ny * L.nz;
     KSum<typename AccT<T>::type> loc;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        split3(t, L.nx, L.ny, i, j, k);
+    for (long row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int i = threadIdx.x; i < L.nx; i += blockDim.x) {
+        const int j = (int)(row % L.ny), k = (int)(row / L.ny);
         const Nb nb = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
         const T v = apply_at(coefs(L, nb), nb, p);
         q[nb.c] = v;
@@ -479,9 +479,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_residual64(Geo g, const doub
     const double hx = 0.5 / (g.hx * g.hx), hy = 0.5 / (g.hy * g.hy), hz = 0.5 / (g.hz * g.hz);
     const double fpi = 4.0 * kPi;
     double s2 = 0.0, sp = 0.0;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        split3(t, g.nx, g.ny, i, j, k);
+    (void)n;
+    for (long row = blockIdx.x; row < (long)g.ny * g.nz; row += gridDim.x)
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+        const int j = (int)(row % g.ny), k = (int)(row / g.ny);
         const Nb nb = neighbours(g.nx, g.ny, g.nz, 1, i, j, k);
         const double e0 = eps[nb.c], p0 = phi[nb.c];
         const double ax = (e0 + eps[nb.xp]) * (phi[nb.xp] - p0) - (e0 + eps[nb.xm]) * (p0 - phi[nb.xm]);
@@ -705,21 +706,25 @@ void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_ba
     const long n = (long)g.nx * g.ny * g.nz;
     k_update_phi<T><<<grid_for(n, 256), 256, 0, s>>>(g, phi, e_full, e_band, band_first, band_nz);
 }
+// row kernels: one block per (j, k) row at a time, threads along x
+int row_threads(int nx) { return nx >= 256 ? 256 : (nx >= 128 ? 128 : (nx > 32 ? 64 : 32)); }
+int row_blocks(long rows) { return (int)(rows < 152L * 32 ? rows : 152L * 32); }
+
 template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s) {
-    const long n = (long)(L.nx / 2) * L.ny * L.nz;
-    k_rbgs<T><<<grid_for(n, 256), 256, 0, s>>>(L, u, f, color);
+    const long rows = (long)L.ny * L.nz;
+    k_rbgs<T><<<row_blocks(rows), row_threads(L.nx / 2), 0, s>>>(L, u, f, color);
 }
 template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* f, T* r, cudaStream_t s) {
-    const long n = (long)L.nx * L.ny * L.nz;
-    k_residual<T><<<grid_for(n, 256), 256, 0, s>>>(L, u, f, r);
+    const long rows = (long)L.ny * L.nz;
+    k_residual<T><<<row_blocks(rows), row_threads(L.nx), 0, s>>>(L, u, f, r);
 }
 template <typename T> void launch_restrict(const LV<T>& F, const T* r, const LV<T>& C, T* fc, cudaStream_t s) {
-    const long n = (long)C.nx * C.ny * C.nz;
-    k_restrict<T><<<grid_for(n, 256), 256, 0, s>>>(F, r, C, fc);
+    const long rows = (long)C.ny * C.nz;
+    k_restrict<T><<<row_blocks(rows), row_threads(C.nx), 0, s>>>(F, r, C, fc);
 }
 template <typename T> void launch_prolong_add(const LV<T>& F, T* u, const LV<T>& C, const T* uc, cudaStream_t s) {
-    const long n = (long)F.nx * F.ny * F.nz;
-    k_prolong_add<T><<<grid_for(n, 256), 256, 0, s>>>(F, u, C, uc);
+    const long rows = (long)F.ny * F.nz;
+    k_prolong_add<T><<<row_blocks(rows), row_threads(F.nx), 0, s>>>(F, u, C, uc);
 }
 template <typename T> void launch_coarsen_faces(const LV<T>& F, int nxc, int nyc, int nzc, T* cx, T* cy, T* cz,
                                                 cudaStream_t s) {
