@@ -414,7 +414,12 @@ void smooth_fine(gp_ctx* c, Hier<T>& H, T* u, const T* f, int nu, int first) {
 template <typename T>
 void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
     const int L = H.L;
-    for (int l = 0; l < L - 1; ++l) {
+    // first level small enough for the persistent single-CTA kernel (never the finest)
+    int lc = L - 1;
+    for (int l = 1; l < L; ++l) {
+        if ((long)H.lv[l].nx * H.lv[l].ny * H.lv[l].nz <= kCoarseBlockPoints) { lc = l; break; }
+    }
+    for (int l = 0; l < lc; ++l) {
         const LV<T>& V = H.lv[l];
         T* u = l == 0 ? u0 : H.u[l];
         const T* f = l == 0 ? f0 : H.f[l];
@@ -434,9 +439,16 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
     }
     {
         ProfScope ps(c, GP_PROF_MG_COARSE, 1);
-        launch_coarse_solve<T>(H.lv[L - 1], H.minv, H.nc, H.f[L - 1], H.u[L - 1], c->s);
+        if (lc < L - 1) {
+            CoarseSet<T> S;
+            S.l0 = lc; S.L = L; S.nc = H.nc; S.nu1 = c->prm.nu1; S.nu2 = c->prm.nu2; S.minv = H.minv;
+            for (int l = 0; l < L; ++l) { S.lv[l] = H.lv[l]; S.u[l] = H.u[l]; S.f[l] = H.f[l]; S.r[l] = H.res[l]; }
+            launch_coarse_vcycle<T>(S, c->s);
+        } else {
+            launch_coarse_solve<T>(H.lv[L - 1], H.minv, H.nc, H.f[L - 1], H.u[L - 1], c->s);
+        }
     }
-    for (int l = L - 2; l >= 0; --l) {
+    for (int l = lc - 1; l >= 0; --l) {
         const LV<T>& V = H.lv[l];
         T* u = l == 0 ? u0 : H.u[l];
         const T* f = l == 0 ? f0 : H.f[l];

@@ -115,6 +115,19 @@ template <typename T> void launch_update_p(const LV<T>& L, T* p, const T* z, con
                                            int num, int den, cudaStream_t s);
 template <typename T> void launch_copy_level(const LV<T>& L, T* dst, const T* src, cudaStream_t s);
 
+// the bottom of a V-cycle in one CTA (k_mg.cu): levels l0 .. L-1
+constexpr int kCoarseBlockPoints = 32768;   // levels up to this size run in the persistent kernel
+template <typename T>
+struct CoarseSet {
+    int l0, L, nc, nu1, nu2;
+    LV<T> lv[16];
+    T* u[16];
+    T* f[16];
+    T* r[16];
+    const T* minv;
+};
+template <typename T> void launch_coarse_vcycle(const CoarseSet<T>& S, cudaStream_t s);
+
 // dry/wet band (k_mg.cu)
 template <typename T> void launch_cast_eps(long n, const double* e64, T* eT, cudaStream_t s);
 template <typename T> void launch_band_eps(const Geo& g, const T* epsT, int first_interior, int band_nz,

@@ -641,7 +641,153 @@ __global__ void k_axpy1(long n, T* x, const T* y) {
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) x[t] += y[t];
 }
 
+// ------------------------------------------------------------ persistent coarse V-cycle
+// The bottom of the V-cycle (levels S.l0 .. S.L-1, each small) in ONE CTA:
+// every smoothing colour, residual, restriction, the coarsest solve and each
+// prolongation is a phase over the level's points, separated by
+// __syncthreads. Replaces a chain of tiny, launch-bound kernels.
+template <typename T>
+__device__ void blk_rbgs(const LV<T>& L, T* u, const T* f, int color) {
+    const int hx = L.nx >> 1;
+    const int np = hx * L.ny * L.nz;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int i2 = t % hx, r = t / hx, j = r % L.ny, k = r / L.ny;
+        const int i = 2 * i2 + ((j + k + color) & 1);
+        const Nb n = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
+        const Co<T> o = coefs(L, n);
+        const T sm = o.xp * u[n.xp] + o.xm * u[n.xm] + o.yp * u[n.yp] + o.ym * u[n.ym] + o.zp * u[n.zp] +
+                     o.zm * u[n.zm];
+        const T d = o.xp + o.xm + o.yp + o.ym + o.zp + o.zm;
+        u[n.c] = (sm - f[n.c]) / d;
+    }
+}
+
+template <typename T>
+__device__ void blk_residual(const LV<T>& L, const T* u, const T* f, T* r) {
+    const int np = L.nx * L.ny * L.nz;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int i = t % L.nx, q = t / L.nx, j = q % L.ny, k = q / L.ny;
+        const Nb nb = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
+        r[nb.c] = f[nb.c] - apply_at(coefs(L, nb), nb, u);
+    }
+}
+
+template <typename T>
+__device__ void blk_restrict(const LV<T>& F, const T* r, const LV<T>& C, T* fc) {
+    const int np = C.nx * C.ny * C.nz;
+    const int zoff = F.zper ? 0 : 1;
+    const long pl = (long)F.nx * F.ny;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int I = t % C.nx, q = t / C.nx, J = q % C.ny, K = q / C.ny;
+        const int kf = 2 * K + zoff;
+        T acc = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            int kk = kf + dz;
+            if (F.zper) kk = (kk + F.nz) % F.nz;
+            const T wz = dz == 0 ? (T)0.5 : (T)0.25;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int jj = (2 * J + dy + F.ny) % F.ny;
+                const T wy = dy == 0 ? (T)0.5 : (T)0.25;
+                const long base = kk * pl + (long)jj * F.nx;
+                const int ic = 2 * I;
+                const int im = ic == 0 ? F.nx - 1 : ic - 1;
+                const int ip = ic == F.nx - 1 ? 0 : ic + 1;
+                acc += wz * wy * ((T)0.25 * r[base + im] + (T)0.5 * r[base + ic] + (T)0.25 * r[base + ip]);
+            }
+        }
+        fc[I + (long)C.nx * (J + (long)C.ny * K)] = acc;
+    }
+}
+
+template <typename T>
+__device__ void blk_prolong_add(const LV<T>& F, T* u, const LV<T>& C, const T* uc) {
+    const int np = F.nx * F.ny * F.nz;
+    const int zoff = F.zper ? 0 : 1;
+    const long cpl = (long)C.nx * C.ny;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int i = t % F.nx, q = t / F.nx, j = q % F.ny, k = q / F.ny;
+        int xi[2], yi[2], zi[2];
+        T xw[2], yw[2], zw[2];
+        int nxp, nyp, nzp;
+        if (i & 1) { xi[0] = i >> 1; xi[1] = (xi[0] + 1) % C.nx; xw[0] = xw[1] = (T)0.5; nxp = 2; }
+        else { xi[0] = i >> 1; xw[0] = 1; nxp = 1; }
+        if (j & 1) { yi[0] = j >> 1; yi[1] = (yi[0] + 1) % C.ny; yw[0] = yw[1] = (T)0.5; nyp = 2; }
+        else { yi[0] = j >> 1; yw[0] = 1; nyp = 1; }
+        const int kk = k - zoff;
+        if (kk & 1) {
+            zi[0] = (kk - 1) >> 1;
+            zi[1] = zi[0] + 1;
+            if (C.zper && zi[1] == C.nz) zi[1] = 0;
+            zw[0] = zw[1] = (T)0.5;
+            nzp = 2;
+        } else { zi[0] = kk >> 1; zw[0] = 1; nzp = 1; }
+        T acc = 0;
+        for (int cc = 0; cc < nzp; ++cc)
+            for (int b = 0; b < nyp; ++b)
+                for (int a = 0; a < nxp; ++a)
+                    acc += zw[cc] * yw[b] * xw[a] * uc[xi[a] + (long)C.nx * yi[b] + cpl * zi[cc]];
+        u[i + (long)F.nx * (j + (long)F.ny * k)] += acc;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseSet<T> S) {
+    __shared__ double red[32];
+    for (int l = S.l0; l < S.L - 1; ++l) {
+        const LV<T>& V = S.lv[l];
+        const int np = V.nx * V.ny * V.nz;
+        for (int t = threadIdx.x; t < np; t += blockDim.x) S.u[l][t] = 0;
+        __syncthreads();
+        for (int it = 0; it < S.nu1; ++it) {
+            blk_rbgs(V, S.u[l], S.f[l], 0);
+            __syncthreads();
+            blk_rbgs(V, S.u[l], S.f[l], 1);
+            __syncthreads();
+        }
+        blk_residual(V, S.u[l], S.f[l], S.r[l]);
+        __syncthreads();
+        blk_restrict(V, S.r[l], S.lv[l + 1], S.f[l + 1]);
+        __syncthreads();
+    }
+    {
+        // coarsest: u = inv (f - mean f) (periodic) or inv f (Dirichlet)
+        const LV<T>& C = S.lv[S.L - 1];
+        const T* f = S.f[S.L - 1];
+        double loc = 0.0;
+        for (int p = threadIdx.x; p < S.nc; p += blockDim.x) loc += (double)f[p];
+        const double tot = block_sum(loc, red);
+        __shared__ double mean;
+        if (threadIdx.x == 0) mean = C.zper ? tot / S.nc : 0.0;
+        __syncthreads();
+        const T mf = (T)mean;
+        for (int p = threadIdx.x; p < S.nc; p += blockDim.x) {
+            T acc = 0;
+            const T* row = S.minv + (long)p * S.nc;
+            for (int q = 0; q < S.nc; ++q) acc += row[q] * (f[q] - mf);
+            S.u[S.L - 1][p] = acc;
+        }
+        __syncthreads();
+    }
+    for (int l = S.L - 2; l >= S.l0; --l) {
+        const LV<T>& V = S.lv[l];
+        blk_prolong_add(V, S.u[l], S.lv[l + 1], S.u[l + 1]);
+        __syncthreads();
+        for (int it = 0; it < S.nu2; ++it) {
+            blk_rbgs(V, S.u[l], S.f[l], 1);
+            __syncthreads();
+            blk_rbgs(V, S.u[l], S.f[l], 0);
+            __syncthreads();
+        }
+    }
+}
+
 }  // namespace
+
+template <typename T> void launch_coarse_vcycle(const CoarseSet<T>& S, cudaStream_t s) {
+    k_coarse_vcycle<T><<<1, 1024, 0, s>>>(S);
+}
+template void launch_coarse_vcycle<float>(const CoarseSet<float>&, cudaStream_t);
+template void launch_coarse_vcycle<double>(const CoarseSet<double>&, cudaStream_t);
 
 // ------------------------------------------------------------ launchers
 #define GP_NV_SWITCH(X)                                                                                  \
