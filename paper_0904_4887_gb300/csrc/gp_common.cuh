@@ -116,7 +116,7 @@ template <typename T> void launch_update_p(const LV<T>& L, T* p, const T* z, con
 template <typename T> void launch_copy_level(const LV<T>& L, T* dst, const T* src, cudaStream_t s);
 
 // the bottom of a V-cycle in one CTA (k_mg.cu): levels l0 .. L-1
-constexpr int kCoarseBlockPoints = 32768;   // levels up to this size run in the persistent kernel
+constexpr int kCoarseBlockPoints = 4096;    // levels up to this size run in the persistent kernel
 template <typename T>
 struct CoarseSet {
     int l0, L, nc, nu1, nu2;

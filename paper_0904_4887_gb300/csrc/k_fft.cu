@@ -301,7 +301,7 @@ __device__ __forceinline__ Cx<T>* sstage(Cx<T>* A, Cx<T>* B, const Cx<T>* tw) {
             Cx<T> v[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                Cx<T> x = A[(j + r * NR) * M + l];
+                Cx<T> x = A[(j + r * NR) * (M + 1) + l];
                 if (r > 0 && kk > 0) {
                     Cx<T> w = tw[r * kk * tstep];
                     if (INV) w.im = -w.im;
@@ -333,7 +333,7 @@ __device__ __forceinline__ Cx<T>* sstage(Cx<T>* A, Cx<T>* B, const Cx<T>* tw) {
             }
             const int base = (j / Ns) * Ns * R + kk;
 #pragma unroll
-            for (int r = 0; r < R; ++r) B[(base + r * Ns) * M + l] = o[r];
+            for (int r = 0; r < R; ++r) B[(base + r * Ns) * (M + 1) + l] = o[r];
         }
         __syncthreads();
         return sstage<T, N, M, INV, ST + 1>(B, A, tw);
@@ -343,7 +343,7 @@ __device__ __forceinline__ Cx<T>* sstage(Cx<T>* A, Cx<T>* B, const Cx<T>* tw) {
 template <typename T, int N>
 constexpr int lines_static() {
     int m = 16;
-    while (m > 1 && 2 * N * m * (int)sizeof(Cx<T>) > 96 * 1024) m >>= 1;
+    while (m > 1 && 2 * N * (m + 1) * (int)sizeof(Cx<T>) > 100 * 1024) m >>= 1;
     return m;
 }
 
@@ -353,21 +353,21 @@ __global__ void __launch_bounds__(256) ks_x_fwd(Geo g, const T* tw, const T* src
     Cx<T>* sw = reinterpret_cast<Cx<T>*>(smem_raw);
     constexpr int nxh = N / 2 + 1;
     Cx<T>* A = sw + N;
-    Cx<T>* B = A + N * M;
+    Cx<T>* B = A + N * (M + 1);
     load_tw(sw, tw, N);
     const long rows = (long)g.ny * g.nz;
     const long row0 = (long)blockIdx.x * M;
     for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
         const int l = q / N, e = q % N;
         const long row = row0 + l;
-        A[e * M + l] = Cx<T>{row < rows ? src[row * N + e] : (T)0, (T)0};
+        A[e * (M + 1) + l] = Cx<T>{row < rows ? src[row * N + e] : (T)0, (T)0};
     }
     __syncthreads();
     Cx<T>* R = sstage<T, N, M, false, 0>(A, B, sw);
     for (int q = threadIdx.x; q < M * nxh; q += blockDim.x) {
         const int l = q / nxh, e = q % nxh;
         const long row = row0 + l;
-        if (row < rows) C[row * nxh + e] = R[e * M + l];
+        if (row < rows) C[row * nxh + e] = R[e * (M + 1) + l];
     }
 }
 
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(256) ks_x_inv(Geo g, const T* tw, const Cx<T>*
     Cx<T>* sw = reinterpret_cast<Cx<T>*>(smem_raw);
     constexpr int nxh = N / 2 + 1;
     Cx<T>* A = sw + N;
-    Cx<T>* B = A + N * M;
+    Cx<T>* B = A + N * (M + 1);
     load_tw(sw, tw, N);
     const long rows = (long)g.ny * g.nz;
     const long row0 = (long)blockIdx.x * M;
@@ -389,14 +389,14 @@ __global__ void __launch_bounds__(256) ks_x_inv(Geo g, const T* tw, const Cx<T>*
             if (e < nxh) v = C[row * nxh + e];
             else { v = C[row * nxh + (N - e)]; v.im = -v.im; }
         }
-        A[e * M + l] = v;
+        A[e * (M + 1) + l] = v;
     }
     __syncthreads();
     Cx<T>* R = sstage<T, N, M, true, 0>(A, B, sw);
     for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
         const int l = q / N, e = q % N;
         const long row = row0 + l;
-        if (row < rows) out[row * N + e] = R[e * M + l].re;
+        if (row < rows) out[row * N + e] = R[e * (M + 1) + l].re;
     }
 }
 
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(256) ks_y(Geo g, const T* tw, Cx<T>* C) {
     Cx<T>* sw = reinterpret_cast<Cx<T>*>(smem_raw);
     const int nxh = g.nx / 2 + 1;
     Cx<T>* A = sw + N;
-    Cx<T>* B = A + N * M;
+    Cx<T>* B = A + N * (M + 1);
     load_tw(sw, tw, N);
     const int nchunks = (nxh + M - 1) / M;
     const int kx0 = (blockIdx.x % nchunks) * M;
@@ -414,13 +414,13 @@ __global__ void __launch_bounds__(256) ks_y(Geo g, const T* tw, Cx<T>* C) {
     Cx<T>* base = C + k * (long)nxh * N;
     for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
         const int e = q / M, l = q % M;
-        A[e * M + l] = (kx0 + l < nxh) ? base[(long)e * nxh + kx0 + l] : Cx<T>{(T)0, (T)0};
+        A[e * (M + 1) + l] = (kx0 + l < nxh) ? base[(long)e * nxh + kx0 + l] : Cx<T>{(T)0, (T)0};
     }
     __syncthreads();
     Cx<T>* R = sstage<T, N, M, INV, 0>(A, B, sw);
     for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
         const int e = q / M, l = q % M;
-        if (kx0 + l < nxh) base[(long)e * nxh + kx0 + l] = R[e * M + l];
+        if (kx0 + l < nxh) base[(long)e * nxh + kx0 + l] = R[e * (M + 1) + l];
     }
 }
 
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) ks_z_solve(Geo g, const T* tw, const T* l
     Cx<T>* sw = reinterpret_cast<Cx<T>*>(smem_raw);
     const int nxh = g.nx / 2 + 1;
     Cx<T>* A = sw + N;
-    Cx<T>* B = A + N * M;
+    Cx<T>* B = A + N * (M + 1);
     load_tw(sw, tw, N);
     const int nchunks = (nxh + M - 1) / M;
     const int kx0 = (blockIdx.x % nchunks) * M;
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(256) ks_z_solve(Geo g, const T* tw, const T* l
     Cx<T>* base = C + (long)ky * nxh;
     for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
         const int e = q / M, l = q % M;
-        A[e * M + l] = (kx0 + l < nxh) ? base[e * zs + kx0 + l] : Cx<T>{(T)0, (T)0};
+        A[e * (M + 1) + l] = (kx0 + l < nxh) ? base[e * zs + kx0 + l] : Cx<T>{(T)0, (T)0};
     }
     __syncthreads();
     Cx<T>* R = sstage<T, N, M, false, 0>(A, B, sw);
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(256) ks_z_solve(Geo g, const T* tw, const T* l
     for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
         const int e = q / M, l = q % M;
         const int kx = kx0 + l;
-        Cx<T> v = R[e * M + l];
+        Cx<T> v = R[e * (M + 1) + l];
         if (kx < nxh) {
             const T lam = (lx[kx] + lyv + lz[e]) / inv_n;
             const T f = (kx == 0 && ky == 0 && e == 0) ? (T)0 : (T)1 / lam;
@@ -459,18 +459,18 @@ __global__ void __launch_bounds__(256) ks_z_solve(Geo g, const T* tw, const T* l
         } else {
             v = Cx<T>{(T)0, (T)0};
         }
-        R[e * M + l] = v;
+        R[e * (M + 1) + l] = v;
     }
     __syncthreads();
     Cx<T>* R2 = sstage<T, N, M, true, 0>(R, O, sw);
     for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
         const int e = q / M, l = q % M;
-        if (kx0 + l < nxh) base[e * zs + kx0 + l] = R2[e * M + l];
+        if (kx0 + l < nxh) base[e * zs + kx0 + l] = R2[e * (M + 1) + l];
     }
 }
 
 template <typename T, int N>
-constexpr size_t smem_static() { return (size_t)N * sizeof(Cx<T>) * (1 + 2 * (size_t)lines_static<T, N>()); }
+constexpr size_t smem_static() { return (size_t)N * sizeof(Cx<T>) * (1 + 2 * ((size_t)lines_static<T, N>() + 1)); }
 
 // one pass of axis `axis` (0 x-forward, 1 y-forward, 2 z-solve, 3 y-inverse, 4 x-inverse) with N
 // known at compile time; returns false if N has no static instance

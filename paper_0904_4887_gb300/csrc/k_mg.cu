@@ -97,6 +97,13 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// row kernels: one block per (j, k) row at a time, threads along x
+int row_threads(int nx) {
+    const int t = (nx + 31) / 32 * 32;
+    return t > 256 ? 256 : (t < 32 ? 32 : t);
+}
+int row_blocks(long rows) { return (int)(rows < 152L * 32 ? rows : 152L * 32); }
+
 int grid_for(long n, int threads) {
     long b = (n + threads - 1) / threads;
     return (int)(b < 152L * 16 ? (b < 1 ? 1 : b) : 152L * 16);
@@ -540,13 +547,12 @@ __global__ void k_band_eps(Geo g, const T* eps, int first, int band_nz, T* beps)
 template <typename T>
 __global__ void k_band_rhs(Geo g, const T* eps, const T* r, const T* ev, int first, int band_nz, T* fb) {
     const long pl = plane_of(g.nx, g.ny);
-    const long n = pl * band_nz;
     const T hx = (T)(0.5 / (g.hx * g.hx)), hy = (T)(0.5 / (g.hy * g.hy)), hz = (T)(0.5 / (g.hz * g.hz));
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        const int kb = (int)(t / pl);
-        const long q = t % pl;
+    for (long row = blockIdx.x; row < (long)g.ny * band_nz; row += gridDim.x)
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+        const int j = (int)(row % g.ny), kb = (int)(row / g.ny);
         const int k = (first + kb) % g.nz;
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const long t = kb * pl + (long)j * g.nx + i;
         const Nb nb = neighbours(g.nx, g.ny, g.nz, 1, i, j, k);
         const T e0 = eps[nb.c], p0 = ev[nb.c];
         const T ax = (e0 + eps[nb.xp]) * (ev[nb.xp] - p0) - (e0 + eps[nb.xm]) * (p0 - ev[nb.xm]);
@@ -609,15 +615,18 @@ __global__ void k_scale_by_norm(long n, const T* src, T* dst, const double* sq) 
 // z = e_vac, plus the band correction on the band planes
 template <typename T>
 __global__ void k_combine(Geo g, const T* ev, const T* eb, int first, int band_nz, T* z) {
-    const long n = (long)g.nx * g.ny * g.nz;
     const long pl = plane_of(g.nx, g.ny);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        T v = ev[t];
-        const int k = (int)(t / pl);
+    for (long row = blockIdx.x; row < (long)g.ny * g.nz; row += gridDim.x) {
+        const int j = (int)(row % g.ny), k = (int)(row / g.ny);
         int kb = k - first;
         if (kb < 0) kb += g.nz;
-        if (kb < band_nz) v += eb[t - k * pl + kb * pl];
-        z[t] = v;
+        const long t0 = k * pl + (long)j * g.nx;
+        const long b0 = kb * pl + (long)j * g.nx;
+        for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+            T v = ev[t0 + i];
+            if (kb < band_nz) v += eb[b0 + i];
+            z[t0 + i] = v;
+        }
     }
 }
 
@@ -813,8 +822,7 @@ template <typename T> void launch_scale_by_norm(long n, const T* src, T* dst, co
 }
 template <typename T> void launch_combine(const Geo& g, const T* ev, const T* eb, int first, int band_nz, T* z,
                                           cudaStream_t s) {
-    const long n = (long)g.nx * g.ny * g.nz;
-    k_combine<T><<<grid_for(n, 256), 256, 0, s>>>(g, ev, eb, first, band_nz, z);
+    k_combine<T><<<row_blocks((long)g.ny * g.nz), row_threads(g.nx), 0, s>>>(g, ev, eb, first, band_nz, z);
 }
 template <typename T> void launch_krylov_combine(long n, T* x, const TVecList<T>& Z, const double* y, cudaStream_t s) {
     k_krylov_combine<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, Z, y);
@@ -852,9 +860,6 @@ void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_ba
     const long n = (long)g.nx * g.ny * g.nz;
     k_update_phi<T><<<grid_for(n, 256), 256, 0, s>>>(g, phi, e_full, e_band, band_first, band_nz);
 }
-// row kernels: one block per (j, k) row at a time, threads along x
-int row_threads(int nx) { return nx >= 256 ? 256 : (nx >= 128 ? 128 : (nx > 32 ? 64 : 32)); }
-int row_blocks(long rows) { return (int)(rows < 152L * 32 ? rows : 152L * 32); }
 
 template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s) {
     const long rows = (long)L.ny * L.nz;
@@ -892,7 +897,7 @@ template <typename T> void launch_coarse_solve(const LV<T>& C, const T* inv, int
     k_coarse_solve<T><<<1, 512, 0, s>>>(C, inv, n, f, u);
 }
 template <typename T> void launch_applyA_dot(const LV<T>& L, const T* p, T* q, double* partial, cudaStream_t s) {
-    k_applyA_dot<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(L, p, q, partial);
+    k_applyA_dot<T><<<kReduceBlocks, row_threads(L.nx), 0, s>>>(L, p, q, partial);
 }
 template <typename T> void launch_dot(const LV<T>& L, const T* a, const T* b, double* partial, cudaStream_t s) {
     const long n = (long)L.nx * L.ny * L.nz;
@@ -922,8 +927,8 @@ template <typename T> void launch_band_eps(const Geo& g, const T* epsT, int firs
 }
 template <typename T> void launch_band_rhs(const Geo& g, const T* epsT, const T* r, const T* ev, int first,
                                            int band_nz, T* fb, cudaStream_t s) {
-    const long n = plane_of(g.nx, g.ny) * band_nz;
-    k_band_rhs<T><<<grid_for(n, 256), 256, 0, s>>>(g, epsT, r, ev, first, band_nz, fb);
+    const long rows = (long)g.ny * band_nz;
+    k_band_rhs<T><<<row_blocks(rows), row_threads(g.nx), 0, s>>>(g, epsT, r, ev, first, band_nz, fb);
 }
 
 #define GP_INST(T)                                                                                           \
