@@ -170,8 +170,8 @@ struct gp_ctx {
     int forces_cap = 0;
     double* gmat = nullptr;        // Gauss-Jordan workspace (2 * 512^2)
     double* sw_coef = nullptr;     // switching-function tables (2 * kSwNI * (kSwDeg+1))
-    double* gtab = nullptr;        // Gaussian factor tables [atom][2][3][3][nmax]
-    size_t gtab_cap = 0;
+    void* gtab = nullptr;          // periodized Gaussian factor tables (GaussTabs)
+    size_t gtab_cap = 0;           // bytes
     SwTables sw{};
 
     // solver state
@@ -275,16 +275,16 @@ void* dalloc(gp_ctx* c, size_t bytes) {
     return p;
 }
 
-double* ensure_gtab(gp_ctx* c, int n_atoms, int& nmax) {
-    nmax = std::max(c->g.nx, std::max(c->g.ny, c->g.nz));
-    const size_t need = (size_t)std::max(n_atoms, 1) * 18 * nmax;
+GaussTabs ensure_gtab(gp_ctx* c, int n_atoms) {
+    const int nmax = std::max(c->g.nx, std::max(c->g.ny, c->g.nz));
+    const size_t need = gauss_tabs_bytes(n_atoms, nmax);
     if (need > c->gtab_cap) {
         if (c->gtab) cudaFree(c->gtab);
         c->gtab = nullptr;
-        if (cudaMalloc(&c->gtab, sizeof(double) * need) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+        if (cudaMalloc(&c->gtab, need) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
         c->gtab_cap = need;
     }
-    return c->gtab;
+    return gauss_tabs_view(c->gtab, n_atoms, nmax);
 }
 
 double sum_host(gp_ctx* c, int ncomp, double* out) {
@@ -1029,9 +1029,7 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
     if (!(cell.lx > 0 && cell.ly > 0 && cell.lz > 0)) return GP_ERR_INVALID_ARG;
     gp_ctx* c = new gp_ctx();
     try {
-        c->g.nx = grid.nx; c->g.ny = grid.ny; c->g.nz = grid.nz;
-        c->g.lx = cell.lx; c->g.ly = cell.ly; c->g.lz = cell.lz;
-        c->g.hx = cell.lx / grid.nx; c->g.hy = cell.ly / grid.ny; c->g.hz = cell.lz / grid.nz;
+        c->g = make_geo(grid.nx, grid.ny, grid.nz, cell.lx, cell.ly, cell.lz);
         c->n = (long)grid.nx * grid.ny * grid.nz;
         c->s = reinterpret_cast<cudaStream_t>(cuda_stream);
         gp_default_params(&c->prm);
@@ -1097,7 +1095,7 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         }
         GP_CHECK_LAUNCH();
         Atoms at{c->atoms, c->atoms32, nullptr, n_atoms};
-        DielParams dp{p.eps0, p.r0, p.w, p.rcut};
+        const DielParams dp = make_diel(p.eps0, p.r0, p.w, p.rcut);
         // switching-function tables for these r0, w (when the tabulated range is away from d = 0)
         SwTables tb{};
         if (p.r0 - 4.0 * p.w > 0.0 && p.r0 + 6.0 * p.w <= p.rcut) {
@@ -1174,12 +1172,11 @@ gp_status gp_build_rho(gp_ctx* c, const double* atoms_dev, const double* gauss_d
             launch_wrap_atoms(c->g, atoms_dev, n_atoms, c->ratoms, c->ratoms32, c->s);
         }
         Atoms at{c->ratoms, c->ratoms32, gauss_dev, n_atoms};
-        int nmax = 0;
-        double* tab = ensure_gtab(c, n_atoms, nmax);
+        const GaussTabs gt = ensure_gtab(c, n_atoms);
         {
-            ProfScope ps(c, GP_PROF_RHO, 2);
-            launch_gauss_tables(c->g, at, cut, nmax, tab, c->s);
-            launch_build_rho_raw(c->g, at, cut, tab, nmax, rho_dev, c->s);
+            ProfScope ps(c, GP_PROF_RHO, n_atoms > 0 ? 2 : 1);
+            launch_gauss_tables(c->g, at, cut, gt, c->s);
+            launch_build_rho_raw(c->g, gt, rho_dev, c->s);
         }
         GP_CHECK_LAUNCH();
         {
@@ -1241,18 +1238,17 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
             GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->s));
             Atoms at{c->atoms, c->atoms32, gauss_dev, n};
-            DielParams dp{c->prm.eps0, c->prm.r0, c->prm.w, c->prm.rcut};
+            const DielParams dp = make_diel(c->prm.eps0, c->prm.r0, c->prm.w, c->prm.rcut);
             {
                 ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
                 launch_forces_eps(c->g, at, dp, c->sw, phi_dev, c->pe64, c->forces_S, c->s);
             }
             GP_CHECK_LAUNCH();
             if (gauss_dev) {
-                int nmax = 0;
-                double* tab = ensure_gtab(c, n, nmax);
+                const GaussTabs gt = ensure_gtab(c, n);
                 ProfScope ps(c, GP_PROF_FORCES_RHO, 2);
-                launch_gauss_tables(c->g, at, 8.0, nmax, tab, c->s);
-                launch_forces_rho(c->g, at, 8.0, tab, nmax, phi_dev, c->forces_T, c->s);
+                launch_gauss_tables(c->g, at, 8.0, gt, c->s);
+                launch_forces_rho(c->g, gt, phi_dev, c->forces_T, c->s);
             }
             GP_CHECK_LAUNCH();
             ProfScope ps(c, GP_PROF_MISC, 1);

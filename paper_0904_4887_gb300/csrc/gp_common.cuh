@@ -37,15 +37,45 @@ struct Atoms {
     int n;
 };
 
+// Grid geometry. The derived constants are filled on the host (make_geo):
+// an FP64 divide costs tens of FP64-pipe instructions, and the FP64 pipe is
+// 1/64 of the FP32 rate here, so no kernel derives them per thread.
 struct Geo {
     int nx, ny, nz;
     double hx, hy, hz;
     double lx, ly, lz;
+    double ihx, ihy, ihz;   // 1 / h
+    double c2x, c2y, c2z;   // 1 / (2 h^2): face-mean operator weight per axis
+    double inv_n;           // 1 / (nx ny nz)
 };
 
+inline Geo make_geo(int nx, int ny, int nz, double lx, double ly, double lz) {
+    Geo g{};
+    g.nx = nx; g.ny = ny; g.nz = nz;
+    g.lx = lx; g.ly = ly; g.lz = lz;
+    g.hx = lx / nx; g.hy = ly / ny; g.hz = lz / nz;
+    g.ihx = 1.0 / g.hx; g.ihy = 1.0 / g.hy; g.ihz = 1.0 / g.hz;
+    g.c2x = 0.5 / (g.hx * g.hx); g.c2y = 0.5 / (g.hy * g.hy); g.c2z = 0.5 / (g.hz * g.hz);
+    g.inv_n = 1.0 / ((double)nx * ny * nz);
+    return g;
+}
+
+// Dielectric parameters (Eq. 8 switching) with host-derived constants.
 struct DielParams {
     double eps0, r0, w, rcut;
+    double iw;        // 1 / w
+    double sp_norm;   // 1 / (w sqrt(pi)): ds/du prefactor
+    double tiny;      // product-below-which eps - 1 rounds away: 5.5e-17 / (eps0 - 1)
 };
+
+inline DielParams make_diel(double eps0, double r0, double w, double rcut) {
+    DielParams p{};
+    p.eps0 = eps0; p.r0 = r0; p.w = w; p.rcut = rcut;
+    p.iw = 1.0 / w;
+    p.sp_norm = 1.0 / (w * 1.7724538509055160273);
+    p.tiny = 5.5e-17 / (eps0 - 1.0 > 0.0 ? eps0 - 1.0 : 1.0);
+    return p;
+}
 
 __host__ __device__ inline long plane_of(int nx, int ny) { return (long)nx * ny; }
 
@@ -64,16 +94,24 @@ void launch_wrap_atoms(const Geo& g, const double* pos, int n, double* w64, floa
 void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, double* h_coef, cudaStream_t s);
 void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, double* eps64, double* pe64,
                       float* eps32, cudaStream_t s);
-void launch_gauss_tables(const Geo& g, Atoms at, double cut_sigmas, int nmax, double* tab, cudaStream_t s);
-void launch_build_rho_raw(const Geo& g, Atoms at, double cut_sigmas, const double* tab, int nmax, double* rho,
-                          cudaStream_t s);
+// Periodized 1D Gaussian factor tables (k_fields.cu), Gaussian ge = 2 atom + {0 core, 1 cloud}
+struct GaussTabs {
+    double* val;    // [G][3][nmax] X, Y, Z factors summed over the images -L, 0, +L
+    double* der;    // [G][3][nmax] the same times d / sigma^2 (centre derivative)
+    double* coef;   // [G] +-Z / (2 pi sigma^2)^(3/2)
+    int* win;       // [G][3][2] conservative index window of the unshifted image
+    int G, nmax;
+};
+size_t gauss_tabs_bytes(int n_atoms, int nmax);
+GaussTabs gauss_tabs_view(void* base, int n_atoms, int nmax);
+void launch_gauss_tables(const Geo& g, Atoms at, double cut_sigmas, const GaussTabs& gt, cudaStream_t s);
+void launch_build_rho_raw(const Geo& g, const GaussTabs& gt, double* rho, cudaStream_t s);
 void launch_plane_max(const Geo& g, const double* eps64, double* plane_max, cudaStream_t s);
 void launch_energy(const Geo& g, const double* rho, const double* phi, const double* eps64,
                    double* partial, cudaStream_t s);
 void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const double* phi,
                        const double* pe64, double* G, cudaStream_t s);
-void launch_forces_rho(const Geo& g, Atoms at, double cut_sigmas, const double* tab, int nmax, const double* phi,
-                       double* G, cudaStream_t s);
+void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, double* T, cudaStream_t s);
 void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,
                           cudaStream_t s);
 

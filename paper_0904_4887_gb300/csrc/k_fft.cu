@@ -235,7 +235,7 @@ __global__ void k_fft_z_solve(Geo g, AxisPlan ap, const T* tw, int M, const doub
     __syncthreads();
     Cx<T>* R = smem_fft<T, false>(A, B, N, M, ap, sw);
     Cx<T>* O = (R == A) ? B : A;
-    const double inv_n = 1.0 / ((double)g.nx * g.ny * g.nz);
+    const double inv_n = g.inv_n;
     for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
         const int e = q / M, l = q % M;
         const int kx = kx0 + l;
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(256) ks_z_solve(Geo g, const T* tw, const T* l
     Cx<T>* R = sstage<T, N, M, false, 0>(A, B, sw);
     Cx<T>* O = (R == A) ? B : A;
     // symbol in the working precision: 1/(lambda N) (no FP64 per element for FP32)
-    const T inv_n = (T)(1.0 / ((double)g.nx * g.ny * g.nz));
+    const T inv_n = (T)g.inv_n;
     const T lyv = ly[ky];
     for (int q = threadIdx.x; q < M * N; q += blockDim.x) {
         const int e = q / M, l = q % M;

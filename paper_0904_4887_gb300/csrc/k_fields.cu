@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p,
     const bool valid = i < g.nx && j < g.ny && k < g.nz;
     const double x = i * g.hx, y = j * g.hy, z = k * g.hz;
     const double rc2 = p.rcut * p.rcut;
-    const double iw = 1.0 / p.w;
-    const double tiny = 5.5e-17 / (p.eps0 - 1.0 > 0.0 ? p.eps0 - 1.0 : 1.0);
+    const double iw = p.iw;
+    const double tiny = p.tiny;
     const float rcf = (float)p.rcut + kMargin;
     double P = 1.0;
     for (int a0 = 0; a0 < at.n; a0 += ACH) {
@@ -248,157 +248,129 @@ __device__ __forceinline__ df df_add(df a, df b) {
 }
 
 // ----------------------------------------------------------------- Gaussian factor tables
-// One-dimensional factors of every Gaussian, exp(-(x_i - c)^2 / 2 sigma^2) with
-// c an image of the atom's coordinate along one axis (shift -L, 0, +L), zero
-// outside the 8 sigma window; indexed [atom][core/cloud][axis][image][i].
-// Tiles then read these instead of evaluating exp per tile.
-__device__ __forceinline__ long gtab_index(int a, int which, int axis, int img, int i, int nmax) {
-    return ((((long)a * 2 + which) * 3 + axis) * 3 + img) * nmax + i;
-}
+// A Gaussian truncated to the cube |x - c|, |y - c|, |z - c| < cut*sigma is a
+// product of three 1D factors, and so is each of its periodic images. The sum
+// over the 27 images (shifts -L, 0, +L per axis; enough while cut*sigma <= L)
+// is therefore the product of three PERIODIZED 1D factors
+//   X(i) = sum_{m=-1,0,1} [|d| < cut sigma] exp(-d^2 / 2 sigma^2),  d = x_i - c - m L,
+// and the derivative of the image sum with respect to the centre takes
+//   X'(i) = sum_m [|d| < cut sigma] exp(-d^2 / 2 sigma^2) d / sigma^2
+// in place of X on the differentiated axis (d g / d R = g (r - R) / sigma^2).
+// One entry per Gaussian then covers all its images.
+__device__ __forceinline__ long gt_row(int ge, int axis, int nmax) { return ((long)ge * 3 + axis) * nmax; }
 
-__global__ void k_gauss_tables(Geo g, Atoms at, double cut, int nmax, double* tab) {
-    const long total = (long)at.n * 2 * 3 * 3 * nmax;
+__global__ void k_gauss_tables(Geo g, Atoms at, double cut, GaussTabs gt) {
+    const long total = (long)gt.G * 3 * gt.nmax;
     for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(q % nmax);
-        long r = q / nmax;
-        const int img = (int)(r % 3); r /= 3;
-        const int axis = (int)(r % 3); r /= 3;
-        const int which = (int)(r % 2);
-        const int a = (int)(r / 2);
+        const int i = (int)(q % gt.nmax);
+        const int axis = (int)((q / gt.nmax) % 3);
+        const int ge = (int)(q / (3L * gt.nmax));
+        const int a = ge >> 1, which = ge & 1;
         const int n = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
-        double v = 0.0;
+        const double h = axis == 0 ? g.hx : (axis == 1 ? g.hy : g.hz);
+        const double L = axis == 0 ? g.lx : (axis == 1 ? g.ly : g.lz);
+        const double sg = at.gauss[3 * a + 1 + which];
+        const double c = at.w64[3 * a + axis];
+        const double rad = cut * sg;
+        double v = 0.0, dv = 0.0;
         if (i < n) {
-            const double h = axis == 0 ? g.hx : (axis == 1 ? g.hy : g.hz);
-            const double L = axis == 0 ? g.lx : (axis == 1 ? g.ly : g.lz);
-            const double sg = at.gauss[3 * a + 1 + which];
-            const double c = at.w64[3 * a + axis] + (img - 1) * L;
-            const double d = i * h - c;
-            if (fabs(d) < cut * sg) v = exp(-d * d / (2.0 * sg * sg));
+            const double i2s = 0.5 / (sg * sg);
+            for (int m = -1; m <= 1; ++m) {
+                const double d = i * h - (c + m * L);
+                if (fabs(d) < rad) {
+                    const double e = exp(-d * d * i2s);
+                    v += e;
+                    dv += e * d * (2.0 * i2s);
+                }
+            }
         }
-        tab[q] = v;
+        gt.val[q] = v;
+        gt.der[q] = dv;
+        if (i == 0) {
+            // conservative index window [lo, hi] of the image around c (unwrapped;
+            // the other images are its shifts by n)
+            const double ih = axis == 0 ? g.ihx : (axis == 1 ? g.ihy : g.ihz);
+            int lo = (int)floor((c - rad) * ih) - 1, hi = (int)ceil((c + rad) * ih) + 1;
+            if (hi - lo + 1 >= n) { lo = 0; hi = n - 1; }
+            gt.win[(ge * 3 + axis) * 2 + 0] = lo;
+            gt.win[(ge * 3 + axis) * 2 + 1] = hi;
+            if (axis == 0) {
+                const double Z = at.gauss[3 * a + 0];
+                const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
+                gt.coef[ge] = (which == 0 ? Z : -Z) * norm;
+            }
+        }
     }
 }
 
-// ----------------------------------------------------------------- rho
-// Separable Gaussians: g(r) = N exp(-dx^2/2s^2) exp(-dy^2/2s^2) exp(-dz^2/2s^2),
-// each factor zero outside |d| < cut*s. A tile tabulates the three 1D factors
-// per (atom, image, Gaussian) entry and every point then costs two products.
-// Entries whose largest value on the tile is below 1e-8 of their peak are
-// tabulated and summed in FP32 (their sum is far below FP64 rounding of the
-// total); the others in FP64.
-constexpr int RCH = 8;                  // atoms per chunk
-constexpr int RMAX = RCH * 27 * 2;      // entries per chunk
-constexpr int RSUB = 32;                // entries tabulated at a time
-constexpr double kTail = 1e-8;
-
-// largest exp(-d^2/2s^2) of a Gaussian centred at c over the tile box
-__device__ __forceinline__ double tile_peak(const Tile& t, const Geo& g, double cx, double cy, double cz, double sg) {
-    const double dx = fmax(fmax(t.i0 * g.hx - cx, cx - t.i1 * g.hx), 0.0);
-    const double dy = fmax(fmax(t.j0 * g.hy - cy, cy - t.j1 * g.hy), 0.0);
-    const double dz = fmax(fmax(t.k0 * g.hz - cz, cz - t.k1 * g.hz), 0.0);
-    return exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sg * sg));
+// does Gaussian ge touch the tile? (window intervals modulo n, per axis)
+__device__ __forceinline__ bool span_hits(int lo, int hi, int n, int t0, int t1) {
+    return (lo <= t1 && hi >= t0) || (lo + n <= t1 && hi + n >= t0) || (lo - n <= t1 && hi - n >= t0);
+}
+__device__ __forceinline__ bool gauss_hits_tile(const GaussTabs& gt, int ge, const Tile& t, const Geo& g) {
+    const int* w = gt.win + ge * 6;
+    return span_hits(w[0], w[1], g.nx, t.i0, t.i1) && span_hits(w[2], w[3], g.ny, t.j0, t.j1) &&
+           span_hits(w[4], w[5], g.nz, t.k0, t.k1);
 }
 
-__global__ void __launch_bounds__(TT) k_build_rho(Geo g, Atoms at, double cut, const double* __restrict__ tab,
-                                                  int nmax, double* rho) {
-    __shared__ double en[RMAX][5];      // cx, cy, cz, sigma, coefficient (near entries from the front,
-                                        //  FP32 tail entries from the back)
-    __shared__ int ekey[RMAX];          // (atom * 2 + which) * 27 + image
-    __shared__ df gx[RSUB][TX];
-    __shared__ double gy[RSUB][TY];
-    __shared__ double gz[RSUB][TZ];
-    __shared__ df gyz[RSUB][TY * TZ];
-    __shared__ float fx32[RSUB][TX];
-    __shared__ float fy32[RSUB][TY];
-    __shared__ float fz32[RSUB][TZ];
-    __shared__ int n64, n32;
+// s += a * b with the product formed exactly to ~2^-48 (df64) and the sum
+// compensated (Neumaier): the FP32 pipe does the work of an FP64 FMA.
+__device__ __forceinline__ void df_acc(float& s, float& c, df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float t = s + p;
+    const float z = t - s;
+    c += ((s - (t - z)) + (p - z)) + e;
+    s = t;
+}
+
+// ----------------------------------------------------------------- rho
+// rho~_ijk = sum_G coef_G X_G(i) Y_G(j) Z_G(k). A tile lists the Gaussians
+// whose windows reach it (one integer test per Gaussian), stages X for its 32
+// columns and the row weights coef Y(j) Z(k) for its 16 rows, and every point
+// then accumulates one compensated product per Gaussian.
+constexpr int RB = 64;                  // Gaussians staged at a time
+
+__global__ void __launch_bounds__(TT) k_build_rho(Geo g, GaussTabs gt, double* rho) {
+    __shared__ int ent[TT];
+    __shared__ df gx[RB][TX];
+    __shared__ df wyz[RB][TY * TZ];
+    __shared__ int ne;
     const Tile t = make_tile(g);
     const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
     const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
     const bool valid = i < g.nx && j < g.ny && k < g.nz;
-    df acc = {0.f, 0.f};
-    float acc32 = 0.f;
-    for (int a0 = 0; a0 < at.n; a0 += RCH) {
-        if (threadIdx.x == 0) { n64 = 0; n32 = 0; }
+    float s = 0.f, c = 0.f;
+    for (int g0 = 0; g0 < gt.G; g0 += TT) {
+        if (threadIdx.x == 0) ne = 0;
         __syncthreads();
-        const int na = min(RCH, at.n - a0);
-        for (int q = threadIdx.x; q < na * 54; q += TT) {
-            const int a = a0 + q / 54, r = q % 54, im = r % 27, which = r / 27;
-            const double sg = at.gauss[3 * a + 1 + which];
-            float fx, fy, fz;
-            image32(at.w32, a, im, g, fx, fy, fz);
-            const float rad = (float)(cut * sg) + kMargin;
-            if (box_dmax(t, fx, fy, fz) < rad) {
-                const double Z = at.gauss[3 * a + 0];
-                double cx, cy, cz;
-                image64(at.w64, a, im, g, cx, cy, cz);
-                const bool tail = tile_peak(t, g, cx, cy, cz, sg) < kTail;
-                const int s = tail ? RMAX - 1 - atomicAdd(&n32, 1) : atomicAdd(&n64, 1);
-                en[s][0] = cx; en[s][1] = cy; en[s][2] = cz; en[s][3] = sg;
-                const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
-                en[s][4] = (which == 0 ? Z : -Z) * norm;
-                ekey[s] = (a * 2 + which) * 27 + im;
-            }
-        }
+        const int q = g0 + threadIdx.x;
+        if (q < gt.G && gauss_hits_tile(gt, q, t, g)) ent[atomicAdd(&ne, 1)] = q;
         __syncthreads();
-        const int m64 = n64, m32 = n32;
-        for (int e0 = 0; e0 < m64; e0 += RSUB) {
-            const int ms = min(RSUB, m64 - e0);
-            for (int q = threadIdx.x; q < ms * (TX + TY + TZ); q += TT) {
-                const int e = q / (TX + TY + TZ), r = q % (TX + TY + TZ);
-                const int key = ekey[e0 + e];
-                const int im = key % 27, aw = key / 27;
-                const int a = aw / 2, which = aw % 2;
-                if (r < TX) {
-                    const int ii = t.i0 + r;
-                    gx[e][r] = df_from(ii < g.nx ? tab[gtab_index(a, which, 0, im % 3, ii, nmax)] : 0.0);
-                } else if (r < TX + TY) {
-                    const int rr = r - TX, jj = t.j0 + rr;
-                    gy[e][rr] = jj < g.ny ? en[e0 + e][4] * tab[gtab_index(a, which, 1, (im / 3) % 3, jj, nmax)] : 0.0;
-                } else {
-                    const int rr = r - TX - TY, kk = t.k0 + rr;
-                    gz[e][rr] = kk < g.nz ? tab[gtab_index(a, which, 2, im / 9, kk, nmax)] : 0.0;
-                }
+        const int m = ne;
+        for (int e0 = 0; e0 < m; e0 += RB) {
+            const int ms = min(RB, m - e0);
+            for (int r = threadIdx.x; r < ms * TX; r += TT) {
+                const int e = r / TX, ii = t.i0 + r % TX;
+                gx[e][r % TX] = df_from(ii < g.nx ? gt.val[gt_row(ent[e0 + e], 0, gt.nmax) + ii] : 0.0);
+            }
+            for (int r = threadIdx.x; r < ms * TY * TZ; r += TT) {
+                const int e = r / (TY * TZ), jj = t.j0 + (r % (TY * TZ)) / TZ, kk = t.k0 + r % TZ;
+                const int ge = ent[e0 + e];
+                const double w = (jj < g.ny && kk < g.nz)
+                                     ? gt.coef[ge] * gt.val[gt_row(ge, 1, gt.nmax) + jj] * gt.val[gt_row(ge, 2, gt.nmax) + kk]
+                                     : 0.0;
+                wyz[e][r % (TY * TZ)] = df_from(w);
             }
             __syncthreads();
-            for (int q = threadIdx.x; q < ms * TY * TZ; q += TT) {
-                const int e = q / (TY * TZ), r = q % (TY * TZ);
-                gyz[e][r] = df_from(gy[e][r / TZ] * gz[e][r % TZ]);
-            }
-            __syncthreads();
-            if (valid) {
-                for (int e = 0; e < ms; ++e) acc = df_add(acc, df_mul(gx[e][tx], gyz[e][ty * TZ + tz]));
-            }
-            __syncthreads();
-        }
-        for (int e0 = 0; e0 < m32; e0 += RSUB) {
-            const int ms = min(RSUB, m32 - e0);
-            for (int q = threadIdx.x; q < ms * (TX + TY + TZ); q += TT) {
-                const int e = q / (TX + TY + TZ), r = q % (TX + TY + TZ);
-                const int slot = RMAX - 1 - (e0 + e);
-                const int key = ekey[slot];
-                const int im = key % 27, aw = key / 27;
-                const int a = aw / 2, which = aw % 2;
-                if (r < TX) {
-                    const int ii = t.i0 + r;
-                    fx32[e][r] = ii < g.nx ? (float)tab[gtab_index(a, which, 0, im % 3, ii, nmax)] : 0.f;
-                } else if (r < TX + TY) {
-                    const int rr = r - TX, jj = t.j0 + rr;
-                    fy32[e][rr] = jj < g.ny ? (float)(en[slot][4] * tab[gtab_index(a, which, 1, (im / 3) % 3, jj, nmax)])
-                                            : 0.f;
-                } else {
-                    const int rr = r - TX - TY, kk = t.k0 + rr;
-                    fz32[e][rr] = kk < g.nz ? (float)tab[gtab_index(a, which, 2, im / 9, kk, nmax)] : 0.f;
-                }
-            }
-            __syncthreads();
-            if (valid) {
-                for (int e = 0; e < ms; ++e) acc32 = fmaf(fx32[e][tx] * fy32[e][ty], fz32[e][tz], acc32);
-            }
+            if (valid)
+                for (int e = 0; e < ms; ++e) df_acc(s, c, gx[e][tx], wyz[e][ty * TZ + tz]);
             __syncthreads();
         }
     }
-    if (valid) rho[i + (long)g.nx * (j + (long)g.ny * k)] = df_to(acc) + (double)acc32;
+    if (valid) rho[i + (long)g.nx * (j + (long)g.ny * k)] = (double)s + (double)c;
 }
 
 // ----------------------------------------------------------------- dry planes
@@ -424,7 +396,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_energy(Geo g, const double* 
     __shared__ double red[2][kReduceThreads];
     const long n = (long)g.nx * g.ny * g.nz;
     const long pl = plane_of(g.nx, g.ny);
-    const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, ihz = 1.0 / g.hz;
+    const double ihx = g.ihx, ihy = g.ihy, ihz = g.ihz;
     double s0 = 0.0, s1 = 0.0;
     for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
         const int i = (int)(c % g.nx);
@@ -486,16 +458,16 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
             const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
             const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
             const double p0 = phi[c];
-            const double ax = (phi[xp] - p0) / g.hx, bx = (p0 - phi[xm]) / g.hx;
-            const double ay = (phi[yp] - p0) / g.hy, by = (p0 - phi[ym]) / g.hy;
-            const double az = (phi[zp] - p0) / g.hz, bz = (p0 - phi[zm]) / g.hz;
-            W = 0.5 * (ax * ax + bx * bx + ay * ay + by * by + az * az + bz * bz) * pe64[c];
+            const double ax = phi[xp] - p0, bx = p0 - phi[xm];
+            const double ay = phi[yp] - p0, by = p0 - phi[ym];
+            const double az = phi[zp] - p0, bz = p0 - phi[zm];
+            W = ((ax * ax + bx * bx) * g.c2x + (ay * ay + by * by) * g.c2y + (az * az + bz * bz) * g.c2z) * pe64[c];
         }
         Ws[threadIdx.x] = W;   // index tx + TX (ty + TY tz)
     }
     const double rc2 = p.rcut * p.rcut;
-    const double iw = 1.0 / p.w;
-    const double sp_norm = 1.0 / (p.w * sqrt(kPi));
+    const double iw = p.iw;
+    const double sp_norm = p.sp_norm;
     const float rcf = (float)p.rcut + kMargin;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int a0 = 0; a0 < at.n; a0 += ACH) {
@@ -555,113 +527,70 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
     }
 }
 
-// charge part: T_a = sum_i phi_i d rho~_i / d R_a with d g / d R = g (r - c)/sigma^2.
-// One warp per (atom, image, Gaussian) entry, lanes along x; the y and z
-// factors are separable, so each lane first sums its column over the 16
-// (y, z) rows. Entries below 1e-8 of their peak on the tile run in FP32.
-__global__ void __launch_bounds__(TT) k_forces_rho(Geo g, Atoms at, double cut, const double* __restrict__ tab,
-                                                   int nmax, const double* phi, double* T) {
-    __shared__ double en[RMAX][5];
-    __shared__ int eatom[RMAX];
-    __shared__ int ekey[RMAX];
-    __shared__ double ph[TT];
+// charge part: T_a = sum_i phi_i d rho~_i / d R_a. With the periodized factors,
+// T_x = coef sum_i X'(i) sum_(j,k) phi_ijk Y(j) Z(k), and likewise for y and z.
+// One warp per (tile, Gaussian): lanes along x; each lane sums its column of
+// 16 (j, k) rows against the three row weights coef {Y Z, Y' Z, Y Z'} (held
+// per warp in shared memory), then scales by X' or X and the warp reduces.
+__global__ void __launch_bounds__(TT) k_forces_rho(Geo g, GaussTabs gt, const double* phi, double* T) {
+    __shared__ int ent[TT];
+    __shared__ df ph[TT];                       // index tx + TX (ty + TY tz)
+    __shared__ df wr[TT / 32][3][TY * TZ];
     __shared__ int ne;
     const Tile t = make_tile(g);
     {
         const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
         const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
-        ph[threadIdx.x] = (i < g.nx && j < g.ny && k < g.nz) ? phi[i + (long)g.nx * (j + (long)g.ny * k)] : 0.0;
+        ph[threadIdx.x] = df_from((i < g.nx && j < g.ny && k < g.nz) ? phi[i + (long)g.nx * (j + (long)g.ny * k)] : 0.0);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = t.i0 + lane;
     const bool lane_ok = i < g.nx;
-    for (int a0 = 0; a0 < at.n; a0 += RCH) {
+    for (int g0 = 0; g0 < gt.G; g0 += TT) {
         if (threadIdx.x == 0) ne = 0;
         __syncthreads();
-        const int na = min(RCH, at.n - a0);
-        for (int q = threadIdx.x; q < na * 54; q += TT) {
-            const int a = a0 + q / 54, r = q % 54, im = r % 27, which = r / 27;
-            const double sg = at.gauss[3 * a + 1 + which];
-            float fx, fy, fz;
-            image32(at.w32, a, im, g, fx, fy, fz);
-            const float rad = (float)(cut * sg) + kMargin;
-            if (box_dmax(t, fx, fy, fz) < rad) {
-                const double Z = at.gauss[3 * a + 0];
-                const int s = atomicAdd(&ne, 1);
-                image64(at.w64, a, im, g, en[s][0], en[s][1], en[s][2]);
-                en[s][3] = sg;
-                const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
-                en[s][4] = (which == 0 ? Z : -Z) * norm / (sg * sg);
-                eatom[s] = a;
-                ekey[s] = (a * 2 + which) * 27 + im;
-            }
-        }
+        const int q = g0 + threadIdx.x;
+        if (q < gt.G && gauss_hits_tile(gt, q, t, g)) ent[atomicAdd(&ne, 1)] = q;
         __syncthreads();
         const int m = ne;
         for (int e = warp; e < m; e += TT / 32) {
-            const double cx = en[e][0], cy = en[e][1], cz = en[e][2], sg = en[e][3], coef = en[e][4];
-            const double rad = cut * sg;
-            const double i2s = 1.0 / (2.0 * sg * sg);
-            const int key = ekey[e], im = key % 27, aw = key / 27, ea = aw / 2, ew = aw % 2;
-            // this lane's x factor and the 8 y / z factors, from the tables
-            const double gxt = lane_ok ? tab[gtab_index(ea, ew, 0, im % 3, i, nmax)] : 0.0;
-            double gyz_t = 0.0;
-            if (lane < TY && t.j0 + lane < g.ny) gyz_t = tab[gtab_index(ea, ew, 1, (im / 3) % 3, t.j0 + lane, nmax)];
-            else if (lane >= TY && lane < TY + TZ && t.k0 + lane - TY < g.nz)
-                gyz_t = tab[gtab_index(ea, ew, 2, im / 9, t.k0 + lane - TY, nmax)];
-            (void)rad; (void)i2s;
-            double fx = 0.0, fy = 0.0, fz = 0.0;
-            if (tile_peak(t, g, cx, cy, cz, sg) < kTail) {
-                // FP32: lane < 8 tabulates one y or z factor, shared by shuffles
-                float d_v = 0.f;
-                if (lane < TY) d_v = (float)((t.j0 + lane) * g.hy - cy);
-                else if (lane < TY + TZ) d_v = (float)((t.k0 + lane - TY) * g.hz - cz);
-                const float gyz_v = (float)gyz_t;
-                const float dxf = (float)(i * g.hx - cx);
-                const float gxf = (float)gxt;
-                float s0 = 0.f, sy = 0.f, sz = 0.f;
-                for (int tz = 0; tz < TZ; ++tz) {
-                    const float gz = __shfl_sync(0xffffffffu, gyz_v, TY + tz);
-                    const float dz = __shfl_sync(0xffffffffu, d_v, TY + tz);
-                    for (int ty = 0; ty < TY; ++ty) {
-                        const float gy = __shfl_sync(0xffffffffu, gyz_v, ty);
-                        const float dy = __shfl_sync(0xffffffffu, d_v, ty);
-                        const float v = (float)ph[lane + TX * (ty + TY * tz)] * gy * gz;
-                        s0 += v; sy += v * dy; sz += v * dz;
-                    }
+            const int ge = ent[e];
+            if (lane < TY * TZ) {
+                const int jj = t.j0 + lane / TZ, kk = t.k0 + lane % TZ;
+                double w0 = 0.0, wy = 0.0, wz = 0.0;
+                if (jj < g.ny && kk < g.nz) {
+                    const double cf = gt.coef[ge];
+                    const double Y = gt.val[gt_row(ge, 1, gt.nmax) + jj], Yd = gt.der[gt_row(ge, 1, gt.nmax) + jj];
+                    const double Z = gt.val[gt_row(ge, 2, gt.nmax) + kk], Zd = gt.der[gt_row(ge, 2, gt.nmax) + kk];
+                    w0 = cf * Y * Z; wy = cf * Yd * Z; wz = cf * Y * Zd;
                 }
-                fx = coef * (double)(dxf * gxf * s0);
-                fy = coef * (double)(gxf * sy);
-                fz = coef * (double)(gxf * sz);
-            } else {
-                double d_v = 0.0;
-                if (lane < TY) d_v = (t.j0 + lane) * g.hy - cy;
-                else if (lane < TY + TZ) d_v = (t.k0 + lane - TY) * g.hz - cz;
-                const double gyz_v = gyz_t;
-                const double dx = i * g.hx - cx;
-                const double gx = gxt;
-                double s0 = 0.0, sy = 0.0, sz = 0.0;
-                for (int tz = 0; tz < TZ; ++tz) {
-                    const double gz = __shfl_sync(0xffffffffu, gyz_v, TY + tz);
-                    const double dz = __shfl_sync(0xffffffffu, d_v, TY + tz);
-                    for (int ty = 0; ty < TY; ++ty) {
-                        const double gy = __shfl_sync(0xffffffffu, gyz_v, ty);
-                        const double dy = __shfl_sync(0xffffffffu, d_v, ty);
-                        const double v = ph[lane + TX * (ty + TY * tz)] * gy * gz;
-                        s0 += v; sy += v * dy; sz += v * dz;
-                    }
-                }
-                fx = coef * dx * gx * s0;
-                fy = coef * gx * sy;
-                fz = coef * gx * sz;
+                wr[warp][0][lane] = df_from(w0);
+                wr[warp][1][lane] = df_from(wy);
+                wr[warp][2][lane] = df_from(wz);
             }
+            __syncwarp();
+            const double X = lane_ok ? gt.val[gt_row(ge, 0, gt.nmax) + i] : 0.0;
+            const double Xd = lane_ok ? gt.der[gt_row(ge, 0, gt.nmax) + i] : 0.0;
+            float s0 = 0.f, c0 = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+#pragma unroll 4
+            for (int r = 0; r < TY * TZ; ++r) {
+                // row r = ty * TZ + tz holds phi at index lane + TX (ty + TY tz)
+                const df p = ph[lane + TX * (r / TZ + TY * (r % TZ))];
+                df_acc(s0, c0, p, wr[warp][0][r]);
+                df_acc(sy, cy, p, wr[warp][1][r]);
+                df_acc(sz, cz, p, wr[warp][2][r]);
+            }
+            double fx = Xd * ((double)s0 + (double)c0);
+            double fy = X * ((double)sy + (double)cy);
+            double fz = X * ((double)sz + (double)cz);
             fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
             if (lane == 0) {
-                const int a = eatom[e];
+                const int a = ge >> 1;
                 if (fx != 0.0) atomicAdd(&T[3 * a + 0], fx);
                 if (fy != 0.0) atomicAdd(&T[3 * a + 1], fy);
                 if (fz != 0.0) atomicAdd(&T[3 * a + 2], fz);
             }
+            __syncwarp();
         }
         __syncthreads();
     }
@@ -691,15 +620,32 @@ void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, 
     k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
 }
 
-void launch_gauss_tables(const Geo& g, Atoms at, double cut, int nmax, double* tab, cudaStream_t s) {
-    const long total = (long)at.n * 18 * nmax;
-    if (total > 0) k_gauss_tables<<<(int)((total + 255) / 256 < 152L * 64 ? (total + 255) / 256 : 152L * 64), 256, 0, s>>>(
-        g, at, cut, nmax, tab);
+size_t gauss_tabs_bytes(int n_atoms, int nmax) {
+    const size_t G = 2 * (size_t)(n_atoms > 0 ? n_atoms : 1);
+    return sizeof(double) * (2 * G * 3 * nmax + G) + sizeof(int) * G * 6 + 64;
 }
 
-void launch_build_rho_raw(const Geo& g, Atoms at, double cut, const double* tab, int nmax, double* rho,
-                          cudaStream_t s) {
-    k_build_rho<<<tile_grid(g), TT, 0, s>>>(g, at, cut, tab, nmax, rho);
+GaussTabs gauss_tabs_view(void* base, int n_atoms, int nmax) {
+    GaussTabs gt{};
+    gt.G = 2 * n_atoms;
+    gt.nmax = nmax;
+    const size_t G = 2 * (size_t)(n_atoms > 0 ? n_atoms : 1);
+    double* d = static_cast<double*>(base);
+    gt.val = d;
+    gt.der = d + G * 3 * nmax;
+    gt.coef = d + 2 * G * 3 * nmax;
+    gt.win = reinterpret_cast<int*>(d + 2 * G * 3 * nmax + G);
+    return gt;
+}
+
+void launch_gauss_tables(const Geo& g, Atoms at, double cut, const GaussTabs& gt, cudaStream_t s) {
+    const long total = (long)gt.G * 3 * gt.nmax;
+    if (total > 0) k_gauss_tables<<<(int)((total + 255) / 256 < 152L * 64 ? (total + 255) / 256 : 152L * 64), 256, 0, s>>>(
+        g, at, cut, gt);
+}
+
+void launch_build_rho_raw(const Geo& g, const GaussTabs& gt, double* rho, cudaStream_t s) {
+    k_build_rho<<<tile_grid(g), TT, 0, s>>>(g, gt, rho);
 }
 
 void launch_plane_max(const Geo& g, const double* eps64, double* out, cudaStream_t s) {
@@ -716,9 +662,8 @@ void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb,
     k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
 }
 
-void launch_forces_rho(const Geo& g, Atoms at, double cut, const double* tab, int nmax, const double* phi,
-                       double* T, cudaStream_t s) {
-    k_forces_rho<<<tile_grid(g), TT, 0, s>>>(g, at, cut, tab, nmax, phi, T);
+void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, double* T, cudaStream_t s) {
+    if (gt.G > 0) k_forces_rho<<<tile_grid(g), TT, 0, s>>>(g, gt, phi, T);
 }
 
 void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,

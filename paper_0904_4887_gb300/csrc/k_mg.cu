@@ -420,7 +420,11 @@ __global__ void k_dot(long n, const T* a, const T* b, double* partial) {
 
 template <typename T>
 __global__ void k_update_xr(long n, T* x, T* r, const T* p, const T* q, const double* scal, int num, int den) {
-    const T alpha = (T)(scal[num] / scal[den]);
+    // one FP64 divide per block, not per thread
+    __shared__ T alpha_s;
+    if (threadIdx.x == 0) alpha_s = (T)(scal[num] / scal[den]);
+    __syncthreads();
+    const T alpha = alpha_s;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         x[t] += alpha * p[t];
         r[t] -= alpha * q[t];
@@ -429,7 +433,10 @@ __global__ void k_update_xr(long n, T* x, T* r, const T* p, const T* q, const do
 
 template <typename T>
 __global__ void k_update_p(long n, T* p, const T* z, const double* scal, int num, int den) {
-    const T beta = (T)(scal[num] / scal[den]);
+    __shared__ T beta_s;
+    if (threadIdx.x == 0) beta_s = (T)(scal[num] / scal[den]);
+    __syncthreads();
+    const T beta = beta_s;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
         p[t] = z[t] + beta * p[t];
 }
@@ -483,7 +490,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_residual64(Geo g, const doub
                                                                const double* eps, T* r_out, double* partial) {
     __shared__ double red[32];
     const long n = (long)g.nx * g.ny * g.nz;
-    const double hx = 0.5 / (g.hx * g.hx), hy = 0.5 / (g.hy * g.hy), hz = 0.5 / (g.hz * g.hz);
+    const double hx = g.c2x, hy = g.c2y, hz = g.c2z;
     const double fpi = 4.0 * kPi;
     double s2 = 0.0, sp = 0.0;
     (void)n;
@@ -547,7 +554,7 @@ __global__ void k_band_eps(Geo g, const T* eps, int first, int band_nz, T* beps)
 template <typename T>
 __global__ void k_band_rhs(Geo g, const T* eps, const T* r, const T* ev, int first, int band_nz, T* fb) {
     const long pl = plane_of(g.nx, g.ny);
-    const T hx = (T)(0.5 / (g.hx * g.hx)), hy = (T)(0.5 / (g.hy * g.hy)), hz = (T)(0.5 / (g.hz * g.hz));
+    const T hx = (T)g.c2x, hy = (T)g.c2y, hz = (T)g.c2z;
     for (long row = blockIdx.x; row < (long)g.ny * band_nz; row += gridDim.x)
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
         const int j = (int)(row % g.ny), kb = (int)(row / g.ny);
@@ -607,7 +614,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_multiaxpy_norm(long n, T* __
 // dst = src / sqrt(*sq)
 template <typename T>
 __global__ void k_scale_by_norm(long n, const T* src, T* dst, const double* sq) {
-    const T f = (T)(1.0 / sqrt(sq[0]));
+    __shared__ T f_s;
+    if (threadIdx.x == 0) f_s = (T)(1.0 / sqrt(sq[0]));
+    __syncthreads();
+    const T f = f_s;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
         dst[t] = src[t] * f;
 }

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_residual64_planes(Geo g, const double* 
     __shared__ double red[2][256];
     const int k = blockIdx.x;
     const long pl = (long)g.nx * g.ny;
-    const double hx = 0.5 / (g.hx * g.hx), hy = 0.5 / (g.hy * g.hy), hz = 0.5 / (g.hz * g.hz);
+    const double hx = g.c2x, hy = g.c2y, hz = g.c2z;
     const double fpi = 4.0 * kPi;
     const long zm = (k == 0 ? (long)(g.nz - 1) : -1L) * pl;
     const long zp = (k == g.nz - 1 ? -(long)(g.nz - 1) : 1L) * pl;
@@ -117,10 +117,7 @@ extern "C" gp_status gp_residual_noalloc(gp_grid grid, gp_cell cell, const doubl
     if (!(cell.lx > 0 && cell.ly > 0 && cell.lz > 0)) return GP_ERR_INVALID_ARG;
     double* scratch = nullptr;
     if (scratch_address(&scratch) != cudaSuccess) return GP_ERR_CUDA;
-    Geo g{};
-    g.nx = grid.nx; g.ny = grid.ny; g.nz = grid.nz;
-    g.lx = cell.lx; g.ly = cell.ly; g.lz = cell.lz;
-    g.hx = cell.lx / grid.nx; g.hy = cell.ly / grid.ny; g.hz = cell.lz / grid.nz;
+    const Geo g = make_geo(grid.nx, grid.ny, grid.nz, cell.lx, cell.ly, cell.lz);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     k_residual64_planes<<<grid.nz, 256, 0, s>>>(g, phi_dev, rho_dev, eps_dev, r_dev, scratch);
     k_noalloc_finish<<<1, 256, 0, s>>>(grid.nz, scratch, rel_dev);
