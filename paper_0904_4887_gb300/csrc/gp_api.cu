@@ -170,6 +170,7 @@ struct gp_ctx {
     int forces_cap = 0;
     double* gmat = nullptr;        // Gauss-Jordan workspace (2 * 512^2)
     double* sw_coef = nullptr;     // switching-function tables (2 * kSwNI * (kSwDeg+1))
+    float4* sw_pack = nullptr;     // their packed FP32 copies (2 * kSwNI * 4)
     void* gtab = nullptr;          // periodized Gaussian factor tables (GaussTabs)
     size_t gtab_cap = 0;           // bytes
     SwTables sw{};
@@ -1042,6 +1043,7 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
         c->dstatus = (int*)dalloc(c, sizeof(int) * 4);
         c->gmat = (double*)dalloc(c, sizeof(double) * 2 * kMaxCoarse * kMaxCoarse);
         c->sw_coef = (double*)dalloc(c, sizeof(double) * 2 * kSwNI * (kSwDeg + 1));
+        c->sw_pack = (float4*)dalloc(c, sizeof(float4) * 2 * kSwNI * 4);
         rb_sweep_init();
         GP_CUDA(cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking));
         GP_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
@@ -1101,14 +1103,19 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         if (p.r0 - 4.0 * p.w > 0.0 && p.r0 + 6.0 * p.w <= p.rcut) {
             tb.s = c->sw_coef;
             tb.h = c->sw_coef + (size_t)kSwNI * (kSwDeg + 1);
+            tb.s32 = c->sw_pack;
+            tb.h32 = c->sw_pack + (size_t)kSwNI * 4;
             tb.s_qlo = (p.r0 - 4.0 * p.w) * (p.r0 - 4.0 * p.w);
             tb.s_qhi = (p.r0 + 6.0 * p.w) * (p.r0 + 6.0 * p.w);
             tb.s_inv_dq = kSwNI / (tb.s_qhi - tb.s_qlo);
+            tb.s_dq = (tb.s_qhi - tb.s_qlo) / kSwNI;
             tb.h_qlo = (p.r0 - 3.5 * p.w) * (p.r0 - 3.5 * p.w);
             tb.h_qhi = (p.r0 + 3.5 * p.w) * (p.r0 + 3.5 * p.w);
             tb.h_inv_dq = kSwNI / (tb.h_qhi - tb.h_qlo);
+            tb.h_dq = (tb.h_qhi - tb.h_qlo) / kSwNI;
             ProfScope ps(c, GP_PROF_EPS, 1);
-            launch_switch_tables(dp, tb, c->sw_coef, c->sw_coef + (size_t)kSwNI * (kSwDeg + 1), c->s);
+            launch_switch_tables(dp, tb, c->sw_coef, c->sw_coef + (size_t)kSwNI * (kSwDeg + 1), c->sw_pack,
+                                 c->sw_pack + (size_t)kSwNI * 4, c->s);
         }
         c->sw = tb;
         {

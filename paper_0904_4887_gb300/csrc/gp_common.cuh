@@ -81,17 +81,24 @@ __host__ __device__ inline long plane_of(int nx, int ny) { return (long)nx * ny;
 
 // switching-function tables (k_fields.cu): s and h = s'/(s d) as polynomials in q = d^2
 constexpr int kSwNI = 256, kSwDeg = 9;
+// Packed FP32 copies, 16 floats per interval: the low-degree coefficients
+// (below kSwSplitS for s, kSwSplitH for h) as hi/lo pairs, then the rest as
+// single floats (they are small enough that FP32 leaves < 1e-14 relative).
+constexpr int kSwSplitS = 4, kSwSplitH = 6;
 struct SwTables {
     const double* s = nullptr;    // kSwNI x (kSwDeg+1) monomial coefficients, or null (use erfc)
     const double* h = nullptr;
-    double s_qlo = 0, s_qhi = 0, s_inv_dq = 0;
-    double h_qlo = 0, h_qhi = 0, h_inv_dq = 0;
+    const float4* s32 = nullptr;  // kSwNI x 4 packed (see above)
+    const float4* h32 = nullptr;
+    double s_qlo = 0, s_qhi = 0, s_inv_dq = 0, s_dq = 0;
+    double h_qlo = 0, h_qhi = 0, h_inv_dq = 0, h_dq = 0;
 };
 
 // ---------------------------------------------------------------- launchers
 // fields (k_fields.cu)
 void launch_wrap_atoms(const Geo& g, const double* pos, int n, double* w64, float4* w32, cudaStream_t s);
-void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, double* h_coef, cudaStream_t s);
+void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, double* h_coef, float4* s_pack,
+                          float4* h_pack, cudaStream_t s);
 void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, double* eps64, double* pe64,
                       float* eps32, cudaStream_t s);
 // Periodized 1D Gaussian factor tables (k_fields.cu), Gaussian ge = 2 atom + {0 core, 1 cloud}

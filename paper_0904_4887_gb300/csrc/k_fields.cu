@@ -67,14 +67,6 @@ __device__ __forceinline__ float box_d2(const Tile& t, float cx, float cy, float
     return dx * dx + dy * dy + dz * dz;
 }
 
-// largest per-axis distance from c to the box (FP32)
-__device__ __forceinline__ float box_dmax(const Tile& t, float cx, float cy, float cz) {
-    float dx = fmaxf(fmaxf(t.bx0 - cx, cx - t.bx1), 0.f);
-    float dy = fmaxf(fmaxf(t.by0 - cy, cy - t.by1), 0.f);
-    float dz = fmaxf(fmaxf(t.bz0 - cz, cz - t.bz1), 0.f);
-    return fmaxf(dx, fmaxf(dy, dz));
-}
-
 // ----------------------------------------------------------------- switching-function tables
 // s(d) = erfc((r0 - d)/w)/2 and h(d) = s'(d)/(s(d) d) tabulated as functions
 // of q = d^2 (no square root per pair): kSwNI equal intervals in q, on each a
@@ -86,13 +78,14 @@ __device__ __forceinline__ float box_dmax(const Tile& t, float cx, float cy, flo
 // 5e-15 relative for s on q in [(r0-4w)^2, (r0+6w)^2] and for h on
 // [(r0-3.5w)^2, (r0+3.5w)^2]; outside those ranges the kernels use exact
 // forms (s = 1, or FP32 special functions on terms below 1e-8).
-__global__ void k_switch_tables(DielParams p, SwTables tb, double* s_coef, double* h_coef) {
+__global__ void k_switch_tables(DielParams p, SwTables tb, double* s_coef, double* h_coef, float4* s_pack,
+                                float4* h_pack) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 2 * kSwNI) return;
     const bool is_h = k >= kSwNI;
     const int iv = is_h ? k - kSwNI : k;
     const double qlo = is_h ? tb.h_qlo : tb.s_qlo;
-    const double dq = 1.0 / (is_h ? tb.h_inv_dq : tb.s_inv_dq);
+    const double dq = is_h ? tb.h_dq : tb.s_dq;
     constexpr int n = kSwDeg + 1;
     double fv[n], c[n];
     for (int j = 0; j < n; ++j) {
@@ -123,6 +116,18 @@ __global__ void k_switch_tables(DielParams p, SwTables tb, double* s_coef, doubl
     }
     double* out = (is_h ? h_coef : s_coef) + (long)iv * n;
     for (int e = 0; e < n; ++e) out[e] = mono[e];
+    float pk[16];
+    const int split = is_h ? kSwSplitH : kSwSplitS;
+    int o = 0;
+    for (int e = 0; e < split; ++e) {
+        const float hi = (float)mono[e];
+        pk[o++] = hi;
+        pk[o++] = (float)(mono[e] - (double)hi);
+    }
+    for (int e = split; e < n; ++e) pk[o++] = (float)mono[e];
+    while (o < 16) pk[o++] = 0.f;
+    float4* dst = (is_h ? h_pack : s_pack) + 4L * iv;
+    for (int v = 0; v < 4; ++v) dst[v] = make_float4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
 }
 
 __device__ __forceinline__ double sw_eval(const double* __restrict__ coef, double qlo, double inv_dq, double q) {
@@ -245,6 +250,11 @@ __device__ __forceinline__ df df_add(df a, df b) {
     float e = (a.hi - (s - v)) + (b.hi - v);
     e += a.lo + b.lo;
     return df_quick(s, e);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // ----------------------------------------------------------------- Gaussian factor tables
@@ -373,6 +383,286 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, GaussTabs gt, double* r
     if (valid) rho[i + (long)g.nx * (j + (long)g.ny * k)] = (double)s + (double)c;
 }
 
+// ----------------------------------------------------------------- switching function in df64
+// The table coordinate of a pair, x = (d^2 - q_lo) / dq, is separable:
+// d^2 = dx^2 + dy^2 + dz^2, so x = X(i) + Y(j) + Z(k) with X = (dx^2 - q_lo)/dq,
+// Y = dy^2/dq, Z = dz^2/dq per column / row of the tile, formed once per
+// (tile, atom image) in FP64. Each is kept as an integer part and a fraction
+// in [0, 1) held as a df (exact to 2^-48 absolute), so a pair costs two integer
+// and two df additions and the interval index needs no FP64 at all.
+struct SwCoord {
+    int n;      // integer part
+    df f;       // fraction in [0, 1)
+};
+
+__device__ __forceinline__ SwCoord sw_coord(double v) {
+    const double fl = floor(v);
+    SwCoord c;
+    c.n = (int)fl;
+    c.f = df_from(v - fl);
+    return c;
+}
+
+// interval k and local variable t = 2 (x - k) - 1 in [-1, 1] (as a df) of
+// x = n + f, f in [0, 3)
+__device__ __forceinline__ int sw_local(int n, df f, df& t) {
+    int kk = (int)f.hi;
+    kk = kk > 2 ? 2 : kk;
+    const float fh = f.hi - (float)kk;      // exact
+    const float a = 2.f * fh;
+    const float s = a - 1.f;                 // two-sum of a and -1
+    const float bb = s - a;
+    float e = (a - (s - bb)) + (-1.f - bb);
+    e += 2.f * f.lo;
+    const float s2 = s + e;                  // renormalise
+    const float b2 = s2 - s;
+    t.lo = (s - (s2 - b2)) + (e - b2);
+    t.hi = s2;
+    return n + kk;
+}
+
+// acc * t + (ch + cl), all df
+__device__ __forceinline__ df df_horner(df acc, df t, float ch, float cl) {
+    const float p = acc.hi * t.hi;
+    float e = fmaf(acc.hi, t.hi, -p);
+    e = fmaf(acc.hi, t.lo, e);
+    e = fmaf(acc.lo, t.hi, e);
+    const float s = p + ch;
+    const float bb = s - p;
+    const float err = (p - (s - bb)) + (ch - bb);
+    return df_quick(s, err + e + cl);
+}
+
+// the polynomial of interval k at t from the packed table (SPLIT df coefficients)
+template <int SPLIT>
+__device__ __forceinline__ df sw_poly(const float4* __restrict__ tab, int k, df t) {
+    float c[16];
+    const float4* src = tab + 4 * k;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float4 q = __ldg(src + v);
+        c[4 * v] = q.x; c[4 * v + 1] = q.y; c[4 * v + 2] = q.z; c[4 * v + 3] = q.w;
+    }
+    float v = c[2 * SPLIT + (kSwDeg - SPLIT)];
+#pragma unroll
+    for (int e = kSwDeg - 1; e >= SPLIT; --e) v = fmaf(v, t.hi, c[2 * SPLIT + (e - SPLIT)]);
+    df acc = {v, 0.f};
+#pragma unroll
+    for (int e = SPLIT - 1; e >= 0; --e) acc = df_horner(acc, t, c[2 * e], c[2 * e + 1]);
+    return acc;
+}
+
+// ----------------------------------------------------------------- eps, tabulated (df64)
+// The same product as k_build_eps, with s from the packed table in df64
+// arithmetic (about 120 FP32 instructions per pair instead of 25 FP64 ones).
+// Pairs with d >= r0 + 6w have s == 1 and are culled with the tile.
+constexpr int EB = 32;                  // atom images staged at a time
+
+__global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb, double* eps64,
+                                                      double* pe64, float* eps32) {
+    __shared__ double ec[MAXE][3];
+    __shared__ int cn[EB][TX + TY + TZ];
+    __shared__ df cf[EB][TX + TY + TZ];
+    __shared__ int ne;
+    const Tile t = make_tile(g);
+    int tx, ty, tz;
+    compact_point(threadIdx.x >> 5, threadIdx.x & 31, tx, ty, tz);
+    const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+    const bool valid = i < g.nx && j < g.ny && k < g.nz;
+    const float tiny = (float)p.tiny;
+    const float reach = (float)fmin(p.rcut, p.r0 + 6.0 * p.w) + kMargin;
+    const float dq = (float)tb.s_dq, qlo = (float)tb.s_qlo;
+    const float r0f = (float)p.r0, iwf = (float)p.iw;
+    df P = {1.f, 0.f};
+    bool live = valid;
+    for (int a0 = 0; a0 < at.n; a0 += ACH) {
+        if (threadIdx.x == 0) ne = 0;
+        __syncthreads();
+        const int na = min(ACH, at.n - a0);
+        for (int q = threadIdx.x; q < na * 27; q += TT) {
+            const int a = a0 + q / 27, im = q % 27;
+            float fx, fy, fz;
+            image32(at.w32, a, im, g, fx, fy, fz);
+            if (box_d2(t, fx, fy, fz) < reach * reach) {
+                const int s = atomicAdd(&ne, 1);
+                image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
+            }
+        }
+        __syncthreads();
+        const int m = ne;
+        for (int e0 = 0; e0 < m; e0 += EB) {
+            const int ms = min(EB, m - e0);
+            for (int r = threadIdx.x; r < ms * (TX + TY + TZ); r += TT) {
+                const int e = r / (TX + TY + TZ), c = r % (TX + TY + TZ);
+                double v;
+                if (c < TX) {
+                    const double d = (t.i0 + c) * g.hx - ec[e0 + e][0];
+                    v = (d * d - tb.s_qlo) * tb.s_inv_dq;
+                } else if (c < TX + TY) {
+                    const double d = (t.j0 + c - TX) * g.hy - ec[e0 + e][1];
+                    v = d * d * tb.s_inv_dq;
+                } else {
+                    const double d = (t.k0 + c - TX - TY) * g.hz - ec[e0 + e][2];
+                    v = d * d * tb.s_inv_dq;
+                }
+                const SwCoord sc = sw_coord(v);
+                cn[e][c] = sc.n;
+                cf[e][c] = sc.f;
+            }
+            __syncthreads();
+            if (live) {
+                for (int e = 0; e < ms; ++e) {
+                    const int n = cn[e][tx] + cn[e][TX + ty] + cn[e][TX + TY + tz];
+                    if (n >= kSwNI) continue;                       // d >= r0 + 6w: s == 1
+                    const df f = df_add(df_add(cf[e][tx], cf[e][TX + ty]), cf[e][TX + TY + tz]);
+                    df tl;
+                    const int kq = sw_local(n, f, tl);
+                    if (kq >= kSwNI) continue;
+                    df sv;
+                    if (kq < 0) {
+                        // d < r0 - 4w: s < 8e-9, FP32 erfc (relative error ~1e-6 of s)
+                        const float qq = ((float)n + f.hi) * dq + qlo;
+                        const float d = sqrtf(fmaxf(qq, 0.f));
+                        sv.hi = 0.5f * erfcf((r0f - d) * iwf);
+                        sv.lo = 0.f;
+                    } else {
+                        sv = sw_poly<kSwSplitS>(tb.s32, kq, tl);
+                    }
+                    P = df_mul(P, sv);
+                    if (P.hi < tiny) { live = false; break; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (valid) {
+        const long idx = i + (long)g.nx * (j + (long)g.ny * k);
+        const double pe = (p.eps0 - 1.0) * df_to(P);
+        const double e = 1.0 + pe;
+        eps64[idx] = e;
+        if (pe64) pe64[idx] = pe;
+        if (eps32) eps32[idx] = (float)e;
+    }
+}
+
+// ----------------------------------------------------------------- eps force, tabulated (df64)
+// The same sum as k_forces_eps with h = s'/(s d) from the packed table in df64
+// arithmetic and the products and sums compensated in FP32 pairs. Each warp
+// stages, for its (atom, image) entry, the table coordinates and the
+// displacements of the tile's 32 columns, 4 rows and 4 planes.
+__global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb,
+                                                       const double* phi, const double* pe64, double* S) {
+    __shared__ double ec[MAXE][3];
+    __shared__ int eatom[MAXE];
+    __shared__ df Ws[TT];
+    __shared__ int wn[TT / 32][TX + TY + TZ];
+    __shared__ df wf[TT / 32][TX + TY + TZ];
+    __shared__ df wd[TT / 32][TX + TY + TZ];
+    __shared__ int ne;
+    const Tile t = make_tile(g);
+    {
+        const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+        const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+        double W = 0.0;
+        if (i < g.nx && j < g.ny && k < g.nz) {
+            const long pl = plane_of(g.nx, g.ny);
+            const long c = i + (long)g.nx * (j + (long)g.ny * k);
+            const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
+            const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
+            const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
+            const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
+            const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
+            const double p0 = phi[c];
+            const double ax = phi[xp] - p0, bx = p0 - phi[xm];
+            const double ay = phi[yp] - p0, by = p0 - phi[ym];
+            const double az = phi[zp] - p0, bz = p0 - phi[zm];
+            W = ((ax * ax + bx * bx) * g.c2x + (ay * ay + by * by) * g.c2y + (az * az + bz * bz) * g.c2z) * pe64[c];
+        }
+        Ws[threadIdx.x] = df_from(-W);   // index tx + TX (ty + TY tz); sign of c = -W h folded in
+    }
+    const float rcf = (float)p.rcut + kMargin;
+    const float rc2f = (float)(p.rcut * p.rcut);
+    const float dq = (float)tb.h_dq, qlo = (float)tb.h_qlo;
+    const float r0f = (float)p.r0, iwf = (float)p.iw, spf_norm = (float)p.sp_norm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int a0 = 0; a0 < at.n; a0 += ACH) {
+        if (threadIdx.x == 0) ne = 0;
+        __syncthreads();
+        const int na = min(ACH, at.n - a0);
+        for (int q = threadIdx.x; q < na * 27; q += TT) {
+            const int a = a0 + q / 27, im = q % 27;
+            float fx, fy, fz;
+            image32(at.w32, a, im, g, fx, fy, fz);
+            if (box_d2(t, fx, fy, fz) < rcf * rcf) {
+                const int s = atomicAdd(&ne, 1);
+                image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
+                eatom[s] = a;
+            }
+        }
+        __syncthreads();
+        const int m = ne;
+        for (int e = warp; e < m; e += TT / 32) {
+            // stage: lane -> column lane; lanes 0..3 also row j0+lane, lanes 4..7 plane k0+lane-4
+            for (int c = lane; c < TX + TY + TZ; c += 32) {
+                double d, v;
+                if (c < TX) {
+                    d = (t.i0 + c) * g.hx - ec[e][0];
+                    v = (d * d - tb.h_qlo) * tb.h_inv_dq;
+                } else if (c < TX + TY) {
+                    d = (t.j0 + c - TX) * g.hy - ec[e][1];
+                    v = d * d * tb.h_inv_dq;
+                } else {
+                    d = (t.k0 + c - TX - TY) * g.hz - ec[e][2];
+                    v = d * d * tb.h_inv_dq;
+                }
+                const SwCoord sc = sw_coord(v);
+                wn[warp][c] = sc.n;
+                wf[warp][c] = sc.f;
+                wd[warp][c] = df_from(d);
+            }
+            __syncwarp();
+            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+            for (int blk = 0; blk < 16; ++blk) {
+                int tx, ty, tz;
+                compact_point(blk, lane, tx, ty, tz);
+                if (t.i0 + tx >= g.nx || t.j0 + ty >= g.ny || t.k0 + tz >= g.nz) continue;
+                const int n = wn[warp][tx] + wn[warp][TX + ty] + wn[warp][TX + TY + tz];
+                const df f = df_add(df_add(wf[warp][tx], wf[warp][TX + ty]), wf[warp][TX + TY + tz]);
+                df tl;
+                const int kq = sw_local(n, f, tl);
+                df ratio;   // s'(d) / (s(d) d)
+                if (kq >= 0 && kq < kSwNI) {
+                    ratio = sw_poly<kSwSplitH>(tb.h32, kq, tl);
+                } else {
+                    // |u| > 3.5: the pair is below 5e-6 of one at the switching radius; FP32
+                    const float qq = ((float)n + f.hi) * dq + qlo;
+                    if (!(qq < rc2f && qq > 0.f)) continue;
+                    const float df_ = sqrtf(qq);
+                    const float uf = (df_ - r0f) * iwf;
+                    const float sf = 0.5f * erfcf(-uf);
+                    const float spf = spf_norm * expf(-uf * uf);
+                    ratio.hi = spf / (sf * df_);
+                    ratio.lo = 0.f;
+                }
+                const df c = df_mul(Ws[tx + TX * (ty + TY * tz)], ratio);
+                df_acc(sx, cx, c, wd[warp][tx]);
+                df_acc(sy, cy, c, wd[warp][TX + ty]);
+                df_acc(sz, cz, c, wd[warp][TX + TY + tz]);
+            }
+            double fx = (double)sx + (double)cx, fy = (double)sy + (double)cy, fz = (double)sz + (double)cz;
+            fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+            if (lane == 0) {
+                const int a = eatom[e];
+                if (fx != 0.0) atomicAdd(&S[3 * a + 0], fx);
+                if (fy != 0.0) atomicAdd(&S[3 * a + 1], fy);
+                if (fz != 0.0) atomicAdd(&S[3 * a + 2], fz);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+}
+
 // ----------------------------------------------------------------- dry planes
 __global__ void k_plane_max(Geo g, const double* eps64, double* out) {
     __shared__ double red[256];
@@ -427,10 +717,6 @@ __global__ void __launch_bounds__(kReduceThreads) k_energy(Geo g, const double* 
 }
 
 // ----------------------------------------------------------------- forces
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // dielectric part: S_a = sum_i W_i sum_images q(d) (-(r_i - c)/d), with
 // W_i = (1/2) sum over the six faces of i of (grad_f phi)^2 times pe_i = eps_i - 1,
@@ -611,13 +897,15 @@ void launch_wrap_atoms(const Geo& g, const double* pos, int n, double* w64, floa
     if (n > 0) k_wrap_atoms<<<(n + 127) / 128, 128, 0, s>>>(g, pos, n, w64, w32);
 }
 
-void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, double* h_coef, cudaStream_t s) {
-    k_switch_tables<<<(2 * kSwNI + 127) / 128, 128, 0, s>>>(p, tb, s_coef, h_coef);
+void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, double* h_coef, float4* s_pack,
+                          float4* h_pack, cudaStream_t s) {
+    k_switch_tables<<<(2 * kSwNI + 127) / 128, 128, 0, s>>>(p, tb, s_coef, h_coef, s_pack, h_pack);
 }
 
 void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, double* eps64, double* pe64,
                       float* eps32, cudaStream_t s) {
-    k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
+    if (tb.s32) k_build_eps_tab<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
+    else k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
 }
 
 size_t gauss_tabs_bytes(int n_atoms, int nmax) {
@@ -659,7 +947,8 @@ void launch_energy(const Geo& g, const double* rho, const double* phi, const dou
 
 void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const double* phi,
                        const double* pe64, double* S, cudaStream_t s) {
-    k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
+    if (tb.h32) k_forces_eps_tab<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
+    else k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
 }
 
 void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, double* T, cudaStream_t s) {
