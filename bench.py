@@ -231,24 +231,35 @@ def gpu_arm(args, rank, world):
     phases = {k: {"ms_per_step": v["ms"] / args.steps, "share": (v["ms"] / total_ms if total_ms else 0.0),
                   "launches_per_step": v["launches"] / args.steps} for k, v in prof.items() if v["launches"]}
 
-    # FP64 full-box comparator (the plain FP64 multigrid) on the same frames
-    comparator = None
-    if not args.no_comparator:
-        s64 = make_solver(0, 0)
-        step(s64, frames[0], phi, rho)
+    # comparators on the same frames: the plain FP64 full-box multigrid, and the
+    # mixed-precision dry/wet split (FFT dry region + band multigrid, coupled)
+    def time_variant(precision, split, label):
+        sv = make_solver(precision, split)
+        step(sv, frames[0], phi, rho)
         torch.cuda.synchronize()
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
         ncmp = max(1, min(args.steps, 3))
         c0.record(stream)
         for i in range(ncmp):
-            step(s64, frames[args.warmup + i], phi, rho)
+            step(sv, frames[args.warmup + i], phi, rho)
         c1.record(stream)
         torch.cuda.synchronize()
-        comparator = {"solver": "FP64 full-box multigrid (precision=0, split=0)",
-                      "value": ncmp / (c0.elapsed_time(c1) / 1e3), "unit": UNIT, "steps": ncmp,
-                      "outer_iterations": s64.stats().outer_iterations}
-        del s64
+        sst = sv.stats()
+        out = {"solver": label, "value": ncmp / (c0.elapsed_time(c1) / 1e3), "unit": UNIT, "steps": ncmp,
+               "outer_iterations": sst.outer_iterations, "vcycles": sst.vcycles,
+               "split_active": bool(sst.split_active), "wet_fraction": sst.wet_fraction}
+        del sv
+        return out
+
+    comparator = None
+    split_variant = None
+    if not args.no_comparator:
+        if not (args.precision == 0 and args.split == 0):
+            comparator = time_variant(0, 0, "FP64 full-box multigrid (precision=0, split=0)")
+        if args.split == 0:
+            split_variant = time_variant(args.precision, 1, "dry/wet split, %s (split=1)"
+                                         % ("mixed" if args.precision == 1 else "FP64"))
 
     # end to end through the public API with host buffers
     e2e = None
@@ -291,7 +302,8 @@ def gpu_arm(args, rank, world):
                    "step": "set_dielectric + build_rho + solve (cold) + energy_forces",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof, "smoother": smooth, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clk, "fp64_fullbox": comparator, "phases": phases, "dominant_kernel_group": dominant,
+        "clocks": clk, "fp64_fullbox": comparator, "split_scheme": split_variant, "phases": phases,
+        "dominant_kernel_group": dominant,
     }
     return line
 
@@ -425,7 +437,7 @@ def main():
     ap.add_argument("--workload", default="mixed_192x192x384", choices=sorted(W.WORKLOADS))
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--precision", type=int, default=1)
-    ap.add_argument("--split", type=int, default=1)
+    ap.add_argument("--split", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

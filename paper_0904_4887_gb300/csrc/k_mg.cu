@@ -299,65 +299,53 @@ __global__ void k_coarse_matrix(LV<T> C, double* M) {
     }
 }
 
-// in-place inverse by Gauss-Jordan elimination with partial pivoting (one CTA);
-// M is n x n, W (second n x n block after M) receives the inverse
-__global__ void k_gauss_jordan(double* M, int n, int* status) {
+// Inverse by Gauss-Jordan elimination without pivoting. The coarse operator
+// is negative definite (Dirichlet walls, or the periodic operator shifted by
+// -s 1 1^T, whose null space it removes), so every pivot is nonzero and no row
+// exchange is needed. Step `col` subtracts multiples of row col from every
+// other row of [M | W], one CTA per row; row col itself is only read during
+// the step. After the last step M is diagonal and the inverse is W / diag(M).
+__global__ void k_gj_init(double* M, int n, int* status) {
     double* W = M + (long)n * n;
-    __shared__ double fcol[kMaxCoarse];
-    __shared__ double bv[1024];
-    __shared__ int bi[1024];
-    for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) W[e] = (e / n == e % n) ? 1.0 : 0.0;
-    __syncthreads();
-    for (int col = 0; col < n; ++col) {
-        double best = -1.0;
-        int bidx = col;
-        for (int r = col + threadIdx.x; r < n; r += blockDim.x) {
-            const double v = fabs(M[(long)r * n + col]);
-            if (v > best) { best = v; bidx = r; }
+    const int r = blockIdx.x;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) W[(long)r * n + q] = (q == r) ? 1.0 : 0.0;
+    if (r == 0 && threadIdx.x == 0) *status = 0;
+}
+
+__global__ void k_gj_step(double* M, int n, int col, int* status) {
+    const int r = blockIdx.x;
+    if (r == col) return;
+    double* W = M + (long)n * n;
+    __shared__ double f;
+    if (threadIdx.x == 0) {
+        const double piv = M[(long)col * n + col];
+        if (!(fabs(piv) > 1e-300)) {
+            f = 0.0;
+            *status = 1;
+        } else {
+            f = M[(long)r * n + col] / piv;
         }
-        bv[threadIdx.x] = best;
-        bi[threadIdx.x] = bidx;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s && bv[threadIdx.x + s] > bv[threadIdx.x]) {
-                bv[threadIdx.x] = bv[threadIdx.x + s];
-                bi[threadIdx.x] = bi[threadIdx.x + s];
-            }
-            __syncthreads();
-        }
-        const int piv = bi[0];
-        if (bv[0] <= 1e-300) {
-            if (threadIdx.x == 0) *status = 1;
-            return;
-        }
-        if (piv != col) {
-            for (int q = threadIdx.x; q < n; q += blockDim.x) {
-                double a = M[(long)col * n + q]; M[(long)col * n + q] = M[(long)piv * n + q]; M[(long)piv * n + q] = a;
-                double b = W[(long)col * n + q]; W[(long)col * n + q] = W[(long)piv * n + q]; W[(long)piv * n + q] = b;
-            }
-        }
-        __syncthreads();
-        const double pv = M[(long)col * n + col];
-        __syncthreads();
-        for (int q = threadIdx.x; q < n; q += blockDim.x) {
-            M[(long)col * n + q] /= pv;
-            W[(long)col * n + q] /= pv;
-        }
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += blockDim.x) fcol[r] = M[(long)r * n + col];
-        __syncthreads();
-        for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
-            const int r = (int)(e / n), q = (int)(e % n);
-            if (r == col) continue;
-            const double f = fcol[r];
-            if (f != 0.0) {
-                M[e] -= f * M[(long)col * n + q];
-                W[e] -= f * W[(long)col * n + q];
-            }
-        }
-        __syncthreads();
     }
-    if (threadIdx.x == 0) *status = 0;
+    __syncthreads();
+    const double fr = f;
+    if (fr == 0.0) return;
+    const double* mc = M + (long)col * n;
+    const double* wc = W + (long)col * n;
+    double* mr = M + (long)r * n;
+    double* wr = W + (long)r * n;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        mr[q] -= fr * mc[q];
+        wr[q] -= fr * wc[q];
+    }
+}
+
+__global__ void k_gj_finish(double* M, int n) {
+    double* W = M + (long)n * n;
+    const int r = blockIdx.x;
+    __shared__ double inv_d;
+    if (threadIdx.x == 0) inv_d = 1.0 / M[(long)r * n + r];
+    __syncthreads();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) W[(long)r * n + q] *= inv_d;
 }
 
 template <typename T>
@@ -895,8 +883,12 @@ template <typename T> void launch_coarsen_faces(const LV<T>& F, int nxc, int nyc
 template <typename T> void launch_coarse_matrix(const LV<T>& C, double* M, cudaStream_t s) {
     k_coarse_matrix<T><<<1, 512, 0, s>>>(C, M);
 }
-void launch_gauss_jordan(double* M, int n, int* status, cudaStream_t s) {
-    k_gauss_jordan<<<1, 1024, 0, s>>>(M, n, status);
+int launch_gauss_jordan(double* M, int n, int* status, cudaStream_t s) {
+    const int th = n >= 256 ? 256 : 128;
+    k_gj_init<<<n, th, 0, s>>>(M, n, status);
+    for (int col = 0; col < n; ++col) k_gj_step<<<n, th, 0, s>>>(M, n, col, status);
+    k_gj_finish<<<n, th, 0, s>>>(M, n);
+    return n + 2;
 }
 template <typename T> void launch_store_inverse(const double* W, int n, T* inv, cudaStream_t s) {
     const long nn = (long)n * n;
