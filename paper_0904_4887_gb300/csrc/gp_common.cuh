@@ -47,6 +47,7 @@ struct Geo {
     double ihx, ihy, ihz;   // 1 / h
     double c2x, c2y, c2z;   // 1 / (2 h^2): face-mean operator weight per axis
     double inv_n;           // 1 / (nx ny nz)
+    float lxf, lyf, lzf;    // cell lengths in FP32 (culling)
 };
 
 inline Geo make_geo(int nx, int ny, int nz, double lx, double ly, double lz) {
@@ -57,6 +58,7 @@ inline Geo make_geo(int nx, int ny, int nz, double lx, double ly, double lz) {
     g.ihx = 1.0 / g.hx; g.ihy = 1.0 / g.hy; g.ihz = 1.0 / g.hz;
     g.c2x = 0.5 / (g.hx * g.hx); g.c2y = 0.5 / (g.hy * g.hy); g.c2z = 0.5 / (g.hz * g.hz);
     g.inv_n = 1.0 / ((double)nx * ny * nz);
+    g.lxf = (float)lx; g.lyf = (float)ly; g.lzf = (float)lz;
     return g;
 }
 

@@ -18,13 +18,17 @@ constexpr float kMargin = 1e-3f;       // FP32 culling slack, Angstrom
 
 __device__ __forceinline__ double wrap_pos(double x, double L) { return x - L * floor(x / L); }
 
-// image `im` (0..26) of wrapped atom a: FP32 centre for culling
+// shift -L, 0 or +L for image digit m in {0, 1, 2} (FP32, no conversion)
+__device__ __forceinline__ float shift32(int m, float L) { return m == 0 ? -L : (m == 1 ? 0.f : L); }
+
+// image `im` (0..26) of wrapped atom a: FP32 centre for culling (no FP64 work:
+// the culling loop visits every atom image for every tile)
 __device__ __forceinline__ void image32(const float4* w32, int a, int im, const Geo& g, float& cx, float& cy,
                                         float& cz) {
     const float4 p = w32[a];
-    cx = p.x + (float)((im % 3 - 1) * g.lx);
-    cy = p.y + (float)(((im / 3) % 3 - 1) * g.ly);
-    cz = p.z + (float)((im / 9 - 1) * g.lz);
+    cx = p.x + shift32(im % 3, g.lxf);
+    cy = p.y + shift32((im / 3) % 3, g.lyf);
+    cz = p.z + shift32(im / 9, g.lzf);
 }
 
 // the same image in FP64
@@ -455,30 +459,51 @@ __device__ __forceinline__ df sw_poly(const float4* __restrict__ tab, int k, df 
 // ----------------------------------------------------------------- eps, tabulated (df64)
 // The same product as k_build_eps, with s from the packed table in df64
 // arithmetic (about 120 FP32 instructions per pair instead of 25 FP64 ones).
-// Pairs with d >= r0 + 6w have s == 1 and are culled with the tile.
+// Tiles are 32 x 4 x 16 points, each thread taking 4 points along z, so the
+// per-(tile, atom image) staging in FP64 is shared by 2048 points. The tile
+// first collects its atom images within reach (r0 + 6w: s == 1 beyond) into
+// one list, processed when full or at the end, in batches of EB images.
+constexpr int EZ = 16;                  // z extent of the tabulated-eps tiles
 constexpr int EB = 32;                  // atom images staged at a time
+constexpr int ACHS = 8;                 // atoms culled per pass (at most 216 images)
+constexpr int ECAP = 640;               // image list capacity
+constexpr int NS = TX + TY + EZ;        // staged columns, rows and planes
+
+__device__ __forceinline__ Tile make_tile_ez(const Geo& g) {
+    Tile t;
+    t.i0 = blockIdx.x * TX; t.j0 = blockIdx.y * TY; t.k0 = blockIdx.z * EZ;
+    t.i1 = min(t.i0 + TX, g.nx) - 1; t.j1 = min(t.j0 + TY, g.ny) - 1; t.k1 = min(t.k0 + EZ, g.nz) - 1;
+    t.bx0 = (float)(t.i0 * g.hx); t.bx1 = (float)(t.i1 * g.hx);
+    t.by0 = (float)(t.j0 * g.hy); t.by1 = (float)(t.j1 * g.hy);
+    t.bz0 = (float)(t.k0 * g.hz); t.bz1 = (float)(t.k1 * g.hz);
+    return t;
+}
 
 __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb, double* eps64,
                                                       double* pe64, float* eps32) {
-    __shared__ double ec[MAXE][3];
-    __shared__ int cn[EB][TX + TY + TZ];
-    __shared__ df cf[EB][TX + TY + TZ];
+    __shared__ double ec[ECAP][3];
+    __shared__ int cn[EB][NS];
+    __shared__ df cf[EB][NS];
     __shared__ int ne;
-    const Tile t = make_tile(g);
+    const Tile t = make_tile_ez(g);
     int tx, ty, tz;
     compact_point(threadIdx.x >> 5, threadIdx.x & 31, tx, ty, tz);
-    const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
-    const bool valid = i < g.nx && j < g.ny && k < g.nz;
+    const int i = t.i0 + tx, j = t.j0 + ty;
+    bool live[4];
+    df P[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        live[r] = i < g.nx && j < g.ny && t.k0 + tz + 4 * r < g.nz;
+        P[r] = df{1.f, 0.f};
+    }
     const float tiny = (float)p.tiny;
     const float reach = (float)fmin(p.rcut, p.r0 + 6.0 * p.w) + kMargin;
     const float dq = (float)tb.s_dq, qlo = (float)tb.s_qlo;
     const float r0f = (float)p.r0, iwf = (float)p.iw;
-    df P = {1.f, 0.f};
-    bool live = valid;
-    for (int a0 = 0; a0 < at.n; a0 += ACH) {
-        if (threadIdx.x == 0) ne = 0;
-        __syncthreads();
-        const int na = min(ACH, at.n - a0);
+    if (threadIdx.x == 0) ne = 0;
+    __syncthreads();
+    for (int a0 = 0; a0 < at.n; a0 += ACHS) {
+        const int na = min(ACHS, at.n - a0);
         for (int q = threadIdx.x; q < na * 27; q += TT) {
             const int a = a0 + q / 27, im = q % 27;
             float fx, fy, fz;
@@ -490,177 +515,260 @@ __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParam
         }
         __syncthreads();
         const int m = ne;
-        for (int e0 = 0; e0 < m; e0 += EB) {
-            const int ms = min(EB, m - e0);
-            for (int r = threadIdx.x; r < ms * (TX + TY + TZ); r += TT) {
-                const int e = r / (TX + TY + TZ), c = r % (TX + TY + TZ);
-                double v;
-                if (c < TX) {
-                    const double d = (t.i0 + c) * g.hx - ec[e0 + e][0];
-                    v = (d * d - tb.s_qlo) * tb.s_inv_dq;
-                } else if (c < TX + TY) {
-                    const double d = (t.j0 + c - TX) * g.hy - ec[e0 + e][1];
-                    v = d * d * tb.s_inv_dq;
-                } else {
-                    const double d = (t.k0 + c - TX - TY) * g.hz - ec[e0 + e][2];
-                    v = d * d * tb.s_inv_dq;
-                }
-                const SwCoord sc = sw_coord(v);
-                cn[e][c] = sc.n;
-                cf[e][c] = sc.f;
-            }
-            __syncthreads();
-            if (live) {
-                for (int e = 0; e < ms; ++e) {
-                    const int n = cn[e][tx] + cn[e][TX + ty] + cn[e][TX + TY + tz];
-                    if (n >= kSwNI) continue;                       // d >= r0 + 6w: s == 1
-                    const df f = df_add(df_add(cf[e][tx], cf[e][TX + ty]), cf[e][TX + TY + tz]);
-                    df tl;
-                    const int kq = sw_local(n, f, tl);
-                    if (kq >= kSwNI) continue;
-                    df sv;
-                    if (kq < 0) {
-                        // d < r0 - 4w: s < 8e-9, FP32 erfc (relative error ~1e-6 of s)
-                        const float qq = ((float)n + f.hi) * dq + qlo;
-                        const float d = sqrtf(fmaxf(qq, 0.f));
-                        sv.hi = 0.5f * erfcf((r0f - d) * iwf);
-                        sv.lo = 0.f;
+        if (m > ECAP - ACHS * 27 || a0 + ACHS >= at.n) {
+            for (int e0 = 0; e0 < m; e0 += EB) {
+                const int ms = min(EB, m - e0);
+                for (int r = threadIdx.x; r < ms * NS; r += TT) {
+                    const int e = r / NS, c = r % NS;
+                    double v;
+                    if (c < TX) {
+                        const double d = (t.i0 + c) * g.hx - ec[e0 + e][0];
+                        v = (d * d - tb.s_qlo) * tb.s_inv_dq;
+                    } else if (c < TX + TY) {
+                        const double d = (t.j0 + c - TX) * g.hy - ec[e0 + e][1];
+                        v = d * d * tb.s_inv_dq;
                     } else {
-                        sv = sw_poly<kSwSplitS>(tb.s32, kq, tl);
+                        const double d = (t.k0 + c - TX - TY) * g.hz - ec[e0 + e][2];
+                        v = d * d * tb.s_inv_dq;
                     }
-                    P = df_mul(P, sv);
-                    if (P.hi < tiny) { live = false; break; }
+                    const SwCoord sc = sw_coord(v);
+                    cn[e][c] = sc.n;
+                    cf[e][c] = sc.f;
                 }
+                __syncthreads();
+                if (live[0] || live[1] || live[2] || live[3]) {
+                    for (int e = 0; e < ms; ++e) {
+                        const int nxy = cn[e][tx] + cn[e][TX + ty];
+                        if (nxy >= kSwNI) continue;                  // already beyond r0 + 6w
+                        const df fxy = df_add(cf[e][tx], cf[e][TX + ty]);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            if (!live[r]) continue;
+                            const int cz = TX + TY + tz + 4 * r;
+                            const int n = nxy + cn[e][cz];
+                            if (n >= kSwNI) continue;               // d >= r0 + 6w: s == 1
+                            df tl;
+                            const int kq = sw_local(n, df_add(fxy, cf[e][cz]), tl);
+                            if (kq >= kSwNI) continue;
+                            df sv;
+                            if (kq < 0) {
+                                // d < r0 - 4w: s < 8e-9, FP32 erfc (relative error ~1e-6 of s)
+                                const float qq = ((float)kq + 0.5f * (tl.hi + 1.f)) * dq + qlo;   // x = kq + (t + 1) / 2
+                                const float d = sqrtf(fmaxf(qq, 0.f));
+                                sv.hi = 0.5f * erfcf((r0f - d) * iwf);
+                                sv.lo = 0.f;
+                            } else {
+                                sv = sw_poly<kSwSplitS>(tb.s32, kq, tl);
+                            }
+                            P[r] = df_mul(P[r], sv);
+                            if (P[r].hi < tiny) live[r] = false;
+                        }
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
+            if (threadIdx.x == 0) ne = 0;
         }
+        __syncthreads();
     }
-    if (valid) {
-        const long idx = i + (long)g.nx * (j + (long)g.ny * k);
-        const double pe = (p.eps0 - 1.0) * df_to(P);
-        const double e = 1.0 + pe;
-        eps64[idx] = e;
-        if (pe64) pe64[idx] = pe;
-        if (eps32) eps32[idx] = (float)e;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int k = t.k0 + tz + 4 * r;
+        if (i < g.nx && j < g.ny && k < g.nz) {
+            const long idx = i + (long)g.nx * (j + (long)g.ny * k);
+            const double pe = (p.eps0 - 1.0) * df_to(P[r]);
+            const double e = 1.0 + pe;
+            eps64[idx] = e;
+            if (pe64) pe64[idx] = pe;
+            if (eps32) eps32[idx] = (float)e;
+        }
     }
 }
 
 // ----------------------------------------------------------------- eps force, tabulated (df64)
 // The same sum as k_forces_eps with h = s'/(s d) from the packed table in df64
-// arithmetic and the products and sums compensated in FP32 pairs. Each warp
-// stages, for its (atom, image) entry, the table coordinates and the
-// displacements of the tile's 32 columns, 4 rows and 4 planes.
+// arithmetic, on 32 x 4 x 16 tiles. One warp per (tile, atom image): it
+// stages in df the table coordinates and displacements of the tile's 32
+// columns, 4 rows and 16 planes (about 1e-14 relative in h, well inside what
+// the force needs), runs over the 2048 points with compensated FP32 sums, and
+// reduces across the warp in df before one FP64 atomic per component.
+constexpr int ECAPF = 384;              // image list capacity of the force kernel
+
+// (s, c) Neumaier pair summed across the warp; returns the total in FP64 on every lane
+__device__ __forceinline__ double warp_sum_pair(float s, float c) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        const float t = s + s2;
+        const float z = t - s;
+        c += c2 + ((s - (t - z)) + (s2 - z));
+        s = t;
+    }
+    return (double)s + (double)c;
+}
+
+// exact-to-2^-48 df of the integer c times h (h as a df)
+__device__ __forceinline__ df df_int_mul(int c, df h) {
+    const float cf_ = (float)c;
+    const float p = cf_ * h.hi;
+    const float e = fmaf(cf_, h.hi, -p) + cf_ * h.lo;
+    return df_quick(p, e);
+}
+
+// table coordinate n + f (f in [0, 1)) of v held as a df
+__device__ __forceinline__ SwCoord sw_coord_df(df v) {
+    SwCoord c;
+    float fl = floorf(v.hi);
+    df f = df_quick(v.hi - fl, v.lo);          // v.hi - fl is exact
+    if (f.hi < 0.f) { fl -= 1.f; f = df_add(f, df{1.f, 0.f}); }
+    else if (f.hi >= 1.f) { fl += 1.f; f = df_add(f, df{-1.f, 0.f}); }
+    c.n = (int)fl;
+    c.f = f;
+    return c;
+}
+
 __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb,
                                                        const double* phi, const double* pe64, double* S) {
-    __shared__ double ec[MAXE][3];
-    __shared__ int eatom[MAXE];
-    __shared__ df Ws[TT];
-    __shared__ int wn[TT / 32][TX + TY + TZ];
-    __shared__ df wf[TT / 32][TX + TY + TZ];
-    __shared__ df wd[TT / 32][TX + TY + TZ];
+    __shared__ df Ws[TX * TY * EZ];              // index tx + TX (ty + TY z)
+    __shared__ df eb[ECAPF][3];                  // displacement of column/row/plane 0 from the image
+    __shared__ int eatom[ECAPF];
+    __shared__ int wn[TT / 32][NS];
+    __shared__ df wf[TT / 32][NS];
+    __shared__ df wd[TT / 32][NS];
     __shared__ int ne;
-    const Tile t = make_tile(g);
+    const Tile t = make_tile_ez(g);
+    const float rcf = (float)p.rcut + kMargin;
+    // the tile's atom images within rcut; the W field is built only if there is one
+    if (threadIdx.x == 0) ne = 0;
+    __syncthreads();
     {
-        const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+        const float4* w32 = at.w32;
+        for (int q = threadIdx.x; q < at.n * 27; q += TT) {
+            const int a = q / 27, im = q % 27;
+            float fx, fy, fz;
+            image32(w32, a, im, g, fx, fy, fz);
+            if (box_d2(t, fx, fy, fz) < rcf * rcf) atomicAdd(&ne, 1);
+        }
+    }
+    __syncthreads();
+    if (ne == 0) return;
+    for (int q = threadIdx.x; q < TX * TY * EZ; q += TT) {
+        const int tx = q % TX, ty = (q / TX) % TY, tz = q / (TX * TY);
         const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
         double W = 0.0;
         if (i < g.nx && j < g.ny && k < g.nz) {
             const long pl = plane_of(g.nx, g.ny);
             const long c = i + (long)g.nx * (j + (long)g.ny * k);
-            const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
-            const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
-            const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
-            const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
-            const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
-            const double p0 = phi[c];
-            const double ax = phi[xp] - p0, bx = p0 - phi[xm];
-            const double ay = phi[yp] - p0, by = p0 - phi[ym];
-            const double az = phi[zp] - p0, bz = p0 - phi[zm];
-            W = ((ax * ax + bx * bx) * g.c2x + (ay * ay + by * by) * g.c2y + (az * az + bz * bz) * g.c2z) * pe64[c];
+            const double pv = pe64[c];
+            if (pv != 0.0) {
+                const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
+                const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
+                const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
+                const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
+                const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
+                const double p0 = phi[c];
+                const double ax = phi[xp] - p0, bx = p0 - phi[xm];
+                const double ay = phi[yp] - p0, by = p0 - phi[ym];
+                const double az = phi[zp] - p0, bz = p0 - phi[zm];
+                W = ((ax * ax + bx * bx) * g.c2x + (ay * ay + by * by) * g.c2y + (az * az + bz * bz) * g.c2z) * pv;
+            }
         }
-        Ws[threadIdx.x] = df_from(-W);   // index tx + TX (ty + TY tz); sign of c = -W h folded in
+        Ws[q] = df_from(-W);   // sign of c = -W h folded in
     }
-    const float rcf = (float)p.rcut + kMargin;
     const float rc2f = (float)(p.rcut * p.rcut);
     const float dq = (float)tb.h_dq, qlo = (float)tb.h_qlo;
     const float r0f = (float)p.r0, iwf = (float)p.iw, spf_norm = (float)p.sp_norm;
+    const df hx = df_from(g.hx), hy = df_from(g.hy), hz = df_from(g.hz);
+    const df inv = df_from(tb.h_inv_dq), mqlo = df_from(-tb.h_qlo);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int a0 = 0; a0 < at.n; a0 += ACH) {
-        if (threadIdx.x == 0) ne = 0;
-        __syncthreads();
-        const int na = min(ACH, at.n - a0);
+    __syncthreads();
+    if (threadIdx.x == 0) ne = 0;
+    __syncthreads();
+    for (int a0 = 0; a0 < at.n; a0 += ACHS) {
+        const int na = min(ACHS, at.n - a0);
         for (int q = threadIdx.x; q < na * 27; q += TT) {
             const int a = a0 + q / 27, im = q % 27;
             float fx, fy, fz;
             image32(at.w32, a, im, g, fx, fy, fz);
             if (box_d2(t, fx, fy, fz) < rcf * rcf) {
                 const int s = atomicAdd(&ne, 1);
-                image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
+                double cx, cy, cz;
+                image64(at.w64, a, im, g, cx, cy, cz);
+                eb[s][0] = df_from(t.i0 * g.hx - cx);
+                eb[s][1] = df_from(t.j0 * g.hy - cy);
+                eb[s][2] = df_from(t.k0 * g.hz - cz);
                 eatom[s] = a;
             }
         }
         __syncthreads();
         const int m = ne;
-        for (int e = warp; e < m; e += TT / 32) {
-            // stage: lane -> column lane; lanes 0..3 also row j0+lane, lanes 4..7 plane k0+lane-4
-            for (int c = lane; c < TX + TY + TZ; c += 32) {
-                double d, v;
-                if (c < TX) {
-                    d = (t.i0 + c) * g.hx - ec[e][0];
-                    v = (d * d - tb.h_qlo) * tb.h_inv_dq;
-                } else if (c < TX + TY) {
-                    d = (t.j0 + c - TX) * g.hy - ec[e][1];
-                    v = d * d * tb.h_inv_dq;
-                } else {
-                    d = (t.k0 + c - TX - TY) * g.hz - ec[e][2];
-                    v = d * d * tb.h_inv_dq;
+        if (m > ECAPF - ACHS * 27 || a0 + ACHS >= at.n) {
+            for (int e = warp; e < m; e += TT / 32) {
+                for (int c = lane; c < NS; c += 32) {
+                    df d, v;
+                    if (c < TX) {
+                        d = df_add(eb[e][0], df_int_mul(c, hx));
+                        v = df_mul(df_add(df_mul(d, d), mqlo), inv);
+                    } else if (c < TX + TY) {
+                        d = df_add(eb[e][1], df_int_mul(c - TX, hy));
+                        v = df_mul(df_mul(d, d), inv);
+                    } else {
+                        d = df_add(eb[e][2], df_int_mul(c - TX - TY, hz));
+                        v = df_mul(df_mul(d, d), inv);
+                    }
+                    const SwCoord sc = sw_coord_df(v);
+                    wn[warp][c] = sc.n;
+                    wf[warp][c] = sc.f;
+                    wd[warp][c] = d;
                 }
-                const SwCoord sc = sw_coord(v);
-                wn[warp][c] = sc.n;
-                wf[warp][c] = sc.f;
-                wd[warp][c] = df_from(d);
-            }
-            __syncwarp();
-            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
-            for (int blk = 0; blk < 16; ++blk) {
-                int tx, ty, tz;
-                compact_point(blk, lane, tx, ty, tz);
-                if (t.i0 + tx >= g.nx || t.j0 + ty >= g.ny || t.k0 + tz >= g.nz) continue;
-                const int n = wn[warp][tx] + wn[warp][TX + ty] + wn[warp][TX + TY + tz];
-                const df f = df_add(df_add(wf[warp][tx], wf[warp][TX + ty]), wf[warp][TX + TY + tz]);
-                df tl;
-                const int kq = sw_local(n, f, tl);
-                df ratio;   // s'(d) / (s(d) d)
-                if (kq >= 0 && kq < kSwNI) {
-                    ratio = sw_poly<kSwSplitH>(tb.h32, kq, tl);
-                } else {
-                    // |u| > 3.5: the pair is below 5e-6 of one at the switching radius; FP32
-                    const float qq = ((float)n + f.hi) * dq + qlo;
-                    if (!(qq < rc2f && qq > 0.f)) continue;
-                    const float df_ = sqrtf(qq);
-                    const float uf = (df_ - r0f) * iwf;
-                    const float sf = 0.5f * erfcf(-uf);
-                    const float spf = spf_norm * expf(-uf * uf);
-                    ratio.hi = spf / (sf * df_);
-                    ratio.lo = 0.f;
+                __syncwarp();
+                float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+                for (int blk = 0; blk < 4 * 16; ++blk) {
+                    int tx, ty, tz;
+                    compact_point(blk & 15, lane, tx, ty, tz);
+                    tz += 4 * (blk >> 4);
+                    if (t.i0 + tx >= g.nx || t.j0 + ty >= g.ny || t.k0 + tz >= g.nz) continue;
+                    const int n = wn[warp][tx] + wn[warp][TX + ty] + wn[warp][TX + TY + tz];
+                    const df f = df_add(df_add(wf[warp][tx], wf[warp][TX + ty]), wf[warp][TX + TY + tz]);
+                    df tl;
+                    const int kq = sw_local(n, f, tl);
+                    df ratio;   // s'(d) / (s(d) d)
+                    if (kq >= 0 && kq < kSwNI) {
+                        ratio = sw_poly<kSwSplitH>(tb.h32, kq, tl);
+                    } else {
+                        // |u| > 3.5: the pair is below 5e-6 of one at the switching radius; FP32
+                        const float qq = ((float)kq + 0.5f * (tl.hi + 1.f)) * dq + qlo;
+                        if (!(qq < rc2f && qq > 0.f)) continue;
+                        const float d_ = sqrtf(qq);
+                        const float uf = (d_ - r0f) * iwf;
+                        const float sf = 0.5f * erfcf(-uf);
+                        const float spf = spf_norm * expf(-uf * uf);
+                        ratio.hi = spf / (sf * d_);
+                        ratio.lo = 0.f;
+                    }
+                    const df c = df_mul(Ws[tx + TX * (ty + TY * tz)], ratio);
+                    df_acc(sx, cx, c, wd[warp][tx]);
+                    df_acc(sy, cy, c, wd[warp][TX + ty]);
+                    df_acc(sz, cz, c, wd[warp][TX + TY + tz]);
                 }
-                const df c = df_mul(Ws[tx + TX * (ty + TY * tz)], ratio);
-                df_acc(sx, cx, c, wd[warp][tx]);
-                df_acc(sy, cy, c, wd[warp][TX + ty]);
-                df_acc(sz, cz, c, wd[warp][TX + TY + tz]);
+                const double fx = warp_sum_pair(sx, cx), fy = warp_sum_pair(sy, cy), fz = warp_sum_pair(sz, cz);
+                if (lane == 0) {
+                    const int a = eatom[e];
+                    if (fx != 0.0) atomicAdd(&S[3 * a + 0], fx);
+                    if (fy != 0.0) atomicAdd(&S[3 * a + 1], fy);
+                    if (fz != 0.0) atomicAdd(&S[3 * a + 2], fz);
+                }
+                __syncwarp();
             }
-            double fx = (double)sx + (double)cx, fy = (double)sy + (double)cy, fz = (double)sz + (double)cz;
-            fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
-            if (lane == 0) {
-                const int a = eatom[e];
-                if (fx != 0.0) atomicAdd(&S[3 * a + 0], fx);
-                if (fy != 0.0) atomicAdd(&S[3 * a + 1], fy);
-                if (fz != 0.0) atomicAdd(&S[3 * a + 2], fz);
-            }
-            __syncwarp();
+            __syncthreads();
+            if (threadIdx.x == 0) ne = 0;
         }
         __syncthreads();
     }
+}
+
+dim3 tile_grid_ez(const Geo& g) {
+    return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + EZ - 1) / EZ);
 }
 
 // ----------------------------------------------------------------- dry planes
@@ -904,7 +1012,7 @@ void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, doub
 
 void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, double* eps64, double* pe64,
                       float* eps32, cudaStream_t s) {
-    if (tb.s32) k_build_eps_tab<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
+    if (tb.s32) k_build_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
     else k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
 }
 
@@ -947,7 +1055,7 @@ void launch_energy(const Geo& g, const double* rho, const double* phi, const dou
 
 void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const double* phi,
                        const double* pe64, double* S, cudaStream_t s) {
-    if (tb.h32) k_forces_eps_tab<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
+    if (tb.h32) k_forces_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
     else k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
 }
 
