@@ -82,6 +82,8 @@ typedef struct {
                              graph (no host round trip), check the residual once, and continue with
                              the checked loop only if it is not yet below tol (warm-started frames);
                              the graph is kept for the same rho/phi buffers (0 = off, <= 16) */
+    int sweep_shape;      /* FP32 finest-level smoother tile (see gp_stats.sweep_shape); -1 = chosen
+                             by the autotuner at gp_set_dielectric (-1) */
 } gp_params;
 
 #define GP_HISTORY 64
@@ -99,8 +101,9 @@ typedef struct {
     double residual;            /* final ||b - A phi|| / ||b|| (FP64) */
     int history_len;
     double history[GP_HISTORY]; /* relative residual after each outer step */
-    int sweep_shape;            /* finest-level smoother tile chosen by the autotuner:
-                                   0: 64x8, 1: 32x16, 2: 128x4, 3: 32x8 points (x, y) */
+    int sweep_shape;            /* finest-level FP32 smoother tile in use: 0: 64x8, 1: 32x16,
+                                   2: 128x4, 3: 32x8 points (x, y); 4, 5, 6: whole x rows times
+                                   4, 6, 8 rows (for nx = 64, 96, 128, 192, 256; otherwise 0) */
 } gp_stats;
 
 /* Fill *p with the defaults listed beside each field. */

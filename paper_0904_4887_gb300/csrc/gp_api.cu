@@ -373,7 +373,10 @@ void coarse_coeffs(gp_ctx* c, Hier<T>& H) {
         launch_store_inverse<T>(c->gmat + (size_t)H.nc * H.nc, H.nc, H.minv, c->s);
     }
     GP_CHECK_LAUNCH();
-    if (sizeof(T) == 4 && H.sweep_shape < 0) {
+    if (sizeof(T) == 4 && c->prm.sweep_shape >= 0) {
+        H.sweep_shape = rb_sweep_resolve<T>(H.lv[0], c->prm.sweep_shape);
+        c->stats.sweep_shape = H.sweep_shape;
+    } else if (sizeof(T) == 4 && H.sweep_shape < 0) {
         // smoother autotuner: time each tile shape on this level once
         H.sweep_shape = rb_sweep_autotune<T>(H.lv[0], H.x, H.r, H.tmp, c->s);
         GP_CHECK_LAUNCH();
@@ -402,7 +405,7 @@ void smooth_fine(gp_ctx* c, Hier<T>& H, T* u, const T* f, int nu, int first) {
     {
         ProfScope ps(c, GP_PROF_SMOOTH0, nu);
         for (int it = 0; it < nu; ++it) {
-            launch_rb_sweep<T>(V, a, f, b, first, c->s, H.sweep_shape < 0 ? 0 : H.sweep_shape);
+            launch_rb_sweep<T>(V, a, f, b, first, c->s, H.sweep_shape < 0 ? 0 : H.sweep_shape, c->dstatus + 1);
             T* t = a; a = b; b = t;
         }
     }
@@ -976,10 +979,17 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         launch_sub_mean(c->n, phi, c->scal + 9, 1.0 / (double)c->n, c->s);
     }
     GP_CHECK_LAUNCH();
+    int expired = 0;
+    GP_CUDA(cudaMemcpyAsync(&expired, c->dstatus + 1, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     GP_CUDA(cudaStreamSynchronize(c->s));
     prof_collect(c);
     if (result == GP_ERR_NOT_CONVERGED) c->err = "not converged within max_outer";
     if (result == GP_ERR_DIVERGED) c->err = "residual diverged";
+    if (expired) {
+        GP_CUDA(cudaMemsetAsync(c->dstatus + 1, 0, sizeof(int), c->s));
+        c->err = "a smoother copy wait expired; the result is not valid";
+        return GP_ERR_TIMEOUT;
+    }
     return result;
 }
 
@@ -1020,6 +1030,7 @@ void gp_default_params(gp_params* p) {
     p->restart = 12;
     p->band_vcycles = 2;
     p->graph_outer = 0;
+    p->sweep_shape = -1;
 }
 
 gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out) {
@@ -1040,7 +1051,8 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
         c->plane_max = (double*)dalloc(c, sizeof(double) * grid.nz);
         c->partial = (double*)dalloc(c, sizeof(double) * kReduceBlocks * (kMaxKrylov + 1));
         c->scal = (double*)dalloc(c, sizeof(double) * 64);
-        c->dstatus = (int*)dalloc(c, sizeof(int) * 4);
+        c->dstatus = (int*)dalloc(c, sizeof(int) * 4);   // [0] coarse inverse, [1] smoother wait expired
+        GP_CUDA(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * 4, c->s));
         c->gmat = (double*)dalloc(c, sizeof(double) * 2 * kMaxCoarse * kMaxCoarse);
         c->sw_coef = (double*)dalloc(c, sizeof(double) * 2 * kSwNI * (kSwDeg + 1));
         c->sw_pack = (float4*)dalloc(c, sizeof(float4) * 2 * kSwNI * 4);
@@ -1073,6 +1085,8 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             throw Err{GP_ERR_INVALID_ARG, "restart must be in 1..15"};
         if (p.band_vcycles < 1) throw Err{GP_ERR_INVALID_ARG, "band_vcycles must be >= 1"};
         if (p.graph_outer < 0 || p.graph_outer > 16) throw Err{GP_ERR_INVALID_ARG, "graph_outer must be 0..16"};
+        if (p.sweep_shape < -1 || p.sweep_shape >= kSweepShapeCount)
+            throw Err{GP_ERR_INVALID_ARG, "sweep_shape must be -1 (autotune) or a valid tile shape"};
         std::string why;
         const int L = plan_levels(c->g.nx, c->g.ny, c->g.nz, 1, p.levels, why);
         if (L < 2) throw Err{GP_ERR_INVALID_ARG, why.empty() ? "grid too small for multigrid" : why};

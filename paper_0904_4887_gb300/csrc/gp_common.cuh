@@ -139,9 +139,13 @@ void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_ba
 template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s);
 // one fused red-black sweep of a cell-eps level: u_new from u_old, colour `first` updated first (k_smooth.cu)
 void rb_sweep_init();
+// err: device flag set to 1 if a TMA wait of the row-tile kernel expired (may be null)
 template <typename T> void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first,
-                                           cudaStream_t s, int shape);
+                                           cudaStream_t s, int shape, int* err = nullptr);
 template <typename T> int rb_sweep_autotune(const LV<T>& L, const T* u_old, const T* f, T* u_new, cudaStream_t s);
+// the shape actually used for a requested one (row tiles fall back to 0 where unavailable)
+template <typename T> int rb_sweep_resolve(const LV<T>& L, int shape);
+constexpr int kSweepShapeCount = 7;     // 4 x-y tiles + 3 row tiles
 template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* f, T* r, cudaStream_t s);
 template <typename T> void launch_restrict(const LV<T>& F, const T* r, const LV<T>& C, T* fc, cudaStream_t s);
 template <typename T> void launch_prolong_add(const LV<T>& F, T* u, const LV<T>& C, const T* uc, cudaStream_t s);

@@ -162,6 +162,285 @@ __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Row-tile variant (FP32): a CTA owns whole x rows (nx = 2 NPX points) times
+// SY rows in y and a chunk of z-planes, so the only halo is one row in y (the
+// x neighbours wrap inside the tile). One thread per x-pair (2p, 2p+1) and
+// row; the thread keeps its own column's values of the neighbouring planes in
+// registers while it marches in z, so shared memory serves only the in-plane
+// neighbours (64-bit accesses, consecutive lanes on consecutive pairs).
+//
+// In a pair one member has each colour. With m1 = (j + q + first) & 1 the
+// member of the first colour at plane q, the member of the second colour at
+// plane q-1 is again m1. Iteration q:
+//   A(q)   first colour at plane q, rows j0-1 .. j0+SY (the halo rows
+//          recomputed from u_old), value kept in a register and in a 2-plane
+//          shared ring;
+//   B(q-1) second colour at plane q-1, rows j0 .. j0+SY-1, from the new
+//          first-colour values at planes q-2, q-1, q; writes plane q-1 of u_new.
+// Planes of u_old, eps and f arrive by TMA bulk copies (one per row, whole
+// rows are contiguous in memory) three planes ahead into a 4-slot ring, each
+// slot completing an mbarrier phase. Every wait is bounded: on expiry the
+// kernel records the fact in *err and runs to its end without further waits.
+template <int NPX, int SY>
+struct RowRing {
+    static constexpr int RU = SY + 4, RF = SY + 2;
+    float2 u[4][RU][NPX];
+    float2 e[4][RU][NPX];
+    float2 f[4][RF][NPX];
+    float2 r[2][RF][NPX];
+    unsigned long long bar[4];
+};
+
+__device__ __forceinline__ int wrap_idx(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// true once the phase with this parity has completed
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait (about a second at most); false if it gave up
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (int it = 0; it < (1 << 20); ++it)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// resident CTAs per SM the row kernel is built for: by shared memory, and by
+// registers at 64 per thread (it needs about 60), at most 4
+template <int NPX, int SY>
+constexpr int rows_min_blocks() {
+    constexpr int by_regs = 1024 / (NPX * (SY + 2));
+    constexpr int by_smem = (int)((227 * 1024) / (sizeof(RowRing<NPX, SY>) + 1024));
+    constexpr int m = by_regs < by_smem ? by_regs : by_smem;
+    return m < 1 ? 1 : (m > 4 ? 4 : m);
+}
+
+template <int NPX, int SY>
+__global__ void __launch_bounds__(NPX * (SY + 2), rows_min_blocks<NPX, SY>())
+    k_rb_sweep_rows(LV<float> L, const float* __restrict__ u_old, const float* __restrict__ f,
+                    float* __restrict__ u_new, int first, int sz, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using RR = RowRing<NPX, SY>;
+    constexpr int NTH = NPX * (SY + 2), RU = RR::RU, RF = RR::RF;
+    constexpr unsigned ROWB = NPX * 8;                    // bytes of one row
+    RR& R = *reinterpret_cast<RR*>(smem_raw);
+    __shared__ int bad;
+    const int nx = 2 * NPX, ny = L.ny, nz = L.nz;
+    const long pl = (long)nx * ny;
+    const int j0 = blockIdx.y * SY;
+    const int z0 = blockIdx.z * sz;
+    const int z1 = min(z0 + sz, nz);
+    if (z0 >= nz) return;
+    const float cx = 0.5f * L.ihx2, cy = 0.5f * L.ihy2, cz = 0.5f * L.ihz2;
+    const int tid = threadIdx.x;
+    const int ra = tid / NPX, p = tid % NPX;
+    const int pm = p == 0 ? NPX - 1 : p - 1, pp = p == NPX - 1 ? 0 : p + 1;
+    const int jB = j0 + ra - 1;
+    const bool doB = ra >= 1 && ra <= SY && jB < ny;
+    const int parA = (j0 - 1 + ra + first + 2 * ny) & 1;   // m1 = (parA + q) & 1
+    const int qb = z0 - 2;                                  // first plane of the march
+
+    if (tid == 0) {
+        bad = 0;
+        for (int k = 0; k < 4; ++k) mbar_init(&R.bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    // plane q into slot (q - qb) & 3: warp 0 issues one bulk copy per row;
+    // planes outside the data (beyond the Dirichlet walls, f on the walls) are
+    // filled by the threads with plain stores instead
+    auto issue = [&](int q) {
+        if (q > z1 + 1) return;
+        const int slot = (q - qb) & 3;
+        int kg;
+        if (L.zper) kg = q < 0 ? q + nz : (q >= nz ? q - nz : q);
+        else kg = (q < -1 || q > nz) ? -99 : q;
+        const bool has_ue = kg != -99, inner = kg >= 0 && kg < nz;
+        if (tid < 32) {
+            const unsigned bytes = (has_ue ? 2u * RU * ROWB : 0u) + (inner ? (unsigned)RF * ROWB : 0u);
+            if (tid == 0) {
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive_tx(&R.bar[slot], bytes);
+            }
+            __syncwarp();
+            const long base = (long)kg * pl;
+            if (has_ue)
+                for (int r = tid; r < 2 * RU; r += 32) {
+                    const int rr = r < RU ? r : r - RU;
+                    const long off = base + (long)wrap_idx(j0 - 2 + rr, ny) * nx;
+                    if (r < RU) bulk_g2s(&R.u[slot][rr][0], u_old + off, ROWB, &R.bar[slot]);
+                    else bulk_g2s(&R.e[slot][rr][0], L.eps + off, ROWB, &R.bar[slot]);
+                }
+            if (inner)
+                for (int r = tid; r < RF; r += 32)
+                    bulk_g2s(&R.f[slot][r][0], f + base + (long)wrap_idx(j0 - 1 + r, ny) * nx, ROWB, &R.bar[slot]);
+        }
+        if (!has_ue)
+            for (int t = tid; t < RU * NPX; t += NTH) {
+                (&R.u[slot][0][0])[t] = make_float2(0.f, 0.f);
+                (&R.e[slot][0][0])[t] = make_float2(1.f, 1.f);
+            }
+        if (!inner) (&R.f[slot][0][0])[tid] = make_float2(0.f, 0.f);
+    };
+    auto wait_plane = [&](int q) {
+        const int t = q - qb;
+        if (!bad && !mbar_wait(&R.bar[t & 3], (unsigned)((t >> 2) & 1))) bad = 1;
+    };
+
+    float2 U_m = make_float2(0.f, 0.f), U_0 = U_m;          // own u_old at q-1, q
+    float2 E_m2 = make_float2(1.f, 1.f), E_m = E_m2, E_0 = E_m2;  // own eps at q-2, q-1, q
+    float2 F_m = make_float2(0.f, 0.f);                      // own f at q-1
+    float R_m2 = 0.f, R_m = 0.f;                             // own first-colour values at q-2, q-1
+    float bxl = 1.f, bxr = 1.f;                              // eps x-neighbours at q-1 (for B)
+    float2 bym = make_float2(1.f, 1.f), byp = bym;           // eps rows j-1, j+1 at q-1 (for B)
+    const int rs = ra + 1;                                   // this thread's row in the u / e arrays
+
+    issue(qb);
+    issue(qb + 1);
+    issue(qb + 2);
+    for (int q = qb; q <= z1; ++q) {
+        if (q == qb) wait_plane(q);
+        wait_plane(q + 1);                                 // planes <= q+1 landed
+        __syncthreads();                                   // every thread done with slot q-1
+        issue(q + 3);                                      // into slot (q+3-qb)&3 == (q-1-qb)&3
+        const int s0 = (q - qb) & 3, s1 = (q + 1 - qb) & 3;
+        if (q == qb) {                                     // prime the z window: own values at z0-2, z0-1
+            U_m = R.u[s0][rs][p];
+            E_m = R.e[s0][rs][p];
+            U_0 = R.u[s1][rs][p];
+            E_0 = R.e[s1][rs][p];
+            continue;
+        }
+        // ---- A(q): first colour at plane q, member m1 of the own pair
+        const int m1 = (parA + q) & 1;
+        const float2 U_p = R.u[s1][rs][p];                 // own at q+1
+        const float2 E_p = R.e[s1][rs][p];
+        const float2 F_0 = R.f[s0][ra][p];
+        const float2 Exm = R.e[s0][rs][pm], Exp = R.e[s0][rs][pp];
+        const float2 Eym = R.e[s0][rs - 1][p], Eyp = R.e[s0][rs + 1][p];
+        float rA;
+        const bool wall = !L.zper && (q == -1 || q == nz);
+        {
+            const float uxa = m1 ? R.u[s0][rs][pp].x : R.u[s0][rs][pm].y;   // the x neighbour outside the pair
+            const float2 Uym = R.u[s0][rs - 1][p], Uyp = R.u[s0][rs + 1][p];
+            const float e0 = m1 ? E_0.y : E_0.x;
+            const float exl = m1 ? E_0.x : Exm.y, exr = m1 ? Exp.x : E_0.y;
+            const float uxl = m1 ? U_0.x : uxa, uxr = m1 ? uxa : U_0.y;
+            const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
+            const float aym = (e0 + (m1 ? Eym.y : Eym.x)) * cy, ayp = (e0 + (m1 ? Eyp.y : Eyp.x)) * cy;
+            const float azm = (e0 + (m1 ? E_m.y : E_m.x)) * cz, azp = (e0 + (m1 ? E_p.y : E_p.x)) * cz;
+            const float sum = axm * uxl + axp * uxr + aym * (m1 ? Uym.y : Uym.x) + ayp * (m1 ? Uyp.y : Uyp.x) +
+                              azm * (m1 ? U_m.y : U_m.x) + azp * (m1 ? U_p.y : U_p.x);
+            const float d = axm + axp + aym + ayp + azm + azp;
+            rA = wall ? (m1 ? U_0.y : U_0.x) : __fdividef(sum - (m1 ? F_0.y : F_0.x), d);
+        }
+        R.r[q & 1][ra][p] = m1 ? make_float2(0.f, rA) : make_float2(rA, 0.f);
+        // ---- B(q-1): second colour at plane q-1 (member m1 again), from first-colour values
+        if (q - 1 >= z0 && doB) {
+            const int sr = (q - 1) & 1;
+            const float rxa = m1 ? R.r[sr][ra][pp].x : R.r[sr][ra][pm].y;    // neighbour outside the pair
+            const float ry_m = m1 ? R.r[sr][ra - 1][p].y : R.r[sr][ra - 1][p].x;
+            const float ry_p = m1 ? R.r[sr][ra + 1][p].y : R.r[sr][ra + 1][p].x;
+            const float e0 = m1 ? E_m.y : E_m.x;
+            const float exl = m1 ? E_m.x : bxl, exr = m1 ? bxr : E_m.y;
+            const float rxl = m1 ? R_m : rxa, rxr = m1 ? rxa : R_m;
+            const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
+            const float aym = (e0 + (m1 ? bym.y : bym.x)) * cy, ayp = (e0 + (m1 ? byp.y : byp.x)) * cy;
+            const float azm = (e0 + (m1 ? E_m2.y : E_m2.x)) * cz, azp = (e0 + (m1 ? E_0.y : E_0.x)) * cz;
+            const float sum = axm * rxl + axp * rxr + aym * ry_m + ayp * ry_p + azm * R_m2 + azp * rA;
+            const float d = axm + axp + aym + ayp + azm + azp;
+            const float vB = __fdividef(sum - (m1 ? F_m.y : F_m.x), d);
+            float2* out = reinterpret_cast<float2*>(u_new + (long)(q - 1) * pl + (long)jB * nx) + p;
+            *out = m1 ? make_float2(R_m, vB) : make_float2(vB, R_m);
+        }
+        // ---- shift the z window; keep the eps neighbours at q for B(q) (member 1 - m1)
+        bxl = Exm.y; bxr = Exp.x; bym = Eym; byp = Eyp;
+        U_m = U_0; U_0 = U_p;
+        E_m2 = E_m; E_m = E_0; E_0 = E_p;
+        F_m = F_0;
+        R_m2 = R_m; R_m = rA;
+    }
+    __syncthreads();
+    if (tid == 0 && bad) {
+        // a wait expired: give the copies still in flight a bounded chance to land before the CTA exits
+        const int tl = z1 + 1 - qb;
+        for (int t = tl > 3 ? tl - 3 : 0; t <= tl; ++t) mbar_wait(&R.bar[t & 3], (unsigned)((t >> 2) & 1));
+        if (err) atomicExch(err, 1);
+    }
+}
+
+template <int NPX, int SY>
+void sweep_rows(const LV<float>& L, const float* u_old, const float* f, float* u_new, int first, cudaStream_t s,
+                bool attr, int* err) {
+    const size_t sm = sizeof(RowRing<NPX, SY>);
+    if (attr) {
+        cudaFuncSetAttribute(k_rb_sweep_rows<NPX, SY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        return;
+    }
+    // z chunks so that y tiles x chunks fill one wave of resident CTAs
+    const int per_sm = rows_min_blocks<NPX, SY>();
+    const int ty = (L.ny + SY - 1) / SY;
+    int chunks = 152 * per_sm / ty;
+    if (chunks < 1) chunks = 1;
+    if (chunks > L.nz) chunks = L.nz;
+    const int sz = (L.nz + chunks - 1) / chunks;
+    dim3 grid(1, ty, (L.nz + sz - 1) / sz);
+    k_rb_sweep_rows<NPX, SY><<<grid, NPX * (SY + 2), sm, s>>>(L, u_old, f, u_new, first, sz, err);
+}
+
+// row-tile kernels exist for these row lengths and heights
+#define GP_ROW_NPX(X) X(32) X(48) X(64) X(96) X(128)
+constexpr int kRowShapes = 3;   // SY = 4, 6, 8 (where NPX (SY + 2) <= 1024)
+static_assert(4 + kRowShapes == kSweepShapeCount, "shape count");
+
+template <int NPX>
+bool rows_dispatch_npx(int sy_id, const LV<float>& L, const float* u_old, const float* f, float* u_new, int first,
+                       cudaStream_t s, bool attr, int* err) {
+    if (sy_id == 0) {
+        if constexpr (NPX * 6 <= 1024) { sweep_rows<NPX, 4>(L, u_old, f, u_new, first, s, attr, err); return true; }
+    } else if (sy_id == 1) {
+        if constexpr (NPX * 8 <= 1024) { sweep_rows<NPX, 6>(L, u_old, f, u_new, first, s, attr, err); return true; }
+    } else if (sy_id == 2) {
+        if constexpr (NPX * 10 <= 1024) { sweep_rows<NPX, 8>(L, u_old, f, u_new, first, s, attr, err); return true; }
+    }
+    return false;
+}
+
+// returns false when no row kernel fits this level (nx not covered, or too many threads)
+bool rows_dispatch(int sy_id, int npx, const LV<float>& L, const float* u_old, const float* f, float* u_new,
+                   int first, cudaStream_t s, bool attr, int* err = nullptr) {
+    switch (npx) {
+#define GP_NPX_CASE(N) \
+    case N: return rows_dispatch_npx<N>(sy_id, L, u_old, f, u_new, first, s, attr, err);
+        GP_ROW_NPX(GP_NPX_CASE)
+#undef GP_NPX_CASE
+    }
+    return false;
+}
+
 // tile shapes the autotuner chooses from (x, y)
 #define GP_SWEEP_SHAPES(X) X(0, 64, 8) X(1, 32, 16) X(2, 128, 4) X(3, 32, 8)
 constexpr int kSweepShapes = 4;
@@ -188,7 +467,13 @@ void sweep_shape(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first
 
 template <typename T>
 void sweep_dispatch(int shape, const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s,
-                    bool attr) {
+                    bool attr, int* err = nullptr) {
+    if constexpr (sizeof(T) == 4) {
+        if (shape >= kSweepShapes) {
+            if (rows_dispatch(shape - kSweepShapes, L.nx / 2, L, u_old, f, u_new, first, s, attr, err)) return;
+            shape = 0;
+        }
+    }
     switch (shape) {
 #define GP_CASE(I, X, Y) \
     case I: sweep_shape<T, X, Y>(L, u_old, f, u_new, first, s, attr); break;
@@ -208,11 +493,18 @@ void rb_sweep_init() {
         sweep_dispatch<float>(k, lf, nullptr, nullptr, nullptr, 0, nullptr, true);
         sweep_dispatch<double>(k, ld, nullptr, nullptr, nullptr, 0, nullptr, true);
     }
+    const int npx[] = {32, 48, 64, 96, 128};
+    for (int n : npx)
+        for (int k = 0; k < kRowShapes; ++k) {
+            LV<float> lf{};
+            rows_dispatch(k, n, lf, nullptr, nullptr, nullptr, 0, nullptr, true);
+        }
 }
 
 template <typename T>
-void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s, int shape) {
-    sweep_dispatch<T>(shape, L, u_old, f, u_new, first, s, false);
+void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s, int shape,
+                     int* err) {
+    sweep_dispatch<T>(shape, L, u_old, f, u_new, first, s, false, err);
 }
 
 // Time every tile shape on this level (three sweeps each, CUDA events on the
@@ -225,7 +517,13 @@ int rb_sweep_autotune(const LV<T>& L, const T* u_old, const T* f, T* u_new, cuda
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 0; }
     int best = 0;
     float best_ms = 1e30f;
-    for (int k = 0; k < kSweepShapes; ++k) {
+    const int nshapes = kSweepShapes + (sizeof(T) == 4 ? kRowShapes : 0);
+    for (int k = 0; k < nshapes; ++k) {
+        if (k >= kSweepShapes) {
+            LV<float> probe{};
+            probe.nx = L.nx;
+            if (!rows_dispatch(k - kSweepShapes, L.nx / 2, probe, nullptr, nullptr, nullptr, 0, s, true)) continue;
+        }
         sweep_dispatch<T>(k, L, u_old, f, u_new, 0, s, false);     // warm-up
         cudaEventRecord(a, s);
         for (int r = 0; r < 3; ++r) sweep_dispatch<T>(k, L, u_old, f, u_new, 0, s, false);
@@ -240,8 +538,21 @@ int rb_sweep_autotune(const LV<T>& L, const T* u_old, const T* f, T* u_new, cuda
     return best;
 }
 
-template void launch_rb_sweep<float>(const LV<float>&, const float*, const float*, float*, int, cudaStream_t, int);
-template void launch_rb_sweep<double>(const LV<double>&, const double*, const double*, double*, int, cudaStream_t, int);
+template <typename T>
+int rb_sweep_resolve(const LV<T>& L, int shape) {
+    if (shape < kSweepShapes) return shape;
+    if (sizeof(T) != 4) return 0;
+    LV<float> probe{};
+    probe.nx = L.nx;
+    return rows_dispatch(shape - kSweepShapes, L.nx / 2, probe, nullptr, nullptr, nullptr, 0, nullptr, true) ? shape : 0;
+}
+
+template int rb_sweep_resolve<float>(const LV<float>&, int);
+template int rb_sweep_resolve<double>(const LV<double>&, int);
+template void launch_rb_sweep<float>(const LV<float>&, const float*, const float*, float*, int, cudaStream_t, int,
+                                     int*);
+template void launch_rb_sweep<double>(const LV<double>&, const double*, const double*, double*, int, cudaStream_t,
+                                      int, int*);
 template int rb_sweep_autotune<float>(const LV<float>&, const float*, const float*, float*, cudaStream_t);
 template int rb_sweep_autotune<double>(const LV<double>&, const double*, const double*, double*, cudaStream_t);
 

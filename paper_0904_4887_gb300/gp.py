@@ -33,7 +33,8 @@ class gp_params(ctypes.Structure):
                 ("n_dirichlet", ctypes.c_int), ("precision", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("levels", ctypes.c_int), ("inner", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("accel", ctypes.c_int), ("restart", ctypes.c_int),
-                ("band_vcycles", ctypes.c_int), ("graph_outer", ctypes.c_int)]
+                ("band_vcycles", ctypes.c_int), ("graph_outer", ctypes.c_int),
+                ("sweep_shape", ctypes.c_int)]
 
 
 class gp_stats(ctypes.Structure):

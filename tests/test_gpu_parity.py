@@ -149,6 +149,34 @@ def test_mixed_solve_matches_oracle(small_cases, k, split, accel):
     assert abs(E - E0) < 1e-8 * abs(E0)
 
 
+ROWCASE = ((64, 48, 48), (10.0, 7.5, 12.0), 2, 2)   # nx = 64: the row-tile smoothers apply; 6 rows ragged
+
+
+@pytest.fixture(scope="module")
+def row_case():
+    g, c, n, l = ROWCASE
+    at, h, eps, rho = _case(g, c, n, l)
+    ref, info = O.solve(rho, eps, h, tol=1e-14)
+    return (at, h, eps, rho), g, c, ref
+
+
+@pytest.mark.parametrize("shape", range(7))
+@pytest.mark.parametrize("split", [0, 1])
+def test_every_sweep_shape_converges_to_oracle(row_case, shape, split):
+    """Each finest-level smoother tile (x-y tiles, whole-row tiles with 4, 6, 8
+    rows), on the periodic box and on the Dirichlet wet band, inside the mixed
+    solve, gives the oracle's solution."""
+    GPSolver = _gpu()
+    (at, h, eps, rho), grid, cell, ref = row_case
+    s = GPSolver(grid, cell, precision=1, split=split, sweep_shape=shape)
+    s.set_atoms(_t(at.pos))
+    assert s.stats().sweep_shape == shape
+    assert s.stats().split_active == split
+    phi = s.solve(_t(rho), tol=1e-12).cpu().numpy()
+    assert _rel(phi, ref) < 1e-8
+    assert s.stats().residual < 1e-12
+
+
 def test_split_band_matches_oracle_planner(small_cases):
     GPSolver = _gpu()
     (at, h, eps, rho), grid, cell = small_cases[0]
