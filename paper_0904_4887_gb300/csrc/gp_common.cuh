@@ -108,6 +108,9 @@ struct GaussTabs {
     double* val;    // [G][3][nmax] X, Y, Z factors summed over the images -L, 0, +L
     double* der;    // [G][3][nmax] the same times d / sigma^2 (centre derivative)
     double* coef;   // [G] +-Z / (2 pi sigma^2)^(3/2)
+    float2* vald;   // val, der, coef again as (hi, lo) float pairs (df64) for the
+    float2* derd;   //   FP32-pipe arithmetic of the density kernels
+    float2* coefd;
     int* win;       // [G][3][2] conservative index window of the unshifted image
     int G, nmax;
 };

@@ -236,6 +236,19 @@ __device__ __forceinline__ df df_from(double v) {
     return {h, (float)(v - (double)h)};
 }
 __device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df as_df(float2 v) { return df{v.x, v.y}; }
+
+// (s, c): a compensated pair (value s + c) summed across the warp in place (Knuth two-sum per step)
+__device__ __forceinline__ void warp_sum_df(float& s, float& c) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        const float t = s + s2;
+        const float z = t - s;
+        c += c2 + ((s - (t - z)) + (s2 - z));
+        s = t;
+    }
+}
 
 __device__ __forceinline__ df df_quick(float s, float e) {   // |s| >= |e|
     const float t = s + e;
@@ -300,6 +313,11 @@ __global__ void k_gauss_tables(Geo g, Atoms at, double cut, GaussTabs gt) {
         }
         gt.val[q] = v;
         gt.der[q] = dv;
+        {
+            const float vh = (float)v, dh = (float)dv;
+            gt.vald[q] = make_float2(vh, (float)(v - (double)vh));
+            gt.derd[q] = make_float2(dh, (float)(dv - (double)dh));
+        }
         if (i == 0) {
             // conservative index window [lo, hi] of the image around c (unwrapped;
             // the other images are its shifts by n)
@@ -311,7 +329,10 @@ __global__ void k_gauss_tables(Geo g, Atoms at, double cut, GaussTabs gt) {
             if (axis == 0) {
                 const double Z = at.gauss[3 * a + 0];
                 const double norm = 1.0 / (2.0 * kPi * sg * sg * sqrt(2.0 * kPi * sg * sg));
-                gt.coef[ge] = (which == 0 ? Z : -Z) * norm;
+                const double cf = (which == 0 ? Z : -Z) * norm;
+                gt.coef[ge] = cf;
+                const float ch = (float)cf;
+                gt.coefd[ge] = make_float2(ch, (float)(cf - (double)ch));
             }
         }
     }
@@ -368,15 +389,16 @@ __global__ void __launch_bounds__(TT) k_build_rho(Geo g, GaussTabs gt, double* r
             const int ms = min(RB, m - e0);
             for (int r = threadIdx.x; r < ms * TX; r += TT) {
                 const int e = r / TX, ii = t.i0 + r % TX;
-                gx[e][r % TX] = df_from(ii < g.nx ? gt.val[gt_row(ent[e0 + e], 0, gt.nmax) + ii] : 0.0);
+                gx[e][r % TX] = ii < g.nx ? as_df(gt.vald[gt_row(ent[e0 + e], 0, gt.nmax) + ii]) : df{0.f, 0.f};
             }
             for (int r = threadIdx.x; r < ms * TY * TZ; r += TT) {
                 const int e = r / (TY * TZ), jj = t.j0 + (r % (TY * TZ)) / TZ, kk = t.k0 + r % TZ;
                 const int ge = ent[e0 + e];
-                const double w = (jj < g.ny && kk < g.nz)
-                                     ? gt.coef[ge] * gt.val[gt_row(ge, 1, gt.nmax) + jj] * gt.val[gt_row(ge, 2, gt.nmax) + kk]
-                                     : 0.0;
-                wyz[e][r % (TY * TZ)] = df_from(w);
+                df w = {0.f, 0.f};
+                if (jj < g.ny && kk < g.nz)
+                    w = df_mul(df_mul(as_df(gt.coefd[ge]), as_df(gt.vald[gt_row(ge, 1, gt.nmax) + jj])),
+                               as_df(gt.vald[gt_row(ge, 2, gt.nmax) + kk]));
+                wyz[e][r % (TY * TZ)] = w;
             }
             __syncthreads();
             if (valid)
@@ -594,19 +616,6 @@ __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParam
 // reduces across the warp in df before one FP64 atomic per component.
 constexpr int ECAPF = 384;              // image list capacity of the force kernel
 
-// (s, c) Neumaier pair summed across the warp; returns the total in FP64 on every lane
-__device__ __forceinline__ double warp_sum_pair(float s, float c) {
-    for (int o = 16; o > 0; o >>= 1) {
-        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-        const float t = s + s2;
-        const float z = t - s;
-        c += c2 + ((s - (t - z)) + (s2 - z));
-        s = t;
-    }
-    return (double)s + (double)c;
-}
-
 // exact-to-2^-48 df of the integer c times h (h as a df)
 __device__ __forceinline__ df df_int_mul(int c, df h) {
     const float cf_ = (float)c;
@@ -751,9 +760,11 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
                     df_acc(sy, cy, c, wd[warp][TX + ty]);
                     df_acc(sz, cz, c, wd[warp][TX + TY + tz]);
                 }
-                const double fx = warp_sum_pair(sx, cx), fy = warp_sum_pair(sy, cy), fz = warp_sum_pair(sz, cz);
+                warp_sum_df(sx, cx); warp_sum_df(sy, cy); warp_sum_df(sz, cz);
                 if (lane == 0) {
                     const int a = eatom[e];
+                    const double fx = (double)sx + (double)cx, fy = (double)sy + (double)cy,
+                                 fz = (double)sz + (double)cz;
                     if (fx != 0.0) atomicAdd(&S[3 * a + 0], fx);
                     if (fy != 0.0) atomicAdd(&S[3 * a + 1], fy);
                     if (fz != 0.0) atomicAdd(&S[3 * a + 2], fz);
@@ -951,20 +962,23 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, GaussTabs gt, const do
             const int ge = ent[e];
             if (lane < TY * TZ) {
                 const int jj = t.j0 + lane / TZ, kk = t.k0 + lane % TZ;
-                double w0 = 0.0, wy = 0.0, wz = 0.0;
+                df w0 = {0.f, 0.f}, wy = w0, wz = w0;
                 if (jj < g.ny && kk < g.nz) {
-                    const double cf = gt.coef[ge];
-                    const double Y = gt.val[gt_row(ge, 1, gt.nmax) + jj], Yd = gt.der[gt_row(ge, 1, gt.nmax) + jj];
-                    const double Z = gt.val[gt_row(ge, 2, gt.nmax) + kk], Zd = gt.der[gt_row(ge, 2, gt.nmax) + kk];
-                    w0 = cf * Y * Z; wy = cf * Yd * Z; wz = cf * Y * Zd;
+                    const df cf = as_df(gt.coefd[ge]);
+                    const df cY = df_mul(cf, as_df(gt.vald[gt_row(ge, 1, gt.nmax) + jj]));
+                    const df cYd = df_mul(cf, as_df(gt.derd[gt_row(ge, 1, gt.nmax) + jj]));
+                    const df Z = as_df(gt.vald[gt_row(ge, 2, gt.nmax) + kk]);
+                    w0 = df_mul(cY, Z);
+                    wy = df_mul(cYd, Z);
+                    wz = df_mul(cY, as_df(gt.derd[gt_row(ge, 2, gt.nmax) + kk]));
                 }
-                wr[warp][0][lane] = df_from(w0);
-                wr[warp][1][lane] = df_from(wy);
-                wr[warp][2][lane] = df_from(wz);
+                wr[warp][0][lane] = w0;
+                wr[warp][1][lane] = wy;
+                wr[warp][2][lane] = wz;
             }
             __syncwarp();
-            const double X = lane_ok ? gt.val[gt_row(ge, 0, gt.nmax) + i] : 0.0;
-            const double Xd = lane_ok ? gt.der[gt_row(ge, 0, gt.nmax) + i] : 0.0;
+            const df X = lane_ok ? as_df(gt.vald[gt_row(ge, 0, gt.nmax) + i]) : df{0.f, 0.f};
+            const df Xd = lane_ok ? as_df(gt.derd[gt_row(ge, 0, gt.nmax) + i]) : df{0.f, 0.f};
             float s0 = 0.f, c0 = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
 #pragma unroll 4
             for (int r = 0; r < TY * TZ; ++r) {
@@ -974,15 +988,16 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, GaussTabs gt, const do
                 df_acc(sy, cy, p, wr[warp][1][r]);
                 df_acc(sz, cz, p, wr[warp][2][r]);
             }
-            double fx = Xd * ((double)s0 + (double)c0);
-            double fy = X * ((double)sy + (double)cy);
-            double fz = X * ((double)sz + (double)cz);
-            fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+            df fx = df_mul(Xd, df_quick(s0, c0));
+            df fy = df_mul(X, df_quick(sy, cy));
+            df fz = df_mul(X, df_quick(sz, cz));
+            warp_sum_df(fx.hi, fx.lo); warp_sum_df(fy.hi, fy.lo); warp_sum_df(fz.hi, fz.lo);
             if (lane == 0) {
                 const int a = ge >> 1;
-                if (fx != 0.0) atomicAdd(&T[3 * a + 0], fx);
-                if (fy != 0.0) atomicAdd(&T[3 * a + 1], fy);
-                if (fz != 0.0) atomicAdd(&T[3 * a + 2], fz);
+                const double vx = df_to(fx), vy = df_to(fy), vz = df_to(fz);
+                if (vx != 0.0) atomicAdd(&T[3 * a + 0], vx);
+                if (vy != 0.0) atomicAdd(&T[3 * a + 1], vy);
+                if (vz != 0.0) atomicAdd(&T[3 * a + 2], vz);
             }
             __syncwarp();
         }
@@ -1018,7 +1033,7 @@ void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, 
 
 size_t gauss_tabs_bytes(int n_atoms, int nmax) {
     const size_t G = 2 * (size_t)(n_atoms > 0 ? n_atoms : 1);
-    return sizeof(double) * (2 * G * 3 * nmax + G) + sizeof(int) * G * 6 + 64;
+    return 2 * (sizeof(double) * (2 * G * 3 * nmax + G)) + sizeof(int) * G * 6 + 64;
 }
 
 GaussTabs gauss_tabs_view(void* base, int n_atoms, int nmax) {
@@ -1030,7 +1045,11 @@ GaussTabs gauss_tabs_view(void* base, int n_atoms, int nmax) {
     gt.val = d;
     gt.der = d + G * 3 * nmax;
     gt.coef = d + 2 * G * 3 * nmax;
-    gt.win = reinterpret_cast<int*>(d + 2 * G * 3 * nmax + G);
+    float2* f = reinterpret_cast<float2*>(d + 2 * G * 3 * nmax + G);
+    gt.vald = f;
+    gt.derd = f + G * 3 * nmax;
+    gt.coefd = f + 2 * G * 3 * nmax;
+    gt.win = reinterpret_cast<int*>(f + 2 * G * 3 * nmax + G);
     return gt;
 }
 

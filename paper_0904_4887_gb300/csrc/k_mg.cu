@@ -11,6 +11,9 @@
 // face normal (two faces in series) and full weighting across it.
 #include "gp_common.cuh"
 
+#include <cstdint>
+#include <initializer_list>
+
 namespace gp {
 namespace {
 
@@ -433,6 +436,120 @@ template <typename T>
 __global__ void k_copy(long n, T* dst, const T* src) {
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
         dst[t] = src[t];
+}
+
+// ------------------------------------------------------------ FP32 vector updates, 16-byte accesses
+__device__ __forceinline__ float4 f4_axpy(float a, float4 x, float4 y) {   // a x + y
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+__global__ void k_update_xr4(long n4, float4* __restrict__ x, float4* __restrict__ r, const float4* __restrict__ p,
+                             const float4* __restrict__ q, const double* scal, int num, int den) {
+    __shared__ float alpha_s;
+    if (threadIdx.x == 0) alpha_s = (float)(scal[num] / scal[den]);
+    __syncthreads();
+    const float alpha = alpha_s;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n4; t += (long)gridDim.x * blockDim.x) {
+        x[t] = f4_axpy(alpha, p[t], x[t]);
+        r[t] = f4_axpy(-alpha, q[t], r[t]);
+    }
+}
+
+__global__ void k_update_p4(long n4, float4* __restrict__ p, const float4* __restrict__ z, const double* scal,
+                            int num, int den) {
+    __shared__ float beta_s;
+    if (threadIdx.x == 0) beta_s = (float)(scal[num] / scal[den]);
+    __syncthreads();
+    const float beta = beta_s;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n4; t += (long)gridDim.x * blockDim.x)
+        p[t] = f4_axpy(beta, p[t], z[t]);
+}
+
+__global__ void k_dot4(long n4, const float4* __restrict__ a, const float4* __restrict__ b, double* partial) {
+    __shared__ double red[32];
+    KSum<float> loc;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n4; t += (long)gridDim.x * blockDim.x) {
+        const float4 u = a[t], v = b[t];
+        loc.add(u.x * v.x); loc.add(u.y * v.y); loc.add(u.z * v.z); loc.add(u.w * v.w);
+    }
+    const double s = block_sum(loc.value(), red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_copy4(long n4, float4* __restrict__ dst, const float4* __restrict__ src) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n4; t += (long)gridDim.x * blockDim.x)
+        dst[t] = src[t];
+}
+
+// ------------------------------------------------------------ vectorised finest level
+// The operator on a cell-eps level in FP32, four consecutive x points per
+// thread (16-byte loads of the centre row and of the y and z neighbour rows,
+// two scalar loads for the x neighbours outside the quad). DOT: q = A p and
+// the block's share of p . q (Kahan within the thread); otherwise the
+// residual q = f - A p. Requires nx % 4 == 0.
+template <bool DOT>
+__global__ void __launch_bounds__(kReduceThreads) k_apply4(LV<float> L, const float* __restrict__ p,
+                                                          const float* __restrict__ f, float* __restrict__ q,
+                                                          double* partial) {
+    __shared__ double red[32];
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nx4 = nx >> 2;
+    const long pl = (long)nx * ny;
+    const int total = nx4 * ny * nz;
+    const float hx = 0.5f * L.ihx2, hy = 0.5f * L.ihy2, hz = 0.5f * L.ihz2;
+    KSum<float> acc;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int i4 = t % nx4;
+        const int row = t / nx4;
+        const int j = row % ny, k = row / ny;
+        const long rb = (long)k * pl + (long)j * nx;
+        const long c = rb + 4 * i4;
+        const long cxm = i4 == 0 ? rb + nx - 1 : c - 1;
+        const long cxp = i4 == nx4 - 1 ? rb : c + 4;
+        const long dym = j == 0 ? (long)(ny - 1) * nx : -(long)nx;
+        const long dyp = j == ny - 1 ? -(long)(ny - 1) * nx : (long)nx;
+        const long dzm = (k == 0 && L.zper) ? (long)(nz - 1) * pl : -pl;
+        const long dzp = (k == nz - 1 && L.zper) ? -(long)(nz - 1) * pl : pl;
+        const float4 u0 = *reinterpret_cast<const float4*>(p + c);
+        const float4 uym = *reinterpret_cast<const float4*>(p + c + dym);
+        const float4 uyp = *reinterpret_cast<const float4*>(p + c + dyp);
+        const float4 uzm = *reinterpret_cast<const float4*>(p + c + dzm);
+        const float4 uzp = *reinterpret_cast<const float4*>(p + c + dzp);
+        const float uxm = p[cxm], uxp = p[cxp];
+        const float4 e0 = *reinterpret_cast<const float4*>(L.eps + c);
+        const float4 eym = *reinterpret_cast<const float4*>(L.eps + c + dym);
+        const float4 eyp = *reinterpret_cast<const float4*>(L.eps + c + dyp);
+        const float4 ezm = *reinterpret_cast<const float4*>(L.eps + c + dzm);
+        const float4 ezp = *reinterpret_cast<const float4*>(L.eps + c + dzp);
+        const float exm = L.eps[cxm], exp_ = L.eps[cxp];
+        const float uu[6] = {uxm, u0.x, u0.y, u0.z, u0.w, uxp};
+        const float ee[6] = {exm, e0.x, e0.y, e0.z, e0.w, exp_};
+        const float ym[4] = {uym.x, uym.y, uym.z, uym.w}, yp[4] = {uyp.x, uyp.y, uyp.z, uyp.w};
+        const float zm[4] = {uzm.x, uzm.y, uzm.z, uzm.w}, zp[4] = {uzp.x, uzp.y, uzp.z, uzp.w};
+        const float eym_[4] = {eym.x, eym.y, eym.z, eym.w}, eyp_[4] = {eyp.x, eyp.y, eyp.z, eyp.w};
+        const float ezm_[4] = {ezm.x, ezm.y, ezm.z, ezm.w}, ezp_[4] = {ezp.x, ezp.y, ezp.z, ezp.w};
+        float out[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float e = ee[m + 1], u = uu[m + 1];
+            const float Au = (e + ee[m + 2]) * hx * (uu[m + 2] - u) - (e + ee[m]) * hx * (u - uu[m]) +
+                             (e + eyp_[m]) * hy * (yp[m] - u) - (e + eym_[m]) * hy * (u - ym[m]) +
+                             (e + ezp_[m]) * hz * (zp[m] - u) - (e + ezm_[m]) * hz * (u - zm[m]);
+            out[m] = Au;
+        }
+        if constexpr (DOT) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) acc.add(uu[m + 1] * out[m]);
+            *reinterpret_cast<float4*>(q + c) = make_float4(out[0], out[1], out[2], out[3]);
+        } else {
+            const float4 fv = *reinterpret_cast<const float4*>(f + c);
+            *reinterpret_cast<float4*>(q + c) =
+                make_float4(fv.x - out[0], fv.y - out[1], fv.z - out[2], fv.w - out[3]);
+        }
+    }
+    if constexpr (DOT) {
+        const double sdot = block_sum(acc.value(), red);
+        if (threadIdx.x == 0) partial[blockIdx.x] = sdot;
+    }
 }
 
 // ------------------------------------------------------------ reductions
@@ -864,6 +981,12 @@ template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int col
     k_rbgs<T><<<row_blocks(rows), row_threads(L.nx / 2), 0, s>>>(L, u, f, color);
 }
 template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* f, T* r, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (L.cell && L.nx % 4 == 0) {
+            k_apply4<false><<<kReduceBlocks * 2, kReduceThreads, 0, s>>>(L, u, f, r, nullptr);
+            return;
+        }
+    }
     const long rows = (long)L.ny * L.nz;
     k_residual<T><<<row_blocks(rows), row_threads(L.nx), 0, s>>>(L, u, f, r);
 }
@@ -899,24 +1022,59 @@ template <typename T> void launch_coarse_solve(const LV<T>& C, const T* inv, int
     k_coarse_solve<T><<<1, 512, 0, s>>>(C, inv, n, f, u);
 }
 template <typename T> void launch_applyA_dot(const LV<T>& L, const T* p, T* q, double* partial, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (L.cell && L.nx % 4 == 0) {
+            k_apply4<true><<<kReduceBlocks, kReduceThreads, 0, s>>>(L, p, nullptr, q, partial);
+            return;
+        }
+    }
     k_applyA_dot<T><<<kReduceBlocks, row_threads(L.nx), 0, s>>>(L, p, q, partial);
 }
+// 16-byte vector path: FP32, a multiple of 4 elements, every pointer 16-byte aligned
+inline bool vec4_ok(long n, int elem, std::initializer_list<const void*> ptrs) {
+    if (elem != 4 || n % 4) return false;
+    for (const void* q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) & 15) return false;
+    return true;
+}
+
 template <typename T> void launch_dot(const LV<T>& L, const T* a, const T* b, double* partial, cudaStream_t s) {
     const long n = (long)L.nx * L.ny * L.nz;
+    if (vec4_ok(n, sizeof(T), {a, b})) {
+        k_dot4<<<kReduceBlocks, kReduceThreads, 0, s>>>(n / 4, reinterpret_cast<const float4*>(a),
+                                                         reinterpret_cast<const float4*>(b), partial);
+        return;
+    }
     k_dot<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, a, b, partial);
 }
 template <typename T> void launch_update_xr(const LV<T>& L, T* x, T* r, const T* p, const T* q, const double* scal,
                                             int num, int den, cudaStream_t s) {
     const long n = (long)L.nx * L.ny * L.nz;
+    if (vec4_ok(n, sizeof(T), {x, r, p, q})) {
+        k_update_xr4<<<grid_for(n / 4, 256), 256, 0, s>>>(n / 4, reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(r),
+                                                          reinterpret_cast<const float4*>(p),
+                                                          reinterpret_cast<const float4*>(q), scal, num, den);
+        return;
+    }
     k_update_xr<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, r, p, q, scal, num, den);
 }
 template <typename T> void launch_update_p(const LV<T>& L, T* p, const T* z, const double* scal, int num, int den,
                                            cudaStream_t s) {
     const long n = (long)L.nx * L.ny * L.nz;
+    if (vec4_ok(n, sizeof(T), {p, z})) {
+        k_update_p4<<<grid_for(n / 4, 256), 256, 0, s>>>(n / 4, reinterpret_cast<float4*>(p),
+                                                         reinterpret_cast<const float4*>(z), scal, num, den);
+        return;
+    }
     k_update_p<T><<<grid_for(n, 256), 256, 0, s>>>(n, p, z, scal, num, den);
 }
 template <typename T> void launch_copy_level(const LV<T>& L, T* dst, const T* src, cudaStream_t s) {
     const long n = (long)L.nx * L.ny * L.nz;
+    if (vec4_ok(n, sizeof(T), {dst, src})) {
+        k_copy4<<<grid_for(n / 4, 256), 256, 0, s>>>(n / 4, reinterpret_cast<float4*>(dst),
+                                                     reinterpret_cast<const float4*>(src));
+        return;
+    }
     k_copy<T><<<grid_for(n, 256), 256, 0, s>>>(n, dst, src);
 }
 template <typename T> void launch_cast_eps(long n, const double* e64, T* eT, cudaStream_t s) {
