@@ -205,6 +205,54 @@ __global__ void k_prolong_add(LV<T> F, T* u, LV<T> C, const T* uc) {
     }
 }
 
+// The same trilinear prolongation, four consecutive fine x points per thread
+// (fine nx % 4 == 0, FP32): coarse x indices 2q, 2q+1, 2q+2 (wrapped) serve
+// the quad, with the one or two coarse rows and planes of its (j, k).
+__global__ void __launch_bounds__(256) k_prolong_add4(LV<float> F, float* __restrict__ u, LV<float> C,
+                                                      const float* __restrict__ uc) {
+    const int nx4 = F.nx >> 2;
+    const int total = nx4 * F.ny * F.nz;
+    const int zoff = F.zper ? 0 : 1;
+    const long cpl = (long)C.nx * C.ny;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int q = t % nx4;
+        const int row = t / nx4;
+        const int j = row % F.ny, k = row / F.ny;
+        const int I0 = 2 * q, I1 = I0 + 1, I2 = (I0 + 2 == C.nx) ? 0 : I0 + 2;
+        int y0 = j >> 1, y1 = y0;
+        float wy0 = 1.f, wy1 = 0.f;
+        if (j & 1) { y1 = (y0 + 1 == C.ny) ? 0 : y0 + 1; wy0 = wy1 = 0.5f; }
+        const int kk = k - zoff;
+        int z0, z1;
+        float wz0 = 1.f, wz1 = 0.f;
+        if (kk & 1) {
+            z0 = (kk - 1) >> 1;
+            z1 = z0 + 1;
+            if (C.zper && z1 == C.nz) z1 = 0;
+            wz0 = wz1 = 0.5f;
+        } else { z0 = kk >> 1; z1 = z0; }
+        // coarse values along x at the (y, z) combinations, weighted
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        {
+            const float* r00 = uc + cpl * z0 + (long)C.nx * y0;
+            const float* r01 = uc + cpl * z0 + (long)C.nx * y1;
+            const float* r10 = uc + cpl * z1 + (long)C.nx * y0;
+            const float* r11 = uc + cpl * z1 + (long)C.nx * y1;
+            const float w00 = wz0 * wy0, w01 = wz0 * wy1, w10 = wz1 * wy0, w11 = wz1 * wy1;
+            a0 = w00 * r00[I0] + w01 * r01[I0] + w10 * r10[I0] + w11 * r11[I0];
+            a1 = w00 * r00[I1] + w01 * r01[I1] + w10 * r10[I1] + w11 * r11[I1];
+            a2 = w00 * r00[I2] + w01 * r01[I2] + w10 * r10[I2] + w11 * r11[I2];
+        }
+        float4* up = reinterpret_cast<float4*>(u + (long)F.nx * (j + (long)F.ny * k)) + q;
+        float4 v = *up;
+        v.x += a0;
+        v.y += 0.5f * (a0 + a1);
+        v.z += a1;
+        v.w += 0.5f * (a1 + a2);
+        *up = v;
+    }
+}
+
 // fine face coefficient along `axis` between (i,j,k) and its + neighbour; k may be -1 (wall face)
 template <typename T>
 __device__ __forceinline__ T fine_face(const LV<T>& F, int axis, int i, int j, int k) {
@@ -603,11 +651,20 @@ __global__ void __launch_bounds__(kReduceThreads) k_residual64(Geo g, const doub
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
         const int j = (int)(row % g.ny), k = (int)(row / g.ny);
         const Nb nb = neighbours(g.nx, g.ny, g.nz, 1, i, j, k);
-        const double e0 = eps[nb.c], p0 = phi[nb.c];
-        const double ax = (e0 + eps[nb.xp]) * (phi[nb.xp] - p0) - (e0 + eps[nb.xm]) * (p0 - phi[nb.xm]);
-        const double ay = (e0 + eps[nb.yp]) * (phi[nb.yp] - p0) - (e0 + eps[nb.ym]) * (p0 - phi[nb.ym]);
-        const double az = (e0 + eps[nb.zp]) * (phi[nb.zp] - p0) - (e0 + eps[nb.zm]) * (p0 - phi[nb.zm]);
-        const double r = -fpi * rho[nb.c] - (hx * ax + hy * ay + hz * az);
+        const double p0 = phi[nb.c];
+        const double pxp = phi[nb.xp], pxm = phi[nb.xm], pyp = phi[nb.yp], pym = phi[nb.ym];
+        const double pzp = phi[nb.zp], pzm = phi[nb.zm];
+        const double e0 = eps[nb.c], exp_ = eps[nb.xp], exm = eps[nb.xm], eyp = eps[nb.yp], eym = eps[nb.ym];
+        const double ezp = eps[nb.zp], ezm = eps[nb.zm];
+        double r = -fpi * rho[nb.c];
+        // A phi is exactly 0 where phi and its six neighbours are 0 (a cold start):
+        // the FP64 stencil is then skipped, with the same result
+        if (p0 != 0.0 || pxp != 0.0 || pxm != 0.0 || pyp != 0.0 || pym != 0.0 || pzp != 0.0 || pzm != 0.0) {
+            const double ax = (e0 + exp_) * (pxp - p0) - (e0 + exm) * (p0 - pxm);
+            const double ay = (e0 + eyp) * (pyp - p0) - (e0 + eym) * (p0 - pym);
+            const double az = (e0 + ezp) * (pzp - p0) - (e0 + ezm) * (p0 - pzm);
+            r -= hx * ax + hy * ay + hz * az;
+        }
         r_out[nb.c] = (T)r;
         s2 += r * r;
         sp += p0;
@@ -995,6 +1052,13 @@ template <typename T> void launch_restrict(const LV<T>& F, const T* r, const LV<
     k_restrict<T><<<row_blocks(rows), row_threads(C.nx), 0, s>>>(F, r, C, fc);
 }
 template <typename T> void launch_prolong_add(const LV<T>& F, T* u, const LV<T>& C, const T* uc, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (F.nx % 4 == 0 && C.nx * 2 == F.nx && (reinterpret_cast<uintptr_t>(u) & 15) == 0) {
+            const long quads = (long)F.nx * F.ny * F.nz / 4;
+            k_prolong_add4<<<grid_for(quads, 256), 256, 0, s>>>(F, u, C, uc);
+            return;
+        }
+    }
     const long rows = (long)F.ny * F.nz;
     k_prolong_add<T><<<row_blocks(rows), row_threads(F.nx), 0, s>>>(F, u, C, uc);
 }
