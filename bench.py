@@ -154,7 +154,8 @@ def gpu_arm(args, rank, world):
     hbm, hbm_src = load_peaks()
 
     def make_solver(precision, split):
-        return P.GPSolver(w.grid, w.cell, precision=precision, split=split, levels=w.levels)
+        return P.GPSolver(w.grid, w.cell, precision=precision, split=split, levels=w.levels,
+                          sweep_shape=args.sweep_shape)
 
     solver = make_solver(args.precision, args.split)
     rho = solver.zeros()
@@ -445,6 +446,8 @@ def main():
     ap.add_argument("--mode", default="step", choices=["step", "md"])
     ap.add_argument("--frames", type=int, default=100)
     ap.add_argument("--graph-outer", type=int, default=2)
+    ap.add_argument("--sweep-shape", type=int, default=-1,
+                    help="finest-level smoother tile (-1: autotuned; fixed shapes keep profiles comparable)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gp":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -18,6 +18,8 @@
 // traffic: read u_old, eps, f and write u_new, 16 bytes per point in FP32.
 #include "gp_common.cuh"
 
+#include <type_traits>
+
 namespace gp {
 namespace {
 
@@ -179,17 +181,20 @@ __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ 
 //   B(q-1) second colour at plane q-1, rows j0 .. j0+SY-1, from the new
 //          first-colour values at planes q-2, q-1, q; writes plane q-1 of u_new.
 // Planes of u_old, eps and f arrive by TMA bulk copies (one per row, whole
-// rows are contiguous in memory) three planes ahead into a 4-slot ring, each
-// slot completing an mbarrier phase. Every wait is bounded: on expiry the
-// kernel records the fact in *err and runs to its end without further waits.
+// rows are contiguous in memory) NSLOT-1 planes ahead into an NSLOT ring, each
+// slot completing an mbarrier phase. Warp 0 waits on the phase and the CTA
+// barrier releases the others. Every wait is bounded: on expiry the kernel
+// records the fact in *err and runs to its end without further waits.
+constexpr int NSLOT = 6;
+
 template <int NPX, int SY>
 struct RowRing {
     static constexpr int RU = SY + 4, RF = SY + 2;
-    float2 u[4][RU][NPX];
-    float2 e[4][RU][NPX];
-    float2 f[4][RF][NPX];
+    float2 u[NSLOT][RU][NPX];
+    float2 e[NSLOT][RU][NPX];
+    float2 f[NSLOT][RF][NPX];
     float2 r[2][RF][NPX];
-    unsigned long long bar[4];
+    unsigned long long bar[NSLOT];
 };
 
 __device__ __forceinline__ int wrap_idx(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -264,17 +269,17 @@ __global__ void __launch_bounds__(NPX * (SY + 2), rows_min_blocks<NPX, SY>())
 
     if (tid == 0) {
         bad = 0;
-        for (int k = 0; k < 4; ++k) mbar_init(&R.bar[k], 1);
+        for (int k = 0; k < NSLOT; ++k) mbar_init(&R.bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
 
-    // plane q into slot (q - qb) & 3: warp 0 issues one bulk copy per row;
+    // plane q into slot (q - qb) % NSLOT: warp 0 issues one bulk copy per row;
     // planes outside the data (beyond the Dirichlet walls, f on the walls) are
     // filled by the threads with plain stores instead
     auto issue = [&](int q) {
         if (q > z1 + 1) return;
-        const int slot = (q - qb) & 3;
+        const int slot = (q - qb) % NSLOT;
         int kg;
         if (L.zper) kg = q < 0 ? q + nz : (q >= nz ? q - nz : q);
         else kg = (q < -1 || q > nz) ? -99 : q;
@@ -305,9 +310,9 @@ __global__ void __launch_bounds__(NPX * (SY + 2), rows_min_blocks<NPX, SY>())
             }
         if (!inner) (&R.f[slot][0][0])[tid] = make_float2(0.f, 0.f);
     };
-    auto wait_plane = [&](int q) {
+    auto wait_plane = [&](int q) {            // warp 0 only
         const int t = q - qb;
-        if (!bad && !mbar_wait(&R.bar[t & 3], (unsigned)((t >> 2) & 1))) bad = 1;
+        if (!bad && !mbar_wait(&R.bar[t % NSLOT], (unsigned)((t / NSLOT) & 1))) bad = 1;
     };
 
     float2 U_m = make_float2(0.f, 0.f), U_0 = U_m;          // own u_old at q-1, q
@@ -318,15 +323,15 @@ __global__ void __launch_bounds__(NPX * (SY + 2), rows_min_blocks<NPX, SY>())
     float2 bym = make_float2(1.f, 1.f), byp = bym;           // eps rows j-1, j+1 at q-1 (for B)
     const int rs = ra + 1;                                   // this thread's row in the u / e arrays
 
-    issue(qb);
-    issue(qb + 1);
-    issue(qb + 2);
+    for (int k = 0; k < NSLOT - 1; ++k) issue(qb + k);
     for (int q = qb; q <= z1; ++q) {
-        if (q == qb) wait_plane(q);
-        wait_plane(q + 1);                                 // planes <= q+1 landed
-        __syncthreads();                                   // every thread done with slot q-1
-        issue(q + 3);                                      // into slot (q+3-qb)&3 == (q-1-qb)&3
-        const int s0 = (q - qb) & 3, s1 = (q + 1 - qb) & 3;
+        if (tid < 32) {
+            if (q == qb) wait_plane(q);
+            wait_plane(q + 1);                             // planes <= q+1 landed
+        }
+        __syncthreads();                                   // ... seen by all; every thread done with slot q-1
+        issue(q + NSLOT - 1);                              // into the slot of plane q-1
+        const int s0 = (q - qb) % NSLOT, s1 = (q + 1 - qb) % NSLOT;
         if (q == qb) {                                     // prime the z window: own values at z0-2, z0-1
             U_m = R.u[s0][rs][p];
             E_m = R.e[s0][rs][p];
@@ -334,49 +339,54 @@ __global__ void __launch_bounds__(NPX * (SY + 2), rows_min_blocks<NPX, SY>())
             E_0 = R.e[s1][rs][p];
             continue;
         }
-        // ---- A(q): first colour at plane q, member m1 of the own pair
-        const int m1 = (parA + q) & 1;
+        // ---- A(q): first colour at plane q, member m1 of the own pair; then
+        // B(q-1): second colour at plane q-1 (member m1 again). m1 is uniform
+        // along a row, so both members get their own straight-line code.
         const float2 U_p = R.u[s1][rs][p];                 // own at q+1
         const float2 E_p = R.e[s1][rs][p];
         const float2 F_0 = R.f[s0][ra][p];
         const float2 Exm = R.e[s0][rs][pm], Exp = R.e[s0][rs][pp];
         const float2 Eym = R.e[s0][rs - 1][p], Eyp = R.e[s0][rs + 1][p];
-        float rA;
         const bool wall = !L.zper && (q == -1 || q == nz);
-        {
-            const float uxa = m1 ? R.u[s0][rs][pp].x : R.u[s0][rs][pm].y;   // the x neighbour outside the pair
-            const float2 Uym = R.u[s0][rs - 1][p], Uyp = R.u[s0][rs + 1][p];
-            const float e0 = m1 ? E_0.y : E_0.x;
-            const float exl = m1 ? E_0.x : Exm.y, exr = m1 ? Exp.x : E_0.y;
-            const float uxl = m1 ? U_0.x : uxa, uxr = m1 ? uxa : U_0.y;
-            const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
-            const float aym = (e0 + (m1 ? Eym.y : Eym.x)) * cy, ayp = (e0 + (m1 ? Eyp.y : Eyp.x)) * cy;
-            const float azm = (e0 + (m1 ? E_m.y : E_m.x)) * cz, azp = (e0 + (m1 ? E_p.y : E_p.x)) * cz;
-            const float sum = axm * uxl + axp * uxr + aym * (m1 ? Uym.y : Uym.x) + ayp * (m1 ? Uyp.y : Uyp.x) +
-                              azm * (m1 ? U_m.y : U_m.x) + azp * (m1 ? U_p.y : U_p.x);
-            const float d = axm + axp + aym + ayp + azm + azp;
-            rA = wall ? (m1 ? U_0.y : U_0.x) : __fdividef(sum - (m1 ? F_0.y : F_0.x), d);
-        }
-        R.r[q & 1][ra][p] = m1 ? make_float2(0.f, rA) : make_float2(rA, 0.f);
-        // ---- B(q-1): second colour at plane q-1 (member m1 again), from first-colour values
-        if (q - 1 >= z0 && doB) {
-            const int sr = (q - 1) & 1;
-            const float rxa = m1 ? R.r[sr][ra][pp].x : R.r[sr][ra][pm].y;    // neighbour outside the pair
-            const float ry_m = m1 ? R.r[sr][ra - 1][p].y : R.r[sr][ra - 1][p].x;
-            const float ry_p = m1 ? R.r[sr][ra + 1][p].y : R.r[sr][ra + 1][p].x;
-            const float e0 = m1 ? E_m.y : E_m.x;
-            const float exl = m1 ? E_m.x : bxl, exr = m1 ? bxr : E_m.y;
-            const float rxl = m1 ? R_m : rxa, rxr = m1 ? rxa : R_m;
-            const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
-            const float aym = (e0 + (m1 ? bym.y : bym.x)) * cy, ayp = (e0 + (m1 ? byp.y : byp.x)) * cy;
-            const float azm = (e0 + (m1 ? E_m2.y : E_m2.x)) * cz, azp = (e0 + (m1 ? E_0.y : E_0.x)) * cz;
-            const float sum = axm * rxl + axp * rxr + aym * ry_m + ayp * ry_p + azm * R_m2 + azp * rA;
-            const float d = axm + axp + aym + ayp + azm + azp;
-            const float vB = __fdividef(sum - (m1 ? F_m.y : F_m.x), d);
-            float2* out = reinterpret_cast<float2*>(u_new + (long)(q - 1) * pl + (long)jB * nx) + p;
-            *out = m1 ? make_float2(R_m, vB) : make_float2(vB, R_m);
-        }
-        // ---- shift the z window; keep the eps neighbours at q for B(q) (member 1 - m1)
+        const bool runB = q - 1 >= z0 && doB;
+        float rA;
+        auto step = [&](auto mc) {
+            constexpr int M = decltype(mc)::value;
+            auto pick = [](float2 v) { return M ? v.y : v.x; };
+            {
+                const float uxa = M ? R.u[s0][rs][pp].x : R.u[s0][rs][pm].y;   // x neighbour outside the pair
+                const float uym = pick(R.u[s0][rs - 1][p]), uyp = pick(R.u[s0][rs + 1][p]);
+                const float e0 = pick(E_0);
+                const float exl = M ? E_0.x : Exm.y, exr = M ? Exp.x : E_0.y;
+                const float uxl = M ? U_0.x : uxa, uxr = M ? uxa : U_0.y;
+                const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
+                const float aym = (e0 + pick(Eym)) * cy, ayp = (e0 + pick(Eyp)) * cy;
+                const float azm = (e0 + pick(E_m)) * cz, azp = (e0 + pick(E_p)) * cz;
+                const float sum = axm * uxl + axp * uxr + aym * uym + ayp * uyp + azm * pick(U_m) + azp * pick(U_p);
+                const float d = axm + axp + aym + ayp + azm + azp;
+                rA = wall ? pick(U_0) : __fdividef(sum - pick(F_0), d);
+            }
+            R.r[q & 1][ra][p] = M ? make_float2(0.f, rA) : make_float2(rA, 0.f);
+            if (runB) {
+                const int sr = (q - 1) & 1;
+                const float rxa = M ? R.r[sr][ra][pp].x : R.r[sr][ra][pm].y;    // neighbour outside the pair
+                const float ry_m = pick(R.r[sr][ra - 1][p]), ry_p = pick(R.r[sr][ra + 1][p]);
+                const float e0 = pick(E_m);
+                const float exl = M ? E_m.x : bxl, exr = M ? bxr : E_m.y;
+                const float rxl = M ? R_m : rxa, rxr = M ? rxa : R_m;
+                const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
+                const float aym = (e0 + pick(bym)) * cy, ayp = (e0 + pick(byp)) * cy;
+                const float azm = (e0 + pick(E_m2)) * cz, azp = (e0 + pick(E_0)) * cz;
+                const float sum = axm * rxl + axp * rxr + aym * ry_m + ayp * ry_p + azm * R_m2 + azp * rA;
+                const float d = axm + axp + aym + ayp + azm + azp;
+                const float vB = __fdividef(sum - pick(F_m), d);
+                float2* out = reinterpret_cast<float2*>(u_new + (long)(q - 1) * pl + (long)jB * nx) + p;
+                *out = M ? make_float2(R_m, vB) : make_float2(vB, R_m);
+            }
+        };
+        if ((parA + q) & 1) step(std::integral_constant<int, 1>{});
+        else step(std::integral_constant<int, 0>{});
+        // ---- shift the z window; keep the eps neighbours at q for B(q) (the other member)
         bxl = Exm.y; bxr = Exp.x; bym = Eym; byp = Eyp;
         U_m = U_0; U_0 = U_p;
         E_m2 = E_m; E_m = E_0; E_0 = E_p;
@@ -387,7 +397,8 @@ __global__ void __launch_bounds__(NPX * (SY + 2), rows_min_blocks<NPX, SY>())
     if (tid == 0 && bad) {
         // a wait expired: give the copies still in flight a bounded chance to land before the CTA exits
         const int tl = z1 + 1 - qb;
-        for (int t = tl > 3 ? tl - 3 : 0; t <= tl; ++t) mbar_wait(&R.bar[t & 3], (unsigned)((t >> 2) & 1));
+        for (int t = tl > NSLOT - 1 ? tl - (NSLOT - 1) : 0; t <= tl; ++t)
+            mbar_wait(&R.bar[t % NSLOT], (unsigned)((t / NSLOT) & 1));
         if (err) atomicExch(err, 1);
     }
 }
