@@ -47,6 +47,34 @@ def load_peaks():
 
 FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (non-tensor), the profiling recipe's table
 
+SWEEP_PROFILE = os.path.join(ROOT, "profiles", "k_rb_sweep_mixed_192x192x384.txt")
+SWEEP_SOURCE = os.path.join(ROOT, "paper_0904_4887_gb300", "csrc", "k_smooth.cu")
+
+
+def source_digest(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def sweep_traffic(kernel_name, workload):
+    """DRAM bytes per launch of the smoother from the committed ncu summary, or
+    None when the summary is for another kernel, workload or kernel source."""
+    try:
+        fields = {}
+        with open(SWEEP_PROFILE) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("workload") != workload or fields.get("source_digest") != source_digest(SWEEP_SOURCE):
+            return None
+        if kernel_name not in fields.get("kernel", ""):
+            return None
+        return float(fields["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
@@ -227,8 +255,15 @@ def gpu_arm(args, rank, world):
     total_ms = sum(v["ms"] for v in prof.values())
     dominant = max(prof, key=lambda k: prof[k]["ms"])
     roof = roofline_for(dominant, prof, n0, hbm, hbm_src, prec_bytes) or {}
-    roof["traffic"] = None
+    shape_kernel = {0: "k_rb_sweep<float, 64, 8>", 1: "k_rb_sweep<float, 32, 16>", 2: "k_rb_sweep<float, 128, 4>",
+                    3: "k_rb_sweep<float, 32, 8>"}.get(stats.sweep_shape, "k_rb_sweep_rows")
     smooth = roofline_for("smooth0", prof, n0, hbm, hbm_src, prec_bytes)
+    if smooth is not None:
+        smooth["kernel"] = shape_kernel + " (finest level, fused red-black sweep)"
+        smooth["traffic"] = sweep_traffic(shape_kernel, w.name) if args.precision == 1 else None
+    roof["traffic"] = smooth["traffic"] if (smooth is not None and dominant == "smooth0") else None
+    if dominant == "smooth0" and smooth is not None:
+        roof["kernel"] = smooth["kernel"]
     phases = {k: {"ms_per_step": v["ms"] / args.steps, "share": (v["ms"] / total_ms if total_ms else 0.0),
                   "launches_per_step": v["launches"] / args.steps} for k, v in prof.items() if v["launches"]}
 
