@@ -159,6 +159,80 @@ def dielectric_gradient_atom(a, grid, cell, pos, P, p: DielectricParams = Dielec
 
 
 # ----------------------------------------------------------------------------
+# the dummy-density dielectric of Eq. 9-10 and its atomic derivative (Eq. 12)
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass(frozen=True)
+class GammaParams:
+    """Eq. 9: gamma(r) = sum_I exp(-(|r - R_I| - Rvdw_I)), over atoms and their
+    periodic images with |r - R_I| < rcut (the paper gives no cut-off; rcut is
+    chosen where gamma^(2 beta) is negligible).
+    Eq. 10: eps = 1 + (eps0 - 1)/2 (1 + (1 - gamma^(2 beta))/(1 + gamma^(2 beta))).
+    """
+    eps0: float = 78.36
+    beta: float = 2.4
+    rcut: float = 8.0
+
+
+def dummy_density(grid, cell, pos, rvdw, p: GammaParams = GammaParams()):
+    """gamma on the grid (Eq. 9)."""
+    g = np.zeros((grid[2], grid[1], grid[0]))
+    for R, rv in zip(pos, rvdw):
+        for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, p.rcut):
+            d = np.sqrt(dx * dx + dy * dy + dz * dz)
+            g[sl] += np.where(d < p.rcut, np.exp(-(d - rv)), 0.0)
+    return g
+
+
+def eps_of_gamma(gamma, p: GammaParams = GammaParams()):
+    """Eq. 10, written as the paper prints it."""
+    t = gamma ** (2.0 * p.beta)
+    return 1.0 + 0.5 * (p.eps0 - 1.0) * (1.0 + (1.0 - t) / (1.0 + t))
+
+
+def deps_dgamma(gamma, p: GammaParams = GammaParams()):
+    """d eps/d gamma of Eq. 10: -(eps0 - 1) 2 beta gamma^(2 beta - 1)/(1 + gamma^(2 beta))^2."""
+    t = gamma ** (2.0 * p.beta)
+    gm = np.where(gamma > 0, gamma, 1.0)
+    return np.where(gamma > 0, -(p.eps0 - 1.0) * 2.0 * p.beta * t / gm / (1.0 + t) ** 2, 0.0)
+
+
+def dielectric_gamma(grid, cell, pos, rvdw, p: GammaParams = GammaParams()):
+    """eps on the grid from Eq. 9-10."""
+    return eps_of_gamma(dummy_density(grid, cell, pos, rvdw, p), p)
+
+
+def dielectric_gamma_points(points, cell, pos, rvdw, p: GammaParams = GammaParams()):
+    """Eq. 9-10 at arbitrary points (M, 3), one by one over atoms and all 27 images."""
+    points = np.asarray(points, dtype=np.float64)
+    cell = np.asarray(cell, dtype=np.float64)
+    g = np.zeros(len(points))
+    for R, rv in zip(pos, rvdw):
+        for n in itertools.product((-1, 0, 1), repeat=3):
+            d = np.linalg.norm(points - (R + np.asarray(n) * cell), axis=1)
+            g += np.where(d < p.rcut, np.exp(-(d - rv)), 0.0)
+    return eps_of_gamma(g, p)
+
+
+def dielectric_gamma_gradient_atom(a, grid, cell, pos, rvdw, gamma, p: GammaParams = GammaParams()):
+    """d eps_i / d R_a (x, y, z arrays) for Eq. 9-10: by the chain rule,
+    (d eps/d gamma) sum_images exp(-(d - Rvdw_a)) (r - R_a)/d, because
+    d|r - R_a|/dR_a = -(r - R_a)/d. This is Eq. 12 with the opposite sign to
+    the printed one: moving an atom towards r raises gamma there and lowers eps.
+    """
+    fe = deps_dgamma(gamma, p)
+    out = [np.zeros_like(gamma) for _ in range(3)]
+    for sl, (dz, dy, dx) in _image_boxes(pos[a], grid, cell, p.rcut):
+        d = np.sqrt(dx * dx + dy * dy + dz * dz)
+        dsafe = np.where(d > 0, d, 1.0)
+        coef = np.where((d < p.rcut) & (d > 0), fe[sl] * np.exp(-(d - rvdw[a])) / dsafe, 0.0)
+        out[0][sl] += coef * dx
+        out[1][sl] += coef * dy
+        out[2][sl] += coef * dz
+    return out
+
+
+# ----------------------------------------------------------------------------
 # charge density: +Z core and -Z cloud Gaussians per atom (Sec. II.A)
 # ----------------------------------------------------------------------------
 
@@ -380,7 +454,7 @@ def variational_energy(rho, phi, eps, grid, cell):
 
 
 def energy_gradient(phi, grid, cell, pos, Z, sigma_core, sigma_cloud,
-                    p: DielectricParams = DielectricParams(), atoms=None, rho_moves=True):
+                    p=DielectricParams(), atoms=None, rho_moves=True, rvdw=None):
     """G_a = dE/dR_a = G^eps_a + G^rho_a, the discrete Eq. 11.
 
     G^eps_a = -h^3/(8 pi) sum_faces (d eps_f/dR_a)(Delta_f phi/h)^2, with
@@ -390,12 +464,18 @@ def energy_gradient(phi, grid, cell, pos, Z, sigma_core, sigma_cloud,
     Returns (G_eps, G_rho), each (n_atoms, 3); rows of atoms not in `atoms` are
     zero. `phi` must be the solution for this geometry: because A is symmetric
     it is its own adjoint (Appendix B), so no further solve is needed.
+    `p` is DielectricParams (erf product) or GammaParams (Eq. 9-10, with the
+    radii `rvdw`).
     """
     h = spacing(grid, cell)
     dv = cell_volume_element(grid, cell)
     n = len(pos)
     atoms = range(n) if atoms is None else atoms
-    P = dielectric_product(grid, cell, pos, p)
+    gamma_form = isinstance(p, GammaParams)
+    if gamma_form:
+        G = dummy_density(grid, cell, pos, rvdw, p)
+    else:
+        P = dielectric_product(grid, cell, pos, p)
     grads2 = []
     for c in range(3):
         ax = AX[c]
@@ -404,7 +484,10 @@ def energy_gradient(phi, grid, cell, pos, Z, sigma_core, sigma_cloud,
     Ge = np.zeros((n, 3))
     Gr = np.zeros((n, 3))
     for a in atoms:
-        de = dielectric_gradient_atom(a, grid, cell, pos, P, p)
+        if gamma_form:
+            de = dielectric_gamma_gradient_atom(a, grid, cell, pos, rvdw, G, p)
+        else:
+            de = dielectric_gradient_atom(a, grid, cell, pos, P, p)
         for comp in range(3):
             s = 0.0
             for ax, g2 in grads2:

@@ -366,3 +366,104 @@ def test_split_fixed_point_equals_full_box():
     split, hist = O.split_solve(rho, eps, h, band, tol=1e-13)
     assert hist[-1] < 1e-12
     assert np.max(np.abs(split - full)) < 1e-10 * np.max(np.abs(full))
+
+
+# -------------------------------------------------------------- Eq. 9-10 dielectric
+
+def _radii(Z):
+    """Synthetic van der Waals radii per species: "O" (Z=6) 1.52 A, "Ti" (Z=4) 2.0 A."""
+    return np.where(np.asarray(Z) == 6, 1.52, 2.0)
+
+
+def test_gamma_dielectric_is_centred_on_the_vdw_radius():
+    """Eq. 10: one atom, a point at |r - R| = Rvdw has gamma = 1 and eps = (1 + eps0)/2
+    whatever beta; eps grows monotonically with the distance along a ray."""
+    grid, cell = (40, 40, 40), (20.0, 20.0, 20.0)          # h = 0.5
+    pos = np.array([[10.0, 10.0, 10.0]])
+    rv = np.array([1.5])
+    for beta in (1.0, 2.4, 4.0):
+        p = O.GammaParams(beta=beta, rcut=7.0)
+        eps = O.dielectric_gamma(grid, cell, pos, rv, p)
+        assert abs(eps[20, 20, 23] - 0.5 * (1.0 + p.eps0)) < 1e-12     # x = 11.5: d = 1.5
+        ray = eps[20, 20, 20:34]
+        assert np.all(np.diff(ray) > 0)
+        assert ray[0] < 1.0 + 0.1 * (p.eps0 - 1.0) and ray[-1] > p.eps0 - 1e-2
+
+
+def test_gamma_dielectric_printed_form_equals_simplified_form():
+    """Eq. 10 as printed, 1 + (eps0-1)/2 (1 + (1 - t)/(1 + t)), equals 1 + (eps0-1)/(1 + t),
+    t = gamma^(2 beta), which is the form the CUDA kernel evaluates."""
+    rng = np.random.default_rng(3)
+    g = np.concatenate([rng.uniform(0, 3, 200), [0.0, 1.0, 1e-8, 50.0]])
+    p = O.GammaParams()
+    simple = 1.0 + (p.eps0 - 1.0) / (1.0 + g ** (2 * p.beta))
+    assert np.max(np.abs(O.eps_of_gamma(g, p) - simple)) < 1e-12 * p.eps0
+
+
+def test_gamma_dielectric_grid_equals_27_image_brute_force():
+    """Bounding-box images of the grid builder against the one-by-one evaluator."""
+    grid, cell = (12, 10, 14), (8.0, 7.0, 9.0)
+    at = W.slab_atoms(cell, 2, 1, seed=4)
+    rv = _radii(at.Z)
+    p = O.GammaParams(rcut=6.5)
+    eps = O.dielectric_gamma(grid, cell, at.pos, rv, p)
+    x, y, z = _grid_points(grid, cell)
+    pts = np.stack([np.broadcast_to(x, eps.shape).ravel(), np.broadcast_to(y, eps.shape).ravel(),
+                    np.broadcast_to(z, eps.shape).ravel()], axis=1)
+    ref = O.dielectric_gamma_points(pts, cell, at.pos, rv, p).reshape(eps.shape)
+    assert np.max(np.abs(eps - ref)) < 1e-12 * p.eps0
+
+
+def test_gamma_dielectric_gradient_matches_fd_and_fixes_eq12_sign():
+    """d eps/d R_a against central differences of the grid eps; the printed Eq. 12
+    (positive prefactor) has the opposite sign of the finite differences."""
+    grid, cell = (16, 16, 16), (8.0, 8.0, 8.0)
+    pos = np.array([[3.1, 4.2, 3.9], [5.0, 3.3, 4.6]])
+    rv = np.array([1.52, 2.0])
+    p = O.GammaParams(rcut=6.0)
+    G = O.dummy_density(grid, cell, pos, rv, p)
+    de = O.dielectric_gamma_gradient_atom(0, grid, cell, pos, rv, G, p)
+    d = 1e-5
+    for c in range(3):
+        pp = pos.copy(); pp[0, c] += d
+        pm = pos.copy(); pm[0, c] -= d
+        fd = (O.dielectric_gamma(grid, cell, pp, rv, p) - O.dielectric_gamma(grid, cell, pm, rv, p)) / (2 * d)
+        scale = np.max(np.abs(fd))
+        assert scale > 1.0
+        assert np.max(np.abs(fd - de[c])) < 1e-6 * scale
+        assert float(np.sum(fd * (-de[c]))) < 0          # the printed sign disagrees with the FD
+
+
+def test_gamma_forces_match_central_differences():
+    """P9 for the Eq. 9-10 dielectric: dE/dR_a (eps term, rho frozen) against central
+    differences of the variational energy J. The cut-off is taken where the
+    truncation of gamma moves eps by < 1e-10 (a cut-off where it is visible puts
+    steps into E(R) that central differences pick up)."""
+    grid, cell = (16, 16, 24), (8.0, 8.0, 12.0)
+    at = W.slab_atoms(cell, 2, 2, seed=1)
+    rv = _radii(at.Z)
+    p = O.GammaParams(rcut=7.9)
+    h = O.spacing(grid, cell)
+    pos = at.pos
+    rho = O.charge_density(grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud)
+
+    def E_of(q):
+        eps = O.dielectric_gamma(grid, cell, q, rv, p)
+        phi, _ = O.solve(rho, eps, h, tol=1e-14)
+        return O.variational_energy(rho, phi, eps, grid, cell)
+
+    eps = O.dielectric_gamma(grid, cell, pos, rv, p)
+    phi, _ = O.solve(rho, eps, h, tol=1e-14)
+    sel = [0, 5]
+    Ge, Gr = O.energy_gradient(phi, grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud, p=p, atoms=sel,
+                               rho_moves=False, rvdw=rv)
+    fd = np.zeros((len(sel), 3))
+    d = 1e-4
+    for t, a in enumerate(sel):
+        for c in range(3):
+            pp = pos.copy(); pp[a, c] += d
+            pm = pos.copy(); pm[a, c] -= d
+            fd[t, c] = (E_of(pp) - E_of(pm)) / (2 * d)
+    scale = np.max(np.abs(fd))
+    assert scale > 1e-3
+    assert np.max(np.abs(fd - Ge[sel])) < 1e-6 * scale
