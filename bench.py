@@ -182,8 +182,11 @@ def gpu_arm(args, rank, world):
     hbm, hbm_src = load_peaks()
 
     def make_solver(precision, split):
+        extra = {"kind": 1, "rcut": args.rcut_gamma} if args.kind == 1 else {}
         return P.GPSolver(w.grid, w.cell, precision=precision, split=split, levels=w.levels,
-                          sweep_shape=args.sweep_shape)
+                          sweep_shape=args.sweep_shape, **extra)
+
+    radii = torch.tensor(W.vdw_radii(at.Z), dtype=torch.float64, device=dev) if args.kind == 1 else None
 
     solver = make_solver(args.precision, args.split)
     rho = solver.zeros()
@@ -192,7 +195,7 @@ def gpu_arm(args, rank, world):
     stream = torch.cuda.current_stream()
 
     def step(s, pos, phi_buf, rho_buf):
-        s.set_atoms(pos)
+        s.set_atoms(pos, radii=radii)
         s.build_rho(pos, gauss, out=rho_buf)
         phi_buf.zero_()
         st = s.ctx.gp_solve(rho_buf, phi_buf, args.tol, check=False)
@@ -331,6 +334,7 @@ def gpu_arm(args, rank, world):
         "vs_baseline": None, "dtype": "f32/f64" if args.precision == 1 else "f64", "data": "synthetic",
         "config": {"workload": w.name, "grid": list(w.grid), "cell_A": list(w.cell), "atoms": int(len(at.Z)),
                    "tol": args.tol, "precision": "mixed" if args.precision == 1 else "fp64",
+                   "dielectric": "erf product" if args.kind == 0 else "Eq. 9-10 (beta 2.4, rcut %.1f A)" % args.rcut_gamma,
                    "split": bool(args.split), "split_active": bool(stats.split_active),
                    "wet_fraction": stats.wet_fraction, "levels": stats.levels,
                    "outer_iterations_mean": float(np.mean(outer)), "vcycles_mean": float(np.mean(vcyc)),
@@ -481,6 +485,9 @@ def main():
     ap.add_argument("--mode", default="step", choices=["step", "md"])
     ap.add_argument("--frames", type=int, default=100)
     ap.add_argument("--graph-outer", type=int, default=2)
+    ap.add_argument("--kind", type=int, default=0, choices=[0, 1],
+                    help="dielectric: 0 erf product (the workloads), 1 Eq. 9-10 dummy density")
+    ap.add_argument("--rcut-gamma", type=float, default=9.0, help="cut-off of gamma for --kind 1 (Angstrom)")
     ap.add_argument("--sweep-shape", type=int, default=-1,
                     help="finest-level smoother tile (-1: autotuned; fixed shapes keep profiles comparable)")
     args = ap.parse_args()

@@ -84,6 +84,11 @@ typedef struct {
                              the graph is kept for the same rho/phi buffers (0 = off, <= 16) */
     int sweep_shape;      /* FP32 finest-level smoother tile (see gp_stats.sweep_shape); -1 = chosen
                              by the autotuner at gp_set_dielectric (-1) */
+    int kind;             /* dielectric form: 0 = the erf product above (0); 1 = Eq. 9-10, the dummy
+                             density gamma(r) = sum_a exp(-(|r-R_a| - rvdw_a)) over atoms and images
+                             with |r-R_a| < rcut, eps = 1 + (eps0-1)/(1 + gamma^(2 beta)); needs the
+                             radii of gp_set_vdw_radii. r0 and w are unused by kind 1 */
+    double beta;          /* kind 1: the exponent beta of Eq. 10 (2.4) */
 } gp_params;
 
 #define GP_HISTORY 64
@@ -117,11 +122,17 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
 
 /* Build eps(R) on the grid from n_atoms positions (device double[n][3]),
  * the per-level multigrid coefficients, the dry-plane flags and the wet band
- * (Sec. II.B Eq. 9-10 idea with the erf switching function; Sec. II.C for the
- * band). Must precede gp_solve and gp_energy_forces; call again whenever the
+ * (Sec. II.B: the erf switching product, params->kind 0, or Eq. 9-10,
+ * kind 1; Sec. II.C for the band). Must precede gp_solve and gp_energy_forces; call again whenever the
  * atoms move. `params` is copied. Errors: GP_ERR_INVALID_ARG, GP_ERR_CUDA. */
 gp_status gp_set_dielectric(gp_ctx* ctx, const double* atoms_dev, int n_atoms,
                             const gp_params* params);
+
+/* Van der Waals radii R_vdw of Eq. 9 (device double[n_atoms], Angstrom, each > 0),
+ * copied into the context for the kind-1 dielectric; the next gp_set_dielectric
+ * with kind 1 must pass the same n_atoms. Errors: GP_ERR_INVALID_ARG (null
+ * pointer, n_atoms < 1), GP_ERR_OOM, GP_ERR_CUDA. */
+gp_status gp_set_vdw_radii(gp_ctx* ctx, const double* radii_dev, int n_atoms);
 
 /* rho(r) = sum_a Z_a [g(r; sigma_core,a) - g(r; sigma_cloud,a)] - mean, with
  * g the normalised Gaussian of standard deviation sigma, each truncated to

@@ -171,6 +171,8 @@ struct gp_ctx {
     double* gmat = nullptr;        // Gauss-Jordan workspace (2 * 512^2)
     double* sw_coef = nullptr;     // switching-function tables (2 * kSwNI * (kSwDeg+1))
     float4* sw_pack = nullptr;     // their packed FP32 copies (2 * kSwNI * 4)
+    double* rvdw = nullptr;        // van der Waals radii for the kind-1 dielectric
+    int rvdw_n = 0, rvdw_cap = 0;
     void* gtab = nullptr;          // periodized Gaussian factor tables (GaussTabs)
     size_t gtab_cap = 0;           // bytes
     SwTables sw{};
@@ -1031,6 +1033,8 @@ void gp_default_params(gp_params* p) {
     p->band_vcycles = 2;
     p->graph_outer = 0;
     p->sweep_shape = -1;
+    p->kind = 0;
+    p->beta = 2.4;
 }
 
 gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out) {
@@ -1087,6 +1091,10 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         if (p.graph_outer < 0 || p.graph_outer > 16) throw Err{GP_ERR_INVALID_ARG, "graph_outer must be 0..16"};
         if (p.sweep_shape < -1 || p.sweep_shape >= kSweepShapeCount)
             throw Err{GP_ERR_INVALID_ARG, "sweep_shape must be -1 (autotune) or a valid tile shape"};
+        if (p.kind != 0 && p.kind != 1) throw Err{GP_ERR_INVALID_ARG, "kind must be 0 (erf product) or 1 (Eq. 9-10)"};
+        if (p.kind == 1 && !(p.beta > 0.0)) throw Err{GP_ERR_INVALID_ARG, "beta must be positive"};
+        if (p.kind == 1 && n_atoms > 0 && c->rvdw_n != n_atoms)
+            throw Err{GP_ERR_STATE, "kind 1 needs gp_set_vdw_radii for the same number of atoms"};
         std::string why;
         const int L = plan_levels(c->g.nx, c->g.ny, c->g.nz, 1, p.levels, why);
         if (L < 2) throw Err{GP_ERR_INVALID_ARG, why.empty() ? "grid too small for multigrid" : why};
@@ -1111,10 +1119,10 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         }
         GP_CHECK_LAUNCH();
         Atoms at{c->atoms, c->atoms32, nullptr, n_atoms};
-        const DielParams dp = make_diel(p.eps0, p.r0, p.w, p.rcut);
+        const DielParams dp = make_diel(p.eps0, p.r0, p.w, p.rcut, p.kind, p.beta);
         // switching-function tables for these r0, w (when the tabulated range is away from d = 0)
         SwTables tb{};
-        if (p.r0 - 4.0 * p.w > 0.0 && p.r0 + 6.0 * p.w <= p.rcut) {
+        if (p.kind == 0 && p.r0 - 4.0 * p.w > 0.0 && p.r0 + 6.0 * p.w <= p.rcut) {
             tb.s = c->sw_coef;
             tb.h = c->sw_coef + (size_t)kSwNI * (kSwDeg + 1);
             tb.s32 = c->sw_pack;
@@ -1134,7 +1142,9 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         c->sw = tb;
         {
             ProfScope ps(c, GP_PROF_EPS, 1);
-            launch_build_eps(c->g, at, dp, tb, c->eps64, c->pe64, c->eps32, c->s);
+            // pe64 holds the per-point factor of d eps/d R: eps - 1 (kind 0) or d eps/d gamma (kind 1)
+            if (p.kind == 1) launch_build_eps_gamma(c->g, at, dp, c->rvdw, c->eps64, c->pe64, c->eps32, c->s);
+            else launch_build_eps(c->g, at, dp, tb, c->eps64, c->pe64, c->eps32, c->s);
         }
         GP_CHECK_LAUNCH();
         {
@@ -1154,6 +1164,30 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         c->have_eps = true;
         prof_collect(c);
         c->err.clear();
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_set_vdw_radii(gp_ctx* c, const double* radii_dev, int n_atoms) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!radii_dev || n_atoms < 1) throw Err{GP_ERR_INVALID_ARG, "radii: null pointer or no atoms"};
+        std::vector<double> hr((size_t)n_atoms);
+        GP_CUDA(cudaMemcpyAsync(hr.data(), radii_dev, sizeof(double) * n_atoms, cudaMemcpyDeviceToHost, c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        for (double v : hr)
+            if (!(v > 0.0)) throw Err{GP_ERR_INVALID_ARG, "van der Waals radii must be positive"};
+        if (n_atoms > c->rvdw_cap) {
+            if (c->rvdw) cudaFree(c->rvdw);
+            c->rvdw = nullptr;
+            if (cudaMalloc(&c->rvdw, sizeof(double) * n_atoms) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+            c->rvdw_cap = n_atoms;
+        }
+        GP_CUDA(cudaMemcpyAsync(c->rvdw, radii_dev, sizeof(double) * n_atoms, cudaMemcpyDeviceToDevice, c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        c->rvdw_n = n_atoms;
         return GP_OK;
     } catch (const Err& e) {
         return fail(c, e);
@@ -1259,10 +1293,13 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
             GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->s));
             Atoms at{c->atoms, c->atoms32, gauss_dev, n};
-            const DielParams dp = make_diel(c->prm.eps0, c->prm.r0, c->prm.w, c->prm.rcut);
+            const DielParams dp = make_diel(c->prm.eps0, c->prm.r0, c->prm.w, c->prm.rcut, c->prm.kind, c->prm.beta);
             {
                 ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
-                launch_forces_eps(c->g, at, dp, c->sw, phi_dev, c->pe64, c->forces_S, c->s);
+                if (c->prm.kind == 1)
+                    launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, c->pe64, c->forces_S, c->s);
+                else
+                    launch_forces_eps(c->g, at, dp, c->sw, phi_dev, c->pe64, c->forces_S, c->s);
             }
             GP_CHECK_LAUNCH();
             if (gauss_dev) {
@@ -1429,6 +1466,7 @@ void gp_destroy(gp_ctx* c) {
     if (c->atoms) cudaFree(c->atoms);
     if (c->atoms32) cudaFree(c->atoms32);
     if (c->gtab) cudaFree(c->gtab);
+    if (c->rvdw) cudaFree(c->rvdw);
     if (c->ratoms) cudaFree(c->ratoms);
     if (c->ratoms32) cudaFree(c->ratoms32);
     if (c->forces_S) cudaFree(c->forces_S);

@@ -62,17 +62,22 @@ inline Geo make_geo(int nx, int ny, int nz, double lx, double ly, double lz) {
     return g;
 }
 
-// Dielectric parameters (Eq. 8 switching) with host-derived constants.
+// Dielectric parameters with host-derived constants: kind 0 is the erf-product
+// switching form, kind 1 the dummy-density form of Eq. 9-10 (beta).
 struct DielParams {
     double eps0, r0, w, rcut;
     double iw;        // 1 / w
     double sp_norm;   // 1 / (w sqrt(pi)): ds/du prefactor
     double tiny;      // product-below-which eps - 1 rounds away: 5.5e-17 / (eps0 - 1)
+    double beta2;     // 2 beta (kind 1)
+    int kind;
 };
 
-inline DielParams make_diel(double eps0, double r0, double w, double rcut) {
+inline DielParams make_diel(double eps0, double r0, double w, double rcut, int kind = 0, double beta = 2.4) {
     DielParams p{};
     p.eps0 = eps0; p.r0 = r0; p.w = w; p.rcut = rcut;
+    p.kind = kind;
+    p.beta2 = 2.0 * beta;
     p.iw = 1.0 / w;
     p.sp_norm = 1.0 / (w * 1.7724538509055160273);
     p.tiny = 5.5e-17 / (eps0 - 1.0 > 0.0 ? eps0 - 1.0 : 1.0);
@@ -103,6 +108,11 @@ void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, doub
                           float4* h_pack, cudaStream_t s);
 void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, double* eps64, double* pe64,
                       float* eps32, cudaStream_t s);
+// Eq. 9-10: gamma = sum exp(-(d - rvdw)), eps = 1 + (eps0 - 1)/(1 + gamma^(2 beta)); fe64 = d eps / d gamma
+void launch_build_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, double* eps64, double* fe64,
+                            float* eps32, cudaStream_t s);
+void launch_forces_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, const double* phi,
+                             const double* fe64, double* S, cudaStream_t s);
 // Periodized 1D Gaussian factor tables (k_fields.cu), Gaussian ge = 2 atom + {0 core, 1 cloud}
 struct GaussTabs {
     double* val;    // [G][3][nmax] X, Y, Z factors summed over the images -L, 0, +L

@@ -782,6 +782,148 @@ dim3 tile_grid_ez(const Geo& g) {
     return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + EZ - 1) / EZ);
 }
 
+// ----------------------------------------------------------------- eps, Eq. 9-10 (dummy density)
+// gamma(r) = sum over atoms and images with d < rcut of exp(-(d - rvdw_a)) (Eq. 9),
+// eps = 1 + (eps0 - 1)/2 (1 + (1 - gamma^(2b))/(1 + gamma^(2b))) = 1 + (eps0 - 1)/(1 + gamma^(2b))
+// (Eq. 10), and the factor d eps/d gamma = -(eps0 - 1) 2b gamma^(2b-1)/(1 + gamma^(2b))^2 of
+// the atomic derivative d eps/d R_a = (d eps/d gamma) exp(-(d - rvdw)) (r - R_a)/d, which is
+// Eq. 12 with the sign that differentiating Eq. 9-10 gives (moving an atom towards r raises
+// gamma and lowers eps). FP64 throughout.
+__global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielParams p, const double* rvdw,
+                                                        double* eps64, double* fe64, float* eps32) {
+    __shared__ double ec[MAXE][4];
+    __shared__ int ne;
+    const Tile t = make_tile(g);
+    int tx, ty, tz;
+    compact_point(threadIdx.x >> 5, threadIdx.x & 31, tx, ty, tz);
+    const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+    const bool valid = i < g.nx && j < g.ny && k < g.nz;
+    const double x = i * g.hx, y = j * g.hy, z = k * g.hz;
+    const double rc2 = p.rcut * p.rcut;
+    const float rcf = (float)p.rcut + kMargin;
+    double gam = 0.0;
+    for (int a0 = 0; a0 < at.n; a0 += ACH) {
+        if (threadIdx.x == 0) ne = 0;
+        __syncthreads();
+        const int na = min(ACH, at.n - a0);
+        for (int q = threadIdx.x; q < na * 27; q += TT) {
+            const int a = a0 + q / 27, im = q % 27;
+            float fx, fy, fz;
+            image32(at.w32, a, im, g, fx, fy, fz);
+            if (box_d2(t, fx, fy, fz) < rcf * rcf) {
+                const int s = atomicAdd(&ne, 1);
+                image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
+                ec[s][3] = rvdw[a];
+            }
+        }
+        __syncthreads();
+        const int m = ne;
+        if (valid)
+            for (int e = 0; e < m; ++e) {
+                const double dx = x - ec[e][0], dy = y - ec[e][1], dz = z - ec[e][2];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 < rc2) gam += exp(ec[e][3] - sqrt(d2));
+            }
+        __syncthreads();
+    }
+    if (valid) {
+        const long idx = i + (long)g.nx * (j + (long)g.ny * k);
+        double e = p.eps0, fe = 0.0;
+        if (gam > 0.0) {
+            const double gb = exp(p.beta2 * log(gam));          // gamma^(2 beta)
+            const double den = 1.0 + gb;
+            e = 1.0 + (p.eps0 - 1.0) / den;
+            fe = -(p.eps0 - 1.0) * p.beta2 * gb / (gam * den * den);
+        }
+        eps64[idx] = e;
+        if (fe64) fe64[idx] = fe;
+        if (eps32) eps32[idx] = (float)e;
+    }
+}
+
+// S_a = sum_i W_i (d eps/d gamma)_i sum_images exp(-(d - rvdw_a)) (r_i - R_a)/d, with
+// W_i = (1/2) sum over the six faces of i of (grad_f phi)^2, so that
+// G_eps_a = -h^3/(8 pi) S_a (applied in k_forces_finish). One warp per
+// (atom, image) entry over the tile's 512 points; FP64.
+__global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielParams p, const double* rvdw,
+                                                         const double* phi, const double* fe64, double* S) {
+    __shared__ double ec[MAXE][4];
+    __shared__ int eatom[MAXE];
+    __shared__ double Ws[TT];
+    __shared__ int ne;
+    const Tile t = make_tile(g);
+    {
+        const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+        const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+        double W = 0.0;
+        if (i < g.nx && j < g.ny && k < g.nz) {
+            const long pl = plane_of(g.nx, g.ny);
+            const long c = i + (long)g.nx * (j + (long)g.ny * k);
+            const double fv = fe64[c];
+            if (fv != 0.0) {
+                const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
+                const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
+                const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
+                const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
+                const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
+                const double p0 = phi[c];
+                const double ax = phi[xp] - p0, bx = p0 - phi[xm];
+                const double ay = phi[yp] - p0, by = p0 - phi[ym];
+                const double az = phi[zp] - p0, bz = p0 - phi[zm];
+                W = ((ax * ax + bx * bx) * g.c2x + (ay * ay + by * by) * g.c2y + (az * az + bz * bz) * g.c2z) * fv;
+            }
+        }
+        Ws[threadIdx.x] = W;   // index tx + TX (ty + TY tz)
+    }
+    const double rc2 = p.rcut * p.rcut;
+    const float rcf = (float)p.rcut + kMargin;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int a0 = 0; a0 < at.n; a0 += ACH) {
+        if (threadIdx.x == 0) ne = 0;
+        __syncthreads();
+        const int na = min(ACH, at.n - a0);
+        for (int q = threadIdx.x; q < na * 27; q += TT) {
+            const int a = a0 + q / 27, im = q % 27;
+            float fx, fy, fz;
+            image32(at.w32, a, im, g, fx, fy, fz);
+            if (box_d2(t, fx, fy, fz) < rcf * rcf) {
+                const int s = atomicAdd(&ne, 1);
+                image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
+                ec[s][3] = rvdw[a];
+                eatom[s] = a;
+            }
+        }
+        __syncthreads();
+        const int m = ne;
+        for (int e = warp; e < m; e += TT / 32) {
+            const double cx = ec[e][0], cy = ec[e][1], cz = ec[e][2], rv = ec[e][3];
+            double fx = 0.0, fy = 0.0, fz = 0.0;
+            for (int blk = 0; blk < 16; ++blk) {
+                int tx, ty, tz;
+                compact_point(blk, lane, tx, ty, tz);
+                const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+                if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
+                const double W = Ws[tx + TX * (ty + TY * tz)];
+                if (W == 0.0) continue;
+                const double dx = i * g.hx - cx, dy = j * g.hy - cy, dz = k * g.hz - cz;
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                if (!(d2 < rc2 && d2 > 0.0)) continue;
+                const double d = sqrt(d2);
+                const double c = W * exp(rv - d) / d;
+                fx += c * dx; fy += c * dy; fz += c * dz;
+            }
+            fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+            if (lane == 0) {
+                const int a = eatom[e];
+                if (fx != 0.0) atomicAdd(&S[3 * a + 0], fx);
+                if (fy != 0.0) atomicAdd(&S[3 * a + 1], fy);
+                if (fz != 0.0) atomicAdd(&S[3 * a + 2], fz);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ----------------------------------------------------------------- dry planes
 __global__ void k_plane_max(Geo g, const double* eps64, double* out) {
     __shared__ double red[256];
@@ -1061,6 +1203,16 @@ void launch_gauss_tables(const Geo& g, Atoms at, double cut, const GaussTabs& gt
 
 void launch_build_rho_raw(const Geo& g, const GaussTabs& gt, double* rho, cudaStream_t s) {
     k_build_rho<<<tile_grid(g), TT, 0, s>>>(g, gt, rho);
+}
+
+void launch_build_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, double* eps64, double* fe64,
+                            float* eps32, cudaStream_t s) {
+    k_build_eps_gamma<<<tile_grid(g), TT, 0, s>>>(g, at, p, rvdw, eps64, fe64, eps32);
+}
+
+void launch_forces_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, const double* phi,
+                             const double* fe64, double* S, cudaStream_t s) {
+    k_forces_eps_gamma<<<tile_grid(g), TT, 0, s>>>(g, at, p, rvdw, phi, fe64, S);
 }
 
 void launch_plane_max(const Geo& g, const double* eps64, double* out, cudaStream_t s) {

@@ -34,7 +34,7 @@ class gp_params(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("levels", ctypes.c_int), ("inner", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("accel", ctypes.c_int), ("restart", ctypes.c_int),
                 ("band_vcycles", ctypes.c_int), ("graph_outer", ctypes.c_int),
-                ("sweep_shape", ctypes.c_int)]
+                ("sweep_shape", ctypes.c_int), ("kind", ctypes.c_int), ("beta", ctypes.c_double)]
 
 
 class gp_stats(ctypes.Structure):
@@ -51,6 +51,7 @@ _SIGNATURES = {
     "gp_default_params": (None, [ctypes.POINTER(gp_params)]),
     "gp_create": (ctypes.c_int, [gp_grid, gp_cell, _P, ctypes.POINTER(_P)]),
     "gp_set_dielectric": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(gp_params)]),
+    "gp_set_vdw_radii": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "gp_build_rho": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "gp_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
     "gp_energy_forces": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
@@ -200,6 +201,9 @@ class Context:
         self.params = params
         return self._check(self._lib.gp_set_dielectric(self._h, _ptr(atoms), int(atoms.shape[0]),
                                                        ctypes.byref(params)))
+
+    def gp_set_vdw_radii(self, radii):
+        return self._check(self._lib.gp_set_vdw_radii(self._h, _ptr(radii), int(radii.shape[0])))
 
     def gp_build_rho(self, atoms, gauss, rho):
         return self._check(self._lib.gp_build_rho(self._h, _ptr(atoms), _ptr(gauss), int(atoms.shape[0]),

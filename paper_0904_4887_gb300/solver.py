@@ -35,10 +35,14 @@ class GPSolver:
     def zeros(self):
         return torch.zeros(self.shape, dtype=torch.float64, device=self.device)
 
-    def set_atoms(self, pos: torch.Tensor, **params):
-        """Build eps(R) and the multigrid hierarchy for these atom positions."""
+    def set_atoms(self, pos: torch.Tensor, radii: torch.Tensor = None, **params):
+        """Build eps(R) and the multigrid hierarchy for these atom positions.
+        `radii`: van der Waals radii (Angstrom, one per atom) for the kind-1
+        dielectric of Eq. 9-10; kept by the context for later calls."""
         for k, v in params.items():
             setattr(self.params, k, v)
+        if radii is not None:
+            self.ctx.gp_set_vdw_radii(radii.detach().to(self.device, torch.float64).contiguous())
         pos = pos.detach().to(self.device, torch.float64).contiguous()
         self.ctx.gp_set_dielectric(pos, self.params)
         self._atoms_version += 1

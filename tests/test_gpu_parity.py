@@ -227,6 +227,60 @@ def test_energy_and_forces_match_oracle():
     assert _rel(Fe.cpu().numpy(), -Ge) < 1e-10
 
 
+# ------------------------------------------------------------------ Eq. 9-10 dielectric (kind 1)
+
+def _radii(Z):
+    return W.vdw_radii(Z)
+
+
+@pytest.mark.parametrize("k", range(len(SMALL)))
+def test_gamma_dielectric_matches_oracle(small_cases, k):
+    GPSolver = _gpu()
+    (at, h, eps, rho), grid, cell = small_cases[k]
+    rc = min(7.0, 0.99 * min(cell))
+    p = O.GammaParams(rcut=rc)
+    rv = _radii(at.Z)
+    ref = O.dielectric_gamma(grid, cell, at.pos, rv, p)
+    s = GPSolver(grid, cell, precision=0, kind=1, beta=p.beta, rcut=rc)
+    s.set_atoms(_t(at.pos), radii=_t(rv))
+    assert _rel(s.eps().cpu().numpy(), ref) < 1e-13
+
+
+def test_gamma_energy_and_forces_match_oracle():
+    """Eq. 9-10 dielectric: solve, energy and both force terms against the oracle (Eq. 11 with
+    the derived Eq. 12 sign)."""
+    GPSolver = _gpu()
+    grid, cell = (32, 32, 48), (10.0, 10.0, 15.0)
+    at, h, _, rho = _case(grid, cell, 2, 3, seed=2)
+    p = O.GammaParams(rcut=9.0)
+    rv = _radii(at.Z)
+    eps = O.dielectric_gamma(grid, cell, at.pos, rv, p)
+    s = GPSolver(grid, cell, precision=0, kind=1, beta=p.beta, rcut=p.rcut)
+    s.set_atoms(_t(at.pos), radii=_t(rv))
+    phi = s.solve(_t(rho), tol=1e-13)
+    ref, _ = O.solve(rho, eps, h, tol=1e-14)
+    pn = phi.cpu().numpy()
+    assert _rel(pn, ref) < 1e-10
+    E, E2, F = s.energy_forces(phi, _t(rho), _t(_gauss(at)))
+    Ge, Gr = O.energy_gradient(pn, grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud, p=p, rvdw=rv)
+    assert _rel(F.cpu().numpy(), -(Ge + Gr)) < 1e-10
+    _, _, Fe = s.energy_forces(phi, _t(rho), None)
+    assert _rel(Fe.cpu().numpy(), -Ge) < 1e-10
+    assert abs(E - E2) < 1e-10 * abs(E)
+
+
+def test_gamma_needs_radii():
+    GPSolver = _gpu()
+    from paper_0904_4887_gb300.gp import GPError
+    grid, cell = (16, 8, 24), (7.0, 6.5, 12.0)
+    at = W.slab_atoms(cell, 1, 2, seed=0)
+    s = GPSolver(grid, cell, kind=1, rcut=6.0)
+    with pytest.raises(GPError):
+        s.set_atoms(_t(at.pos))
+    with pytest.raises(GPError):
+        s.set_atoms(_t(at.pos), radii=_t(-np.ones(len(at.Z))))
+
+
 def test_autograd_forces_match_central_differences():
     """dE/dR from the hand-written backward against central differences of E
     (h = 1e-4 A) on 6 seeded atoms, rho moving with its atoms."""

@@ -371,8 +371,7 @@ def test_split_fixed_point_equals_full_box():
 # -------------------------------------------------------------- Eq. 9-10 dielectric
 
 def _radii(Z):
-    """Synthetic van der Waals radii per species: "O" (Z=6) 1.52 A, "Ti" (Z=4) 2.0 A."""
-    return np.where(np.asarray(Z) == 6, 1.52, 2.0)
+    return W.vdw_radii(Z)
 
 
 def test_gamma_dielectric_is_centred_on_the_vdw_radius():

@@ -152,3 +152,9 @@ def random_field(shape, seed=0, mean_zero=True):
     if mean_zero:
         f -= f.mean()
     return f
+
+
+def vdw_radii(Z):
+    """Synthetic van der Waals radii (Angstrom) per species for the Eq. 9-10
+    dielectric: "O" (Z = 6) 1.52, "Ti" (Z = 4) 2.0."""
+    return np.where(np.asarray(Z) == 6, 1.52, 2.0)
