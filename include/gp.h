@@ -85,10 +85,16 @@ typedef struct {
     int sweep_shape;      /* FP32 finest-level smoother tile (see gp_stats.sweep_shape); -1 = chosen
                              by the autotuner at gp_set_dielectric (-1) */
     int kind;             /* dielectric form: 0 = the erf product above (0); 1 = Eq. 9-10, the dummy
-                             density gamma(r) = sum_a exp(-(|r-R_a| - rvdw_a)) over atoms and images
-                             with |r-R_a| < rcut, eps = 1 + (eps0-1)/(1 + gamma^(2 beta)); needs the
-                             radii of gp_set_vdw_radii. r0 and w are unused by kind 1 */
-    double beta;          /* kind 1: the exponent beta of Eq. 10 (2.4) */
+                             density gamma(r) = sum_a exp(-(|r-R_a| - rvdw_a)) T(|r-R_a|) over atoms
+                             and images, T a quintic taper from 1 at rcut-1 A to 0 at rcut,
+                             eps = 1 + (eps0-1)/(1 + gamma^(2 beta)); 2 = Eq. 19, kind 1 with the
+                             solvent excluded below every atom with z_a <= zlim (its term is
+                             exp(+(d - rvdw_a)) from its nearest image at points with z < z_a, both
+                             inside the cell; eps = 1 where such an exponent reaches
+                             (ln(eps0-1)+37)/(2 beta)). Kinds 1, 2 need gp_set_vdw_radii; they do
+                             not use r0 and w */
+    double beta;          /* kinds 1, 2: the exponent beta of Eq. 10 (2.4) */
+    double zlim;          /* kind 2: z_lim of Eq. 19, Angstrom inside the cell (0) */
 } gp_params;
 
 #define GP_HISTORY 64
@@ -122,15 +128,15 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
 
 /* Build eps(R) on the grid from n_atoms positions (device double[n][3]),
  * the per-level multigrid coefficients, the dry-plane flags and the wet band
- * (Sec. II.B: the erf switching product, params->kind 0, or Eq. 9-10,
- * kind 1; Sec. II.C for the band). Must precede gp_solve and gp_energy_forces; call again whenever the
+ * (Sec. II.B: the erf switching product, params->kind 0, Eq. 9-10, kind 1,
+ * or Eq. 19, kind 2; Sec. II.C for the band). Must precede gp_solve and gp_energy_forces; call again whenever the
  * atoms move. `params` is copied. Errors: GP_ERR_INVALID_ARG, GP_ERR_CUDA. */
 gp_status gp_set_dielectric(gp_ctx* ctx, const double* atoms_dev, int n_atoms,
                             const gp_params* params);
 
 /* Van der Waals radii R_vdw of Eq. 9 (device double[n_atoms], Angstrom, each > 0),
- * copied into the context for the kind-1 dielectric; the next gp_set_dielectric
- * with kind 1 must pass the same n_atoms. Errors: GP_ERR_INVALID_ARG (null
+ * copied into the context for the kind-1 and kind-2 dielectrics; the next
+ * gp_set_dielectric with kind 1 or 2 must pass the same n_atoms. Errors: GP_ERR_INVALID_ARG (null
  * pointer, n_atoms < 1), GP_ERR_OOM, GP_ERR_CUDA. */
 gp_status gp_set_vdw_radii(gp_ctx* ctx, const double* radii_dev, int n_atoms);
 

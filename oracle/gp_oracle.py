@@ -164,14 +164,27 @@ def dielectric_gradient_atom(a, grid, cell, pos, P, p: DielectricParams = Dielec
 
 @dataclasses.dataclass(frozen=True)
 class GammaParams:
-    """Eq. 9: gamma(r) = sum_I exp(-(|r - R_I| - Rvdw_I)), over atoms and their
-    periodic images with |r - R_I| < rcut (the paper gives no cut-off; rcut is
-    chosen where gamma^(2 beta) is negligible).
+    """Eq. 9: gamma(r) = sum_I exp(-(|r - R_I| - Rvdw_I)) T(|r - R_I|), over atoms
+    and their periodic images. The paper gives no cut-off; here each term is
+    tapered to zero between rcut - TAPER and rcut by the quintic smoothstep
+    T, so that eps stays twice differentiable in the positions (a hard cut
+    would put steps into E(R) wherever a cut-off sphere crosses a grid point).
     Eq. 10: eps = 1 + (eps0 - 1)/2 (1 + (1 - gamma^(2 beta))/(1 + gamma^(2 beta))).
     """
     eps0: float = 78.36
     beta: float = 2.4
     rcut: float = 8.0
+
+
+TAPER = 1.0   # width of the cut-off taper of Eq. 9 terms, Angstrom
+
+
+def taper(d, rcut):
+    """(T, dT/dd): 1 below rcut - TAPER, 0 beyond rcut, 1 - 10u^3 + 15u^4 - 6u^5 between."""
+    u = np.clip((d - (rcut - TAPER)) / TAPER, 0.0, 1.0)
+    T = 1.0 - u ** 3 * (10.0 - 15.0 * u + 6.0 * u * u)
+    dT = -30.0 * u * u * (1.0 - u) ** 2 / TAPER
+    return T, dT
 
 
 def dummy_density(grid, cell, pos, rvdw, p: GammaParams = GammaParams()):
@@ -180,7 +193,8 @@ def dummy_density(grid, cell, pos, rvdw, p: GammaParams = GammaParams()):
     for R, rv in zip(pos, rvdw):
         for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, p.rcut):
             d = np.sqrt(dx * dx + dy * dy + dz * dz)
-            g[sl] += np.where(d < p.rcut, np.exp(-(d - rv)), 0.0)
+            T, _ = taper(d, p.rcut)
+            g[sl] += np.exp(-(d - rv)) * T
     return g
 
 
@@ -210,26 +224,125 @@ def dielectric_gamma_points(points, cell, pos, rvdw, p: GammaParams = GammaParam
     for R, rv in zip(pos, rvdw):
         for n in itertools.product((-1, 0, 1), repeat=3):
             d = np.linalg.norm(points - (R + np.asarray(n) * cell), axis=1)
-            g += np.where(d < p.rcut, np.exp(-(d - rv)), 0.0)
+            T, _ = taper(d, p.rcut)
+            g += np.exp(-(d - rv)) * T
     return eps_of_gamma(g, p)
 
 
 def dielectric_gamma_gradient_atom(a, grid, cell, pos, rvdw, gamma, p: GammaParams = GammaParams()):
     """d eps_i / d R_a (x, y, z arrays) for Eq. 9-10: by the chain rule,
-    (d eps/d gamma) sum_images exp(-(d - Rvdw_a)) (r - R_a)/d, because
-    d|r - R_a|/dR_a = -(r - R_a)/d. This is Eq. 12 with the opposite sign to
-    the printed one: moving an atom towards r raises gamma there and lowers eps.
+    (d eps/d gamma) sum_images exp(-(d - Rvdw_a)) (T - T') (r - R_a)/d, because
+    d|r - R_a|/dR_a = -(r - R_a)/d. With T = 1 this is Eq. 12 with the opposite
+    sign to the printed one: moving an atom towards r raises gamma there and
+    lowers eps.
     """
     fe = deps_dgamma(gamma, p)
     out = [np.zeros_like(gamma) for _ in range(3)]
     for sl, (dz, dy, dx) in _image_boxes(pos[a], grid, cell, p.rcut):
         d = np.sqrt(dx * dx + dy * dy + dz * dz)
         dsafe = np.where(d > 0, d, 1.0)
-        coef = np.where((d < p.rcut) & (d > 0), fe[sl] * np.exp(-(d - rvdw[a])) / dsafe, 0.0)
+        T, dT = taper(d, p.rcut)
+        coef = np.where(d > 0, fe[sl] * np.exp(-(d - rvdw[a])) * (T - dT) / dsafe, 0.0)
         out[0][sl] += coef * dx
         out[1][sl] += coef * dy
         out[2][sl] += coef * dz
     return out
+
+
+# ----------------------------------------------------------------------------
+# Eq. 19: the dummy density with the solvent excluded below z_lim
+# ----------------------------------------------------------------------------
+# Reading of Eq. 19 (the paper states it for a cell whose z runs from 0 at the
+# bottom to Lz at the top): for an atom with z_I <= z_lim the exponent's sign is
+# that of z - z_I, both taken inside the cell [0, Lz) (+1 at z = z_I), so below
+# such an atom its term grows as exp(+(|r - R_I| - Rvdw)) and eps saturates to 1.
+# A growing term uses the nearest periodic image of the atom (an image sum of
+# growing exponentials has no limit) and no cut-off. Once one growing exponent
+# reaches sat_exponent(p) = (ln(eps0 - 1) + 37)/(2 beta), eps - 1 is below
+# exp(-37) < 1e-16 and d eps/d gamma is as small: such a point is "saturated",
+# with eps = 1 and d eps/d gamma = 0. Atoms with z_I > z_lim, and lower atoms at
+# points with z >= z_I, contribute as in Eq. 9 (images within rcut).
+def sat_exponent(p):
+    return (math.log(p.eps0 - 1.0) + 37.0) / (2.0 * p.beta)
+
+
+def _min_image(dv, L):
+    return dv - L * np.round(dv / L)
+
+
+def dummy_density_eq19(grid, cell, pos, rvdw, zlim, p: GammaParams = GammaParams()):
+    """(gamma, saturated) on the grid for Eq. 19 (see the reading above)."""
+    x, y, z = _grid_coords(grid, cell)
+    g = np.zeros((grid[2], grid[1], grid[0]))
+    sat = np.zeros(g.shape, dtype=bool)
+    posw = np.mod(pos, np.asarray(cell))
+    lower = posw[:, 2] <= zlim
+    for a, (R, rv) in enumerate(zip(posw, rvdw)):
+        below = (z < R[2]) if lower[a] else np.zeros_like(z, dtype=bool)
+        for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, p.rcut):
+            d = np.sqrt(dx * dx + dy * dy + dz * dz)
+            T, _ = taper(d, p.rcut)
+            keep = ~np.broadcast_to(below, g.shape)[sl]
+            g[sl] += np.where(keep, np.exp(-(d - rv)) * T, 0.0)
+        if lower[a]:
+            ddx = _min_image(x - R[0], cell[0])
+            ddy = _min_image(y - R[1], cell[1])
+            ddz = _min_image(z - R[2], cell[2])
+            d = np.sqrt(ddx * ddx + ddy * ddy + ddz * ddz)
+            e = d - rv
+            es = sat_exponent(p)
+            grow = np.broadcast_to(below, g.shape)
+            sat |= grow & (e >= es)
+            g += np.where(grow & (e < es), np.exp(np.minimum(e, es)), 0.0)
+    return g, sat
+
+
+def dielectric_eq19(grid, cell, pos, rvdw, zlim, p: GammaParams = GammaParams()):
+    """eps on the grid for Eq. 19 with Eq. 10 (simplified form, which stays finite)."""
+    g, sat = dummy_density_eq19(grid, cell, pos, rvdw, zlim, p)
+    t = np.where(sat, np.inf, g ** (2.0 * p.beta))
+    return np.where(sat, 1.0, 1.0 + (p.eps0 - 1.0) / (1.0 + t))
+
+
+def dielectric_eq19_gradient_atom(a, grid, cell, pos, rvdw, zlim, gamma, sat, p: GammaParams = GammaParams()):
+    """d eps_i/d R_a for Eq. 19: decaying (tapered) terms as Eq. 9, a growing
+    term exp(+(d - Rvdw)) gives -(d eps/d gamma) exp(d - Rvdw) (r - R_a)/d;
+    zero at saturated points."""
+    x, y, z = _grid_coords(grid, cell)
+    fe = np.where(sat, 0.0, deps_dgamma(np.where(sat, 1.0, gamma), p))
+    out = [np.zeros_like(gamma) for _ in range(3)]
+    posw = np.mod(pos, np.asarray(cell))
+    R, rv = posw[a], rvdw[a]
+    lower = R[2] <= zlim
+    below = np.broadcast_to((z < R[2]) if lower else np.zeros_like(z, dtype=bool), gamma.shape)
+    for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, p.rcut):
+        d = np.sqrt(dx * dx + dy * dy + dz * dz)
+        dsafe = np.where(d > 0, d, 1.0)
+        T, dT = taper(d, p.rcut)
+        coef = np.where((d > 0) & ~below[sl], fe[sl] * np.exp(-(d - rv)) * (T - dT) / dsafe, 0.0)
+        out[0][sl] += coef * dx
+        out[1][sl] += coef * dy
+        out[2][sl] += coef * dz
+    if lower:
+        ddx = np.broadcast_to(_min_image(x - R[0], cell[0]), gamma.shape)
+        ddy = np.broadcast_to(_min_image(y - R[1], cell[1]), gamma.shape)
+        ddz = np.broadcast_to(_min_image(z - R[2], cell[2]), gamma.shape)
+        d = np.sqrt(ddx * ddx + ddy * ddy + ddz * ddz)
+        dsafe = np.where(d > 0, d, 1.0)
+        es = sat_exponent(p)
+        coef = np.where(below & (d - rv < es) & (d > 0), -fe * np.exp(np.minimum(d - rv, es)) / dsafe, 0.0)
+        out[0] += coef * ddx
+        out[1] += coef * ddy
+        out[2] += coef * ddz
+    return out
+
+
+def _grid_coords(grid, cell):
+    h = spacing(grid, cell)
+    x = (np.arange(grid[0]) * h[0])[None, None, :]
+    y = (np.arange(grid[1]) * h[1])[None, :, None]
+    z = (np.arange(grid[2]) * h[2])[:, None, None]
+    return x, y, z
 
 
 # ----------------------------------------------------------------------------
@@ -454,7 +567,7 @@ def variational_energy(rho, phi, eps, grid, cell):
 
 
 def energy_gradient(phi, grid, cell, pos, Z, sigma_core, sigma_cloud,
-                    p=DielectricParams(), atoms=None, rho_moves=True, rvdw=None):
+                    p=DielectricParams(), atoms=None, rho_moves=True, rvdw=None, zlim=None):
     """G_a = dE/dR_a = G^eps_a + G^rho_a, the discrete Eq. 11.
 
     G^eps_a = -h^3/(8 pi) sum_faces (d eps_f/dR_a)(Delta_f phi/h)^2, with
@@ -465,14 +578,16 @@ def energy_gradient(phi, grid, cell, pos, Z, sigma_core, sigma_cloud,
     zero. `phi` must be the solution for this geometry: because A is symmetric
     it is its own adjoint (Appendix B), so no further solve is needed.
     `p` is DielectricParams (erf product) or GammaParams (Eq. 9-10, with the
-    radii `rvdw`).
+    radii `rvdw`; Eq. 19 when `zlim` is given).
     """
     h = spacing(grid, cell)
     dv = cell_volume_element(grid, cell)
     n = len(pos)
     atoms = range(n) if atoms is None else atoms
     gamma_form = isinstance(p, GammaParams)
-    if gamma_form:
+    if gamma_form and zlim is not None:
+        G, SAT = dummy_density_eq19(grid, cell, pos, rvdw, zlim, p)
+    elif gamma_form:
         G = dummy_density(grid, cell, pos, rvdw, p)
     else:
         P = dielectric_product(grid, cell, pos, p)
@@ -484,7 +599,9 @@ def energy_gradient(phi, grid, cell, pos, Z, sigma_core, sigma_cloud,
     Ge = np.zeros((n, 3))
     Gr = np.zeros((n, 3))
     for a in atoms:
-        if gamma_form:
+        if gamma_form and zlim is not None:
+            de = dielectric_eq19_gradient_atom(a, grid, cell, pos, rvdw, zlim, G, SAT, p)
+        elif gamma_form:
             de = dielectric_gamma_gradient_atom(a, grid, cell, pos, rvdw, G, p)
         else:
             de = dielectric_gradient_atom(a, grid, cell, pos, P, p)

@@ -1035,6 +1035,7 @@ void gp_default_params(gp_params* p) {
     p->sweep_shape = -1;
     p->kind = 0;
     p->beta = 2.4;
+    p->zlim = 0.0;
 }
 
 gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out) {
@@ -1091,10 +1092,12 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         if (p.graph_outer < 0 || p.graph_outer > 16) throw Err{GP_ERR_INVALID_ARG, "graph_outer must be 0..16"};
         if (p.sweep_shape < -1 || p.sweep_shape >= kSweepShapeCount)
             throw Err{GP_ERR_INVALID_ARG, "sweep_shape must be -1 (autotune) or a valid tile shape"};
-        if (p.kind != 0 && p.kind != 1) throw Err{GP_ERR_INVALID_ARG, "kind must be 0 (erf product) or 1 (Eq. 9-10)"};
-        if (p.kind == 1 && !(p.beta > 0.0)) throw Err{GP_ERR_INVALID_ARG, "beta must be positive"};
-        if (p.kind == 1 && n_atoms > 0 && c->rvdw_n != n_atoms)
-            throw Err{GP_ERR_STATE, "kind 1 needs gp_set_vdw_radii for the same number of atoms"};
+        if (p.kind < 0 || p.kind > 2)
+            throw Err{GP_ERR_INVALID_ARG, "kind must be 0 (erf product), 1 (Eq. 9-10) or 2 (Eq. 19)"};
+        if (p.kind != 0 && !(p.beta > 0.0)) throw Err{GP_ERR_INVALID_ARG, "beta must be positive"};
+        if (p.kind != 0 && !(p.rcut > 1.0)) throw Err{GP_ERR_INVALID_ARG, "rcut must exceed the 1 A taper"};
+        if (p.kind != 0 && n_atoms > 0 && c->rvdw_n != n_atoms)
+            throw Err{GP_ERR_STATE, "kinds 1 and 2 need gp_set_vdw_radii for the same number of atoms"};
         std::string why;
         const int L = plan_levels(c->g.nx, c->g.ny, c->g.nz, 1, p.levels, why);
         if (L < 2) throw Err{GP_ERR_INVALID_ARG, why.empty() ? "grid too small for multigrid" : why};
@@ -1119,7 +1122,7 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         }
         GP_CHECK_LAUNCH();
         Atoms at{c->atoms, c->atoms32, nullptr, n_atoms};
-        const DielParams dp = make_diel(p.eps0, p.r0, p.w, p.rcut, p.kind, p.beta);
+        const DielParams dp = make_diel(p.eps0, p.r0, p.w, p.rcut, p.kind, p.beta, p.zlim);
         // switching-function tables for these r0, w (when the tabulated range is away from d = 0)
         SwTables tb{};
         if (p.kind == 0 && p.r0 - 4.0 * p.w > 0.0 && p.r0 + 6.0 * p.w <= p.rcut) {
@@ -1142,8 +1145,8 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         c->sw = tb;
         {
             ProfScope ps(c, GP_PROF_EPS, 1);
-            // pe64 holds the per-point factor of d eps/d R: eps - 1 (kind 0) or d eps/d gamma (kind 1)
-            if (p.kind == 1) launch_build_eps_gamma(c->g, at, dp, c->rvdw, c->eps64, c->pe64, c->eps32, c->s);
+            // pe64 holds the per-point factor of d eps/d R: eps - 1 (kind 0) or d eps/d gamma (kinds 1, 2)
+            if (p.kind != 0) launch_build_eps_gamma(c->g, at, dp, c->rvdw, c->eps64, c->pe64, c->eps32, c->s);
             else launch_build_eps(c->g, at, dp, tb, c->eps64, c->pe64, c->eps32, c->s);
         }
         GP_CHECK_LAUNCH();
@@ -1293,10 +1296,11 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
             GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->s));
             Atoms at{c->atoms, c->atoms32, gauss_dev, n};
-            const DielParams dp = make_diel(c->prm.eps0, c->prm.r0, c->prm.w, c->prm.rcut, c->prm.kind, c->prm.beta);
+            const DielParams dp =
+                make_diel(c->prm.eps0, c->prm.r0, c->prm.w, c->prm.rcut, c->prm.kind, c->prm.beta, c->prm.zlim);
             {
                 ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
-                if (c->prm.kind == 1)
+                if (c->prm.kind != 0)
                     launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, c->pe64, c->forces_S, c->s);
                 else
                     launch_forces_eps(c->g, at, dp, c->sw, phi_dev, c->pe64, c->forces_S, c->s);

@@ -6,6 +6,8 @@
 
 #include "gp.h"
 
+#include <cmath>
+
 namespace gp {
 
 constexpr int kReduceBlocks = 608;      // 4 x 152 SMs: fixed partial count, deterministic sums
@@ -69,15 +71,20 @@ struct DielParams {
     double iw;        // 1 / w
     double sp_norm;   // 1 / (w sqrt(pi)): ds/du prefactor
     double tiny;      // product-below-which eps - 1 rounds away: 5.5e-17 / (eps0 - 1)
-    double beta2;     // 2 beta (kind 1)
+    double beta2;     // 2 beta (kinds 1, 2)
+    double zlim;      // kind 2: atoms with z <= zlim exclude the solvent below them (Eq. 19)
+    double esat;      // kind 2: growing exponent beyond which eps = 1 exactly (ln(eps0-1)+37)/(2 beta)
     int kind;
 };
 
-inline DielParams make_diel(double eps0, double r0, double w, double rcut, int kind = 0, double beta = 2.4) {
+inline DielParams make_diel(double eps0, double r0, double w, double rcut, int kind = 0, double beta = 2.4,
+                            double zlim = 0.0) {
     DielParams p{};
     p.eps0 = eps0; p.r0 = r0; p.w = w; p.rcut = rcut;
     p.kind = kind;
     p.beta2 = 2.0 * beta;
+    p.zlim = zlim;
+    p.esat = (std::log(eps0 - 1.0 > 1.0 ? eps0 - 1.0 : 1.0) + 37.0) / (2.0 * beta);
     p.iw = 1.0 / w;
     p.sp_norm = 1.0 / (w * 1.7724538509055160273);
     p.tiny = 5.5e-17 / (eps0 - 1.0 > 0.0 ? eps0 - 1.0 : 1.0);

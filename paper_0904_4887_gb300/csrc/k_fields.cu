@@ -782,16 +782,31 @@ dim3 tile_grid_ez(const Geo& g) {
     return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + EZ - 1) / EZ);
 }
 
-// ----------------------------------------------------------------- eps, Eq. 9-10 (dummy density)
-// gamma(r) = sum over atoms and images with d < rcut of exp(-(d - rvdw_a)) (Eq. 9),
+// ----------------------------------------------------------------- eps, Eq. 9-10 and Eq. 19 (dummy density)
+// gamma(r) = sum over atoms and images of exp(-(d - rvdw_a)) T(d) (Eq. 9), T the
+// quintic taper from 1 at rcut - 1 A to 0 at rcut (keeps eps smooth in R),
 // eps = 1 + (eps0 - 1)/2 (1 + (1 - gamma^(2b))/(1 + gamma^(2b))) = 1 + (eps0 - 1)/(1 + gamma^(2b))
 // (Eq. 10), and the factor d eps/d gamma = -(eps0 - 1) 2b gamma^(2b-1)/(1 + gamma^(2b))^2 of
-// the atomic derivative d eps/d R_a = (d eps/d gamma) exp(-(d - rvdw)) (r - R_a)/d, which is
-// Eq. 12 with the sign that differentiating Eq. 9-10 gives (moving an atom towards r raises
-// gamma and lowers eps). FP64 throughout.
+// the atomic derivative d eps/d R_a = (d eps/d gamma) exp(-(d - rvdw)) (T - T') (r - R_a)/d,
+// Eq. 12 with the sign that differentiating Eq. 9-10 gives (moving an atom towards r
+// raises gamma and lowers eps).
+// Kind 2 (Eq. 19): an atom with z_a <= zlim contributes, at points with z < z_a (both
+// inside the cell), exp(+(d - rvdw)) from its nearest image with no cut-off; once such
+// an exponent reaches esat, eps = 1 and d eps/d gamma = 0 there ("saturated"). FP64.
+constexpr double kTaper = 1.0;
+
+__device__ __forceinline__ void taper_fn(double d, double rcut, double& T, double& dT) {
+    double u = (d - (rcut - kTaper)) * (1.0 / kTaper);
+    u = fmin(fmax(u, 0.0), 1.0);
+    T = 1.0 - u * u * u * (10.0 - 15.0 * u + 6.0 * u * u);
+    dT = -30.0 * u * u * (1.0 - u) * (1.0 - u) * (1.0 / kTaper);
+}
+
+__device__ __forceinline__ double min_image(double v, double L) { return v - L * rint(v / L); }
+
 __global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielParams p, const double* rvdw,
                                                         double* eps64, double* fe64, float* eps32) {
-    __shared__ double ec[MAXE][4];
+    __shared__ double ec[MAXE][5];              // image centre, rvdw, z of the atom in the cell (kind 2 lower) or -1
     __shared__ int ne;
     const Tile t = make_tile(g);
     int tx, ty, tz;
@@ -801,7 +816,9 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielPar
     const double x = i * g.hx, y = j * g.hy, z = k * g.hz;
     const double rc2 = p.rcut * p.rcut;
     const float rcf = (float)p.rcut + kMargin;
+    const bool eq19 = p.kind == 2;
     double gam = 0.0;
+    bool sat = false;
     for (int a0 = 0; a0 < at.n; a0 += ACH) {
         if (threadIdx.x == 0) ne = 0;
         __syncthreads();
@@ -814,22 +831,42 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielPar
                 const int s = atomicAdd(&ne, 1);
                 image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
                 ec[s][3] = rvdw[a];
+                const double za = at.w64[3 * a + 2];
+                ec[s][4] = (eq19 && za <= p.zlim) ? za : -1.0;
             }
         }
         __syncthreads();
         const int m = ne;
         if (valid)
             for (int e = 0; e < m; ++e) {
+                if (z < ec[e][4]) continue;                 // below a lower atom: the growing term instead
                 const double dx = x - ec[e][0], dy = y - ec[e][1], dz = z - ec[e][2];
                 const double d2 = dx * dx + dy * dy + dz * dz;
-                if (d2 < rc2) gam += exp(ec[e][3] - sqrt(d2));
+                if (d2 < rc2) {
+                    const double d = sqrt(d2);
+                    double T, dT;
+                    taper_fn(d, p.rcut, T, dT);
+                    gam += exp(ec[e][3] - d) * T;
+                }
             }
         __syncthreads();
     }
+    if (eq19 && valid)
+        for (int a = 0; a < at.n && !sat; ++a) {
+            const double za = at.w64[3 * a + 2];
+            if (za > p.zlim || !(z < za)) continue;
+            const double dx = min_image(x - at.w64[3 * a], g.lx), dy = min_image(y - at.w64[3 * a + 1], g.ly);
+            const double dz = min_image(z - za, g.lz);
+            const double ex = sqrt(dx * dx + dy * dy + dz * dz) - rvdw[a];
+            if (ex >= p.esat) sat = true;
+            else gam += exp(ex);
+        }
     if (valid) {
         const long idx = i + (long)g.nx * (j + (long)g.ny * k);
         double e = p.eps0, fe = 0.0;
-        if (gam > 0.0) {
+        if (sat) {
+            e = 1.0;
+        } else if (gam > 0.0) {
             const double gb = exp(p.beta2 * log(gam));          // gamma^(2 beta)
             const double den = 1.0 + gb;
             e = 1.0 + (p.eps0 - 1.0) / den;
@@ -841,17 +878,21 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielPar
     }
 }
 
-// S_a = sum_i W_i (d eps/d gamma)_i sum_images exp(-(d - rvdw_a)) (r_i - R_a)/d, with
-// W_i = (1/2) sum over the six faces of i of (grad_f phi)^2, so that
-// G_eps_a = -h^3/(8 pi) S_a (applied in k_forces_finish). One warp per
-// (atom, image) entry over the tile's 512 points; FP64.
+// S_a = sum_i W_i (d eps/d gamma)_i (d gamma_i / d R_a), with W_i = (1/2) sum over the six
+// faces of i of (grad_f phi)^2, so that G_eps_a = -h^3/(8 pi) S_a (applied in
+// k_forces_finish). d gamma/d R_a: exp(-(d - rvdw)) (T - T') (r - R_a)/d per decaying
+// image term, -exp(d - rvdw) (r - R_a)/d for a growing (kind 2) term. One warp per
+// (atom, image) entry, and for kind 2 one warp per lower atom, over the tile's 512
+// points; FP64.
 __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielParams p, const double* rvdw,
                                                          const double* phi, const double* fe64, double* S) {
-    __shared__ double ec[MAXE][4];
+    __shared__ double ec[MAXE][5];
     __shared__ int eatom[MAXE];
     __shared__ double Ws[TT];
     __shared__ int ne;
     const Tile t = make_tile(g);
+    const bool eq19 = p.kind == 2;
+    int any = 0;
     {
         const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
         const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
@@ -874,7 +915,9 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielPa
             }
         }
         Ws[threadIdx.x] = W;   // index tx + TX (ty + TY tz)
+        any = W != 0.0;
     }
+    if (__syncthreads_or(any) == 0) return;                // every point of the tile has d eps/d gamma = 0
     const double rc2 = p.rcut * p.rcut;
     const float rcf = (float)p.rcut + kMargin;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -890,13 +933,15 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielPa
                 const int s = atomicAdd(&ne, 1);
                 image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
                 ec[s][3] = rvdw[a];
+                const double za = at.w64[3 * a + 2];
+                ec[s][4] = (eq19 && za <= p.zlim) ? za : -1.0;
                 eatom[s] = a;
             }
         }
         __syncthreads();
         const int m = ne;
         for (int e = warp; e < m; e += TT / 32) {
-            const double cx = ec[e][0], cy = ec[e][1], cz = ec[e][2], rv = ec[e][3];
+            const double cx = ec[e][0], cy = ec[e][1], cz = ec[e][2], rv = ec[e][3], zl = ec[e][4];
             double fx = 0.0, fy = 0.0, fz = 0.0;
             for (int blk = 0; blk < 16; ++blk) {
                 int tx, ty, tz;
@@ -905,11 +950,14 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielPa
                 if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
                 const double W = Ws[tx + TX * (ty + TY * tz)];
                 if (W == 0.0) continue;
+                if (k * g.hz < zl) continue;                 // growing branch of a lower atom
                 const double dx = i * g.hx - cx, dy = j * g.hy - cy, dz = k * g.hz - cz;
                 const double d2 = dx * dx + dy * dy + dz * dz;
                 if (!(d2 < rc2 && d2 > 0.0)) continue;
                 const double d = sqrt(d2);
-                const double c = W * exp(rv - d) / d;
+                double T, dT;
+                taper_fn(d, p.rcut, T, dT);
+                const double c = W * exp(rv - d) * (T - dT) / d;
                 fx += c * dx; fy += c * dy; fz += c * dz;
             }
             fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
@@ -922,6 +970,34 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielPa
         }
         __syncthreads();
     }
+    if (eq19)
+        for (int a = warp; a < at.n; a += TT / 32) {
+            const double za = at.w64[3 * a + 2];
+            if (za > p.zlim || t.k0 * g.hz >= za) continue;  // no point of the tile is below the atom
+            const double ax = at.w64[3 * a], ay = at.w64[3 * a + 1], rv = rvdw[a];
+            double fx = 0.0, fy = 0.0, fz = 0.0;
+            for (int blk = 0; blk < 16; ++blk) {
+                int tx, ty, tz;
+                compact_point(blk, lane, tx, ty, tz);
+                const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+                if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
+                const double W = Ws[tx + TX * (ty + TY * tz)];
+                const double z = k * g.hz;
+                if (W == 0.0 || !(z < za)) continue;
+                const double dx = min_image(i * g.hx - ax, g.lx), dy = min_image(j * g.hy - ay, g.ly);
+                const double dz = min_image(z - za, g.lz);
+                const double d = sqrt(dx * dx + dy * dy + dz * dz);
+                if (!(d > 0.0) || d - rv >= p.esat) continue;
+                const double c = -W * exp(d - rv) / d;
+                fx += c * dx; fy += c * dy; fz += c * dz;
+            }
+            fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+            if (lane == 0) {
+                if (fx != 0.0) atomicAdd(&S[3 * a + 0], fx);
+                if (fy != 0.0) atomicAdd(&S[3 * a + 1], fy);
+                if (fz != 0.0) atomicAdd(&S[3 * a + 2], fz);
+            }
+        }
 }
 
 // ----------------------------------------------------------------- dry planes

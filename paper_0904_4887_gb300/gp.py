@@ -34,7 +34,8 @@ class gp_params(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("levels", ctypes.c_int), ("inner", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("accel", ctypes.c_int), ("restart", ctypes.c_int),
                 ("band_vcycles", ctypes.c_int), ("graph_outer", ctypes.c_int),
-                ("sweep_shape", ctypes.c_int), ("kind", ctypes.c_int), ("beta", ctypes.c_double)]
+                ("sweep_shape", ctypes.c_int), ("kind", ctypes.c_int), ("beta", ctypes.c_double),
+                ("zlim", ctypes.c_double)]
 
 
 class gp_stats(ctypes.Structure):

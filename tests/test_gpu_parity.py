@@ -269,6 +269,56 @@ def test_gamma_energy_and_forces_match_oracle():
     assert abs(E - E2) < 1e-10 * abs(E)
 
 
+def _eq19_setup(grid, cell, n, layers, seed=0):
+    at = W.slab_atoms(cell, n, layers, seed=seed)
+    zs = np.sort(at.pos[:, 2])
+    per = len(zs) // layers
+    zlim = 0.5 * (zs[per - 1] + zs[per])                  # the lowest layer excludes the solvent below it
+    return at, W.vdw_radii(at.Z), zlim
+
+
+@pytest.mark.parametrize("grid,cell,n,layers", [((32, 32, 64), (10.0, 10.0, 20.0), 2, 3),
+                                                ((24, 24, 48), (10.0, 10.0, 20.0), 2, 3)])
+def test_eq19_dielectric_matches_oracle(grid, cell, n, layers):
+    GPSolver = _gpu()
+    at, rv, zlim = _eq19_setup(grid, cell, n, layers)
+    p = O.GammaParams(rcut=8.0)
+    ref = O.dielectric_eq19(grid, cell, at.pos, rv, zlim, p)
+    s = GPSolver(grid, cell, precision=0, kind=2, beta=p.beta, rcut=p.rcut, zlim=zlim)
+    s.set_atoms(_t(at.pos), radii=_t(rv))
+    assert _rel(s.eps().cpu().numpy(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("split,precision", [(0, 0), (1, 0), (1, 1)])
+def test_eq19_solve_and_forces_match_oracle(split, precision):
+    """Eq. 19 makes the region below the slab dry, so the split's band (with the whole
+    dry run as Dirichlet planes) is about half the box; the solve (full box or split)
+    and the forces match the oracle."""
+    GPSolver = _gpu()
+    grid, cell = (32, 32, 64), (10.0, 10.0, 20.0)
+    at, rv, zlim = _eq19_setup(grid, cell, 2, 3, seed=1)
+    p = O.GammaParams(rcut=8.0)
+    h = O.spacing(grid, cell)
+    eps = O.dielectric_eq19(grid, cell, at.pos, rv, zlim, p)
+    rho = O.charge_density(grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud)
+    ref, _ = O.solve(rho, eps, h, tol=1e-14)
+    s = GPSolver(grid, cell, precision=precision, split=split, kind=2, beta=p.beta, rcut=p.rcut, zlim=zlim,
+                 n_dirichlet=0)
+    s.set_atoms(_t(at.pos), radii=_t(rv))
+    st = s.stats()
+    if split:
+        assert st.split_active == 1 and st.wet_fraction < 0.7
+    phi = s.solve(_t(rho), tol=1e-13 if precision == 0 else 1e-12)
+    pn = phi.cpu().numpy()
+    assert _rel(pn, ref) < (1e-10 if precision == 0 else 1e-8)
+    if precision == 0:
+        E, E2, F = s.energy_forces(phi, _t(rho), _t(_gauss(at)))
+        Ge, Gr = O.energy_gradient(pn, grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud, p=p, rvdw=rv,
+                                   zlim=zlim)
+        assert _rel(F.cpu().numpy(), -(Ge + Gr)) < 1e-10
+        assert abs(E - E2) < 1e-10 * abs(E)
+
+
 def test_gamma_needs_radii():
     GPSolver = _gpu()
     from paper_0904_4887_gb300.gp import GPError

@@ -435,9 +435,8 @@ def test_gamma_dielectric_gradient_matches_fd_and_fixes_eq12_sign():
 
 def test_gamma_forces_match_central_differences():
     """P9 for the Eq. 9-10 dielectric: dE/dR_a (eps term, rho frozen) against central
-    differences of the variational energy J. The cut-off is taken where the
-    truncation of gamma moves eps by < 1e-10 (a cut-off where it is visible puts
-    steps into E(R) that central differences pick up)."""
+    differences of the variational energy J (the tapered cut-off keeps E(R)
+    smooth)."""
     grid, cell = (16, 16, 24), (8.0, 8.0, 12.0)
     at = W.slab_atoms(cell, 2, 2, seed=1)
     rv = _radii(at.Z)
@@ -456,6 +455,106 @@ def test_gamma_forces_match_central_differences():
     sel = [0, 5]
     Ge, Gr = O.energy_gradient(phi, grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud, p=p, atoms=sel,
                                rho_moves=False, rvdw=rv)
+    fd = np.zeros((len(sel), 3))
+    d = 1e-4
+    for t, a in enumerate(sel):
+        for c in range(3):
+            pp = pos.copy(); pp[a, c] += d
+            pm = pos.copy(); pm[a, c] -= d
+            fd[t, c] = (E_of(pp) - E_of(pm)) / (2 * d)
+    scale = np.max(np.abs(fd))
+    assert scale > 1e-3
+    assert np.max(np.abs(fd - Ge[sel])) < 1e-6 * scale
+
+
+# -------------------------------------------------------------- Eq. 19 solvent exclusion
+
+def _eq19_case(seed=0):
+    grid, cell = (16, 16, 32), (8.0, 8.0, 16.0)
+    at = W.slab_atoms(cell, 2, 3, seed=seed)
+    zs = np.sort(at.pos[:, 2])
+    zlim = 0.5 * (zs[len(zs) // 3 - 1] + zs[len(zs) // 3])  # between layers 1 and 2: layer 1 is lower
+    return grid, cell, at, W.vdw_radii(at.Z), zlim
+
+
+def test_eq19_without_lower_atoms_is_eq10():
+    """With z_lim below every atom, Eq. 19 is Eq. 9 term by term."""
+    grid, cell, at, rv, _ = _eq19_case()
+    p = O.GammaParams(rcut=7.9)
+    a = O.dielectric_eq19(grid, cell, at.pos, rv, -1.0, p)
+    b = O.dielectric_gamma(grid, cell, at.pos, rv, p)
+    assert np.max(np.abs(a - b)) < 1e-12 * p.eps0
+
+
+def test_eq19_dries_the_region_below_the_lower_layer():
+    """Below the lower atoms eps saturates to 1 (dry planes); far above the slab
+    it is the solvent's eps0; with Eq. 10 alone the region below stays wet."""
+    grid, cell, at, rv, zlim = _eq19_case()
+    p = O.GammaParams(rcut=7.9)
+    eps = O.dielectric_eq19(grid, cell, at.pos, rv, zlim, p)
+    pm = (eps - 1.0).reshape(grid[2], -1).max(axis=1)
+    zmin = at.pos[:, 2].min()
+    h = O.spacing(grid, cell)[2]
+    below = [k for k in range(grid[2]) if k * h < zmin - 3.0]
+    assert below and np.all(pm[below] < 1e-6)
+    assert O.dielectric_gamma(grid, cell, at.pos, rv, p).reshape(grid[2], -1).max(axis=1)[below[0]] > 1.0
+    zmax = at.pos[:, 2].max()
+    above = [k for k in range(grid[2]) if zmax + 5.0 < k * h < cell[2] - 1.0]
+    assert above and np.all(eps.reshape(grid[2], -1)[above].min(axis=1) > p.eps0 - 0.1)
+
+
+def test_eq19_sign_is_plus_on_the_atom_plane():
+    """At z = z_I a lower atom's term decays (the sign factor is +1 there)."""
+    grid, cell = (16, 16, 16), (8.0, 8.0, 8.0)
+    pos = np.array([[4.0, 4.0, 4.0]])                      # on grid point (8, 8, 8)
+    rv = np.array([1.5])
+    p = O.GammaParams(rcut=7.9)
+    eps19 = O.dielectric_eq19(grid, cell, pos, rv, 5.0, p)
+    eps10 = O.dielectric_gamma(grid, cell, pos, rv, p)
+    assert np.max(np.abs(eps19[8] - eps10[8])) < 1e-13 * p.eps0      # the plane z = z_I
+    x, y, z = _grid_points(grid, cell)
+    d = np.sqrt((x - 4.0) ** 2 + (y - 4.0) ** 2 + (z - 4.0) ** 2)
+    out = np.broadcast_to((z < 4.0) & (d > rv[0]), eps19.shape)
+    assert np.all(eps19[out] <= eps10[out])                      # below, outside the vdW sphere: drier
+
+
+def test_eq19_gradient_matches_fd():
+    """d eps/d R for both branches against central differences (the atom's z is
+    away from grid planes, so no point changes side)."""
+    grid, cell, at, rv, zlim = _eq19_case(seed=2)
+    p = O.GammaParams(rcut=7.9)
+    pos = at.pos.copy()
+    a = int(np.argmin(pos[:, 2]))                              # a lower atom
+    G, S = O.dummy_density_eq19(grid, cell, pos, rv, zlim, p)
+    de = O.dielectric_eq19_gradient_atom(a, grid, cell, pos, rv, zlim, G, S, p)
+    d = 1e-4
+    for c in range(3):
+        pp = pos.copy(); pp[a, c] += d
+        pm = pos.copy(); pm[a, c] -= d
+        fd = (O.dielectric_eq19(grid, cell, pp, rv, zlim, p) - O.dielectric_eq19(grid, cell, pm, rv, zlim, p)) / (2 * d)
+        scale = np.max(np.abs(fd))
+        assert scale > 0.1
+        assert np.max(np.abs(fd - de[c])) < 1e-6 * scale
+
+
+def test_eq19_forces_match_central_differences():
+    """P9 for Eq. 19: dE/dR_a (eps term, rho frozen) against central differences of J."""
+    grid, cell, at, rv, zlim = _eq19_case(seed=1)
+    p = O.GammaParams(rcut=7.9)
+    h = O.spacing(grid, cell)
+    pos = at.pos
+    rho = O.charge_density(grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud)
+
+    def E_of(q):
+        eps = O.dielectric_eq19(grid, cell, q, rv, zlim, p)
+        phi, _ = O.solve(rho, eps, h, tol=1e-14)
+        return O.variational_energy(rho, phi, eps, grid, cell)
+
+    eps = O.dielectric_eq19(grid, cell, pos, rv, zlim, p)
+    phi, _ = O.solve(rho, eps, h, tol=1e-14)
+    sel = [int(np.argmin(pos[:, 2])), int(np.argmax(pos[:, 2]))]
+    Ge, _ = O.energy_gradient(phi, grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud, p=p, atoms=sel,
+                              rho_moves=False, rvdw=rv, zlim=zlim)
     fd = np.zeros((len(sel), 3))
     d = 1e-4
     for t, a in enumerate(sel):
