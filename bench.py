@@ -181,12 +181,15 @@ def gpu_arm(args, rank, world):
     frames = [torch.tensor(traj[i % len(traj)], dtype=torch.float64, device=dev) for i in range(nfr)]
     hbm, hbm_src = load_peaks()
 
-    def make_solver(precision, split):
-        extra = {"kind": 1, "rcut": args.rcut_gamma} if args.kind == 1 else {}
-        return P.GPSolver(w.grid, w.cell, precision=precision, split=split, levels=w.levels,
-                          sweep_shape=args.sweep_shape, **extra)
+    zlim = W.lower_layer_zlim(at, w) if args.kind == 2 else 0.0
+    n_dir = args.n_dirichlet if args.n_dirichlet >= 0 else (0 if args.kind == 2 else 1)
 
-    radii = torch.tensor(W.vdw_radii(at.Z), dtype=torch.float64, device=dev) if args.kind == 1 else None
+    def make_solver(precision, split):
+        extra = {"kind": args.kind, "rcut": args.rcut_gamma, "zlim": zlim} if args.kind else {}
+        return P.GPSolver(w.grid, w.cell, precision=precision, split=split, levels=w.levels,
+                          sweep_shape=args.sweep_shape, n_dirichlet=n_dir, **extra)
+
+    radii = torch.tensor(W.vdw_radii(at.Z), dtype=torch.float64, device=dev) if args.kind else None
 
     solver = make_solver(args.precision, args.split)
     rho = solver.zeros()
@@ -334,7 +337,8 @@ def gpu_arm(args, rank, world):
         "vs_baseline": None, "dtype": "f32/f64" if args.precision == 1 else "f64", "data": "synthetic",
         "config": {"workload": w.name, "grid": list(w.grid), "cell_A": list(w.cell), "atoms": int(len(at.Z)),
                    "tol": args.tol, "precision": "mixed" if args.precision == 1 else "fp64",
-                   "dielectric": "erf product" if args.kind == 0 else "Eq. 9-10 (beta 2.4, rcut %.1f A)" % args.rcut_gamma,
+                   "dielectric": {0: "erf product", 1: "Eq. 9-10 (beta 2.4, rcut %.1f A)" % args.rcut_gamma,
+                                  2: "Eq. 19 (beta 2.4, rcut %.1f A, z_lim %.3f A)" % (args.rcut_gamma, zlim)}[args.kind],
                    "split": bool(args.split), "split_active": bool(stats.split_active),
                    "wet_fraction": stats.wet_fraction, "levels": stats.levels,
                    "outer_iterations_mean": float(np.mean(outer)), "vcycles_mean": float(np.mean(vcyc)),
@@ -485,8 +489,11 @@ def main():
     ap.add_argument("--mode", default="step", choices=["step", "md"])
     ap.add_argument("--frames", type=int, default=100)
     ap.add_argument("--graph-outer", type=int, default=2)
-    ap.add_argument("--kind", type=int, default=0, choices=[0, 1],
-                    help="dielectric: 0 erf product (the workloads), 1 Eq. 9-10 dummy density")
+    ap.add_argument("--kind", type=int, default=0, choices=[0, 1, 2],
+                    help="dielectric: 0 erf product (the workloads), 1 Eq. 9-10 dummy density, "
+                         "2 Eq. 19 (solvent excluded below the lowest layer)")
+    ap.add_argument("--n-dirichlet", type=int, default=-1,
+                    help="split: Dirichlet planes (-1: 0 = the whole dry run for --kind 2, else 1)")
     ap.add_argument("--rcut-gamma", type=float, default=9.0, help="cut-off of gamma for --kind 1 (Angstrom)")
     ap.add_argument("--sweep-shape", type=int, default=-1,
                     help="finest-level smoother tile (-1: autotuned; fixed shapes keep profiles comparable)")

@@ -158,3 +158,11 @@ def vdw_radii(Z):
     """Synthetic van der Waals radii (Angstrom) per species for the Eq. 9-10
     dielectric: "O" (Z = 6) 1.52, "Ti" (Z = 4) 2.0."""
     return np.where(np.asarray(Z) == 6, 1.52, 2.0)
+
+
+def lower_layer_zlim(at, w):
+    """z_lim of Eq. 19 between the lowest layer of the slab and the next one (in
+    the cell), so that the lowest layer excludes the solvent below it."""
+    zs = np.sort(np.mod(at.pos[:, 2], w.cell[2]))
+    per = len(zs) // w.layers
+    return float(0.5 * (zs[per - 1] + zs[per]))
