@@ -68,7 +68,9 @@ typedef struct {
     double dry_thresh;    /* 1e-3: a z-plane is dry when max(eps-1) < dry_thresh */
     int split;            /* 0: multigrid on the whole box; 1: dry/wet split (Scheme 1) */
     int n_dirichlet;      /* split: Dirichlet planes in the dry band (1 default; 0 = all the run allows) */
-    int precision;        /* 0: FP64 throughout; 1: FP32 multigrid inside FP64 defect correction */
+    int precision;        /* 0: FP64 throughout; 1: FP32 multigrid inside FP64 defect correction (for
+                             tol >= 1e-10 the outer residual runs in df64, FP32 hi/lo pairs, whose
+                             floor is ~1e-11 of ||b||; in FP64 below that) */
     int nu1, nu2;         /* red-black Gauss-Seidel sweeps before / after the coarse correction (2, 2) */
     int levels;           /* multigrid levels; 0 = coarsen until the coarsest grid has <= 512 points */
     int inner;            /* multigrid-preconditioned CG iterations per outer FP64 correction */

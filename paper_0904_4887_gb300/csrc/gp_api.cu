@@ -172,6 +172,10 @@ struct gp_ctx {
     double* sw_coef = nullptr;     // switching-function tables (2 * kSwNI * (kSwDeg+1))
     float4* sw_pack = nullptr;     // their packed FP32 copies (2 * kSwNI * 4)
     double* rvdw = nullptr;        // van der Waals radii for the kind-1 dielectric
+    float2* phid = nullptr;        // df64 copies for the mixed-precision residual: phi, b = -4 pi rho, eps
+    float2* bd = nullptr;
+    float2* epsd = nullptr;
+    bool epsd_ok = false;          // epsd matches eps64
     int rvdw_n = 0, rvdw_cap = 0;
     void* gtab = nullptr;          // periodized Gaussian factor tables (GaussTabs)
     size_t gtab_cap = 0;           // bytes
@@ -879,6 +883,34 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
     }
     T* rT = split ? reinterpret_cast<T*>(c->rfull) : F.r;
     T* ev = reinterpret_cast<T*>(c->evac);
+    // mixed precision: the outer residual in df64 (FP32 pairs) when the tolerance
+    // allows it (its floor is ~1e-11 of ||b||), in FP64 otherwise
+    const bool use_df = sizeof(T) == 4 && tol >= 1e-10;
+    if (use_df) {
+        if (!c->phid) {
+            c->phid = (float2*)dalloc(c, sizeof(float2) * c->n);
+            c->bd = (float2*)dalloc(c, sizeof(float2) * c->n);
+            c->epsd = (float2*)dalloc(c, sizeof(float2) * c->n);
+        }
+        ProfScope ps(c, GP_PROF_RES64, c->epsd_ok ? 1 : 2);
+        if (!c->epsd_ok) launch_to_df(c->n, c->eps64, 1.0, c->epsd, c->s);
+        launch_to_df(c->n, rho, -4.0 * kPi, c->bd, c->s);
+        c->epsd_ok = true;
+    }
+    GP_CHECK_LAUNCH();
+    // the FP64 (or df64) outer residual of the current phi into `rdst`, with its partial sums
+    auto outer_residual = [&](T* rdst) {
+        if constexpr (sizeof(T) == 4) {
+            if (use_df) {
+                ProfScope ps(c, GP_PROF_RES64, 2);
+                launch_to_df(c->n, phi, 1.0, c->phid, c->s);
+                launch_residual_df(c->g, c->phid, c->bd, c->epsd, rdst, c->partial, c->s);
+                return;
+            }
+        }
+        ProfScope ps(c, GP_PROF_RES64, 1);
+        launch_residual64<T>(c->g, phi, rho, c->eps64, rdst, c->partial, c->s);
+    };
     double best = INFINITY;
     gp_status result = GP_ERR_NOT_CONVERGED;
     const bool krylov = split && c->prm.accel;
@@ -892,25 +924,23 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
             F.solve_phi = phi;
             F.solve_rho = rho;
         }
-        const long key = ((long)k << 24) | ((long)c->prm.inner << 16) | ((long)c->prm.nu1 << 8) | c->prm.nu2;
+        const long key = ((long)use_df << 40) | ((long)k << 24) | ((long)c->prm.inner << 16) |
+                         ((long)c->prm.nu1 << 8) | c->prm.nu2;
         run_graph(c, F.solve_g, key, [&] {
             for (int it = 0; it < k; ++it) {
                 if (it > 0) {
                     ProfScope ps(c, GP_PROF_UPDATE64, 1);
                     launch_update_phi<T>(c->g, phi, F.x, (const T*)nullptr, 0, 0, c->s);
                 }
-                {
-                    ProfScope ps(c, GP_PROF_RES64, 1);
-                    launch_residual64<T>(c->g, phi, rho, c->eps64, F.r, c->partial, c->s);
-                }
+                outer_residual(F.r);
                 pcg_body(c, F, c->prm.inner);
             }
             {
                 ProfScope ps(c, GP_PROF_UPDATE64, 1);
                 launch_update_phi<T>(c->g, phi, F.x, (const T*)nullptr, 0, 0, c->s);
             }
-            ProfScope ps(c, GP_PROF_RES64, 2);
-            launch_residual64<T>(c->g, phi, rho, c->eps64, F.r, c->partial, c->s);
+            outer_residual(F.r);
+            ProfScope ps(c, GP_PROF_MISC, 1);
             launch_finalize(c->partial, kReduceBlocks, 2, c->scal + 8, c->s);
             GP_CHECK_LAUNCH();
         });
@@ -941,10 +971,7 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
             else launch_update_phi<T>(c->g, phi, F.x, (const T*)nullptr, 0, 0, c->s);
             GP_CHECK_LAUNCH();
         }
-        {
-            ProfScope ps(c, GP_PROF_RES64, 1);
-            launch_residual64<T>(c->g, phi, rho, c->eps64, rT, c->partial, c->s);
-        }
+        outer_residual(rT);
         GP_CHECK_LAUNCH();
         double s2[2];
         sum_host(c, 2, s2);
@@ -1149,6 +1176,7 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             if (p.kind != 0) launch_build_eps_gamma(c->g, at, dp, c->rvdw, c->eps64, c->pe64, c->eps32, c->s);
             else launch_build_eps(c->g, at, dp, tb, c->eps64, c->pe64, c->eps32, c->s);
         }
+        c->epsd_ok = false;
         GP_CHECK_LAUNCH();
         {
             ProfScope ps(c, GP_PROF_MISC, 1);

@@ -147,6 +147,10 @@ void launch_forces_finish(const double* S, const double* T, int n, double ce, do
 // reductions and FP64 full-box passes (k_mg.cu)
 void launch_finalize(const double* partial, int nparts, int ncomp, double* out, cudaStream_t s);
 void launch_rho_stats(long n, const double* rho, double* partial, cudaStream_t s);
+// df64 (hi, lo FP32 pair) copies and the df64 full-box residual of the mixed-precision path
+void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStream_t s);
+void launch_residual_df(const Geo& g, const float2* phid, const float2* bd, const float2* epsd, float* r_out,
+                        double* partial, cudaStream_t s);
 void launch_sub_mean(long n, double* x, const double* sum_slot, double scale, cudaStream_t s);
 template <typename T>
 void launch_residual64(const Geo& g, const double* phi, const double* rho, const double* eps64,

@@ -675,6 +675,81 @@ __global__ void __launch_bounds__(kReduceThreads) k_residual64(Geo g, const doub
     if (threadIdx.x == 0) partial[2 * blockIdx.x + 1] = s;
 }
 
+// ------------------------------------------------------------ df64 full box (mixed precision)
+// The outer residual of the mixed-precision solve in df64: every value is an
+// unevaluated sum hi + lo of two FP32 numbers (Dekker 1971, Knuth's two-sum),
+// which carries ~48 bits on the FP32 pipe (GB300's FP64 pipe runs at 1/64 of
+// it). phi, eps and b = -4 pi rho are kept as (hi, lo) pairs; the residual of
+// the pair-rounded phi is within ~1e-11 of ||b|| of the FP64 one, far below the
+// tolerances this path serves (the host uses it only for tol >= 1e-10).
+struct d2 { float hi, lo; };
+__device__ __forceinline__ d2 d2_quick(float s, float e) {
+    const float t = s + e;
+    return {t, e - (t - s)};
+}
+__device__ __forceinline__ d2 d2_add(d2 a, d2 b) {
+    const float s = a.hi + b.hi;
+    const float v = s - a.hi;
+    float e = (a.hi - (s - v)) + (b.hi - v);
+    e += a.lo + b.lo;
+    return d2_quick(s, e);
+}
+__device__ __forceinline__ d2 d2_neg(d2 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ d2 d2_mul(d2 a, d2 b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return d2_quick(p, e);
+}
+__device__ __forceinline__ d2 d2_ld(const float2* p, long i) {
+    const float2 v = p[i];
+    return {v.x, v.y};
+}
+
+// dst = (hi, lo) split of scale * src
+__global__ void k_to_df(long n, const double* __restrict__ src, double scale, float2* __restrict__ dst) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const double v = scale * src[t];
+        const float hi = (float)v;
+        dst[t] = make_float2(hi, (float)(v - (double)hi));
+    }
+}
+
+// r = b - A phi on the periodic full box (cell eps, face means), in df64;
+// r_out = the residual rounded to FP32; partial[2b] = block's sum r^2,
+// partial[2b+1] = block's sum phi (compensated FP32 sums, FP64 across threads)
+__global__ void __launch_bounds__(kReduceThreads) k_residual_df(Geo g, const float2* __restrict__ phid,
+                                                               const float2* __restrict__ bd,
+                                                               const float2* __restrict__ epsd, d2 cxd, d2 cyd,
+                                                               d2 czd, float* __restrict__ r_out,
+                                                               double* partial) {
+    __shared__ double red[32];
+    KSum<float> s2, sp;
+    for (long row = blockIdx.x; row < (long)g.ny * g.nz; row += gridDim.x)
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+        const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+        const Nb nb = neighbours(g.nx, g.ny, g.nz, 1, i, j, k);
+        const d2 p0 = d2_ld(phid, nb.c), e0 = d2_ld(epsd, nb.c);
+        const d2 mp0 = d2_neg(p0);
+        auto axis = [&](long ip, long im, d2 c) {
+            const d2 fp = d2_mul(d2_add(e0, d2_ld(epsd, ip)), d2_add(d2_ld(phid, ip), mp0));
+            const d2 fm = d2_mul(d2_add(e0, d2_ld(epsd, im)), d2_add(p0, d2_neg(d2_ld(phid, im))));
+            return d2_mul(c, d2_add(fp, d2_neg(fm)));
+        };
+        const d2 ap = d2_add(d2_add(axis(nb.xp, nb.xm, cxd), axis(nb.yp, nb.ym, cyd)), axis(nb.zp, nb.zm, czd));
+        const d2 r = d2_add(d2_ld(bd, nb.c), d2_neg(ap));
+        r_out[nb.c] = r.hi;
+        s2.add(r.hi * r.hi);
+        sp.add(p0.hi);
+        sp.add(p0.lo);
+    }
+    double s = block_sum(s2.value(), red);
+    if (threadIdx.x == 0) partial[2 * blockIdx.x] = s;
+    s = block_sum(sp.value(), red);
+    if (threadIdx.x == 0) partial[2 * blockIdx.x + 1] = s;
+}
+
 // phi += e_full (+ e_band on the band planes); band plane kb <-> global plane
 // (band_first + kb) mod nz, kb < band_nz
 template <typename T>
@@ -1026,6 +1101,16 @@ void launch_residual64(const Geo& g, const double* phi, const double* rho, const
                        double* partial, cudaStream_t s) {
     k_residual64<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(g, phi, rho, eps64, r_out, partial);
 }
+void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStream_t s) {
+    k_to_df<<<grid_for(n, 256), 256, 0, s>>>(n, src, scale, dst);
+}
+void launch_residual_df(const Geo& g, const float2* phid, const float2* bd, const float2* epsd, float* r_out,
+                        double* partial, cudaStream_t s) {
+    auto split = [](double v) { const float h = (float)v; return d2{h, (float)(v - (double)h)}; };
+    k_residual_df<<<kReduceBlocks, kReduceThreads, 0, s>>>(g, phid, bd, epsd, split(g.c2x), split(g.c2y),
+                                                           split(g.c2z), r_out, partial);
+}
+
 template <typename T>
 void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_band, int band_first, int band_nz,
                        cudaStream_t s) {

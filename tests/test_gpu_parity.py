@@ -177,6 +177,26 @@ def test_every_sweep_shape_converges_to_oracle(row_case, shape, split):
     assert s.stats().residual < 1e-12
 
 
+@pytest.mark.parametrize("k", range(len(SMALL)))
+@pytest.mark.parametrize("graph_outer", [0, 2])
+def test_mixed_df64_residual_path(small_cases, k, graph_outer):
+    """Mixed precision at tol 1e-9 runs its outer residual in df64: the residual it
+    reports is the FP64 residual of the phi it returns (checked by the oracle) and
+    the energy is within 1e-8 of the oracle's."""
+    GPSolver = _gpu()
+    (at, h, eps, rho), grid, cell = small_cases[k]
+    s = GPSolver(grid, cell, precision=1, split=0, graph_outer=graph_outer)
+    s.set_atoms(_t(at.pos))
+    phi = s.solve(_t(rho), tol=1e-9).cpu().numpy()
+    st = s.stats()
+    true_res = O.residual_norm(phi, rho, eps, h)
+    assert st.residual <= 1e-9 and true_res <= 2e-9
+    assert abs(true_res - st.residual) <= 1e-11 + 0.01 * true_res
+    ref, _ = O.solve(rho, eps, h, tol=1e-14)
+    E, E0 = O.energy(rho, phi, grid, cell), O.energy(rho, ref, grid, cell)
+    assert abs(E - E0) < 1e-8 * abs(E0)
+
+
 def test_split_band_matches_oracle_planner(small_cases):
     GPSolver = _gpu()
     (at, h, eps, rho), grid, cell = small_cases[0]
