@@ -750,6 +750,72 @@ __global__ void __launch_bounds__(kReduceThreads) k_residual_df(Geo g, const flo
     if (threadIdx.x == 0) partial[2 * blockIdx.x + 1] = s;
 }
 
+// The same residual, four consecutive x points per thread (nx % 4 == 0):
+// 16-byte loads of the (hi, lo) pairs of the centre, y and z neighbour rows.
+__device__ __forceinline__ void ld4(const float2* p, long i, d2 (&v)[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(p + i);
+    const float4 b = *reinterpret_cast<const float4*>(p + i + 2);
+    v[0] = {a.x, a.y}; v[1] = {a.z, a.w}; v[2] = {b.x, b.y}; v[3] = {b.z, b.w};
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_residual_df4(Geo g, const float2* __restrict__ phid,
+                                                                const float2* __restrict__ bd,
+                                                                const float2* __restrict__ epsd, d2 cxd, d2 cyd,
+                                                                d2 czd, float* __restrict__ r_out,
+                                                                double* partial) {
+    __shared__ double red[32];
+    KSum<float> s2, sp;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nx4 = nx >> 2;
+    const long pl = (long)nx * ny;
+    const int total = nx4 * ny * nz;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int i4 = t % nx4;
+        const int row = t / nx4;
+        const int j = row % ny, k = row / ny;
+        const long rb = (long)k * pl + (long)j * nx;
+        const long c = rb + 4 * i4;
+        const long cxm = i4 == 0 ? rb + nx - 1 : c - 1;
+        const long cxp = i4 == nx4 - 1 ? rb : c + 4;
+        const long dym = j == 0 ? (long)(ny - 1) * nx : -(long)nx;
+        const long dyp = j == ny - 1 ? -(long)(ny - 1) * nx : (long)nx;
+        const long dzm = k == 0 ? (long)(nz - 1) * pl : -pl;
+        const long dzp = k == nz - 1 ? -(long)(nz - 1) * pl : pl;
+        d2 p[6], e[6], pym[4], pyp[4], pzm[4], pzp[4], eym[4], eyp[4], ezm[4], ezp[4], b[4];
+        {
+            d2 v[4];
+            ld4(phid, c, v);
+            p[1] = v[0]; p[2] = v[1]; p[3] = v[2]; p[4] = v[3];
+            ld4(epsd, c, v);
+            e[1] = v[0]; e[2] = v[1]; e[3] = v[2]; e[4] = v[3];
+        }
+        p[0] = d2_ld(phid, cxm); p[5] = d2_ld(phid, cxp);
+        e[0] = d2_ld(epsd, cxm); e[5] = d2_ld(epsd, cxp);
+        ld4(phid, c + dym, pym); ld4(phid, c + dyp, pyp); ld4(phid, c + dzm, pzm); ld4(phid, c + dzp, pzp);
+        ld4(epsd, c + dym, eym); ld4(epsd, c + dyp, eyp); ld4(epsd, c + dzm, ezm); ld4(epsd, c + dzp, ezp);
+        ld4(bd, c, b);
+        float out[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const d2 p0 = p[m + 1], e0 = e[m + 1], mp0 = d2_neg(p0);
+            auto face = [&](d2 en, d2 pn) { return d2_mul(d2_add(e0, en), d2_add(pn, mp0)); };
+            // A phi = sum_axes c [ (e0+e+)(p+ - p0) + (e0+e-)(p- - p0) ]
+            const d2 ax = d2_mul(cxd, d2_add(face(e[m + 2], p[m + 2]), face(e[m], p[m])));
+            const d2 ay = d2_mul(cyd, d2_add(face(eyp[m], pyp[m]), face(eym[m], pym[m])));
+            const d2 az = d2_mul(czd, d2_add(face(ezp[m], pzp[m]), face(ezm[m], pzm[m])));
+            const d2 r = d2_add(b[m], d2_neg(d2_add(d2_add(ax, ay), az)));
+            out[m] = r.hi;
+            s2.add(r.hi * r.hi);
+            sp.add(p0.hi);
+            sp.add(p0.lo);
+        }
+        *reinterpret_cast<float4*>(r_out + c) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+    double sum = block_sum(s2.value(), red);
+    if (threadIdx.x == 0) partial[2 * blockIdx.x] = sum;
+    sum = block_sum(sp.value(), red);
+    if (threadIdx.x == 0) partial[2 * blockIdx.x + 1] = sum;
+}
+
 // phi += e_full (+ e_band on the band planes); band plane kb <-> global plane
 // (band_first + kb) mod nz, kb < band_nz
 template <typename T>
@@ -1107,8 +1173,14 @@ void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStre
 void launch_residual_df(const Geo& g, const float2* phid, const float2* bd, const float2* epsd, float* r_out,
                         double* partial, cudaStream_t s) {
     auto split = [](double v) { const float h = (float)v; return d2{h, (float)(v - (double)h)}; };
-    k_residual_df<<<kReduceBlocks, kReduceThreads, 0, s>>>(g, phid, bd, epsd, split(g.c2x), split(g.c2y),
-                                                           split(g.c2z), r_out, partial);
+    const bool vec = g.nx % 4 == 0 && ((reinterpret_cast<uintptr_t>(phid) | reinterpret_cast<uintptr_t>(bd) |
+                                        reinterpret_cast<uintptr_t>(epsd) | reinterpret_cast<uintptr_t>(r_out)) & 15) == 0;
+    if (vec)
+        k_residual_df4<<<kReduceBlocks, kReduceThreads, 0, s>>>(g, phid, bd, epsd, split(g.c2x), split(g.c2y),
+                                                                split(g.c2z), r_out, partial);
+    else
+        k_residual_df<<<kReduceBlocks, kReduceThreads, 0, s>>>(g, phid, bd, epsd, split(g.c2x), split(g.c2y),
+                                                               split(g.c2z), r_out, partial);
 }
 
 template <typename T>
