@@ -163,6 +163,9 @@ void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_ba
 template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s);
 // one fused red-black sweep of a cell-eps level: u_new from u_old, colour `first` updated first (k_smooth.cu)
 void rb_sweep_init();
+// polls per mbarrier wait of the whole-row smoother's main loop (< 0: the default);
+// gp_create sets it from GP_TEST_SWEEP_WAIT_POLLS, which only tests use
+void rb_sweep_set_wait_polls(int polls);
 // err: device flag set to 1 if a TMA wait of the row-tile kernel expired (may be null)
 template <typename T> void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first,
                                            cudaStream_t s, int shape, int* err = nullptr);

@@ -187,6 +187,10 @@ __global__ void __launch_bounds__(NT) k_rb_sweep(LV<T> L, const T* __restrict__ 
 // records the fact in *err and runs to its end without further waits.
 constexpr int NSLOT = 6;
 
+// polls per phase wait in the main loop of the row sweep (the exit drain always
+// uses the default); lowered only to test the expiry path
+int g_wait_polls = 1 << 20;
+
 template <int NPX, int SY>
 struct RowRing {
     static constexpr int RU = SY + 4, RF = SY + 2;
@@ -218,9 +222,10 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned pari
         : "memory");
     return ok != 0;
 }
-// bounded wait (about a second at most); false if it gave up
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (int it = 0; it < (1 << 20); ++it)
+// bounded wait (`limit` polls, about a second for the default); false if it gave up
+constexpr int kWaitPolls = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int limit = kWaitPolls) {
+    for (int it = 0; it < limit; ++it)
         if (mbar_test(bar, parity)) return true;
     return false;
 }
@@ -245,7 +250,7 @@ constexpr int rows_min_blocks() {
 template <int NPX, int SY>
 __global__ void __launch_bounds__(NPX * (SY + 2), rows_min_blocks<NPX, SY>())
     k_rb_sweep_rows(LV<float> L, const float* __restrict__ u_old, const float* __restrict__ f,
-                    float* __restrict__ u_new, int first, int sz, int* err) {
+                    float* __restrict__ u_new, int first, int sz, int* err, int wait_limit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using RR = RowRing<NPX, SY>;
     constexpr int NTH = NPX * (SY + 2), RU = RR::RU, RF = RR::RF;
@@ -277,9 +282,12 @@ __global__ void __launch_bounds__(NPX * (SY + 2), rows_min_blocks<NPX, SY>())
     // plane q into slot (q - qb) % NSLOT: warp 0 issues one bulk copy per row;
     // planes outside the data (beyond the Dirichlet walls, f on the walls) are
     // filled by the threads with plain stores instead
+    int last_issued = -1;                                 // local index of the last plane sent (uniform)
+    int waited = -1;                                      // warp 0: planes <= this one have landed
     auto issue = [&](int q) {
-        if (q > z1 + 1) return;
+        if (q > z1 + 1 || bad) return;                    // after an expired wait nothing new is sent
         const int slot = (q - qb) % NSLOT;
+        last_issued = q - qb;
         int kg;
         if (L.zper) kg = q < 0 ? q + nz : (q >= nz ? q - nz : q);
         else kg = (q < -1 || q > nz) ? -99 : q;
@@ -312,7 +320,9 @@ __global__ void __launch_bounds__(NPX * (SY + 2), rows_min_blocks<NPX, SY>())
     };
     auto wait_plane = [&](int q) {            // warp 0 only
         const int t = q - qb;
-        if (!bad && !mbar_wait(&R.bar[t % NSLOT], (unsigned)((t / NSLOT) & 1))) bad = 1;
+        if (bad) return;
+        if (mbar_wait(&R.bar[t % NSLOT], (unsigned)((t / NSLOT) & 1), wait_limit)) waited = t;
+        else bad = 1;
     };
 
     float2 U_m = make_float2(0.f, 0.f), U_0 = U_m;          // own u_old at q-1, q
@@ -395,10 +405,9 @@ __global__ void __launch_bounds__(NPX * (SY + 2), rows_min_blocks<NPX, SY>())
     }
     __syncthreads();
     if (tid == 0 && bad) {
-        // a wait expired: give the copies still in flight a bounded chance to land before the CTA exits
-        const int tl = z1 + 1 - qb;
-        for (int t = tl > NSLOT - 1 ? tl - (NSLOT - 1) : 0; t <= tl; ++t)
-            mbar_wait(&R.bar[t % NSLOT], (unsigned)((t / NSLOT) & 1));
+        // a wait expired: give the copies still in flight (planes after the last one
+        // that landed, up to the last one sent) a bounded chance to land before the CTA exits
+        for (int t = waited + 1; t <= last_issued; ++t) mbar_wait(&R.bar[t % NSLOT], (unsigned)((t / NSLOT) & 1));
         if (err) atomicExch(err, 1);
     }
 }
@@ -419,7 +428,7 @@ void sweep_rows(const LV<float>& L, const float* u_old, const float* f, float* u
     if (chunks > L.nz) chunks = L.nz;
     const int sz = (L.nz + chunks - 1) / chunks;
     dim3 grid(1, ty, (L.nz + sz - 1) / sz);
-    k_rb_sweep_rows<NPX, SY><<<grid, NPX * (SY + 2), sm, s>>>(L, u_old, f, u_new, first, sz, err);
+    k_rb_sweep_rows<NPX, SY><<<grid, NPX * (SY + 2), sm, s>>>(L, u_old, f, u_new, first, sz, err, g_wait_polls);
 }
 
 // row-tile kernels exist for these row lengths and heights
@@ -495,6 +504,8 @@ void sweep_dispatch(int shape, const LV<T>& L, const T* u_old, const T* f, T* u_
 }
 
 }  // namespace
+
+void rb_sweep_set_wait_polls(int polls) { g_wait_polls = polls < 0 ? (1 << 20) : polls; }
 
 // allow the dynamic shared memory of every sweep shape (called before any capture)
 void rb_sweep_init() {
