@@ -472,12 +472,13 @@ void sweep_shape(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first
         cudaFuncSetAttribute(k_rb_sweep<T, SX, SY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         return;
     }
-    // z chunk: about one wave of resident CTAs
-    int per_sm = (int)((220 * 1024) / sm);
+    // z chunks: at most one wave of resident CTAs (a second, partial wave would
+    // double the time), resident count from the shared memory per CTA
+    int per_sm = (int)((227 * 1024) / (sm + 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 8) per_sm = 8;
     const int txy = ((L.nx + SX - 1) / SX) * ((L.ny + SY - 1) / SY);
-    int chunks = (152 * per_sm + txy - 1) / txy;
+    int chunks = 152 * per_sm / txy;
     if (chunks > L.nz) chunks = L.nz;
     if (chunks < 1) chunks = 1;
     const int sz = (L.nz + chunks - 1) / chunks;
