@@ -898,18 +898,43 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         c->epsd_ok = true;
     }
     GP_CHECK_LAUNCH();
+    // On the full box the df64 path keeps phi itself as pairs (phid) through the
+    // loop, updated in FP32 arithmetic, and writes the FP64 phi once at the end.
+    const bool master_df = use_df && !split;
+    if (master_df) {
+        ProfScope ps(c, GP_PROF_UPDATE64, 1);
+        launch_to_df(c->n, phi, 1.0, c->phid, c->s);
+    }
+    GP_CHECK_LAUNCH();
     // the FP64 (or df64) outer residual of the current phi into `rdst`, with its partial sums
     auto outer_residual = [&](T* rdst) {
         if constexpr (sizeof(T) == 4) {
             if (use_df) {
-                ProfScope ps(c, GP_PROF_RES64, 2);
-                launch_to_df(c->n, phi, 1.0, c->phid, c->s);
+                ProfScope ps(c, GP_PROF_RES64, master_df ? 1 : 2);
+                if (!master_df) launch_to_df(c->n, phi, 1.0, c->phid, c->s);
                 launch_residual_df(c->g, c->phid, c->bd, c->epsd, rdst, c->partial, c->s);
                 return;
             }
         }
         ProfScope ps(c, GP_PROF_RES64, 1);
         launch_residual64<T>(c->g, phi, rho, c->eps64, rdst, c->partial, c->s);
+    };
+    // phi += the full-box correction x
+    auto update_full = [&](const T* x) {
+        ProfScope ps(c, GP_PROF_UPDATE64, 1);
+        if constexpr (sizeof(T) == 4) {
+            if (master_df) {
+                launch_update_phid(c->n, c->phid, x, c->s);
+                return;
+            }
+        }
+        launch_update_phi<T>(c->g, phi, x, (const T*)nullptr, 0, 0, c->s);
+    };
+    auto finish_phi = [&] {
+        if (master_df) {
+            ProfScope ps(c, GP_PROF_UPDATE64, 1);
+            launch_from_df(c->n, c->phid, phi, c->s);
+        }
     };
     double best = INFINITY;
     gp_status result = GP_ERR_NOT_CONVERGED;
@@ -928,17 +953,11 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
                          ((long)c->prm.nu1 << 8) | c->prm.nu2;
         run_graph(c, F.solve_g, key, [&] {
             for (int it = 0; it < k; ++it) {
-                if (it > 0) {
-                    ProfScope ps(c, GP_PROF_UPDATE64, 1);
-                    launch_update_phi<T>(c->g, phi, F.x, (const T*)nullptr, 0, 0, c->s);
-                }
+                if (it > 0) update_full(F.x);
                 outer_residual(F.r);
                 pcg_body(c, F, c->prm.inner);
             }
-            {
-                ProfScope ps(c, GP_PROF_UPDATE64, 1);
-                launch_update_phi<T>(c->g, phi, F.x, (const T*)nullptr, 0, 0, c->s);
-            }
+            update_full(F.x);
             outer_residual(F.r);
             ProfScope ps(c, GP_PROF_MISC, 1);
             launch_finalize(c->partial, kReduceBlocks, 2, c->scal + 8, c->s);
@@ -952,6 +971,7 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         if (st.history_len < GP_HISTORY) st.history[st.history_len++] = rn;
         st.residual = rn;
         if (rn <= tol) {
+            finish_phi();
             {
                 ProfScope ps(c, GP_PROF_MISC, 1);
                 launch_sub_mean(c->n, phi, c->scal + 9, 1.0 / (double)c->n, c->s);
@@ -965,10 +985,13 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
     }
     for (int it = 0; it < c->prm.max_outer; ++it) {
         if (it > 0) {
-            ProfScope ps(c, GP_PROF_UPDATE64, 1);
-            if (krylov) launch_update_phi<T>(c->g, phi, ekry, (const T*)nullptr, 0, 0, c->s);
-            else if (split) launch_update_phi<T>(c->g, phi, ev, B.x, c->band_first_interior, c->band_nz, c->s);
-            else launch_update_phi<T>(c->g, phi, F.x, (const T*)nullptr, 0, 0, c->s);
+            if (!split) {
+                update_full(F.x);
+            } else {
+                ProfScope ps(c, GP_PROF_UPDATE64, 1);
+                if (krylov) launch_update_phi<T>(c->g, phi, ekry, (const T*)nullptr, 0, 0, c->s);
+                else launch_update_phi<T>(c->g, phi, ev, B.x, c->band_first_interior, c->band_nz, c->s);
+            }
             GP_CHECK_LAUNCH();
         }
         outer_residual(rT);
@@ -1003,6 +1026,7 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         }
     }
     // gauge: the last residual pass summed phi into scal[9]
+    finish_phi();
     {
         ProfScope ps(c, GP_PROF_MISC, 1);
         launch_sub_mean(c->n, phi, c->scal + 9, 1.0 / (double)c->n, c->s);

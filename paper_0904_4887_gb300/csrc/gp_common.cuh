@@ -151,6 +151,9 @@ void launch_rho_stats(long n, const double* rho, double* partial, cudaStream_t s
 void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStream_t s);
 void launch_residual_df(const Geo& g, const float2* phid, const float2* bd, const float2* epsd, float* r_out,
                         double* partial, cudaStream_t s);
+// phid += e (n even, 16-byte aligned); phi = hi + lo
+void launch_update_phid(long n, float2* phid, const float* e, cudaStream_t s);
+void launch_from_df(long n, const float2* src, double* dst, cudaStream_t s);
 void launch_sub_mean(long n, double* x, const double* sum_slot, double scale, cudaStream_t s);
 template <typename T>
 void launch_residual64(const Geo& g, const double* phi, const double* rho, const double* eps64,

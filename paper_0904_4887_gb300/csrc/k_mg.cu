@@ -816,6 +816,25 @@ __global__ void __launch_bounds__(kReduceThreads) k_residual_df4(Geo g, const fl
     if (threadIdx.x == 0) partial[2 * blockIdx.x + 1] = sum;
 }
 
+// phid += e (df64 + FP32, 16-byte accesses: two points per float4) and its inverse,
+// phi = hi + lo in FP64, for the mixed-precision full-box loop that keeps phi as pairs
+__global__ void k_update_phid(long n2, float4* __restrict__ phid, const float2* __restrict__ e) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n2; t += (long)gridDim.x * blockDim.x) {
+        const float4 p = phid[t];
+        const float2 v = e[t];
+        const d2 a = d2_add({p.x, p.y}, {v.x, 0.f});
+        const d2 b = d2_add({p.z, p.w}, {v.y, 0.f});
+        phid[t] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+}
+
+__global__ void k_from_df(long n, const float2* __restrict__ src, double* __restrict__ dst) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const float2 v = src[t];
+        dst[t] = (double)v.x + (double)v.y;
+    }
+}
+
 // phi += e_full (+ e_band on the band planes); band plane kb <-> global plane
 // (band_first + kb) mod nz, kb < band_nz
 template <typename T>
@@ -1170,6 +1189,14 @@ void launch_residual64(const Geo& g, const double* phi, const double* rho, const
 void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStream_t s) {
     k_to_df<<<grid_for(n, 256), 256, 0, s>>>(n, src, scale, dst);
 }
+void launch_update_phid(long n, float2* phid, const float* e, cudaStream_t s) {
+    k_update_phid<<<grid_for(n / 2, 256), 256, 0, s>>>(n / 2, reinterpret_cast<float4*>(phid),
+                                                       reinterpret_cast<const float2*>(e));
+}
+void launch_from_df(long n, const float2* src, double* dst, cudaStream_t s) {
+    k_from_df<<<grid_for(n, 256), 256, 0, s>>>(n, src, dst);
+}
+
 void launch_residual_df(const Geo& g, const float2* phid, const float2* bd, const float2* epsd, float* r_out,
                         double* partial, cudaStream_t s) {
     auto split = [](double v) { const float h = (float)v; return d2{h, (float)(v - (double)h)}; };
