@@ -132,6 +132,43 @@ __global__ void k_rbgs(LV<T> L, T* u, const T* f, int color) {
     }
 }
 
+// The same half sweep on a face-coefficient level in FP32, one thread per x-pair
+// with 8-byte loads of the pair and of its y and z neighbour pairs (32-bit
+// index arithmetic).
+__device__ __forceinline__ float2 ld_f2(const float* p, long i) { return *reinterpret_cast<const float2*>(p + i); }
+
+__global__ void __launch_bounds__(256) k_rbgs_pairs(LV<float> L, float* __restrict__ u, const float* __restrict__ f,
+                                                    int color) {
+    const int nx = L.nx, ny = L.ny, nz = L.nz, np = nx >> 1;
+    const long pl = (long)nx * ny;
+    const int total = np * ny * nz;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int p = t % np;
+        const int row = t / np;
+        const int j = row % ny, k = row / ny;
+        const int m = (j + k + color) & 1;                 // the member (x = 2p + m) of this colour
+        const long rb = (long)k * pl + (long)j * nx;
+        const long c2 = rb + 2 * p;
+        const long dym = j == 0 ? (long)(ny - 1) * nx : -(long)nx;
+        const long dyp = j == ny - 1 ? -(long)(ny - 1) * nx : (long)nx;
+        const long dzm = (k == 0 && L.zper) ? (long)(nz - 1) * pl : -pl;
+        const long dzp = (k == nz - 1 && L.zper) ? -(long)(nz - 1) * pl : pl;
+        const long cl = p == 0 ? rb + nx - 1 : c2 - 1;     // x - 1 of the even member
+        const long cr = p == np - 1 ? rb : c2 + 2;         // x + 1 of the odd member
+        const float2 uo = ld_f2(u, c2);
+        auto pick = [m](float2 v) { return m ? v.y : v.x; };
+        const float uxm = m ? uo.x : u[cl], uxp = m ? u[cr] : uo.y;
+        const float2 cxo = ld_f2(L.cx, c2);
+        const float cxm = m ? cxo.x : L.cx[cl], cxp = m ? cxo.y : cxo.x;
+        const float cym = pick(ld_f2(L.cy, c2 + dym)), cyp = pick(ld_f2(L.cy, c2));
+        const float czm = pick(ld_f2(L.cz, c2 + dzm)), czp = pick(ld_f2(L.cz, c2));
+        const float sum = cxp * uxp + cxm * uxm + cyp * pick(ld_f2(u, c2 + dyp)) + cym * pick(ld_f2(u, c2 + dym)) +
+                          czp * pick(ld_f2(u, c2 + dzp)) + czm * pick(ld_f2(u, c2 + dzm));
+        const float d = cxp + cxm + cyp + cym + czp + czm;
+        u[c2 + m] = __fdividef(sum - pick(ld_f2(f, c2)), d);
+    }
+}
+
 template <typename T>
 __global__ void k_residual(LV<T> L, const T* u, const T* f, T* r) {
     const long rows = (long)L.ny * L.nz;
@@ -1218,6 +1255,13 @@ void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_ba
 }
 
 template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (!L.cell) {
+            const long pairs = (long)(L.nx / 2) * L.ny * L.nz;
+            k_rbgs_pairs<<<grid_for(pairs, 256), 256, 0, s>>>(L, u, f, color);
+            return;
+        }
+    }
     const long rows = (long)L.ny * L.nz;
     k_rbgs<T><<<row_blocks(rows), row_threads(L.nx / 2), 0, s>>>(L, u, f, color);
 }
