@@ -431,10 +431,301 @@ void sweep_rows(const LV<float>& L, const float* u_old, const float* f, float* u
     k_rb_sweep_rows<NPX, SY><<<grid, NPX * (SY + 2), sm, s>>>(L, u_old, f, u_new, first, sz, err, g_wait_polls);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised row-tile variant (FP32). Same tile as above (whole x rows,
+// SY output rows, a chunk of z-planes), but the loop has no CTA barrier:
+//   * one producer warp streams planes of u_old, eps and f into an NSW-slot
+//     ring with bulk copies, one row per copy; slot s completes phase
+//     `full[s]` when its bytes have landed;
+//   * the consumer threads own a pair column (2p, 2p+1) over K adjacent rows,
+//     so the y neighbours inside the K rows and the z neighbours come from
+//     registers; shared memory serves the x neighbour outside the pair and
+//     the rows just above and below the K rows;
+//   * iteration t handles plane q = qb + t: the first colour at q (A), whose
+//     values go to an NRW-plane ring `r`, then the second colour at q-1 (B).
+//     Each consumer warp arrives on `rdy[t % NRW]` right after A(t), by which
+//     point it has also read everything it needs from the slot of plane t.
+//     B waits for rdy(t-1): every first-colour value of plane q-1 is in `r`.
+//     The producer refills the slot of plane t only once rdy(t) completed.
+// A warp that writes r(t) has seen rdy(t-2), so every warp has finished
+// iteration t-3 and with it B(t-4), the last reader of the slot r(t) reuses
+// (NRW = 4). The producer is at most NSW - 1 planes ahead of the slowest warp,
+// and no barrier can complete a phase twice while a waiter still polls the
+// older one, so the parity waits never alias.
+constexpr int NSW = 4, NRW = 4;
+
+template <int NPX, int SY>
+struct WsRing {
+    static constexpr int RU = SY + 4, RF = SY + 2;
+    float2 u[NSW][RU][NPX];
+    float2 e[NSW][RU][NPX];
+    float2 f[NSW][RF][NPX];
+    float r[NRW][RF][NPX];
+    unsigned long long full[NSW];
+    unsigned long long rdy[NRW];
+};
+
+template <int NPX, int SY, int K>
+constexpr int ws_threads() { return NPX * ((SY + 2) / K) + 32; }
+
+// resident CTAs per SM: by shared memory, and by registers at 72 per thread
+template <int NPX, int SY, int K>
+constexpr int ws_min_blocks() {
+    constexpr int by_smem = (int)((227 * 1024) / (sizeof(WsRing<NPX, SY>) + 1024));
+    constexpr int by_regs = 65536 / (72 * ws_threads<NPX, SY, K>());
+    constexpr int m = by_smem < by_regs ? by_smem : by_regs;
+    return m < 1 ? 1 : (m > 8 ? 8 : m);
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int NPX, int SY, int K>
+__global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, SY, K>())
+    k_rb_sweep_ws(LV<float> L, const float* __restrict__ u_old, const float* __restrict__ f,
+                  float* __restrict__ u_new, int first, int sz, int* err, int wait_limit) {
+    static_assert((SY + 2) % K == 0, "K must divide the A rows");
+    constexpr int G = (SY + 2) / K, NC = NPX * G, NWC = NC / 32;
+    static_assert(NC % 32 == 0, "consumer threads must fill whole warps");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using WR = WsRing<NPX, SY>;
+    constexpr int RU = WR::RU, RF = WR::RF;
+    constexpr unsigned ROWB = NPX * 8;
+    WR& R = *reinterpret_cast<WR*>(smem_raw);
+    __shared__ volatile int bad;
+    const int nx = 2 * NPX, ny = L.ny, nz = L.nz;
+    const long pl = (long)nx * ny;
+    const int j0 = blockIdx.y * SY;
+    const int z0 = blockIdx.z * sz;
+    const int z1 = min(z0 + sz, nz);
+    if (z0 >= nz) return;
+    const int qb = z0 - 2;
+    const int T = z1 + 2 - qb;                       // planes qb .. z1+1; iterations 0 .. T-2
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        bad = 0;
+        for (int k = 0; k < NSW; ++k) mbar_init(&R.full[k], 1);
+        for (int k = 0; k < NRW; ++k) mbar_init(&R.rdy[k], NWC);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    if (tid >= NC) {
+        // ---------------- producer warp
+        const int lane = tid - NC;
+        int issued = 0;                              // planes 0 .. issued-1 sent
+        for (int t = 0; t < T; ++t) {
+            if (t >= NSW) {                          // slot of plane t - NSW: every warp done with iteration t - NSW
+                const int i = t - NSW;
+                bool ok = !bad && mbar_wait(&R.rdy[i % NRW], (unsigned)((i / NRW) & 1), wait_limit);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) { if (lane == 0) bad = 1; break; }
+            }
+            const int q = qb + t, slot = t % NSW;
+            int kg;
+            if (L.zper) kg = q < 0 ? q + nz : (q >= nz ? q - nz : q);
+            else kg = (q < -1 || q > nz) ? -99 : q;
+            const bool has_ue = kg != -99, inner = kg >= 0 && kg < nz;
+            if (!has_ue)
+                for (int x = lane; x < RU * NPX; x += 32) {
+                    (&R.u[slot][0][0])[x] = make_float2(0.f, 0.f);
+                    (&R.e[slot][0][0])[x] = make_float2(1.f, 1.f);
+                }
+            if (!inner)
+                for (int x = lane; x < RF * NPX; x += 32) (&R.f[slot][0][0])[x] = make_float2(0.f, 0.f);
+            __syncwarp();
+            const unsigned bytes = (has_ue ? 2u * RU * ROWB : 0u) + (inner ? (unsigned)RF * ROWB : 0u);
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive_tx(&R.full[slot], bytes);
+            }
+            __syncwarp();
+            const long base = (long)kg * pl;
+            if (has_ue)
+                for (int r = lane; r < 2 * RU; r += 32) {
+                    const int rr = r < RU ? r : r - RU;
+                    const long off = base + (long)wrap_idx(j0 - 2 + rr, ny) * nx;
+                    if (r < RU) bulk_g2s(&R.u[slot][rr][0], u_old + off, ROWB, &R.full[slot]);
+                    else bulk_g2s(&R.e[slot][rr][0], L.eps + off, ROWB, &R.full[slot]);
+                }
+            if (inner)
+                for (int r = lane; r < RF; r += 32)
+                    bulk_g2s(&R.f[slot][r][0], f + base + (long)wrap_idx(j0 - 1 + r, ny) * nx, ROWB, &R.full[slot]);
+            issued = t + 1;
+        }
+        // every copy sent must land before the CTA may exit (bounded, default limit)
+        if (lane == 0) {
+            for (int t = issued - NSW < 0 ? 0 : issued - NSW; t < issued; ++t)
+                if (!mbar_wait(&R.full[t % NSW], (unsigned)((t / NSW) & 1))) bad = 1;
+            if (bad && err) atomicExch(err, 1);
+        }
+        return;
+    }
+
+    // ---------------- consumer threads
+    const float cx = 0.5f * L.ihx2, cy = 0.5f * L.ihy2, cz = 0.5f * L.ihz2;
+    const int g = tid / NPX, p = tid % NPX;
+    const int pm = p == 0 ? NPX - 1 : p - 1, pp = p == NPX - 1 ? 0 : p + 1;
+    const int a0 = g * K;                            // first A row (A row a is global row j0 - 1 + a)
+    const int par0 = (j0 - 1 + a0 + first + 2 * ny) & 1;   // member of the first colour at row a0: (par0 + q) & 1
+    const int lane = tid & 31;
+    bool live = true;                                // false once a wait has expired
+    auto wait_full = [&](int t) {
+        if (!live) return;
+        if (bad || !mbar_wait(&R.full[t % NSW], (unsigned)((t / NSW) & 1), wait_limit)) { live = false; bad = 1; }
+    };
+    auto wait_rdy = [&](int i) {
+        if (!live) return;
+        if (bad || !mbar_wait(&R.rdy[i % NRW], (unsigned)((i / NRW) & 1), wait_limit)) { live = false; bad = 1; }
+    };
+    auto arrive = [&](int i) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&R.rdy[i % NRW]);
+    };
+
+    // The member a later use needs is known when a value arrives (the colours
+    // alternate along z), so values used once more are kept as that member only.
+    float um[K];                                     // own u_old at q-1, member of the first colour at q
+    float2 U_0[K];                                   // own u_old at q
+    float em2[K];                                    // own eps at q-2, member of the second colour at q-1
+    float2 E_m[K], E_0[K];                           // own eps at q-1, q
+    float fm[K];                                     // own f at q-1, member of the second colour there
+    float R_m2[K], R_m[K];                           // own first-colour values at q-2, q-1
+    float bx[K];                                     // eps at q-1 next to that member, outside the pair
+    float bylo = 1.f, byhi = 1.f;                    // eps rows a0-1, a0+K at q-1, same member
+    {
+        wait_full(0);
+        wait_full(1);
+        const int m0 = (par0 + qb + 1) & 1;          // first-colour member of row a0 at plane qb+1
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float2 u0 = R.u[0][a0 + k + 1][p];
+            um[k] = (m0 ^ (k & 1)) ? u0.y : u0.x;
+            E_m[k] = R.e[0][a0 + k + 1][p];
+            U_0[k] = R.u[1][a0 + k + 1][p];
+            E_0[k] = R.e[1][a0 + k + 1][p];
+            em2[k] = 1.f; fm[k] = 0.f; bx[k] = 1.f;
+            R_m2[k] = 0.f; R_m[k] = 0.f;
+        }
+        arrive(0);
+    }
+    for (int t = 1; t <= T - 2; ++t) {
+        const int q = qb + t;
+        wait_full(t + 1);
+        const int s0 = t % NSW, s1 = (t + 1) % NSW, rw = t % NRW, rr = (t - 1) % NRW;
+        const bool wall = !L.zper && (q == -1 || q == nz);
+        const bool runB = q - 1 >= z0;
+        auto step = [&](auto mc) {
+            constexpr int M0 = decltype(mc)::value;
+            float2 U_p[K], E_p[K], F_0[K];
+            float exm[K], exq[K], rA[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                U_p[k] = R.u[s1][a0 + k + 1][p];
+                E_p[k] = R.e[s1][a0 + k + 1][p];
+                F_0[k] = R.f[s0][a0 + k][p];
+                exm[k] = R.e[s0][a0 + k + 1][pm].y;
+                exq[k] = R.e[s0][a0 + k + 1][pp].x;
+            }
+            const float2 elo = R.e[s0][a0][p], ehi = R.e[s0][a0 + K + 1][p];
+            // ---- A(q): first colour at plane q, rows a0 .. a0+K-1 (member M of the pair)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int M = M0 ^ (k & 1);
+                auto pick = [M](float2 v) { return M ? v.y : v.x; };
+                const float uxa = M ? R.u[s0][a0 + k + 1][pp].x : R.u[s0][a0 + k + 1][pm].y;
+                const float e0 = pick(E_0[k]);
+                const float exl = M ? E_0[k].x : exm[k], exr = M ? exq[k] : E_0[k].y;
+                const float uxl = M ? U_0[k].x : uxa, uxr = M ? uxa : U_0[k].y;
+                const float eyl = k == 0 ? pick(elo) : pick(E_0[k - 1 < 0 ? 0 : k - 1]);
+                const float eyh = k == K - 1 ? pick(ehi) : pick(E_0[k + 1 < K ? k + 1 : K - 1]);
+                const float uyl = k == 0 ? (M ? R.u[s0][a0][p].y : R.u[s0][a0][p].x)
+                                         : pick(U_0[k - 1 < 0 ? 0 : k - 1]);
+                const float uyh = k == K - 1 ? (M ? R.u[s0][a0 + K + 1][p].y : R.u[s0][a0 + K + 1][p].x)
+                                             : pick(U_0[k + 1 < K ? k + 1 : K - 1]);
+                const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
+                const float aym = (e0 + eyl) * cy, ayp = (e0 + eyh) * cy;
+                const float azm = (e0 + pick(E_m[k])) * cz, azp = (e0 + pick(E_p[k])) * cz;
+                const float sum = axm * uxl + axp * uxr + aym * uyl + ayp * uyh + azm * um[k] + azp * pick(U_p[k]);
+                const float d = axm + axp + aym + ayp + azm + azp;
+                rA[k] = wall ? pick(U_0[k]) : __fdividef(sum - pick(F_0[k]), d);
+                R.r[rw][a0 + k][p] = rA[k];
+            }
+            arrive(t);
+            // ---- B(q-1): second colour at plane q-1 (the same members)
+            wait_rdy(t - 1);
+            if (runB) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int a = a0 + k;
+                    const int jB = j0 - 1 + a;
+                    if (a < 1 || a > SY || jB >= ny) continue;
+                    const int M = M0 ^ (k & 1);
+                    auto pick = [M](float2 v) { return M ? v.y : v.x; };
+                    const float rxa = M ? R.r[rr][a][pp] : R.r[rr][a][pm];
+                    const float ryl = k == 0 ? R.r[rr][a - 1][p] : R_m[k - 1 < 0 ? 0 : k - 1];
+                    const float ryh = k == K - 1 ? R.r[rr][a + 1][p] : R_m[k + 1 < K ? k + 1 : K - 1];
+                    const float e0 = pick(E_m[k]);
+                    const float exl = M ? E_m[k].x : bx[k], exr = M ? bx[k] : E_m[k].y;
+                    const float rxl = M ? R_m[k] : rxa, rxr = M ? rxa : R_m[k];
+                    const float eyl = k == 0 ? bylo : pick(E_m[k - 1 < 0 ? 0 : k - 1]);
+                    const float eyh = k == K - 1 ? byhi : pick(E_m[k + 1 < K ? k + 1 : K - 1]);
+                    const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
+                    const float aym = (e0 + eyl) * cy, ayp = (e0 + eyh) * cy;
+                    const float azm = (e0 + em2[k]) * cz, azp = (e0 + pick(E_0[k])) * cz;
+                    const float sum = axm * rxl + axp * rxr + aym * ryl + ayp * ryh + azm * R_m2[k] + azp * rA[k];
+                    const float d = axm + axp + aym + ayp + azm + azp;
+                    const float vB = __fdividef(sum - fm[k], d);
+                    float2* out = reinterpret_cast<float2*>(u_new + (long)(q - 1) * pl + (long)jB * nx) + p;
+                    *out = M ? make_float2(R_m[k], vB) : make_float2(vB, R_m[k]);
+                }
+            }
+            // ---- shift the z window. At plane q+1 the members swap: the first
+            // colour of row k is member 1-M, which is also the member B(q) uses.
+            bylo = M0 ? elo.x : elo.y;
+            byhi = (M0 ^ ((K - 1) & 1)) ? ehi.x : ehi.y;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int M = M0 ^ (k & 1);
+                bx[k] = M ? exm[k] : exq[k];
+                um[k] = M ? U_0[k].x : U_0[k].y;
+                U_0[k] = U_p[k];
+                em2[k] = M ? E_m[k].x : E_m[k].y;
+                E_m[k] = E_0[k]; E_0[k] = E_p[k];
+                fm[k] = M ? F_0[k].x : F_0[k].y;
+                R_m2[k] = R_m[k]; R_m[k] = rA[k];
+            }
+        };
+        if ((par0 + q) & 1) step(std::integral_constant<int, 1>{});
+        else step(std::integral_constant<int, 0>{});
+    }
+    if (!live && err) atomicExch(err, 1);
+}
+
+template <int NPX, int SY, int K>
+void sweep_ws(const LV<float>& L, const float* u_old, const float* f, float* u_new, int first, cudaStream_t s,
+              bool attr, int* err) {
+    const size_t sm = sizeof(WsRing<NPX, SY>);
+    if (attr) {
+        cudaFuncSetAttribute(k_rb_sweep_ws<NPX, SY, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        return;
+    }
+    const int per_sm = ws_min_blocks<NPX, SY, K>();
+    const int ty = (L.ny + SY - 1) / SY;
+    int chunks = 152 * per_sm / ty;
+    if (chunks < 1) chunks = 1;
+    if (chunks > L.nz) chunks = L.nz;
+    const int sz = (L.nz + chunks - 1) / chunks;
+    dim3 grid(1, ty, (L.nz + sz - 1) / sz);
+    k_rb_sweep_ws<NPX, SY, K><<<grid, ws_threads<NPX, SY, K>(), sm, s>>>(L, u_old, f, u_new, first, sz, err,
+                                                                         g_wait_polls);
+}
+
 // row-tile kernels exist for these row lengths and heights
 #define GP_ROW_NPX(X) X(32) X(48) X(64) X(96) X(128)
 constexpr int kRowShapes = 3;   // SY = 4, 6, 8 (where NPX (SY + 2) <= 1024)
-static_assert(4 + kRowShapes == kSweepShapeCount, "shape count");
 
 template <int NPX>
 bool rows_dispatch_npx(int sy_id, const LV<float>& L, const float* u_old, const float* f, float* u_new, int first,
@@ -449,9 +740,45 @@ bool rows_dispatch_npx(int sy_id, const LV<float>& L, const float* u_old, const 
     return false;
 }
 
+// warp-specialised row shapes: (SY, K) = (6, 2), (4, 2), (6, 4), (4, 3)
+constexpr int kWsShapes = 4;
+
+template <int NPX, int SY, int K>
+bool ws_try(const LV<float>& L, const float* u_old, const float* f, float* u_new, int first, cudaStream_t s,
+            bool attr, int* err) {
+    if constexpr ((NPX * ((SY + 2) / K)) % 32 == 0 && ws_threads<NPX, SY, K>() <= 1024) {
+        sweep_ws<NPX, SY, K>(L, u_old, f, u_new, first, s, attr, err);
+        return true;
+    }
+    return false;
+}
+
+template <int NPX>
+bool ws_dispatch_npx(int id, const LV<float>& L, const float* u_old, const float* f, float* u_new, int first,
+                     cudaStream_t s, bool attr, int* err) {
+    switch (id) {
+    case 0: return ws_try<NPX, 6, 2>(L, u_old, f, u_new, first, s, attr, err);
+    case 1: return ws_try<NPX, 4, 2>(L, u_old, f, u_new, first, s, attr, err);
+    case 2: return ws_try<NPX, 6, 4>(L, u_old, f, u_new, first, s, attr, err);
+    case 3: return ws_try<NPX, 4, 3>(L, u_old, f, u_new, first, s, attr, err);
+    }
+    return false;
+}
+
+static_assert(4 + kRowShapes + kWsShapes == kSweepShapeCount, "shape count");
+
 // returns false when no row kernel fits this level (nx not covered, or too many threads)
 bool rows_dispatch(int sy_id, int npx, const LV<float>& L, const float* u_old, const float* f, float* u_new,
                    int first, cudaStream_t s, bool attr, int* err = nullptr) {
+    if (sy_id >= kRowShapes) {
+        switch (npx) {
+#define GP_NPX_WS(N) \
+    case N: return ws_dispatch_npx<N>(sy_id - kRowShapes, L, u_old, f, u_new, first, s, attr, err);
+            GP_ROW_NPX(GP_NPX_WS)
+#undef GP_NPX_WS
+        }
+        return false;
+    }
     switch (npx) {
 #define GP_NPX_CASE(N) \
     case N: return rows_dispatch_npx<N>(sy_id, L, u_old, f, u_new, first, s, attr, err);
@@ -518,7 +845,7 @@ void rb_sweep_init() {
     }
     const int npx[] = {32, 48, 64, 96, 128};
     for (int n : npx)
-        for (int k = 0; k < kRowShapes; ++k) {
+        for (int k = 0; k < kRowShapes + kWsShapes; ++k) {
             LV<float> lf{};
             rows_dispatch(k, n, lf, nullptr, nullptr, nullptr, 0, nullptr, true);
         }
@@ -540,7 +867,7 @@ int rb_sweep_autotune(const LV<T>& L, const T* u_old, const T* f, T* u_new, cuda
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 0; }
     int best = 0;
     float best_ms = 1e30f;
-    const int nshapes = kSweepShapes + (sizeof(T) == 4 ? kRowShapes : 0);
+    const int nshapes = kSweepShapes + (sizeof(T) == 4 ? kRowShapes + kWsShapes : 0);
     for (int k = 0; k < nshapes; ++k) {
         if (k >= kSweepShapes) {
             LV<float> probe{};

@@ -1,4 +1,4 @@
-"""Failure detection on the GPU without a fault: the whole-row smoother's
+"""Failure detection on the GPU without a fault: the whole-row smoothers'
 bounded mbarrier waits are made to expire (the test hook sets their poll
 budget to zero, so the first wait gives up at once), the kernel drains its own
 copies with the normal bound and records the expiry, gp_solve reports
@@ -23,14 +23,15 @@ def _t(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-def test_expired_smoother_wait_reports_timeout_and_gpu_stays_usable():
+@pytest.mark.parametrize("shape", [4, 7])     # CTA-barrier row tiles; producer-warp row tiles
+def test_expired_smoother_wait_reports_timeout_and_gpu_stays_usable(shape):
     from paper_0904_4887_gb300 import GPSolver, GPError
     grid, cell = (64, 48, 48), (10.0, 7.5, 12.0)
     at = W.slab_atoms(cell, 2, 2, seed=0)
     rho = O.charge_density(grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud)
     os.environ["GP_TEST_SWEEP_WAIT_POLLS"] = "0"
     try:
-        s = GPSolver(grid, cell, precision=1, sweep_shape=4)     # whole-row tiles: nx = 64
+        s = GPSolver(grid, cell, precision=1, sweep_shape=shape)  # whole-row tiles: nx = 64
         s.set_atoms(_t(at.pos))
         with pytest.raises(GPError) as e:
             s.solve(_t(rho), tol=1e-8)
@@ -39,7 +40,7 @@ def test_expired_smoother_wait_reports_timeout_and_gpu_stays_usable():
         del s
     finally:
         del os.environ["GP_TEST_SWEEP_WAIT_POLLS"]
-    s2 = GPSolver(grid, cell, precision=1, sweep_shape=4)
+    s2 = GPSolver(grid, cell, precision=1, sweep_shape=shape)
     s2.set_atoms(_t(at.pos))
     phi = s2.solve(_t(rho), tol=1e-12).cpu().numpy()
     eps = O.dielectric(grid, cell, at.pos)

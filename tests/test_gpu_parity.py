@@ -160,11 +160,11 @@ def row_case():
     return (at, h, eps, rho), g, c, ref
 
 
-@pytest.mark.parametrize("shape", range(7))
+@pytest.mark.parametrize("shape", range(11))
 @pytest.mark.parametrize("split", [0, 1])
 def test_every_sweep_shape_converges_to_oracle(row_case, shape, split):
     """Each finest-level smoother tile (x-y tiles, whole-row tiles with 4, 6, 8
-    rows), on the periodic box and on the Dirichlet wet band, inside the mixed
+    rows, warp-specialised whole-row tiles), on the periodic box and on the Dirichlet wet band, inside the mixed
     solve, gives the oracle's solution."""
     GPSolver = _gpu()
     (at, h, eps, rho), grid, cell, ref = row_case
