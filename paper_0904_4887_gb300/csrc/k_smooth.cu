@@ -477,6 +477,15 @@ constexpr int ws_min_blocks() {
     return m < 1 ? 1 : (m > 8 ? 8 : m);
 }
 
+// 1/x with the hardware reciprocal (about 1 ulp): the Gauss-Seidel value
+// only feeds the next iteration of a smoother, and this is several
+// instructions shorter than a full-range divide
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -611,13 +620,17 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
         }
         arrive(0);
     }
-    for (int t = 1; t <= T - 2; ++t) {
+    // one iteration; M0, the first-colour member of row a0, alternates with the
+    // plane, so the loop runs two iterations per trip with M0 fixed in each and
+    // the z window rotates through registers without copies
+    auto iter = [&](const int t, auto mc) {
         const int q = qb + t;
         wait_full(t + 1);
-        const int s0 = t % NSW, s1 = (t + 1) % NSW, rw = t % NRW, rr = (t - 1) % NRW;
+        const unsigned tu = (unsigned)t;
+        const int s0 = tu % NSW, s1 = (tu + 1) % NSW, rw = tu % NRW, rr = (tu - 1) % NRW;
         const bool wall = !L.zper && (q == -1 || q == nz);
         const bool runB = q - 1 >= z0;
-        auto step = [&](auto mc) {
+        {
             constexpr int M0 = decltype(mc)::value;
             float2 U_p[K], E_p[K], F_0[K];
             float exm[K], exq[K], rA[K];
@@ -650,7 +663,7 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
                 const float azm = (e0 + pick(E_m[k])) * cz, azp = (e0 + pick(E_p[k])) * cz;
                 const float sum = axm * uxl + axp * uxr + aym * uyl + ayp * uyh + azm * um[k] + azp * pick(U_p[k]);
                 const float d = axm + axp + aym + ayp + azm + azp;
-                rA[k] = wall ? pick(U_0[k]) : __fdividef(sum - pick(F_0[k]), d);
+                rA[k] = wall ? pick(U_0[k]) : (sum - pick(F_0[k])) * rcp_approx(d);
                 R.r[rw][a0 + k][p] = rA[k];
             }
             arrive(t);
@@ -677,7 +690,7 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
                     const float azm = (e0 + em2[k]) * cz, azp = (e0 + pick(E_0[k])) * cz;
                     const float sum = axm * rxl + axp * rxr + aym * ryl + ayp * ryh + azm * R_m2[k] + azp * rA[k];
                     const float d = axm + axp + aym + ayp + azm + azp;
-                    const float vB = __fdividef(sum - fm[k], d);
+                    const float vB = (sum - fm[k]) * rcp_approx(d);
                     float2* out = reinterpret_cast<float2*>(u_new + (long)(q - 1) * pl + (long)jB * nx) + p;
                     *out = M ? make_float2(R_m[k], vB) : make_float2(vB, R_m[k]);
                 }
@@ -697,9 +710,17 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
                 fm[k] = M ? F_0[k].x : F_0[k].y;
                 R_m2[k] = R_m[k]; R_m[k] = rA[k];
             }
-        };
-        if ((par0 + q) & 1) step(std::integral_constant<int, 1>{});
-        else step(std::integral_constant<int, 0>{});
+        }
+    };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    int t = 1;
+    if ((par0 + qb + 1) & 1) {
+        for (; t + 1 <= T - 2; t += 2) { iter(t, I1{}); iter(t + 1, I0{}); }
+        if (t <= T - 2) iter(t, I1{});
+    } else {
+        for (; t + 1 <= T - 2; t += 2) { iter(t, I0{}); iter(t + 1, I1{}); }
+        if (t <= T - 2) iter(t, I0{});
     }
     if (!live && err) atomicExch(err, 1);
 }
