@@ -275,8 +275,13 @@ def gpu_arm(args, rank, world):
     total_ms = sum(v["ms"] for v in prof.values())
     dominant = max(prof, key=lambda k: prof[k]["ms"])
     roof = roofline_for(dominant, prof, n0, hbm, hbm_src, prec_bytes) or {}
+    npx = w.grid[0] // 2
     shape_kernel = {0: "k_rb_sweep<float, 64, 8>", 1: "k_rb_sweep<float, 32, 16>", 2: "k_rb_sweep<float, 128, 4>",
-                    3: "k_rb_sweep<float, 32, 8>"}.get(stats.sweep_shape, "k_rb_sweep_rows")
+                    3: "k_rb_sweep<float, 32, 8>", 4: "k_rb_sweep_rows<%d, 4>" % npx,
+                    5: "k_rb_sweep_rows<%d, 6>" % npx, 6: "k_rb_sweep_rows<%d, 8>" % npx,
+                    7: "k_rb_sweep_ws<%d, 6, 2>" % npx, 8: "k_rb_sweep_ws<%d, 4, 2>" % npx,
+                    9: "k_rb_sweep_ws<%d, 6, 4>" % npx, 10: "k_rb_sweep_ws<%d, 4, 3>" % npx,
+                    }.get(stats.sweep_shape, "k_rb_sweep")
     smooth = roofline_for("smooth0", prof, n0, hbm, hbm_src, prec_bytes)
     if smooth is not None:
         smooth["kernel"] = shape_kernel + " (finest level, fused red-black sweep)"

@@ -468,11 +468,12 @@ struct WsRing {
 template <int NPX, int SY, int K>
 constexpr int ws_threads() { return NPX * ((SY + 2) / K) + 32; }
 
-// resident CTAs per SM: by shared memory, and by registers at 72 per thread
+// resident CTAs per SM: by shared memory, and by registers at about 72 per
+// thread for two rows per thread, 128 for three or four
 template <int NPX, int SY, int K>
 constexpr int ws_min_blocks() {
     constexpr int by_smem = (int)((227 * 1024) / (sizeof(WsRing<NPX, SY>) + 1024));
-    constexpr int by_regs = 65536 / (72 * ws_threads<NPX, SY, K>());
+    constexpr int by_regs = 65536 / ((K <= 2 ? 72 : 128) * ws_threads<NPX, SY, K>());
     constexpr int m = by_smem < by_regs ? by_smem : by_regs;
     return m < 1 ? 1 : (m > 8 ? 8 : m);
 }
@@ -580,6 +581,11 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
     const int a0 = g * K;                            // first A row (A row a is global row j0 - 1 + a)
     const int par0 = (j0 - 1 + a0 + first + 2 * ny) & 1;   // member of the first colour at row a0: (par0 + q) & 1
     const int lane = tid & 31;
+    unsigned bmask = 0;                              // rows k whose second colour this thread writes
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if (a0 + k >= 1 && a0 + k <= SY && j0 - 1 + a0 + k < ny) bmask |= 1u << k;
+    const int obase = (j0 - 1 + a0) * NPX + p;       // float2 index of row a0, pair p, in a plane
     bool live = true;                                // false once a wait has expired
     auto wait_full = [&](int t) {
         if (!live) return;
@@ -670,11 +676,11 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
             // ---- B(q-1): second colour at plane q-1 (the same members)
             wait_rdy(t - 1);
             if (runB) {
+                float2* ob = reinterpret_cast<float2*>(u_new + (long)(q - 1) * pl) + obase;
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     const int a = a0 + k;
-                    const int jB = j0 - 1 + a;
-                    if (a < 1 || a > SY || jB >= ny) continue;
+                    if (!(bmask & (1u << k))) continue;
                     const int M = M0 ^ (k & 1);
                     auto pick = [M](float2 v) { return M ? v.y : v.x; };
                     const float rxa = M ? R.r[rr][a][pp] : R.r[rr][a][pm];
@@ -691,8 +697,7 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
                     const float sum = axm * rxl + axp * rxr + aym * ryl + ayp * ryh + azm * R_m2[k] + azp * rA[k];
                     const float d = axm + axp + aym + ayp + azm + azp;
                     const float vB = (sum - fm[k]) * rcp_approx(d);
-                    float2* out = reinterpret_cast<float2*>(u_new + (long)(q - 1) * pl + (long)jB * nx) + p;
-                    *out = M ? make_float2(R_m[k], vB) : make_float2(vB, R_m[k]);
+                    ob[k * NPX] = M ? make_float2(R_m[k], vB) : make_float2(vB, R_m[k]);
                 }
             }
             // ---- shift the z window. At plane q+1 the members swap: the first
