@@ -281,6 +281,8 @@ def gpu_arm(args, rank, world):
                     5: "k_rb_sweep_rows<%d, 6>" % npx, 6: "k_rb_sweep_rows<%d, 8>" % npx,
                     7: "k_rb_sweep_ws<%d, 6, 2>" % npx, 8: "k_rb_sweep_ws<%d, 4, 2>" % npx,
                     9: "k_rb_sweep_ws<%d, 6, 4>" % npx, 10: "k_rb_sweep_ws<%d, 4, 3>" % npx,
+                    11: "k_rb_sweep_ws<%d, 16, 2>" % npx, 12: "k_rb_sweep_ws<%d, 14, 4>" % npx,
+                    13: "k_rb_sweep_ws<%d, 14, 2>" % npx, 14: "k_rb_sweep_ws<%d, 12, 2>" % npx,
                     }.get(stats.sweep_shape, "k_rb_sweep")
     smooth = roofline_for("smooth0", prof, n0, hbm, hbm_src, prec_bytes)
     if smooth is not None:

@@ -116,9 +116,10 @@ typedef struct {
     double history[GP_HISTORY]; /* relative residual after each outer step */
     int sweep_shape;            /* finest-level FP32 smoother tile in use: 0: 64x8, 1: 32x16,
                                    2: 128x4, 3: 32x8 points (x, y); 4, 5, 6: whole x rows times
-                                   4, 6, 8 rows; 7, 8, 9, 10: whole x rows times 6, 4, 6, 4 rows
-                                   with a producer warp and 2, 2, 4, 3 rows per thread (shapes 4 to
-                                   10 for nx = 64, 96, 128, 192, 256; otherwise 0) */
+                                   4, 6, 8 rows; 7 to 14: whole x rows times 6, 4, 6, 4, 16, 14,
+                                   14, 12 rows with a producer warp and 2, 2, 4, 3, 2, 4, 2, 2 rows
+                                   per thread (shapes 4 to 14 for nx = 64, 96, 128, 192, 256 where
+                                   the tile fits one CTA; otherwise 0) */
 } gp_stats;
 
 /* Fill *p with the defaults listed beside each field. */

@@ -175,7 +175,7 @@ template <typename T> void launch_rb_sweep(const LV<T>& L, const T* u_old, const
 template <typename T> int rb_sweep_autotune(const LV<T>& L, const T* u_old, const T* f, T* u_new, cudaStream_t s);
 // the shape actually used for a requested one (row tiles fall back to 0 where unavailable)
 template <typename T> int rb_sweep_resolve(const LV<T>& L, int shape);
-constexpr int kSweepShapeCount = 11;    // 4 x-y tiles + 3 row tiles + 4 warp-specialised row tiles
+constexpr int kSweepShapeCount = 15;    // 4 x-y tiles + 3 row tiles + 8 warp-specialised row tiles
 template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* f, T* r, cudaStream_t s);
 template <typename T> void launch_restrict(const LV<T>& F, const T* r, const LV<T>& C, T* fc, cudaStream_t s);
 template <typename T> void launch_prolong_add(const LV<T>& F, T* u, const LV<T>& C, const T* uc, cudaStream_t s);

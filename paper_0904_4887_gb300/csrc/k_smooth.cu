@@ -459,7 +459,6 @@ struct WsRing {
     static constexpr int RU = SY + 4, RF = SY + 2;
     float2 u[NSW][RU][NPX];
     float2 e[NSW][RU][NPX];
-    float2 f[NSW][RF][NPX];
     float r[NRW][RF][NPX];
     unsigned long long full[NSW];
     unsigned long long rdy[NRW];
@@ -468,14 +467,25 @@ struct WsRing {
 template <int NPX, int SY, int K>
 constexpr int ws_threads() { return NPX * ((SY + 2) / K) + 32; }
 
-// resident CTAs per SM: by shared memory, and by registers at about 72 per
-// thread for two rows per thread, 128 for three or four
+// resident CTAs per SM the tile is built for: as many as shared memory and
+// the registers the consumers' z window wants (about 72 per thread for two
+// rows, 128 for three or four) allow, at most two; and the register ceiling per
+// thread that lets that many reside: the register file is split evenly over the
+// four schedulers (16384 each) and a warp's registers come from one of them,
+// in 8-register steps. The host reads the residency back from the occupancy
+// calculator.
 template <int NPX, int SY, int K>
 constexpr int ws_min_blocks() {
     constexpr int by_smem = (int)((227 * 1024) / (sizeof(WsRing<NPX, SY>) + 1024));
     constexpr int by_regs = 65536 / ((K <= 2 ? 72 : 128) * ws_threads<NPX, SY, K>());
     constexpr int m = by_smem < by_regs ? by_smem : by_regs;
-    return m < 1 ? 1 : (m > 8 ? 8 : m);
+    return m < 1 ? 1 : (m > 2 ? 2 : m);
+}
+template <int NPX, int SY, int K>
+constexpr int ws_max_regs() {
+    constexpr int warps = ws_min_blocks<NPX, SY, K>() * ((ws_threads<NPX, SY, K>() + 31) / 32);
+    constexpr int r = (16384 / ((warps + 3) / 4) / 32) / 8 * 8;
+    return r > 255 ? 255 : r;
 }
 
 // 1/x with the hardware reciprocal (about 1 ulp): the Gauss-Seidel value
@@ -492,7 +502,7 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
 }
 
 template <int NPX, int SY, int K>
-__global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, SY, K>())
+__global__ void __maxnreg__((ws_max_regs<NPX, SY, K>()))
     k_rb_sweep_ws(LV<float> L, const float* __restrict__ u_old, const float* __restrict__ f,
                   float* __restrict__ u_new, int first, int sz, int* err, int wait_limit) {
     static_assert((SY + 2) % K == 0, "K must divide the A rows");
@@ -500,7 +510,7 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
     static_assert(NC % 32 == 0, "consumer threads must fill whole warps");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using WR = WsRing<NPX, SY>;
-    constexpr int RU = WR::RU, RF = WR::RF;
+    constexpr int RU = WR::RU;
     constexpr unsigned ROWB = NPX * 8;
     WR& R = *reinterpret_cast<WR*>(smem_raw);
     __shared__ volatile int bad;
@@ -537,16 +547,14 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
             int kg;
             if (L.zper) kg = q < 0 ? q + nz : (q >= nz ? q - nz : q);
             else kg = (q < -1 || q > nz) ? -99 : q;
-            const bool has_ue = kg != -99, inner = kg >= 0 && kg < nz;
+            const bool has_ue = kg != -99;
             if (!has_ue)
                 for (int x = lane; x < RU * NPX; x += 32) {
                     (&R.u[slot][0][0])[x] = make_float2(0.f, 0.f);
                     (&R.e[slot][0][0])[x] = make_float2(1.f, 1.f);
                 }
-            if (!inner)
-                for (int x = lane; x < RF * NPX; x += 32) (&R.f[slot][0][0])[x] = make_float2(0.f, 0.f);
             __syncwarp();
-            const unsigned bytes = (has_ue ? 2u * RU * ROWB : 0u) + (inner ? (unsigned)RF * ROWB : 0u);
+            const unsigned bytes = has_ue ? 2u * RU * ROWB : 0u;
             if (lane == 0) {
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 mbar_arrive_tx(&R.full[slot], bytes);
@@ -560,9 +568,6 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
                     if (r < RU) bulk_g2s(&R.u[slot][rr][0], u_old + off, ROWB, &R.full[slot]);
                     else bulk_g2s(&R.e[slot][rr][0], L.eps + off, ROWB, &R.full[slot]);
                 }
-            if (inner)
-                for (int r = lane; r < RF; r += 32)
-                    bulk_g2s(&R.f[slot][r][0], f + base + (long)wrap_idx(j0 - 1 + r, ny) * nx, ROWB, &R.full[slot]);
             issued = t + 1;
         }
         // every copy sent must land before the CTA may exit (bounded, default limit)
@@ -586,6 +591,21 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
     for (int k = 0; k < K; ++k)
         if (a0 + k >= 1 && a0 + k <= SY && j0 - 1 + a0 + k < ny) bmask |= 1u << k;
     const int obase = (j0 - 1 + a0) * NPX + p;       // float2 index of row a0, pair p, in a plane
+    // f has no neighbour terms: each thread reads its own rows with plain loads,
+    // one plane ahead, which keeps a third of the bytes off the bulk copies
+    int frow[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) frow[k] = (wrap_idx(j0 - 1 + a0 + k, ny) * NPX + p) * 2;
+    auto load_f = [&](int q, float2 (&F)[K]) {
+        int kg;
+        if (L.zper) kg = q < 0 ? q + nz : (q >= nz ? q - nz : q);
+        else kg = q;
+        const bool inner = kg >= 0 && kg < nz;
+        const float* fp = f + (long)(inner ? kg : 0) * pl;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            F[k] = inner ? __ldg(reinterpret_cast<const float2*>(fp + frow[k])) : make_float2(0.f, 0.f);
+    };
     bool live = true;                                // false once a wait has expired
     auto wait_full = [&](int t) {
         if (!live) return;
@@ -607,6 +627,7 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
     float em2[K];                                    // own eps at q-2, member of the second colour at q-1
     float2 E_m[K], E_0[K];                           // own eps at q-1, q
     float fm[K];                                     // own f at q-1, member of the second colour there
+    float2 F_0[K];                                   // own f at q
     float R_m2[K], R_m[K];                           // own first-colour values at q-2, q-1
     float bx[K];                                     // eps at q-1 next to that member, outside the pair
     float bylo = 1.f, byhi = 1.f;                    // eps rows a0-1, a0+K at q-1, same member
@@ -614,6 +635,7 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
         wait_full(0);
         wait_full(1);
         const int m0 = (par0 + qb + 1) & 1;          // first-colour member of row a0 at plane qb+1
+        load_f(qb + 1, F_0);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const float2 u0 = R.u[0][a0 + k + 1][p];
@@ -638,13 +660,13 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
         const bool runB = q - 1 >= z0;
         {
             constexpr int M0 = decltype(mc)::value;
-            float2 U_p[K], E_p[K], F_0[K];
+            float2 U_p[K], E_p[K], F_p[K];
+            load_f(q + 1, F_p);                      // used by the next iteration
             float exm[K], exq[K], rA[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 U_p[k] = R.u[s1][a0 + k + 1][p];
                 E_p[k] = R.e[s1][a0 + k + 1][p];
-                F_0[k] = R.f[s0][a0 + k][p];
                 exm[k] = R.e[s0][a0 + k + 1][pm].y;
                 exq[k] = R.e[s0][a0 + k + 1][pp].x;
             }
@@ -713,6 +735,7 @@ __global__ void __launch_bounds__(ws_threads<NPX, SY, K>(), ws_min_blocks<NPX, S
                 em2[k] = M ? E_m[k].x : E_m[k].y;
                 E_m[k] = E_0[k]; E_0[k] = E_p[k];
                 fm[k] = M ? F_0[k].x : F_0[k].y;
+                F_0[k] = F_p[k];
                 R_m2[k] = R_m[k]; R_m[k] = rA[k];
             }
         }
@@ -738,7 +761,14 @@ void sweep_ws(const LV<float>& L, const float* u_old, const float* f, float* u_n
         cudaFuncSetAttribute(k_rb_sweep_ws<NPX, SY, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         return;
     }
-    const int per_sm = ws_min_blocks<NPX, SY, K>();
+    static int per_sm = 0;                           // resident CTAs per SM (first launch asks)
+    if (per_sm == 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rb_sweep_ws<NPX, SY, K>, ws_threads<NPX, SY, K>(),
+                                                          sm) != cudaSuccess || n < 1)
+            n = 1;
+        per_sm = n;
+    }
     const int ty = (L.ny + SY - 1) / SY;
     int chunks = 152 * per_sm / ty;
     if (chunks < 1) chunks = 1;
@@ -766,13 +796,16 @@ bool rows_dispatch_npx(int sy_id, const LV<float>& L, const float* u_old, const 
     return false;
 }
 
-// warp-specialised row shapes: (SY, K) = (6, 2), (4, 2), (6, 4), (4, 3)
-constexpr int kWsShapes = 4;
+// warp-specialised row shapes: (SY, K) = (6, 2), (4, 2), (6, 4), (4, 3) at two
+// CTAs per SM; (16, 2), (14, 4), (14, 2), (12, 2) at one CTA per SM, whose
+// taller tiles copy fewer halo rows per output row
+constexpr int kWsShapes = 8;
 
 template <int NPX, int SY, int K>
 bool ws_try(const LV<float>& L, const float* u_old, const float* f, float* u_new, int first, cudaStream_t s,
             bool attr, int* err) {
-    if constexpr ((NPX * ((SY + 2) / K)) % 32 == 0 && ws_threads<NPX, SY, K>() <= 1024) {
+    if constexpr ((NPX * ((SY + 2) / K)) % 32 == 0 && ws_threads<NPX, SY, K>() <= 1024 &&
+                  sizeof(WsRing<NPX, SY>) <= 227 * 1024) {
         sweep_ws<NPX, SY, K>(L, u_old, f, u_new, first, s, attr, err);
         return true;
     }
@@ -787,6 +820,10 @@ bool ws_dispatch_npx(int id, const LV<float>& L, const float* u_old, const float
     case 1: return ws_try<NPX, 4, 2>(L, u_old, f, u_new, first, s, attr, err);
     case 2: return ws_try<NPX, 6, 4>(L, u_old, f, u_new, first, s, attr, err);
     case 3: return ws_try<NPX, 4, 3>(L, u_old, f, u_new, first, s, attr, err);
+    case 4: return ws_try<NPX, 16, 2>(L, u_old, f, u_new, first, s, attr, err);
+    case 5: return ws_try<NPX, 14, 4>(L, u_old, f, u_new, first, s, attr, err);
+    case 6: return ws_try<NPX, 14, 2>(L, u_old, f, u_new, first, s, attr, err);
+    case 7: return ws_try<NPX, 12, 2>(L, u_old, f, u_new, first, s, attr, err);
     }
     return false;
 }

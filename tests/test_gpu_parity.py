@@ -160,7 +160,7 @@ def row_case():
     return (at, h, eps, rho), g, c, ref
 
 
-@pytest.mark.parametrize("shape", range(11))
+@pytest.mark.parametrize("shape", range(15))
 @pytest.mark.parametrize("split", [0, 1])
 def test_every_sweep_shape_converges_to_oracle(row_case, shape, split):
     """Each finest-level smoother tile (x-y tiles, whole-row tiles with 4, 6, 8
