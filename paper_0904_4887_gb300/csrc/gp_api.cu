@@ -1113,6 +1113,7 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
         c->sw_coef = (double*)dalloc(c, sizeof(double) * 2 * kSwNI * (kSwDeg + 1));
         c->sw_pack = (float4*)dalloc(c, sizeof(float4) * 2 * kSwNI * 4);
         rb_sweep_init();
+        coarse_vcycle_init();
         {
             const char* wp = std::getenv("GP_TEST_SWEEP_WAIT_POLLS");
             rb_sweep_set_wait_polls(wp ? std::atoi(wp) : -1);

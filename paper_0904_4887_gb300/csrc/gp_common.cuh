@@ -208,6 +208,7 @@ struct CoarseSet {
     const T* minv;
 };
 template <typename T> void launch_coarse_vcycle(const CoarseSet<T>& S, cudaStream_t s);
+void coarse_vcycle_init();    // allow the shared-memory variant its dynamic shared memory (before any capture)
 
 // dry/wet band (k_mg.cu)
 template <typename T> void launch_cast_eps(long n, const double* e64, T* eT, cudaStream_t s);

@@ -209,6 +209,42 @@ __global__ void k_restrict(LV<T> F, const T* r, LV<T> C, T* fc) {
     }
 }
 
+// The same full weighting in FP32, two coarse x points per thread: per fine
+// row one 16-byte load (fine x 4h .. 4h+3) and the point before it serve
+// both (fine nx % 4 == 0, coarse nx even, fine nx = 2 coarse nx).
+__global__ void __launch_bounds__(256) k_restrict4(LV<float> F, const float* __restrict__ r, LV<float> C,
+                                                   float* __restrict__ fc) {
+    const int nh = C.nx >> 1;
+    const int total = nh * C.ny * C.nz;
+    const int zoff = F.zper ? 0 : 1;
+    const long pl = (long)F.nx * F.ny;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int h = t % nh;
+        const int row = t / nh;
+        const int J = row % C.ny, K = row / C.ny;
+        const int x0 = 4 * h, xm = x0 == 0 ? F.nx - 1 : x0 - 1;
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            int kk = 2 * K + zoff + dz;
+            if (F.zper) kk = kk < 0 ? kk + F.nz : (kk >= F.nz ? kk - F.nz : kk);
+            const float wz = dz == 0 ? 0.5f : 0.25f;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                int jj = 2 * J + dy;
+                jj = jj < 0 ? jj + F.ny : (jj >= F.ny ? jj - F.ny : jj);
+                const float w = wz * (dy == 0 ? 0.5f : 0.25f);
+                const float* rp = r + (long)kk * pl + (long)jj * F.nx;
+                const float4 v = *reinterpret_cast<const float4*>(rp + x0);
+                const float vm = rp[xm];
+                a0 += w * (0.25f * vm + 0.5f * v.x + 0.25f * v.y);
+                a1 += w * (0.25f * v.y + 0.5f * v.z + 0.25f * v.w);
+            }
+        }
+        *reinterpret_cast<float2*>(fc + (long)C.nx * (J + (long)C.ny * K) + 2 * h) = make_float2(a0, a1);
+    }
+}
+
 // trilinear interpolation of the coarse correction, added to u
 template <typename T>
 __global__ void k_prolong_add(LV<T> F, T* u, LV<T> C, const T* uc) {
@@ -458,11 +494,14 @@ __global__ void k_coarse_solve(LV<T> C, const T* inv, int n, const T* f, T* u) {
     __syncthreads();
     for (int p = threadIdx.x; p < n; p += blockDim.x) fs[p] -= (T)mean;
     __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        T acc = 0;
+    // one warp per row of the inverse: coalesced loads, a warp reduction
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int p = threadIdx.x >> 5; p < n; p += nw) {
         const T* row = inv + (long)p * n;
-        for (int q = 0; q < n; ++q) acc += row[q] * fs[q];
-        u[p] = acc;
+        T acc = 0;
+        for (int q = lane; q < n; q += 32) acc += row[q] * fs[q];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) u[p] = acc;
     }
 }
 
@@ -1138,11 +1177,13 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseSet<T> S) {
         if (threadIdx.x == 0) mean = C.zper ? tot / S.nc : 0.0;
         __syncthreads();
         const T mf = (T)mean;
-        for (int p = threadIdx.x; p < S.nc; p += blockDim.x) {
-            T acc = 0;
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int p = threadIdx.x >> 5; p < S.nc; p += nw) {
             const T* row = S.minv + (long)p * S.nc;
-            for (int q = 0; q < S.nc; ++q) acc += row[q] * (f[q] - mf);
-            S.u[S.L - 1][p] = acc;
+            T acc = 0;
+            for (int q = lane; q < S.nc; q += 32) acc += row[q] * (f[q] - mf);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) S.u[S.L - 1][p] = acc;
         }
         __syncthreads();
     }
@@ -1159,10 +1200,241 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseSet<T> S) {
     }
 }
 
+// The same bottom of the V-cycle with the levels' fields and face coefficients
+// held in shared memory: each phase then waits on shared-memory latency rather
+// than on an L2 round trip. The arrays keep the padded layout of the global
+// levels (one plane below and one above: the Dirichlet walls of a band); u
+// starts at zero, f of the first level comes from the level above, and u of
+// the first level goes back to global memory for the prolongation above.
+constexpr size_t kCoarseSmemBytes = 200 * 1024;
+
+// n / d for n, d < 2^16 from m = ceil(2^32 / d): (n m) >> 32 is exact there,
+// and costs one wide multiply instead of a division routine
+__device__ __forceinline__ int qdiv(int n, unsigned long long m) {
+    return (int)(((unsigned long long)(unsigned)n * m) >> 32);
+}
+__device__ __forceinline__ unsigned long long qmagic(int d) {
+    return (0x100000000ull + (unsigned long long)d - 1ull) / (unsigned long long)d;
+}
+struct QDiv { unsigned long long nx, ny, hx; };      // magics for a level's nx, ny and nx / 2
+
+// the block phases of the shared-memory coarse V-cycle, with 32-bit indices
+// (padded arrays: plane -1 and plane nz exist) and the divisions above
+template <typename T>
+__device__ void sm_rbgs(const LV<T>& L, const QDiv& D, T* u, const T* f, int color) {
+    const int nx = L.nx, ny = L.ny, nz = L.nz, hx = nx >> 1, pl = nx * ny;
+    const int np = hx * ny * nz;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int r = qdiv(t, D.hx), i2 = t - r * hx;
+        const int k = qdiv(r, D.ny), j = r - k * ny;
+        const int i = 2 * i2 + ((j + k + color) & 1);
+        const int c = i + nx * j + pl * k;
+        const int xm = c + (i == 0 ? nx - 1 : -1), xp = c + (i == nx - 1 ? 1 - nx : 1);
+        const int ym = c + (j == 0 ? (ny - 1) * nx : -nx), yp = c + (j == ny - 1 ? -(ny - 1) * nx : nx);
+        const int zm = c + ((k == 0 && L.zper) ? (nz - 1) * pl : -pl);
+        const int zp = c + ((k == nz - 1 && L.zper) ? -(nz - 1) * pl : pl);
+        const T cxm = L.cx[xm], cxp = L.cx[c], cym = L.cy[ym], cyp = L.cy[c], czm = L.cz[zm], czp = L.cz[c];
+        const T sm = cxp * u[xp] + cxm * u[xm] + cyp * u[yp] + cym * u[ym] + czp * u[zp] + czm * u[zm];
+        const T d = cxp + cxm + cyp + cym + czp + czm;
+        u[c] = (sm - f[c]) / d;
+    }
+}
+
+template <typename T>
+__device__ void sm_residual(const LV<T>& L, const QDiv& D, const T* u, const T* f, T* r) {
+    const int nx = L.nx, ny = L.ny, nz = L.nz, pl = nx * ny;
+    const int np = pl * nz;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int q = qdiv(t, D.nx), i = t - q * nx;
+        const int k = qdiv(q, D.ny), j = q - k * ny;
+        const int c = t;
+        const int xm = c + (i == 0 ? nx - 1 : -1), xp = c + (i == nx - 1 ? 1 - nx : 1);
+        const int ym = c + (j == 0 ? (ny - 1) * nx : -nx), yp = c + (j == ny - 1 ? -(ny - 1) * nx : nx);
+        const int zm = c + ((k == 0 && L.zper) ? (nz - 1) * pl : -pl);
+        const int zp = c + ((k == nz - 1 && L.zper) ? -(nz - 1) * pl : pl);
+        const T u0 = u[c];
+        const T au = L.cx[c] * (u[xp] - u0) - L.cx[xm] * (u0 - u[xm]) + L.cy[c] * (u[yp] - u0) -
+                     L.cy[ym] * (u0 - u[ym]) + L.cz[c] * (u[zp] - u0) - L.cz[zm] * (u0 - u[zm]);
+        r[c] = f[c] - au;
+    }
+}
+
+template <typename T>
+__device__ void sm_restrict(const LV<T>& F, const T* r, const LV<T>& C, const QDiv& DC, T* fc) {
+    const int np = C.nx * C.ny * C.nz;
+    const int zoff = F.zper ? 0 : 1;
+    const int pl = F.nx * F.ny;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int q = qdiv(t, DC.nx), I = t - q * C.nx;
+        const int K = qdiv(q, DC.ny), J = q - K * C.ny;
+        const int kf = 2 * K + zoff;
+        const int ic = 2 * I, im = ic == 0 ? F.nx - 1 : ic - 1, ip = ic == F.nx - 1 ? 0 : ic + 1;
+        T acc = 0;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            int kk = kf + dz;
+            if (F.zper) kk = kk < 0 ? kk + F.nz : (kk >= F.nz ? kk - F.nz : kk);
+            const T wz = dz == 0 ? (T)0.5 : (T)0.25;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                int jj = 2 * J + dy;
+                jj = jj < 0 ? jj + F.ny : (jj >= F.ny ? jj - F.ny : jj);
+                const T wy = dy == 0 ? (T)0.5 : (T)0.25;
+                const T* row = r + kk * pl + jj * F.nx;
+                acc += wz * wy * ((T)0.25 * row[im] + (T)0.5 * row[ic] + (T)0.25 * row[ip]);
+            }
+        }
+        fc[t] = acc;
+    }
+}
+
+template <typename T>
+__device__ void sm_prolong_add(const LV<T>& F, const QDiv& DF, T* u, const LV<T>& C, const T* uc) {
+    const int np = F.nx * F.ny * F.nz;
+    const int zoff = F.zper ? 0 : 1;
+    const int cpl = C.nx * C.ny;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int q = qdiv(t, DF.nx), i = t - q * F.nx;
+        const int k = qdiv(q, DF.ny), j = q - k * F.ny;
+        const int x0 = i >> 1, x1 = (i & 1) ? (x0 + 1 == C.nx ? 0 : x0 + 1) : x0;
+        const int y0 = j >> 1, y1 = (j & 1) ? (y0 + 1 == C.ny ? 0 : y0 + 1) : y0;
+        const T wx = (i & 1) ? (T)0.5 : (T)1, wy = (j & 1) ? (T)0.5 : (T)1;
+        const int kk = k - zoff;
+        int z0, z1;
+        T wz;
+        if (kk & 1) {
+            z0 = (kk - 1) >> 1;                  // floor division: -1 -> -1 (the lower wall)
+            z1 = z0 + 1;
+            if (C.zper && z1 == C.nz) z1 = 0;
+            wz = (T)0.5;
+        } else { z0 = kk >> 1; z1 = z0; wz = (T)1; }
+        auto at = [&](int x, int y, int z) { return uc[x + C.nx * y + cpl * z]; };
+        // with a weight of 1 the second index repeats the first, weighted 0 below
+        const T wx1 = (i & 1) ? wx : (T)0, wy1 = (j & 1) ? wy : (T)0, wz1 = (kk & 1) ? wz : (T)0;
+        const T a0 = wy * (wx * at(x0, y0, z0) + wx1 * at(x1, y0, z0)) + wy1 * (wx * at(x0, y1, z0) + wx1 * at(x1, y1, z0));
+        const T a1 = wy * (wx * at(x0, y0, z1) + wx1 * at(x1, y0, z1)) + wy1 * (wx * at(x0, y1, z1) + wx1 * at(x1, y1, z1));
+        u[t] += wz * a0 + wz1 * a1;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_vcycle_smem(CoarseSet<T> S) {
+    extern __shared__ __align__(16) unsigned char craw[];
+    __shared__ double red[32];
+    __shared__ LV<T> lv[16];
+    __shared__ T* su[16];
+    __shared__ T* sf[16];
+    __shared__ T* sr[16];
+    __shared__ QDiv qd[16];
+    if (threadIdx.x == 0) {
+        T* q = reinterpret_cast<T*>(craw);
+        for (int l = S.l0; l < S.L; ++l) {
+            const LV<T>& G = S.lv[l];
+            const long pl = (long)G.nx * G.ny, P = pl * (G.nz + 2);
+            LV<T> v = G;
+            v.cx = q + pl; q += P;
+            v.cy = q + pl; q += P;
+            v.cz = q + pl; q += P;
+            su[l] = q + pl; q += P;
+            sf[l] = q + pl; q += P;
+            sr[l] = nullptr;
+            if (l < S.L - 1) { sr[l] = q + pl; q += P; }
+            lv[l] = v;
+            qd[l].nx = qmagic(G.nx); qd[l].ny = qmagic(G.ny); qd[l].hx = qmagic(G.nx >> 1 > 0 ? G.nx >> 1 : 1);
+        }
+    }
+    __syncthreads();
+    for (int l = S.l0; l < S.L; ++l) {
+        const LV<T>& G = S.lv[l];
+        const long pl = (long)G.nx * G.ny, P = pl * (G.nz + 2);
+        T* x = const_cast<T*>(lv[l].cx) - pl;
+        T* y = const_cast<T*>(lv[l].cy) - pl;
+        T* z = const_cast<T*>(lv[l].cz) - pl;
+        T* uu = su[l] - pl;
+        T* ff = sf[l] - pl;
+        T* rr = sr[l] ? sr[l] - pl : nullptr;
+        const T* gf = S.f[l] - pl;
+        for (long t = threadIdx.x; t < P; t += blockDim.x) {
+            x[t] = G.cx[t - pl];
+            y[t] = G.cy[t - pl];
+            z[t] = G.cz[t - pl];
+            uu[t] = 0;
+            ff[t] = l == S.l0 ? gf[t] : (T)0;
+            if (rr) rr[t] = 0;
+        }
+    }
+    __syncthreads();
+    for (int l = S.l0; l < S.L - 1; ++l) {
+        for (int it = 0; it < S.nu1; ++it) {
+            sm_rbgs(lv[l], qd[l], su[l], sf[l], 0);
+            __syncthreads();
+            sm_rbgs(lv[l], qd[l], su[l], sf[l], 1);
+            __syncthreads();
+        }
+        sm_residual(lv[l], qd[l], su[l], sf[l], sr[l]);
+        __syncthreads();
+        sm_restrict(lv[l], sr[l], lv[l + 1], qd[l + 1], sf[l + 1]);
+        __syncthreads();
+    }
+    {
+        // coarsest: u = inv (f - mean f) (periodic) or inv f (Dirichlet)
+        const LV<T>& C = lv[S.L - 1];
+        const T* f = sf[S.L - 1];
+        double loc = 0.0;
+        for (int p = threadIdx.x; p < S.nc; p += blockDim.x) loc += (double)f[p];
+        const double tot = block_sum(loc, red);
+        __shared__ double mean;
+        if (threadIdx.x == 0) mean = C.zper ? tot / S.nc : 0.0;
+        __syncthreads();
+        const T mf = (T)mean;
+        // one warp per row of the inverse: coalesced loads, a warp reduction
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int p = threadIdx.x >> 5; p < S.nc; p += nw) {
+            const T* row = S.minv + (long)p * S.nc;
+            T acc = 0;
+            for (int q = lane; q < S.nc; q += 32) acc += row[q] * (f[q] - mf);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) su[S.L - 1][p] = acc;
+        }
+        __syncthreads();
+    }
+    for (int l = S.L - 2; l >= S.l0; --l) {
+        sm_prolong_add(lv[l], qd[l], su[l], lv[l + 1], su[l + 1]);
+        __syncthreads();
+        for (int it = 0; it < S.nu2; ++it) {
+            sm_rbgs(lv[l], qd[l], su[l], sf[l], 1);
+            __syncthreads();
+            sm_rbgs(lv[l], qd[l], su[l], sf[l], 0);
+            __syncthreads();
+        }
+    }
+    const LV<T>& G = S.lv[S.l0];
+    const int np = G.nx * G.ny * G.nz;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) S.u[S.l0][t] = su[S.l0][t];
+}
+
+template <typename T>
+size_t coarse_smem_bytes(const CoarseSet<T>& S) {
+    size_t b = 0;
+    for (int l = S.l0; l < S.L; ++l) {
+        const LV<T>& G = S.lv[l];
+        if (G.cell) return ~(size_t)0;                // the shared copy holds face coefficients only
+        b += (size_t)G.nx * G.ny * (G.nz + 2) * sizeof(T) * (l < S.L - 1 ? 6 : 5);
+    }
+    return b;
+}
+
 }  // namespace
 
+void coarse_vcycle_init() {
+    cudaFuncSetAttribute(k_coarse_vcycle_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemBytes);
+    cudaFuncSetAttribute(k_coarse_vcycle_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemBytes);
+}
+
 template <typename T> void launch_coarse_vcycle(const CoarseSet<T>& S, cudaStream_t s) {
-    k_coarse_vcycle<T><<<1, 1024, 0, s>>>(S);
+    const size_t b = coarse_smem_bytes(S);
+    if (b <= kCoarseSmemBytes) k_coarse_vcycle_smem<T><<<1, 1024, b, s>>>(S);
+    else k_coarse_vcycle<T><<<1, 1024, 0, s>>>(S);
 }
 template void launch_coarse_vcycle<float>(const CoarseSet<float>&, cudaStream_t);
 template void launch_coarse_vcycle<double>(const CoarseSet<double>&, cudaStream_t);
@@ -1276,6 +1548,14 @@ template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* 
     k_residual<T><<<row_blocks(rows), row_threads(L.nx), 0, s>>>(L, u, f, r);
 }
 template <typename T> void launch_restrict(const LV<T>& F, const T* r, const LV<T>& C, T* fc, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (F.nx % 4 == 0 && C.nx * 2 == F.nx && C.nx % 2 == 0 &&
+            ((reinterpret_cast<uintptr_t>(r) & 15) | (reinterpret_cast<uintptr_t>(fc) & 7)) == 0) {
+            const long pairs = (long)C.nx * C.ny * C.nz / 2;
+            k_restrict4<<<grid_for(pairs, 256), 256, 0, s>>>(F, r, C, fc);
+            return;
+        }
+    }
     const long rows = (long)C.ny * C.nz;
     k_restrict<T><<<row_blocks(rows), row_threads(C.nx), 0, s>>>(F, r, C, fc);
 }
