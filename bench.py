@@ -204,6 +204,8 @@ def gpu_arm(args, rank, world):
 
     def make_solver(precision, split):
         extra = {"kind": args.kind, "rcut": args.rcut_gamma, "zlim": zlim} if args.kind else {}
+        if args.nu_coarse is not None:
+            extra["nu_coarse"] = args.nu_coarse
         return P.GPSolver(w.grid, w.cell, precision=precision, split=split, levels=w.levels,
                           sweep_shape=args.sweep_shape, n_dirichlet=n_dir, **extra)
 
@@ -523,6 +525,8 @@ def main():
     ap.add_argument("--n-dirichlet", type=int, default=-1,
                     help="split: Dirichlet planes (-1: 0 = the whole dry run for --kind 2, else 1)")
     ap.add_argument("--rcut-gamma", type=float, default=9.0, help="cut-off of gamma for --kind 1 (Angstrom)")
+    ap.add_argument("--nu-coarse", type=int, default=None,
+                    help="smoothing sweeps on the levels below the finest (default: the library's)")
     ap.add_argument("--sweep-shape", type=int, default=-1,
                     help="finest-level smoother tile (-1: autotuned; fixed shapes keep profiles comparable)")
     args = ap.parse_args()

@@ -97,6 +97,8 @@ typedef struct {
                              not use r0 and w */
     double beta;          /* kinds 1, 2: the exponent beta of Eq. 10 (2.4) */
     double zlim;          /* kind 2: z_lim of Eq. 19, Angstrom inside the cell (0) */
+    int nu_coarse;        /* sweeps before and after the coarse correction on the levels below the
+                             finest; 0 = nu1, nu2 there too (0) */
 } gp_params;
 
 #define GP_HISTORY 64

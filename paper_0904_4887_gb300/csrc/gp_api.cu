@@ -424,6 +424,8 @@ void smooth_fine(gp_ctx* c, Hier<T>& H, T* u, const T* f, int nu, int first) {
 template <typename T>
 void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
     const int L = H.L;
+    const int nuc1 = c->prm.nu_coarse > 0 ? c->prm.nu_coarse : c->prm.nu1;   // levels below the finest
+    const int nuc2 = c->prm.nu_coarse > 0 ? c->prm.nu_coarse : c->prm.nu2;
     // first level small enough for the persistent single-CTA kernel (never the finest)
     int lc = L - 1;
     for (int l = 1; l < L; ++l) {
@@ -437,8 +439,8 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
         if (l == 0) {
             smooth_fine(c, H, u, f, c->prm.nu1, 0);
         } else {
-            ProfScope ps(c, GP_PROF_MG_COARSE, 2 * c->prm.nu1);
-            for (int it = 0; it < c->prm.nu1; ++it) {
+            ProfScope ps(c, GP_PROF_MG_COARSE, 2 * nuc1);
+            for (int it = 0; it < nuc1; ++it) {
                 launch_rbgs<T>(V, u, f, 0, c->s);
                 launch_rbgs<T>(V, u, f, 1, c->s);
             }
@@ -451,7 +453,7 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
         ProfScope ps(c, GP_PROF_MG_COARSE, 1);
         if (lc < L - 1) {
             CoarseSet<T> S;
-            S.l0 = lc; S.L = L; S.nc = H.nc; S.nu1 = c->prm.nu1; S.nu2 = c->prm.nu2; S.minv = H.minv;
+            S.l0 = lc; S.L = L; S.nc = H.nc; S.nu1 = nuc1; S.nu2 = nuc2; S.minv = H.minv;
             for (int l = 0; l < L; ++l) { S.lv[l] = H.lv[l]; S.u[l] = H.u[l]; S.f[l] = H.f[l]; S.r[l] = H.res[l]; }
             launch_coarse_vcycle<T>(S, c->s);
         } else {
@@ -470,8 +472,8 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
             smooth_fine(c, H, u, f, c->prm.nu2, 1);
             continue;
         }
-        ProfScope ps(c, GP_PROF_MG_COARSE, 2 * c->prm.nu2);
-        for (int it = 0; it < c->prm.nu2; ++it) {
+        ProfScope ps(c, GP_PROF_MG_COARSE, 2 * nuc2);
+        for (int it = 0; it < nuc2; ++it) {
             launch_rbgs<T>(V, u, f, 1, c->s);
             launch_rbgs<T>(V, u, f, 0, c->s);
         }
@@ -570,7 +572,7 @@ void pcg_body(gp_ctx* c, Hier<T>& H, int iters);
 // round trip) is one CUDA graph per hierarchy.
 template <typename T>
 void pcg(gp_ctx* c, Hier<T>& H, int iters) {
-    const long key = ((long)iters << 16) | ((long)c->prm.nu1 << 8) | (long)c->prm.nu2;
+    const long key = ((long)c->prm.nu_coarse << 32) | ((long)iters << 16) | ((long)c->prm.nu1 << 8) | (long)c->prm.nu2;
     run_graph(c, H.pcg_g, key, [&] { pcg_body(c, H, iters); });
 }
 
@@ -761,7 +763,8 @@ template <typename T>
 void split_precondition(gp_ctx* c, int j, const T* v, T* z) {
     Hier<T>& B = band_hier<T>(c);
     if ((int)B.prec_g.size() <= j) B.prec_g.resize(j + 1);
-    const long key = ((long)c->prm.band_vcycles << 16) | ((long)c->prm.nu1 << 8) | (long)c->prm.nu2;
+    const long key = ((long)c->prm.nu_coarse << 32) | ((long)c->prm.band_vcycles << 16) | ((long)c->prm.nu1 << 8) |
+                     (long)c->prm.nu2;
     run_graph(c, B.prec_g[j], key, [&] { split_precondition_body<T>(c, v, z); });
 }
 
@@ -949,8 +952,8 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
             F.solve_phi = phi;
             F.solve_rho = rho;
         }
-        const long key = ((long)use_df << 40) | ((long)k << 24) | ((long)c->prm.inner << 16) |
-                         ((long)c->prm.nu1 << 8) | c->prm.nu2;
+        const long key = ((long)c->prm.nu_coarse << 48) | ((long)use_df << 40) | ((long)k << 24) |
+                         ((long)c->prm.inner << 16) | ((long)c->prm.nu1 << 8) | c->prm.nu2;
         run_graph(c, F.solve_g, key, [&] {
             for (int it = 0; it < k; ++it) {
                 if (it > 0) update_full(F.x);
@@ -1084,6 +1087,7 @@ void gp_default_params(gp_params* p) {
     p->band_vcycles = 2;
     p->graph_outer = 0;
     p->sweep_shape = -1;
+    p->nu_coarse = 0;
     p->kind = 0;
     p->beta = 2.4;
     p->zlim = 0.0;
@@ -1146,6 +1150,7 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             throw Err{GP_ERR_INVALID_ARG, "restart must be in 1..15"};
         if (p.band_vcycles < 1) throw Err{GP_ERR_INVALID_ARG, "band_vcycles must be >= 1"};
         if (p.graph_outer < 0 || p.graph_outer > 16) throw Err{GP_ERR_INVALID_ARG, "graph_outer must be 0..16"};
+        if (p.nu_coarse < 0 || p.nu_coarse > 8) throw Err{GP_ERR_INVALID_ARG, "nu_coarse must be 0 .. 8"};
         if (p.sweep_shape < -1 || p.sweep_shape >= kSweepShapeCount)
             throw Err{GP_ERR_INVALID_ARG, "sweep_shape must be -1 (autotune) or a valid tile shape"};
         if (p.kind < 0 || p.kind > 2)
