@@ -676,6 +676,133 @@ __global__ void __launch_bounds__(kReduceThreads) k_apply4(LV<float> L, const fl
     }
 }
 
+// The same A p (with p.q) or f - A u on the finest level, marching in z: a CTA
+// owns whole x rows times kZmRows rows and a chunk of z-planes; each thread
+// holds four consecutive x points of one row (rows j0-1 and j0+kZmRows only
+// load), keeps its own column of p and eps for planes k-1 .. k+2 in registers
+// (loads issued two planes ahead) and passes plane k to its neighbours through
+// a double-buffered shared tile, one barrier per plane. Every value crosses
+// from L2 once (plus the two halo rows), where the 4-point kernel above loads
+// each one five times. DOT: one partial per CTA, the unused partial slots up to
+// kReduceBlocks are zeroed so the fixed-order sum stays the same length.
+constexpr int kZmRows = 8;
+
+template <bool DOT>
+__global__ void __launch_bounds__(1024) k_apply_zm(LV<float> L, const float* __restrict__ p,
+                                                   const float* __restrict__ f, float* __restrict__ q,
+                                                   double* partial, int sz) {
+    extern __shared__ __align__(16) float zsm[];
+    __shared__ double red[32];
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nx4 = nx >> 2;
+    const long pl = (long)nx * ny;
+    const int tid = threadIdx.x;
+    const int r = tid / nx4, x4 = tid - r * nx4;           // tile row r holds global row j0 - 1 + r
+    const bool active = r < kZmRows + 2;
+    const int j0 = blockIdx.x * kZmRows;
+    const int jr = j0 - 1 + r;
+    const int jw = jr < 0 ? jr + ny : (jr >= ny ? jr - ny : jr);
+    const bool inner = active && r >= 1 && r <= kZmRows && jr < ny;
+    const int z0 = blockIdx.y * sz, z1 = min(z0 + sz, nz);
+    const float hx = 0.5f * L.ihx2, hy = 0.5f * L.ihy2, hz = 0.5f * L.ihz2;
+    const int rowlen = nx, tile = (kZmRows + 2) * nx;
+    float* sp = zsm;                                      // [2][kZmRows+2][nx] of p
+    float* se = zsm + 2 * tile;                           // the same of eps
+    const long col = (long)jw * nx + 4 * x4;
+    auto off = [&](int k) -> long {                       // plane k (wrapped; -1 and nz are the walls)
+        if (L.zper) k = k < 0 ? k + nz : (k >= nz ? k - nz : k);
+        else if (k > nz) k = nz;                          // the prefetch past the last wall: never used
+        return (long)k * pl + col;
+    };
+    auto ld4 = [](const float* a, long o) { return *reinterpret_cast<const float4*>(a + o); };
+    float4 Pm = make_float4(0.f, 0.f, 0.f, 0.f), P0 = Pm, Pp = Pm, Pn = Pm;
+    float4 Em = Pm, E0 = Pm, Ep = Pm, En = Pm;
+    KSum<float> acc;
+    if (z0 < nz) {
+        if (active) {
+            Pm = ld4(p, off(z0 - 1)); Em = ld4(L.eps, off(z0 - 1));
+            P0 = ld4(p, off(z0)); E0 = ld4(L.eps, off(z0));
+            Pp = ld4(p, off(z0 + 1)); Ep = ld4(L.eps, off(z0 + 1));
+        }
+        const int xl = x4 == 0 ? nx - 1 : 4 * x4 - 1, xr = x4 == nx4 - 1 ? 0 : 4 * x4 + 4;
+        for (int k = z0; k < z1; ++k) {
+            const int b = (k - z0) & 1;
+            float* bp = sp + b * tile;
+            float* be = se + b * tile;
+            if (active) {
+                Pn = ld4(p, off(k + 2));                  // planes up to nz exist (wrapped or the wall)
+                En = ld4(L.eps, off(k + 2));
+                *reinterpret_cast<float4*>(bp + r * rowlen + 4 * x4) = P0;
+                *reinterpret_cast<float4*>(be + r * rowlen + 4 * x4) = E0;
+            }
+            __syncthreads();
+            if (inner) {
+                const float* pr = bp + r * rowlen;
+                const float* er = be + r * rowlen;
+                const float4 pym = *reinterpret_cast<const float4*>(pr - rowlen + 4 * x4);
+                const float4 pyp = *reinterpret_cast<const float4*>(pr + rowlen + 4 * x4);
+                const float4 eym = *reinterpret_cast<const float4*>(er - rowlen + 4 * x4);
+                const float4 eyp = *reinterpret_cast<const float4*>(er + rowlen + 4 * x4);
+                const float uu[6] = {pr[xl], P0.x, P0.y, P0.z, P0.w, pr[xr]};
+                const float ee[6] = {er[xl], E0.x, E0.y, E0.z, E0.w, er[xr]};
+                const float ym[4] = {pym.x, pym.y, pym.z, pym.w}, yp[4] = {pyp.x, pyp.y, pyp.z, pyp.w};
+                const float zm[4] = {Pm.x, Pm.y, Pm.z, Pm.w}, zp[4] = {Pp.x, Pp.y, Pp.z, Pp.w};
+                const float eym_[4] = {eym.x, eym.y, eym.z, eym.w}, eyp_[4] = {eyp.x, eyp.y, eyp.z, eyp.w};
+                const float ezm_[4] = {Em.x, Em.y, Em.z, Em.w}, ezp_[4] = {Ep.x, Ep.y, Ep.z, Ep.w};
+                float out[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const float e = ee[m + 1], u = uu[m + 1];
+                    out[m] = (e + ee[m + 2]) * hx * (uu[m + 2] - u) - (e + ee[m]) * hx * (u - uu[m]) +
+                             (e + eyp_[m]) * hy * (yp[m] - u) - (e + eym_[m]) * hy * (u - ym[m]) +
+                             (e + ezp_[m]) * hz * (zp[m] - u) - (e + ezm_[m]) * hz * (u - zm[m]);
+                }
+                const long o = (long)k * pl + col;
+                if constexpr (DOT) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) acc.add(uu[m + 1] * out[m]);
+                    *reinterpret_cast<float4*>(q + o) = make_float4(out[0], out[1], out[2], out[3]);
+                } else {
+                    const float4 fv = ld4(f, o);
+                    *reinterpret_cast<float4*>(q + o) =
+                        make_float4(fv.x - out[0], fv.y - out[1], fv.z - out[2], fv.w - out[3]);
+                }
+            }
+            Pm = P0; P0 = Pp; Pp = Pn;
+            Em = E0; E0 = Ep; Ep = En;
+        }
+    }
+    if constexpr (DOT) {
+        const double sdot = block_sum(acc.value(), red);
+        const int nb = gridDim.x * gridDim.y, bid = blockIdx.x + gridDim.x * blockIdx.y;
+        if (threadIdx.x == 0) partial[bid] = sdot;
+        if (bid == 0)
+            for (int i = nb + threadIdx.x; i < kReduceBlocks; i += blockDim.x) partial[i] = 0.0;
+    }
+}
+
+// grid of the z-marching apply: y tiles times z chunks, one wave of resident
+// CTAs and at most kReduceBlocks CTAs; false when the level does not fit it
+bool apply_zm_grid(const LV<float>& L, dim3& grid, int& sz, size_t& smem, int& threads) {
+    if (!L.cell || L.nx % 4 != 0) return false;
+    threads = (kZmRows + 2) * (L.nx / 4);
+    if (threads > 1024) return false;
+    threads = (threads + 31) / 32 * 32;
+    smem = sizeof(float) * 4 * (kZmRows + 2) * (size_t)L.nx;
+    if (smem > 48 * 1024) return false;                   // the default dynamic shared memory
+    const int ty = (L.ny + kZmRows - 1) / kZmRows;
+    int per_sm = 65536 / (64 * threads);                  // by registers (64 per thread)
+    if (per_sm > 2048 / threads) per_sm = 2048 / threads;
+    if (per_sm > 8) per_sm = 8;
+    if (per_sm < 1) per_sm = 1;
+    int tz = 152 * per_sm / ty;
+    if (tz > kReduceBlocks / ty) tz = kReduceBlocks / ty;
+    if (tz > L.nz) tz = L.nz;
+    if (tz < 1) return false;
+    sz = (L.nz + tz - 1) / tz;
+    grid = dim3(ty, (L.nz + sz - 1) / sz);
+    return (long)grid.x * grid.y <= kReduceBlocks;
+}
+
 // ------------------------------------------------------------ reductions
 // out[c] = sum_b partial[b * ncomp + c], in a fixed order
 __global__ void k_finalize(const double* partial, int nparts, int ncomp, double* out) {
@@ -1539,6 +1666,11 @@ template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int col
 }
 template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* f, T* r, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
+        dim3 grid; int sz, th; size_t sm;
+        if (apply_zm_grid(L, grid, sz, sm, th)) {
+            k_apply_zm<false><<<grid, th, sm, s>>>(L, u, f, r, nullptr, sz);
+            return;
+        }
         if (L.cell && L.nx % 4 == 0) {
             k_apply4<false><<<kReduceBlocks * 2, kReduceThreads, 0, s>>>(L, u, f, r, nullptr);
             return;
@@ -1595,6 +1727,11 @@ template <typename T> void launch_coarse_solve(const LV<T>& C, const T* inv, int
 }
 template <typename T> void launch_applyA_dot(const LV<T>& L, const T* p, T* q, double* partial, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
+        dim3 grid; int sz, th; size_t sm;
+        if (apply_zm_grid(L, grid, sz, sm, th)) {
+            k_apply_zm<true><<<grid, th, sm, s>>>(L, p, nullptr, q, partial, sz);
+            return;
+        }
         if (L.cell && L.nx % 4 == 0) {
             k_apply4<true><<<kReduceBlocks, kReduceThreads, 0, s>>>(L, p, nullptr, q, partial);
             return;
