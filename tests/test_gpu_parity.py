@@ -197,6 +197,26 @@ def test_mixed_df64_residual_path(small_cases, k, graph_outer):
     assert abs(E - E0) < 1e-8 * abs(E0)
 
 
+@pytest.mark.parametrize("nu_coarse", [1, 3])
+@pytest.mark.parametrize("split", [0, 1])
+def test_coarse_sweep_count_converges_to_oracle(small_cases, nu_coarse, split):
+    """Other sweep counts on the levels below the finest (nu_coarse; the shared-
+    memory bottom of the V-cycle and the band levels included) give the oracle's
+    solution; a count outside 0 .. 8 is refused."""
+    GPSolver = _gpu()
+    from paper_0904_4887_gb300 import GPError
+    (at, h, eps, rho), grid, cell = small_cases[0]
+    s = GPSolver(grid, cell, precision=1, split=split, nu_coarse=nu_coarse)
+    s.set_atoms(_t(at.pos))
+    phi = s.solve(_t(rho), tol=1e-12).cpu().numpy()
+    ref, _ = O.solve(rho, eps, h, tol=1e-14)
+    assert _rel(phi, ref) < 1e-8
+    assert s.stats().residual < 1e-12
+    with pytest.raises(GPError) as e:
+        GPSolver(grid, cell, precision=1, nu_coarse=9).set_atoms(_t(at.pos))
+    assert e.value.status == 1                      # GP_ERR_INVALID_ARG
+
+
 def test_split_band_matches_oracle_planner(small_cases):
     GPSolver = _gpu()
     (at, h, eps, rho), grid, cell = small_cases[0]
