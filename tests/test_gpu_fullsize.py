@@ -1,0 +1,189 @@
+"""GPU parity at the full sizes of the benchmark configurations.
+
+Each configuration runs as bench.py runs it (the same solver parameters, the
+smoother tile chosen by the autotuner), and is checked on what the FP64 oracle
+can evaluate at that size:
+  * eps and rho at seeded grid points (and at the grid point nearest each of
+    the first atoms), one by one; rho through differences between points,
+    since the solver removes the grid mean;
+  * the FP64 residual of the returned phi, measured with the oracle's own
+    operator on the returned eps and rho;
+  * both forms of Eq. 4 recomputed by the oracle, and their equality at
+    convergence;
+  * the forces of seeded atoms from the oracle's gradient (Eq. 11) on the
+    returned phi, and (adjoint configuration) central differences of E.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W
+from oracle import gp_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0904_4887_gb300 import GPSolver
+    return GPSolver
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _gauss(at):
+    return np.stack([at.Z, at.sigma_core, at.sigma_cloud], axis=1)
+
+
+def _sample(grid, cell, pos, m=1500, near=50, seed=0):
+    """Flat indices (z-major arrays) and coordinates of seeded grid points plus
+    the grid point nearest each of the first `near` atoms."""
+    nx, ny, nz = grid
+    h = O.spacing(grid, cell)
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, nx, m)
+    j = rng.integers(0, ny, m)
+    k = rng.integers(0, nz, m)
+    a = np.asarray(pos)[:near]
+    i = np.concatenate([i, np.rint(a[:, 0] / h[0]).astype(int) % nx])
+    j = np.concatenate([j, np.rint(a[:, 1] / h[1]).astype(int) % ny])
+    k = np.concatenate([k, np.rint(a[:, 2] / h[2]).astype(int) % nz])
+    flat = (k * ny + j) * nx + i
+    pts = np.stack([i * h[0], j * h[1], k * h[2]], axis=1)
+    return flat, pts
+
+
+def _check_fields(grid, cell, at, eps, rho):
+    flat, pts = _sample(grid, cell, at.pos)
+    e_or = O.dielectric_points(pts, cell, at.pos)
+    assert np.max(np.abs(eps.ravel()[flat] - e_or)) < 1e-13 * np.max(e_or)
+    r_or = O.charge_density_points(pts, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud)
+    d_gpu = rho.ravel()[flat] - rho.ravel()[flat[0]]
+    d_or = r_or - r_or[0]
+    assert np.max(np.abs(d_gpu - d_or)) < 1e-12 * np.max(np.abs(r_or))
+
+
+def _check_solution(grid, cell, phi, rho, eps, tol, reported, E, E2, identity):
+    h = O.spacing(grid, cell)
+    res = O.residual_norm(phi, rho, eps, h)
+    assert res <= 1.05 * tol, res
+    assert abs(res - reported) <= 1e-13 + 0.02 * res
+    Eo = O.energy(rho, phi, grid, cell)
+    assert abs(E - Eo) < 1e-12 * abs(Eo)
+    assert abs(E2 - O.field_energy(phi, eps, grid, cell)) < 1e-12 * abs(Eo)
+    assert abs(E - E2) < identity * abs(E)                    # Eq. 4 identity at convergence
+
+
+def _check_forces(grid, cell, at, phi, F, atoms, rel):
+    Ge, Gr = O.energy_gradient(phi, grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud, atoms=atoms)
+    Fo = -(Ge + Gr)[atoms]
+    err = np.max(np.abs(F[atoms] - Fo)) / np.max(np.abs(Fo))
+    assert err < rel, err
+
+
+def test_mixed_192x192x384_full_size():
+    """Mixed precision, 288 atoms, sigma ~ U[0.3, 1.0] A, solved to 1e-10."""
+    GPSolver = _gpu()
+    w = W.WORKLOADS["mixed_192x192x384"]
+    at = W.workload_atoms(w)
+    s = GPSolver(w.grid, w.cell, precision=1, split=0, levels=w.levels)
+    pos, gauss = _t(at.pos), _t(_gauss(at))
+    s.set_atoms(pos)
+    rho = s.build_rho(pos, gauss)
+    phi = s.solve(rho, tol=1e-10)
+    E, E2, F = s.energy_forces(phi, rho, gauss)
+    p, r, e = phi.cpu().numpy(), rho.cpu().numpy(), s.eps().cpu().numpy()
+    _check_fields(w.grid, w.cell, at, e, r)
+    _check_solution(w.grid, w.cell, p, r, e, 1e-10, s.stats().residual, E, E2, 1e-8)
+    _check_forces(w.grid, w.cell, at, p, F.cpu().numpy(), W.fd_atom_indices(len(at.Z), 3, seed=1), 1e-9)
+
+
+def test_split_96x96x192_full_size():
+    """FP64 dry/wet split with 5 levels, 72 atoms, coupled to 1e-10."""
+    GPSolver = _gpu()
+    w = W.WORKLOADS["split_96x96x192"]
+    at = W.workload_atoms(w)
+    s = GPSolver(w.grid, w.cell, precision=0, split=1, levels=w.levels)
+    pos, gauss = _t(at.pos), _t(_gauss(at))
+    s.set_atoms(pos)
+    rho = s.build_rho(pos, gauss)
+    phi = s.solve(rho, tol=1e-10)
+    assert s.stats().split_active == 1
+    E, E2, F = s.energy_forces(phi, rho, gauss)
+    p, r, e = phi.cpu().numpy(), rho.cpu().numpy(), s.eps().cpu().numpy()
+    _check_fields(w.grid, w.cell, at, e, r)
+    _check_solution(w.grid, w.cell, p, r, e, 1e-10, s.stats().residual, E, E2, 1e-8)
+    _check_forces(w.grid, w.cell, at, p, F.cpu().numpy(), W.fd_atom_indices(len(at.Z), 2, seed=2), 1e-9)
+
+
+def test_adjoint_64x64x128_full_size():
+    """FP64 energy through the autograd function: dE/dR against central
+    differences (h = 1e-4 A) on 6 seeded atoms, and dE/drho against a central
+    difference along a seeded neutral direction of rho."""
+    GPSolver = _gpu()
+    from paper_0904_4887_gb300 import poisson_energy
+    w = W.WORKLOADS["adjoint_64x64x128"]
+    at = W.workload_atoms(w)
+    s = GPSolver(w.grid, w.cell, precision=0, levels=w.levels)
+    gauss = _t(_gauss(at))
+
+    def energy(p):
+        pt = _t(p)
+        E, _ = poisson_energy(pt, s.build_rho(pt, gauss), s, tol=1e-13, gauss=gauss)
+        return float(E)
+
+    pos = _t(at.pos).requires_grad_(True)
+    rho = s.build_rho(pos.detach(), gauss).requires_grad_(True)
+    E, phi = poisson_energy(pos, rho, s, tol=1e-13, gauss=gauss)
+    E.backward()
+    # dE/drho along a seeded neutral direction: E is quadratic in rho, so the
+    # central difference equals the gradient up to the solve tolerance
+    delta = W.random_field(tuple(rho.shape), seed=5)
+    delta = _t(delta - delta.mean())
+    tstep = 1e-3 * float(rho.detach().abs().max()) / float(delta.abs().max())
+    Ep, _ = poisson_energy(pos.detach(), rho.detach() + tstep * delta, s, tol=1e-13, gauss=gauss)
+    Em, _ = poisson_energy(pos.detach(), rho.detach() - tstep * delta, s, tol=1e-13, gauss=gauss)
+    fd_rho = (float(Ep) - float(Em)) / (2 * tstep)
+    an_rho = float(torch.sum(rho.grad * delta))
+    assert abs(fd_rho - an_rho) < 1e-8 * abs(an_rho)
+    G = pos.grad.cpu().numpy()
+    idx = W.fd_atom_indices(len(at.Z), 6, seed=0)
+    d = 1e-4
+    fd = np.zeros((len(idx), 3))
+    for t, a in enumerate(idx):
+        for c in range(3):
+            pp = at.pos.copy(); pp[a, c] += d
+            pm = at.pos.copy(); pm[a, c] -= d
+            fd[t, c] = (energy(pp) - energy(pm)) / (2 * d)
+    err = np.max(np.abs(fd - G[idx])) / np.max(np.abs(fd))
+    assert err < 1e-6, err
+
+
+def test_md_128x128x256_frames_full_size():
+    """Warm-started, graph-captured mixed solves on consecutive MD frames (the
+    bench's MD mode: graph_outer 2, tol 1e-8), checked on the last frame."""
+    GPSolver = _gpu()
+    w = W.WORKLOADS["md_128x128x256"]
+    at = W.workload_atoms(w)
+    traj = W.md_frames(at, w.cell, 3, dt_fs=0.5, temperature=300.0, seed=0)
+    s = GPSolver(w.grid, w.cell, precision=1, levels=w.levels, graph_outer=2)
+    gauss = _t(_gauss(at))
+    phi = s.zeros()
+    for f in range(3):
+        pos = _t(traj[f])
+        s.set_atoms(pos)
+        rho = s.build_rho(pos, gauss)
+        s.solve(rho, phi, tol=1e-8)
+        assert s.stats().residual <= 1e-8
+    E, E2, F = s.energy_forces(phi, rho, gauss)
+    last = W.Atoms(**{**at.__dict__, "pos": traj[2]})
+    p, r, e = phi.cpu().numpy(), rho.cpu().numpy(), s.eps().cpu().numpy()
+    _check_fields(w.grid, w.cell, last, e, r)
+    _check_solution(w.grid, w.cell, p, r, e, 1e-8, s.stats().residual, E, E2, 1e-6)
+    _check_forces(w.grid, w.cell, last, p, F.cpu().numpy(), W.fd_atom_indices(len(at.Z), 2, seed=3), 1e-9)
