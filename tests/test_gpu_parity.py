@@ -177,6 +177,36 @@ def test_every_sweep_shape_converges_to_oracle(row_case, shape, split):
     assert s.stats().residual < 1e-12
 
 
+ROWLEN = {96: ((96, 24, 48), (15.0, 7.5, 12.0)), 128: ((128, 24, 48), (20.0, 7.5, 12.0)),
+          256: ((256, 32, 48), (40.0, 10.0, 12.0))}
+
+
+@pytest.fixture(scope="module")
+def rowlen_cases():
+    out = {}
+    for nx, (g, c) in ROWLEN.items():
+        at, h, eps, rho = _case(g, c, 2, 2, seed=3)
+        ref, _ = O.solve(rho, eps, h, tol=1e-14)
+        out[nx] = (at, rho, ref, g, c)
+    return out
+
+
+@pytest.mark.parametrize("nx", sorted(ROWLEN))
+@pytest.mark.parametrize("shape", range(4, 15))
+def test_row_tiles_on_other_row_lengths(rowlen_cases, nx, shape):
+    """The whole-row tiles (48, 64 and 128 pairs per row; 24 or 32 rows, so
+    the 14- and 12-row tiles are ragged), forced through sweep_shape, give the
+    oracle's solution; a tile that does not fit a row length resolves to shape 0."""
+    GPSolver = _gpu()
+    at, rho, ref, grid, cell = rowlen_cases[nx]
+    s = GPSolver(grid, cell, precision=1, sweep_shape=shape)
+    s.set_atoms(_t(at.pos))
+    assert s.stats().sweep_shape in (shape, 0)
+    phi = s.solve(_t(rho), tol=1e-12).cpu().numpy()
+    assert _rel(phi, ref) < 1e-8
+    assert s.stats().residual < 1e-12
+
+
 @pytest.mark.parametrize("k", range(len(SMALL)))
 @pytest.mark.parametrize("graph_outer", [0, 2])
 def test_mixed_df64_residual_path(small_cases, k, graph_outer):
