@@ -365,7 +365,7 @@ void coarse_coeffs(gp_ctx* c, Hier<T>& H) {
     const LV<T>& C = H.lv[levels - 1];
     if (levels == 1) throw Err{GP_ERR_INVALID_ARG, "multigrid needs at least two levels"};
     {
-        ProfScope ps(c, GP_PROF_SETUP, 1 + H.nc + 2);
+        ProfScope ps(c, GP_PROF_SETUP, 1 + gauss_jordan_launches(H.nc));
         launch_coarse_matrix<T>(C, c->gmat, c->s);
         launch_gauss_jordan(c->gmat, H.nc, c->dstatus, c->s);
     }

@@ -183,6 +183,7 @@ template <typename T> void launch_coarsen_faces(const LV<T>& F, int nxc, int nyc
                                                 T* cx, T* cy, T* cz, cudaStream_t s);
 template <typename T> void launch_coarse_matrix(const LV<T>& C, double* M, cudaStream_t s);
 int launch_gauss_jordan(double* M, int n, int* status, cudaStream_t s);   // returns the launch count
+int gauss_jordan_launches(int n);
 template <typename T> void launch_store_inverse(const double* M, int n, T* inv, cudaStream_t s);
 template <typename T> void launch_coarse_solve(const LV<T>& C, const T* inv, int n, const T* f, T* u,
                                                cudaStream_t s);

@@ -472,6 +472,43 @@ __global__ void k_gj_finish(double* M, int n) {
     for (int q = threadIdx.x; q < n; q += blockDim.x) W[(long)r * n + q] *= inv_d;
 }
 
+// The same elimination for a small coarsest grid in ONE CTA: [M | I] lives in
+// shared memory (n rows of 2n doubles), each column takes two phases (the
+// row factors, then the row updates) separated by the CTA barrier, and the
+// inverse goes to the second half of M's buffer as in the multi-CTA version.
+constexpr int kGjSmemMax = 110;          // 2 n^2 + n doubles within 200 KB of shared memory
+
+__global__ void __launch_bounds__(1024) k_gj_smem(double* M, int n, int* status) {
+    extern __shared__ double gja[];
+    double* A = gja;                      // [n][2n]
+    double* fac = gja + 2 * n * n;        // [n]
+    const int w = 2 * n, tid = threadIdx.x;
+    for (int e = tid; e < n * w; e += blockDim.x) {
+        const int r = e / w, q = e - r * w;
+        A[e] = q < n ? M[(long)r * n + q] : (q - n == r ? 1.0 : 0.0);
+    }
+    if (tid == 0) *status = 0;
+    __syncthreads();
+    for (int col = 0; col < n; ++col) {
+        const double piv = A[col * w + col];
+        const bool ok = fabs(piv) > 1e-300;
+        if (!ok && tid == 0) *status = 1;
+        for (int r = tid; r < n; r += blockDim.x) fac[r] = (ok && r != col) ? A[r * w + col] / piv : 0.0;
+        __syncthreads();
+        for (int e = tid; e < n * w; e += blockDim.x) {
+            const int r = e / w, q = e - r * w;
+            const double f = fac[r];
+            if (f != 0.0) A[e] -= f * A[col * w + q];
+        }
+        __syncthreads();
+    }
+    double* W = M + (long)n * n;
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        const int r = e / n, q = e - r * n;
+        W[e] = A[r * w + n + q] / A[r * w + r];
+    }
+}
+
 template <typename T>
 __global__ void k_store_inverse(const double* W, long nn, T* inv) {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x)
@@ -1553,7 +1590,11 @@ size_t coarse_smem_bytes(const CoarseSet<T>& S) {
 
 }  // namespace
 
+int gauss_jordan_launches(int n) { return n <= kGjSmemMax ? 1 : n + 2; }
+
 void coarse_vcycle_init() {
+    cudaFuncSetAttribute(k_gj_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(double) * (2 * kGjSmemMax * kGjSmemMax + kGjSmemMax)));
     cudaFuncSetAttribute(k_coarse_vcycle_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemBytes);
     cudaFuncSetAttribute(k_coarse_vcycle_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemBytes);
 }
@@ -1711,6 +1752,10 @@ template <typename T> void launch_coarse_matrix(const LV<T>& C, double* M, cudaS
     k_coarse_matrix<T><<<1, 512, 0, s>>>(C, M);
 }
 int launch_gauss_jordan(double* M, int n, int* status, cudaStream_t s) {
+    if (n <= kGjSmemMax) {
+        k_gj_smem<<<1, 1024, sizeof(double) * (2 * (size_t)n * n + n), s>>>(M, n, status);
+        return 1;
+    }
     const int th = n >= 256 ? 256 : 128;
     k_gj_init<<<n, th, 0, s>>>(M, n, status);
     for (int col = 0; col < n; ++col) k_gj_step<<<n, th, 0, s>>>(M, n, col, status);
