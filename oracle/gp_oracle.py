@@ -16,6 +16,8 @@ solid-liquid interfaces with a continuum solvent" (arXiv:0904.4887):
   * Sec. II.C, Scheme 1   dry/wet split: FFT on the whole box, multigrid on the
             wet sub-domain with Dirichlet values from the FFT solution,
             combined self-consistently (abstract; Sec. I)
+  * Sec. III, Eq. 16-18   the sixth-order non-conservative stencil, its solve
+            and the adjoint solve its forces need (the last section)
 
 Readings of points where the paper is silent (the dielectric form, the
 stencil, the charge model, the split's self-consistent loop) are listed in the
@@ -26,7 +28,9 @@ the flat index is i + nx*(j + ny*k): x fastest, z-planes contiguous.
 Units: Angstrom and elementary charge, Gaussian electrostatics (k = 1).
 
 Parity status: every function below is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_pins.py`` (closed forms, invariants, brute force).
+``tests/test_oracle_pins.py``, ``tests/test_oracle_helper_pins.py`` or
+``tests/test_oracle_stencil6_pins.py`` (closed forms, invariants, brute force,
+the paper's printed values under ``tests/golden/``).
 """
 from __future__ import annotations
 
@@ -737,3 +741,251 @@ def split_solve(rho, eps, h, band, tol=1e-13, maxit=200):
         if change < tol:
             break
     return combined - combined.mean(), hist
+
+
+# ----------------------------------------------------------------------------
+# the sixth-order non-conservative stencil (Sec. III, Eq. 16-18)
+# ----------------------------------------------------------------------------
+#
+# Eq. 16 expands Eq. 3 by the product rule, grad(eps).grad(phi) + eps lap(phi)
+# = -4 pi rho (the printed eps lap(eps) is read as eps lap(phi)), and Eq. 17-18
+# discretise each first and second derivative with seven points along its axis.
+# The resulting 19-point operator A6 annihilates constants but is neither
+# symmetric nor conservative: its left null vector is not the constant vector,
+# so a neutral rho is not exactly in its range on the periodic grid. The
+# reading used here adds the smallest correction that restores solvability in
+# the divided form lap(phi) + grad(ln eps).grad(phi) = -4 pi rho/eps, a uniform
+# shift there, i.e. mu * eps here:
+#
+#     A6 phi + mu eps = -4 pi rho,   sum(phi) = 0,
+#
+# whose mu vanishes with the truncation error (O(h^6) for smooth fields).
+
+# Eq. 17-18 as printed: alpha_{-n} = -alpha_n, beta_{-n} = beta_n, n = 0..3
+FD6_ALPHA = (0.0, 3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0)
+FD6_BETA = (-49.0 / 18.0, 27.0 / 18.0, -27.0 / 180.0, 2.0 / 180.0)
+
+
+def fd6_first(u, c, h):
+    """du/dx_c at every grid point, (1/h) sum_{n=-3..3} alpha_n u_{i+n} (Eq. 17),
+    periodic."""
+    ax = AX[c]
+    out = np.zeros_like(u)
+    for n in (1, 2, 3):
+        out += FD6_ALPHA[n] * (np.roll(u, -n, axis=ax) - np.roll(u, n, axis=ax))
+    return out / h[c]
+
+
+def fd6_second(u, c, h):
+    """d2u/dx_c^2 at every grid point, (1/h^2) sum_{n=-3..3} beta_n u_{i+n}
+    (Eq. 18), periodic."""
+    ax = AX[c]
+    out = FD6_BETA[0] * u
+    for n in (1, 2, 3):
+        out = out + FD6_BETA[n] * (np.roll(u, -n, axis=ax) + np.roll(u, n, axis=ax))
+    return out / (h[c] * h[c])
+
+
+def apply_A6(phi, eps, h):
+    """(A6 phi)_i = sum_axes [(D1 eps)_i (D1 phi)_i + eps_i (D2 phi)_i]: Eq. 16
+    with the derivatives of Eq. 17-18."""
+    out = np.zeros_like(phi)
+    for c in range(3):
+        out += fd6_first(eps, c, h) * fd6_first(phi, c, h) + eps * fd6_second(phi, c, h)
+    return out
+
+
+def apply_A6_transpose(lam, eps, h):
+    """A6^T lam. D1 is antisymmetric and D2 symmetric on the periodic grid, so
+    A6^T lam = sum_axes [-D1((D1 eps) lam) + D2(eps lam)]."""
+    out = np.zeros_like(lam)
+    for c in range(3):
+        out += -fd6_first(fd6_first(eps, c, h) * lam, c, h) + fd6_second(eps * lam, c, h)
+    return out
+
+
+def assemble_A6(eps, h):
+    """A6 as a scipy sparse matrix (same definition as apply_A6), flat x-fastest.
+    Row i, column i+n along axis c holds (D1 eps)_i alpha_n/h_c + eps_i beta_n/h_c^2."""
+    import scipy.sparse as sp
+    n = eps.size
+    idx = np.arange(n).reshape(eps.shape)
+    rows, cols, vals = [], [], []
+    diag = np.zeros(eps.shape)
+    for c in range(3):
+        ax = AX[c]
+        de = fd6_first(eps, c, h)
+        diag += eps * FD6_BETA[0] / (h[c] * h[c])
+        for m in (1, 2, 3):
+            for sgn in (1, -1):
+                coef = sgn * FD6_ALPHA[m] * de / h[c] + FD6_BETA[m] * eps / (h[c] * h[c])
+                rows.append(idx.ravel())
+                cols.append(np.roll(idx, -sgn * m, axis=ax).ravel())
+                vals.append(coef.ravel())
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    vals.append(diag.ravel())
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(n, n))
+
+
+def fd6_symbol(grid, h):
+    """Eigenvalues of sum_axes D2 (the eps = 1 case of A6) on the periodic grid,
+    sum_axes (beta_0 + 2 sum_n beta_n cos(n theta_a))/h_a^2, in numpy's rfftn
+    layout (nz, ny, nx//2+1)."""
+    nx, ny, nz = grid
+
+    def axis(N, hh, k):
+        t = 2.0 * np.pi * k / N
+        return (FD6_BETA[0] + 2.0 * sum(FD6_BETA[n] * np.cos(n * t) for n in (1, 2, 3))) / (hh * hh)
+
+    lx = axis(nx, h[0], np.arange(nx // 2 + 1))
+    ly = axis(ny, h[1], np.fft.fftfreq(ny) * ny)
+    lz = axis(nz, h[2], np.fft.fftfreq(nz) * nz)
+    return lz[:, None, None] + ly[None, :, None] + lx[None, None, :]
+
+
+def _fd6_lap_inverse(src, lam):
+    """Mean-zero solution of (sum_axes D2) u = src - mean(src) by FFT."""
+    s = np.fft.rfftn(src)
+    l = lam.copy()
+    l[0, 0, 0] = 1.0
+    s = s / l
+    s[0, 0, 0] = 0.0
+    return np.fft.irfftn(s, s=src.shape, axes=(0, 1, 2))
+
+
+def _bordered6(eps, h, rhs, transpose, tol, method):
+    """Solve the bordered system K [x; m] = [rhs; 0] with
+    K = [[A6, eps], [1^T, 0]] (or its transpose K^T = [[A6^T, 1], [eps^T, 0]]).
+
+    method "direct": sparse LU of K (small grids). method "gmres": restarted
+    GMRES on K, preconditioned by the exact inverse of the bordered system
+    with A6 replaced by diag(eps) D2 (D2 diag(eps) for the transpose), which
+    the FFT inverts. Returns (x, m, iterations, relative residual)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    shape = rhs.shape
+    n = rhs.size
+    if method is None:
+        method = "direct" if n <= 4096 else "gmres"
+    col_e = eps.ravel()[:, None]
+    nb = np.linalg.norm(rhs)
+
+    def K(v):
+        x = v[:n].reshape(shape)
+        m = v[n]
+        if transpose:
+            return np.concatenate([(apply_A6_transpose(x, eps, h) + m).ravel(), [float(np.sum(eps * x))]])
+        return np.concatenate([(apply_A6(x, eps, h) + m * eps).ravel(), [float(np.sum(x))]])
+
+    if method == "direct":
+        A = assemble_A6(eps, h)
+        ones = np.ones((n, 1))
+        if transpose:
+            Kmat = sp.bmat([[A.T, sp.csr_matrix(ones)], [sp.csr_matrix(col_e.T), None]])
+        else:
+            Kmat = sp.bmat([[A, sp.csr_matrix(col_e)], [sp.csr_matrix(ones.T), None]])
+        v = spl.spsolve(Kmat.tocsc(), np.concatenate([rhs.ravel(), [0.0]]))
+        iters = 1
+    else:
+        lam = fd6_symbol((shape[2], shape[1], shape[0]), h)
+        inv_e = 1.0 / eps
+
+        def P(v):
+            r = v[:n].reshape(shape)
+            s = v[n]
+            if transpose:
+                # A6^T ~ D2 diag(eps): m = mean(r), eps x = D2^-1 (r - m) + c, sum(eps x) = s
+                m = float(np.mean(r))
+                x = (_fd6_lap_inverse(r - m, lam) + s / n) * inv_e
+            else:
+                # A6 ~ diag(eps) D2: r/eps - m has mean zero, x = D2^-1 (r/eps - m) + s/n
+                q = r * inv_e
+                m = float(np.mean(q))
+                x = _fd6_lap_inverse(q - m, lam) + s / n
+            return np.concatenate([x.ravel(), [m]])
+
+        count = [0]
+        Kop = spl.LinearOperator((n + 1, n + 1), matvec=K)
+        Pop = spl.LinearOperator((n + 1, n + 1), matvec=P)
+        v, _ = spl.gmres(Kop, np.concatenate([rhs.ravel(), [0.0]]), rtol=tol, atol=0.0, restart=60,
+                         maxiter=50, M=Pop, callback=lambda _r: count.__setitem__(0, count[0] + 1),
+                         callback_type="pr_norm")
+        iters = count[0]
+    r = K(v)
+    r[:n] -= rhs.ravel()
+    res = float(np.linalg.norm(r) / nb) if nb > 0 else float(np.linalg.norm(r))
+    return v[:n].reshape(shape), float(v[n]), iters, res
+
+
+def solve6(rho, eps, h, tol=1e-13, method=None):
+    """phi, mu with A6 phi + mu eps = -4 pi rho and sum(phi) = 0 (Eq. 16-18 with
+    the compatibility shift described above). rho has its grid mean removed
+    first, as for the conservative operator. Returns (phi, mu, SolveInfo); the
+    info's residual is ||b - A6 phi - mu eps|| / ||b||."""
+    b = -FOUR_PI * (rho - rho.mean())
+    phi, mu, it, res = _bordered6(eps, h, b, False, tol, method)
+    return phi, mu, SolveInfo(it, res)
+
+
+def adjoint6(rho, eps, h, tol=1e-13, method=None):
+    """lam, nu with A6^T lam + nu = rho - mean(rho) and sum(eps lam) = 0: the
+    transposed bordered system, whose solution gives rho . dphi for any change
+    of the right side or of eps (Appendix B without the symmetry that makes
+    phi its own adjoint for the conservative operator)."""
+    lam, nu, it, res = _bordered6(eps, h, rho - rho.mean(), True, tol, method)
+    return lam, nu, SolveInfo(it, res)
+
+
+def residual6_norm(phi, mu, rho, eps, h):
+    """||b - A6 phi - mu eps||_2 / ||b||_2 with b = -4 pi (rho - mean(rho))."""
+    b = -FOUR_PI * (rho - rho.mean())
+    r = b - apply_A6(phi, eps, h) - mu * eps
+    return float(np.linalg.norm(r) / np.linalg.norm(b))
+
+
+def energy_gradient6(phi, mu, lam, grid, cell, pos, Z, sigma_core, sigma_cloud,
+                     p=DielectricParams(), atoms=None, rho_moves=True, rvdw=None):
+    """G_a = dE/dR_a for E = 1/2 h^3 rho.phi (Eq. 4) with phi from the sixth-order
+    system (solve6), given its adjoint lam (adjoint6).
+
+    Differentiating [A6 phi + mu eps = b, sum(phi) = 0] and using lam:
+      rho . dphi = lam . (db - (dA6) phi - mu d eps),  db = -4 pi d rho,
+    and A6 is linear in eps, so lam . (dA6) phi = sum_j d eps_j g_j with
+      g = sum_axes [-D1(lam D1 phi) + lam D2 phi].
+    Hence
+      G^eps_a = -h^3/2 sum_j (d eps_j/dR_a) (g_j + mu lam_j)
+      G^rho_a =  h^3/2 sum_j (phi_j - 4 pi lam_j) d rho_j/dR_a,
+    with rho = rho~ - mean(rho~). Returns (G_eps, G_rho), each (n_atoms, 3);
+    rows of atoms not in `atoms` are zero. `p` is DielectricParams (erf
+    product) or GammaParams (Eq. 9-10, with the radii `rvdw`).
+    """
+    h = spacing(grid, cell)
+    dv = cell_volume_element(grid, cell)
+    n = len(pos)
+    atoms = range(n) if atoms is None else atoms
+    gamma_form = isinstance(p, GammaParams)
+    if gamma_form:
+        G = dummy_density(grid, cell, pos, rvdw, p)
+    else:
+        P = dielectric_product(grid, cell, pos, p)
+    g = np.zeros_like(phi)
+    for c in range(3):
+        g += -fd6_first(lam * fd6_first(phi, c, h), c, h) + lam * fd6_second(phi, c, h)
+    weps = g + mu * lam
+    wrho = phi - FOUR_PI * lam
+    Ge = np.zeros((n, 3))
+    Gr = np.zeros((n, 3))
+    for a in atoms:
+        if gamma_form:
+            de = dielectric_gamma_gradient_atom(a, grid, cell, pos, rvdw, G, p)
+        else:
+            de = dielectric_gradient_atom(a, grid, cell, pos, P, p)
+        for comp in range(3):
+            Ge[a, comp] = -0.5 * dv * float(np.sum(de[comp] * weps))
+        if rho_moves:
+            dr = charge_density_gradient_atom(a, grid, cell, pos, Z, sigma_core, sigma_cloud)
+            for comp in range(3):
+                Gr[a, comp] = 0.5 * dv * float(np.sum(wrho * (dr[comp] - dr[comp].mean())))
+    return Ge, Gr

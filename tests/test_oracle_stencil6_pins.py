@@ -1,0 +1,296 @@
+"""Pins of the oracle's sixth-order stencil (Sec. III, Eq. 16-18) against facts
+that do not come from the oracle itself: the weights the paper prints
+(tests/golden/fd6_coefficients.txt), Taylor moment conditions in exact
+rational arithmetic, exactness on polynomials, plane-wave eigenvalues, brute
+force through a dense matrix assembled column by column, the paper's stated
+accuracy on a manufactured solution (tests/golden/fd6_accuracy.txt), and
+central differences of the energy for the adjoint-based forces."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import gp_oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _printed_weights():
+    """{name: [w_0, w_1, w_2, w_3]} as exact fractions, from the golden file."""
+    w = {"alpha": [None] * 4, "beta": [None] * 4}
+    for name, n, frac in _read_golden("fd6_coefficients.txt"):
+        num, den = frac.split("/")
+        w[name][int(n)] = Fraction(int(num), int(den))
+    return w
+
+
+def _full_stencil(w, odd):
+    """Weights for n = -3..3 from the printed n = 0..3 and the stated symmetry."""
+    return {n: (w[abs(n)] if n >= 0 or not odd else -w[abs(n)]) for n in range(-3, 4)}
+
+
+def test_oracle_weights_are_the_printed_ones():
+    w = _printed_weights()
+    assert O.FD6_ALPHA == tuple(float(v) for v in w["alpha"])
+    assert O.FD6_BETA == tuple(float(v) for v in w["beta"])
+
+
+def test_printed_weights_are_the_unique_sixth_order_central_weights():
+    """sum_n w_n n^k / k! must be 1 for the derivative's own order and 0 for the
+    other k = 0..6: seven conditions on seven weights with a nonsingular
+    Vandermonde matrix, so they fix the weights. The first moment that
+    survives (k = 7 for the first derivative, k = 8 for the second) gives the
+    leading truncation term, O(h^6) for both (the paper prints O(h^7))."""
+    w = _printed_weights()
+    a = _full_stencil(w["alpha"], odd=True)
+    b = _full_stencil(w["beta"], odd=False)
+    for k in range(7):
+        ma = sum(a[n] * Fraction(n) ** k for n in a) / math.factorial(k)
+        mb = sum(b[n] * Fraction(n) ** k for n in b) / math.factorial(k)
+        assert ma == (1 if k == 1 else 0), (k, ma)
+        assert mb == (1 if k == 2 else 0), (k, mb)
+    # beta's seventh moment vanishes by symmetry; alpha's seventh and beta's
+    # eighth do not: both schemes are sixth order, not seventh
+    assert sum(b[n] * Fraction(n) ** 7 for n in b) == 0
+    assert sum(a[n] * Fraction(n) ** 7 for n in a) != 0
+    assert sum(b[n] * Fraction(n) ** 8 for n in b) != 0
+
+
+@pytest.mark.parametrize("c", [0, 1, 2])
+def test_fd6_derivatives_are_exact_on_polynomials(c):
+    """Away from the periodic wrap, D1 reproduces d/dx of x^k exactly for
+    k <= 6 and D2 reproduces d2/dx2 for k <= 7; the next power is not exact.
+    Run along each axis in turn to catch a swapped axis or roll direction."""
+    N = 40
+    shape = [1, 1, 1]
+    shape[O.AX[c]] = N
+    hh = 0.37
+    h = [1.0, 1.0, 1.0]
+    h[c] = hh
+    x = ((np.arange(N) - N // 2) * hh).reshape(shape)
+    inner = [slice(None)] * 3
+    inner[O.AX[c]] = slice(3, N - 3)
+    inner = tuple(inner)
+    for k in range(0, 9):
+        u = x ** k
+        d1 = O.fd6_first(u, c, h)[inner]
+        d2 = O.fd6_second(u, c, h)[inner]
+        e1 = (k * x ** (k - 1) if k >= 1 else 0.0 * x)[inner]
+        e2 = (k * (k - 1) * x ** (k - 2) if k >= 2 else 0.0 * x)[inner]
+        s1 = 1e-12 * max(1.0, np.max(np.abs(u))) / hh
+        s2 = 1e-12 * max(1.0, np.max(np.abs(u))) / hh ** 2
+        err1 = np.max(np.abs(d1 - e1))
+        err2 = np.max(np.abs(d2 - e2))
+        if k <= 6:
+            assert err1 < s1, (k, err1)
+        else:
+            assert err1 > 1e3 * s1, (k, err1)
+        if k <= 7:
+            assert err2 < s2, (k, err2)
+        else:
+            assert err2 > 1e3 * s2, (k, err2)
+
+
+def test_fd6_plane_wave_eigenvalues_and_symbol():
+    """exp(i theta j) along an axis is an eigenfunction of D1 and D2 with
+    eigenvalues (2i/h) sum alpha_n sin(n theta) and (1/h^2)(beta_0 +
+    2 sum beta_n cos(n theta)); these approach i theta/h and -theta^2/h^2 with
+    errors of order theta^7 and theta^8. The oracle's rfft-layout symbol holds
+    the same values (with eps = 1, A6 is sum_axes D2)."""
+    grid = (16, 12, 20)
+    h = (0.3, 0.5, 0.4)
+    z, y, x = np.meshgrid(np.arange(grid[2]), np.arange(grid[1]), np.arange(grid[0]), indexing="ij")
+    jj = (x, y, z)
+    w = _printed_weights()
+    al = [float(v) for v in w["alpha"]]
+    be = [float(v) for v in w["beta"]]
+    lam = O.fd6_symbol(grid, h)
+    for c in range(3):
+        N = grid[c]
+        for m in range(0, N // 2 + 1):
+            th = 2 * np.pi * m / N
+            u = np.exp(1j * th * jj[c])
+            ev1 = 2j / h[c] * sum(al[n] * np.sin(n * th) for n in (1, 2, 3))
+            ev2 = (be[0] + 2 * sum(be[n] * np.cos(n * th) for n in (1, 2, 3))) / h[c] ** 2
+            assert np.max(np.abs(O.fd6_first(u, c, h) - ev1 * u)) < 1e-12 / h[c]
+            assert np.max(np.abs(O.fd6_second(u, c, h) - ev2 * u)) < 1e-11 / h[c] ** 2
+            for c2 in range(3):           # a wave along c is constant along the others
+                if c2 != c:
+                    assert np.max(np.abs(O.fd6_first(u, c2, h))) < 1e-12
+                    assert np.max(np.abs(O.fd6_second(u, c2, h))) < 1e-11
+            Av = O.apply_A6(u, np.ones(u.shape), h)
+            assert np.max(np.abs(Av - ev2 * u)) < 1e-11 / h[c] ** 2
+            idx = [0, 0, 0]
+            idx[O.AX[c]] = m if c == 0 else (m % N)
+            assert abs(lam[tuple(idx)] - ev2) < 1e-11 / h[c] ** 2
+            if 0 < th < 0.6:
+                assert abs(ev1.imag * h[c] - th) < 0.02 * th ** 7
+                assert abs(ev2 * h[c] ** 2 + th * th) < 0.01 * th ** 8
+
+
+def _dense_from_apply(fn, shape):
+    n = int(np.prod(shape))
+    M = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        M[:, j] = fn(e.reshape(shape)).ravel()
+    return M
+
+
+def test_A6_assembled_transposed_and_null_vector_by_brute_force():
+    rng = np.random.default_rng(11)
+    shape = (7, 8, 9)                 # at least 7 points per axis, so no offsets alias
+    h = (0.4, 0.55, 0.3)
+    eps = 1.0 + 6.0 * rng.random(shape)
+    A = _dense_from_apply(lambda v: O.apply_A6(v, eps, h), shape)
+    scale = np.max(np.abs(A))
+    assert np.max(np.abs(O.assemble_A6(eps, h).toarray() - A)) < 1e-13 * scale
+    At = _dense_from_apply(lambda v: O.apply_A6_transpose(v, eps, h), shape)
+    assert np.max(np.abs(At - A.T)) < 1e-13 * scale
+    assert np.max(np.abs(A @ np.ones(A.shape[1]))) < 1e-12 * scale          # constants
+    assert np.max(np.abs(A - A.T)) > 1e-3 * scale                           # not symmetric
+    assert np.max(np.abs(np.ones(A.shape[0]) @ A)) > 1e-3 * scale           # not conservative
+    # 19 points per row: the centre and three neighbours each way per axis
+    assert np.all(np.count_nonzero(np.abs(A) > 0, axis=1) == 19)
+    # a uniform eps gives c times the symmetric sixth-order Laplacian
+    A1 = _dense_from_apply(lambda v: O.apply_A6(v, 2.5 * np.ones(shape), h), shape)
+    assert np.max(np.abs(A1 - A1.T)) < 1e-13 * np.max(np.abs(A1))
+
+
+@pytest.mark.parametrize("method", ["direct", "gmres"])
+def test_solve6_is_the_bordered_system_solved_densely(method):
+    """The reading A6 phi + mu eps = b, sum(phi) = 0, solved with numpy's dense
+    LAPACK solve of the matrix assembled from apply_A6 column by column."""
+    rng = np.random.default_rng(12)
+    shape = (6, 5, 8)
+    h = (0.4, 0.5, 0.35)
+    eps = 1.0 + 8.0 * rng.random(shape)
+    rho = rng.standard_normal(shape)
+    A = _dense_from_apply(lambda v: O.apply_A6(v, eps, h), shape)
+    n = A.shape[0]
+    K = np.zeros((n + 1, n + 1))
+    K[:n, :n] = A
+    K[:n, n] = eps.ravel()
+    K[n, :n] = 1.0
+    b = -4 * np.pi * (rho - rho.mean())
+    x = np.linalg.solve(K, np.concatenate([b.ravel(), [0.0]]))
+    phi, mu, info = O.solve6(rho, eps, h, tol=1e-13, method=method)
+    assert np.max(np.abs(phi.ravel() - x[:n])) < 1e-10 * np.max(np.abs(x[:n]))
+    assert abs(mu - x[n]) < 1e-10 * max(abs(x[n]), 1e-3)
+    assert info.residual < 1e-12
+    assert abs(O.residual6_norm(phi, mu, rho, eps, h) - np.linalg.norm(b.ravel() - A @ phi.ravel() - mu * eps.ravel()) / np.linalg.norm(b)) < 1e-14
+    # adjoint: K^T [lam; nu] = [rho - mean; 0]
+    y = np.linalg.solve(K.T, np.concatenate([(rho - rho.mean()).ravel(), [0.0]]))
+    lam, nu, li = O.adjoint6(rho, eps, h, tol=1e-13, method=method)
+    assert np.max(np.abs(lam.ravel() - y[:n])) < 1e-10 * np.max(np.abs(y[:n]))
+    assert abs(nu - y[n]) < 1e-10 * max(abs(y[n]), 1e-3)
+
+
+def test_solve6_with_uniform_eps_is_the_fft_solution():
+    """eps = c: mu = 0 and phi = FFT solution of c sum_axes D2 phi = b with the
+    plane-wave eigenvalues (pinned above); the adjoint is -phi/(4 pi)."""
+    rng = np.random.default_rng(13)
+    shape = (20, 12, 16)
+    h = (0.3, 0.45, 0.35)
+    c = 3.7
+    rho = rng.standard_normal(shape)
+    rho -= rho.mean()
+    eps = np.full(shape, c)
+    phi, mu, info = O.solve6(rho, eps, h, tol=1e-13)
+    lam = O.fd6_symbol((shape[2], shape[1], shape[0]), h)
+    lam[0, 0, 0] = 1.0
+    s = np.fft.rfftn(-4 * np.pi * rho) / (c * lam)
+    s[0, 0, 0] = 0.0
+    ref = np.fft.irfftn(s, s=shape, axes=(0, 1, 2))
+    assert abs(mu) < 1e-13
+    assert np.max(np.abs(phi - ref)) < 1e-11 * np.max(np.abs(ref))
+    lad, _, _ = O.adjoint6(rho, eps, h, tol=1e-13)
+    assert np.max(np.abs(lad + phi / (4 * np.pi))) < 1e-11 * np.max(np.abs(lad))
+
+
+def _manufactured(N, L, a, b, beta):
+    """phi = exp(-a r^2), eps = 1 + beta exp(-b r^2), centred off the grid;
+    div(eps grad phi) analytically, so rho = -div/(4 pi)."""
+    hh = L / N
+    x = np.arange(N) * hh - (L / 2 + 0.37 * hh)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    r2 = X * X + Y * Y + Z * Z
+    ph = np.exp(-a * r2)
+    eb = np.exp(-b * r2)
+    eps = 1.0 + beta * eb
+    div = (-2 * b * beta * eb) * (-2 * a * ph) * r2 + eps * (4 * a * a * r2 - 6 * a) * ph
+    return ph, eps, -div / (4 * np.pi), (hh, hh, hh)
+
+
+def test_sixth_order_accuracy_stated_in_the_paper():
+    """On the printed mesh, with decay constants inside the printed range, the
+    relative error of phi is below the printed bound, and halving h divides it
+    by ~2^6. Reading: the printed test functions exp(-ar), exp(-br) have a
+    cusp at r = 0 (rho ~ 1/r) and eps -> 0 far away, where no finite-difference
+    scheme is sixth order; the smooth profiles exp(-a r^2) and 1 + beta exp(-b r^2)
+    stand in for them."""
+    g = {k: float(v) for k, v in _read_golden("fd6_accuracy.txt")}
+    a, b, beta, L = 0.9, 0.6, 20.0, 14.0
+    assert g["a_min"] < a < g["a_max"] and g["b_min"] < b < g["b_max"]
+    errs, mus = [], []
+    for N in (int(g["mesh"]) // 2, int(g["mesh"])):
+        ph, eps, rho, h = _manufactured(N, L, a, b, beta)
+        phi, mu, info = O.solve6(rho, eps, h, tol=1e-13)
+        assert info.residual < 1e-12
+        ref = ph - ph.mean()
+        errs.append(np.max(np.abs(phi - ref)) / np.max(np.abs(ph)))
+        mus.append(abs(mu))
+    assert errs[1] < g["max_relative_error"], errs
+    assert 2 ** 5.3 < errs[0] / errs[1] < 2 ** 6.5, errs
+    assert 2 ** 5.3 < mus[0] / mus[1] < 2 ** 6.7, mus     # the compatibility shift is truncation-sized
+
+
+@pytest.mark.parametrize("rho_moves", [False, True])
+def test_forces6_match_central_differences(rho_moves):
+    """dE/dR_a from the adjoint (energy_gradient6) against central differences of
+    E = 1/2 h^3 rho.phi with phi from solve6, for three atoms; rho frozen (eps
+    term only) or moving with its atoms (both terms)."""
+    grid, cell = (16, 16, 24), (8.0, 8.0, 12.0)
+    at = W.slab_atoms(cell, 2, 2, seed=1)
+    h = O.spacing(grid, cell)
+    pos = at.pos
+
+    def E_of(p):
+        eps = O.dielectric(grid, cell, p)
+        src = p if rho_moves else pos
+        rho = O.charge_density(grid, cell, src, at.Z, at.sigma_core, at.sigma_cloud)
+        phi, _, _ = O.solve6(rho, eps, h, tol=1e-14)
+        return O.energy(rho - rho.mean(), phi, grid, cell)
+
+    eps = O.dielectric(grid, cell, pos)
+    rho = O.charge_density(grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud)
+    phi, mu, _ = O.solve6(rho, eps, h, tol=1e-14)
+    lam, _, _ = O.adjoint6(rho, eps, h, tol=1e-14)
+    sel = [0, 3, 5]
+    Ge, Gr = O.energy_gradient6(phi, mu, lam, grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud,
+                                atoms=sel, rho_moves=rho_moves)
+    G = Ge + Gr
+    fd = np.zeros((len(sel), 3))
+    d = 1e-4
+    for t, a in enumerate(sel):
+        for c in range(3):
+            pp = pos.copy(); pp[a, c] += d
+            pm = pos.copy(); pm[a, c] -= d
+            fd[t, c] = (E_of(pp) - E_of(pm)) / (2 * d)
+    scale = np.max(np.abs(fd))
+    assert scale > 1e-3
+    assert np.max(np.abs(fd - G[sel])) < 2e-6 * scale
