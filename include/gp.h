@@ -184,6 +184,21 @@ gp_status gp_energy_forces(gp_ctx* ctx, const double* phi_dev, const double* rho
 gp_status gp_residual(gp_ctx* ctx, const double* rho_dev, const double* phi_dev,
                       double* r_dev, double* rel_host);
 
+/* Residual of the sixth-order operator of Sec. III (Eq. 16-18), in FP64:
+ *   r = b - A6 phi - mu eps,  b = -4 pi rho,
+ *   (A6 phi)_i = sum_axes (D1 eps)_i (D1 phi)_i + eps_i (D2 phi)_i,
+ * D1, D2 the seven-point central first and second derivatives of Eq. 17-18
+ * (weights 3/4, -3/20, 1/60 and -49/18, 3/2, -3/20, 1/90), periodic on all
+ * axes, with the cell eps of the last gp_set_dielectric. mu is the uniform
+ * shift (in the form divided by eps) that makes the periodic non-conservative
+ * system solvable: A6 phi + mu eps = b; pass 0 for the plain A6 residual.
+ * rho_dev, phi_dev, r_dev: grid-sized FP64 device arrays (x fastest), owned by
+ * the caller; r_dev must not alias the inputs. ||r||_2 / ||b||_2 goes to
+ * *rel_host (may be NULL). Errors: GP_ERR_INVALID_ARG (null array, mu not
+ * finite), GP_ERR_STATE (no dielectric yet), GP_ERR_CUDA. */
+gp_status gp_residual6(gp_ctx* ctx, const double* rho_dev, const double* phi_dev, double mu,
+                       double* r_dev, double* rel_host);
+
 /* Vacuum solve L phi = src with the 7-point Laplacian (eps = 1), by the
  * hand-written FFT (Eq. 15 with the symbol of the discrete operator); the
  * k = 0 mode is dropped so phi has mean zero. src_dev, phi_dev grid-sized

@@ -1413,6 +1413,32 @@ gp_status gp_residual(gp_ctx* c, const double* rho_dev, const double* phi_dev, d
     }
 }
 
+gp_status gp_residual6(gp_ctx* c, const double* rho_dev, const double* phi_dev, double mu, double* r_dev,
+                       double* rel_host) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!rho_dev || !phi_dev || !r_dev || !std::isfinite(mu)) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_residual6"};
+        count_launch(1);
+        launch_residual6(c->g, phi_dev, rho_dev, c->eps64, mu, r_dev, c->partial, c->s);
+        GP_CHECK_LAUNCH();
+        double s2[1];
+        sum_host(c, 1, s2);
+        if (rel_host) {
+            count_launch(1);
+            launch_rho_stats(c->n, rho_dev, c->partial, c->s);
+            GP_CHECK_LAUNCH();
+            double h3[3];
+            sum_host(c, 3, h3);
+            const double nb = 4.0 * kPi * std::sqrt(h3[2]);
+            *rel_host = nb > 0 ? std::sqrt(s2[0]) / nb : std::sqrt(s2[0]);
+        }
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
 gp_status gp_fft_poisson(gp_ctx* c, const double* src_dev, double* phi_dev) {
     if (!c) return GP_ERR_INVALID_ARG;
     try {

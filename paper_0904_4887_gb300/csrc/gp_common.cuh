@@ -158,6 +158,9 @@ void launch_sub_mean(long n, double* x, const double* sum_slot, double scale, cu
 template <typename T>
 void launch_residual64(const Geo& g, const double* phi, const double* rho, const double* eps64,
                        T* r_out, double* partial, cudaStream_t s);
+// sixth-order residual (k_fd6.cu): r = -4 pi rho - A6 phi - mu eps, partial[b] = sum r^2
+void launch_residual6(const Geo& g, const double* phi, const double* rho, const double* eps64, double mu,
+                      double* r_out, double* partial, cudaStream_t s);
 template <typename T>
 void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_band,
                        int band_first, int band_nz, cudaStream_t s);

@@ -57,6 +57,7 @@ _SIGNATURES = {
     "gp_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
     "gp_energy_forces": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "gp_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "gp_residual6": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double)]),
     "gp_fft_poisson": (ctypes.c_int, [_P, _P, _P]),
     "gp_get_eps": (ctypes.c_int, [_P, _P]),
     "gp_get_plane_max": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
@@ -222,6 +223,12 @@ class Context:
     def gp_residual(self, rho, phi, r):
         rel = ctypes.c_double()
         self._check(self._lib.gp_residual(self._h, _ptr(rho), _ptr(phi), _ptr(r), ctypes.byref(rel)))
+        return rel.value
+
+    def gp_residual6(self, rho, phi, mu, r):
+        rel = ctypes.c_double()
+        self._check(self._lib.gp_residual6(self._h, _ptr(rho), _ptr(phi), ctypes.c_double(mu), _ptr(r),
+                                           ctypes.byref(rel)))
         return rel.value
 
     def gp_fft_poisson(self, src, out):

@@ -71,6 +71,13 @@ class GPSolver:
         rel = self.ctx.gp_residual(rho, phi, r)
         return r, rel
 
+    def residual6(self, rho, phi, mu=0.0):
+        """b - A6 phi - mu eps with the sixth-order operator of Eq. 16-18, and its
+        norm relative to b = -4 pi rho."""
+        r = self.zeros()
+        rel = self.ctx.gp_residual6(rho, phi, mu, r)
+        return r, rel
+
     def fft_poisson(self, src):
         out = self.zeros()
         self.ctx.gp_fft_poisson(src.contiguous(), out)
