@@ -456,6 +456,92 @@ def md_arm(args, rank, world):
                            "max": float(lat.max())}}
 
 
+# ----------------------------------------------------------------------------- sixth-order residual
+# FP64 flops per point of k_residual6 (an FMA counts 2): per axis 8 + 8 for the
+# two first-derivative sums (phi, eps), 10 for the second-derivative sum, 3 to
+# combine them; 5 to weight the axes by 1/h^2; 1 + 1 + 2 for -4 pi rho, the
+# subtraction and mu eps; 2 for the r^2 partial sum
+FD6_FLOPS_PER_POINT = 3 * (8 + 8 + 10 + 3) + 5 + 4 + 2
+FD6_BYTES_PER_POINT = 32          # read phi, eps, rho (FP64), write r (FP64)
+FD6_CALLS_PER_STEP = 100
+
+
+def residual6_arm(args, rank, world):
+    """Time gp_residual6 (the sixth-order residual of Eq. 16-18, FP64) on the
+    workload's dielectric and a solved phi: a step is 100 residual evaluations,
+    each the kernel, the finalisation of its partial sums and the 8-byte
+    readback of the sum of squares (no norm of b).
+    Reported against the nominal FP64 rate (the kernel is FP64-ALU bound) with
+    the HBM rate of its algorithmic bytes beside it."""
+    import torch
+    import paper_0904_4887_gb300 as P
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.WORKLOADS[args.workload]
+    at, traj, gauss_np = make_inputs(w, 1, seed=rank)
+    s = P.GPSolver(w.grid, w.cell, precision=args.precision, levels=w.levels)
+    pos = torch.tensor(traj[0], dtype=torch.float64, device=dev)
+    gauss = torch.tensor(gauss_np, dtype=torch.float64, device=dev)
+    s.set_atoms(pos)
+    rho = s.build_rho(pos, gauss)
+    phi = s.solve(rho, tol=1e-8)
+    r = s.zeros()
+    import ctypes
+    from paper_0904_4887_gb300 import gp as G
+
+    def call():
+        # rel_host NULL: the kernel, the finalisation of its partial sums and the readback
+        st = s.ctx._lib.gp_residual6(s.ctx._h, G._ptr(rho), G._ptr(phi), ctypes.c_double(0.0), G._ptr(r), None)
+        if st != 0:
+            raise RuntimeError("gp_residual6 failed with status %d" % st)
+
+    for _ in range(args.warmup):
+        call()
+    stream = torch.cuda.current_stream()
+    n = int(np.prod(w.grid))
+    clocks = ClockSampler(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = G.gp_launch_count()
+    e0.record(stream)
+    for _ in range(args.steps * FD6_CALLS_PER_STEP):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = G.gp_launch_count() - launches0
+    total = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    if rank != 0:
+        return None
+    per_call_s = total / 1e3 / (args.steps * FD6_CALLS_PER_STEP)
+    gflops = FD6_FLOPS_PER_POINT * n / per_call_s / 1e9
+    gbs = FD6_BYTES_PER_POINT * n / per_call_s / 1e9
+    hbm, hbm_src = load_peaks()
+    return {"metric": "sixth-order FP64 residual evaluations/s (Eq. 16-18)",
+            "value": job_throughput(args.steps * FD6_CALLS_PER_STEP, world, total / 1e3),
+            "unit": "residuals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.grid), "atoms": int(len(at.Z)),
+                       "calls_per_step": FD6_CALLS_PER_STEP,
+                       "l2": "inputs larger than L2 (4 FP64 fields of %d MB)" % (8 * n // 10 ** 6)},
+            "roofline": {"bound": "alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                         "frac": gflops / FP64_PEAK_GFLOPS, "peak_source": "nominal FP64 (non-tensor)",
+                         "kernel": "k_residual6", "flops_per_point": FD6_FLOPS_PER_POINT,
+                         "avg_call_ms": per_call_s * 1e3, "traffic": None},
+            "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "peak_source": hbm_src,
+                    "bytes_per_point": FD6_BYTES_PER_POINT},
+            "gpu_launches": int(launches),
+            "clocks": clk}
+
+
 # ----------------------------------------------------------------------------- oracle (CPU) arm
 def oracle_sample(w, at, pos, budget_s=20.0):
     """Time the FP64 oracle on bounded samples of the workload and scale to one
@@ -534,7 +620,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "md"])
+    ap.add_argument("--mode", default="step", choices=["step", "md", "residual6"])
     ap.add_argument("--frames", type=int, default=100)
     ap.add_argument("--graph-outer", type=int, default=2)
     ap.add_argument("--kind", type=int, default=0, choices=[0, 1, 2],
@@ -562,6 +648,8 @@ def main():
         line = reference_arm(args, rank, world)
     elif args.mode == "md":
         line = md_arm(args, rank, world)
+    elif args.mode == "residual6":
+        line = residual6_arm(args, rank, world)
     else:
         line = gpu_arm(args, rank, world)
     if line is not None:
