@@ -72,7 +72,8 @@ typedef struct {
                              tol >= 1e-10 the outer residual runs in df64, FP32 hi/lo pairs, whose
                              floor is ~1e-11 of ||b||; in FP64 below that) */
     int nu1, nu2;         /* red-black Gauss-Seidel sweeps before / after the coarse correction (2, 2) */
-    int levels;           /* multigrid levels; 0 = coarsen until the coarsest grid has <= 512 points */
+    int levels;           /* multigrid levels; 0 = automatic (gp_plan_levels: coarsest grid <= 64
+                             points where the grid allows, else <= 512) */
     int inner;            /* multigrid-preconditioned CG iterations per outer FP64 correction */
     int max_outer;        /* outer FP64 corrections before GP_ERR_NOT_CONVERGED */
     int accel;            /* split: 1 = each FP64 outer correction is solved by flexible GMRES in the
@@ -221,9 +222,13 @@ gp_status gp_get_plane_max(gp_ctx* ctx, double* plane_max_host);
 int gp_plan_band(const int* dry, int nz, int levels, int n_dirichlet, int* first, int* nd);
 
 /* Host-only: multigrid levels for a grid (zper = 1 periodic z with nz planes,
- * 0 Dirichlet z with nz interior planes): `requested` if the grid coarsens that
- * far with <= 512 coarsest points, else (requested = 0) the fewest levels >= 2
- * reaching <= 512 points. Returns -1 if impossible. Needs no GPU. */
+ * 0 Dirichlet z with nz interior planes). Each coarsening halves nx, ny and the
+ * periodic nz (the Dirichlet nz interior planes become (nz+1)/2 - 1) and needs
+ * every extent to divide evenly and stay >= 2 (a Dirichlet nz >= 1).
+ * requested > 0: `requested` if the grid coarsens requested-1 times with <= 512
+ * coarsest points, else -1. requested = 0: the fewest levels (>= 2) whose
+ * coarsest grid has <= 64 points, else the most levels whose coarsest grid has
+ * <= 512 points, else -1. Needs no GPU. */
 int gp_plan_levels(int nx, int ny, int nz, int zper, int requested);
 
 /* Largest nz accepted by gp_residual_noalloc: its scratch holds two partial

@@ -57,3 +57,57 @@ def test_level_planner():
     assert G.gp_plan_levels(8, 8, 8) == 2
     assert G.gp_plan_levels(192, 192, 383, 0) == 7    # Dirichlet band: (383+1)/64 - 1 = 5 planes
     assert G.gp_plan_levels(96, 96, 192, 1, 9) == -1
+
+
+def _levels_rule(nx, ny, nz, zper, requested):
+    """The documented level rule, restated: coarse extents at depth l, then the
+    requested count or the automatic choice (<= 64 points, else <= 512)."""
+    def coarse(l):
+        m = 2 ** l
+        if nx % m or ny % m:
+            return None
+        cx, cy = nx // m, ny // m
+        if zper:
+            if nz % m:
+                return None
+            cz = nz // m
+            if cz < 2:
+                return None
+        else:
+            if (nz + 1) % m:
+                return None
+            cz = (nz + 1) // m - 1
+            if cz < 1:
+                return None
+        if cx < 2 or cy < 2:
+            return None
+        return cx * cy * cz
+    if requested > 0:
+        pts = coarse(requested - 1) if requested <= 16 else None
+        return requested if pts is not None and pts <= 512 else -1
+    depths = []
+    for l in range(1, 16):
+        pts = coarse(l)
+        if pts is None:
+            break
+        depths.append((l, pts))
+    for l, pts in depths:
+        if pts <= 64:
+            return l + 1
+    ok = [l for l, pts in depths if pts <= 512]
+    return max(ok) + 1 if ok else -1
+
+
+def test_level_planner_matches_the_documented_rule():
+    ext = [8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
+    dir_nz = [7, 11, 15, 23, 31, 47, 63, 95, 127, 191, 255, 383, 9, 13]
+    cases = 0
+    for nx in ext:
+        for ny in ext[::2]:
+            for zper, zs in ((1, ext), (0, dir_nz)):
+                for nz in zs:
+                    for req in (0, 1, 2, 3, 5, 7, 9, 17):
+                        got = G.gp_plan_levels(nx, ny, nz, zper, req)
+                        assert got == _levels_rule(nx, ny, nz, zper, req), (nx, ny, nz, zper, req, got)
+                        cases += 1
+    assert cases > 2000
