@@ -138,7 +138,12 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
  * the per-level multigrid coefficients, the dry-plane flags and the wet band
  * (Sec. II.B: the erf switching product, params->kind 0, Eq. 9-10, kind 1,
  * or Eq. 19, kind 2; Sec. II.C for the band). Must precede gp_solve and gp_energy_forces; call again whenever the
- * atoms move. `params` is copied. Errors: GP_ERR_INVALID_ARG, GP_ERR_CUDA. */
+ * atoms move. `params` is copied. Errors: GP_ERR_INVALID_ARG (null params,
+ * n_atoms < 0, null atoms with n_atoms > 0, any parameter out of the range
+ * stated beside it, rcut larger than the cell, a grid or `levels` that does not
+ * coarsen; gp_last_error names which), GP_ERR_STATE (kind 1 or 2 without
+ * gp_set_vdw_radii for the same n_atoms), GP_ERR_OOM (the multigrid
+ * hierarchy is allocated here), GP_ERR_CUDA. */
 gp_status gp_set_dielectric(gp_ctx* ctx, const double* atoms_dev, int n_atoms,
                             const gp_params* params);
 
@@ -152,8 +157,9 @@ gp_status gp_set_vdw_radii(gp_ctx* ctx, const double* radii_dev, int n_atoms);
  * g the normalised Gaussian of standard deviation sigma, each truncated to
  * |dx|,|dy|,|dz| < 8 sigma and summed over periodic images (the Gaussian
  * ionic densities of Sec. II.A). Writes rho_dev (grid-sized). Independent of
- * gp_set_dielectric. Errors: GP_ERR_INVALID_ARG (a 8 sigma window wider than
- * the cell), GP_ERR_CUDA. */
+ * gp_set_dielectric; n_atoms = 0 gives rho = 0. Errors: GP_ERR_INVALID_ARG
+ * (null rho_dev, n_atoms < 0, null atom arrays with n_atoms > 0, a sigma <= 0
+ * or an 8 sigma window wider than the cell), GP_ERR_OOM, GP_ERR_CUDA. */
 gp_status gp_build_rho(gp_ctx* ctx, const double* atoms_dev, const double* gauss_dev,
                        int n_atoms, double* rho_dev);
 
@@ -161,9 +167,12 @@ gp_status gp_build_rho(gp_ctx* ctx, const double* atoms_dev, const double* gauss
  * arithmetic face means) to ||b - A phi||_2 <= tol ||b||_2, b = -4 pi rho.
  * phi_dev is read as the starting guess (warm start) and overwritten with the
  * solution, returned with mean zero. rho must be neutral (its caller removes
- * the mean). Errors: GP_ERR_STATE (no dielectric), GP_ERR_NOT_NEUTRAL,
- * GP_ERR_NOT_CONVERGED / GP_ERR_DIVERGED (phi holds the last iterate and
- * gp_get_stats the residuals), GP_ERR_INVALID_ARG (tol <= 0), GP_ERR_CUDA. */
+ * the mean). Errors: GP_ERR_INVALID_ARG (null array, tol <= 0), GP_ERR_STATE
+ * (no dielectric), GP_ERR_NOT_NEUTRAL, GP_ERR_NOT_CONVERGED / GP_ERR_DIVERGED
+ * (phi holds the last iterate and gp_get_stats the residuals), GP_ERR_TIMEOUT
+ * (a bounded wait of the finest-level smoother gave up; phi is not valid, the
+ * context stays usable), GP_ERR_OOM (workspaces are allocated on first use),
+ * GP_ERR_CUDA. */
 gp_status gp_solve(gp_ctx* ctx, const double* rho_dev, double* phi_dev, double tol);
 
 /* Energy and forces for the atoms of the last gp_set_dielectric, given the
@@ -175,13 +184,16 @@ gp_status gp_solve(gp_ctx* ctx, const double* rho_dev, double* phi_dev, double t
  * G_rho_a = h^3 sum_i phi_i d rho_i / d R_a (Eq. 11, Appendix B). gauss_dev
  * (as in gp_build_rho) may be NULL, then G_rho is omitted (rho held fixed).
  * Because the operator is symmetric, phi is its own adjoint: no extra solve.
- * energy_host may be NULL. Errors: GP_ERR_STATE, GP_ERR_CUDA. */
+ * energy_host may be NULL. Errors: GP_ERR_INVALID_ARG (null phi_dev or
+ * rho_dev), GP_ERR_STATE (no dielectric), GP_ERR_OOM, GP_ERR_CUDA. */
 gp_status gp_energy_forces(gp_ctx* ctx, const double* phi_dev, const double* rho_dev,
                            const double* gauss_dev, double* energy_host, double* forces_dev);
 
 /* Residual r = b - A phi (b = -4 pi rho) in FP64 into r_dev (grid-sized,
- * device), and ||r||_2 / ||b||_2 into *rel_host (may be NULL). Uses the eps of
- * the last gp_set_dielectric. Errors: GP_ERR_STATE, GP_ERR_CUDA. */
+ * device; must not alias rho_dev or phi_dev), and ||r||_2 / ||b||_2 into
+ * *rel_host (may be NULL). Uses the eps of the last gp_set_dielectric.
+ * Errors: GP_ERR_INVALID_ARG (null array), GP_ERR_STATE (no dielectric),
+ * GP_ERR_CUDA. */
 gp_status gp_residual(gp_ctx* ctx, const double* rho_dev, const double* phi_dev,
                       double* r_dev, double* rel_host);
 
@@ -203,13 +215,17 @@ gp_status gp_residual6(gp_ctx* ctx, const double* rho_dev, const double* phi_dev
 /* Vacuum solve L phi = src with the 7-point Laplacian (eps = 1), by the
  * hand-written FFT (Eq. 15 with the symbol of the discrete operator); the
  * k = 0 mode is dropped so phi has mean zero. src_dev, phi_dev grid-sized
- * device arrays (may alias). Errors: GP_ERR_CUDA. */
+ * device arrays (may alias). The plan and its workspace are made on the first
+ * call. Errors: GP_ERR_INVALID_ARG (null array, or an extent the FFT cannot
+ * plan), GP_ERR_OOM, GP_ERR_CUDA. */
 gp_status gp_fft_poisson(gp_ctx* ctx, const double* src_dev, double* phi_dev);
 
-/* Copy eps (FP64, grid-sized) of the last gp_set_dielectric into eps_dev. */
+/* Copy eps (FP64, grid-sized) of the last gp_set_dielectric into eps_dev.
+ * Errors: GP_ERR_INVALID_ARG (null), GP_ERR_STATE (no dielectric), GP_ERR_CUDA. */
 gp_status gp_get_eps(gp_ctx* ctx, double* eps_dev);
 
-/* Per-plane max_xy(eps - 1) into plane_max_host[nz] (host memory). */
+/* Per-plane max_xy(eps - 1) into plane_max_host[nz] (host memory).
+ * Errors: GP_ERR_INVALID_ARG (null), GP_ERR_STATE (no dielectric), GP_ERR_CUDA. */
 gp_status gp_get_plane_max(gp_ctx* ctx, double* plane_max_host);
 
 /* Host-only planner of the wet band (Sec. II.C reading): from per-plane dry
