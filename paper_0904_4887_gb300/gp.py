@@ -123,6 +123,8 @@ def gp_residual_noalloc(grid, cell, eps, rho, phi, r, rel, stream=None):
     """Allocation-free FP64 residual (no context); rel is a 1-element device tensor."""
     import torch
     st = torch.cuda.current_stream() if stream is None else stream
+    # no size checks here: this wrapper passes its arguments through unchanged so
+    # that the C function's own argument checks stay reachable
     return load().gp_residual_noalloc(gp_grid(*grid), gp_cell(*cell), _ptr(eps), _ptr(rho), _ptr(phi), _ptr(r),
                                       _ptr(rel), ctypes.c_void_p(st.cuda_stream))
 
@@ -143,15 +145,27 @@ def default_params(**overrides) -> gp_params:
     return p
 
 
-def _ptr(t):
+def _ptr(t, numel=None, what="array"):
+    """Device pointer of a contiguous float64 CUDA tensor (None passes through).
+    The C ABI takes bare pointers and cannot see sizes, so `numel`, when given,
+    is checked first: a short array would let the kernels write past its end."""
     if t is None:
         return None
     import torch
     if not isinstance(t, torch.Tensor):
         raise TypeError("expected a torch tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s: expected %d float64 values, got %d" % (what, numel, t.numel()))
     if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
         raise TypeError("expected a contiguous float64 CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _atoms_count(t, what):
+    """n for an (n, 3) array of atoms."""
+    if t.dim() != 2 or t.shape[1] != 3:
+        raise ValueError("%s: expected shape (n, 3), got %s" % (what, tuple(t.shape)))
+    return int(t.shape[0])
 
 
 class Context:
@@ -175,6 +189,8 @@ class Context:
             raise GPError(st, "gp_create failed (grid extents must be 2^a 3^b, >= 8, nx even)")
         self._h = h
         self.params = None
+        self._npts = self.grid[0] * self.grid[1] * self.grid[2]
+        self._n_atoms = None          # atoms of the last gp_set_dielectric
 
     # -- plumbing
     def _check(self, st):
@@ -199,43 +215,57 @@ class Context:
         return (nz, ny, nx)
 
     # -- the C calls
+    def _field(self, t, what):
+        return _ptr(t, self._npts, what)
+
     def gp_set_dielectric(self, atoms, params: gp_params):
+        n = _atoms_count(atoms, "atoms")
+        p = _ptr(atoms, 3 * n, "atoms")
         self.params = params
-        return self._check(self._lib.gp_set_dielectric(self._h, _ptr(atoms), int(atoms.shape[0]),
-                                                       ctypes.byref(params)))
+        st = self._check(self._lib.gp_set_dielectric(self._h, p, n, ctypes.byref(params)))
+        self._n_atoms = n
+        return st
 
     def gp_set_vdw_radii(self, radii):
-        return self._check(self._lib.gp_set_vdw_radii(self._h, _ptr(radii), int(radii.shape[0])))
+        if radii.dim() != 1:
+            raise ValueError("radii: expected shape (n,), got %s" % (tuple(radii.shape),))
+        n = int(radii.shape[0])
+        return self._check(self._lib.gp_set_vdw_radii(self._h, _ptr(radii, n, "radii"), n))
 
     def gp_build_rho(self, atoms, gauss, rho):
-        return self._check(self._lib.gp_build_rho(self._h, _ptr(atoms), _ptr(gauss), int(atoms.shape[0]),
-                                                  _ptr(rho)))
+        n = _atoms_count(atoms, "atoms")
+        return self._check(self._lib.gp_build_rho(self._h, _ptr(atoms, 3 * n, "atoms"), _ptr(gauss, 3 * n, "gauss"),
+                                                  n, self._field(rho, "rho")))
 
     def gp_solve(self, rho, phi, tol, check=True):
-        st = self._lib.gp_solve(self._h, _ptr(rho), _ptr(phi), ctypes.c_double(tol))
+        st = self._lib.gp_solve(self._h, self._field(rho, "rho"), self._field(phi, "phi"), ctypes.c_double(tol))
         return self._check(st) if check else st
 
     def gp_energy_forces(self, phi, rho, gauss=None, forces=None):
+        # gauss and forces belong to the atoms of the last gp_set_dielectric
+        na = None if self._n_atoms is None else 3 * self._n_atoms
         e = (ctypes.c_double * 2)()
-        self._check(self._lib.gp_energy_forces(self._h, _ptr(phi), _ptr(rho), _ptr(gauss), e, _ptr(forces)))
+        self._check(self._lib.gp_energy_forces(self._h, self._field(phi, "phi"), self._field(rho, "rho"),
+                                               _ptr(gauss, na, "gauss"), e, _ptr(forces, na, "forces")))
         return e[0], e[1]
 
     def gp_residual(self, rho, phi, r):
         rel = ctypes.c_double()
-        self._check(self._lib.gp_residual(self._h, _ptr(rho), _ptr(phi), _ptr(r), ctypes.byref(rel)))
+        self._check(self._lib.gp_residual(self._h, self._field(rho, "rho"), self._field(phi, "phi"),
+                                          self._field(r, "r"), ctypes.byref(rel)))
         return rel.value
 
     def gp_residual6(self, rho, phi, mu, r):
         rel = ctypes.c_double()
-        self._check(self._lib.gp_residual6(self._h, _ptr(rho), _ptr(phi), ctypes.c_double(mu), _ptr(r),
-                                           ctypes.byref(rel)))
+        self._check(self._lib.gp_residual6(self._h, self._field(rho, "rho"), self._field(phi, "phi"),
+                                           ctypes.c_double(mu), self._field(r, "r"), ctypes.byref(rel)))
         return rel.value
 
     def gp_fft_poisson(self, src, out):
-        return self._check(self._lib.gp_fft_poisson(self._h, _ptr(src), _ptr(out)))
+        return self._check(self._lib.gp_fft_poisson(self._h, self._field(src, "src"), self._field(out, "out")))
 
     def gp_get_eps(self, out):
-        return self._check(self._lib.gp_get_eps(self._h, _ptr(out)))
+        return self._check(self._lib.gp_get_eps(self._h, self._field(out, "out")))
 
     def gp_get_plane_max(self):
         import numpy as np

@@ -111,3 +111,44 @@ def test_level_planner_matches_the_documented_rule():
                         assert got == _levels_rule(nx, ny, nz, zper, req), (nx, ny, nz, zper, req, got)
                         cases += 1
     assert cases > 2000
+
+
+def test_binding_checks_array_sizes_before_any_device_call():
+    """The C ABI takes bare pointers, so the binding checks every array's size
+    against the grid (or the atom count) first: a wrong size raises ValueError
+    before the CUDA check; a right size gets as far as the CUDA check (no GPU
+    here)."""
+    import torch
+    class NoLib:                                  # every C function fails if it is ever reached
+        def __getattr__(self, name):
+            def reached(*args):
+                raise AssertionError("%s reached the library" % name)
+            return reached
+
+    ctx = G.Context.__new__(G.Context)          # no gp_create: nothing reaches the library
+    ctx.grid, ctx._npts, ctx._n_atoms, ctx._h = (8, 8, 16), 8 * 8 * 16, 5, None
+    ctx._lib = NoLib()
+    good = torch.zeros((16, 8, 8), dtype=torch.float64)
+    short = torch.zeros((16, 8, 7), dtype=torch.float64)
+    # on the CPU every right-sized tensor stops at the CUDA check, so each call
+    # varies the first array it checks
+    calls = [lambda a: ctx.gp_solve(a, good, 1e-8), lambda a: ctx.gp_residual(a, good, good),
+             lambda a: ctx.gp_residual6(a, good, 0.0, good), lambda a: ctx.gp_fft_poisson(a, good),
+             lambda a: ctx.gp_get_eps(a), lambda a: ctx.gp_energy_forces(a, good)]
+    for call in calls:
+        with pytest.raises(ValueError):
+            call(short)
+        with pytest.raises(TypeError):          # size fine: stops at "not a CUDA tensor"
+            call(good)
+    atoms5 = torch.zeros((5, 3), dtype=torch.float64)
+    with pytest.raises(TypeError):
+        ctx.gp_build_rho(atoms5, atoms5, good)
+    for bad in (torch.zeros(15, dtype=torch.float64), torch.zeros((5, 2), dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            ctx.gp_set_dielectric(bad, G.gp_params())           # not (n, 3)
+        with pytest.raises(ValueError):
+            ctx.gp_build_rho(bad, atoms5, good)
+    with pytest.raises(ValueError):
+        ctx.gp_set_vdw_radii(torch.zeros((5, 1), dtype=torch.float64))
+    with pytest.raises(ValueError):
+        G._ptr(torch.zeros(7, dtype=torch.float64), 8, "x")
