@@ -89,6 +89,7 @@ T* alloc_level(Hier<T>& H, int nx, int ny, int nz) {
 template <typename T>
 void free_hier(Hier<T>& H) {
     clear_slot(H.pcg_g);
+    clear_slot(H.solve_g);
     for (GraphSlot& g : H.prec_g) clear_slot(g);
     for (void* p : H.allocs) cudaFree(p);
     H = Hier<T>();
