@@ -143,7 +143,9 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
  * stated beside it, rcut larger than the cell, a grid or `levels` that does not
  * coarsen; gp_last_error names which), GP_ERR_STATE (kind 1 or 2 without
  * gp_set_vdw_radii for the same n_atoms), GP_ERR_OOM (the multigrid
- * hierarchy is allocated here), GP_ERR_CUDA. */
+ * hierarchy is allocated here), GP_ERR_CUDA. Argument errors leave the
+ * previous dielectric in place; a failure after the checks leaves the context
+ * without one until a later call succeeds. */
 gp_status gp_set_dielectric(gp_ctx* ctx, const double* atoms_dev, int n_atoms,
                             const gp_params* params);
 

@@ -1163,14 +1163,19 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         std::string why;
         const int L = plan_levels(c->g.nx, c->g.ny, c->g.nz, 1, p.levels, why);
         if (L < 2) throw Err{GP_ERR_INVALID_ARG, why.empty() ? "grid too small for multigrid" : why};
+        // from here on the context changes: a failure below leaves no dielectric
+        // (GP_ERR_STATE for the calls that need one) rather than a half-built one
+        c->have_eps = false;
         c->prm = p;
         c->full_levels = L;
         if (n_atoms > c->atoms_cap) {
             void* a = nullptr;
             void* b = nullptr;
-            if (cudaMalloc(&a, sizeof(double) * 3 * n_atoms) != cudaSuccess ||
-                cudaMalloc(&b, sizeof(float4) * n_atoms) != cudaSuccess)
+            if (cudaMalloc(&a, sizeof(double) * 3 * n_atoms) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+            if (cudaMalloc(&b, sizeof(float4) * n_atoms) != cudaSuccess) {
+                cudaFree(a);
                 throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+            }
             if (c->atoms) cudaFree(c->atoms);
             if (c->atoms32) cudaFree(c->atoms32);
             c->atoms = (double*)a;
