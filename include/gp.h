@@ -28,6 +28,12 @@
  *     stated otherwise.
  *   - Every call returns a gp_status; on failure gp_last_error() describes
  *     it. A CUDA error leaves the context unusable (GP_ERR_CUDA).
+ *   - Environment, read by gp_create: GP_NO_GRAPHS=1 runs every launch
+ *     sequence directly instead of through captured CUDA graphs (same
+ *     results, more host work); GP_TEST_SWEEP_WAIT_POLLS=n sets the poll
+ *     budget of the finest-level smoother's bounded waits for every context
+ *     of the process (a test hook: 0 makes them expire, so gp_solve returns
+ *     GP_ERR_TIMEOUT).
  */
 #ifndef GP_GB300_H
 #define GP_GB300_H
