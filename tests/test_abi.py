@@ -152,3 +152,37 @@ def test_binding_checks_array_sizes_before_any_device_call():
         ctx.gp_set_vdw_radii(torch.zeros((5, 1), dtype=torch.float64))
     with pytest.raises(ValueError):
         G._ptr(torch.zeros(7, dtype=torch.float64), 8, "x")
+
+
+def test_host_argument_checks_return_before_any_device_work():
+    """Calls whose arguments are rejected on the host return their status
+    without touching CUDA, so they behave the same on a machine without a GPU:
+    bad extents or cell for gp_create, and every context call given a NULL
+    context."""
+    import ctypes
+    lib = G.load()
+    INVALID = 1                                             # GP_ERR_INVALID_ARG
+    h = ctypes.c_void_p(123)
+    for grid, cell in (((10, 16, 16), (8.0, 8.0, 8.0)),     # 10 is not 2^a 3^b
+                       ((4, 16, 16), (8.0, 8.0, 8.0)),      # below 8
+                       ((24, 16, 18), (8.0, 8.0, 8.0)),     # 18 = 2 * 9
+                       ((16, 16, 16), (8.0, 0.0, 8.0))):    # non-positive side
+        assert lib.gp_create(G.gp_grid(*grid), G.gp_cell(*cell), None, ctypes.byref(h)) == INVALID
+        assert h.value is None                              # *out is cleared
+    assert lib.gp_create(G.gp_grid(16, 16, 16), G.gp_cell(8.0, 8.0, 8.0), None, None) == INVALID
+    p = G.gp_params()
+    lib.gp_default_params(ctypes.byref(p))
+    assert lib.gp_set_dielectric(None, None, 0, ctypes.byref(p)) == INVALID
+    assert lib.gp_set_vdw_radii(None, None, 0) == INVALID
+    assert lib.gp_build_rho(None, None, None, 0, None) == INVALID
+    assert lib.gp_solve(None, None, None, ctypes.c_double(1e-8)) == INVALID
+    assert lib.gp_energy_forces(None, None, None, None, None, None) == INVALID
+    assert lib.gp_residual(None, None, None, None, None) == INVALID
+    assert lib.gp_residual6(None, None, None, ctypes.c_double(0.0), None, None) == INVALID
+    assert lib.gp_fft_poisson(None, None, None) == INVALID
+    assert lib.gp_get_eps(None, None) == INVALID
+    assert lib.gp_get_plane_max(None, None) == INVALID
+    assert lib.gp_get_stats(None, None) == INVALID
+    assert lib.gp_profile(None, 1) == INVALID
+    assert lib.gp_last_error(None) == b"null context"
+    lib.gp_destroy(None)                                    # a no-op
