@@ -65,10 +65,13 @@ GAUSS_CUT_SIGMAS = 8.0   # Gaussian window half-width in sigmas: exp(-32) ~ 1e-1
 
 
 def spacing(grid, cell):
+    """Grid spacing h = L/N per axis of the real-space mesh (Sec. III)."""
     return tuple(float(cell[a]) / int(grid[a]) for a in range(3))
 
 
 def cell_volume_element(grid, cell):
+    """h_x h_y h_z: the volume element of the grid sums that stand for the
+    integrals of Eq. 4 and Eq. 11."""
     hx, hy, hz = spacing(grid, cell)
     return hx * hy * hz
 
@@ -103,16 +106,20 @@ def _image_boxes(center, grid, cell, radius):
 # ----------------------------------------------------------------------------
 
 def switching(d, p: DielectricParams):
+    """s(d) = (1 + erf((d - r0)/w))/2: one atom's factor in the erf-product
+    dielectric, the reading used for the position-dependent eps of Sec. II.B."""
     return 0.5 * (1.0 + erf((d - p.r0) / p.w))
 
 
 def switching_derivative(d, p: DielectricParams):
-    """ds/dd = exp(-((d - r0)/w)^2) / (w sqrt(pi))."""
+    """ds/dd = exp(-((d - r0)/w)^2) / (w sqrt(pi)), the factor d eps/d R of
+    Eq. 11 needs for the erf-product dielectric."""
     return np.exp(-((d - p.r0) / p.w) ** 2) / (p.w * math.sqrt(math.pi))
 
 
 def dielectric_product(grid, cell, pos, p: DielectricParams = DielectricParams()):
-    """P = prod over atoms and images within rcut of s(d); eps = 1 + (eps0-1) P."""
+    """P = prod over atoms and images within rcut of s(d); eps = 1 + (eps0-1) P
+    (Sec. II.B, erf-product reading)."""
     P = np.ones((grid[2], grid[1], grid[0]))
     for R in pos:
         for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, p.rcut):
@@ -128,7 +135,8 @@ def dielectric(grid, cell, pos, p: DielectricParams = DielectricParams()):
 
 
 def dielectric_points(points, cell, pos, p: DielectricParams = DielectricParams()):
-    """eps at arbitrary points (M, 3), one by one over atoms and all 27 images."""
+    """eps at arbitrary points (M, 3), one by one over atoms and all 27 images
+    (Sec. II.B, erf-product reading)."""
     points = np.asarray(points, dtype=np.float64)
     cell = np.asarray(cell, dtype=np.float64)
     P = np.ones(len(points))
@@ -140,7 +148,8 @@ def dielectric_points(points, cell, pos, p: DielectricParams = DielectricParams(
 
 
 def dielectric_gradient_atom(a, grid, cell, pos, P, p: DielectricParams = DielectricParams()):
-    """d eps_i / d R_a on the grid, as three arrays (x, y, z components).
+    """d eps_i / d R_a on the grid, as three arrays (x, y, z components): the
+    derivative inside the solvent term of Eq. 11 (Appendix B).
 
     Product rule over the factors that belong to atom a (one per image within
     rcut): d eps/dR_a = (eps0-1) sum_images [P / s(d)] s'(d) dd/dR_a, with
@@ -184,7 +193,9 @@ TAPER = 1.0   # width of the cut-off taper of Eq. 9 terms, Angstrom
 
 
 def taper(d, rcut):
-    """(T, dT/dd): 1 below rcut - TAPER, 0 beyond rcut, 1 - 10u^3 + 15u^4 - 6u^5 between."""
+    """(T, dT/dd): 1 below rcut - TAPER, 0 beyond rcut, 1 - 10u^3 + 15u^4 - 6u^5
+    between. The smooth cut-off applied to each term of the Eq. 9 sum (a
+    reading: the paper sums over all atoms)."""
     u = np.clip((d - (rcut - TAPER)) / TAPER, 0.0, 1.0)
     T = 1.0 - u ** 3 * (10.0 - 15.0 * u + 6.0 * u * u)
     dT = -30.0 * u * u * (1.0 - u) ** 2 / TAPER
@@ -267,10 +278,13 @@ def dielectric_gamma_gradient_atom(a, grid, cell, pos, rvdw, gamma, p: GammaPara
 # with eps = 1 and d eps/d gamma = 0. Atoms with z_I > z_lim, and lower atoms at
 # points with z >= z_I, contribute as in Eq. 9 (images within rcut).
 def sat_exponent(p):
+    """Growing exponent of Eq. 19 beyond which eps - 1 = (eps0-1)/(1+gamma^(2 beta))
+    is below 1e-16 (exp(-37) of eps0 - 1), so that eps is taken as exactly 1."""
     return (math.log(p.eps0 - 1.0) + 37.0) / (2.0 * p.beta)
 
 
 def _min_image(dv, L):
+    """The periodic image of a displacement closest to zero (used by Eq. 19)."""
     return dv - L * np.round(dv / L)
 
 
@@ -342,6 +356,7 @@ def dielectric_eq19_gradient_atom(a, grid, cell, pos, rvdw, zlim, gamma, sat, p:
 
 
 def _grid_coords(grid, cell):
+    """Coordinates r_ijk = (i h_x, j h_y, k h_z) as broadcastable arrays."""
     h = spacing(grid, cell)
     x = (np.arange(grid[0]) * h[0])[None, None, :]
     y = (np.arange(grid[1]) * h[1])[None, :, None]
@@ -354,7 +369,8 @@ def _grid_coords(grid, cell):
 # ----------------------------------------------------------------------------
 
 def gaussian(d2, sigma):
-    """Normalised 3D Gaussian of standard deviation sigma at squared distance d2."""
+    """Normalised 3D Gaussian of standard deviation sigma at squared distance d2
+    (the Gaussian ionic charges of Sec. II.A)."""
     return np.exp(-d2 / (2.0 * sigma * sigma)) / (2.0 * math.pi * sigma * sigma) ** 1.5
 
 
@@ -367,7 +383,7 @@ def _in_window(dx, dy, dz, rad):
 
 def charge_density_raw(grid, cell, pos, Z, sigma_core, sigma_cloud, cut=GAUSS_CUT_SIGMAS):
     """rho~_i = sum_a Z_a [g(d; sigma_core,a) - g(d; sigma_cloud,a)] over periodic
-    images, each Gaussian truncated to its window (_in_window)."""
+    images, each Gaussian truncated to its window (_in_window); Sec. II.A."""
     rho = np.zeros((grid[2], grid[1], grid[0]))
     for a, R in enumerate(pos):
         for sign, sig in ((1.0, sigma_core[a]), (-1.0, sigma_cloud[a])):
@@ -379,13 +395,14 @@ def charge_density_raw(grid, cell, pos, Z, sigma_core, sigma_cloud, cut=GAUSS_CU
 
 
 def charge_density(grid, cell, pos, Z, sigma_core, sigma_cloud, cut=GAUSS_CUT_SIGMAS):
-    """Neutral rho: the raw Gaussian sum minus its grid mean (discrete neutrality)."""
+    """Neutral rho: the raw Gaussian sum minus its grid mean (discrete neutrality
+    of the periodic Eq. 3)."""
     raw = charge_density_raw(grid, cell, pos, Z, sigma_core, sigma_cloud, cut)
     return raw - raw.mean()
 
 
 def charge_density_points(points, cell, pos, Z, sigma_core, sigma_cloud, cut=GAUSS_CUT_SIGMAS):
-    """rho~ (before mean removal) at arbitrary points, one by one."""
+    """rho~ (before mean removal) at arbitrary points, one by one (Sec. II.A)."""
     points = np.asarray(points, dtype=np.float64)
     cell = np.asarray(cell, dtype=np.float64)
     out = np.zeros(len(points))
@@ -402,7 +419,8 @@ def charge_density_points(points, cell, pos, Z, sigma_core, sigma_cloud, cut=GAU
 
 def charge_density_gradient_atom(a, grid, cell, pos, Z, sigma_core, sigma_cloud,
                                  cut=GAUSS_CUT_SIGMAS):
-    """d rho~_i / d R_a (x, y, z arrays): d g/dR = g (r - R)/sigma^2."""
+    """d rho~_i / d R_a (x, y, z arrays): d g/dR = g (r - R)/sigma^2; the charge
+    term of Eq. 11."""
     out = [np.zeros((grid[2], grid[1], grid[0])) for _ in range(3)]
     for sign, sig in ((1.0, sigma_core[a]), (-1.0, sigma_cloud[a])):
         rad = cut * sig
@@ -420,7 +438,8 @@ def charge_density_gradient_atom(a, grid, cell, pos, Z, sigma_core, sigma_cloud,
 # ----------------------------------------------------------------------------
 
 def face_mean(eps, axis):
-    """eps on the face between i and i+1 along `axis`: the arithmetic mean."""
+    """eps on the face between i and i+1 along `axis`: the arithmetic mean (the
+    face coefficient of the conservative discretisation of Eq. 3)."""
     return 0.5 * (eps + np.roll(eps, -1, axis=axis))
 
 
@@ -445,12 +464,14 @@ def apply_L(phi, h):
 
 def polarisation_term(phi, eps, h):
     """div((eps-1) grad phi) on the grid: the charge 4 pi rho_pol that the
-    dielectric adds to the vacuum problem, so that A phi = L phi + this."""
+    dielectric adds to the vacuum problem, so that A phi = L phi + this
+    (the coupling of Sec. II.C, Scheme 1)."""
     return apply_A(phi, eps - 1.0, h)
 
 
 def laplacian_symbol(grid, h):
-    """Eigenvalues of the 7-point Laplacian on the periodic grid,
+    """Eigenvalues of the 7-point Laplacian on the periodic grid (the divisor of
+    the FFT solve of Eq. 15 in its discrete form),
     lambda(k) = sum_axes (2 cos(2 pi k_a / N_a) - 2)/h_a^2, as an (nz, ny, nx//2+1)
     array matching numpy's rfftn layout."""
     nx, ny, nz = grid
@@ -484,12 +505,13 @@ def vacuum_potential(rho, h):
 
 @dataclasses.dataclass
 class SolveInfo:
+    """Iterations and final relative residual of a solve of Eq. 3 (or Eq. 16)."""
     iterations: int
     residual: float      # ||b - A phi|| / ||b|| of the returned phi
 
 
 def residual_norm(phi, rho, eps, h):
-    """||b - A phi||_2 / ||b||_2 with b = -4 pi rho, all in FP64."""
+    """||b - A phi||_2 / ||b||_2 with b = -4 pi rho, all in FP64 (Eq. 3)."""
     b = -FOUR_PI * rho
     r = b - apply_A(phi, eps, h)
     nb = np.linalg.norm(b)
@@ -497,7 +519,7 @@ def residual_norm(phi, rho, eps, h):
 
 
 def solve(rho, eps, h, tol=1e-14, maxiter=3000, phi0=None):
-    """phi with A phi = -4 pi rho and mean(phi) = 0.
+    """phi with A phi = -4 pi rho and mean(phi) = 0 (Eq. 3).
 
     Conjugate gradients on -A (symmetric, positive definite on mean-zero
     vectors), preconditioned by the inverse vacuum Laplacian (the FFT solve).
@@ -563,8 +585,8 @@ def field_energy(phi, eps, grid, cell):
 
 
 def variational_energy(rho, phi, eps, grid, cell):
-    """J(phi) = h^3 rho.phi + h^3/(8 pi) phi.A phi; equals E at the solution,
-    with an error quadratic in the error of phi."""
+    """J(phi) = h^3 rho.phi + h^3/(8 pi) phi.A phi; equals E of Eq. 4 at the
+    solution, with an error quadratic in the error of phi."""
     h = spacing(grid, cell)
     dv = cell_volume_element(grid, cell)
     return dv * float(np.sum(rho * phi)) + dv / (8.0 * math.pi) * float(np.sum(phi * apply_A(phi, eps, h)))
@@ -626,13 +648,14 @@ def energy_gradient(phi, grid, cell, pos, Z, sigma_core, sigma_cloud,
 # ----------------------------------------------------------------------------
 
 def dry_planes(eps, thresh=1e-3):
-    """z-planes on which eps - 1 < thresh everywhere ("dry": eps is 1 there)."""
+    """z-planes on which eps - 1 < thresh everywhere ("dry": eps is 1 there;
+    Sec. II.C)."""
     return (eps - 1.0).max(axis=(1, 2)) < thresh
 
 
 def plan_band(dry, levels, n_dirichlet=1):
     """Choose the wet band Omega_1 (a periodic run of z-planes) and its
-    Dirichlet planes, from the per-plane dry flags.
+    Dirichlet planes, from the per-plane dry flags (Sec. II.C).
 
     Reading: the Dirichlet planes sit in the middle of the longest periodic run
     of dry planes; there are n_dirichlet of them (0 = as many as the run holds),
@@ -671,12 +694,12 @@ def plan_band(dry, levels, n_dirichlet=1):
 
 def band_planes(nz, first, nd):
     """Interior planes of the band, in order: the nz - nd planes after the
-    Dirichlet block (periodic)."""
+    Dirichlet block (periodic; Sec. II.C)."""
     return [(first + nd + t) % nz for t in range(nz - nd)]
 
 
 def assemble_A(eps, h):
-    """A as a scipy sparse matrix (same definition as apply_A), flat x-fastest."""
+    """A as a scipy sparse matrix (same definition as apply_A, Eq. 3), flat x-fastest."""
     import scipy.sparse as sp
     nz, ny, nx = eps.shape
     n = eps.size
@@ -796,7 +819,7 @@ def apply_A6(phi, eps, h):
 
 
 def apply_A6_transpose(lam, eps, h):
-    """A6^T lam. D1 is antisymmetric and D2 symmetric on the periodic grid, so
+    """A6^T lam (Eq. 16-18). D1 is antisymmetric and D2 symmetric on the periodic grid, so
     A6^T lam = sum_axes [-D1((D1 eps) lam) + D2(eps lam)]."""
     out = np.zeros_like(lam)
     for c in range(3):
@@ -805,7 +828,7 @@ def apply_A6_transpose(lam, eps, h):
 
 
 def assemble_A6(eps, h):
-    """A6 as a scipy sparse matrix (same definition as apply_A6), flat x-fastest.
+    """A6 as a scipy sparse matrix (same definition as apply_A6, Eq. 16-18), flat x-fastest.
     Row i, column i+n along axis c holds (D1 eps)_i alpha_n/h_c + eps_i beta_n/h_c^2."""
     import scipy.sparse as sp
     n = eps.size
@@ -830,7 +853,7 @@ def assemble_A6(eps, h):
 
 
 def fd6_symbol(grid, h):
-    """Eigenvalues of sum_axes D2 (the eps = 1 case of A6) on the periodic grid,
+    """Eigenvalues of sum_axes D2 (Eq. 18; the eps = 1 case of A6) on the periodic grid,
     sum_axes (beta_0 + 2 sum_n beta_n cos(n theta_a))/h_a^2, in numpy's rfftn
     layout (nz, ny, nx//2+1)."""
     nx, ny, nz = grid
@@ -939,7 +962,7 @@ def adjoint6(rho, eps, h, tol=1e-13, method=None):
 
 
 def residual6_norm(phi, mu, rho, eps, h):
-    """||b - A6 phi - mu eps||_2 / ||b||_2 with b = -4 pi (rho - mean(rho))."""
+    """||b - A6 phi - mu eps||_2 / ||b||_2 with b = -4 pi (rho - mean(rho)) (Eq. 16-18)."""
     b = -FOUR_PI * (rho - rho.mean())
     r = b - apply_A6(phi, eps, h) - mu * eps
     return float(np.linalg.norm(r) / np.linalg.norm(b))
