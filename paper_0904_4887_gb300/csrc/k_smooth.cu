@@ -434,9 +434,10 @@ void sweep_rows(const LV<float>& L, const float* u_old, const float* f, float* u
 // ---------------------------------------------------------------------------
 // Warp-specialised row-tile variant (FP32). Same tile as above (whole x rows,
 // SY output rows, a chunk of z-planes), but the loop has no CTA barrier:
-//   * one producer warp streams planes of u_old, eps and f into an NSW-slot
+//   * one producer warp streams planes of u_old and eps into an NSW-slot
 //     ring with bulk copies, one row per copy; slot s completes phase
-//     `full[s]` when its bytes have landed;
+//     `full[s]` when its bytes have landed; f does not pass through the ring:
+//     each consumer thread loads its own f values one plane ahead;
 //   * the consumer threads own a pair column (2p, 2p+1) over K adjacent rows,
 //     so the y neighbours inside the K rows and the z neighbours come from
 //     registers; shared memory serves the x neighbour outside the pair and
