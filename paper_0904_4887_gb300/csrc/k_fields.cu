@@ -2,10 +2,13 @@
 // charge density (Sec. II.A), the dry-plane test (Sec. II.C), the energy
 // (Eq. 4) and the forces (Eq. 11, Appendix B).
 //
-// Every kernel here works on 32 x 4 x 4 tiles of grid points, one thread per
-// point. A tile first culls the periodic images of a chunk of atoms against
-// its bounding box (in FP32, with a safety margin), keeps the survivors in
-// shared memory, and then every thread runs over that short list in FP64.
+// The kernels work on tiles of grid points: 32 x 4 x 4 with one thread per
+// point, or 32 x 4 x 16 for the tabulated dielectric and its force (each
+// thread takes 4 points along z). A tile first culls the periodic images of
+// a chunk of atoms against its bounding box (in FP32, with a safety margin),
+// keeps the survivors in shared memory, and then every thread runs over that
+// short list: in FP64, or in df64 (pairs of FP32 numbers) where a kernel says
+// so, because GB300's FP64 pipe runs at 1/64 of its FP32 rate.
 #include "gp_common.cuh"
 
 namespace gp {
