@@ -101,7 +101,9 @@ size_t level_bytes(const LV<T>& L) { return (size_t)L.nx * L.ny * (L.nz + 2) * s
 template <typename T>
 T* lbase(const LV<T>& L, T* p) { return p - (size_t)L.nx * L.ny; }
 
-// level plan: number of levels such that the coarsest grid has <= kMaxCoarse points
+// level plan: `requested` levels if the grid coarsens that far with <= kMaxCoarse
+// coarsest points; otherwise the fewest levels reaching <= kAutoCoarse points,
+// else the most levels reaching <= kMaxCoarse (the rule stated for gp_plan_levels)
 int plan_levels(int nx, int ny, int nz, int zper, int requested, std::string& why) {
     auto dims_ok = [&](int l, long& pts) {
         const int m = 1 << l;
