@@ -149,3 +149,18 @@ def test_polarisation_term_is_the_dielectric_excess_of_the_operator():
     rhs = O.apply_L(phi, h) + O.polarisation_term(phi, eps, h)
     assert np.max(np.abs(lhs - rhs)) < 1e-12 * np.max(np.abs(lhs))
     assert np.max(np.abs(O.polarisation_term(phi, np.ones(shape), h))) == 0.0
+
+
+def test_eq10_beta_default_is_the_printed_value():
+    """beta of Eq. 10: the oracle's default and the library's default both equal
+    the value the paper prints (tests/golden/paper_parameters.txt)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_parameters.txt")
+    vals = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    assert O.GammaParams().beta == vals["beta"]
+    from paper_0904_4887_gb300 import gp as G
+    assert G.default_params().beta == vals["beta"]
