@@ -366,6 +366,13 @@ def test_split_fixed_point_equals_full_box():
     split, hist = O.split_solve(rho, eps, h, band, tol=1e-13)
     assert hist[-1] < 1e-12
     assert np.max(np.abs(split - full)) < 1e-10 * np.max(np.abs(full))
+    # the one-shot scheme (one band solve on the vacuum potential's Dirichlet
+    # data) is a close approximation but not the solution: the reason the
+    # coupling is iterated to self-consistency
+    one, _ = O.split_solve(rho, eps, h, band, tol=1e-13, maxit=1)
+    err1 = np.max(np.abs(one - full)) / np.max(np.abs(full))
+    err_vac = np.max(np.abs(O.vacuum_potential(rho, h) - full)) / np.max(np.abs(full))
+    assert 1e-4 < err1 < 1e-2 and err1 < 0.1 * err_vac
 
 
 # -------------------------------------------------------------- Eq. 9-10 dielectric
