@@ -336,6 +336,38 @@ def test_forces_match_central_differences(rho_moves):
     assert np.max(np.abs(fd - G[sel])) < 1e-6 * scale
 
 
+def test_vacuum_force_between_gaussian_atoms_closed_form():
+    """P12 (the eps = 1 limit of Eq. 11, the Hartree force of Eq. 14): two
+    neutral atoms, each a +Z core and a -Z cloud Gaussian, interact through
+    E_int(R) = sum_ij q_i q_j erf(R/s_ij)/R with s_ij = sqrt(2(sigma_i^2 + sigma_j^2)),
+    since a spherically symmetric neutral charge has no field outside itself
+    (images decay like erfc). The discrete gradient G^rho of Eq. 11 converges
+    to dE_int/dR_a at O(h^2)."""
+    L = 16.0
+    pos = np.array([[8.1, 7.9, 8.3], [9.3, 8.6, 7.5]])
+    Z = np.array([4.0, 6.0])
+    sc, scl = np.array([0.5, 0.55]), np.array([0.9, 1.0])
+    d = pos[0] - pos[1]
+    R = np.linalg.norm(d)
+    dE = 0.0
+    for qi, si in ((Z[0], sc[0]), (-Z[0], scl[0])):
+        for qj, sj in ((Z[1], sc[1]), (-Z[1], scl[1])):
+            s = math.sqrt(2.0 * (si * si + sj * sj))
+            dE += qi * qj * (2.0 / math.sqrt(math.pi) * math.exp(-(R / s) ** 2) / (s * R) - erf(R / s) / R ** 2)
+    G_exact = dE * d / R
+    errs = []
+    for n in (48, 96):
+        grid, cell = (n, n, n), (L, L, L)
+        h = O.spacing(grid, cell)
+        rho = O.charge_density(grid, cell, pos, Z, sc, scl)
+        phi = O.vacuum_potential(rho, h)
+        Ge, Gr = O.energy_gradient(phi, grid, cell, pos, Z, sc, scl, p=O.DielectricParams(eps0=1.0), atoms=[0])
+        assert np.max(np.abs(Ge)) == 0.0                    # no dielectric term at eps = 1
+        errs.append(np.linalg.norm(Gr[0] - G_exact) / np.linalg.norm(G_exact))
+    assert errs[1] < 5e-3, errs
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
 # -------------------------------------------------------------- dry/wet split
 
 def test_plan_band_brute_force():
