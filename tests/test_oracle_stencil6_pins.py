@@ -294,3 +294,40 @@ def test_forces6_match_central_differences(rho_moves):
     scale = np.max(np.abs(fd))
     assert scale > 1e-3
     assert np.max(np.abs(fd - G[sel])) < 2e-6 * scale
+
+
+def test_forces6_gamma_dielectric_match_central_differences():
+    """The same adjoint forces with the dielectric of Eq. 9-10 (the gamma branch
+    of energy_gradient6): eps term with rho frozen, both terms with rho moving."""
+    grid, cell = (16, 16, 24), (8.0, 8.0, 12.0)
+    at = W.slab_atoms(cell, 2, 2, seed=1)
+    rv = W.vdw_radii(at.Z)
+    p = O.GammaParams(rcut=7.9)
+    h = O.spacing(grid, cell)
+    pos = at.pos
+    sel = [0, 5]
+    for rho_moves in (False, True):
+        def E_of(q):
+            eps = O.dielectric_gamma(grid, cell, q, rv, p)
+            src = q if rho_moves else pos
+            rho = O.charge_density(grid, cell, src, at.Z, at.sigma_core, at.sigma_cloud)
+            phi, _, _ = O.solve6(rho, eps, h, tol=1e-14)
+            return O.energy(rho - rho.mean(), phi, grid, cell)
+
+        eps = O.dielectric_gamma(grid, cell, pos, rv, p)
+        rho = O.charge_density(grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud)
+        phi, mu, _ = O.solve6(rho, eps, h, tol=1e-14)
+        lam, _, _ = O.adjoint6(rho, eps, h, tol=1e-14)
+        Ge, Gr = O.energy_gradient6(phi, mu, lam, grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud,
+                                    p=p, atoms=sel, rho_moves=rho_moves, rvdw=rv)
+        G = Ge + Gr
+        fd = np.zeros((len(sel), 3))
+        d = 1e-4
+        for t, a in enumerate(sel):
+            for c in range(3):
+                pp = pos.copy(); pp[a, c] += d
+                pm = pos.copy(); pm[a, c] -= d
+                fd[t, c] = (E_of(pp) - E_of(pm)) / (2 * d)
+        scale = np.max(np.abs(fd))
+        assert scale > 1e-3
+        assert np.max(np.abs(fd - G[sel])) < 2e-6 * scale, (rho_moves, np.max(np.abs(fd - G[sel])) / scale)
