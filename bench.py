@@ -203,7 +203,7 @@ def gpu_arm(args, rank, world):
     n_dir = args.n_dirichlet if args.n_dirichlet >= 0 else (0 if args.kind == 2 else 1)
 
     def make_solver(precision, split):
-        extra = {"kind": args.kind, "rcut": args.rcut_gamma, "zlim": zlim} if args.kind else {}
+        extra = {"kind": args.kind, "gamma_tail": args.gamma_tail, "zlim": zlim} if args.kind else {}
         if args.nu_coarse is not None:
             extra["nu_coarse"] = args.nu_coarse
         return P.GPSolver(w.grid, w.cell, precision=precision, split=split, levels=w.levels,
@@ -378,8 +378,11 @@ def gpu_arm(args, rank, world):
         "vs_baseline": None, "dtype": "f32/f64" if args.precision == 1 else "f64", "data": "synthetic",
         "config": {"workload": w.name, "grid": list(w.grid), "cell_A": list(w.cell), "atoms": int(len(at.Z)),
                    "tol": args.tol, "precision": "mixed" if args.precision == 1 else "fp64",
-                   "dielectric": {0: "erf product", 1: "Eq. 9-10 (beta 2.4, rcut %.1f A)" % args.rcut_gamma,
-                                  2: "Eq. 19 (beta 2.4, rcut %.1f A, z_lim %.3f A)" % (args.rcut_gamma, zlim)}[args.kind],
+                   "dielectric": {0: "erf product",
+                                  1: "Eq. 9-10 (beta 2.4, image sum to %.1f A, tail < %.0e)"
+                                     % (stats.gamma_cutoff, args.gamma_tail),
+                                  2: "Eq. 19 (beta 2.4, image sum to %.1f A, tail < %.0e, z_lim %.3f A)"
+                                     % (stats.gamma_cutoff, args.gamma_tail, zlim)}[args.kind],
                    "split": bool(args.split), "split_active": bool(stats.split_active),
                    "wet_fraction": stats.wet_fraction, "levels": stats.levels,
                    "outer_iterations_mean": float(np.mean(outer)), "vcycles_mean": float(np.mean(vcyc)),
@@ -628,7 +631,8 @@ def main():
                          "2 Eq. 19 (solvent excluded below the lowest layer)")
     ap.add_argument("--n-dirichlet", type=int, default=-1,
                     help="split: Dirichlet planes (-1: 0 = the whole dry run for --kind 2, else 1)")
-    ap.add_argument("--rcut-gamma", type=float, default=9.0, help="cut-off of gamma for --kind 1 (Angstrom)")
+    ap.add_argument("--gamma-tail", type=float, default=1e-13,
+                    help="--kind 1, 2: bound on the part of gamma's image sum left out")
     ap.add_argument("--nu-coarse", type=int, default=None,
                     help="smoothing sweeps on the levels below the finest (default: the library's)")
     ap.add_argument("--sweep-shape", type=int, default=-1,

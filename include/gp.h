@@ -60,7 +60,7 @@ typedef enum {
 
 /* Grid: each extent a power of two, or three times one, and >= 8; nx even. */
 typedef struct { int nx, ny, nz; } gp_grid;
-/* Orthorhombic periodic cell, Angstrom; every side > rcut of the dielectric. */
+/* Orthorhombic periodic cell, Angstrom; every side >= rcut of the kind-0 dielectric. */
 typedef struct { double lx, ly, lz; } gp_cell;
 
 /* Solver and dielectric parameters; gp_default_params() fills the defaults. */
@@ -94,8 +94,9 @@ typedef struct {
     int sweep_shape;      /* FP32 finest-level smoother tile (see gp_stats.sweep_shape); -1 = chosen
                              by the autotuner at gp_set_dielectric (-1) */
     int kind;             /* dielectric form: 0 = the erf product above (0); 1 = Eq. 9-10, the dummy
-                             density gamma(r) = sum_a exp(-(|r-R_a| - rvdw_a)) T(|r-R_a|) over atoms
-                             and images, T a quintic taper from 1 at rcut-1 A to 0 at rcut,
+                             density gamma(r) = sum_a exp(-(|r-R_a| - rvdw_a)) over every atom and
+                             periodic image within the radius where a bound on the rest of the sum
+                             falls below gamma_tail (gp_stats.gamma_cutoff; rcut is not used),
                              eps = 1 + (eps0-1)/(1 + gamma^(2 beta)); 2 = Eq. 19, kind 1 with the
                              solvent excluded below every atom with z_a <= zlim (its term is
                              exp(+(d - rvdw_a)) from its nearest image at points with z < z_a, both
@@ -106,6 +107,11 @@ typedef struct {
     double zlim;          /* kind 2: z_lim of Eq. 19, Angstrom inside the cell (0) */
     int nu_coarse;        /* sweeps before and after the coarse correction on the levels below the
                              finest; 0 = nu1, nu2 there too (0) */
+    double gamma_tail;    /* kinds 1, 2: bound on the part of gamma the image sum leaves out, in
+                             (0, 1e-3] (1e-13). The radius R is the smallest with
+                             (4 pi/3V) exp(-R)(u^3 + 3u^2 + 6u + 6) sum_a exp(rvdw_a) <= gamma_tail,
+                             u = R + half the cell diagonal, V the cell volume: the images of an
+                             atom within r of a point number at most (4 pi/3)(r + u - R)^3/V */
 } gp_params;
 
 #define GP_HISTORY 64
@@ -129,6 +135,7 @@ typedef struct {
                                    14, 12 rows with a producer warp and 2, 2, 4, 3, 2, 4, 2, 2 rows
                                    per thread (shapes 4 to 14 for nx = 64, 96, 128, 192, 256 where
                                    the tile fits one CTA; otherwise 0) */
+    double gamma_cutoff;        /* kinds 1, 2: radius of the Eq. 9 image sum (Angstrom), else 0 */
 } gp_stats;
 
 /* Fill *p with the defaults listed beside each field. */
@@ -146,7 +153,7 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
  * or Eq. 19, kind 2; Sec. II.C for the band). Must precede gp_solve and gp_energy_forces; call again whenever the
  * atoms move. `params` is copied. Errors: GP_ERR_INVALID_ARG (null params,
  * n_atoms < 0, null atoms with n_atoms > 0, any parameter out of the range
- * stated beside it, rcut larger than the cell, a grid or `levels` that does not
+ * stated beside it, rcut larger than the cell (kind 0), a grid or `levels` that does not
  * coarsen; gp_last_error names which), GP_ERR_STATE (kind 1 or 2 without
  * gp_set_vdw_radii for the same n_atoms), GP_ERR_OOM (the multigrid
  * hierarchy is allocated here), GP_ERR_CUDA. Argument errors leave the
@@ -180,7 +187,9 @@ gp_status gp_build_rho(gp_ctx* ctx, const double* atoms_dev, const double* gauss
  * (phi holds the last iterate and gp_get_stats the residuals), GP_ERR_TIMEOUT
  * (a bounded wait of the finest-level smoother gave up; phi is not valid, the
  * context stays usable), GP_ERR_OOM (workspaces are allocated on first use),
- * GP_ERR_CUDA. */
+ * GP_ERR_CUDA. On GP_ERR_TIMEOUT the solve has stopped at the first residual
+ * readback after the expiry: gp_get_stats then records only the outer
+ * iterations that ran before it. */
 gp_status gp_solve(gp_ctx* ctx, const double* rho_dev, double* phi_dev, double tol);
 
 /* Energy and forces for the atoms of the last gp_set_dielectric, given the
@@ -228,6 +237,12 @@ gp_status gp_residual6(gp_ctx* ctx, const double* rho_dev, const double* phi_dev
  * plan), GP_ERR_OOM, GP_ERR_CUDA. */
 gp_status gp_fft_poisson(gp_ctx* ctx, const double* src_dev, double* phi_dev);
 
+/* The same vacuum solve in FP32 arithmetic: the instance the mixed-precision
+ * dry/wet split applies to its working-precision residual (Scheme 1, Eq. 15).
+ * src_dev, phi_dev: grid-sized float32 device arrays (may alias); plan,
+ * workspace and errors as for gp_fft_poisson. */
+gp_status gp_fft_poisson_f32(gp_ctx* ctx, const float* src_dev, float* phi_dev);
+
 /* Copy eps (FP64, grid-sized) of the last gp_set_dielectric into eps_dev.
  * Errors: GP_ERR_INVALID_ARG (null), GP_ERR_STATE (no dielectric), GP_ERR_CUDA. */
 gp_status gp_get_eps(gp_ctx* ctx, double* eps_dev);
@@ -265,7 +280,8 @@ int gp_plan_levels(int nx, int ny, int nz, int zper, int requested);
  * must not grow, or in a plug-in that may not create a solver context). The
  * paper has no counterpart; this is a deployment entry point.
  *
- *   r = -4 pi rho - A phi  (Eq. 3 operator, FP64, eps given by the caller)
+ *   r = -4 pi rho - A phi  (the FP64 7-point face-mean operator of gp_residual,
+ *                           with eps given by the caller instead of a context)
  *   rel_dev[0] = ||r||_2 / ||4 pi rho||_2
  *
  * Arguments: grid and cell as for gp_create; eps_dev, rho_dev, phi_dev and

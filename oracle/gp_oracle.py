@@ -177,39 +177,102 @@ def dielectric_gradient_atom(a, grid, cell, pos, P, p: DielectricParams = Dielec
 
 @dataclasses.dataclass(frozen=True)
 class GammaParams:
-    """Eq. 9: gamma(r) = sum_I exp(-(|r - R_I| - Rvdw_I)) T(|r - R_I|), over atoms
-    and their periodic images. The paper gives no cut-off; here each term is
-    tapered to zero between rcut - TAPER and rcut by the quintic smoothstep
-    T, so that eps stays twice differentiable in the positions (a hard cut
-    would put steps into E(R) wherever a cut-off sphere crosses a grid point).
-    Eq. 10: eps = 1 + (eps0 - 1)/2 (1 + (1 - gamma^(2 beta))/(1 + gamma^(2 beta))).
+    """Eq. 9: gamma(r) = sum_I exp(-(|r - R_I| - Rvdw_I)) over every atom and
+    every periodic image; Eq. 10: eps = 1 + (eps0 - 1)/2 (1 + (1 - gamma^(2 beta))
+    /(1 + gamma^(2 beta))).
+
+    The paper sums over all atoms. The image sum converges (its terms decay like
+    exp(-d) while their number grows like d^2), so it is taken over the images
+    within the radius gamma_cutoff(cell, rvdw, tail), beyond which
+    gamma_tail_bound proves the neglected part of gamma to be below `tail`
+    everywhere. No taper: a term at the cut-off is below ~1e-17, so the step it
+    puts into E(R) where a cut-off sphere crosses a grid point is below
+    rounding.
     """
     eps0: float = 78.36
     beta: float = 2.4
-    rcut: float = 8.0
+    tail: float = 1e-13
 
 
-TAPER = 1.0   # width of the cut-off taper of Eq. 9 terms, Angstrom
+def gamma_tail_bound(radius, cell, rvdw):
+    """Upper bound on sum_I exp(-(d_I - Rvdw_I)) over all atoms and images with
+    d_I > radius, at any point of the cell.
+
+    The images of one atom form the lattice {R + nL}. Around each image put the
+    cell-shaped box it is the centre of; these boxes do not overlap, and every
+    box of an image within distance r lies inside the ball of radius r + c, c
+    half the cell diagonal. So at most N(r) = (4 pi/3)(r + c)^3 / V images lie
+    within r. With that count, sum_{d > R} exp(-d) = int_R^inf exp(-r) dN(r)
+    <= int_R^inf exp(-r) N(r) dr (integration by parts, the boundary term being
+    negative), and int_R^inf exp(-r)(r + c)^3 dr = exp(-R)(u^3 + 3u^2 + 6u + 6)
+    with u = R + c. Each atom's sum carries the factor exp(Rvdw_I).
+    """
+    L = np.asarray(cell, dtype=np.float64)
+    V = float(L[0] * L[1] * L[2])
+    u = float(radius) + 0.5 * float(np.sqrt(np.sum(L * L)))
+    poly = u ** 3 + 3.0 * u ** 2 + 6.0 * u + 6.0
+    return (4.0 * math.pi / (3.0 * V)) * math.exp(-float(radius)) * poly * float(np.sum(np.exp(rvdw)))
 
 
-def taper(d, rcut):
-    """(T, dT/dd): 1 below rcut - TAPER, 0 beyond rcut, 1 - 10u^3 + 15u^4 - 6u^5
-    between. The smooth cut-off applied to each term of the Eq. 9 sum (a
-    reading: the paper sums over all atoms)."""
-    u = np.clip((d - (rcut - TAPER)) / TAPER, 0.0, 1.0)
-    T = 1.0 - u ** 3 * (10.0 - 15.0 * u + 6.0 * u * u)
-    dT = -30.0 * u * u * (1.0 - u) ** 2 / TAPER
-    return T, dT
+def gamma_cutoff(cell, rvdw, tail):
+    """The smallest radius (to 1e-6 A, by bisection) at which gamma_tail_bound
+    is at most `tail`; the bound falls monotonically with the radius (its
+    derivative is -exp(-R) u^3)."""
+    lo, hi = 0.0, 1.0
+    while gamma_tail_bound(hi, cell, rvdw) > tail:
+        hi *= 2.0
+    while hi - lo > 1e-6:
+        mid = 0.5 * (lo + hi)
+        if gamma_tail_bound(mid, cell, rvdw) > tail:
+            lo = mid
+        else:
+            hi = mid
+    return hi
+
+
+def _image_boxes_any(center, grid, cell, radius):
+    """Like _image_boxes for any radius (also beyond one cell): every image
+    centre + n L within `radius` of the grid's box [0, L) per axis, with the
+    sub-box of grid points within `radius` of it."""
+    h = spacing(grid, cell)
+    rng = []
+    for a in range(3):
+        n0 = int(math.floor((-radius - center[a]) / cell[a]))
+        n1 = int(math.ceil((cell[a] + radius - center[a]) / cell[a]))
+        rng.append(range(n0, n1 + 1))
+    for n in itertools.product(*rng):
+        c = [center[a] + n[a] * cell[a] for a in range(3)]
+        lo = [max(int(math.ceil((c[a] - radius) / h[a])), 0) for a in range(3)]
+        hi = [min(int(math.floor((c[a] + radius) / h[a])), grid[a] - 1) for a in range(3)]
+        if any(lo[a] > hi[a] for a in range(3)):
+            continue
+        dx = np.arange(lo[0], hi[0] + 1) * h[0] - c[0]
+        dy = np.arange(lo[1], hi[1] + 1) * h[1] - c[1]
+        dz = np.arange(lo[2], hi[2] + 1) * h[2] - c[2]
+        sl = (slice(lo[2], hi[2] + 1), slice(lo[1], hi[1] + 1), slice(lo[0], hi[0] + 1))
+        yield sl, (dz[:, None, None], dy[None, :, None], dx[None, None, :])
+
+
+def _point_images(points, center, cell, radius):
+    """Displacements (M, 3) from every image of `center` that lies within
+    `radius` of the cell box to the points, one image at a time."""
+    rng = []
+    for a in range(3):
+        n0 = int(math.floor((-radius - center[a]) / cell[a]))
+        n1 = int(math.ceil((cell[a] + radius - center[a]) / cell[a]))
+        rng.append(range(n0, n1 + 1))
+    for n in itertools.product(*rng):
+        yield points - (center + np.asarray(n) * cell)
 
 
 def dummy_density(grid, cell, pos, rvdw, p: GammaParams = GammaParams()):
-    """gamma on the grid (Eq. 9)."""
+    """gamma on the grid (Eq. 9), over every image within gamma_cutoff."""
+    rc = gamma_cutoff(cell, rvdw, p.tail)
     g = np.zeros((grid[2], grid[1], grid[0]))
     for R, rv in zip(pos, rvdw):
-        for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, p.rcut):
+        for sl, (dz, dy, dx) in _image_boxes_any(R, grid, cell, rc):
             d = np.sqrt(dx * dx + dy * dy + dz * dz)
-            T, _ = taper(d, p.rcut)
-            g[sl] += np.exp(-(d - rv)) * T
+            g[sl] += np.where(d < rc, np.exp(-(d - rv)), 0.0)
     return g
 
 
@@ -232,32 +295,32 @@ def dielectric_gamma(grid, cell, pos, rvdw, p: GammaParams = GammaParams()):
 
 
 def dielectric_gamma_points(points, cell, pos, rvdw, p: GammaParams = GammaParams()):
-    """Eq. 9-10 at arbitrary points (M, 3), one by one over atoms and all 27 images."""
+    """Eq. 9-10 at arbitrary points (M, 3), one atom image at a time over every
+    image within gamma_cutoff."""
     points = np.asarray(points, dtype=np.float64)
     cell = np.asarray(cell, dtype=np.float64)
+    rc = gamma_cutoff(cell, rvdw, p.tail)
     g = np.zeros(len(points))
     for R, rv in zip(pos, rvdw):
-        for n in itertools.product((-1, 0, 1), repeat=3):
-            d = np.linalg.norm(points - (R + np.asarray(n) * cell), axis=1)
-            T, _ = taper(d, p.rcut)
-            g += np.exp(-(d - rv)) * T
+        for dv in _point_images(points, np.asarray(R, dtype=np.float64), cell, rc):
+            d = np.linalg.norm(dv, axis=1)
+            g += np.where(d < rc, np.exp(-(d - rv)), 0.0)
     return eps_of_gamma(g, p)
 
 
 def dielectric_gamma_gradient_atom(a, grid, cell, pos, rvdw, gamma, p: GammaParams = GammaParams()):
     """d eps_i / d R_a (x, y, z arrays) for Eq. 9-10: by the chain rule,
-    (d eps/d gamma) sum_images exp(-(d - Rvdw_a)) (T - T') (r - R_a)/d, because
-    d|r - R_a|/dR_a = -(r - R_a)/d. With T = 1 this is Eq. 12 with the opposite
-    sign to the printed one: moving an atom towards r raises gamma there and
-    lowers eps.
+    (d eps/d gamma) sum_images exp(-(d - Rvdw_a)) (r - R_a)/d, because
+    d|r - R_a|/dR_a = -(r - R_a)/d. This is Eq. 12 with the opposite sign to
+    the printed one: moving an atom towards r raises gamma there and lowers eps.
     """
+    rc = gamma_cutoff(cell, rvdw, p.tail)
     fe = deps_dgamma(gamma, p)
     out = [np.zeros_like(gamma) for _ in range(3)]
-    for sl, (dz, dy, dx) in _image_boxes(pos[a], grid, cell, p.rcut):
+    for sl, (dz, dy, dx) in _image_boxes_any(pos[a], grid, cell, rc):
         d = np.sqrt(dx * dx + dy * dy + dz * dz)
         dsafe = np.where(d > 0, d, 1.0)
-        T, dT = taper(d, p.rcut)
-        coef = np.where(d > 0, fe[sl] * np.exp(-(d - rvdw[a])) * (T - dT) / dsafe, 0.0)
+        coef = np.where((d > 0) & (d < rc), fe[sl] * np.exp(-(d - rvdw[a])) / dsafe, 0.0)
         out[0][sl] += coef * dx
         out[1][sl] += coef * dy
         out[2][sl] += coef * dz
@@ -276,7 +339,8 @@ def dielectric_gamma_gradient_atom(a, grid, cell, pos, rvdw, gamma, p: GammaPara
 # reaches sat_exponent(p) = (ln(eps0 - 1) + 37)/(2 beta), eps - 1 is below
 # exp(-37) < 1e-16 and d eps/d gamma is as small: such a point is "saturated",
 # with eps = 1 and d eps/d gamma = 0. Atoms with z_I > z_lim, and lower atoms at
-# points with z >= z_I, contribute as in Eq. 9 (images within rcut).
+# points with z >= z_I, contribute as in Eq. 9 (every image within
+# gamma_cutoff).
 def sat_exponent(p):
     """Growing exponent of Eq. 19 beyond which eps - 1 = (eps0-1)/(1+gamma^(2 beta))
     is below 1e-16 (exp(-37) of eps0 - 1), so that eps is taken as exactly 1."""
@@ -295,13 +359,13 @@ def dummy_density_eq19(grid, cell, pos, rvdw, zlim, p: GammaParams = GammaParams
     sat = np.zeros(g.shape, dtype=bool)
     posw = np.mod(pos, np.asarray(cell))
     lower = posw[:, 2] <= zlim
+    rc = gamma_cutoff(cell, rvdw, p.tail)
     for a, (R, rv) in enumerate(zip(posw, rvdw)):
         below = (z < R[2]) if lower[a] else np.zeros_like(z, dtype=bool)
-        for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, p.rcut):
+        for sl, (dz, dy, dx) in _image_boxes_any(R, grid, cell, rc):
             d = np.sqrt(dx * dx + dy * dy + dz * dz)
-            T, _ = taper(d, p.rcut)
             keep = ~np.broadcast_to(below, g.shape)[sl]
-            g[sl] += np.where(keep, np.exp(-(d - rv)) * T, 0.0)
+            g[sl] += np.where(keep & (d < rc), np.exp(-(d - rv)), 0.0)
         if lower[a]:
             ddx = _min_image(x - R[0], cell[0])
             ddy = _min_image(y - R[1], cell[1])
@@ -323,9 +387,9 @@ def dielectric_eq19(grid, cell, pos, rvdw, zlim, p: GammaParams = GammaParams())
 
 
 def dielectric_eq19_gradient_atom(a, grid, cell, pos, rvdw, zlim, gamma, sat, p: GammaParams = GammaParams()):
-    """d eps_i/d R_a for Eq. 19: decaying (tapered) terms as Eq. 9, a growing
-    term exp(+(d - Rvdw)) gives -(d eps/d gamma) exp(d - Rvdw) (r - R_a)/d;
-    zero at saturated points."""
+    """d eps_i/d R_a for Eq. 19: decaying terms as Eq. 9, a growing term
+    exp(+(d - Rvdw)) gives -(d eps/d gamma) exp(d - Rvdw) (r - R_a)/d; zero at
+    saturated points."""
     x, y, z = _grid_coords(grid, cell)
     fe = np.where(sat, 0.0, deps_dgamma(np.where(sat, 1.0, gamma), p))
     out = [np.zeros_like(gamma) for _ in range(3)]
@@ -333,11 +397,11 @@ def dielectric_eq19_gradient_atom(a, grid, cell, pos, rvdw, zlim, gamma, sat, p:
     R, rv = posw[a], rvdw[a]
     lower = R[2] <= zlim
     below = np.broadcast_to((z < R[2]) if lower else np.zeros_like(z, dtype=bool), gamma.shape)
-    for sl, (dz, dy, dx) in _image_boxes(R, grid, cell, p.rcut):
+    rc = gamma_cutoff(cell, rvdw, p.tail)
+    for sl, (dz, dy, dx) in _image_boxes_any(R, grid, cell, rc):
         d = np.sqrt(dx * dx + dy * dy + dz * dz)
         dsafe = np.where(d > 0, d, 1.0)
-        T, dT = taper(d, p.rcut)
-        coef = np.where((d > 0) & ~below[sl], fe[sl] * np.exp(-(d - rv)) * (T - dT) / dsafe, 0.0)
+        coef = np.where((d > 0) & (d < rc) & ~below[sl], fe[sl] * np.exp(-(d - rv)) / dsafe, 0.0)
         out[0][sl] += coef * dx
         out[1][sl] += coef * dy
         out[2][sl] += coef * dz

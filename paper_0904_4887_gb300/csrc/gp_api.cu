@@ -175,6 +175,8 @@ struct gp_ctx {
     double* sw_coef = nullptr;     // switching-function tables (2 * kSwNI * (kSwDeg+1))
     float4* sw_pack = nullptr;     // their packed FP32 copies (2 * kSwNI * 4)
     double* rvdw = nullptr;        // van der Waals radii for the kind-1 dielectric
+    std::vector<double> rvdw_host; // the same on the host (the image-sum radius depends on them)
+    DielParams dp{};               // dielectric constants of the last gp_set_dielectric
     float2* phid = nullptr;        // df64 copies for the mixed-precision residual: phi, b = -4 pi rho, eps
     float2* bd = nullptr;
     float2* epsd = nullptr;
@@ -942,6 +944,20 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
             launch_from_df(c->n, c->phid, phi, c->s);
         }
     };
+    // a bounded smoother wait that gave up leaves the fields undefined: the flag is
+    // read with every residual readback (no extra synchronisation), and the solve
+    // stops at the first one that shows it, before any further V-cycle runs
+    int expired = 0;
+    auto queue_expired_read = [&] {
+        GP_CUDA(cudaMemcpyAsync(&expired, c->dstatus + 1, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    };
+    auto timeout_exit = [&]() -> gp_status {
+        GP_CUDA(cudaMemsetAsync(c->dstatus + 1, 0, sizeof(int), c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        prof_collect(c);
+        c->err = "a smoother copy wait expired; the result is not valid";
+        return GP_ERR_TIMEOUT;
+    };
     double best = INFINITY;
     gp_status result = GP_ERR_NOT_CONVERGED;
     const bool krylov = split && c->prm.accel;
@@ -971,7 +987,9 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         });
         double s2[2];
         GP_CUDA(cudaMemcpyAsync(s2, c->scal + 8, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->s));
+        queue_expired_read();
         GP_CUDA(cudaStreamSynchronize(c->s));
+        if (expired) return timeout_exit();   // the graph's residual is not recorded
         const double rn = std::sqrt(s2[0]) / nb;
         st.outer_iterations += k + 1;
         if (st.history_len < GP_HISTORY) st.history[st.history_len++] = rn;
@@ -1002,8 +1020,10 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         }
         outer_residual(rT);
         GP_CHECK_LAUNCH();
+        queue_expired_read();
         double s2[2];
         sum_host(c, 2, s2);
+        if (expired) return timeout_exit();   // the residual of undefined fields is not recorded
         const double rn = std::sqrt(s2[0]) / nb;
         st.outer_iterations++;
         if (st.history_len < GP_HISTORY) st.history[st.history_len++] = rn;
@@ -1038,23 +1058,67 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         launch_sub_mean(c->n, phi, c->scal + 9, 1.0 / (double)c->n, c->s);
     }
     GP_CHECK_LAUNCH();
-    int expired = 0;
-    GP_CUDA(cudaMemcpyAsync(&expired, c->dstatus + 1, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    queue_expired_read();
     GP_CUDA(cudaStreamSynchronize(c->s));
+    if (expired) return timeout_exit();
     prof_collect(c);
     if (result == GP_ERR_NOT_CONVERGED) c->err = "not converged within max_outer";
     if (result == GP_ERR_DIVERGED) c->err = "residual diverged";
-    if (expired) {
-        GP_CUDA(cudaMemsetAsync(c->dstatus + 1, 0, sizeof(int), c->s));
-        c->err = "a smoother copy wait expired; the result is not valid";
-        return GP_ERR_TIMEOUT;
-    }
     return result;
 }
 
 gp_status fail(gp_ctx* c, const Err& e) {
     if (c) c->err = e.msg;
     return e.st;
+}
+
+// Upper bound on the part of gamma (Eq. 9) that an image sum cut at `radius` drops,
+// at any point of the cell, for sum_a exp(rvdw_a) = se. At most (4 pi/3)(r + c)^3 / V
+// images of an atom lie within r of a point (c half the cell diagonal: the
+// cell-shaped boxes centred on the images do not overlap and lie in the ball of
+// radius r + c); integrating exp(-r) against that count from `radius` on gives
+// exp(-R)(u^3 + 3u^2 + 6u + 6) with u = R + c.
+double gamma_tail_bound(double radius, const Geo& g, double se) {
+    const double V = g.lx * g.ly * g.lz;
+    const double u = radius + 0.5 * std::sqrt(g.lx * g.lx + g.ly * g.ly + g.lz * g.lz);
+    return 4.0 * kPi / (3.0 * V) * std::exp(-radius) * (((u + 3.0) * u + 6.0) * u + 6.0) * se;
+}
+
+// the smallest radius (to 1e-6 A, bisection) whose bound is at most `tail`; the
+// bound decreases with the radius (its derivative is -exp(-R) u^3)
+double gamma_cutoff(const Geo& g, double se, double tail) {
+    double lo = 0.0, hi = 1.0;
+    while (gamma_tail_bound(hi, g, se) > tail) hi *= 2.0;
+    while (hi - lo > 1e-6) {
+        const double mid = 0.5 * (lo + hi);
+        if (gamma_tail_bound(mid, g, se) > tail) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+template <typename T>
+gp_status fft_poisson_call(gp_ctx* c, const T* src_dev, T* phi_dev) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!src_dev || !phi_dev) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        if (!c->fft) {
+            c->fft = fft_create(c->g, c->s);
+            if (!c->fft) throw Err{GP_ERR_INVALID_ARG, "grid extents must be 2^a 3^b for the FFT"};
+        }
+        if (!c->fft_work) {
+            const size_t wb = fft_workspace_bytes(c->g, true);   // the FP64 size serves both precisions
+            c->fft_work = dalloc(c, wb);
+            c->fft_work_bytes = wb;
+        }
+        count_launch(5);
+        fft_poisson<T>(c->fft, src_dev, phi_dev, c->fft_work, c->s);
+        GP_CHECK_LAUNCH();
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
 }
 
 bool good_extent(int n) {
@@ -1092,6 +1156,7 @@ void gp_default_params(gp_params* p) {
     p->sweep_shape = -1;
     p->nu_coarse = 0;
     p->kind = 0;
+    p->gamma_tail = 1e-13;
     p->beta = 2.4;
     p->zlim = 0.0;
 }
@@ -1143,7 +1208,7 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
     try {
         if (!params || n_atoms < 0 || (n_atoms > 0 && !atoms_dev)) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
         gp_params p = *params;
-        if (!(p.rcut > 0 && p.rcut <= c->g.lx && p.rcut <= c->g.ly && p.rcut <= c->g.lz))
+        if (p.kind == 0 && !(p.rcut > 0 && p.rcut <= c->g.lx && p.rcut <= c->g.ly && p.rcut <= c->g.lz))
             throw Err{GP_ERR_INVALID_ARG, "rcut must be positive and not exceed the cell"};
         if (!(p.w > 0) || !(p.eps0 >= 1.0)) throw Err{GP_ERR_INVALID_ARG, "need w > 0 and eps0 >= 1"};
         if (p.precision != 0 && p.precision != 1) throw Err{GP_ERR_INVALID_ARG, "precision must be 0 or 1"};
@@ -1159,7 +1224,8 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         if (p.kind < 0 || p.kind > 2)
             throw Err{GP_ERR_INVALID_ARG, "kind must be 0 (erf product), 1 (Eq. 9-10) or 2 (Eq. 19)"};
         if (p.kind != 0 && !(p.beta > 0.0)) throw Err{GP_ERR_INVALID_ARG, "beta must be positive"};
-        if (p.kind != 0 && !(p.rcut > 1.0)) throw Err{GP_ERR_INVALID_ARG, "rcut must exceed the 1 A taper"};
+        if (p.kind != 0 && !(p.gamma_tail > 0.0 && p.gamma_tail <= 1e-3))
+            throw Err{GP_ERR_INVALID_ARG, "gamma_tail must be in (0, 1e-3]"};
         if (p.kind != 0 && n_atoms > 0 && c->rvdw_n != n_atoms)
             throw Err{GP_ERR_STATE, "kinds 1 and 2 need gp_set_vdw_radii for the same number of atoms"};
         std::string why;
@@ -1191,7 +1257,20 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         }
         GP_CHECK_LAUNCH();
         Atoms at{c->atoms, c->atoms32, nullptr, n_atoms};
-        const DielParams dp = make_diel(p.eps0, p.r0, p.w, p.rcut, p.kind, p.beta, p.zlim);
+        DielParams dp = make_diel(p.eps0, p.r0, p.w, p.rcut, p.kind, p.beta, p.zlim);
+        c->stats.gamma_cutoff = 0.0;
+        if (p.kind != 0) {
+            // Eq. 9 sums over every image: take those within the radius where the
+            // bound on the rest falls below gamma_tail, and the image range that reaches it
+            double se = 0.0;
+            for (int a = 0; a < n_atoms; ++a) se += std::exp(c->rvdw_host[a]);
+            dp.rcut = n_atoms > 0 ? gamma_cutoff(c->g, se, p.gamma_tail) : 1.0;
+            dp.mx = (int)std::ceil(dp.rcut / c->g.lx);
+            dp.my = (int)std::ceil(dp.rcut / c->g.ly);
+            dp.mz = (int)std::ceil(dp.rcut / c->g.lz);
+            c->stats.gamma_cutoff = dp.rcut;
+        }
+        c->dp = dp;
         // switching-function tables for these r0, w (when the tabulated range is away from d = 0)
         SwTables tb{};
         if (p.kind == 0 && p.r0 - 4.0 * p.w > 0.0 && p.r0 + 6.0 * p.w <= p.rcut) {
@@ -1260,6 +1339,7 @@ gp_status gp_set_vdw_radii(gp_ctx* c, const double* radii_dev, int n_atoms) {
         }
         GP_CUDA(cudaMemcpyAsync(c->rvdw, radii_dev, sizeof(double) * n_atoms, cudaMemcpyDeviceToDevice, c->s));
         GP_CUDA(cudaStreamSynchronize(c->s));
+        c->rvdw_host = hr;
         c->rvdw_n = n_atoms;
         return GP_OK;
     } catch (const Err& e) {
@@ -1366,8 +1446,7 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
             GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->s));
             Atoms at{c->atoms, c->atoms32, gauss_dev, n};
-            const DielParams dp =
-                make_diel(c->prm.eps0, c->prm.r0, c->prm.w, c->prm.rcut, c->prm.kind, c->prm.beta, c->prm.zlim);
+            const DielParams dp = c->dp;
             {
                 ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
                 if (c->prm.kind != 0)
@@ -1448,26 +1527,11 @@ gp_status gp_residual6(gp_ctx* c, const double* rho_dev, const double* phi_dev, 
 }
 
 gp_status gp_fft_poisson(gp_ctx* c, const double* src_dev, double* phi_dev) {
-    if (!c) return GP_ERR_INVALID_ARG;
-    try {
-        if (!src_dev || !phi_dev) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
-        if (!c->fft) {
-            c->fft = fft_create(c->g, c->s);
-            if (!c->fft) throw Err{GP_ERR_INVALID_ARG, "grid extents must be 2^a 3^b for the FFT"};
-        }
-        if (!c->fft_work) {
-            const size_t wb = fft_workspace_bytes(c->g, true);
-            c->fft_work = dalloc(c, wb);
-            c->fft_work_bytes = wb;
-        }
-        count_launch(5);
-        fft_poisson<double>(c->fft, src_dev, phi_dev, c->fft_work, c->s);
-        GP_CHECK_LAUNCH();
-        GP_CUDA(cudaStreamSynchronize(c->s));
-        return GP_OK;
-    } catch (const Err& e) {
-        return fail(c, e);
-    }
+    return fft_poisson_call<double>(c, src_dev, phi_dev);
+}
+
+gp_status gp_fft_poisson_f32(gp_ctx* c, const float* src_dev, float* phi_dev) {
+    return fft_poisson_call<float>(c, src_dev, phi_dev);
 }
 
 gp_status gp_get_eps(gp_ctx* c, double* eps_dev) {

@@ -75,6 +75,7 @@ struct DielParams {
     double zlim;      // kind 2: atoms with z <= zlim exclude the solvent below them (Eq. 19)
     double esat;      // kind 2: growing exponent beyond which eps = 1 exactly (ln(eps0-1)+37)/(2 beta)
     int kind;
+    int mx, my, mz;   // kinds 1, 2: images n in [-m, m] per axis reach every point within rcut
 };
 
 inline DielParams make_diel(double eps0, double r0, double w, double rcut, int kind = 0, double beta = 2.4,
@@ -88,6 +89,7 @@ inline DielParams make_diel(double eps0, double r0, double w, double rcut, int k
     p.iw = 1.0 / w;
     p.sp_norm = 1.0 / (w * 1.7724538509055160273);
     p.tiny = 5.5e-17 / (eps0 - 1.0 > 0.0 ? eps0 - 1.0 : 1.0);
+    p.mx = p.my = p.mz = 1;
     return p;
 }
 

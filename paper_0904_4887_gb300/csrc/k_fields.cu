@@ -786,26 +786,60 @@ dim3 tile_grid_ez(const Geo& g) {
 }
 
 // ----------------------------------------------------------------- eps, Eq. 9-10 and Eq. 19 (dummy density)
-// gamma(r) = sum over atoms and images of exp(-(d - rvdw_a)) T(d) (Eq. 9), T the
-// quintic taper from 1 at rcut - 1 A to 0 at rcut (keeps eps smooth in R),
+// gamma(r) = sum over atoms and every periodic image of exp(-(d - rvdw_a)) (Eq. 9),
+// taken over the images within p.rcut: the host picks that radius so that a
+// proven bound on the dropped tail is below the requested tolerance (1e-13 by
+// default), which is why the image range p.mx, p.my, p.mz may span several cells.
 // eps = 1 + (eps0 - 1)/2 (1 + (1 - gamma^(2b))/(1 + gamma^(2b))) = 1 + (eps0 - 1)/(1 + gamma^(2b))
 // (Eq. 10), and the factor d eps/d gamma = -(eps0 - 1) 2b gamma^(2b-1)/(1 + gamma^(2b))^2 of
-// the atomic derivative d eps/d R_a = (d eps/d gamma) exp(-(d - rvdw)) (T - T') (r - R_a)/d,
+// the atomic derivative d eps/d R_a = (d eps/d gamma) exp(-(d - rvdw)) (r - R_a)/d,
 // Eq. 12 with the sign that differentiating Eq. 9-10 gives (moving an atom towards r
 // raises gamma and lowers eps).
 // Kind 2 (Eq. 19): an atom with z_a <= zlim contributes, at points with z < z_a (both
 // inside the cell), exp(+(d - rvdw)) from its nearest image with no cut-off; once such
 // an exponent reaches esat, eps = 1 and d eps/d gamma = 0 there ("saturated"). FP64.
-constexpr double kTaper = 1.0;
-
-__device__ __forceinline__ void taper_fn(double d, double rcut, double& T, double& dT) {
-    double u = (d - (rcut - kTaper)) * (1.0 / kTaper);
-    u = fmin(fmax(u, 0.0), 1.0);
-    T = 1.0 - u * u * u * (10.0 - 15.0 * u + 6.0 * u * u);
-    dT = -30.0 * u * u * (1.0 - u) * (1.0 - u) * (1.0 / kTaper);
-}
+//
+// The candidates (atom a, image n) are numbered q = a * nimg + im and culled against
+// the tile's box MAXE at a time; the survivors go to shared memory.
 
 __device__ __forceinline__ double min_image(double v, double L) { return v - L * rint(v / L); }
+
+// image `im` of the (2 mx + 1)(2 my + 1)(2 mz + 1) images of wrapped atom a
+__device__ __forceinline__ void gimage32(const float4* w32, int a, int im, const Geo& g, const DielParams& p,
+                                         float& cx, float& cy, float& cz) {
+    const int nxi = 2 * p.mx + 1, nyi = 2 * p.my + 1;
+    const float4 w = w32[a];
+    cx = w.x + (float)(im % nxi - p.mx) * g.lxf;
+    cy = w.y + (float)((im / nxi) % nyi - p.my) * g.lyf;
+    cz = w.z + (float)(im / (nxi * nyi) - p.mz) * g.lzf;
+}
+
+__device__ __forceinline__ void gimage64(const double* w64, int a, int im, const Geo& g, const DielParams& p,
+                                         double& cx, double& cy, double& cz) {
+    const int nxi = 2 * p.mx + 1, nyi = 2 * p.my + 1;
+    cx = w64[3 * a + 0] + (im % nxi - p.mx) * g.lx;
+    cy = w64[3 * a + 1] + ((im / nxi) % nyi - p.my) * g.ly;
+    cz = w64[3 * a + 2] + (im / (nxi * nyi) - p.mz) * g.lz;
+}
+
+// cull candidates [q0, q0 + MAXE) of the tile into ec / eatom (ne survivors)
+__device__ __forceinline__ void cull_gamma(const Tile& t, const Geo& g, const Atoms& at, const DielParams& p,
+                                           const double* rvdw, long q0, long nq, int nimg, float rcf, bool eq19,
+                                           double (*ec)[5], int* eatom, int* ne) {
+    for (long q = q0 + threadIdx.x; q < min(q0 + MAXE, nq); q += TT) {
+        const int a = (int)(q / nimg), im = (int)(q % nimg);
+        float fx, fy, fz;
+        gimage32(at.w32, a, im, g, p, fx, fy, fz);
+        if (box_d2(t, fx, fy, fz) < rcf * rcf) {
+            const int s = atomicAdd(ne, 1);
+            gimage64(at.w64, a, im, g, p, ec[s][0], ec[s][1], ec[s][2]);
+            ec[s][3] = rvdw[a];
+            const double za = at.w64[3 * a + 2];
+            ec[s][4] = (eq19 && za <= p.zlim) ? za : -1.0;
+            if (eatom) eatom[s] = a;
+        }
+    }
+}
 
 __global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielParams p, const double* rvdw,
                                                         double* eps64, double* fe64, float* eps32) {
@@ -820,24 +854,14 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielPar
     const double rc2 = p.rcut * p.rcut;
     const float rcf = (float)p.rcut + kMargin;
     const bool eq19 = p.kind == 2;
+    const int nimg = (2 * p.mx + 1) * (2 * p.my + 1) * (2 * p.mz + 1);
+    const long nq = (long)at.n * nimg;
     double gam = 0.0;
     bool sat = false;
-    for (int a0 = 0; a0 < at.n; a0 += ACH) {
+    for (long q0 = 0; q0 < nq; q0 += MAXE) {
         if (threadIdx.x == 0) ne = 0;
         __syncthreads();
-        const int na = min(ACH, at.n - a0);
-        for (int q = threadIdx.x; q < na * 27; q += TT) {
-            const int a = a0 + q / 27, im = q % 27;
-            float fx, fy, fz;
-            image32(at.w32, a, im, g, fx, fy, fz);
-            if (box_d2(t, fx, fy, fz) < rcf * rcf) {
-                const int s = atomicAdd(&ne, 1);
-                image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
-                ec[s][3] = rvdw[a];
-                const double za = at.w64[3 * a + 2];
-                ec[s][4] = (eq19 && za <= p.zlim) ? za : -1.0;
-            }
-        }
+        cull_gamma(t, g, at, p, rvdw, q0, nq, nimg, rcf, eq19, ec, nullptr, &ne);
         __syncthreads();
         const int m = ne;
         if (valid)
@@ -845,12 +869,7 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielPar
                 if (z < ec[e][4]) continue;                 // below a lower atom: the growing term instead
                 const double dx = x - ec[e][0], dy = y - ec[e][1], dz = z - ec[e][2];
                 const double d2 = dx * dx + dy * dy + dz * dz;
-                if (d2 < rc2) {
-                    const double d = sqrt(d2);
-                    double T, dT;
-                    taper_fn(d, p.rcut, T, dT);
-                    gam += exp(ec[e][3] - d) * T;
-                }
+                if (d2 < rc2) gam += exp(ec[e][3] - sqrt(d2));
             }
         __syncthreads();
     }
@@ -883,8 +902,8 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielPar
 
 // S_a = sum_i W_i (d eps/d gamma)_i (d gamma_i / d R_a), with W_i = (1/2) sum over the six
 // faces of i of (grad_f phi)^2, so that G_eps_a = -h^3/(8 pi) S_a (applied in
-// k_forces_finish). d gamma/d R_a: exp(-(d - rvdw)) (T - T') (r - R_a)/d per decaying
-// image term, -exp(d - rvdw) (r - R_a)/d for a growing (kind 2) term. One warp per
+// k_forces_finish). d gamma/d R_a: exp(-(d - rvdw)) (r - R_a)/d per decaying image
+// term, -exp(d - rvdw) (r - R_a)/d for a growing (kind 2) term. One warp per
 // (atom, image) entry, and for kind 2 one warp per lower atom, over the tile's 512
 // points; FP64.
 __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielParams p, const double* rvdw,
@@ -924,23 +943,12 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielPa
     const double rc2 = p.rcut * p.rcut;
     const float rcf = (float)p.rcut + kMargin;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int a0 = 0; a0 < at.n; a0 += ACH) {
+    const int nimg = (2 * p.mx + 1) * (2 * p.my + 1) * (2 * p.mz + 1);
+    const long nq = (long)at.n * nimg;
+    for (long q0 = 0; q0 < nq; q0 += MAXE) {
         if (threadIdx.x == 0) ne = 0;
         __syncthreads();
-        const int na = min(ACH, at.n - a0);
-        for (int q = threadIdx.x; q < na * 27; q += TT) {
-            const int a = a0 + q / 27, im = q % 27;
-            float fx, fy, fz;
-            image32(at.w32, a, im, g, fx, fy, fz);
-            if (box_d2(t, fx, fy, fz) < rcf * rcf) {
-                const int s = atomicAdd(&ne, 1);
-                image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
-                ec[s][3] = rvdw[a];
-                const double za = at.w64[3 * a + 2];
-                ec[s][4] = (eq19 && za <= p.zlim) ? za : -1.0;
-                eatom[s] = a;
-            }
-        }
+        cull_gamma(t, g, at, p, rvdw, q0, nq, nimg, rcf, eq19, ec, eatom, &ne);
         __syncthreads();
         const int m = ne;
         for (int e = warp; e < m; e += TT / 32) {
@@ -958,9 +966,7 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielPa
                 const double d2 = dx * dx + dy * dy + dz * dz;
                 if (!(d2 < rc2 && d2 > 0.0)) continue;
                 const double d = sqrt(d2);
-                double T, dT;
-                taper_fn(d, p.rcut, T, dT);
-                const double c = W * exp(rv - d) * (T - dT) / d;
+                const double c = W * exp(rv - d) / d;
                 fx += c * dx; fy += c * dy; fz += c * dz;
             }
             fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);

@@ -35,7 +35,7 @@ class gp_params(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("accel", ctypes.c_int), ("restart", ctypes.c_int),
                 ("band_vcycles", ctypes.c_int), ("graph_outer", ctypes.c_int),
                 ("sweep_shape", ctypes.c_int), ("kind", ctypes.c_int), ("beta", ctypes.c_double),
-                ("zlim", ctypes.c_double), ("nu_coarse", ctypes.c_int)]
+                ("zlim", ctypes.c_double), ("nu_coarse", ctypes.c_int), ("gamma_tail", ctypes.c_double)]
 
 
 class gp_stats(ctypes.Structure):
@@ -44,7 +44,7 @@ class gp_stats(ctypes.Structure):
                 ("band_first", ctypes.c_int), ("band_dirichlet", ctypes.c_int), ("dry_planes", ctypes.c_int),
                 ("wet_fraction", ctypes.c_double), ("b_norm", ctypes.c_double), ("residual", ctypes.c_double),
                 ("history_len", ctypes.c_int), ("history", ctypes.c_double * GP_HISTORY),
-                ("sweep_shape", ctypes.c_int)]
+                ("sweep_shape", ctypes.c_int), ("gamma_cutoff", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -59,6 +59,7 @@ _SIGNATURES = {
     "gp_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gp_residual6": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double)]),
     "gp_fft_poisson": (ctypes.c_int, [_P, _P, _P]),
+    "gp_fft_poisson_f32": (ctypes.c_int, [_P, _P, _P]),
     "gp_get_eps": (ctypes.c_int, [_P, _P]),
     "gp_get_plane_max": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "gp_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(gp_stats)]),
@@ -158,6 +159,18 @@ def _ptr(t, numel=None, what="array"):
         raise ValueError("%s: expected %d float64 values, got %d" % (what, numel, t.numel()))
     if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
         raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ptr32(t, numel, what="array"):
+    """Device pointer of a contiguous float32 CUDA tensor of `numel` values."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if t.numel() != numel:
+        raise ValueError("%s: expected %d float32 values, got %d" % (what, numel, t.numel()))
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -263,6 +276,10 @@ class Context:
 
     def gp_fft_poisson(self, src, out):
         return self._check(self._lib.gp_fft_poisson(self._h, self._field(src, "src"), self._field(out, "out")))
+
+    def gp_fft_poisson_f32(self, src, out):
+        return self._check(self._lib.gp_fft_poisson_f32(self._h, _ptr32(src, self._npts, "src"),
+                                                        _ptr32(out, self._npts, "out")))
 
     def gp_get_eps(self, out):
         return self._check(self._lib.gp_get_eps(self._h, self._field(out, "out")))

@@ -83,6 +83,12 @@ class GPSolver:
         self.ctx.gp_fft_poisson(src.contiguous(), out)
         return out
 
+    def fft_poisson_f32(self, src):
+        """The FP32 instance of the vacuum solve (the one the mixed split uses)."""
+        out = torch.zeros(self.shape, dtype=torch.float32, device=self.device)
+        self.ctx.gp_fft_poisson_f32(src.contiguous(), out)
+        return out
+
     def eps(self):
         out = self.zeros()
         self.ctx.gp_get_eps(out)

@@ -2,7 +2,9 @@
 bounded mbarrier waits are made to expire (the test hook sets their poll
 budget to zero, so the first wait gives up at once), the kernel drains its own
 copies with the normal bound and records the expiry, gp_solve reports
-GP_ERR_TIMEOUT, and a new context on the same GPU works normally."""
+GP_ERR_TIMEOUT after the first outer correction (no V-cycle runs on the
+undefined fields that follow), and a new context on the same GPU works
+normally."""
 import os
 import sys
 
@@ -37,6 +39,10 @@ def test_expired_smoother_wait_reports_timeout_and_gpu_stays_usable(shape):
             s.solve(_t(rho), tol=1e-8)
         assert e.value.status == 5                                # GP_ERR_TIMEOUT
         assert "wait expired" in str(e.value)
+        # the solve stops at the first residual readback after the expiry: only
+        # the initial residual is recorded, and no second correction ran
+        st = s.stats()
+        assert st.outer_iterations == 1 and st.history_len == 1
         del s
     finally:
         del os.environ["GP_TEST_SWEEP_WAIT_POLLS"]

@@ -1,0 +1,112 @@
+"""Errors of every solver path against the FP64 oracle's own answer.
+
+The oracle solves A phi = -4 pi rho to 1e-14 (1e-13 at full size) and computes
+E = h^3/2 sum rho phi (Eq. 4) and the forces -dE/dR (Eq. 11) from ITS OWN phi.
+Each GPU path (mixed full box, mixed dry/wet split, FP64 split, FP64 full box)
+solves to a relative residual of 1e-8, 1e-10 or 1e-12 and returns phi, E and
+the forces from the library's kernels. The test compares the two results:
+phi element by element, E, and every force component, relative to the
+largest component. The targets are 1e-8 relative for E and 1e-6 for the
+forces; phi's error is stated (printed with -s), since a residual of tol does
+not bound phi's error by tol (the operator's condition number is ~1e5).
+
+The full-size case is the 192x192x384, 288-atom mixed-precision workload that
+bench.py times, at the bench's tolerance 1e-8 and at 1e-10, with the forces of
+8 seeded atoms.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W
+from oracle import gp_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+PATHS = {"mixed_fullbox": dict(precision=1, split=0), "mixed_split": dict(precision=1, split=1),
+         "fp64_split": dict(precision=0, split=1), "fp64_fullbox": dict(precision=0, split=0)}
+
+
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0904_4887_gb300 import GPSolver
+    return GPSolver
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _gauss(at):
+    return np.stack([at.Z, at.sigma_core, at.sigma_cloud], axis=1)
+
+
+def _oracle_answer(grid, cell, at, tol, atoms=None):
+    h = O.spacing(grid, cell)
+    eps = O.dielectric(grid, cell, at.pos)
+    rho = O.charge_density(grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud)
+    phi, info = O.solve(rho, eps, h, tol=tol)
+    E = O.energy(rho, phi, grid, cell)
+    Ge, Gr = O.energy_gradient(phi, grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud, atoms=atoms)
+    return rho, phi, E, -(Ge + Gr), info
+
+
+def _errors(s, at, rho, phi_o, E_o, F_o, tol, sel):
+    phi = s.solve(_t(rho), tol=tol)
+    E, _, F = s.energy_forces(phi, _t(rho), _t(_gauss(at)))
+    F = F.cpu().numpy()[sel]
+    Fo = F_o[sel]
+    e_phi = float(np.max(np.abs(phi.cpu().numpy() - phi_o)) / np.max(np.abs(phi_o)))
+    e_E = abs(E - E_o) / abs(E_o)
+    e_F = float(np.max(np.abs(F - Fo)) / np.max(np.abs(Fo)))
+    return e_phi, e_E, e_F, s.stats().residual
+
+
+@pytest.fixture(scope="module")
+def small():
+    grid, cell = (32, 32, 64), (10.0, 10.0, 20.0)
+    at = W.slab_atoms(cell, 2, 3, seed=0)
+    rho, phi, E, F, _ = _oracle_answer(grid, cell, at, 1e-14)
+    return grid, cell, at, rho, phi, E, F
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+@pytest.mark.parametrize("tol", [1e-8, 1e-10, 1e-12])
+def test_path_errors_against_the_oracle_answer(small, path, tol):
+    GPSolver = _gpu()
+    grid, cell, at, rho, phi_o, E_o, F_o = small
+    s = GPSolver(grid, cell, **PATHS[path])
+    s.set_atoms(_t(at.pos))
+    sel = np.arange(len(at.pos))
+    e_phi, e_E, e_F, res = _errors(s, at, rho, phi_o, E_o, F_o, tol, sel)
+    print("\n%-13s tol %.0e: residual %.2e  phi %.2e  E %.2e  F %.2e" % (path, tol, res, e_phi, e_E, e_F))
+    assert res <= tol
+    assert e_E < 1e-8 and e_F < 1e-6
+    if tol <= 1e-10:
+        assert e_phi < 1e-7
+    if tol <= 1e-12:
+        assert e_phi < 1e-9 and e_E < 1e-11 and e_F < 1e-9
+
+
+def test_headline_workload_errors_at_full_size():
+    """The bench's workload and solver (mixed precision, full box, autotuned
+    smoother) at tol 1e-8 and 1e-10 against the oracle solved to 1e-13 on the
+    host (a few minutes of NumPy)."""
+    GPSolver = _gpu()
+    w = W.WORKLOADS["mixed_192x192x384"]
+    at = W.workload_atoms(w, seed=0)
+    sel = np.random.default_rng(5).choice(len(at.pos), 8, replace=False)
+    rho, phi_o, E_o, F_o, info = _oracle_answer(w.grid, w.cell, at, 1e-13, atoms=sel)
+    assert info.residual <= 1e-13
+    s = GPSolver(w.grid, w.cell, precision=1, split=0, levels=w.levels)
+    s.set_atoms(_t(at.pos))
+    for tol, phi_bound in ((1e-8, 1e-5), (1e-10, 1e-7)):
+        e_phi, e_E, e_F, res = _errors(s, at, rho, phi_o, E_o, F_o, tol, sel)
+        print("\nmixed_192x192x384 tol %.0e: residual %.2e  phi %.2e  E %.2e  F %.2e (8 atoms)"
+              % (tol, res, e_phi, e_E, e_F))
+        assert res <= tol
+        assert e_E < 1e-8 and e_F < 1e-6 and e_phi < phi_bound

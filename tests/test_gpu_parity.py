@@ -305,15 +305,34 @@ def _radii(Z):
 
 @pytest.mark.parametrize("k", range(len(SMALL)))
 def test_gamma_dielectric_matches_oracle(small_cases, k):
+    """Eq. 9-10 over every image within the tail-bounded radius (several cells
+    wide on these grids): the library picks the oracle's radius and matches its
+    eps element by element."""
     GPSolver = _gpu()
     (at, h, eps, rho), grid, cell = small_cases[k]
-    rc = min(7.0, 0.99 * min(cell))
-    p = O.GammaParams(rcut=rc)
+    p = O.GammaParams()
     rv = _radii(at.Z)
     ref = O.dielectric_gamma(grid, cell, at.pos, rv, p)
-    s = GPSolver(grid, cell, precision=0, kind=1, beta=p.beta, rcut=rc)
+    s = GPSolver(grid, cell, precision=0, kind=1, beta=p.beta)
     s.set_atoms(_t(at.pos), radii=_t(rv))
+    assert abs(s.stats().gamma_cutoff - O.gamma_cutoff(cell, rv, p.tail)) < 1e-5
+    assert s.stats().gamma_cutoff > 2.0 * max(cell)
     assert _rel(s.eps().cpu().numpy(), ref) < 1e-13
+
+
+def test_gamma_tail_parameter_moves_the_radius():
+    """A looser tail bound shortens the radius the way the oracle's bound says,
+    and eps follows the oracle at that radius too."""
+    GPSolver = _gpu()
+    grid, cell = (16, 8, 24), (7.0, 6.5, 12.0)
+    at = W.slab_atoms(cell, 1, 2, seed=0)
+    rv = _radii(at.Z)
+    p = O.GammaParams(tail=1e-6)
+    s = GPSolver(grid, cell, precision=0, kind=1, beta=p.beta, gamma_tail=p.tail)
+    s.set_atoms(_t(at.pos), radii=_t(rv))
+    rc = O.gamma_cutoff(cell, rv, p.tail)
+    assert abs(s.stats().gamma_cutoff - rc) < 1e-5 and rc < O.gamma_cutoff(cell, rv, 1e-13) - 5.0
+    assert _rel(s.eps().cpu().numpy(), O.dielectric_gamma(grid, cell, at.pos, rv, p)) < 1e-13
 
 
 def test_gamma_energy_and_forces_match_oracle():
@@ -322,10 +341,10 @@ def test_gamma_energy_and_forces_match_oracle():
     GPSolver = _gpu()
     grid, cell = (32, 32, 48), (10.0, 10.0, 15.0)
     at, h, _, rho = _case(grid, cell, 2, 3, seed=2)
-    p = O.GammaParams(rcut=9.0)
+    p = O.GammaParams()
     rv = _radii(at.Z)
     eps = O.dielectric_gamma(grid, cell, at.pos, rv, p)
-    s = GPSolver(grid, cell, precision=0, kind=1, beta=p.beta, rcut=p.rcut)
+    s = GPSolver(grid, cell, precision=0, kind=1, beta=p.beta)
     s.set_atoms(_t(at.pos), radii=_t(rv))
     phi = s.solve(_t(rho), tol=1e-13)
     ref, _ = O.solve(rho, eps, h, tol=1e-14)
@@ -337,6 +356,40 @@ def test_gamma_energy_and_forces_match_oracle():
     _, _, Fe = s.energy_forces(phi, _t(rho), None)
     assert _rel(Fe.cpu().numpy(), -Ge) < 1e-10
     assert abs(E - E2) < 1e-10 * abs(E)
+
+
+def test_gamma_forces_match_central_differences_on_the_gpu():
+    """Eq. 9-10 forces of the library against central differences (h = 1e-4 A)
+    of its own energy, every step on the GPU: the solvent term with rho frozen,
+    on 4 seeded atoms, to 1e-6 of the largest component."""
+    GPSolver = _gpu()
+    grid, cell = (32, 32, 48), (10.0, 10.0, 15.0)
+    at, h, _, rho = _case(grid, cell, 2, 3, seed=2)
+    rv = _t(_radii(at.Z))
+    s = GPSolver(grid, cell, precision=0, kind=1)
+    rho_t = _t(rho)
+
+    def J(q):
+        s.set_atoms(_t(q), radii=rv)
+        phi = s.solve(rho_t, tol=1e-13)
+        E, E2, _ = s.energy_forces(phi, rho_t, None, forces=False)
+        return 2.0 * E - E2            # the variational energy: second order in phi's error
+
+    s.set_atoms(_t(at.pos), radii=rv)
+    phi = s.solve(rho_t, tol=1e-13)
+    _, _, F = s.energy_forces(phi, rho_t, None)
+    F = F.cpu().numpy()
+    sel = np.random.default_rng(11).choice(len(at.pos), 4, replace=False)
+    d = 1e-4
+    fd = np.zeros((len(sel), 3))
+    for t_, a in enumerate(sel):
+        for c in range(3):
+            pp = at.pos.copy(); pp[a, c] += d
+            pm = at.pos.copy(); pm[a, c] -= d
+            fd[t_, c] = -(J(pp) - J(pm)) / (2 * d)
+    scale = np.max(np.abs(fd))
+    assert scale > 1e-3
+    assert np.max(np.abs(fd - F[sel])) < 1e-6 * scale
 
 
 def _eq19_setup(grid, cell, n, layers, seed=0):
@@ -352,9 +405,9 @@ def _eq19_setup(grid, cell, n, layers, seed=0):
 def test_eq19_dielectric_matches_oracle(grid, cell, n, layers):
     GPSolver = _gpu()
     at, rv, zlim = _eq19_setup(grid, cell, n, layers)
-    p = O.GammaParams(rcut=8.0)
+    p = O.GammaParams()
     ref = O.dielectric_eq19(grid, cell, at.pos, rv, zlim, p)
-    s = GPSolver(grid, cell, precision=0, kind=2, beta=p.beta, rcut=p.rcut, zlim=zlim)
+    s = GPSolver(grid, cell, precision=0, kind=2, beta=p.beta, zlim=zlim)
     s.set_atoms(_t(at.pos), radii=_t(rv))
     assert _rel(s.eps().cpu().numpy(), ref) < 1e-13
 
@@ -367,12 +420,12 @@ def test_eq19_solve_and_forces_match_oracle(split, precision):
     GPSolver = _gpu()
     grid, cell = (32, 32, 64), (10.0, 10.0, 20.0)
     at, rv, zlim = _eq19_setup(grid, cell, 2, 3, seed=1)
-    p = O.GammaParams(rcut=8.0)
+    p = O.GammaParams()
     h = O.spacing(grid, cell)
     eps = O.dielectric_eq19(grid, cell, at.pos, rv, zlim, p)
     rho = O.charge_density(grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud)
     ref, _ = O.solve(rho, eps, h, tol=1e-14)
-    s = GPSolver(grid, cell, precision=precision, split=split, kind=2, beta=p.beta, rcut=p.rcut, zlim=zlim,
+    s = GPSolver(grid, cell, precision=precision, split=split, kind=2, beta=p.beta, zlim=zlim,
                  n_dirichlet=0)
     s.set_atoms(_t(at.pos), radii=_t(rv))
     st = s.stats()
@@ -394,7 +447,7 @@ def test_gamma_needs_radii():
     from paper_0904_4887_gb300.gp import GPError
     grid, cell = (16, 8, 24), (7.0, 6.5, 12.0)
     at = W.slab_atoms(cell, 1, 2, seed=0)
-    s = GPSolver(grid, cell, kind=1, rcut=6.0)
+    s = GPSolver(grid, cell, kind=1)
     with pytest.raises(GPError):
         s.set_atoms(_t(at.pos))
     with pytest.raises(GPError):

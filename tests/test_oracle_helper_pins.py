@@ -35,21 +35,76 @@ def test_switching_derivative_matches_central_differences():
     assert np.max(np.abs(fd - O.switching_derivative(d, p))) < 1e-8
 
 
-def test_taper_is_a_c2_smoothstep():
-    """T = 1 below rcut - 1 A, 0 beyond rcut, 1/2 half way, with zero slope at
-    both ends and dT matching central differences of T."""
-    rc = 8.0
-    T, dT = O.taper(np.array([0.0, rc - 1.0, rc - 0.5, rc, rc + 3.0]), rc)
-    assert np.allclose(T, [1.0, 1.0, 0.5, 0.0, 0.0], rtol=0, atol=1e-15)
-    assert dT[0] == 0.0 and dT[1] == 0.0 and dT[3] == 0.0 and dT[4] == 0.0
-    d = np.linspace(rc - 0.99, rc - 0.01, 30)
-    e = 1e-6
-    fd = (O.taper(d + e, rc)[0] - O.taper(d - e, rc)[0]) / (2 * e)
-    assert np.max(np.abs(fd - O.taper(d, rc)[1])) < 1e-8
-    # second derivative vanishes at both ends (C2): the slope changes quadratically there
-    for end in (rc - 1.0, rc):
-        s1 = O.taper(np.array([end + 1e-4 * (1 if end < rc else -1)]), rc)[1][0]
-        assert abs(s1) < 1e-6
+def _lattice_count(r, cell, point, center):
+    """Images center + nL within distance r of `point`, counted one by one."""
+    L = np.asarray(cell)
+    K = [int(math.ceil((r + L[a]) / L[a])) + 1 for a in range(3)]
+    n = 0
+    for i in range(-K[0], K[0] + 1):
+        for j in range(-K[1], K[1] + 1):
+            for k in range(-K[2], K[2] + 1):
+                d = point - (center + np.array([i, j, k]) * L)
+                n += float(np.sqrt(d @ d)) <= r
+    return n
+
+
+def test_image_count_bound_holds():
+    """The counting step of gamma_tail_bound: at most (4 pi/3)(r + c)^3 / V
+    images of an atom lie within r of any point (c = half the cell diagonal),
+    checked by counting lattice points one by one."""
+    cell = (3.0, 4.0, 5.5)
+    V = cell[0] * cell[1] * cell[2]
+    c = 0.5 * math.sqrt(sum(x * x for x in cell))
+    rng = np.random.default_rng(2)
+    for r in (0.5, 2.0, 7.0, 13.0):
+        for _ in range(3):
+            pt, ce = rng.uniform(0, 1, 3) * cell, rng.uniform(0, 1, 3) * cell
+            assert _lattice_count(r, cell, pt, ce) <= 4.0 * math.pi / 3.0 * (r + c) ** 3 / V
+
+
+def test_gamma_cutoff_is_the_smallest_radius_meeting_the_tail():
+    """gamma_cutoff returns a radius whose bound is at most the tail, while a
+    radius 1e-5 A shorter is not; the bound falls with the radius."""
+    cell = (10.0, 10.0, 20.0)
+    rv = np.array([2.0, 1.52, 1.52, 2.0])
+    for tail in (1e-6, 1e-10, 1e-13):
+        rc = O.gamma_cutoff(cell, rv, tail)
+        assert O.gamma_tail_bound(rc, cell, rv) <= tail < O.gamma_tail_bound(rc - 1e-5, cell, rv)
+    r = np.linspace(1.0, 60.0, 100)
+    b = [O.gamma_tail_bound(x, cell, rv) for x in r]
+    assert np.all(np.diff(b) < 0)
+
+
+def test_gamma_tail_is_within_its_bound_against_a_larger_brute_force_sum():
+    """gamma (Eq. 9) from the oracle's tail-bounded image sum against an
+    independent brute-force sum over every image within the cut-off + 12 A, at
+    random points of a small cell: they differ by less than the stated bound
+    (the neglected tail), and the difference is not negligible compared with
+    it (the bound is not vacuous by orders of magnitude)."""
+    cell = (6.0, 5.0, 7.0)
+    pos = np.array([[1.0, 2.0, 3.0], [4.2, 0.7, 6.1], [3.3, 3.9, 0.4]])
+    rv = np.array([2.0, 1.52, 1.7])
+    for tail in (1e-6, 1e-13):
+        p = O.GammaParams(tail=tail)
+        rc = O.gamma_cutoff(cell, rv, tail)
+        pts = np.random.default_rng(7).uniform(0.0, 1.0, (6, 3)) * np.asarray(cell)
+        eps = O.dielectric_gamma_points(pts, cell, pos, rv, p)
+        R = rc + 12.0
+        L = np.asarray(cell)
+        K = [int(math.ceil((R + L[a]) / L[a])) + 1 for a in range(3)]
+        ii, jj, kk = np.meshgrid(*[np.arange(-K[a], K[a] + 1) for a in range(3)], indexing="ij")
+        shifts = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1) * L
+        for m, pt in enumerate(pts):
+            g = 0.0
+            for R0, r0 in zip(pos, rv):
+                d = np.linalg.norm(pt - (R0 + shifts), axis=1)
+                g += float(np.sum(np.exp(r0 - d[d < R])))
+            # invert Eq. 10 for the oracle's gamma: eps = 1 + (eps0-1)/(1 + gamma^(2 beta))
+            go = ((p.eps0 - 1.0) / (eps[m] - 1.0) - 1.0) ** (1.0 / (2.0 * p.beta))
+            diff = g - go
+            assert -1e-13 * g <= diff <= O.gamma_tail_bound(rc, cell, rv) + 1e-13 * g
+        if tail == 1e-6:
+            assert diff > 1e-4 * tail          # the neglected tail is real at this tolerance
 
 
 def test_deps_dgamma_matches_the_complex_step_derivative():

@@ -416,14 +416,15 @@ def _radii(Z):
 def test_gamma_dielectric_is_centred_on_the_vdw_radius():
     """Eq. 10: one atom, a point at |r - R| = Rvdw has gamma = 1 and eps = (1 + eps0)/2
     whatever beta; eps grows monotonically with the distance along a ray."""
-    grid, cell = (40, 40, 40), (20.0, 20.0, 20.0)          # h = 0.5
-    pos = np.array([[10.0, 10.0, 10.0]])
+    # a 40 A cell, so that the other images add below 1e-15 to gamma at the point
+    grid, cell = (80, 80, 80), (40.0, 40.0, 40.0)          # h = 0.5
+    pos = np.array([[20.0, 20.0, 20.0]])
     rv = np.array([1.5])
     for beta in (1.0, 2.4, 4.0):
-        p = O.GammaParams(beta=beta, rcut=7.0)
+        p = O.GammaParams(beta=beta)
         eps = O.dielectric_gamma(grid, cell, pos, rv, p)
-        assert abs(eps[20, 20, 23] - 0.5 * (1.0 + p.eps0)) < 1e-12     # x = 11.5: d = 1.5
-        ray = eps[20, 20, 20:34]
+        assert abs(eps[40, 40, 43] - 0.5 * (1.0 + p.eps0)) < 1e-12     # x = 21.5: d = 1.5
+        ray = eps[40, 40, 40:54]
         assert np.all(np.diff(ray) > 0)
         assert ray[0] < 1.0 + 0.1 * (p.eps0 - 1.0) and ray[-1] > p.eps0 - 1e-2
 
@@ -438,12 +439,12 @@ def test_gamma_dielectric_printed_form_equals_simplified_form():
     assert np.max(np.abs(O.eps_of_gamma(g, p) - simple)) < 1e-12 * p.eps0
 
 
-def test_gamma_dielectric_grid_equals_27_image_brute_force():
+def test_gamma_dielectric_grid_equals_the_point_evaluator():
     """Bounding-box images of the grid builder against the one-by-one evaluator."""
     grid, cell = (12, 10, 14), (8.0, 7.0, 9.0)
     at = W.slab_atoms(cell, 2, 1, seed=4)
     rv = _radii(at.Z)
-    p = O.GammaParams(rcut=6.5)
+    p = O.GammaParams()
     eps = O.dielectric_gamma(grid, cell, at.pos, rv, p)
     x, y, z = _grid_points(grid, cell)
     pts = np.stack([np.broadcast_to(x, eps.shape).ravel(), np.broadcast_to(y, eps.shape).ravel(),
@@ -458,7 +459,7 @@ def test_gamma_dielectric_gradient_matches_fd_and_fixes_eq12_sign():
     grid, cell = (16, 16, 16), (8.0, 8.0, 8.0)
     pos = np.array([[3.1, 4.2, 3.9], [5.0, 3.3, 4.6]])
     rv = np.array([1.52, 2.0])
-    p = O.GammaParams(rcut=6.0)
+    p = O.GammaParams()
     G = O.dummy_density(grid, cell, pos, rv, p)
     de = O.dielectric_gamma_gradient_atom(0, grid, cell, pos, rv, G, p)
     d = 1e-5
@@ -474,12 +475,12 @@ def test_gamma_dielectric_gradient_matches_fd_and_fixes_eq12_sign():
 
 def test_gamma_forces_match_central_differences():
     """P9 for the Eq. 9-10 dielectric: dE/dR_a (eps term, rho frozen) against central
-    differences of the variational energy J (the tapered cut-off keeps E(R)
-    smooth)."""
+    differences of the variational energy J (E(R) is smooth: the image sum's
+    cut-off drops terms below 1e-17)."""
     grid, cell = (16, 16, 24), (8.0, 8.0, 12.0)
-    at = W.slab_atoms(cell, 2, 2, seed=1)
+    at = W.slab_atoms(cell, 1, 2, seed=1)
     rv = _radii(at.Z)
-    p = O.GammaParams(rcut=7.9)
+    p = O.GammaParams()
     h = O.spacing(grid, cell)
     pos = at.pos
     rho = O.charge_density(grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud)
@@ -491,7 +492,7 @@ def test_gamma_forces_match_central_differences():
 
     eps = O.dielectric_gamma(grid, cell, pos, rv, p)
     phi, _ = O.solve(rho, eps, h, tol=1e-14)
-    sel = [0, 5]
+    sel = [0, 3]
     Ge, Gr = O.energy_gradient(phi, grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud, p=p, atoms=sel,
                                rho_moves=False, rvdw=rv)
     fd = np.zeros((len(sel), 3))
@@ -508,9 +509,9 @@ def test_gamma_forces_match_central_differences():
 
 # -------------------------------------------------------------- Eq. 19 solvent exclusion
 
-def _eq19_case(seed=0):
+def _eq19_case(seed=0, n=2):
     grid, cell = (16, 16, 32), (8.0, 8.0, 16.0)
-    at = W.slab_atoms(cell, 2, 3, seed=seed)
+    at = W.slab_atoms(cell, n, 3, seed=seed)
     zs = np.sort(at.pos[:, 2])
     zlim = 0.5 * (zs[len(zs) // 3 - 1] + zs[len(zs) // 3])  # between layers 1 and 2: layer 1 is lower
     return grid, cell, at, W.vdw_radii(at.Z), zlim
@@ -519,7 +520,7 @@ def _eq19_case(seed=0):
 def test_eq19_without_lower_atoms_is_eq10():
     """With z_lim below every atom, Eq. 19 is Eq. 9 term by term."""
     grid, cell, at, rv, _ = _eq19_case()
-    p = O.GammaParams(rcut=7.9)
+    p = O.GammaParams()
     a = O.dielectric_eq19(grid, cell, at.pos, rv, -1.0, p)
     b = O.dielectric_gamma(grid, cell, at.pos, rv, p)
     assert np.max(np.abs(a - b)) < 1e-12 * p.eps0
@@ -529,7 +530,7 @@ def test_eq19_dries_the_region_below_the_lower_layer():
     """Below the lower atoms eps saturates to 1 (dry planes); far above the slab
     it is the solvent's eps0; with Eq. 10 alone the region below stays wet."""
     grid, cell, at, rv, zlim = _eq19_case()
-    p = O.GammaParams(rcut=7.9)
+    p = O.GammaParams()
     eps = O.dielectric_eq19(grid, cell, at.pos, rv, zlim, p)
     pm = (eps - 1.0).reshape(grid[2], -1).max(axis=1)
     zmin = at.pos[:, 2].min()
@@ -547,7 +548,7 @@ def test_eq19_sign_is_plus_on_the_atom_plane():
     grid, cell = (16, 16, 16), (8.0, 8.0, 8.0)
     pos = np.array([[4.0, 4.0, 4.0]])                      # on grid point (8, 8, 8)
     rv = np.array([1.5])
-    p = O.GammaParams(rcut=7.9)
+    p = O.GammaParams()
     eps19 = O.dielectric_eq19(grid, cell, pos, rv, 5.0, p)
     eps10 = O.dielectric_gamma(grid, cell, pos, rv, p)
     assert np.max(np.abs(eps19[8] - eps10[8])) < 1e-13 * p.eps0      # the plane z = z_I
@@ -560,8 +561,8 @@ def test_eq19_sign_is_plus_on_the_atom_plane():
 def test_eq19_gradient_matches_fd():
     """d eps/d R for both branches against central differences (the atom's z is
     away from grid planes, so no point changes side)."""
-    grid, cell, at, rv, zlim = _eq19_case(seed=2)
-    p = O.GammaParams(rcut=7.9)
+    grid, cell, at, rv, zlim = _eq19_case(seed=2, n=1)
+    p = O.GammaParams()
     pos = at.pos.copy()
     a = int(np.argmin(pos[:, 2]))                              # a lower atom
     G, S = O.dummy_density_eq19(grid, cell, pos, rv, zlim, p)
@@ -578,8 +579,8 @@ def test_eq19_gradient_matches_fd():
 
 def test_eq19_forces_match_central_differences():
     """P9 for Eq. 19: dE/dR_a (eps term, rho frozen) against central differences of J."""
-    grid, cell, at, rv, zlim = _eq19_case(seed=1)
-    p = O.GammaParams(rcut=7.9)
+    grid, cell, at, rv, zlim = _eq19_case(seed=1, n=1)
+    p = O.GammaParams()
     h = O.spacing(grid, cell)
     pos = at.pos
     rho = O.charge_density(grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud)

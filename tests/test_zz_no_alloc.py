@@ -7,9 +7,9 @@ against the context-based gp_residual, twice in a row with different inputs
 (the shared scratch keeps the previous call's contents). The file name makes
 pytest collect it last.
 """
-import math
+import os
+import re
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -18,6 +18,20 @@ import workloads as W
 from oracle import gp_oracle as O
 
 pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _max_planes():
+    """GP_NOALLOC_MAX_PLANES as the header defines it (so that the limit test
+    follows any change of the limit)."""
+    text = open(os.path.join(ROOT, "include", "gp.h")).read()
+    m = re.search(r"#define\s+GP_NOALLOC_MAX_PLANES\s+(\d+)", text)
+    assert m, "GP_NOALLOC_MAX_PLANES is not defined in include/gp.h"
+    return int(m.group(1))
+
+
+G_MAX = _max_planes()
 
 
 def test_noalloc_residual_matches_gp_residual_twice():
@@ -47,12 +61,19 @@ def test_noalloc_residual_matches_gp_residual_twice():
 
 
 def test_noalloc_rejects_too_many_planes():
+    """One plane more than the scratch holds is refused before any launch; the
+    arrays are grid-sized, so even a call that went ahead would stay in bounds."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_0904_4887_gb300 import gp as G
-    x = torch.zeros(1, dtype=torch.float64, device="cuda")
-    st = G.gp_residual_noalloc((8, 8, G_MAX + 1), (8.0, 8.0, 8.0), x, x, x, x, x)
-    assert st == 1
-
-
-G_MAX = 4096
+    grid = (8, 8, G_MAX + 1)
+    n = grid[0] * grid[1] * grid[2]
+    eps = torch.ones(n, dtype=torch.float64, device="cuda")
+    rho = torch.zeros(n, dtype=torch.float64, device="cuda")
+    phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+    r = torch.full((n,), 7.0, dtype=torch.float64, device="cuda")
+    rel = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
+    st = G.gp_residual_noalloc(grid, (8.0, 8.0, 8.0 * grid[2] / 8), eps, rho, phi, r, rel)
+    torch.cuda.synchronize()
+    assert st == 1                                   # GP_ERR_INVALID_ARG
+    assert bool((r == 7.0).all()) and float(rel) == 7.0   # nothing was written
