@@ -1,6 +1,6 @@
 """Errors of every solver path against the FP64 oracle's own answer.
 
-The oracle solves A phi = -4 pi rho to 1e-14 (1e-13 at full size) and computes
+The oracle solves A phi = -4 pi rho to 1e-14 (2e-13 at full size) and computes
 E = h^3/2 sum rho phi (Eq. 4) and the forces -dE/dR (Eq. 11) from ITS OWN phi.
 Each GPU path (mixed full box, mixed dry/wet split, FP64 split, FP64 full box)
 solves to a relative residual of 1e-8, 1e-10 or 1e-12 and returns phi, E and
@@ -94,14 +94,15 @@ def test_path_errors_against_the_oracle_answer(small, path, tol):
 
 def test_headline_workload_errors_at_full_size():
     """The bench's workload and solver (mixed precision, full box, autotuned
-    smoother) at tol 1e-8 and 1e-10 against the oracle solved to 1e-13 on the
+    smoother) at tol 1e-8 and 1e-10 against the oracle solved to 2e-13 on the
     host (a few minutes of NumPy)."""
     GPSolver = _gpu()
     w = W.WORKLOADS["mixed_192x192x384"]
     at = W.workload_atoms(w, seed=0)
     sel = np.random.default_rng(5).choice(len(at.pos), 8, replace=False)
-    rho, phi_o, E_o, F_o, info = _oracle_answer(w.grid, w.cell, at, 1e-13, atoms=sel)
-    assert info.residual <= 1e-13
+    # the oracle's CG stagnates near 1e-13 at this size (132 iterations reached 1.04e-13)
+    rho, phi_o, E_o, F_o, info = _oracle_answer(w.grid, w.cell, at, 2e-13, atoms=sel)
+    assert info.residual <= 2e-13
     s = GPSolver(w.grid, w.cell, precision=1, split=0, levels=w.levels)
     s.set_atoms(_t(at.pos))
     for tol, phi_bound in ((1e-8, 1e-5), (1e-10, 1e-7)):
