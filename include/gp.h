@@ -229,6 +229,49 @@ gp_status gp_residual(gp_ctx* ctx, const double* rho_dev, const double* phi_dev,
 gp_status gp_residual6(gp_ctx* ctx, const double* rho_dev, const double* phi_dev, double mu,
                        double* r_dev, double* rel_host);
 
+/* Solve of the sixth-order operator of Sec. III (Eq. 16-18). The periodic
+ * operator is not conservative, so the system is bordered (the paper does not
+ * treat the periodic case; this is the reading used):
+ *   A6 phi + mu eps = -4 pi (rho - mean rho),   sum(phi) = 0,
+ * mu a uniform compatibility shift of the form divided by eps. phi_dev
+ * (grid-sized FP64, device) is read as the starting guess and overwritten;
+ * *mu_host (may be NULL) receives mu. Stops when ||r||_2 <= tol ||b||_2,
+ * r = b - A6 phi - mu eps, b = -4 pi (rho - mean rho) (gp_get_stats has the
+ * history). Method: flexible GMRES(restart) in FP64 on the field system with
+ * the border eliminated, right-preconditioned by `inner` steps of the 7-point
+ * multigrid-preconditioned CG in the context's precision. Uses the eps of the
+ * last gp_set_dielectric. Errors: GP_ERR_INVALID_ARG (null array, tol <= 0),
+ * GP_ERR_STATE (no dielectric), GP_ERR_NOT_NEUTRAL, GP_ERR_NOT_CONVERGED /
+ * GP_ERR_DIVERGED (phi holds the last iterate), GP_ERR_OOM (work fields are
+ * allocated on first use), GP_ERR_CUDA. */
+gp_status gp_solve6(gp_ctx* ctx, const double* rho_dev, double* phi_dev, double* mu_host, double tol);
+
+/* The adjoint of gp_solve6, which its forces need (Appendix B's argument
+ * without the symmetry of the conservative operator): the transposed bordered
+ * system
+ *   A6^T lam + nu 1 = rho - mean rho,   sum(eps lam) = 0,
+ * A6^T lam = sum_axes [-D1((D1 eps) lam) + D2(eps lam)]. lam_dev (grid-sized
+ * FP64, device) is the starting guess and the result; *nu_host (may be NULL)
+ * receives nu. Stops when ||r||_2 <= tol ||rho - mean rho||_2. Same method
+ * and errors as gp_solve6. */
+gp_status gp_adjoint6(gp_ctx* ctx, const double* rho_dev, double* lam_dev, double* nu_host, double tol);
+
+/* Energy and forces of the sixth-order solution (Eq. 4, Eq. 11 through the
+ * adjoint): with phi, mu from gp_solve6 and lam from gp_adjoint6 for the same
+ * rho and dielectric,
+ *   energy_host[0] = E = h^3/2 sum rho phi
+ *   forces_dev[a]  = -(G_eps_a + G_rho_a)   (device double[n][3], may be NULL)
+ *   G_eps_a = -h^3/2 sum_j (d eps_j / d R_a) (g_j + mu lam_j),
+ *   g = sum_axes [-D1(lam D1 phi) + lam D2 phi],
+ *   G_rho_a = h^3/2 sum_j (phi_j - 4 pi lam_j) d rho_j / d R_a (mean removed),
+ * gauss_dev as in gp_energy_forces (NULL: rho held fixed, G_rho omitted).
+ * energy_host (double[1]) may be NULL; lam_dev may be NULL when forces_dev is.
+ * Errors: GP_ERR_INVALID_ARG (null phi or rho, mu not finite, forces without
+ * lam), GP_ERR_STATE (no dielectric), GP_ERR_OOM, GP_ERR_CUDA. */
+gp_status gp_energy_forces6(gp_ctx* ctx, const double* phi_dev, double mu, const double* lam_dev,
+                            const double* rho_dev, const double* gauss_dev, double* energy_host,
+                            double* forces_dev);
+
 /* Vacuum solve L phi = src with the 7-point Laplacian (eps = 1), by the
  * hand-written FFT (Eq. 15 with the symbol of the discrete operator); the
  * k = 0 mode is dropped so phi has mean zero. src_dev, phi_dev grid-sized

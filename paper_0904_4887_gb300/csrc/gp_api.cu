@@ -205,6 +205,12 @@ struct gp_ctx {
     int k_m = 0;
     int k_bytes = 0;
     std::vector<void*> misc;
+    // sixth-order operator (Sec. III): D1 eps per axis, work fields
+    double* f6_d1e = nullptr;      // 3 n: D1 eps, valid for eps_version f6_d1e_version
+    double* f6_r = nullptr;        // n: residual / operator output
+    double* f6_w = nullptr;        // n: force weights
+    double* f6_t3 = nullptr;       // 3 n: lam D1 phi per axis
+    long eps_version = 0, f6_d1e_version = -1;
 
     // CUDA graphs: captured on a library stream that is ordered after / before the user's stream
     bool use_graphs = true;
@@ -1067,6 +1073,220 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
     return result;
 }
 
+// ------------------------------------------------------------ sixth-order solve (Sec. III, Eq. 16-18)
+// The periodic sixth-order operator is not conservative, so its system carries
+// a border (a reading of the paper, which is silent on the periodic case):
+//   forward   A6 phi + mu eps = -4 pi (rho - mean rho),   sum(phi) = 0
+//   adjoint   A6^T lam + nu 1 = rho - mean rho,           sum(eps lam) = 0
+// Eliminating the border, the field solves P A6 phi = P b on zero-mean fields,
+// P v = v - (sum v / sum eps) eps (Q v = v - mean(v) and sum(eps lam) = 0 for the
+// adjoint), and the border value is the removed multiple. Flexible GMRES in
+// FP64 on that projected system, right-preconditioned by the 7-point multigrid
+// (`inner` MG-preconditioned CG steps in the context's working precision): both
+// operators discretise div(eps grad), which is self-adjoint, so A7^-1 serves the
+// forward and the transposed system alike. Device scalars used: 40..42 rho
+// statistics, 44 sum of the last operator output, 45/46 sums of z and eps z,
+// 47 n, 48..50 eps statistics (48 = sum eps).
+constexpr int kS6Rho = 40, kS6Out = 44, kS6Z = 45, kS6N = 47, kS6Eps = 48;
+
+void ensure_fd6(gp_ctx* c, bool transpose) {
+    if (!c->f6_r) c->f6_r = (double*)dalloc(c, sizeof(double) * c->n);
+    if (transpose) {
+        if (!c->f6_d1e) c->f6_d1e = (double*)dalloc(c, sizeof(double) * 3 * c->n);
+        if (c->f6_d1e_version != c->eps_version) {
+            ProfScope ps(c, GP_PROF_SETUP, 1);
+            launch_fd6_d1(c->g, c->eps64, nullptr, c->f6_d1e, c->s);
+            c->f6_d1e_version = c->eps_version;
+        }
+    }
+    GP_CHECK_LAUNCH();
+}
+
+// y = sb (rho - mean rho) + sa Op x, Op = A6 or A6^T, then projected (P or Q);
+// scal[kS6Out] holds sum(y) before the projection
+void fd6_operator(gp_ctx* c, const double* x, const double* rho, double sb, double sa, double* y, bool transpose) {
+    ProfScope ps(c, GP_PROF_KRYLOV, 3);
+    if (transpose)
+        launch_fd6_apply_t(c->g, x, c->eps64, c->f6_d1e, rho, sb, c->scal + kS6Rho, sa, y, c->partial, c->s);
+    else
+        launch_fd6_apply(c->g, x, c->eps64, rho, sb, c->scal + kS6Rho, sa, y, c->partial, c->s);
+    launch_finalize(c->partial, kReduceBlocks, 1, c->scal + kS6Out, c->s);
+    if (transpose) launch_fd6_sub_ratio(c->n, y, nullptr, c->scal + kS6Out, c->scal + kS6N, c->s);
+    else launch_fd6_sub_ratio(c->n, y, c->eps64, c->scal + kS6Out, c->scal + kS6Eps, c->s);
+}
+
+// z = M v with the constant of z fixed by the constraint (mean zero forward,
+// sum(eps z) = 0 for the adjoint)
+void fd6_fix_constant(gp_ctx* c, double* z, bool transpose) {
+    launch_fd6_to64<double>(c->n, z, c->eps64, z, c->partial, c->s);
+    launch_finalize(c->partial, kReduceBlocks, 2, c->scal + kS6Z, c->s);
+    if (transpose) launch_fd6_sub_ratio(c->n, z, nullptr, c->scal + kS6Z + 1, c->scal + kS6Eps, c->s);
+    else launch_fd6_sub_ratio(c->n, z, nullptr, c->scal + kS6Z, c->scal + kS6N, c->s);
+}
+
+template <typename T>
+void fd6_precondition(gp_ctx* c, const double* v, double* z, bool transpose) {
+    Hier<T>& F = full_hier<T>(c);
+    {
+        ProfScope ps(c, GP_PROF_MISC, 1);
+        launch_cast_eps<T>(c->n, v, F.r, c->s);
+    }
+    pcg<T>(c, F, c->prm.inner);
+    ProfScope ps(c, GP_PROF_MISC, 3);
+    launch_fd6_to64<T>(c->n, F.x, c->eps64, z, c->partial, c->s);
+    launch_finalize(c->partial, kReduceBlocks, 2, c->scal + kS6Z, c->s);
+    if (transpose) launch_fd6_sub_ratio(c->n, z, nullptr, c->scal + kS6Z + 1, c->scal + kS6Eps, c->s);
+    else launch_fd6_sub_ratio(c->n, z, nullptr, c->scal + kS6Z, c->scal + kS6N, c->s);
+    GP_CHECK_LAUNCH();
+}
+
+template <typename T>
+gp_status solve6_impl(gp_ctx* c, const double* rho, double* x, double tol, bool transpose, double* border) {
+    gp_stats& st = c->stats;
+    st.outer_iterations = 0; st.inner_iterations = 0; st.vcycles = 0; st.history_len = 0;
+    st.residual = NAN;
+    const long n = c->n;
+    ensure_fd6(c, transpose);
+    const int m = std::min(std::max(c->prm.restart, 1), kMaxKrylov - 1);
+    ensure_krylov<double>(c, m);
+    auto Vp = [&](int j) { return reinterpret_cast<double*>(c->kV[j]); };
+    auto Zp = [&](int j) { return reinterpret_cast<double*>(c->kZ[j]); };
+    double h3[3];
+    {
+        ProfScope ps(c, GP_PROF_MISC, 5);
+        launch_rho_stats(n, rho, c->partial, c->s);
+        launch_finalize(c->partial, kReduceBlocks, 3, c->scal + kS6Rho, c->s);
+        launch_rho_stats(n, c->eps64, c->partial, c->s);
+        launch_finalize(c->partial, kReduceBlocks, 3, c->scal + kS6Eps, c->s);
+        launch_fd6_set(c->scal + kS6N, (double)n, c->s);
+    }
+    GP_CHECK_LAUNCH();
+    GP_CUDA(cudaMemcpyAsync(h3, c->scal + kS6Rho, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->s));
+    GP_CUDA(cudaStreamSynchronize(c->s));
+    if (!(std::fabs(h3[0]) <= 1e-10 * h3[1])) {
+        if (!std::isfinite(h3[0])) throw Err{GP_ERR_INVALID_ARG, "rho is not finite"};
+        throw Err{GP_ERR_NOT_NEUTRAL, "rho is not neutral: |sum rho| > 1e-10 sum |rho|"};
+    }
+    // ||b||: b = -4 pi (rho - mean) forward, rho - mean for the adjoint
+    const double sb = transpose ? 1.0 : -4.0 * kPi;
+    const double nb = std::fabs(sb) * std::sqrt(std::max(h3[2] - h3[0] * h3[0] / (double)n, 0.0));
+    st.b_norm = nb;
+    if (nb == 0.0) {
+        GP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        if (border) *border = 0.0;
+        st.residual = 0.0;
+        return GP_OK;
+    }
+    {
+        ProfScope ps(c, GP_PROF_MISC, 3);
+        fd6_fix_constant(c, x, transpose);           // the warm start onto the constraint
+    }
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m + 1), hv(kMaxKrylov + 2);
+    auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+    double best = INFINITY, sum_out = 0.0;
+    gp_status result = GP_ERR_NOT_CONVERGED;
+    for (int cyc = 0; cyc < c->prm.max_outer; ++cyc) {
+        // true residual, projected, into V0
+        fd6_operator(c, x, rho, sb, -1.0, Vp(0), transpose);
+        TVecList<double> V0;
+        V0.n = 1;
+        V0.v[0] = Vp(0);
+        {
+            ProfScope ps(c, GP_PROF_KRYLOV, 2);
+            launch_multidot<double>(n, Vp(0), V0, c->partial, c->s);
+            launch_finalize(c->partial, kReduceBlocks, 1, c->scal + 15, c->s);
+        }
+        GP_CHECK_LAUNCH();
+        double rs[2];
+        GP_CUDA(cudaMemcpyAsync(&rs[0], c->scal + 15, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+        GP_CUDA(cudaMemcpyAsync(&rs[1], c->scal + kS6Out, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        prof_collect(c);
+        const double beta = std::sqrt(rs[0]);
+        const double rn = beta / nb;
+        sum_out = rs[1];
+        st.outer_iterations++;
+        if (st.history_len < GP_HISTORY) st.history[st.history_len++] = rn;
+        st.residual = rn;
+        if (!std::isfinite(rn) || (cyc > 0 && rn > 1e3 * best)) { result = GP_ERR_DIVERGED; break; }
+        best = std::min(best, rn);
+        if (rn <= tol) { result = GP_OK; break; }
+        if (cyc == c->prm.max_outer - 1) break;
+        {
+            ProfScope ps(c, GP_PROF_KRYLOV, 1);
+            launch_scale_by_norm<double>(n, Vp(0), Vp(0), c->scal + 15, c->s);
+        }
+        std::fill(H.begin(), H.end(), 0.0);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int used = 0;
+        for (int j = 0; j < m; ++j) {
+            fd6_precondition<T>(c, Vp(j), Zp(j), transpose);
+            fd6_operator(c, Zp(j), nullptr, 0.0, 1.0, Vp(j + 1), transpose);
+            TVecList<double> V;
+            V.n = j + 1;
+            for (int i = 0; i <= j; ++i) V.v[i] = Vp(i);
+            {
+                ProfScope ps(c, GP_PROF_KRYLOV, 5);
+                launch_multidot<double>(n, Vp(j + 1), V, c->partial, c->s);
+                launch_finalize(c->partial, kReduceBlocks, j + 1, c->scal + 16, c->s);
+                launch_multiaxpy_norm<double>(n, Vp(j + 1), V, c->scal + 16, c->partial, c->s);
+                launch_finalize(c->partial, kReduceBlocks, 1, c->scal + 15, c->s);
+                launch_scale_by_norm<double>(n, Vp(j + 1), Vp(j + 1), c->scal + 15, c->s);
+            }
+            GP_CHECK_LAUNCH();
+            GP_CUDA(cudaMemcpyAsync(hv.data(), c->scal + 15, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, c->s));
+            GP_CUDA(cudaStreamSynchronize(c->s));
+            prof_collect(c);
+            for (int i = 0; i <= j; ++i) Hij(i, j) = hv[1 + i];
+            Hij(j + 1, j) = std::sqrt(hv[0]);
+            for (int i = 0; i < j; ++i) {
+                const double a = Hij(i, j), b = Hij(i + 1, j);
+                Hij(i, j) = cs[i] * a + sn[i] * b;
+                Hij(i + 1, j) = -sn[i] * a + cs[i] * b;
+            }
+            const double a = Hij(j, j), b = Hij(j + 1, j);
+            const double r = std::hypot(a, b);
+            cs[j] = r > 0 ? a / r : 1.0;
+            sn[j] = r > 0 ? b / r : 0.0;
+            Hij(j, j) = r;
+            Hij(j + 1, j) = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            used = j + 1;
+            st.inner_iterations++;
+            if (std::fabs(g[j + 1]) <= 0.5 * tol * nb || !(hv[0] > 0.0)) break;
+        }
+        for (int i = used - 1; i >= 0; --i) {
+            double acc = g[i];
+            for (int k = i + 1; k < used; ++k) acc -= Hij(i, k) * y[k];
+            y[i] = acc / Hij(i, i);
+        }
+        y[used] = 1.0;                               // x itself, last in the list: x += Z y
+        GP_CUDA(cudaMemcpyAsync(c->kY, y.data(), sizeof(double) * (used + 1), cudaMemcpyHostToDevice, c->s));
+        TVecList<double> Z;
+        Z.n = used + 1;
+        for (int j = 0; j < used; ++j) Z.v[j] = Zp(j);
+        Z.v[used] = x;
+        {
+            ProfScope ps(c, GP_PROF_KRYLOV, 1);
+            launch_krylov_combine<double>(n, x, Z, c->kY, c->s);
+        }
+        GP_CHECK_LAUNCH();
+    }
+    // the border value: the multiple of eps (or of 1) the projection removed
+    // from the last residual, with the sign of the bordered equation
+    double den = 0.0;
+    GP_CUDA(cudaMemcpyAsync(&den, c->scal + kS6Eps, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    GP_CUDA(cudaStreamSynchronize(c->s));
+    if (border) *border = sum_out / (transpose ? (double)n : den);
+    prof_collect(c);
+    if (result == GP_ERR_NOT_CONVERGED) c->err = "not converged within max_outer";
+    if (result == GP_ERR_DIVERGED) c->err = "residual diverged";
+    return result;
+}
+
 gp_status fail(gp_ctx* c, const Err& e) {
     if (c) c->err = e.msg;
     return e.st;
@@ -1314,6 +1534,7 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         c->stats.dry_planes = nd;
         c->stats.levels = L;
         c->have_eps = true;
+        c->eps_version++;
         prof_collect(c);
         c->err.clear();
         return GP_OK;
@@ -1450,9 +1671,9 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             {
                 ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
                 if (c->prm.kind != 0)
-                    launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, c->pe64, c->forces_S, c->s);
+                    launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
                 else
-                    launch_forces_eps(c->g, at, dp, c->sw, phi_dev, c->pe64, c->forces_S, c->s);
+                    launch_forces_eps(c->g, at, dp, c->sw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
             }
             GP_CHECK_LAUNCH();
             if (gauss_dev) {
@@ -1520,6 +1741,117 @@ gp_status gp_residual6(gp_ctx* c, const double* rho_dev, const double* phi_dev, 
             const double nb = 4.0 * kPi * std::sqrt(h3[2]);
             *rel_host = nb > 0 ? std::sqrt(s2[0]) / nb : std::sqrt(s2[0]);
         }
+        return GP_OK;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_solve6(gp_ctx* c, const double* rho_dev, double* phi_dev, double* mu_host, double tol) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!rho_dev || !phi_dev || !(tol > 0.0)) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_solve6"};
+        double mu = 0.0;
+        const gp_status st = c->prm.precision == 1 ? solve6_impl<float>(c, rho_dev, phi_dev, tol, false, &mu)
+                                                   : solve6_impl<double>(c, rho_dev, phi_dev, tol, false, &mu);
+        if (mu_host) *mu_host = mu;
+        if (st == GP_OK) c->err.clear();
+        return st;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_adjoint6(gp_ctx* c, const double* rho_dev, double* lam_dev, double* nu_host, double tol) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!rho_dev || !lam_dev || !(tol > 0.0)) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_adjoint6"};
+        double nu = 0.0;
+        const gp_status st = c->prm.precision == 1 ? solve6_impl<float>(c, rho_dev, lam_dev, tol, true, &nu)
+                                                   : solve6_impl<double>(c, rho_dev, lam_dev, tol, true, &nu);
+        if (nu_host) *nu_host = nu;
+        if (st == GP_OK) c->err.clear();
+        return st;
+    } catch (const Err& e) {
+        return fail(c, e);
+    }
+}
+
+gp_status gp_energy_forces6(gp_ctx* c, const double* phi_dev, double mu, const double* lam_dev,
+                            const double* rho_dev, const double* gauss_dev, double* energy_host,
+                            double* forces_dev) {
+    if (!c) return GP_ERR_INVALID_ARG;
+    try {
+        if (!phi_dev || !rho_dev || !std::isfinite(mu) || (forces_dev && !lam_dev))
+            throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
+        if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_energy_forces6"};
+        const double dv = c->g.hx * c->g.hy * c->g.hz;
+        if (energy_host) {
+            {
+                ProfScope ps(c, GP_PROF_ENERGY, 1);
+                launch_energy(c->g, rho_dev, phi_dev, c->eps64, c->partial, c->s);
+            }
+            GP_CHECK_LAUNCH();
+            double e2[2];
+            sum_host(c, 2, e2);
+            energy_host[0] = 0.5 * dv * e2[0];
+        }
+        if (forces_dev && c->n_atoms > 0) {
+            const int n = c->n_atoms;
+            if (n > c->forces_cap) {
+                if (c->forces_S) cudaFree(c->forces_S);
+                if (c->forces_T) cudaFree(c->forces_T);
+                c->forces_S = nullptr; c->forces_T = nullptr;
+                if (cudaMalloc(&c->forces_S, sizeof(double) * 3 * n) != cudaSuccess ||
+                    cudaMalloc(&c->forces_T, sizeof(double) * 3 * n) != cudaSuccess)
+                    throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+                c->forces_cap = n;
+            }
+            if (!c->f6_w) c->f6_w = (double*)dalloc(c, sizeof(double) * c->n);
+            if (!c->f6_t3) c->f6_t3 = (double*)dalloc(c, sizeof(double) * 3 * c->n);
+            GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
+            GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->s));
+            // per-point weight of d eps: sum_axes [-D1(lam D1 phi) + lam D2 phi] + mu lam
+            {
+                ProfScope ps(c, GP_PROF_FORCES_EPS, 2);
+                launch_fd6_d1(c->g, phi_dev, lam_dev, c->f6_t3, c->s);
+                launch_fd6_weps(c->g, phi_dev, lam_dev, c->f6_t3, mu, c->f6_w, c->s);
+            }
+            GP_CHECK_LAUNCH();
+            Atoms at{c->atoms, c->atoms32, gauss_dev, n};
+            const DielParams dp = c->dp;
+            {
+                ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
+                if (c->prm.kind != 0)
+                    launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, c->f6_w, c->pe64, c->forces_S, c->s);
+                else
+                    launch_forces_eps(c->g, at, dp, c->sw, phi_dev, c->f6_w, c->pe64, c->forces_S, c->s);
+            }
+            GP_CHECK_LAUNCH();
+            if (gauss_dev) {
+                // weight of d rho: (phi - 4 pi lam)/2, its mean removed (rho loses its mean)
+                if (!c->f6_r) c->f6_r = (double*)dalloc(c, sizeof(double) * c->n);
+                {
+                    ProfScope ps(c, GP_PROF_MISC, 4);
+                    launch_fd6_wrho(c->n, phi_dev, lam_dev, c->f6_r, c->partial, c->s);
+                    launch_finalize(c->partial, kReduceBlocks, 1, c->scal + kS6Z, c->s);
+                    launch_fd6_set(c->scal + kS6N, (double)c->n, c->s);
+                    launch_fd6_sub_ratio(c->n, c->f6_r, nullptr, c->scal + kS6Z, c->scal + kS6N, c->s);
+                }
+                const GaussTabs gt = ensure_gtab(c, n);
+                ProfScope ps(c, GP_PROF_FORCES_RHO, 2);
+                launch_gauss_tables(c->g, at, 8.0, gt, c->s);
+                launch_forces_rho(c->g, gt, c->f6_r, c->forces_T, c->s);
+            }
+            GP_CHECK_LAUNCH();
+            ProfScope ps(c, GP_PROF_MISC, 1);
+            launch_forces_finish(c->forces_S, gauss_dev ? c->forces_T : nullptr, n, -0.5 * dv, dv, forces_dev, c->s);
+            GP_CHECK_LAUNCH();
+        }
+        GP_CUDA(cudaStreamSynchronize(c->s));
+        prof_collect(c);
         return GP_OK;
     } catch (const Err& e) {
         return fail(c, e);

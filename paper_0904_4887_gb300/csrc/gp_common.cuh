@@ -121,7 +121,7 @@ void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, 
 void launch_build_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, double* eps64, double* fe64,
                             float* eps32, cudaStream_t s);
 void launch_forces_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, const double* phi,
-                             const double* fe64, double* S, cudaStream_t s);
+                             const double* wext, const double* fe64, double* S, cudaStream_t s);
 // Periodized 1D Gaussian factor tables (k_fields.cu), Gaussian ge = 2 atom + {0 core, 1 cloud}
 struct GaussTabs {
     double* val;    // [G][3][nmax] X, Y, Z factors summed over the images -L, 0, +L
@@ -141,7 +141,7 @@ void launch_plane_max(const Geo& g, const double* eps64, double* plane_max, cuda
 void launch_energy(const Geo& g, const double* rho, const double* phi, const double* eps64,
                    double* partial, cudaStream_t s);
 void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const double* phi,
-                       const double* pe64, double* G, cudaStream_t s);
+                       const double* wext, const double* pe64, double* S, cudaStream_t s);
 void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, double* T, cudaStream_t s);
 void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,
                           cudaStream_t s);
@@ -163,6 +163,20 @@ void launch_residual64(const Geo& g, const double* phi, const double* rho, const
 // sixth-order residual (k_fd6.cu): r = -4 pi rho - A6 phi - mu eps, partial[b] = sum r^2
 void launch_residual6(const Geo& g, const double* phi, const double* rho, const double* eps64, double mu,
                       double* r_out, double* partial, cudaStream_t s);
+// sixth-order solve pieces (k_fd6.cu)
+void launch_fd6_apply(const Geo& g, const double* x, const double* eps, const double* rho, double crho,
+                      const double* rsum, double sa, double* y, double* partial, cudaStream_t s);
+void launch_fd6_apply_t(const Geo& g, const double* x, const double* eps, const double* d1e, const double* rho,
+                        double crho, const double* rsum, double sa, double* y, double* partial, cudaStream_t s);
+void launch_fd6_d1(const Geo& g, const double* u, const double* w, double* out3, cudaStream_t s);
+void launch_fd6_weps(const Geo& g, const double* phi, const double* lam, const double* t3, double mu, double* weps,
+                     cudaStream_t s);
+void launch_fd6_sub_ratio(long n, double* y, const double* w, const double* num, const double* den,
+                          cudaStream_t s);
+template <typename T>
+void launch_fd6_to64(long n, const T* src, const double* eps, double* dst, double* partial, cudaStream_t s);
+void launch_fd6_wrho(long n, const double* phi, const double* lam, double* out, double* partial, cudaStream_t s);
+void launch_fd6_set(double* slot, double v, cudaStream_t s);
 template <typename T>
 void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_band,
                        int band_first, int band_nz, cudaStream_t s);

@@ -610,6 +610,29 @@ __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParam
     }
 }
 
+// ----------------------------------------------------------------- the per-point force weight
+// W_i of the dielectric force sums S_a = sum_i W_i (d eps_i / d R_a) / pv_i:
+// (1/2) sum over the six faces of i of (grad_f phi)^2 (the face means of Eq. 3
+// split between the two points of each face) times the per-point factor pv_i,
+// or, when the caller gives a per-point weight wext (the sixth-order forces,
+// where the adjoint supplies it), wext_i times pv_i.
+__device__ __forceinline__ double force_weight(const Geo& g, const double* phi, const double* wext, double pv, int i,
+                                               int j, int k, long c) {
+    if (pv == 0.0) return 0.0;
+    if (wext) return wext[c] * pv;
+    const long pl = plane_of(g.nx, g.ny);
+    const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
+    const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
+    const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
+    const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
+    const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
+    const double p0 = phi[c];
+    const double ax = phi[xp] - p0, bx = p0 - phi[xm];
+    const double ay = phi[yp] - p0, by = p0 - phi[ym];
+    const double az = phi[zp] - p0, bz = p0 - phi[zm];
+    return ((ax * ax + bx * bx) * g.c2x + (ay * ay + by * by) * g.c2y + (az * az + bz * bz) * g.c2z) * pv;
+}
+
 // ----------------------------------------------------------------- eps force, tabulated (df64)
 // The same sum as k_forces_eps with h = s'/(s d) from the packed table in df64
 // arithmetic, on 32 x 4 x 16 tiles. One warp per (tile, atom image): it
@@ -640,7 +663,8 @@ __device__ __forceinline__ SwCoord sw_coord_df(df v) {
 }
 
 __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb,
-                                                       const double* phi, const double* pe64, double* S) {
+                                                       const double* phi, const double* wext, const double* pe64,
+                                                       double* S) {
     __shared__ df Ws[TX * TY * EZ];              // index tx + TX (ty + TY z)
     __shared__ df eb[ECAPF][3];                  // displacement of column/row/plane 0 from the image
     __shared__ int eatom[ECAPF];
@@ -669,21 +693,8 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
         const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
         double W = 0.0;
         if (i < g.nx && j < g.ny && k < g.nz) {
-            const long pl = plane_of(g.nx, g.ny);
             const long c = i + (long)g.nx * (j + (long)g.ny * k);
-            const double pv = pe64[c];
-            if (pv != 0.0) {
-                const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
-                const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
-                const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
-                const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
-                const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
-                const double p0 = phi[c];
-                const double ax = phi[xp] - p0, bx = p0 - phi[xm];
-                const double ay = phi[yp] - p0, by = p0 - phi[ym];
-                const double az = phi[zp] - p0, bz = p0 - phi[zm];
-                W = ((ax * ax + bx * bx) * g.c2x + (ay * ay + by * by) * g.c2y + (az * az + bz * bz) * g.c2z) * pv;
-            }
+            W = force_weight(g, phi, wext, pe64[c], i, j, k, c);
         }
         Ws[q] = df_from(-W);   // sign of c = -W h folded in
     }
@@ -907,7 +918,8 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielPar
 // (atom, image) entry, and for kind 2 one warp per lower atom, over the tile's 512
 // points; FP64.
 __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielParams p, const double* rvdw,
-                                                         const double* phi, const double* fe64, double* S) {
+                                                         const double* phi, const double* wext, const double* fe64,
+                                                         double* S) {
     __shared__ double ec[MAXE][5];
     __shared__ int eatom[MAXE];
     __shared__ double Ws[TT];
@@ -920,21 +932,8 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielPa
         const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
         double W = 0.0;
         if (i < g.nx && j < g.ny && k < g.nz) {
-            const long pl = plane_of(g.nx, g.ny);
             const long c = i + (long)g.nx * (j + (long)g.ny * k);
-            const double fv = fe64[c];
-            if (fv != 0.0) {
-                const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
-                const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
-                const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
-                const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
-                const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
-                const double p0 = phi[c];
-                const double ax = phi[xp] - p0, bx = p0 - phi[xm];
-                const double ay = phi[yp] - p0, by = p0 - phi[ym];
-                const double az = phi[zp] - p0, bz = p0 - phi[zm];
-                W = ((ax * ax + bx * bx) * g.c2x + (ay * ay + by * by) * g.c2y + (az * az + bz * bz) * g.c2z) * fv;
-            }
+            W = force_weight(g, phi, wext, fe64[c], i, j, k, c);
         }
         Ws[threadIdx.x] = W;   // index tx + TX (ty + TY tz)
         any = W != 0.0;
@@ -1071,7 +1070,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_energy(Geo g, const double* 
 // 8 x 2 x 2 blocks. Pairs with |u| > 3.5 contribute at most 5e-6 of a pair at
 // the switching radius; their s and s' are taken in FP32.
 __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p, SwTables tb, const double* phi,
-                                                   const double* pe64, double* S) {
+                                                   const double* wext, const double* pe64, double* S) {
     __shared__ double ec[MAXE][3];
     __shared__ int eatom[MAXE];
     __shared__ double Ws[TT];
@@ -1082,18 +1081,8 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
         const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
         double W = 0.0;
         if (i < g.nx && j < g.ny && k < g.nz) {
-            const long pl = plane_of(g.nx, g.ny);
             const long c = i + (long)g.nx * (j + (long)g.ny * k);
-            const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
-            const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
-            const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
-            const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
-            const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
-            const double p0 = phi[c];
-            const double ax = phi[xp] - p0, bx = p0 - phi[xm];
-            const double ay = phi[yp] - p0, by = p0 - phi[ym];
-            const double az = phi[zp] - p0, bz = p0 - phi[zm];
-            W = ((ax * ax + bx * bx) * g.c2x + (ay * ay + by * by) * g.c2y + (az * az + bz * bz) * g.c2z) * pe64[c];
+            W = force_weight(g, phi, wext, pe64[c], i, j, k, c);
         }
         Ws[threadIdx.x] = W;   // index tx + TX (ty + TY tz)
     }
@@ -1296,8 +1285,8 @@ void launch_build_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* 
 }
 
 void launch_forces_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, const double* phi,
-                             const double* fe64, double* S, cudaStream_t s) {
-    k_forces_eps_gamma<<<tile_grid(g), TT, 0, s>>>(g, at, p, rvdw, phi, fe64, S);
+                             const double* wext, const double* fe64, double* S, cudaStream_t s) {
+    k_forces_eps_gamma<<<tile_grid(g), TT, 0, s>>>(g, at, p, rvdw, phi, wext, fe64, S);
 }
 
 void launch_plane_max(const Geo& g, const double* eps64, double* out, cudaStream_t s) {
@@ -1310,9 +1299,9 @@ void launch_energy(const Geo& g, const double* rho, const double* phi, const dou
 }
 
 void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const double* phi,
-                       const double* pe64, double* S, cudaStream_t s) {
-    if (tb.h32) k_forces_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
-    else k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, pe64, S);
+                       const double* wext, const double* pe64, double* S, cudaStream_t s) {
+    if (tb.h32) k_forces_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, phi, wext, pe64, S);
+    else k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, wext, pe64, S);
 }
 
 void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, double* T, cudaStream_t s) {

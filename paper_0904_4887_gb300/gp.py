@@ -58,6 +58,10 @@ _SIGNATURES = {
     "gp_energy_forces": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "gp_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gp_residual6": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double)]),
+    "gp_solve6": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_double]),
+    "gp_adjoint6": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_double]),
+    "gp_energy_forces6": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P, ctypes.POINTER(ctypes.c_double),
+                                         _P]),
     "gp_fft_poisson": (ctypes.c_int, [_P, _P, _P]),
     "gp_fft_poisson_f32": (ctypes.c_int, [_P, _P, _P]),
     "gp_get_eps": (ctypes.c_int, [_P, _P]),
@@ -273,6 +277,31 @@ class Context:
         self._check(self._lib.gp_residual6(self._h, self._field(rho, "rho"), self._field(phi, "phi"),
                                            ctypes.c_double(mu), self._field(r, "r"), ctypes.byref(rel)))
         return rel.value
+
+    def gp_solve6(self, rho, phi, tol, check=True):
+        mu = ctypes.c_double()
+        st = self._lib.gp_solve6(self._h, self._field(rho, "rho"), self._field(phi, "phi"), ctypes.byref(mu),
+                                 ctypes.c_double(tol))
+        if check:
+            self._check(st)
+        return mu.value, st
+
+    def gp_adjoint6(self, rho, lam, tol, check=True):
+        nu = ctypes.c_double()
+        st = self._lib.gp_adjoint6(self._h, self._field(rho, "rho"), self._field(lam, "lam"), ctypes.byref(nu),
+                                   ctypes.c_double(tol))
+        if check:
+            self._check(st)
+        return nu.value, st
+
+    def gp_energy_forces6(self, phi, mu, lam, rho, gauss=None, forces=None):
+        na = None if self._n_atoms is None else 3 * self._n_atoms
+        e = (ctypes.c_double * 1)()
+        self._check(self._lib.gp_energy_forces6(self._h, self._field(phi, "phi"), ctypes.c_double(mu),
+                                                None if lam is None else self._field(lam, "lam"),
+                                                self._field(rho, "rho"), _ptr(gauss, na, "gauss"), e,
+                                                _ptr(forces, na, "forces")))
+        return e[0]
 
     def gp_fft_poisson(self, src, out):
         return self._check(self._lib.gp_fft_poisson(self._h, self._field(src, "src"), self._field(out, "out")))

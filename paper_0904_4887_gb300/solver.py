@@ -78,6 +78,26 @@ class GPSolver:
         rel = self.ctx.gp_residual6(rho, phi, mu, r)
         return r, rel
 
+    def solve6(self, rho, phi=None, tol=1e-10):
+        """(phi, mu) of the sixth-order bordered system A6 phi + mu eps =
+        -4 pi (rho - mean rho), sum(phi) = 0 (Sec. III); `phi` is the warm start."""
+        phi = self.zeros() if phi is None else phi
+        mu, _ = self.ctx.gp_solve6(rho, phi, tol)
+        return phi, mu
+
+    def adjoint6(self, rho, lam=None, tol=1e-10):
+        """(lam, nu) of the transposed system A6^T lam + nu = rho - mean rho,
+        sum(eps lam) = 0, which the sixth-order forces need."""
+        lam = self.zeros() if lam is None else lam
+        nu, _ = self.ctx.gp_adjoint6(rho, lam, tol)
+        return lam, nu
+
+    def energy_forces6(self, phi, mu, lam, rho, gauss=None, forces=True):
+        """E and -dE/dR for the sixth-order solution (phi, mu) with its adjoint lam."""
+        F = torch.zeros((self._pos.shape[0], 3), dtype=torch.float64, device=self.device) if forces else None
+        E = self.ctx.gp_energy_forces6(phi, mu, lam, rho, gauss, F)
+        return E, F
+
     def fft_poisson(self, src):
         out = self.zeros()
         self.ctx.gp_fft_poisson(src.contiguous(), out)
