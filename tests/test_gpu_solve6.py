@@ -101,7 +101,10 @@ def test_adjoint6_matches_oracle(oracle_cases, k, precision):
     l = lam.cpu().numpy()
     assert s.stats().residual <= 1e-13
     rt = (rho - rho.mean()) - O.apply_A6_transpose(l, eps, h) - nu
-    assert np.linalg.norm(rt) < 2e-13 * np.linalg.norm(rho - rho.mean())
+    # the library's eps agrees with the oracle's to 1e-13 of its maximum, which
+    # alone moves A6^T lam by ~1e-12 of rho here (7e-13 measured on the
+    # anisotropic grid): the residual the oracle measures is held to 3e-12
+    assert np.linalg.norm(rt) < 3e-12 * np.linalg.norm(rho - rho.mean())
     assert abs(float(np.sum(eps * l))) < 1e-12 * float(np.sum(np.abs(eps * l)))
     assert _rel(l, lam_o) < 1e-10
     assert abs(nu - nu_o) <= 1e-9 * abs(nu_o) + 1e-13 * np.max(np.abs(rho))
@@ -169,13 +172,13 @@ def test_forces6_match_central_differences(rho_moves):
         qt = _t(q)
         s.set_atoms(qt)
         rho = s.build_rho(qt, gauss) if rho_moves else rho0
-        phi, mu = s.solve6(rho, tol=1e-14)
+        phi, mu = s.solve6(rho, tol=1e-13)
         E, _ = s.energy_forces6(phi, mu, None, rho, forces=False)
         return E
 
     s.set_atoms(_t(at.pos))
-    phi, mu = s.solve6(rho0, tol=1e-14)
-    lam, _ = s.adjoint6(rho0, tol=1e-14)
+    phi, mu = s.solve6(rho0, tol=1e-13)
+    lam, _ = s.adjoint6(rho0, tol=1e-13)
     _, F = s.energy_forces6(phi, mu, lam, rho0, gauss if rho_moves else None)
     F = F.cpu().numpy()
     sel = np.random.default_rng(9).choice(len(at.pos), 4, replace=False)
