@@ -185,9 +185,19 @@ def roofline_for(kind, prof, n0, hbm, hbm_src, prec_bytes):
         # FP64: one launch = one colour of a sweep, half of 32 B/pt
         bytes_per_launch = 16.0 * n0
         achieved = bytes_per_launch / per_launch_s / 1e9
-        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_source": hbm_src, "kernel": "k_rb_sweep (finest level, fused red-black sweep)" if prec_bytes == 4 else "k_rbgs (finest level, one colour)",
-                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": per_launch_s * 1e3}
+        out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+               "peak_source": hbm_src,
+               "kernel": "k_rb_sweep (finest level, fused red-black sweep)" if prec_bytes == 4
+               else "k_rbgs (finest level, one colour)",
+               "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": per_launch_s * 1e3}
+        if prec_bytes == 8:
+            # the FP64 colour sweep is bound by the FP64 pipe, not HBM: 30 FP64 flops per
+            # updated point (six face means, the weighted sum, the diagonal, the update)
+            gf = 30.0 * (n0 / 2) / per_launch_s / 1e9
+            out["fp64"] = {"achieved": gf, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                           "frac": gf / FP64_PEAK_GFLOPS, "peak_source": "nominal FP64 (recipe table)",
+                           "flops_per_updated_point": 30}
+        return out
     if kind == "res64":
         # read phi, rho, eps (FP64), write r in the working precision; 30 FP64 flops per point
         bytes_per_launch = (24 + prec_bytes) * n0
@@ -612,6 +622,73 @@ def residual6_arm(args, rank, world):
             "clocks": clk}
 
 
+# ----------------------------------------------------------------------------- sixth-order solve
+def solve6_arm(args, rank, world):
+    """--mode solve6: the sixth-order path of Sec. III (Eq. 16-18) on the
+    workload: a step is eps + rho, the bordered solve to `tol`, the adjoint
+    solve, energy and forces through the adjoint, on a new frame each step."""
+    import torch
+    import paper_0904_4887_gb300 as P
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.WORKLOADS[args.workload]
+    nfr = args.warmup + args.steps
+    at, traj, gauss_np = make_inputs(w, max(nfr, 2), seed=rank)
+    gauss = torch.tensor(gauss_np, dtype=torch.float64, device=dev)
+    frames = [torch.tensor(traj[i % len(traj)], dtype=torch.float64, device=dev) for i in range(nfr)]
+    s = P.GPSolver(w.grid, w.cell, precision=args.precision, levels=w.levels)
+    rho, phi, lam = s.zeros(), s.zeros(), s.zeros()
+    F = torch.zeros((len(at.Z), 3), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    stats = []
+
+    def step(pos):
+        s.set_atoms(pos)
+        s.build_rho(pos, gauss, out=rho)
+        phi.zero_()
+        lam.zero_()
+        mu, st = s.ctx.gp_solve6(rho, phi, args.tol, check=False)
+        st1 = s.stats()
+        nu, st2 = s.ctx.gp_adjoint6(rho, lam, args.tol, check=False)
+        if st != 0 or st2 != 0:
+            raise RuntimeError("sixth-order solve failed: %d %d" % (st, st2))
+        s.ctx.gp_energy_forces6(phi, mu, lam, rho, gauss, F)
+        return st1.outer_iterations, st1.inner_iterations
+
+    for i in range(args.warmup):
+        step(frames[i])
+    from paper_0904_4887_gb300 import gp as G
+    launches0 = G.gp_launch_count()
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        stats.append(step(frames[args.warmup + i]))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = G.gp_launch_count() - launches0
+    total = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    if rank != 0:
+        return None
+    return {"metric": "sixth-order solves/s (Eq. 16-18: bordered solve + adjoint + forces)",
+            "value": job_throughput(args.steps, world, total / 1e3), "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (FGMRES, operator, residual)+%s (multigrid preconditioner)+df64 (fields)"
+                     % ("f32" if args.precision == 1 else "f64"),
+            "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.grid), "atoms": int(len(at.Z)), "tol": args.tol,
+                       "restart": 12, "fgmres_cycles_mean": float(np.mean([a for a, _ in stats])),
+                       "krylov_and_pcg_steps_mean": float(np.mean([b for _, b in stats])),
+                       "step": "set_dielectric + build_rho + gp_solve6 + gp_adjoint6 + gp_energy_forces6"},
+            "gpu_launches": int(launches), "clocks": clk}
+
+
 # ----------------------------------------------------------------------------- oracle (CPU) timing
 def _split(seq, parts):
     """`seq` in `parts` contiguous chunks of near-equal length (none empty)."""
@@ -629,6 +706,7 @@ _W = {}
 
 
 def _worker_init(payload):
+    from oracle import gp_oracle  # noqa: F401  (imported once per worker, before the clock)
     _W.update(payload)
 
 
@@ -827,7 +905,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "md", "residual6", "oracle"])
+    ap.add_argument("--mode", default="step", choices=["step", "md", "residual6", "solve6", "oracle"])
     ap.add_argument("--oracle-workers", type=int, nargs="+", default=[1, 0],
                     help="--mode oracle: process counts to time the complete step with (0 = every host core)")
     ap.add_argument("--frames", type=int, default=100)
@@ -864,6 +942,8 @@ def main():
         line = md_arm(args, rank, world)
     elif args.mode == "residual6":
         line = residual6_arm(args, rank, world)
+    elif args.mode == "solve6":
+        line = solve6_arm(args, rank, world)
     else:
         line = gpu_arm(args, rank, world)
     if line is not None:

@@ -502,37 +502,7 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// One Gauss-Seidel value from the six neighbours u_* and their cell eps e_* around a
-// point with eps e0 and right side fv: (sum_nb a_nb u_nb - f) / sum_nb a_nb with the
-// face coefficient a_nb = c_axis (e0 + e_nb). On a cubic mesh (ISO: one c for all
-// axes, ic = 1/c) the same value is (e0 sum u + sum e u - f/c) / (6 e0 + sum e),
-// five fewer multiplies.
-template <bool ISO>
-__device__ __forceinline__ float gs_value(float e0, float exl, float exr, float eyl, float eyh, float ezl, float ezh,
-                                          float uxl, float uxr, float uyl, float uyh, float uzl, float uzh, float fv,
-                                          float cx, float cy, float cz, float ic) {
-    if constexpr (ISO) {   // the general form is written out where it is used
-        const float su = ((uxl + uxr) + (uyl + uyh)) + (uzl + uzh);
-        const float se = ((exl + exr) + (eyl + eyh)) + (ezl + ezh);
-        float p = exl * uxl;
-        p = fmaf(exr, uxr, p);
-        p = fmaf(eyl, uyl, p);
-        p = fmaf(eyh, uyh, p);
-        p = fmaf(ezl, uzl, p);
-        p = fmaf(ezh, uzh, p);
-        const float num = fmaf(-fv, ic, fmaf(e0, su, p));
-        return num * rcp_approx(fmaf(6.f, e0, se));
-    } else {
-        const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
-        const float aym = (e0 + eyl) * cy, ayp = (e0 + eyh) * cy;
-        const float azm = (e0 + ezl) * cz, azp = (e0 + ezh) * cz;
-        const float sum = axm * uxl + axp * uxr + aym * uyl + ayp * uyh + azm * uzl + azp * uzh;
-        const float d = axm + axp + aym + ayp + azm + azp;
-        return (sum - fv) * rcp_approx(d);
-    }
-}
-
-template <int NPX, int SY, int K, bool ISO>
+template <int NPX, int SY, int K>
 __global__ void __maxnreg__((ws_max_regs<NPX, SY, K>()))
     k_rb_sweep_ws(LV<float> L, const float* __restrict__ u_old, const float* __restrict__ f,
                   float* __restrict__ u_new, int first, int sz, int* err, int wait_limit) {
@@ -611,7 +581,7 @@ __global__ void __maxnreg__((ws_max_regs<NPX, SY, K>()))
     }
 
     // ---------------- consumer threads
-    const float cx = 0.5f * L.ihx2, cy = 0.5f * L.ihy2, cz = 0.5f * L.ihz2, ic = 1.f / cx;
+    const float cx = 0.5f * L.ihx2, cy = 0.5f * L.ihy2, cz = 0.5f * L.ihz2;
     const int g = tid / NPX, p = tid % NPX;
     const int pm = p == 0 ? NPX - 1 : p - 1, pp = p == NPX - 1 ? 0 : p + 1;
     const int a0 = g * K;                            // first A row (A row a is global row j0 - 1 + a)
@@ -717,18 +687,12 @@ __global__ void __maxnreg__((ws_max_regs<NPX, SY, K>()))
                                          : pick(U_0[k - 1 < 0 ? 0 : k - 1]);
                 const float uyh = k == K - 1 ? (M ? R.u[s0][a0 + K + 1][p].y : R.u[s0][a0 + K + 1][p].x)
                                              : pick(U_0[k + 1 < K ? k + 1 : K - 1]);
-                if constexpr (ISO) {
-                    const float v = gs_value<true>(e0, exl, exr, eyl, eyh, pick(E_m[k]), pick(E_p[k]), uxl, uxr, uyl,
-                                                   uyh, um[k], pick(U_p[k]), pick(F_0[k]), cx, cy, cz, ic);
-                    rA[k] = wall ? pick(U_0[k]) : v;
-                } else {
-                    const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
-                    const float aym = (e0 + eyl) * cy, ayp = (e0 + eyh) * cy;
-                    const float azm = (e0 + pick(E_m[k])) * cz, azp = (e0 + pick(E_p[k])) * cz;
-                    const float sum = axm * uxl + axp * uxr + aym * uyl + ayp * uyh + azm * um[k] + azp * pick(U_p[k]);
-                    const float d = axm + axp + aym + ayp + azm + azp;
-                    rA[k] = wall ? pick(U_0[k]) : (sum - pick(F_0[k])) * rcp_approx(d);
-                }
+                const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
+                const float aym = (e0 + eyl) * cy, ayp = (e0 + eyh) * cy;
+                const float azm = (e0 + pick(E_m[k])) * cz, azp = (e0 + pick(E_p[k])) * cz;
+                const float sum = axm * uxl + axp * uxr + aym * uyl + ayp * uyh + azm * um[k] + azp * pick(U_p[k]);
+                const float d = axm + axp + aym + ayp + azm + azp;
+                rA[k] = wall ? pick(U_0[k]) : (sum - pick(F_0[k])) * rcp_approx(d);
                 R.r[rw][a0 + k][p] = rA[k];
             }
             arrive(t);
@@ -750,18 +714,12 @@ __global__ void __maxnreg__((ws_max_regs<NPX, SY, K>()))
                     const float rxl = M ? R_m[k] : rxa, rxr = M ? rxa : R_m[k];
                     const float eyl = k == 0 ? bylo : pick(E_m[k - 1 < 0 ? 0 : k - 1]);
                     const float eyh = k == K - 1 ? byhi : pick(E_m[k + 1 < K ? k + 1 : K - 1]);
-                    float vB;
-                    if constexpr (ISO) {
-                        vB = gs_value<true>(e0, exl, exr, eyl, eyh, em2[k], pick(E_0[k]), rxl, rxr, ryl, ryh, R_m2[k],
-                                            rA[k], fm[k], cx, cy, cz, ic);
-                    } else {
-                        const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
-                        const float aym = (e0 + eyl) * cy, ayp = (e0 + eyh) * cy;
-                        const float azm = (e0 + em2[k]) * cz, azp = (e0 + pick(E_0[k])) * cz;
-                        const float sum = axm * rxl + axp * rxr + aym * ryl + ayp * ryh + azm * R_m2[k] + azp * rA[k];
-                        const float d = axm + axp + aym + ayp + azm + azp;
-                        vB = (sum - fm[k]) * rcp_approx(d);
-                    }
+                    const float axm = (e0 + exl) * cx, axp = (e0 + exr) * cx;
+                    const float aym = (e0 + eyl) * cy, ayp = (e0 + eyh) * cy;
+                    const float azm = (e0 + em2[k]) * cz, azp = (e0 + pick(E_0[k])) * cz;
+                    const float sum = axm * rxl + axp * rxr + aym * ryl + ayp * ryh + azm * R_m2[k] + azp * rA[k];
+                    const float d = axm + axp + aym + ayp + azm + azp;
+                    const float vB = (sum - fm[k]) * rcp_approx(d);
                     ob[k * NPX] = M ? make_float2(R_m[k], vB) : make_float2(vB, R_m[k]);
                 }
             }
@@ -801,22 +759,16 @@ void sweep_ws(const LV<float>& L, const float* u_old, const float* f, float* u_n
               bool attr, int* err) {
     const size_t sm = sizeof(WsRing<NPX, SY>);
     if (attr) {
-        cudaFuncSetAttribute(k_rb_sweep_ws<NPX, SY, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_rb_sweep_ws<NPX, SY, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_rb_sweep_ws<NPX, SY, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         return;
     }
-    // a cubic mesh takes the shorter update (the face coefficients share one 1/h^2)
-    const bool iso = L.ihx2 == L.ihy2 && L.ihy2 == L.ihz2;
     static int per_sm = 0;                           // resident CTAs per SM (first launch asks)
     if (per_sm == 0) {
-        int n = 0, m = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rb_sweep_ws<NPX, SY, K, false>,
-                                                          ws_threads<NPX, SY, K>(), sm) != cudaSuccess || n < 1)
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rb_sweep_ws<NPX, SY, K>, ws_threads<NPX, SY, K>(),
+                                                          sm) != cudaSuccess || n < 1)
             n = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_rb_sweep_ws<NPX, SY, K, true>,
-                                                          ws_threads<NPX, SY, K>(), sm) != cudaSuccess || m < 1)
-            m = 1;
-        per_sm = n < m ? n : m;
+        per_sm = n;
     }
     const int ty = (L.ny + SY - 1) / SY;
     int chunks = 152 * per_sm / ty;
@@ -824,12 +776,8 @@ void sweep_ws(const LV<float>& L, const float* u_old, const float* f, float* u_n
     if (chunks > L.nz) chunks = L.nz;
     const int sz = (L.nz + chunks - 1) / chunks;
     dim3 grid(1, ty, (L.nz + sz - 1) / sz);
-    if (iso)
-        k_rb_sweep_ws<NPX, SY, K, true><<<grid, ws_threads<NPX, SY, K>(), sm, s>>>(L, u_old, f, u_new, first, sz, err,
-                                                                                 g_wait_polls);
-    else
-        k_rb_sweep_ws<NPX, SY, K, false><<<grid, ws_threads<NPX, SY, K>(), sm, s>>>(L, u_old, f, u_new, first, sz,
-                                                                                  err, g_wait_polls);
+    k_rb_sweep_ws<NPX, SY, K><<<grid, ws_threads<NPX, SY, K>(), sm, s>>>(L, u_old, f, u_new, first, sz, err,
+                                                                         g_wait_polls);
 }
 
 // row-tile kernels exist for these row lengths and heights
