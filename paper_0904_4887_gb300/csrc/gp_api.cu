@@ -217,6 +217,7 @@ struct gp_ctx {
     bool capturing = false;
     cudaStream_t gs = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // the charge-force branch of gp_energy_forces
 
     // optional per-kernel-group timing (gp_profile)
     bool prof_on = false;
@@ -248,12 +249,12 @@ cudaEvent_t prof_event(gp_ctx* c) {
 
 // brackets a group of `launches` kernels of one kind with events on the stream
 struct ProfScope {
-    gp_ctx* c; int kind; int launches; cudaEvent_t a{}, b{};
-    ProfScope(gp_ctx* c_, int k, int n) : c(c_), kind(k), launches(n) {
+    gp_ctx* c; int kind; int launches; cudaEvent_t a{}, b{}; cudaStream_t st;
+    ProfScope(gp_ctx* c_, int k, int n, cudaStream_t on = nullptr) : c(c_), kind(k), launches(n), st(on ? on : c_->s) {
         count_launch(n);
         if (c->prof_on) {
             a = prof_event(c);
-            GP_CUDA(cudaEventRecordWithFlags(a, c->s, c->capturing ? cudaEventRecordExternal : 0));
+            GP_CUDA(cudaEventRecordWithFlags(a, st, c->capturing ? cudaEventRecordExternal : 0));
         }
     }
     ~ProfScope() {
@@ -262,7 +263,7 @@ struct ProfScope {
             cudaEvent_t e = nullptr;
             if (!c->event_pool.empty()) { e = c->event_pool.back(); c->event_pool.pop_back(); }
             else if (cudaEventCreate(&e) != cudaSuccess) return;
-            if (cudaEventRecordWithFlags(e, c->s, c->capturing ? cudaEventRecordExternal : 0) != cudaSuccess) {
+            if (cudaEventRecordWithFlags(e, st, c->capturing ? cudaEventRecordExternal : 0) != cudaSuccess) {
                 c->event_pool.push_back(e);
                 return;
             }
@@ -303,6 +304,19 @@ GaussTabs ensure_gtab(gp_ctx* c, int n_atoms) {
         c->gtab_cap = need;
     }
     return gauss_tabs_view(c->gtab, n_atoms, nmax);
+}
+
+// per-atom partial sums of the two force terms, sized for n atoms
+void ensure_forces(gp_ctx* c, int n) {
+    if (n <= c->forces_cap) return;
+    if (c->forces_S) cudaFree(c->forces_S);
+    if (c->forces_T) cudaFree(c->forces_T);
+    c->forces_S = nullptr; c->forces_T = nullptr;
+    c->forces_cap = 0;
+    if (cudaMalloc(&c->forces_S, sizeof(double) * 3 * n) != cudaSuccess ||
+        cudaMalloc(&c->forces_T, sizeof(double) * 3 * n) != cudaSuccess)
+        throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+    c->forces_cap = n;
 }
 
 double sum_host(gp_ctx* c, int ncomp, double* out) {
@@ -1413,6 +1427,8 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
         GP_CUDA(cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking));
         GP_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
         GP_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+        GP_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        GP_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
         const char* ev = std::getenv("GP_NO_GRAPHS");
         c->use_graphs = !(ev && ev[0] == '1');
     } catch (const Err& e) {
@@ -1642,6 +1658,40 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
         if (!phi_dev || !rho_dev) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
         if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_energy_forces"};
         const double dv = c->g.hx * c->g.hy * c->g.hz;
+        const bool forces = forces_dev && c->n_atoms > 0;
+        const bool branch = forces && gauss_dev;
+        const int n = c->n_atoms;
+        if (forces) ensure_forces(c, n);
+        // The charge term (df64 on the FP32 pipe) runs on a second stream beside the
+        // energy and the dielectric term (both bound by the FP64 pipe), so that the
+        // two pipes work at once; the streams join before the forces are assembled.
+        if (branch) {
+            GP_CUDA(cudaEventRecord(c->ev_fork, c->s));
+            GP_CUDA(cudaStreamWaitEvent(c->gs, c->ev_fork, 0));
+            GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->gs));
+            Atoms at{c->atoms, c->atoms32, gauss_dev, n};
+            const GaussTabs gt = ensure_gtab(c, n);
+            {
+                ProfScope ps(c, GP_PROF_FORCES_RHO, 2, c->gs);
+                launch_gauss_tables(c->g, at, 8.0, gt, c->gs);
+                launch_forces_rho(c->g, gt, phi_dev, c->forces_T, c->gs);
+            }
+            GP_CHECK_LAUNCH();
+            GP_CUDA(cudaEventRecord(c->ev_join, c->gs));
+        }
+        if (forces) {
+            GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
+            Atoms at{c->atoms, c->atoms32, gauss_dev, n};
+            const DielParams dp = c->dp;
+            {
+                ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
+                if (c->prm.kind != 0)
+                    launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
+                else
+                    launch_forces_eps(c->g, at, dp, c->sw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
+            }
+            GP_CHECK_LAUNCH();
+        }
         if (energy_host) {
             {
                 ProfScope ps(c, GP_PROF_ENERGY, 1);
@@ -1653,36 +1703,8 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             energy_host[0] = 0.5 * dv * e2[0];
             energy_host[1] = dv / (8.0 * kPi) * e2[1];
         }
-        if (forces_dev && c->n_atoms > 0) {
-            const int n = c->n_atoms;
-            if (n > c->forces_cap) {
-                if (c->forces_S) cudaFree(c->forces_S);
-                if (c->forces_T) cudaFree(c->forces_T);
-                c->forces_S = nullptr; c->forces_T = nullptr;
-                if (cudaMalloc(&c->forces_S, sizeof(double) * 3 * n) != cudaSuccess ||
-                    cudaMalloc(&c->forces_T, sizeof(double) * 3 * n) != cudaSuccess)
-                    throw Err{GP_ERR_OOM, "cudaMalloc failed"};
-                c->forces_cap = n;
-            }
-            GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
-            GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->s));
-            Atoms at{c->atoms, c->atoms32, gauss_dev, n};
-            const DielParams dp = c->dp;
-            {
-                ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
-                if (c->prm.kind != 0)
-                    launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
-                else
-                    launch_forces_eps(c->g, at, dp, c->sw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
-            }
-            GP_CHECK_LAUNCH();
-            if (gauss_dev) {
-                const GaussTabs gt = ensure_gtab(c, n);
-                ProfScope ps(c, GP_PROF_FORCES_RHO, 2);
-                launch_gauss_tables(c->g, at, 8.0, gt, c->s);
-                launch_forces_rho(c->g, gt, phi_dev, c->forces_T, c->s);
-            }
-            GP_CHECK_LAUNCH();
+        if (forces) {
+            if (branch) GP_CUDA(cudaStreamWaitEvent(c->s, c->ev_join, 0));
             ProfScope ps(c, GP_PROF_MISC, 1);
             launch_forces_finish(c->forces_S, gauss_dev ? c->forces_T : nullptr, n, -dv / (8.0 * kPi), dv,
                                  forces_dev, c->s);
@@ -1800,15 +1822,7 @@ gp_status gp_energy_forces6(gp_ctx* c, const double* phi_dev, double mu, const d
         }
         if (forces_dev && c->n_atoms > 0) {
             const int n = c->n_atoms;
-            if (n > c->forces_cap) {
-                if (c->forces_S) cudaFree(c->forces_S);
-                if (c->forces_T) cudaFree(c->forces_T);
-                c->forces_S = nullptr; c->forces_T = nullptr;
-                if (cudaMalloc(&c->forces_S, sizeof(double) * 3 * n) != cudaSuccess ||
-                    cudaMalloc(&c->forces_T, sizeof(double) * 3 * n) != cudaSuccess)
-                    throw Err{GP_ERR_OOM, "cudaMalloc failed"};
-                c->forces_cap = n;
-            }
+            ensure_forces(c, n);
             if (!c->f6_w) c->f6_w = (double*)dalloc(c, sizeof(double) * c->n);
             if (!c->f6_t3) c->f6_t3 = (double*)dalloc(c, sizeof(double) * 3 * c->n);
             GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
@@ -1957,6 +1971,8 @@ void gp_destroy(gp_ctx* c) {
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->gs) cudaStreamDestroy(c->gs);
     for (void* p : c->misc) cudaFree(p);
     if (c->atoms) cudaFree(c->atoms);
