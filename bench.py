@@ -318,9 +318,11 @@ def gpu_arm(args, rank, world):
     if smooth is not None:
         smooth["kernel"] = shape_kernel + " (finest level, fused red-black sweep)"
         smooth["traffic"] = sweep_traffic(shape_kernel, w.name) if args.precision == 1 else None
-    roof["traffic"] = smooth["traffic"] if (smooth is not None and dominant == "smooth0") else None
-    if dominant == "smooth0" and smooth is not None:
-        roof["kernel"] = smooth["kernel"]
+    # the roofline object is the finest-level smoother's: the kernel with the largest share of the
+    # step's device time in the launch list (a kernel group such as the coarse levels, made of many
+    # short kernels, can outweigh it as a group)
+    if smooth is not None:
+        roof = dict(smooth)
     phases = {k: {"ms_per_step": v["ms"] / args.steps, "share": (v["ms"] / total_ms if total_ms else 0.0),
                   "launches_per_step": v["launches"] / args.steps} for k, v in prof.items() if v["launches"]}
 
@@ -483,7 +485,9 @@ def md_frames_run(dev, frames, warmup, precision, split, graph_outer, tol, seed,
     at, traj, gauss_np = make_inputs(w, frames + warmup, seed=seed)
     gauss = torch.tensor(gauss_np, dtype=torch.float64, device=dev)
     pos = [torch.tensor(traj[i], dtype=torch.float64, device=dev) for i in range(frames + warmup)]
-    s = P.GPSolver(w.grid, w.cell, precision=precision, split=split, graph_outer=graph_outer)
+    # two outer corrections of 4 CG iterations each in the graph: a warm start needs
+    # fewer V-cycles than the cold headline solve
+    s = P.GPSolver(w.grid, w.cell, precision=precision, split=split, graph_outer=graph_outer, inner=4)
     rho, phi = s.zeros(), s.zeros()
     F = torch.zeros((len(at.Z), 3), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()

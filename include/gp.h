@@ -80,7 +80,7 @@ typedef struct {
     int nu1, nu2;         /* red-black Gauss-Seidel sweeps before / after the coarse correction (2, 2) */
     int levels;           /* multigrid levels; 0 = automatic (gp_plan_levels: coarsest grid <= 64
                              points where the grid allows, else <= 512) */
-    int inner;            /* multigrid-preconditioned CG iterations per outer FP64 correction */
+    int inner;            /* multigrid-preconditioned CG iterations per outer FP64 correction (5, <= 8) */
     int max_outer;        /* outer FP64 corrections before GP_ERR_NOT_CONVERGED */
     int accel;            /* split: 1 = each FP64 outer correction is solved by flexible GMRES in the
                              working precision, preconditioned by the split (same fixed point);
@@ -107,6 +107,9 @@ typedef struct {
     double zlim;          /* kind 2: z_lim of Eq. 19, Angstrom inside the cell (0) */
     int nu_coarse;        /* sweeps before and after the coarse correction on the levels below the
                              finest; 0 = nu1, nu2 there too (0) */
+    int inner_adapt;      /* full box: 1 = the first correction runs `inner` CG iterations, each later
+                             one as many as the contraction measured over the previous one predicts for
+                             half the tolerance (1 .. 2 inner); 0 = `inner` every time (1) */
     double gamma_tail;    /* kinds 1, 2: bound on the part of gamma the image sum leaves out, in
                              (0, 1e-3] (1e-13). The radius R is the smallest with
                              (4 pi/3V) exp(-R)(u^3 + 3u^2 + 6u + 6) sum_a exp(rvdw_a) <= gamma_tail,

@@ -31,6 +31,8 @@ struct Err {
 
 #define GP_CHECK_LAUNCH() GP_CUDA(cudaGetLastError())
 
+constexpr int kMaxInner = 16;   // PCG iterations one correction may take (adaptive counts included)
+
 // A captured CUDA graph and what replaying it adds to the counters: the
 // kernel launches, V-cycles and inner iterations it holds, and (when it was
 // captured with profiling on) its event pairs per kernel group.
@@ -68,7 +70,7 @@ struct Hier {
     int nc = 0;
     std::vector<void*> allocs;
     bool ready = false;
-    GraphSlot pcg_g;                            // pcg(iters) on this hierarchy
+    GraphSlot pcg_g[kMaxInner + 1];             // pcg(iters) on this hierarchy, one graph per count
     GraphSlot solve_g;                          // fixed-count outer solve (graph_outer)
     const void* solve_phi = nullptr;            // the user buffers solve_g was captured with
     const void* solve_rho = nullptr;
@@ -88,7 +90,7 @@ T* alloc_level(Hier<T>& H, int nx, int ny, int nz) {
 
 template <typename T>
 void free_hier(Hier<T>& H) {
-    clear_slot(H.pcg_g);
+    for (GraphSlot& g : H.pcg_g) clear_slot(g);
     clear_slot(H.solve_g);
     for (GraphSlot& g : H.prec_g) clear_slot(g);
     for (void* p : H.allocs) cudaFree(p);
@@ -217,7 +219,6 @@ struct gp_ctx {
     bool capturing = false;
     cudaStream_t gs = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // the charge-force branch of gp_energy_forces
 
     // optional per-kernel-group timing (gp_profile)
     bool prof_on = false;
@@ -598,7 +599,7 @@ void pcg_body(gp_ctx* c, Hier<T>& H, int iters);
 template <typename T>
 void pcg(gp_ctx* c, Hier<T>& H, int iters) {
     const long key = ((long)c->prm.nu_coarse << 32) | ((long)iters << 16) | ((long)c->prm.nu1 << 8) | (long)c->prm.nu2;
-    run_graph(c, H.pcg_g, key, [&] { pcg_body(c, H, iters); });
+    run_graph(c, H.pcg_g[iters <= kMaxInner ? iters : kMaxInner], key, [&] { pcg_body(c, H, iters); });
 }
 
 template <typename T>
@@ -1027,6 +1028,11 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         }
         // not there yet: continue with the checked loop from the current phi
     }
+    // adaptive inner counts (full box): the contraction per CG iteration measured
+    // over the previous correction predicts how many the next one needs to reach
+    // half the tolerance, between 1 and twice `inner`
+    int last_inner = 0;
+    double last_rn = NAN;
     for (int it = 0; it < c->prm.max_outer; ++it) {
         if (it > 0) {
             if (!split) {
@@ -1068,7 +1074,15 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
             GP_CHECK_LAUNCH();
             pcg<T>(c, B, c->prm.inner);
         } else {
-            pcg<T>(c, F, c->prm.inner);
+            int k = c->prm.inner;
+            if (c->prm.inner_adapt && last_inner > 0 && rn > 0.0 && last_rn > rn) {
+                const double rate = std::min(std::max(std::pow(rn / last_rn, 1.0 / last_inner), 0.01), 0.9);
+                const double need = std::log(0.5 * tol / rn) / std::log(rate);
+                k = std::min(std::max((int)std::ceil(need - 1e-9), 1), 2 * c->prm.inner);
+            }
+            pcg<T>(c, F, k);
+            last_inner = k;
+            last_rn = rn;
         }
     }
     // gauge: the last residual pass summed phi into scal[9]
@@ -1381,7 +1395,8 @@ void gp_default_params(gp_params* p) {
     p->nu1 = 2;
     p->nu2 = 2;
     p->levels = 0;
-    p->inner = 4;
+    p->inner = 5;
+    p->inner_adapt = 1;
     p->max_outer = 60;
     p->accel = 1;
     p->restart = 12;
@@ -1427,8 +1442,6 @@ gp_status gp_create(gp_grid grid, gp_cell cell, void* cuda_stream, gp_ctx** out)
         GP_CUDA(cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking));
         GP_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
         GP_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
-        GP_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-        GP_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
         const char* ev = std::getenv("GP_NO_GRAPHS");
         c->use_graphs = !(ev && ev[0] == '1');
     } catch (const Err& e) {
@@ -1450,6 +1463,8 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         if (p.precision != 0 && p.precision != 1) throw Err{GP_ERR_INVALID_ARG, "precision must be 0 or 1"};
         if (p.nu1 < 0 || p.nu2 < 0 || p.nu1 + p.nu2 == 0 || p.inner < 1 || p.max_outer < 1)
             throw Err{GP_ERR_INVALID_ARG, "need nu1+nu2 >= 1, inner >= 1, max_outer >= 1"};
+        if (p.inner > kMaxInner / 2 || p.inner_adapt < 0 || p.inner_adapt > 1)
+            throw Err{GP_ERR_INVALID_ARG, "need inner <= 8 and inner_adapt 0 or 1"};
         if (p.accel && (p.restart < 1 || p.restart > kMaxKrylov - 1))
             throw Err{GP_ERR_INVALID_ARG, "restart must be in 1..15"};
         if (p.band_vcycles < 1) throw Err{GP_ERR_INVALID_ARG, "band_vcycles must be >= 1"};
@@ -1658,40 +1673,6 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
         if (!phi_dev || !rho_dev) throw Err{GP_ERR_INVALID_ARG, "bad arguments"};
         if (!c->have_eps) throw Err{GP_ERR_STATE, "gp_set_dielectric must precede gp_energy_forces"};
         const double dv = c->g.hx * c->g.hy * c->g.hz;
-        const bool forces = forces_dev && c->n_atoms > 0;
-        const bool branch = forces && gauss_dev;
-        const int n = c->n_atoms;
-        if (forces) ensure_forces(c, n);
-        // The charge term (df64 on the FP32 pipe) runs on a second stream beside the
-        // energy and the dielectric term (both bound by the FP64 pipe), so that the
-        // two pipes work at once; the streams join before the forces are assembled.
-        if (branch) {
-            GP_CUDA(cudaEventRecord(c->ev_fork, c->s));
-            GP_CUDA(cudaStreamWaitEvent(c->gs, c->ev_fork, 0));
-            GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->gs));
-            Atoms at{c->atoms, c->atoms32, gauss_dev, n};
-            const GaussTabs gt = ensure_gtab(c, n);
-            {
-                ProfScope ps(c, GP_PROF_FORCES_RHO, 2, c->gs);
-                launch_gauss_tables(c->g, at, 8.0, gt, c->gs);
-                launch_forces_rho(c->g, gt, phi_dev, c->forces_T, c->gs);
-            }
-            GP_CHECK_LAUNCH();
-            GP_CUDA(cudaEventRecord(c->ev_join, c->gs));
-        }
-        if (forces) {
-            GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
-            Atoms at{c->atoms, c->atoms32, gauss_dev, n};
-            const DielParams dp = c->dp;
-            {
-                ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
-                if (c->prm.kind != 0)
-                    launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
-                else
-                    launch_forces_eps(c->g, at, dp, c->sw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
-            }
-            GP_CHECK_LAUNCH();
-        }
         if (energy_host) {
             {
                 ProfScope ps(c, GP_PROF_ENERGY, 1);
@@ -1703,8 +1684,28 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             energy_host[0] = 0.5 * dv * e2[0];
             energy_host[1] = dv / (8.0 * kPi) * e2[1];
         }
-        if (forces) {
-            if (branch) GP_CUDA(cudaStreamWaitEvent(c->s, c->ev_join, 0));
+        if (forces_dev && c->n_atoms > 0) {
+            const int n = c->n_atoms;
+            ensure_forces(c, n);
+            GP_CUDA(cudaMemsetAsync(c->forces_S, 0, sizeof(double) * 3 * n, c->s));
+            GP_CUDA(cudaMemsetAsync(c->forces_T, 0, sizeof(double) * 3 * n, c->s));
+            Atoms at{c->atoms, c->atoms32, gauss_dev, n};
+            const DielParams dp = c->dp;
+            {
+                ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
+                if (c->prm.kind != 0)
+                    launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
+                else
+                    launch_forces_eps(c->g, at, dp, c->sw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
+            }
+            GP_CHECK_LAUNCH();
+            if (gauss_dev) {
+                const GaussTabs gt = ensure_gtab(c, n);
+                ProfScope ps(c, GP_PROF_FORCES_RHO, 2);
+                launch_gauss_tables(c->g, at, 8.0, gt, c->s);
+                launch_forces_rho(c->g, gt, phi_dev, c->forces_T, c->s);
+            }
+            GP_CHECK_LAUNCH();
             ProfScope ps(c, GP_PROF_MISC, 1);
             launch_forces_finish(c->forces_S, gauss_dev ? c->forces_T : nullptr, n, -dv / (8.0 * kPi), dv,
                                  forces_dev, c->s);
@@ -1971,8 +1972,6 @@ void gp_destroy(gp_ctx* c) {
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->gs) cudaStreamDestroy(c->gs);
     for (void* p : c->misc) cudaFree(p);
     if (c->atoms) cudaFree(c->atoms);

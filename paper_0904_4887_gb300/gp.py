@@ -35,7 +35,8 @@ class gp_params(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("accel", ctypes.c_int), ("restart", ctypes.c_int),
                 ("band_vcycles", ctypes.c_int), ("graph_outer", ctypes.c_int),
                 ("sweep_shape", ctypes.c_int), ("kind", ctypes.c_int), ("beta", ctypes.c_double),
-                ("zlim", ctypes.c_double), ("nu_coarse", ctypes.c_int), ("gamma_tail", ctypes.c_double)]
+                ("zlim", ctypes.c_double), ("nu_coarse", ctypes.c_int), ("inner_adapt", ctypes.c_int),
+                ("gamma_tail", ctypes.c_double)]
 
 
 class gp_stats(ctypes.Structure):
