@@ -109,7 +109,8 @@ typedef struct {
                              finest; 0 = nu1, nu2 there too (0) */
     int inner_adapt;      /* full box: 1 = the first correction runs `inner` CG iterations, each later
                              one as many as the contraction measured over the previous one predicts for
-                             half the tolerance (1 .. 2 inner); 0 = `inner` every time (1) */
+                             half the tolerance (1 .. 2 inner; with precision 1 for at most a 1e-5
+                             reduction, the reach of one FP32 correction); 0 = `inner` every time (1) */
     double gamma_tail;    /* kinds 1, 2: bound on the part of gamma the image sum leaves out, in
                              (0, 1e-3] (1e-13). The radius R is the smallest with
                              (4 pi/3V) exp(-R)(u^3 + 3u^2 + 6u + 6) sum_a exp(rvdw_a) <= gamma_tail,

@@ -184,6 +184,9 @@ struct gp_ctx {
     float2* epsd = nullptr;
     bool epsd_ok = false;          // epsd matches eps64
     int rvdw_n = 0, rvdw_cap = 0;
+    void* ctab = nullptr;          // coordinate tables of the tabulated dielectric and its force (CoordTabs)
+    size_t ctab_cap = 0;           // bytes
+    CoordTabs ct_s{}, ct_h{};      // views: s(d) coordinates (build), h(d) coordinates and displacements (force)
     void* gtab = nullptr;          // periodized Gaussian factor tables (GaussTabs)
     size_t gtab_cap = 0;           // bytes
     SwTables sw{};
@@ -1077,7 +1080,10 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
             int k = c->prm.inner;
             if (c->prm.inner_adapt && last_inner > 0 && rn > 0.0 && last_rn > rn) {
                 const double rate = std::min(std::max(std::pow(rn / last_rn, 1.0 / last_inner), 0.01), 0.9);
-                const double need = std::log(0.5 * tol / rn) / std::log(rate);
+                // an FP32 correction cannot reduce the residual by much more than 1e-5 (its own
+                // rounding), so no more iterations are spent on one than that reduction needs
+                const double target = sizeof(T) == 4 ? std::max(0.5 * tol, 1e-5 * rn) : 0.5 * tol;
+                const double need = std::log(target / rn) / std::log(rate);
                 k = std::min(std::max((int)std::ceil(need - 1e-9), 1), 2 * c->prm.inner);
             }
             pcg<T>(c, F, k);
@@ -1537,16 +1543,33 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             tb.h_qhi = (p.r0 + 3.5 * p.w) * (p.r0 + 3.5 * p.w);
             tb.h_inv_dq = kSwNI / (tb.h_qhi - tb.h_qlo);
             tb.h_dq = (tb.h_qhi - tb.h_qlo) / kSwNI;
-            ProfScope ps(c, GP_PROF_EPS, 1);
-            launch_switch_tables(dp, tb, c->sw_coef, c->sw_coef + (size_t)kSwNI * (kSwDeg + 1), c->sw_pack,
-                                 c->sw_pack + (size_t)kSwNI * 4, c->s);
+            {
+                ProfScope ps(c, GP_PROF_EPS, 1);
+                launch_switch_tables(dp, tb, c->sw_coef, c->sw_coef + (size_t)kSwNI * (kSwDeg + 1), c->sw_pack,
+                                     c->sw_pack + (size_t)kSwNI * 4, c->s);
+            }
+            // the per-atom table coordinates of both tables (one FP64 pass, then loads)
+            const int nmax = std::max(c->g.nx, std::max(c->g.ny, c->g.nz));
+            const size_t bs = coord_tabs_bytes(n_atoms, nmax, false), bh = coord_tabs_bytes(n_atoms, nmax, true);
+            if (bs + bh > c->ctab_cap) {
+                if (c->ctab) cudaFree(c->ctab);
+                c->ctab = nullptr;
+                c->ctab_cap = 0;
+                if (cudaMalloc(&c->ctab, bs + bh) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+                c->ctab_cap = bs + bh;
+            }
+            c->ct_s = coord_tabs_view(c->ctab, n_atoms, nmax, false);
+            c->ct_h = coord_tabs_view(static_cast<char*>(c->ctab) + bs, n_atoms, nmax, true);
+            ProfScope ps(c, GP_PROF_EPS, 2);
+            launch_coord_tables(c->g, at, tb.s_qlo, tb.s_inv_dq, c->ct_s, c->s);
+            launch_coord_tables(c->g, at, tb.h_qlo, tb.h_inv_dq, c->ct_h, c->s);
         }
         c->sw = tb;
         {
             ProfScope ps(c, GP_PROF_EPS, 1);
             // pe64 holds the per-point factor of d eps/d R: eps - 1 (kind 0) or d eps/d gamma (kinds 1, 2)
             if (p.kind != 0) launch_build_eps_gamma(c->g, at, dp, c->rvdw, c->eps64, c->pe64, c->eps32, c->s);
-            else launch_build_eps(c->g, at, dp, tb, c->eps64, c->pe64, c->eps32, c->s);
+            else launch_build_eps(c->g, at, dp, tb, c->ct_s, c->eps64, c->pe64, c->eps32, c->s);
         }
         c->epsd_ok = false;
         GP_CHECK_LAUNCH();
@@ -1585,6 +1608,7 @@ gp_status gp_set_vdw_radii(gp_ctx* c, const double* radii_dev, int n_atoms) {
             if (!(v > 0.0)) throw Err{GP_ERR_INVALID_ARG, "van der Waals radii must be positive"};
         if (n_atoms > c->rvdw_cap) {
             if (c->rvdw) cudaFree(c->rvdw);
+    if (c->ctab) cudaFree(c->ctab);
             c->rvdw = nullptr;
             if (cudaMalloc(&c->rvdw, sizeof(double) * n_atoms) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
             c->rvdw_cap = n_atoms;
@@ -1696,7 +1720,7 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
                 if (c->prm.kind != 0)
                     launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
                 else
-                    launch_forces_eps(c->g, at, dp, c->sw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
+                    launch_forces_eps(c->g, at, dp, c->sw, c->ct_h, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
             }
             GP_CHECK_LAUNCH();
             if (gauss_dev) {
@@ -1842,7 +1866,7 @@ gp_status gp_energy_forces6(gp_ctx* c, const double* phi_dev, double mu, const d
                 if (c->prm.kind != 0)
                     launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, c->f6_w, c->pe64, c->forces_S, c->s);
                 else
-                    launch_forces_eps(c->g, at, dp, c->sw, phi_dev, c->f6_w, c->pe64, c->forces_S, c->s);
+                    launch_forces_eps(c->g, at, dp, c->sw, c->ct_h, phi_dev, c->f6_w, c->pe64, c->forces_S, c->s);
             }
             GP_CHECK_LAUNCH();
             if (gauss_dev) {

@@ -110,13 +110,26 @@ struct SwTables {
     double h_qlo = 0, h_qhi = 0, h_inv_dq = 0, h_dq = 0;
 };
 
+// Table coordinates of the separable squared distance, per atom, image digit
+// m in {0, 1, 2} (shift (m - 1) L) and grid index along each axis:
+//   X = ((i hx - cx)^2 - qlo) / dq,  Y = (j hy - cy)^2 / dq,  Z = (k hz - cz)^2 / dq,
+// computed once per dielectric in FP64 and kept as an integer part n and a df
+// fraction f in [0, 1) (and, for the force tables, the displacement d as a df),
+// so that the tile kernels stage them with loads instead of FP64 arithmetic.
+// Entry (a, m, axis, i) sits at ((a * 3 + m) * 3 + axis) * nmax + i.
+struct CoordTabs {
+    int* n;
+    float2* f;
+    float2* d;      // displacement i h - c (force tables), or null
+    int nmax;
+};
 // ---------------------------------------------------------------- launchers
 // fields (k_fields.cu)
 void launch_wrap_atoms(const Geo& g, const double* pos, int n, double* w64, float4* w32, cudaStream_t s);
 void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, double* h_coef, float4* s_pack,
                           float4* h_pack, cudaStream_t s);
-void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, double* eps64, double* pe64,
-                      float* eps32, cudaStream_t s);
+void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct, double* eps64,
+                      double* pe64, float* eps32, cudaStream_t s);
 // Eq. 9-10: gamma = sum exp(-(d - rvdw)), eps = 1 + (eps0 - 1)/(1 + gamma^(2 beta)); fe64 = d eps / d gamma
 void launch_build_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, double* eps64, double* fe64,
                             float* eps32, cudaStream_t s);
@@ -133,6 +146,9 @@ struct GaussTabs {
     int* win;       // [G][3][2] conservative index window of the unshifted image
     int G, nmax;
 };
+size_t coord_tabs_bytes(int n_atoms, int nmax, bool with_d);
+CoordTabs coord_tabs_view(void* base, int n_atoms, int nmax, bool with_d);
+void launch_coord_tables(const Geo& g, Atoms at, double qlo, double inv_dq, const CoordTabs& ct, cudaStream_t s);
 size_t gauss_tabs_bytes(int n_atoms, int nmax);
 GaussTabs gauss_tabs_view(void* base, int n_atoms, int nmax);
 void launch_gauss_tables(const Geo& g, Atoms at, double cut_sigmas, const GaussTabs& gt, cudaStream_t s);
@@ -140,8 +156,8 @@ void launch_build_rho_raw(const Geo& g, const GaussTabs& gt, double* rho, cudaSt
 void launch_plane_max(const Geo& g, const double* eps64, double* plane_max, cudaStream_t s);
 void launch_energy(const Geo& g, const double* rho, const double* phi, const double* eps64,
                    double* partial, cudaStream_t s);
-void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const double* phi,
-                       const double* wext, const double* pe64, double* S, cudaStream_t s);
+void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct,
+                       const double* phi, const double* wext, const double* pe64, double* S, cudaStream_t s);
 void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, double* T, cudaStream_t s);
 void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,
                           cudaStream_t s);

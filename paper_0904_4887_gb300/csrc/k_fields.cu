@@ -481,13 +481,51 @@ __device__ __forceinline__ df sw_poly(const float4* __restrict__ tab, int k, df 
     return acc;
 }
 
+// ----------------------------------------------------------------- coordinate tables
+// One thread per (atom a, image digit m, axis, grid index i): the table coordinate
+// of the separable squared distance from grid line i to the image centre
+// c = w64[a] + (m - 1) L, as an integer part and a df fraction (sw_coord), and the
+// displacement i h - c as a df, all from one FP64 evaluation. The tile kernels
+// that stage these per (tile, atom image) then load them instead of computing
+// them: on GB300 every FP64 instruction of a warp holds the FP64 pipe for about
+// 64 cycles, and the per-tile staging was most of the dielectric kernels' time.
+__global__ void k_coord_tables(Geo g, Atoms at, double qlo, double inv_dq, CoordTabs ct) {
+    const long total = (long)at.n * 9 * ct.nmax;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % ct.nmax);
+        const long r = q / ct.nmax;
+        const int axis = (int)(r % 3), m = (int)((r / 3) % 3), a = (int)(r / 9);
+        const int nax = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+        if (i >= nax) continue;
+        const double h = axis == 0 ? g.hx : (axis == 1 ? g.hy : g.hz);
+        const double L = axis == 0 ? g.lx : (axis == 1 ? g.ly : g.lz);
+        // the same operations, in the same order, as the per-tile staging they replace
+        const double c = at.w64[3 * a + axis] + (m - 1) * L;
+        const double d = i * h - c;
+        const double v = axis == 0 ? (d * d - qlo) * inv_dq : d * d * inv_dq;
+        const SwCoord sc = sw_coord(v);
+        ct.n[q] = sc.n;
+        ct.f[q] = make_float2(sc.f.hi, sc.f.lo);
+        if (ct.d) {
+            const df dd = df_from(d);
+            ct.d[q] = make_float2(dd.hi, dd.lo);
+        }
+    }
+}
+
+__device__ __forceinline__ long ctab_index(const CoordTabs& ct, int a, int im, int axis, int i) {
+    const int m = axis == 0 ? im % 3 : (axis == 1 ? (im / 3) % 3 : im / 9);
+    return ((long)(a * 3 + m) * 3 + axis) * ct.nmax + i;
+}
+
 // ----------------------------------------------------------------- eps, tabulated (df64)
 // The same product as k_build_eps, with s from the packed table in df64
 // arithmetic (about 120 FP32 instructions per pair instead of 25 FP64 ones).
 // Tiles are 32 x 4 x 16 points, each thread taking 4 points along z, so the
-// per-(tile, atom image) staging in FP64 is shared by 2048 points. The tile
-// first collects its atom images within reach (r0 + 6w: s == 1 beyond) into
-// one list, processed when full or at the end, in batches of EB images.
+// per-(tile, atom image) staging (table coordinates loaded from the coordinate
+// tables) is shared by 2048 points. The tile first collects its atom images
+// within reach (r0 + 6w: s == 1 beyond) into one list, processed when full or at
+// the end, in batches of EB images.
 constexpr int EZ = 16;                  // z extent of the tabulated-eps tiles
 constexpr int EB = 32;                  // atom images staged at a time
 constexpr int ACHS = 8;                 // atoms culled per pass (at most 216 images)
@@ -504,9 +542,9 @@ __device__ __forceinline__ Tile make_tile_ez(const Geo& g) {
     return t;
 }
 
-__global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb, double* eps64,
-                                                      double* pe64, float* eps32) {
-    __shared__ double ec[ECAP][3];
+__global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb, CoordTabs ct,
+                                                      double* eps64, double* pe64, float* eps32) {
+    __shared__ int eai[ECAP][2];                 // (atom, image) of each surviving image
     __shared__ int cn[EB][NS];
     __shared__ df cf[EB][NS];
     __shared__ int ne;
@@ -535,7 +573,8 @@ __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParam
             image32(at.w32, a, im, g, fx, fy, fz);
             if (box_d2(t, fx, fy, fz) < reach * reach) {
                 const int s = atomicAdd(&ne, 1);
-                image64(at.w64, a, im, g, ec[s][0], ec[s][1], ec[s][2]);
+                eai[s][0] = a;
+                eai[s][1] = im;
             }
         }
         __syncthreads();
@@ -545,20 +584,15 @@ __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParam
                 const int ms = min(EB, m - e0);
                 for (int r = threadIdx.x; r < ms * NS; r += TT) {
                     const int e = r / NS, c = r % NS;
-                    double v;
-                    if (c < TX) {
-                        const double d = (t.i0 + c) * g.hx - ec[e0 + e][0];
-                        v = (d * d - tb.s_qlo) * tb.s_inv_dq;
-                    } else if (c < TX + TY) {
-                        const double d = (t.j0 + c - TX) * g.hy - ec[e0 + e][1];
-                        v = d * d * tb.s_inv_dq;
-                    } else {
-                        const double d = (t.k0 + c - TX - TY) * g.hz - ec[e0 + e][2];
-                        v = d * d * tb.s_inv_dq;
-                    }
-                    const SwCoord sc = sw_coord(v);
-                    cn[e][c] = sc.n;
-                    cf[e][c] = sc.f;
+                    // grid index of this staged column / row / plane, clamped on ragged tiles
+                    // (the clamped values are never read: those points are not live)
+                    int axis, gi;
+                    if (c < TX) { axis = 0; gi = min(t.i0 + c, g.nx - 1); }
+                    else if (c < TX + TY) { axis = 1; gi = min(t.j0 + c - TX, g.ny - 1); }
+                    else { axis = 2; gi = min(t.k0 + c - TX - TY, g.nz - 1); }
+                    const long q = ctab_index(ct, eai[e0 + e][0], eai[e0 + e][1], axis, gi);
+                    cn[e][c] = __ldg(ct.n + q);
+                    cf[e][c] = as_df(__ldg(ct.f + q));
                 }
                 __syncthreads();
                 if (live[0] || live[1] || live[2] || live[3]) {
@@ -636,38 +670,19 @@ __device__ __forceinline__ double force_weight(const Geo& g, const double* phi, 
 // ----------------------------------------------------------------- eps force, tabulated (df64)
 // The same sum as k_forces_eps with h = s'/(s d) from the packed table in df64
 // arithmetic, on 32 x 4 x 16 tiles. One warp per (tile, atom image): it
-// stages in df the table coordinates and displacements of the tile's 32
-// columns, 4 rows and 16 planes (about 1e-14 relative in h, well inside what
-// the force needs), runs over the 2048 points with compensated FP32 sums, and
-// reduces across the warp in df before one FP64 atomic per component.
+// loads the table coordinates and displacements of the tile's 32 columns, 4
+// rows and 16 planes from the coordinate tables (FP64-exact, as df), runs over
+// the 2048 points with compensated FP32 sums, and reduces across the warp in
+// df; the CTA then turns every image's sum into FP64 atomics with full warps.
 constexpr int ECAPF = 384;              // image list capacity of the force kernel
 
-// exact-to-2^-48 df of the integer c times h (h as a df)
-__device__ __forceinline__ df df_int_mul(int c, df h) {
-    const float cf_ = (float)c;
-    const float p = cf_ * h.hi;
-    const float e = fmaf(cf_, h.hi, -p) + cf_ * h.lo;
-    return df_quick(p, e);
-}
-
-// table coordinate n + f (f in [0, 1)) of v held as a df
-__device__ __forceinline__ SwCoord sw_coord_df(df v) {
-    SwCoord c;
-    float fl = floorf(v.hi);
-    df f = df_quick(v.hi - fl, v.lo);          // v.hi - fl is exact
-    if (f.hi < 0.f) { fl -= 1.f; f = df_add(f, df{1.f, 0.f}); }
-    else if (f.hi >= 1.f) { fl += 1.f; f = df_add(f, df{-1.f, 0.f}); }
-    c.n = (int)fl;
-    c.f = f;
-    return c;
-}
-
-__global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb,
+__global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb, CoordTabs ct,
                                                        const double* phi, const double* wext, const double* pe64,
                                                        double* S) {
     __shared__ df Ws[TX * TY * EZ];              // index tx + TX (ty + TY z)
-    __shared__ df eb[ECAPF][3];                  // displacement of column/row/plane 0 from the image
+    __shared__ df eres[ECAPF][3];                // each image's sum, converted to FP64 by a full warp
     __shared__ int eatom[ECAPF];
+    __shared__ int eimg[ECAPF];
     __shared__ int wn[TT / 32][NS];
     __shared__ df wf[TT / 32][NS];
     __shared__ df wd[TT / 32][NS];
@@ -701,8 +716,6 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
     const float rc2f = (float)(p.rcut * p.rcut);
     const float dq = (float)tb.h_dq, qlo = (float)tb.h_qlo;
     const float r0f = (float)p.r0, iwf = (float)p.iw, spf_norm = (float)p.sp_norm;
-    const df hx = df_from(g.hx), hy = df_from(g.hy), hz = df_from(g.hz);
-    const df inv = df_from(tb.h_inv_dq), mqlo = df_from(-tb.h_qlo);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
     if (threadIdx.x == 0) ne = 0;
@@ -715,12 +728,8 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
             image32(at.w32, a, im, g, fx, fy, fz);
             if (box_d2(t, fx, fy, fz) < rcf * rcf) {
                 const int s = atomicAdd(&ne, 1);
-                double cx, cy, cz;
-                image64(at.w64, a, im, g, cx, cy, cz);
-                eb[s][0] = df_from(t.i0 * g.hx - cx);
-                eb[s][1] = df_from(t.j0 * g.hy - cy);
-                eb[s][2] = df_from(t.k0 * g.hz - cz);
                 eatom[s] = a;
+                eimg[s] = im;
             }
         }
         __syncthreads();
@@ -728,21 +737,15 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
         if (m > ECAPF - ACHS * 27 || a0 + ACHS >= at.n) {
             for (int e = warp; e < m; e += TT / 32) {
                 for (int c = lane; c < NS; c += 32) {
-                    df d, v;
-                    if (c < TX) {
-                        d = df_add(eb[e][0], df_int_mul(c, hx));
-                        v = df_mul(df_add(df_mul(d, d), mqlo), inv);
-                    } else if (c < TX + TY) {
-                        d = df_add(eb[e][1], df_int_mul(c - TX, hy));
-                        v = df_mul(df_mul(d, d), inv);
-                    } else {
-                        d = df_add(eb[e][2], df_int_mul(c - TX - TY, hz));
-                        v = df_mul(df_mul(d, d), inv);
-                    }
-                    const SwCoord sc = sw_coord_df(v);
-                    wn[warp][c] = sc.n;
-                    wf[warp][c] = sc.f;
-                    wd[warp][c] = d;
+                    // grid index of this column / row / plane, clamped on ragged tiles (never read there)
+                    int axis, gi;
+                    if (c < TX) { axis = 0; gi = min(t.i0 + c, g.nx - 1); }
+                    else if (c < TX + TY) { axis = 1; gi = min(t.j0 + c - TX, g.ny - 1); }
+                    else { axis = 2; gi = min(t.k0 + c - TX - TY, g.nz - 1); }
+                    const long q = ctab_index(ct, eatom[e], eimg[e], axis, gi);
+                    wn[warp][c] = __ldg(ct.n + q);
+                    wf[warp][c] = as_df(__ldg(ct.f + q));
+                    wd[warp][c] = as_df(__ldg(ct.d + q));
                 }
                 __syncwarp();
                 float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
@@ -776,14 +779,20 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
                 }
                 warp_sum_df(sx, cx); warp_sum_df(sy, cy); warp_sum_df(sz, cz);
                 if (lane == 0) {
-                    const int a = eatom[e];
-                    const double fx = (double)sx + (double)cx, fy = (double)sy + (double)cy,
-                                 fz = (double)sz + (double)cz;
-                    if (fx != 0.0) atomicAdd(&S[3 * a + 0], fx);
-                    if (fy != 0.0) atomicAdd(&S[3 * a + 1], fy);
-                    if (fz != 0.0) atomicAdd(&S[3 * a + 2], fz);
+                    eres[e][0] = df{sx, cx};
+                    eres[e][1] = df{sy, cy};
+                    eres[e][2] = df{sz, cz};
                 }
                 __syncwarp();
+            }
+            __syncthreads();
+            // the images' sums to FP64 and into S: one entry per thread, so each FP64
+            // instruction runs with a full warp (a warp instruction holds the FP64 pipe
+            // for as long whether one lane or 32 are active)
+            for (int e = threadIdx.x; e < 3 * m; e += TT) {
+                const int ee = e / 3, comp = e % 3;
+                const double v = (double)eres[ee][comp].hi + (double)eres[ee][comp].lo;
+                if (v != 0.0) atomicAdd(&S[3 * eatom[ee] + comp], v);
             }
             __syncthreads();
             if (threadIdx.x == 0) ne = 0;
@@ -1155,6 +1164,7 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
 // per warp in shared memory), then scales by X' or X and the warp reduces.
 __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, GaussTabs gt, const double* phi, double* T) {
     __shared__ int ent[TT];
+    __shared__ df eres[TT][3];                  // each Gaussian's sum, converted to FP64 by a full warp
     __shared__ df ph[TT];                       // index tx + TX (ty + TY tz)
     __shared__ df wr[TT / 32][3][TY * TZ];
     __shared__ int ne;
@@ -1209,13 +1219,18 @@ __global__ void __launch_bounds__(TT) k_forces_rho(Geo g, GaussTabs gt, const do
             df fz = df_mul(X, df_quick(sz, cz));
             warp_sum_df(fx.hi, fx.lo); warp_sum_df(fy.hi, fy.lo); warp_sum_df(fz.hi, fz.lo);
             if (lane == 0) {
-                const int a = ge >> 1;
-                const double vx = df_to(fx), vy = df_to(fy), vz = df_to(fz);
-                if (vx != 0.0) atomicAdd(&T[3 * a + 0], vx);
-                if (vy != 0.0) atomicAdd(&T[3 * a + 1], vy);
-                if (vz != 0.0) atomicAdd(&T[3 * a + 2], vz);
+                eres[e][0] = fx;
+                eres[e][1] = fy;
+                eres[e][2] = fz;
             }
             __syncwarp();
+        }
+        __syncthreads();
+        // to FP64 and into T with full warps (see k_forces_eps_tab)
+        for (int e = threadIdx.x; e < 3 * m; e += TT) {
+            const int ee = e / 3, comp = e % 3;
+            const double v = df_to(eres[ee][comp]);
+            if (v != 0.0) atomicAdd(&T[3 * (ent[ee] >> 1) + comp], v);
         }
         __syncthreads();
     }
@@ -1241,9 +1256,31 @@ void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, doub
     k_switch_tables<<<(2 * kSwNI + 127) / 128, 128, 0, s>>>(p, tb, s_coef, h_coef, s_pack, h_pack);
 }
 
-void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, double* eps64, double* pe64,
-                      float* eps32, cudaStream_t s) {
-    if (tb.s32) k_build_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
+size_t coord_tabs_bytes(int n_atoms, int nmax, bool with_d) {
+    const size_t e = (size_t)(n_atoms > 0 ? n_atoms : 1) * 9 * nmax;
+    return e * (sizeof(int) + sizeof(float2) + (with_d ? sizeof(float2) : 0)) + 256;
+}
+
+CoordTabs coord_tabs_view(void* base, int n_atoms, int nmax, bool with_d) {
+    const size_t e = (size_t)(n_atoms > 0 ? n_atoms : 1) * 9 * nmax;
+    CoordTabs ct{};
+    ct.nmax = nmax;
+    ct.f = static_cast<float2*>(base);
+    ct.d = with_d ? ct.f + e : nullptr;
+    ct.n = reinterpret_cast<int*>(ct.f + (with_d ? 2 : 1) * e);
+    return ct;
+}
+
+void launch_coord_tables(const Geo& g, Atoms at, double qlo, double inv_dq, const CoordTabs& ct, cudaStream_t s) {
+    const long total = (long)at.n * 9 * ct.nmax;
+    if (total > 0)
+        k_coord_tables<<<(int)((total + 255) / 256 < 152L * 16 ? (total + 255) / 256 : 152L * 16), 256, 0, s>>>(
+            g, at, qlo, inv_dq, ct);
+}
+
+void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct, double* eps64,
+                      double* pe64, float* eps32, cudaStream_t s) {
+    if (tb.s32) k_build_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, ct, eps64, pe64, eps32);
     else k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
 }
 
@@ -1298,9 +1335,9 @@ void launch_energy(const Geo& g, const double* rho, const double* phi, const dou
     k_energy<<<kReduceBlocks, kReduceThreads, 0, s>>>(g, rho, phi, eps64, partial);
 }
 
-void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const double* phi,
-                       const double* wext, const double* pe64, double* S, cudaStream_t s) {
-    if (tb.h32) k_forces_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, phi, wext, pe64, S);
+void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct,
+                       const double* phi, const double* wext, const double* pe64, double* S, cudaStream_t s) {
+    if (tb.h32) k_forces_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, ct, phi, wext, pe64, S);
     else k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, wext, pe64, S);
 }
 
