@@ -1522,6 +1522,8 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             double se = 0.0;
             for (int a = 0; a < n_atoms; ++a) se += std::exp(c->rvdw_host[a]);
             dp.rcut = n_atoms > 0 ? gamma_cutoff(c->g, se, p.gamma_tail) : 1.0;
+            dp.rcutf = (float)dp.rcut;
+            dp.rc2f = (float)(dp.rcut * dp.rcut);
             dp.mx = (int)std::ceil(dp.rcut / c->g.lx);
             dp.my = (int)std::ceil(dp.rcut / c->g.ly);
             dp.mz = (int)std::ceil(dp.rcut / c->g.lz);
@@ -1543,6 +1545,8 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             tb.h_qhi = (p.r0 + 3.5 * p.w) * (p.r0 + 3.5 * p.w);
             tb.h_inv_dq = kSwNI / (tb.h_qhi - tb.h_qlo);
             tb.h_dq = (tb.h_qhi - tb.h_qlo) / kSwNI;
+            tb.s_qlof = (float)tb.s_qlo; tb.s_dqf = (float)tb.s_dq;
+            tb.h_qlof = (float)tb.h_qlo; tb.h_dqf = (float)tb.h_dq;
             {
                 ProfScope ps(c, GP_PROF_EPS, 1);
                 launch_switch_tables(dp, tb, c->sw_coef, c->sw_coef + (size_t)kSwNI * (kSwDeg + 1), c->sw_pack,

@@ -50,6 +50,7 @@ struct Geo {
     double c2x, c2y, c2z;   // 1 / (2 h^2): face-mean operator weight per axis
     double inv_n;           // 1 / (nx ny nz)
     float lxf, lyf, lzf;    // cell lengths in FP32 (culling)
+    float hxf, hyf, hzf;    // spacings in FP32 (culling boxes)
 };
 
 inline Geo make_geo(int nx, int ny, int nz, double lx, double ly, double lz) {
@@ -61,6 +62,7 @@ inline Geo make_geo(int nx, int ny, int nz, double lx, double ly, double lz) {
     g.c2x = 0.5 / (g.hx * g.hx); g.c2y = 0.5 / (g.hy * g.hy); g.c2z = 0.5 / (g.hz * g.hz);
     g.inv_n = 1.0 / ((double)nx * ny * nz);
     g.lxf = (float)lx; g.lyf = (float)ly; g.lzf = (float)lz;
+    g.hxf = (float)g.hx; g.hyf = (float)g.hy; g.hzf = (float)g.hz;
     return g;
 }
 
@@ -76,7 +78,40 @@ struct DielParams {
     double esat;      // kind 2: growing exponent beyond which eps = 1 exactly (ln(eps0-1)+37)/(2 beta)
     int kind;
     int mx, my, mz;   // kinds 1, 2: images n in [-m, m] per axis reach every point within rcut
+    // FP32 copies for the culling and the FP32 branches, made on the host: a kernel that
+    // converted them per thread would spend FP64-pipe instructions on it (and may redo them)
+    float rcutf, rc2f, reachf, tinyf, r0f, iwf, spnf;
 };
+
+// (hi, lo) = (RN_float(x), RN_float(x - hi)): the float pair of a double, as a cast
+// would give it, from the bits with integer instructions. On GB300 each FP64
+// instruction of a warp (casts between double and float included) holds the
+// FP64 pipe for about 64 cycles; this takes none. IEEE 754 binary64 -> binary32
+// rounding to nearest even: keep the top 23 of the 52 mantissa bits, round on
+// the other 29 (a carry moves into the exponent field by itself); the residual
+// is those 29 bits less the rounding, times 2^(E - 1075), exact in a double and
+// rounded once by the int-to-float cast. Below 2^-63, where lo might be
+// subnormal, and above the float range the casts themselves are used.
+__device__ __forceinline__ float2 split_to_float2(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
+    const unsigned sign = h & 0x80000000u;
+    const int E = (int)((h >> 20) & 0x7ffu);
+    const int e = E - 1023 + 127;
+    if (E < 960) {                     // |x| < 2^-63: lo might be subnormal; the casts (rare)
+        const float hi = (float)x;
+        return make_float2(hi, (float)(x - (double)hi));
+    }
+    if (e >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+    const unsigned m23 = ((h & 0xfffffu) << 3) | (l >> 29);
+    const unsigned rem = l & 0x1fffffffu;
+    const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
+    const float hi = __uint_as_float(sign | ((((unsigned)e << 23) | m23) + up));
+    const int r = (int)rem - (int)(up << 29);
+    float lo = ldexpf((float)r, E - 1075);
+    if (sign && r != 0) lo = -lo;          // x - hi = 0 is +0, as the cast gives it
+    return make_float2(hi, lo);
+}
 
 inline DielParams make_diel(double eps0, double r0, double w, double rcut, int kind = 0, double beta = 2.4,
                             double zlim = 0.0) {
@@ -90,6 +125,13 @@ inline DielParams make_diel(double eps0, double r0, double w, double rcut, int k
     p.sp_norm = 1.0 / (w * 1.7724538509055160273);
     p.tiny = 5.5e-17 / (eps0 - 1.0 > 0.0 ? eps0 - 1.0 : 1.0);
     p.mx = p.my = p.mz = 1;
+    p.rcutf = (float)rcut;
+    p.rc2f = (float)(rcut * rcut);
+    p.reachf = (float)(rcut < r0 + 6.0 * w ? rcut : r0 + 6.0 * w);
+    p.tinyf = (float)p.tiny;
+    p.r0f = (float)r0;
+    p.iwf = (float)p.iw;
+    p.spnf = (float)p.sp_norm;
     return p;
 }
 
@@ -108,6 +150,7 @@ struct SwTables {
     const float4* h32 = nullptr;
     double s_qlo = 0, s_qhi = 0, s_inv_dq = 0, s_dq = 0;
     double h_qlo = 0, h_qhi = 0, h_inv_dq = 0, h_dq = 0;
+    float s_qlof = 0, s_dqf = 0, h_qlof = 0, h_dqf = 0;   // FP32 copies, set on the host
 };
 
 // Table coordinates of the separable squared distance, per atom, image digit

@@ -60,9 +60,9 @@ __device__ __forceinline__ Tile make_tile(const Geo& g) {
     Tile t;
     t.i0 = blockIdx.x * TX; t.j0 = blockIdx.y * TY; t.k0 = blockIdx.z * TZ;
     t.i1 = min(t.i0 + TX, g.nx) - 1; t.j1 = min(t.j0 + TY, g.ny) - 1; t.k1 = min(t.k0 + TZ, g.nz) - 1;
-    t.bx0 = (float)(t.i0 * g.hx); t.bx1 = (float)(t.i1 * g.hx);
-    t.by0 = (float)(t.j0 * g.hy); t.by1 = (float)(t.j1 * g.hy);
-    t.bz0 = (float)(t.k0 * g.hz); t.bz1 = (float)(t.k1 * g.hz);
+    t.bx0 = (float)t.i0 * g.hxf; t.bx1 = (float)t.i1 * g.hxf;   // FP32: the culling keeps a margin
+    t.by0 = (float)t.j0 * g.hyf; t.by1 = (float)t.j1 * g.hyf;
+    t.bz0 = (float)t.k0 * g.hzf; t.bz1 = (float)t.k1 * g.hzf;
     return t;
 }
 
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p,
     const double rc2 = p.rcut * p.rcut;
     const double iw = p.iw;
     const double tiny = p.tiny;
-    const float rcf = (float)p.rcut + kMargin;
+    const float rcf = p.rcutf + kMargin;
     double P = 1.0;
     for (int a0 = 0; a0 < at.n; a0 += ACH) {
         if (threadIdx.x == 0) ne = 0;
@@ -235,8 +235,8 @@ __global__ void __launch_bounds__(TT) k_build_eps(Geo g, Atoms at, DielParams p,
 struct df { float hi, lo; };
 
 __device__ __forceinline__ df df_from(double v) {
-    const float h = (float)v;
-    return {h, (float)(v - (double)h)};
+    const float2 p = split_to_float2(v);      // the casts' result, without the FP64 pipe
+    return {p.x, p.y};
 }
 __device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ df as_df(float2 v) { return df{v.x, v.y}; }
@@ -536,9 +536,9 @@ __device__ __forceinline__ Tile make_tile_ez(const Geo& g) {
     Tile t;
     t.i0 = blockIdx.x * TX; t.j0 = blockIdx.y * TY; t.k0 = blockIdx.z * EZ;
     t.i1 = min(t.i0 + TX, g.nx) - 1; t.j1 = min(t.j0 + TY, g.ny) - 1; t.k1 = min(t.k0 + EZ, g.nz) - 1;
-    t.bx0 = (float)(t.i0 * g.hx); t.bx1 = (float)(t.i1 * g.hx);
-    t.by0 = (float)(t.j0 * g.hy); t.by1 = (float)(t.j1 * g.hy);
-    t.bz0 = (float)(t.k0 * g.hz); t.bz1 = (float)(t.k1 * g.hz);
+    t.bx0 = (float)t.i0 * g.hxf; t.bx1 = (float)t.i1 * g.hxf;   // FP32: the culling keeps a margin
+    t.by0 = (float)t.j0 * g.hyf; t.by1 = (float)t.j1 * g.hyf;
+    t.bz0 = (float)t.k0 * g.hzf; t.bz1 = (float)t.k1 * g.hzf;
     return t;
 }
 
@@ -559,10 +559,10 @@ __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParam
         live[r] = i < g.nx && j < g.ny && t.k0 + tz + 4 * r < g.nz;
         P[r] = df{1.f, 0.f};
     }
-    const float tiny = (float)p.tiny;
-    const float reach = (float)fmin(p.rcut, p.r0 + 6.0 * p.w) + kMargin;
-    const float dq = (float)tb.s_dq, qlo = (float)tb.s_qlo;
-    const float r0f = (float)p.r0, iwf = (float)p.iw;
+    const float tiny = p.tinyf;
+    const float reach = p.reachf + kMargin;
+    const float dq = tb.s_dqf, qlo = tb.s_qlof;
+    const float r0f = p.r0f, iwf = p.iwf;
     if (threadIdx.x == 0) ne = 0;
     __syncthreads();
     for (int a0 = 0; a0 < at.n; a0 += ACHS) {
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
     __shared__ df wd[TT / 32][NS];
     __shared__ int ne;
     const Tile t = make_tile_ez(g);
-    const float rcf = (float)p.rcut + kMargin;
+    const float rcf = p.rcutf + kMargin;
     // the tile's atom images within rcut; the W field is built only if there is one
     if (threadIdx.x == 0) ne = 0;
     __syncthreads();
@@ -713,9 +713,9 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
         }
         Ws[q] = df_from(-W);   // sign of c = -W h folded in
     }
-    const float rc2f = (float)(p.rcut * p.rcut);
-    const float dq = (float)tb.h_dq, qlo = (float)tb.h_qlo;
-    const float r0f = (float)p.r0, iwf = (float)p.iw, spf_norm = (float)p.sp_norm;
+    const float rc2f = p.rc2f;
+    const float dq = tb.h_dqf, qlo = tb.h_qlof;
+    const float r0f = p.r0f, iwf = p.iwf, spf_norm = p.spnf;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
     if (threadIdx.x == 0) ne = 0;
@@ -872,7 +872,7 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma(Geo g, Atoms at, DielPar
     const bool valid = i < g.nx && j < g.ny && k < g.nz;
     const double x = i * g.hx, y = j * g.hy, z = k * g.hz;
     const double rc2 = p.rcut * p.rcut;
-    const float rcf = (float)p.rcut + kMargin;
+    const float rcf = p.rcutf + kMargin;
     const bool eq19 = p.kind == 2;
     const int nimg = (2 * p.mx + 1) * (2 * p.my + 1) * (2 * p.mz + 1);
     const long nq = (long)at.n * nimg;
@@ -949,7 +949,7 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielPa
     }
     if (__syncthreads_or(any) == 0) return;                // every point of the tile has d eps/d gamma = 0
     const double rc2 = p.rcut * p.rcut;
-    const float rcf = (float)p.rcut + kMargin;
+    const float rcf = p.rcutf + kMargin;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nimg = (2 * p.mx + 1) * (2 * p.my + 1) * (2 * p.mz + 1);
     const long nq = (long)at.n * nimg;
@@ -1035,27 +1035,48 @@ __global__ void k_plane_max(Geo g, const double* eps64, double* out) {
 
 // ----------------------------------------------------------------- energy
 // partial[2b] = sum rho phi, partial[2b+1] = sum_f eps_f (grad_f phi)^2 over block b
-__global__ void __launch_bounds__(kReduceThreads) k_energy(Geo g, const double* rho, const double* phi,
-                                                           const double* eps, double* partial) {
+// s0 = sum rho phi and s1 = sum over the x, y, z faces of each point of
+// (eps_i + eps_nb)/2 * ((phi_nb - phi_i)/h)^2 (partial[2b], partial[2b+1]).
+// Rows (j, k) are strided over the blocks, so no index division per point. The
+// face differences are taken in FP64 (their cancellation needs it); everything
+// else is df64 on the FP32 pipe (values split by split_to_float2), each
+// thread's sums compensated float pairs, the threads' sums added in FP64: about
+// 2^-46 relative per term, all of whose s1 terms are positive.
+__device__ __forceinline__ void df_acc2(float& s, float& e, df v) {
+    const float t = s + v.hi;
+    const float z = t - s;
+    e += ((s - (t - z)) + (v.hi - z)) + v.lo;
+    s = t;
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_energy(Geo g, const double* __restrict__ rho,
+                                                           const double* __restrict__ phi,
+                                                           const double* __restrict__ eps, double* partial) {
     __shared__ double red[2][kReduceThreads];
-    const long n = (long)g.nx * g.ny * g.nz;
-    const long pl = plane_of(g.nx, g.ny);
-    const double ihx = g.ihx, ihy = g.ihy, ihz = g.ihz;
-    double s0 = 0.0, s1 = 0.0;
-    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(c % g.nx);
-        const int j = (int)((c / g.nx) % g.ny);
-        const int k = (int)(c / pl);
-        const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1);
-        const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
-        const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
-        const double p0 = phi[c], e0 = eps[c];
-        s0 += rho[c] * p0;
-        double gx = (phi[xp] - p0) * ihx, gy = (phi[yp] - p0) * ihy, gz = (phi[zp] - p0) * ihz;
-        s1 += 0.5 * ((e0 + eps[xp]) * gx * gx + (e0 + eps[yp]) * gy * gy + (e0 + eps[zp]) * gz * gz);
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long pl = plane_of(nx, ny);
+    const df wx = df_from(g.c2x), wy = df_from(g.c2y), wz = df_from(g.c2z);   // 1/(2 h^2) per axis
+    float s0 = 0.f, e0s = 0.f, s1 = 0.f, e1s = 0.f;
+    for (long row = blockIdx.x; row < (long)ny * nz; row += gridDim.x) {
+        const int j = (int)(row % ny), k = (int)(row / ny);
+        const long base = (long)k * pl + (long)j * nx;
+        const long dy = j == ny - 1 ? (1 - ny) * (long)nx : nx;
+        const long dz = k == nz - 1 ? (1 - nz) * pl : pl;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const long c = base + i;
+            const long xp = c + (i == nx - 1 ? 1 - nx : 1), yp = c + dy, zp = c + dz;
+            const double p0 = __ldg(phi + c);
+            df_acc2(s0, e0s, df_mul(df_from(__ldg(rho + c)), df_from(p0)));
+            const df ec = df_from(__ldg(eps + c));
+            const df gx = df_from(__ldg(phi + xp) - p0), gy = df_from(__ldg(phi + yp) - p0),
+                     gz = df_from(__ldg(phi + zp) - p0);
+            df_acc2(s1, e1s, df_mul(df_mul(df_add(ec, df_from(__ldg(eps + xp))), df_mul(gx, gx)), wx));
+            df_acc2(s1, e1s, df_mul(df_mul(df_add(ec, df_from(__ldg(eps + yp))), df_mul(gy, gy)), wy));
+            df_acc2(s1, e1s, df_mul(df_mul(df_add(ec, df_from(__ldg(eps + zp))), df_mul(gz, gz)), wz));
+        }
     }
-    red[0][threadIdx.x] = s0;
-    red[1][threadIdx.x] = s1;
+    red[0][threadIdx.x] = (double)s0 + (double)e0s;
+    red[1][threadIdx.x] = (double)s1 + (double)e1s;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
@@ -1098,7 +1119,7 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
     const double rc2 = p.rcut * p.rcut;
     const double iw = p.iw;
     const double sp_norm = p.sp_norm;
-    const float rcf = (float)p.rcut + kMargin;
+    const float rcf = p.rcutf + kMargin;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int a0 = 0; a0 < at.n; a0 += ACH) {
         if (threadIdx.x == 0) ne = 0;
@@ -1129,7 +1150,7 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
                 if (!(d2 < rc2 && d2 > 0.0)) continue;
                 const double W = Ws[tx + TX * (ty + TY * tz)];
                 const float df = sqrtf((float)d2);
-                const float uf = (df - (float)p.r0) * (float)iw;
+                const float uf = (df - p.r0f) * p.iwf;
                 double ratio;   // s'(d) / (s(d) d)
                 if (fabsf(uf) > 3.45f) {
                     const float sf = 0.5f * erfcf(-uf);

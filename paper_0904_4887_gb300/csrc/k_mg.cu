@@ -853,14 +853,32 @@ __global__ void k_finalize(const double* partial, int nparts, int ncomp, double*
     }
 }
 
-// partial[3b..3b+2] = sum rho, sum |rho|, sum rho^2
+// (s, e) += (x, y): a compensated FP32 pair accumulation (Knuth's two-sum of the
+// leading parts, the low parts added)
+__device__ __forceinline__ void pair_acc(float& s, float& e, float x, float y) {
+    const float t = s + x;
+    const float z = t - s;
+    e += ((s - (t - z)) + (x - z)) + y;
+    s = t;
+}
+
+// partial[3b..3b+2] = sum rho, sum |rho|, sum rho^2. Each thread sums its values
+// as compensated float pairs (the value split by split_to_float2, the square as
+// an exact product hi*hi by FMA plus the cross terms): no FP64 instruction per
+// value, about 2^-44 of each thread's sum; the threads' sums meet in FP64.
 __global__ void k_rho_stats(long n, const double* rho, double* partial) {
     __shared__ double red[32];
-    double a = 0.0, b = 0.0, c = 0.0;
+    float as = 0.f, ae = 0.f, bs = 0.f, be = 0.f, cs = 0.f, ce = 0.f;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        const double v = rho[t];
-        a += v; b += fabs(v); c += v * v;
+        const float2 v = split_to_float2(rho[t]);
+        pair_acc(as, ae, v.x, v.y);
+        const bool neg = v.x < 0.f;
+        pair_acc(bs, be, neg ? -v.x : v.x, neg ? -v.y : v.y);
+        const float p = v.x * v.x;
+        const float q = fmaf(v.x, v.x, -p) + 2.f * v.x * v.y;
+        pair_acc(cs, ce, p, q);
     }
+    double a = (double)as + (double)ae, b = (double)bs + (double)be, c = (double)cs + (double)ce;
     double s = block_sum(a, red);
     if (threadIdx.x == 0) partial[3 * blockIdx.x] = s;
     s = block_sum(b, red);
@@ -949,11 +967,11 @@ __device__ __forceinline__ d2 d2_ld(const float2* p, long i) {
 
 // dst = (hi, lo) split of scale * src
 __global__ void k_to_df(long n, const double* __restrict__ src, double scale, float2* __restrict__ dst) {
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        const double v = scale * src[t];
-        const float hi = (float)v;
-        dst[t] = make_float2(hi, (float)(v - (double)hi));
-    }
+    // the split by integer instructions (split_to_float2): one FP64 multiply per
+    // value where scale != 1 instead of five FP64-pipe instructions
+    const bool one = scale == 1.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        dst[t] = split_to_float2(one ? src[t] : scale * src[t]);
 }
 
 // r = b - A phi on the periodic full box (cell eps, face means), in df64;
