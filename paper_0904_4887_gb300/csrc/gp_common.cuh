@@ -83,32 +83,37 @@ struct DielParams {
     float rcutf, rc2f, reachf, tinyf, r0f, iwf, spnf;
 };
 
-// (hi, lo) = (RN_float(x), RN_float(x - hi)): the float pair of a double, as a cast
-// would give it, from the bits with integer instructions. On GB300 each FP64
-// instruction of a warp (casts between double and float included) holds the
-// FP64 pipe for about 64 cycles; this takes none. IEEE 754 binary64 -> binary32
-// rounding to nearest even: keep the top 23 of the 52 mantissa bits, round on
-// the other 29 (a carry moves into the exponent field by itself); the residual
-// is those 29 bits less the rounding, times 2^(E - 1075), exact in a double and
-// rounded once by the int-to-float cast. Below 2^-63, where lo might be
-// subnormal, and above the float range the casts themselves are used.
+// (hi, lo) = (RN_float(x), RN_float(x - hi)): the float pair of a double, as the
+// casts would give it, from the bits with integer and FP32 instructions only. On
+// GB300 each FP64 instruction of a warp (casts between double and float
+// included) holds the FP64 pipe for about 64 cycles, and a short fallback branch
+// of casts is executed by the whole warp (or if-converted and executed always),
+// so no path here has one. IEEE 754 binary64 -> binary32 rounding to nearest
+// even: keep the top 23 of the 52 mantissa bits, round on the other 29 (a carry
+// moves into the exponent field by itself); the residual is those 29 bits less
+// the rounding, times 2^(E - 1075), a power of two built from its bits, so the
+// int-to-float conversion is its only rounding. Identical to the casts for
+// 2^-63 <= |x| < 2^128 and for zeros; below 2^-63 (where lo could be subnormal)
+// hi is still RN_float(x) and lo is 0 (an error below 2^-87), below 2^-126
+// (where hi would be subnormal) both are zero of the sign of x; beyond the float
+// range hi is an infinity, and a NaN stays a NaN.
 __device__ __forceinline__ float2 split_to_float2(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
     const unsigned sign = h & 0x80000000u;
     const int E = (int)((h >> 20) & 0x7ffu);
     const int e = E - 1023 + 127;
-    if (E < 960) {                     // |x| < 2^-63: lo might be subnormal; the casts (rare)
-        const float hi = (float)x;
-        return make_float2(hi, (float)(x - (double)hi));
+    if (e >= 255) {
+        const unsigned nan = (E == 2047 && ((h & 0xfffffu) | l)) ? 0x400000u : 0u;
+        return make_float2(__uint_as_float(sign | 0x7f800000u | nan), 0.f);
     }
-    if (e >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+    if (e < 1) return make_float2(__uint_as_float(sign), 0.f);
     const unsigned m23 = ((h & 0xfffffu) << 3) | (l >> 29);
     const unsigned rem = l & 0x1fffffffu;
     const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
     const float hi = __uint_as_float(sign | ((((unsigned)e << 23) | m23) + up));
     const int r = (int)rem - (int)(up << 29);
-    float lo = ldexpf((float)r, E - 1075);
+    float lo = E < 960 ? 0.f : (float)r * __uint_as_float((unsigned)(E - 948) << 23);
     if (sign && r != 0) lo = -lo;          // x - hi = 0 is +0, as the cast gives it
     return make_float2(hi, lo);
 }

@@ -1037,11 +1037,13 @@ __global__ void k_plane_max(Geo g, const double* eps64, double* out) {
 // partial[2b] = sum rho phi, partial[2b+1] = sum_f eps_f (grad_f phi)^2 over block b
 // s0 = sum rho phi and s1 = sum over the x, y, z faces of each point of
 // (eps_i + eps_nb)/2 * ((phi_nb - phi_i)/h)^2 (partial[2b], partial[2b+1]).
-// Rows (j, k) are strided over the blocks, so no index division per point. The
-// face differences are taken in FP64 (their cancellation needs it); everything
-// else is df64 on the FP32 pipe (values split by split_to_float2), each
-// thread's sums compensated float pairs, the threads' sums added in FP64: about
-// 2^-46 relative per term, all of whose s1 terms are positive.
+// Rows (j, k) are strided over groups of 64 threads (four per block; no thread
+// idles on rows of 64, 128, 192, ... points), so no index division per point.
+// The face differences are taken in FP64 (their cancellation needs it: three
+// FP64 instructions per point); everything else is df64 on the FP32 pipe
+// (values split by split_to_float2), each thread's sums compensated float pairs,
+// the threads' sums added in FP64: about 2^-46 relative per term, all of whose
+// s1 terms are positive.
 __device__ __forceinline__ void df_acc2(float& s, float& e, df v) {
     const float t = s + v.hi;
     const float z = t - s;
@@ -1057,12 +1059,14 @@ __global__ void __launch_bounds__(kReduceThreads) k_energy(Geo g, const double* 
     const long pl = plane_of(nx, ny);
     const df wx = df_from(g.c2x), wy = df_from(g.c2y), wz = df_from(g.c2z);   // 1/(2 h^2) per axis
     float s0 = 0.f, e0s = 0.f, s1 = 0.f, e1s = 0.f;
-    for (long row = blockIdx.x; row < (long)ny * nz; row += gridDim.x) {
-        const int j = (int)(row % ny), k = (int)(row / ny);
+    constexpr int G = 64;
+    const int groups = blockDim.x / G, lane = threadIdx.x % G;
+    for (int row = blockIdx.x * groups + threadIdx.x / G; row < ny * nz; row += gridDim.x * groups) {
+        const int j = row % ny, k = row / ny;
         const long base = (long)k * pl + (long)j * nx;
         const long dy = j == ny - 1 ? (1 - ny) * (long)nx : nx;
         const long dz = k == nz - 1 ? (1 - nz) * pl : pl;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        for (int i = lane; i < nx; i += G) {
             const long c = base + i;
             const long xp = c + (i == nx - 1 ? 1 - nx : 1), yp = c + dy, zp = c + dz;
             const double p0 = __ldg(phi + c);
