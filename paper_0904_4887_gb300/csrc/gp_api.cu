@@ -176,6 +176,8 @@ struct gp_ctx {
     double* gmat = nullptr;        // Gauss-Jordan workspace (2 * 512^2)
     double* sw_coef = nullptr;     // switching-function tables (2 * kSwNI * (kSwDeg+1))
     float4* sw_pack = nullptr;     // their packed FP32 copies (2 * kSwNI * 4)
+    double sw_key[4] = {0, 0, 0, 0};   // (eps0, r0, w, rcut) the tables were built for
+    bool sw_built = false;
     double* rvdw = nullptr;        // van der Waals radii for the kind-1 dielectric
     std::vector<double> rvdw_host; // the same on the host (the image-sum radius depends on them)
     DielParams dp{};               // dielectric constants of the last gp_set_dielectric
@@ -396,7 +398,7 @@ void coarse_coeffs(gp_ctx* c, Hier<T>& H) {
     {
         ProfScope ps(c, GP_PROF_SETUP, 1 + gauss_jordan_launches(H.nc));
         launch_coarse_matrix<T>(C, c->gmat, c->s);
-        launch_gauss_jordan(c->gmat, H.nc, c->dstatus, c->s);
+        launch_gauss_jordan(c->gmat, H.nc, c->dstatus, c->s, sizeof(T) == 4);
     }
     GP_CHECK_LAUNCH();
     int st = 0;
@@ -1547,10 +1549,15 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             tb.h_dq = (tb.h_qhi - tb.h_qlo) / kSwNI;
             tb.s_qlof = (float)tb.s_qlo; tb.s_dqf = (float)tb.s_dq;
             tb.h_qlof = (float)tb.h_qlo; tb.h_dqf = (float)tb.h_dq;
-            {
+            // they depend on the parameters alone: built again only when those change
+            const double key[4] = {p.eps0, p.r0, p.w, p.rcut};
+            if (!c->sw_built || std::memcmp(key, c->sw_key, sizeof(key)) != 0) {
                 ProfScope ps(c, GP_PROF_EPS, 1);
                 launch_switch_tables(dp, tb, c->sw_coef, c->sw_coef + (size_t)kSwNI * (kSwDeg + 1), c->sw_pack,
                                      c->sw_pack + (size_t)kSwNI * 4, c->s);
+                GP_CHECK_LAUNCH();
+                std::memcpy(c->sw_key, key, sizeof(key));
+                c->sw_built = true;
             }
             // the per-atom table coordinates of both tables (one FP64 pass, then loads)
             const int nmax = std::max(c->g.nx, std::max(c->g.ny, c->g.nz));

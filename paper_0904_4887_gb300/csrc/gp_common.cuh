@@ -265,7 +265,9 @@ template <typename T> void launch_prolong_add(const LV<T>& F, T* u, const LV<T>&
 template <typename T> void launch_coarsen_faces(const LV<T>& F, int nxc, int nyc, int nzc,
                                                 T* cx, T* cy, T* cz, cudaStream_t s);
 template <typename T> void launch_coarse_matrix(const LV<T>& C, double* M, cudaStream_t s);
-int launch_gauss_jordan(double* M, int n, int* status, cudaStream_t s);   // returns the launch count
+// the inverse of the dense n x n M into M + n*n; pairs: the one-CTA version in
+// float-pair arithmetic (for an FP32 multigrid), else FP64. Returns the launch count.
+int launch_gauss_jordan(double* M, int n, int* status, cudaStream_t s, bool pairs);
 int gauss_jordan_launches(int n);
 template <typename T> void launch_store_inverse(const double* M, int n, T* inv, cudaStream_t s);
 template <typename T> void launch_coarse_solve(const LV<T>& C, const T* inv, int n, const T* f, T* u,

@@ -389,6 +389,57 @@ __global__ void k_coarsen_faces(LV<T> F, int nxc, int nyc, int nzc, T* cx, T* cy
     }
 }
 
+// The same coarsening from a periodic cell level (the finest level of the full
+// box): one thread per coarse point loads once, into registers, the 4 x 4 x 4
+// block of eps (fine x, y, z from 2I-1, 2J-1, 2K-1 on, wrapped) that the 27
+// fine faces of its three coarse faces use, instead of evaluating each of the
+// 54 fine faces from two loads and six wrapped-index divisions; the same weights
+// and series rule, the 1/(2 h^2) factor taken out of the sums (the series rule
+// is homogeneous of degree one).
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarsen_faces_cell(LV<T> F, int nxc, int nyc, int nzc, T* cx, T* cy,
+                                                            T* cz) {
+    const int total = nxc * nyc * nzc;
+    const long pl = (long)F.nx * F.ny;
+    const T w[3] = {(T)0.25, (T)0.5, (T)0.25};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int I = t % nxc, r = t / nxc, J = r % nyc, K = r / nyc;
+        int xs[4];
+        long ys[4], zs[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            int x = 2 * I - 1 + a, y = 2 * J - 1 + a, z = 2 * K - 1 + a;
+            x = x < 0 ? x + F.nx : (x >= F.nx ? x - F.nx : x);
+            y = y < 0 ? y + F.ny : (y >= F.ny ? y - F.ny : y);
+            z = z < 0 ? z + F.nz : (z >= F.nz ? z - F.nz : z);
+            xs[a] = x;
+            ys[a] = (long)y * F.nx;
+            zs[a] = (long)z * pl;
+        }
+        T e[4][4][4];                                   // [z][y][x]
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int a = 0; a < 4; ++a) e[c][b][a] = __ldg(F.eps + zs[c] + ys[b] + xs[a]);
+        T ax = 0, ay = 0, az = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const T wt = w[c] * w[b];
+                ax += wt * series_quarter(e[c][b][1] + e[c][b][2], e[c][b][2] + e[c][b][3]);
+                ay += wt * series_quarter(e[c][1][b] + e[c][2][b], e[c][2][b] + e[c][3][b]);
+                az += wt * series_quarter(e[1][c][b] + e[2][c][b], e[2][c][b] + e[3][c][b]);
+            }
+        const long o = I + (long)nxc * (J + (long)nyc * K);
+        cx[o] = ax * (T)0.5 * F.ihx2;
+        cy[o] = ay * (T)0.5 * F.ihy2;
+        cz[o] = az * (T)0.5 * F.ihz2;
+    }
+}
+
 // dense matrix of the coarsest operator (row p = point p), periodic levels
 // regularised by -(max|diag|/n) 1 1^T so that mean-zero data give the
 // mean-zero solution
@@ -506,6 +557,83 @@ __global__ void __launch_bounds__(1024) k_gj_smem(double* M, int n, int* status)
     for (int e = tid; e < n * n; e += blockDim.x) {
         const int r = e / n, q = e - r * n;
         W[e] = A[r * w + n + q] / A[r * w + r];
+    }
+}
+
+// The same one-CTA elimination with [M | I] held as float pairs (hi, lo) and
+// every step in pair arithmetic on the FP32 pipe (Dekker's products by FMA,
+// Knuth's two-sum, a pair quotient from the float quotient and one correction):
+// about 2^-46 relative per operation. It serves the FP32 multigrid, which stores
+// the inverse in FP32; on one SM the FP64 version is bound by the FP64 pipe
+// (1/64 of the FP32 rate). Rows go to warps and columns to lanes, so no index
+// division; step `col` updates only columns col.. of each row (those before it
+// are already eliminated and stay as they are).
+struct gjp { float hi, lo; };
+__device__ __forceinline__ gjp gjp_quick(float s, float e) {   // |s| >= |e|
+    const float t = s + e;
+    return {t, e - (t - s)};
+}
+__device__ __forceinline__ gjp gjp_mul(gjp a, gjp b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return gjp_quick(p, e);
+}
+__device__ __forceinline__ gjp gjp_sub(gjp a, gjp b) {
+    const float s = a.hi - b.hi;
+    const float v = s - a.hi;
+    float e = (a.hi - (s - v)) - (b.hi + v);
+    e += a.lo - b.lo;
+    return gjp_quick(s, e);
+}
+__device__ __forceinline__ gjp gjp_div(gjp a, gjp b) {
+    const float q1 = a.hi / b.hi;
+    const gjp r = gjp_sub(a, gjp_mul({q1, 0.f}, b));
+    return gjp_quick(q1, r.hi / b.hi);
+}
+
+__global__ void __launch_bounds__(1024) k_gj_smem_pairs(double* M, int n, int* status) {
+    extern __shared__ float2 gjq[];
+    float2* A = gjq;                      // [n][2n]
+    float2* fac = gjq + 2 * n * n;        // [n]
+    const int w = 2 * n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    for (int r = warp; r < n; r += nw)
+        for (int q = lane; q < w; q += 32)
+            A[r * w + q] = q < n ? split_to_float2(M[(long)r * n + q]) : make_float2(q - n == r ? 1.f : 0.f, 0.f);
+    if (tid == 0) *status = 0;
+    __syncthreads();
+    for (int col = 0; col < n; ++col) {
+        const float2 pv = A[col * w + col];
+        const gjp piv{pv.x, pv.y};
+        const bool ok = fabsf(piv.hi) > 1e-30f;
+        if (!ok && tid == 0) *status = 1;
+        for (int r = tid; r < n; r += blockDim.x) {
+            const float2 a = A[r * w + col];
+            const gjp f = (ok && r != col) ? gjp_div({a.x, a.y}, piv) : gjp{0.f, 0.f};
+            fac[r] = make_float2(f.hi, f.lo);
+        }
+        __syncthreads();
+        for (int r = warp; r < n; r += nw) {
+            const float2 fr = fac[r];
+            if (fr.x == 0.f) continue;
+            const gjp f{fr.x, fr.y};
+            for (int q = col + lane; q < w; q += 32) {
+                const float2 a = A[r * w + q], m = A[col * w + q];
+                const gjp v = gjp_sub({a.x, a.y}, gjp_mul(f, {m.x, m.y}));
+                A[r * w + q] = make_float2(v.hi, v.lo);
+            }
+        }
+        __syncthreads();
+    }
+    double* W = M + (long)n * n;
+    for (int r = warp; r < n; r += nw) {
+        const float2 d = A[r * w + r];
+        for (int q = lane; q < n; q += 32) {
+            const float2 a = A[r * w + n + q];
+            const gjp v = gjp_div({a.x, a.y}, {d.x, d.y});
+            W[(long)r * n + q] = (double)v.hi + (double)v.lo;
+        }
     }
 }
 
@@ -1613,6 +1741,8 @@ int gauss_jordan_launches(int n) { return n <= kGjSmemMax ? 1 : n + 2; }
 void coarse_vcycle_init() {
     cudaFuncSetAttribute(k_gj_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(double) * (2 * kGjSmemMax * kGjSmemMax + kGjSmemMax)));
+    cudaFuncSetAttribute(k_gj_smem_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(float2) * (2 * kGjSmemMax * kGjSmemMax + kGjSmemMax)));
     cudaFuncSetAttribute(k_coarse_vcycle_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemBytes);
     cudaFuncSetAttribute(k_coarse_vcycle_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemBytes);
 }
@@ -1763,15 +1893,20 @@ template <typename T> void launch_prolong_add(const LV<T>& F, T* u, const LV<T>&
 }
 template <typename T> void launch_coarsen_faces(const LV<T>& F, int nxc, int nyc, int nzc, T* cx, T* cy, T* cz,
                                                 cudaStream_t s) {
+    if (F.cell && F.zper) {
+        k_coarsen_faces_cell<T><<<grid_for((long)nxc * nyc * nzc, 256), 256, 0, s>>>(F, nxc, nyc, nzc, cx, cy, cz);
+        return;
+    }
     const long n = (long)nxc * nyc * (nzc + 1);
     k_coarsen_faces<T><<<grid_for(n, 256), 256, 0, s>>>(F, nxc, nyc, nzc, cx, cy, cz);
 }
 template <typename T> void launch_coarse_matrix(const LV<T>& C, double* M, cudaStream_t s) {
     k_coarse_matrix<T><<<1, 512, 0, s>>>(C, M);
 }
-int launch_gauss_jordan(double* M, int n, int* status, cudaStream_t s) {
+int launch_gauss_jordan(double* M, int n, int* status, cudaStream_t s, bool pairs) {
     if (n <= kGjSmemMax) {
-        k_gj_smem<<<1, 1024, sizeof(double) * (2 * (size_t)n * n + n), s>>>(M, n, status);
+        if (pairs) k_gj_smem_pairs<<<1, 1024, sizeof(float2) * (2 * (size_t)n * n + n), s>>>(M, n, status);
+        else k_gj_smem<<<1, 1024, sizeof(double) * (2 * (size_t)n * n + n), s>>>(M, n, status);
         return 1;
     }
     const int th = n >= 256 ? 256 : 128;
