@@ -170,6 +170,7 @@ struct gp_ctx {
     double* partial = nullptr;     // kReduceBlocks * (kMaxKrylov + 1)
     double* scal = nullptr;        // device scalars
     int* dstatus = nullptr;
+    float2* rho_phid = nullptr;    // phi as float pairs for the charge-force kernel
     double* forces_S = nullptr;
     double* forces_T = nullptr;
     int forces_cap = 0;
@@ -314,6 +315,7 @@ GaussTabs ensure_gtab(gp_ctx* c, int n_atoms) {
 
 // per-atom partial sums of the two force terms, sized for n atoms
 void ensure_forces(gp_ctx* c, int n) {
+    if (!c->rho_phid) c->rho_phid = (float2*)dalloc(c, sizeof(float2) * c->n);
     if (n <= c->forces_cap) return;
     if (c->forces_S) cudaFree(c->forces_S);
     if (c->forces_T) cudaFree(c->forces_T);
@@ -1736,9 +1738,9 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             GP_CHECK_LAUNCH();
             if (gauss_dev) {
                 const GaussTabs gt = ensure_gtab(c, n);
-                ProfScope ps(c, GP_PROF_FORCES_RHO, 2);
+                ProfScope ps(c, GP_PROF_FORCES_RHO, 3);
                 launch_gauss_tables(c->g, at, 8.0, gt, c->s);
-                launch_forces_rho(c->g, gt, phi_dev, c->forces_T, c->s);
+                launch_forces_rho(c->g, gt, phi_dev, c->rho_phid, c->forces_T, c->s);
             }
             GP_CHECK_LAUNCH();
             ProfScope ps(c, GP_PROF_MISC, 1);
@@ -1891,9 +1893,9 @@ gp_status gp_energy_forces6(gp_ctx* c, const double* phi_dev, double mu, const d
                     launch_fd6_sub_ratio(c->n, c->f6_r, nullptr, c->scal + kS6Z, c->scal + kS6N, c->s);
                 }
                 const GaussTabs gt = ensure_gtab(c, n);
-                ProfScope ps(c, GP_PROF_FORCES_RHO, 2);
+                ProfScope ps(c, GP_PROF_FORCES_RHO, 3);
                 launch_gauss_tables(c->g, at, 8.0, gt, c->s);
-                launch_forces_rho(c->g, gt, c->f6_r, c->forces_T, c->s);
+                launch_forces_rho(c->g, gt, c->f6_r, c->rho_phid, c->forces_T, c->s);
             }
             GP_CHECK_LAUNCH();
             ProfScope ps(c, GP_PROF_MISC, 1);

@@ -206,7 +206,9 @@ void launch_energy(const Geo& g, const double* rho, const double* phi, const dou
                    double* partial, cudaStream_t s);
 void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct,
                        const double* phi, const double* wext, const double* pe64, double* S, cudaStream_t s);
-void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, double* T, cudaStream_t s);
+// phid: scratch of nx*ny*nz float pairs (phi is converted into it first)
+void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, float2* phid, double* T,
+                       cudaStream_t s);
 void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,
                           cudaStream_t s);
 

@@ -755,10 +755,28 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
                     tz += 4 * (blk >> 4);
                     if (t.i0 + tx >= g.nx || t.j0 + ty >= g.ny || t.k0 + tz >= g.nz) continue;
                     const int n = wn[warp][tx] + wn[warp][TX + ty] + wn[warp][TX + TY + tz];
+                    df ratio;   // s'(d) / (s(d) d)
+                    if (n >= kSwNI) {
+                        // d >= r0 + 3.5w (the integer parts of the table coordinate alone
+                        // pass its end): culled at rcut on the FP32 distance; inside it
+                        // u >= 3.5 and s = 1 - erfc(u)/2 is 1 to 3.7e-7, so the ratio is
+                        // s'/d in FP32 (the pair is below 5e-6 of one at the switching radius)
+                        const float dx = wd[warp][tx].hi, dy = wd[warp][TX + ty].hi, dz = wd[warp][TX + TY + tz].hi;
+                        const float qq = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (!(qq < rc2f)) continue;
+                        const float d_ = sqrtf(qq);
+                        const float uf = (d_ - r0f) * iwf;
+                        ratio.hi = spf_norm * expf(-uf * uf) / d_;
+                        ratio.lo = 0.f;
+                        const df c = df_mul(Ws[tx + TX * (ty + TY * tz)], ratio);
+                        df_acc(sx, cx, c, wd[warp][tx]);
+                        df_acc(sy, cy, c, wd[warp][TX + ty]);
+                        df_acc(sz, cz, c, wd[warp][TX + TY + tz]);
+                        continue;
+                    }
                     const df f = df_add(df_add(wf[warp][tx], wf[warp][TX + ty]), wf[warp][TX + TY + tz]);
                     df tl;
                     const int kq = sw_local(n, f, tl);
-                    df ratio;   // s'(d) / (s(d) d)
                     if (kq >= 0 && kq < kSwNI) {
                         ratio = sw_poly<kSwSplitH>(tb.h32, kq, tl);
                     } else {
@@ -1183,81 +1201,88 @@ __global__ void __launch_bounds__(TT) k_forces_eps(Geo g, Atoms at, DielParams p
 }
 
 // charge part: T_a = sum_i phi_i d rho~_i / d R_a. With the periodized factors,
-// T_x = coef sum_i X'(i) sum_(j,k) phi_ijk Y(j) Z(k), and likewise for y and z.
-// One warp per (tile, Gaussian): lanes along x; each lane sums its column of
-// 16 (j, k) rows against the three row weights coef {Y Z, Y' Z, Y Z'} (held
-// per warp in shared memory), then scales by X' or X and the warp reduces.
-__global__ void __launch_bounds__(TT) k_forces_rho(Geo g, GaussTabs gt, const double* phi, double* T) {
-    __shared__ int ent[TT];
-    __shared__ df eres[TT][3];                  // each Gaussian's sum, converted to FP64 by a full warp
-    __shared__ df ph[TT];                       // index tx + TX (ty + TY tz)
-    __shared__ df wr[TT / 32][3][TY * TZ];
-    __shared__ int ne;
-    const Tile t = make_tile(g);
-    {
-        const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
-        const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
-        ph[threadIdx.x] = df_from((i < g.nx && j < g.ny && k < g.nz) ? phi[i + (long)g.nx * (j + (long)g.ny * k)] : 0.0);
+// T_x = coef sum_(i,j,k) X'(i) Y(j) Z(k) phi_ijk, T_y the same with Y', T_z with
+// Z', over the Gaussian's index window (each grid index once: the factors sum
+// the images). The sum is separable, so each (i, j) column of the window is
+// contracted along z once against Z and Z' (two products per point, instead
+// of three per point over the whole tiles the window touches), and the two
+// column sums are weighted by X' Y, X Y' and X Y. Blocks: kRhoChunks per
+// Gaussian, each a contiguous share of the window's columns, one column per
+// thread at a time (consecutive x across the threads: coalesced). phi arrives
+// as float pairs (df64, converted once per call); products and sums are df64
+// with compensated accumulation; each block adds its three sums, times coef, to
+// T in FP64.
+constexpr int kRhoChunks = 16;
+constexpr int kRhoThreads = 256;
+constexpr int kRhoZStage = 1024;
+
+__global__ void __launch_bounds__(kRhoThreads) k_forces_rho(Geo g, GaussTabs gt, const float2* __restrict__ phid,
+                                                             double* T) {
+    __shared__ df zs[2][kRhoZStage];           // Z and Z' over the window's planes, when it fits
+    __shared__ df red[kRhoThreads / 32][3];
+    const int ge = blockIdx.x / kRhoChunks, chunk = blockIdx.x % kRhoChunks;
+    const int* w = gt.win + ge * 6;
+    const int wx = w[1] - w[0] + 1, wy = w[3] - w[2] + 1, wz = w[5] - w[4] + 1;
+    const int ncol = wx * wy;
+    const int c0 = (int)((long)ncol * chunk / kRhoChunks), c1 = (int)((long)ncol * (chunk + 1) / kRhoChunks);
+    if (c0 >= c1) return;
+    const long rz = gt_row(ge, 2, gt.nmax);
+    const bool staged = wz <= kRhoZStage;
+    for (int q = threadIdx.x; staged && q < wz; q += blockDim.x) {
+        int k = w[4] + q;
+        k = k < 0 ? k + g.nz : (k >= g.nz ? k - g.nz : k);
+        zs[0][q] = as_df(gt.vald[rz + k]);
+        zs[1][q] = as_df(gt.derd[rz + k]);
     }
+    __syncthreads();
+    const long pl = plane_of(g.nx, g.ny);
+    const long rx = gt_row(ge, 0, gt.nmax), ry = gt_row(ge, 1, gt.nmax);
+    int k0 = w[4];
+    k0 = k0 < 0 ? k0 + g.nz : (k0 >= g.nz ? k0 - g.nz : k0);
+    float tx = 0.f, ex = 0.f, ty = 0.f, ey = 0.f, tz = 0.f, ez = 0.f;
+    for (int col = c0 + threadIdx.x; col < c1; col += blockDim.x) {
+        int i = w[0] + col % wx, j = w[2] + col / wx;
+        i = i < 0 ? i + g.nx : (i >= g.nx ? i - g.nx : i);
+        j = j < 0 ? j + g.ny : (j >= g.ny ? j - g.ny : j);
+        const float2* pc = phid + i + (long)g.nx * j;
+        float a0 = 0.f, e0 = 0.f, a1 = 0.f, e1 = 0.f;
+        int k = k0;
+        if (staged) {
+            for (int q = 0; q < wz; ++q) {
+                const df p = as_df(__ldg(pc + pl * k));
+                df_acc(a0, e0, p, zs[0][q]);
+                df_acc(a1, e1, p, zs[1][q]);
+                k = k + 1 == g.nz ? 0 : k + 1;
+            }
+        } else {
+            for (int q = 0; q < wz; ++q) {
+                const df p = as_df(__ldg(pc + pl * k));
+                df_acc(a0, e0, p, as_df(gt.vald[rz + k]));
+                df_acc(a1, e1, p, as_df(gt.derd[rz + k]));
+                k = k + 1 == g.nz ? 0 : k + 1;
+            }
+        }
+        const df A0 = df_quick(a0, e0), A1 = df_quick(a1, e1);
+        const df X = as_df(gt.vald[rx + i]), Xd = as_df(gt.derd[rx + i]);
+        const df Y = as_df(gt.vald[ry + j]), Yd = as_df(gt.derd[ry + j]);
+        df_acc(tx, ex, df_mul(Xd, Y), A0);
+        df_acc(ty, ey, df_mul(X, Yd), A0);
+        df_acc(tz, ez, df_mul(X, Y), A1);
+    }
+    warp_sum_df(tx, ex); warp_sum_df(ty, ey); warp_sum_df(tz, ez);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = t.i0 + lane;
-    const bool lane_ok = i < g.nx;
-    for (int g0 = 0; g0 < gt.G; g0 += TT) {
-        if (threadIdx.x == 0) ne = 0;
-        __syncthreads();
-        const int q = g0 + threadIdx.x;
-        if (q < gt.G && gauss_hits_tile(gt, q, t, g)) ent[atomicAdd(&ne, 1)] = q;
-        __syncthreads();
-        const int m = ne;
-        for (int e = warp; e < m; e += TT / 32) {
-            const int ge = ent[e];
-            if (lane < TY * TZ) {
-                const int jj = t.j0 + lane / TZ, kk = t.k0 + lane % TZ;
-                df w0 = {0.f, 0.f}, wy = w0, wz = w0;
-                if (jj < g.ny && kk < g.nz) {
-                    const df cf = as_df(gt.coefd[ge]);
-                    const df cY = df_mul(cf, as_df(gt.vald[gt_row(ge, 1, gt.nmax) + jj]));
-                    const df cYd = df_mul(cf, as_df(gt.derd[gt_row(ge, 1, gt.nmax) + jj]));
-                    const df Z = as_df(gt.vald[gt_row(ge, 2, gt.nmax) + kk]);
-                    w0 = df_mul(cY, Z);
-                    wy = df_mul(cYd, Z);
-                    wz = df_mul(cY, as_df(gt.derd[gt_row(ge, 2, gt.nmax) + kk]));
-                }
-                wr[warp][0][lane] = w0;
-                wr[warp][1][lane] = wy;
-                wr[warp][2][lane] = wz;
-            }
-            __syncwarp();
-            const df X = lane_ok ? as_df(gt.vald[gt_row(ge, 0, gt.nmax) + i]) : df{0.f, 0.f};
-            const df Xd = lane_ok ? as_df(gt.derd[gt_row(ge, 0, gt.nmax) + i]) : df{0.f, 0.f};
-            float s0 = 0.f, c0 = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
-#pragma unroll 4
-            for (int r = 0; r < TY * TZ; ++r) {
-                // row r = ty * TZ + tz holds phi at index lane + TX (ty + TY tz)
-                const df p = ph[lane + TX * (r / TZ + TY * (r % TZ))];
-                df_acc(s0, c0, p, wr[warp][0][r]);
-                df_acc(sy, cy, p, wr[warp][1][r]);
-                df_acc(sz, cz, p, wr[warp][2][r]);
-            }
-            df fx = df_mul(Xd, df_quick(s0, c0));
-            df fy = df_mul(X, df_quick(sy, cy));
-            df fz = df_mul(X, df_quick(sz, cz));
-            warp_sum_df(fx.hi, fx.lo); warp_sum_df(fy.hi, fy.lo); warp_sum_df(fz.hi, fz.lo);
-            if (lane == 0) {
-                eres[e][0] = fx;
-                eres[e][1] = fy;
-                eres[e][2] = fz;
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-        // to FP64 and into T with full warps (see k_forces_eps_tab)
-        for (int e = threadIdx.x; e < 3 * m; e += TT) {
-            const int ee = e / 3, comp = e % 3;
-            const double v = df_to(eres[ee][comp]);
-            if (v != 0.0) atomicAdd(&T[3 * (ent[ee] >> 1) + comp], v);
-        }
-        __syncthreads();
+    if (lane == 0) {
+        red[warp][0] = df{tx, ex};
+        red[warp][1] = df{ty, ey};
+        red[warp][2] = df{tz, ez};
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int comp = threadIdx.x;
+        float s = 0.f, e = 0.f;
+        for (int v = 0; v < kRhoThreads / 32; ++v) df_acc(s, e, red[v][comp], df{1.f, 0.f});
+        const double v = df_to(df_mul(as_df(gt.coefd[ge]), df_quick(s, e)));
+        if (v != 0.0) atomicAdd(&T[3 * (ge >> 1) + comp], v);
     }
 }
 
@@ -1366,8 +1391,11 @@ void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb,
     else k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, wext, pe64, S);
 }
 
-void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, double* T, cudaStream_t s) {
-    if (gt.G > 0) k_forces_rho<<<tile_grid(g), TT, 0, s>>>(g, gt, phi, T);
+void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, float2* phid, double* T,
+                       cudaStream_t s) {
+    if (gt.G <= 0) return;
+    launch_to_df((long)g.nx * g.ny * g.nz, phi, 1.0, phid, s);
+    k_forces_rho<<<gt.G * kRhoChunks, kRhoThreads, 0, s>>>(g, gt, phid, T);
 }
 
 void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,
