@@ -232,8 +232,9 @@ def gpu_arm(args, rank, world):
 
     def make_solver(precision, split):
         extra = {"kind": args.kind, "gamma_tail": args.gamma_tail, "zlim": zlim} if args.kind else {}
-        if args.nu_coarse is not None:
-            extra["nu_coarse"] = args.nu_coarse
+        for key in ("nu_coarse", "nu1", "nu2"):
+            if getattr(args, key) is not None:
+                extra[key] = getattr(args, key)
         return P.GPSolver(w.grid, w.cell, precision=precision, split=split, levels=w.levels,
                           sweep_shape=args.sweep_shape, n_dirichlet=n_dir, **extra)
 
@@ -944,6 +945,8 @@ def main():
                     help="--kind 1, 2: bound on the part of gamma's image sum left out")
     ap.add_argument("--nu-coarse", type=int, default=None,
                     help="smoothing sweeps on the levels below the finest (default: the library's)")
+    ap.add_argument("--nu1", type=int, default=None, help="pre-smoothing sweeps (default: the library's)")
+    ap.add_argument("--nu2", type=int, default=None, help="post-smoothing sweeps (default: the library's)")
     ap.add_argument("--sweep-shape", type=int, default=-1,
                     help="finest-level smoother tile (-1: autotuned; fixed shapes keep profiles comparable)")
     args = ap.parse_args()

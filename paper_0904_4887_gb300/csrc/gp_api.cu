@@ -1413,7 +1413,7 @@ void gp_default_params(gp_params* p) {
     p->band_vcycles = 2;
     p->graph_outer = 0;
     p->sweep_shape = -1;
-    p->nu_coarse = 0;
+    p->nu_coarse = 4;
     p->kind = 0;
     p->gamma_tail = 1e-13;
     p->beta = 2.4;

@@ -227,10 +227,10 @@ def test_mixed_df64_residual_path(small_cases, k, graph_outer):
     assert abs(E - E0) < 1e-8 * abs(E0)
 
 
-@pytest.mark.parametrize("nu_coarse", [1, 3])
+@pytest.mark.parametrize("nu_coarse", [0, 1, 3])
 @pytest.mark.parametrize("split", [0, 1])
 def test_coarse_sweep_count_converges_to_oracle(small_cases, nu_coarse, split):
-    """Other sweep counts on the levels below the finest (nu_coarse; the shared-
+    """Other sweep counts on the levels below the finest (nu_coarse; 0 = nu1, nu2; the shared-
     memory bottom of the V-cycle and the band levels included) give the oracle's
     solution; a count outside 0 .. 8 is refused."""
     GPSolver = _gpu()
