@@ -468,13 +468,17 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
         const LV<T>& V = H.lv[l];
         T* u = l == 0 ? u0 : H.u[l];
         const T* f = l == 0 ? f0 : H.f[l];
-        GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
         if (l == 0) {
+            GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
             smooth_fine(c, H, u, f, c->prm.nu1, 0);
+        } else if (nuc1 == 0) {
+            GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
         } else {
+            // the first half sweep starts from u = 0 (the halo planes were zeroed at
+            // allocation and no kernel writes them), so the level needs no clearing
             ProfScope ps(c, GP_PROF_MG_COARSE, 2 * nuc1);
             for (int it = 0; it < nuc1; ++it) {
-                launch_rbgs<T>(V, u, f, 0, c->s);
+                launch_rbgs<T>(V, u, f, 0, c->s, it == 0);
                 launch_rbgs<T>(V, u, f, 1, c->s);
             }
         }

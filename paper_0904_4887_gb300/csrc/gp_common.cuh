@@ -16,6 +16,19 @@ constexpr int kMaxCoarse = 512;         // largest coarsest grid solved by a den
 constexpr int kAutoCoarse = 64;         // automatic level choice: coarsen to <= 64 points
 constexpr double kPi = 3.14159265358979323846;
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may be scheduled while the kernel before it
+// in the stream is still finishing, which hides most of the gap between two
+// short kernels. Such a kernel calls this before its first access to global
+// memory: it waits until the previous kernel has completed and its writes are
+// visible. Launched without the attribute it returns at once.
+// It then lets the next such kernel be scheduled (its blocks wait in turn), so
+// that it is resident by the time this one ends.
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- level view
 // One multigrid level. Arrays are addressed with a base pointer at plane 0 and
 // own one halo plane below (k = -1) and one above (k = nz): for Dirichlet
@@ -248,7 +261,10 @@ void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_ba
                        int band_first, int band_nz, cudaStream_t s);
 
 // multigrid (k_mg.cu)
-template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s);
+// init: the first half sweep from u = 0 (neighbours read as zero, so u needs no clearing
+// before it; the other colour is overwritten by the next half sweep)
+template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s,
+                                       bool init = false);
 // one fused red-black sweep of a cell-eps level: u_new from u_old, colour `first` updated first (k_smooth.cu)
 void rb_sweep_init();
 // polls per mbarrier wait of the whole-row smoother's main loop (< 0: the default);

@@ -116,7 +116,8 @@ int grid_for(long n, int threads) {
 // Red-black Gauss-Seidel half sweep for A u = f: u_i = (sum c u_nb - f_i) / sum c.
 // One thread per x-pair; it updates the member of the pair with the colour.
 template <typename T>
-__global__ void k_rbgs(LV<T> L, T* u, const T* f, int color) {
+__global__ void k_rbgs(LV<T> L, T* u, const T* f, int color, int init) {
+    griddep_wait();
     const int hx = L.nx >> 1;
     const long rows = (long)L.ny * L.nz;
     for (long row = blockIdx.x; row < rows; row += gridDim.x)
@@ -125,8 +126,8 @@ __global__ void k_rbgs(LV<T> L, T* u, const T* f, int color) {
         const int i = 2 * i2 + ((j + k + color) & 1);
         const Nb n = neighbours(L.nx, L.ny, L.nz, L.zper, i, j, k);
         const Co<T> o = coefs(L, n);
-        const T s = o.xp * u[n.xp] + o.xm * u[n.xm] + o.yp * u[n.yp] + o.ym * u[n.ym] + o.zp * u[n.zp] +
-                    o.zm * u[n.zm];
+        const T s = init ? (T)0 : o.xp * u[n.xp] + o.xm * u[n.xm] + o.yp * u[n.yp] + o.ym * u[n.ym] +
+                                     o.zp * u[n.zp] + o.zm * u[n.zm];
         const T d = o.xp + o.xm + o.yp + o.ym + o.zp + o.zm;
         u[n.c] = (s - f[n.c]) / d;
     }
@@ -138,7 +139,8 @@ __global__ void k_rbgs(LV<T> L, T* u, const T* f, int color) {
 __device__ __forceinline__ float2 ld_f2(const float* p, long i) { return *reinterpret_cast<const float2*>(p + i); }
 
 __global__ void __launch_bounds__(256) k_rbgs_pairs(LV<float> L, float* __restrict__ u, const float* __restrict__ f,
-                                                    int color) {
+                                                    int color, int init) {
+    griddep_wait();
     const int nx = L.nx, ny = L.ny, nz = L.nz, np = nx >> 1;
     const long pl = (long)nx * ny;
     const int total = np * ny * nz;
@@ -162,8 +164,10 @@ __global__ void __launch_bounds__(256) k_rbgs_pairs(LV<float> L, float* __restri
         const float cxm = m ? cxo.x : L.cx[cl], cxp = m ? cxo.y : cxo.x;
         const float cym = pick(ld_f2(L.cy, c2 + dym)), cyp = pick(ld_f2(L.cy, c2));
         const float czm = pick(ld_f2(L.cz, c2 + dzm)), czp = pick(ld_f2(L.cz, c2));
-        const float sum = cxp * uxp + cxm * uxm + cyp * pick(ld_f2(u, c2 + dyp)) + cym * pick(ld_f2(u, c2 + dym)) +
-                          czp * pick(ld_f2(u, c2 + dzp)) + czm * pick(ld_f2(u, c2 + dzm));
+        const float sum = init ? 0.f
+                               : cxp * uxp + cxm * uxm + cyp * pick(ld_f2(u, c2 + dyp)) +
+                                     cym * pick(ld_f2(u, c2 + dym)) + czp * pick(ld_f2(u, c2 + dzp)) +
+                                     czm * pick(ld_f2(u, c2 + dzm));
         const float d = cxp + cxm + cyp + cym + czp + czm;
         u[c2 + m] = __fdividef(sum - pick(ld_f2(f, c2)), d);
     }
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(256) k_rbgs_pairs(LV<float> L, float* __restri
 
 template <typename T>
 __global__ void k_residual(LV<T> L, const T* u, const T* f, T* r) {
+    griddep_wait();
     const long rows = (long)L.ny * L.nz;
     for (long row = blockIdx.x; row < rows; row += gridDim.x)
     for (int i = threadIdx.x; i < L.nx; i += blockDim.x) {
@@ -183,6 +188,7 @@ __global__ void k_residual(LV<T> L, const T* u, const T* f, T* r) {
 // full weighting (1/4, 1/2, 1/4) per axis
 template <typename T>
 __global__ void k_restrict(LV<T> F, const T* r, LV<T> C, T* fc) {
+    griddep_wait();
     const long rows = (long)C.ny * C.nz;
     const int zoff = F.zper ? 0 : 1;
     const long pl = (long)F.nx * F.ny;
@@ -214,6 +220,7 @@ __global__ void k_restrict(LV<T> F, const T* r, LV<T> C, T* fc) {
 // both (fine nx % 4 == 0, coarse nx even, fine nx = 2 coarse nx).
 __global__ void __launch_bounds__(256) k_restrict4(LV<float> F, const float* __restrict__ r, LV<float> C,
                                                    float* __restrict__ fc) {
+    griddep_wait();
     const int nh = C.nx >> 1;
     const int total = nh * C.ny * C.nz;
     const int zoff = F.zper ? 0 : 1;
@@ -248,6 +255,7 @@ __global__ void __launch_bounds__(256) k_restrict4(LV<float> F, const float* __r
 // trilinear interpolation of the coarse correction, added to u
 template <typename T>
 __global__ void k_prolong_add(LV<T> F, T* u, LV<T> C, const T* uc) {
+    griddep_wait();
     const long rows = (long)F.ny * F.nz;
     const int zoff = F.zper ? 0 : 1;
     const long cpl = (long)C.nx * C.ny;
@@ -283,6 +291,7 @@ __global__ void k_prolong_add(LV<T> F, T* u, LV<T> C, const T* uc) {
 // the quad, with the one or two coarse rows and planes of its (j, k).
 __global__ void __launch_bounds__(256) k_prolong_add4(LV<float> F, float* __restrict__ u, LV<float> C,
                                                       const float* __restrict__ uc) {
+    griddep_wait();
     const int nx4 = F.nx >> 2;
     const int total = nx4 * F.ny * F.nz;
     const int zoff = F.zper ? 0 : 1;
@@ -735,6 +744,7 @@ __device__ __forceinline__ float4 f4_axpy(float a, float4 x, float4 y) {   // a 
 __global__ void k_update_xr4(long n4, float4* __restrict__ x, float4* __restrict__ r, const float4* __restrict__ p,
                              const float4* __restrict__ q, const double* scal, int num, int den) {
     __shared__ float alpha_s;
+    griddep_wait();
     if (threadIdx.x == 0) alpha_s = (float)(scal[num] / scal[den]);
     __syncthreads();
     const float alpha = alpha_s;
@@ -747,6 +757,7 @@ __global__ void k_update_xr4(long n4, float4* __restrict__ x, float4* __restrict
 __global__ void k_update_p4(long n4, float4* __restrict__ p, const float4* __restrict__ z, const double* scal,
                             int num, int den) {
     __shared__ float beta_s;
+    griddep_wait();
     if (threadIdx.x == 0) beta_s = (float)(scal[num] / scal[den]);
     __syncthreads();
     const float beta = beta_s;
@@ -756,6 +767,7 @@ __global__ void k_update_p4(long n4, float4* __restrict__ p, const float4* __res
 
 __global__ void k_dot4(long n4, const float4* __restrict__ a, const float4* __restrict__ b, double* partial) {
     __shared__ double red[32];
+    griddep_wait();
     KSum<float> loc;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n4; t += (long)gridDim.x * blockDim.x) {
         const float4 u = a[t], v = b[t];
@@ -766,6 +778,7 @@ __global__ void k_dot4(long n4, const float4* __restrict__ a, const float4* __re
 }
 
 __global__ void k_copy4(long n4, float4* __restrict__ dst, const float4* __restrict__ src) {
+    griddep_wait();
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n4; t += (long)gridDim.x * blockDim.x)
         dst[t] = src[t];
 }
@@ -858,6 +871,7 @@ __global__ void __launch_bounds__(1024) k_apply_zm(LV<float> L, const float* __r
                                                    double* partial, int sz) {
     extern __shared__ __align__(16) float zsm[];
     __shared__ double red[32];
+    griddep_wait();
     const int nx = L.nx, ny = L.ny, nz = L.nz, nx4 = nx >> 2;
     const long pl = (long)nx * ny;
     const int tid = threadIdx.x;
@@ -972,6 +986,7 @@ bool apply_zm_grid(const LV<float>& L, dim3& grid, int& sz, size_t& smem, int& t
 // out[c] = sum_b partial[b * ncomp + c], in a fixed order
 __global__ void k_finalize(const double* partial, int nparts, int ncomp, double* out) {
     __shared__ double red[32];
+    griddep_wait();
     for (int c = 0; c < ncomp; ++c) {
         double loc = 0.0;
         for (int b = threadIdx.x; b < nparts; b += blockDim.x) loc += partial[(long)b * ncomp + c];
@@ -1460,6 +1475,7 @@ __device__ void blk_prolong_add(const LV<T>& F, T* u, const LV<T>& C, const T* u
 template <typename T>
 __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseSet<T> S) {
     __shared__ double red[32];
+    griddep_wait();
     for (int l = S.l0; l < S.L - 1; ++l) {
         const LV<T>& V = S.lv[l];
         const int np = V.nx * V.ny * V.nz;
@@ -1632,6 +1648,7 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle_smem(CoarseSet<T> S) {
     extern __shared__ __align__(16) unsigned char craw[];
     __shared__ double red[32];
     __shared__ LV<T> lv[16];
+    griddep_wait();
     __shared__ T* su[16];
     __shared__ T* sf[16];
     __shared__ T* sr[16];
@@ -1747,10 +1764,27 @@ void coarse_vcycle_init() {
     cudaFuncSetAttribute(k_coarse_vcycle_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemBytes);
 }
 
+// A launch with programmatic stream serialization (see griddep_wait): the
+// kernel must call griddep_wait() before its first global memory access.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <typename T> void launch_coarse_vcycle(const CoarseSet<T>& S, cudaStream_t s) {
     const size_t b = coarse_smem_bytes(S);
-    if (b <= kCoarseSmemBytes) k_coarse_vcycle_smem<T><<<1, 1024, b, s>>>(S);
-    else k_coarse_vcycle<T><<<1, 1024, 0, s>>>(S);
+    if (b <= kCoarseSmemBytes) launch_pdl(k_coarse_vcycle_smem<T>, dim3(1), dim3(1024), b, s, S);
+    else launch_pdl(k_coarse_vcycle<T>, dim3(1), dim3(1024), 0, s, S);
 }
 template void launch_coarse_vcycle<float>(const CoarseSet<float>&, cudaStream_t);
 template void launch_coarse_vcycle<double>(const CoarseSet<double>&, cudaStream_t);
@@ -1798,7 +1832,7 @@ template <typename T> void launch_axpy1(const LV<T>& L, T* x, const T* y, cudaSt
 GP_KINST(float)
 GP_KINST(double)
 void launch_finalize(const double* partial, int nparts, int ncomp, double* out, cudaStream_t s) {
-    k_finalize<<<1, 1024, 0, s>>>(partial, nparts, ncomp, out);
+    launch_pdl(k_finalize, dim3(1), dim3(1024), 0, s, partial, nparts, ncomp, out);
 }
 void launch_rho_stats(long n, const double* rho, double* partial, cudaStream_t s) {
     k_rho_stats<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, rho, partial);
@@ -1842,22 +1876,22 @@ void launch_update_phi(const Geo& g, double* phi, const T* e_full, const T* e_ba
     k_update_phi<T><<<grid_for(n, 256), 256, 0, s>>>(g, phi, e_full, e_band, band_first, band_nz);
 }
 
-template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s) {
+template <typename T> void launch_rbgs(const LV<T>& L, T* u, const T* f, int color, cudaStream_t s, bool init) {
     if constexpr (sizeof(T) == 4) {
         if (!L.cell) {
             const long pairs = (long)(L.nx / 2) * L.ny * L.nz;
-            k_rbgs_pairs<<<grid_for(pairs, 256), 256, 0, s>>>(L, u, f, color);
+            launch_pdl(k_rbgs_pairs, dim3(grid_for(pairs, 256)), dim3(256), 0, s, L, u, f, color, (int)init);
             return;
         }
     }
     const long rows = (long)L.ny * L.nz;
-    k_rbgs<T><<<row_blocks(rows), row_threads(L.nx / 2), 0, s>>>(L, u, f, color);
+    launch_pdl(k_rbgs<T>, dim3(row_blocks(rows)), dim3(row_threads(L.nx / 2)), 0, s, L, u, f, color, (int)init);
 }
 template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* f, T* r, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         dim3 grid; int sz, th; size_t sm;
         if (apply_zm_grid(L, grid, sz, sm, th)) {
-            k_apply_zm<false><<<grid, th, sm, s>>>(L, u, f, r, nullptr, sz);
+            launch_pdl(k_apply_zm<false>, grid, dim3(th), sm, s, L, u, f, r, (double*)nullptr, sz);
             return;
         }
         if (L.cell && L.nx % 4 == 0) {
@@ -1866,30 +1900,30 @@ template <typename T> void launch_residual(const LV<T>& L, const T* u, const T* 
         }
     }
     const long rows = (long)L.ny * L.nz;
-    k_residual<T><<<row_blocks(rows), row_threads(L.nx), 0, s>>>(L, u, f, r);
+    launch_pdl(k_residual<T>, dim3(row_blocks(rows)), dim3(row_threads(L.nx)), 0, s, L, u, f, r);
 }
 template <typename T> void launch_restrict(const LV<T>& F, const T* r, const LV<T>& C, T* fc, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (F.nx % 4 == 0 && C.nx * 2 == F.nx && C.nx % 2 == 0 &&
             ((reinterpret_cast<uintptr_t>(r) & 15) | (reinterpret_cast<uintptr_t>(fc) & 7)) == 0) {
             const long pairs = (long)C.nx * C.ny * C.nz / 2;
-            k_restrict4<<<grid_for(pairs, 256), 256, 0, s>>>(F, r, C, fc);
+            launch_pdl(k_restrict4, dim3(grid_for(pairs, 256)), dim3(256), 0, s, F, r, C, fc);
             return;
         }
     }
     const long rows = (long)C.ny * C.nz;
-    k_restrict<T><<<row_blocks(rows), row_threads(C.nx), 0, s>>>(F, r, C, fc);
+    launch_pdl(k_restrict<T>, dim3(row_blocks(rows)), dim3(row_threads(C.nx)), 0, s, F, r, C, fc);
 }
 template <typename T> void launch_prolong_add(const LV<T>& F, T* u, const LV<T>& C, const T* uc, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (F.nx % 4 == 0 && C.nx * 2 == F.nx && (reinterpret_cast<uintptr_t>(u) & 15) == 0) {
             const long quads = (long)F.nx * F.ny * F.nz / 4;
-            k_prolong_add4<<<grid_for(quads, 256), 256, 0, s>>>(F, u, C, uc);
+            launch_pdl(k_prolong_add4, dim3(grid_for(quads, 256)), dim3(256), 0, s, F, u, C, uc);
             return;
         }
     }
     const long rows = (long)F.ny * F.nz;
-    k_prolong_add<T><<<row_blocks(rows), row_threads(F.nx), 0, s>>>(F, u, C, uc);
+    launch_pdl(k_prolong_add<T>, dim3(row_blocks(rows)), dim3(row_threads(F.nx)), 0, s, F, u, C, uc);
 }
 template <typename T> void launch_coarsen_faces(const LV<T>& F, int nxc, int nyc, int nzc, T* cx, T* cy, T* cz,
                                                 cudaStream_t s) {
@@ -1927,7 +1961,7 @@ template <typename T> void launch_applyA_dot(const LV<T>& L, const T* p, T* q, d
     if constexpr (sizeof(T) == 4) {
         dim3 grid; int sz, th; size_t sm;
         if (apply_zm_grid(L, grid, sz, sm, th)) {
-            k_apply_zm<true><<<grid, th, sm, s>>>(L, p, nullptr, q, partial, sz);
+            launch_pdl(k_apply_zm<true>, grid, dim3(th), sm, s, L, p, (const float*)nullptr, q, partial, sz);
             return;
         }
         if (L.cell && L.nx % 4 == 0) {
@@ -1948,8 +1982,8 @@ inline bool vec4_ok(long n, int elem, std::initializer_list<const void*> ptrs) {
 template <typename T> void launch_dot(const LV<T>& L, const T* a, const T* b, double* partial, cudaStream_t s) {
     const long n = (long)L.nx * L.ny * L.nz;
     if (vec4_ok(n, sizeof(T), {a, b})) {
-        k_dot4<<<kReduceBlocks, kReduceThreads, 0, s>>>(n / 4, reinterpret_cast<const float4*>(a),
-                                                         reinterpret_cast<const float4*>(b), partial);
+        launch_pdl(k_dot4, dim3(kReduceBlocks), dim3(kReduceThreads), 0, s, n / 4, reinterpret_cast<const float4*>(a),
+                   reinterpret_cast<const float4*>(b), partial);
         return;
     }
     k_dot<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, a, b, partial);
@@ -1958,9 +1992,9 @@ template <typename T> void launch_update_xr(const LV<T>& L, T* x, T* r, const T*
                                             int num, int den, cudaStream_t s) {
     const long n = (long)L.nx * L.ny * L.nz;
     if (vec4_ok(n, sizeof(T), {x, r, p, q})) {
-        k_update_xr4<<<grid_for(n / 4, 256), 256, 0, s>>>(n / 4, reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(r),
-                                                          reinterpret_cast<const float4*>(p),
-                                                          reinterpret_cast<const float4*>(q), scal, num, den);
+        launch_pdl(k_update_xr4, dim3(grid_for(n / 4, 256)), dim3(256), 0, s, n / 4, reinterpret_cast<float4*>(x),
+                   reinterpret_cast<float4*>(r), reinterpret_cast<const float4*>(p), reinterpret_cast<const float4*>(q),
+                   scal, num, den);
         return;
     }
     k_update_xr<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, r, p, q, scal, num, den);
@@ -1969,8 +2003,8 @@ template <typename T> void launch_update_p(const LV<T>& L, T* p, const T* z, con
                                            cudaStream_t s) {
     const long n = (long)L.nx * L.ny * L.nz;
     if (vec4_ok(n, sizeof(T), {p, z})) {
-        k_update_p4<<<grid_for(n / 4, 256), 256, 0, s>>>(n / 4, reinterpret_cast<float4*>(p),
-                                                         reinterpret_cast<const float4*>(z), scal, num, den);
+        launch_pdl(k_update_p4, dim3(grid_for(n / 4, 256)), dim3(256), 0, s, n / 4, reinterpret_cast<float4*>(p),
+                   reinterpret_cast<const float4*>(z), scal, num, den);
         return;
     }
     k_update_p<T><<<grid_for(n, 256), 256, 0, s>>>(n, p, z, scal, num, den);
@@ -1978,8 +2012,8 @@ template <typename T> void launch_update_p(const LV<T>& L, T* p, const T* z, con
 template <typename T> void launch_copy_level(const LV<T>& L, T* dst, const T* src, cudaStream_t s) {
     const long n = (long)L.nx * L.ny * L.nz;
     if (vec4_ok(n, sizeof(T), {dst, src})) {
-        k_copy4<<<grid_for(n / 4, 256), 256, 0, s>>>(n / 4, reinterpret_cast<float4*>(dst),
-                                                     reinterpret_cast<const float4*>(src));
+        launch_pdl(k_copy4, dim3(grid_for(n / 4, 256)), dim3(256), 0, s, n / 4, reinterpret_cast<float4*>(dst),
+                   reinterpret_cast<const float4*>(src));
         return;
     }
     k_copy<T><<<grid_for(n, 256), 256, 0, s>>>(n, dst, src);
@@ -2002,7 +2036,7 @@ template <typename T> void launch_band_rhs(const Geo& g, const T* epsT, const T*
     template void launch_residual64<T>(const Geo&, const double*, const double*, const double*, T*, double*, \
                                        cudaStream_t);                                                        \
     template void launch_update_phi<T>(const Geo&, double*, const T*, const T*, int, int, cudaStream_t);     \
-    template void launch_rbgs<T>(const LV<T>&, T*, const T*, int, cudaStream_t);                             \
+    template void launch_rbgs<T>(const LV<T>&, T*, const T*, int, cudaStream_t, bool);                             \
     template void launch_residual<T>(const LV<T>&, const T*, const T*, T*, cudaStream_t);                    \
     template void launch_restrict<T>(const LV<T>&, const T*, const LV<T>&, T*, cudaStream_t);                \
     template void launch_prolong_add<T>(const LV<T>&, T*, const LV<T>&, const T*, cudaStream_t);             \
