@@ -232,7 +232,7 @@ def gpu_arm(args, rank, world):
 
     def make_solver(precision, split):
         extra = {"kind": args.kind, "gamma_tail": args.gamma_tail, "zlim": zlim} if args.kind else {}
-        for key in ("nu_coarse", "nu1", "nu2"):
+        for key in ("nu_coarse", "nu1", "nu2", "inner"):
             if getattr(args, key) is not None:
                 extra[key] = getattr(args, key)
         return P.GPSolver(w.grid, w.cell, precision=precision, split=split, levels=w.levels,
@@ -947,6 +947,8 @@ def main():
                     help="smoothing sweeps on the levels below the finest (default: the library's)")
     ap.add_argument("--nu1", type=int, default=None, help="pre-smoothing sweeps (default: the library's)")
     ap.add_argument("--nu2", type=int, default=None, help="post-smoothing sweeps (default: the library's)")
+    ap.add_argument("--inner", type=int, default=None,
+                    help="CG iterations of the first outer correction (default: the library's)")
     ap.add_argument("--sweep-shape", type=int, default=-1,
                     help="finest-level smoother tile (-1: autotuned; fixed shapes keep profiles comparable)")
     args = ap.parse_args()

@@ -105,9 +105,10 @@ typedef struct {
                              not use r0 and w */
     double beta;          /* kinds 1, 2: the exponent beta of Eq. 10 (2.4) */
     double zlim;          /* kind 2: z_lim of Eq. 19, Angstrom inside the cell (0) */
-    int nu_coarse;        /* sweeps before and after the coarse correction on the levels below the
-                             finest, 0 .. 8; 0 = nu1, nu2 there too (4: the levels below the finest
-                             are cheap per sweep, and more sweeps there cut the V-cycles per solve) */
+    int nu_coarse;        /* sweeps before and after the coarse correction on the second coarse level
+                             and below, 0 .. 8; the first coarse level and the finest use nu1, nu2;
+                             0 = nu1, nu2 everywhere (4: those levels are cheap per sweep, and more
+                             sweeps there cut the V-cycles per solve) */
     int inner_adapt;      /* full box: 1 = the first correction runs `inner` CG iterations, each later
                              one as many as the contraction measured over the previous one predicts for
                              half the tolerance (1 .. 2 inner; with precision 1 for at most a 1e-5

@@ -457,8 +457,12 @@ void smooth_fine(gp_ctx* c, Hier<T>& H, T* u, const T* f, int nu, int first) {
 template <typename T>
 void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
     const int L = H.L;
-    const int nuc1 = c->prm.nu_coarse > 0 ? c->prm.nu_coarse : c->prm.nu1;   // levels below the finest
+    const int nuc1 = c->prm.nu_coarse > 0 ? c->prm.nu_coarse : c->prm.nu1;   // levels 2 and below
     const int nuc2 = c->prm.nu_coarse > 0 ? c->prm.nu_coarse : c->prm.nu2;
+    // level 1 keeps the finest level's counts: its sweeps are the dearest of the
+    // coarse ones, and more of them did not lower the V-cycle count
+    auto pre_sweeps = [&](int l) { return l == 1 ? c->prm.nu1 : nuc1; };
+    auto post_sweeps = [&](int l) { return l == 1 ? c->prm.nu2 : nuc2; };
     // first level small enough for the persistent single-CTA kernel (never the finest)
     int lc = L - 1;
     for (int l = 1; l < L; ++l) {
@@ -471,13 +475,13 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
         if (l == 0) {
             GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
             smooth_fine(c, H, u, f, c->prm.nu1, 0);
-        } else if (nuc1 == 0) {
+        } else if (pre_sweeps(l) == 0) {
             GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
         } else {
             // the first half sweep starts from u = 0 (the halo planes were zeroed at
             // allocation and no kernel writes them), so the level needs no clearing
-            ProfScope ps(c, GP_PROF_MG_COARSE, 2 * nuc1);
-            for (int it = 0; it < nuc1; ++it) {
+            ProfScope ps(c, GP_PROF_MG_COARSE, 2 * pre_sweeps(l));
+            for (int it = 0; it < pre_sweeps(l); ++it) {
                 launch_rbgs<T>(V, u, f, 0, c->s, it == 0);
                 launch_rbgs<T>(V, u, f, 1, c->s);
             }
@@ -509,8 +513,8 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
             smooth_fine(c, H, u, f, c->prm.nu2, 1);
             continue;
         }
-        ProfScope ps(c, GP_PROF_MG_COARSE, 2 * nuc2);
-        for (int it = 0; it < nuc2; ++it) {
+        ProfScope ps(c, GP_PROF_MG_COARSE, 2 * post_sweeps(l));
+        for (int it = 0; it < post_sweeps(l); ++it) {
             launch_rbgs<T>(V, u, f, 1, c->s);
             launch_rbgs<T>(V, u, f, 0, c->s);
         }
