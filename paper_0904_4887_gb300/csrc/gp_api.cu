@@ -974,10 +974,15 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         }
         launch_update_phi<T>(c->g, phi, x, (const T*)nullptr, 0, 0, c->s);
     };
+    // phi from its pairs where the loop kept it as pairs, and the gauge: the last
+    // residual pass summed phi into scal[9]
     auto finish_phi = [&] {
         if (master_df) {
             ProfScope ps(c, GP_PROF_UPDATE64, 1);
-            launch_from_df(c->n, c->phid, phi, c->s);
+            launch_from_df_gauge(c->n, c->phid, c->scal + 9, 1.0 / (double)c->n, phi, c->s);
+        } else {
+            ProfScope ps(c, GP_PROF_MISC, 1);
+            launch_sub_mean(c->n, phi, c->scal + 9, 1.0 / (double)c->n, c->s);
         }
     };
     // a bounded smoother wait that gave up leaves the fields undefined: the flag is
@@ -1032,10 +1037,6 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
         st.residual = rn;
         if (rn <= tol) {
             finish_phi();
-            {
-                ProfScope ps(c, GP_PROF_MISC, 1);
-                launch_sub_mean(c->n, phi, c->scal + 9, 1.0 / (double)c->n, c->s);
-            }
             GP_CHECK_LAUNCH();
             GP_CUDA(cudaStreamSynchronize(c->s));
             prof_collect(c);
@@ -1103,12 +1104,7 @@ gp_status solve_impl(gp_ctx* c, const double* rho, double* phi, double tol) {
             last_rn = rn;
         }
     }
-    // gauge: the last residual pass summed phi into scal[9]
     finish_phi();
-    {
-        ProfScope ps(c, GP_PROF_MISC, 1);
-        launch_sub_mean(c->n, phi, c->scal + 9, 1.0 / (double)c->n, c->s);
-    }
     GP_CHECK_LAUNCH();
     queue_expired_read();
     GP_CUDA(cudaStreamSynchronize(c->s));
@@ -1586,15 +1582,16 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             launch_coord_tables(c->g, at, tb.h_qlo, tb.h_inv_dq, c->ct_h, c->s);
         }
         c->sw = tb;
+        bool have_pmax = false;
         {
             ProfScope ps(c, GP_PROF_EPS, 1);
             // pe64 holds the per-point factor of d eps/d R: eps - 1 (kind 0) or d eps/d gamma (kinds 1, 2)
             if (p.kind != 0) launch_build_eps_gamma(c->g, at, dp, c->rvdw, c->eps64, c->pe64, c->eps32, c->s);
-            else launch_build_eps(c->g, at, dp, tb, c->ct_s, c->eps64, c->pe64, c->eps32, c->s);
+            else have_pmax = launch_build_eps(c->g, at, dp, tb, c->ct_s, c->eps64, c->pe64, c->eps32, c->plane_max, c->s);
         }
         c->epsd_ok = false;
         GP_CHECK_LAUNCH();
-        {
+        if (!have_pmax) {
             ProfScope ps(c, GP_PROF_MISC, 1);
             launch_plane_max(c->g, c->eps64, c->plane_max, c->s);
         }
@@ -1737,18 +1734,21 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
             Atoms at{c->atoms, c->atoms32, gauss_dev, n};
             const DielParams dp = c->dp;
             {
-                ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
+                // phi as float pairs, once, for both force kernels
+                ProfScope ps(c, GP_PROF_FORCES_EPS, 2);
+                launch_to_df(c->n, phi_dev, 1.0, c->rho_phid, c->s);
                 if (c->prm.kind != 0)
                     launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
                 else
-                    launch_forces_eps(c->g, at, dp, c->sw, c->ct_h, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
+                    launch_forces_eps(c->g, at, dp, c->sw, c->ct_h, phi_dev, c->rho_phid, nullptr, c->pe64,
+                                      c->forces_S, c->s);
             }
             GP_CHECK_LAUNCH();
             if (gauss_dev) {
                 const GaussTabs gt = ensure_gtab(c, n);
-                ProfScope ps(c, GP_PROF_FORCES_RHO, 3);
+                ProfScope ps(c, GP_PROF_FORCES_RHO, 2);
                 launch_gauss_tables(c->g, at, 8.0, gt, c->s);
-                launch_forces_rho(c->g, gt, phi_dev, c->rho_phid, c->forces_T, c->s);
+                launch_forces_rho(c->g, gt, nullptr, c->rho_phid, c->forces_T, c->s);
             }
             GP_CHECK_LAUNCH();
             ProfScope ps(c, GP_PROF_MISC, 1);
@@ -1887,7 +1887,8 @@ gp_status gp_energy_forces6(gp_ctx* c, const double* phi_dev, double mu, const d
                 if (c->prm.kind != 0)
                     launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, c->f6_w, c->pe64, c->forces_S, c->s);
                 else
-                    launch_forces_eps(c->g, at, dp, c->sw, c->ct_h, phi_dev, c->f6_w, c->pe64, c->forces_S, c->s);
+                    launch_forces_eps(c->g, at, dp, c->sw, c->ct_h, phi_dev, nullptr, c->f6_w, c->pe64,
+                                      c->forces_S, c->s);
             }
             GP_CHECK_LAUNCH();
             if (gauss_dev) {

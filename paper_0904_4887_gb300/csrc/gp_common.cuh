@@ -131,6 +131,28 @@ __device__ __forceinline__ float2 split_to_float2(double x) {
     return make_float2(hi, lo);
 }
 
+// The double of a float, exactly as the cast gives it, from the bits with integer
+// instructions (the cast is an FP64-pipe instruction on GB300): exponent rebased
+// from 127 to 1023, mantissa moved up 29 bits; a subnormal float is normalised
+// first (its leading one moved to the hidden bit); infinities and NaNs keep
+// their pattern.
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned e = (u >> 23) & 0xffu;
+    unsigned m = u & 0x7fffffu;
+    unsigned long long bits;
+    if (e == 0xffu) bits = sign | (0x7ffull << 52) | ((unsigned long long)m << 29);
+    else if (e != 0) bits = sign | ((unsigned long long)(e + 896) << 52) | ((unsigned long long)m << 29);
+    else if (m == 0) bits = sign;
+    else {
+        const int lz = __clz(m) - 8;              // the leading one sits at bit 23 - lz
+        m = (m << lz) & 0x7fffffu;
+        bits = sign | ((unsigned long long)(897 - lz) << 52) | ((unsigned long long)m << 29);
+    }
+    return __longlong_as_double((long long)bits);
+}
+
 inline DielParams make_diel(double eps0, double r0, double w, double rcut, int kind = 0, double beta = 2.4,
                             double zlim = 0.0) {
     DielParams p{};
@@ -189,8 +211,10 @@ struct CoordTabs {
 void launch_wrap_atoms(const Geo& g, const double* pos, int n, double* w64, float4* w32, cudaStream_t s);
 void launch_switch_tables(DielParams p, const SwTables& tb, double* s_coef, double* h_coef, float4* s_pack,
                           float4* h_pack, cudaStream_t s);
-void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct, double* eps64,
-                      double* pe64, float* eps32, cudaStream_t s);
+// true when the tabulated kernel ran, which also leaves each z-plane's max of eps - 1 in
+// plane_max (nz values); otherwise plane_max is untouched
+bool launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct, double* eps64,
+                      double* pe64, float* eps32, double* plane_max, cudaStream_t s);
 // Eq. 9-10: gamma = sum exp(-(d - rvdw)), eps = 1 + (eps0 - 1)/(1 + gamma^(2 beta)); fe64 = d eps / d gamma
 void launch_build_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, double* eps64, double* fe64,
                             float* eps32, cudaStream_t s);
@@ -217,9 +241,12 @@ void launch_build_rho_raw(const Geo& g, const GaussTabs& gt, double* rho, cudaSt
 void launch_plane_max(const Geo& g, const double* eps64, double* plane_max, cudaStream_t s);
 void launch_energy(const Geo& g, const double* rho, const double* phi, const double* eps64,
                    double* partial, cudaStream_t s);
+// phid: phi as float pairs, which the tabulated kernel reads unless wext is given
 void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct,
-                       const double* phi, const double* wext, const double* pe64, double* S, cudaStream_t s);
-// phid: scratch of nx*ny*nz float pairs (phi is converted into it first)
+                       const double* phi, const float2* phid, const double* wext, const double* pe64, double* S,
+                       cudaStream_t s);
+// phid: nx*ny*nz float pairs; phi is converted into it first unless phi is null
+// (phid then already holds it)
 void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, float2* phid, double* T,
                        cudaStream_t s);
 void launch_forces_finish(const double* S, const double* T, int n, double ce, double cr, double* F,
@@ -235,6 +262,9 @@ void launch_residual_df(const Geo& g, const float2* phid, const float2* bd, cons
 // phid += e (n even, 16-byte aligned); phi = hi + lo
 void launch_update_phid(long n, float2* phid, const float* e, cudaStream_t s);
 void launch_from_df(long n, const float2* src, double* dst, cudaStream_t s);
+// dst = src - scale * sum_slot[0] (pairs to doubles, the mean taken off)
+void launch_from_df_gauge(long n, const float2* src, const double* sum_slot, double scale, double* dst,
+                          cudaStream_t s);
 void launch_sub_mean(long n, double* x, const double* sum_slot, double scale, cudaStream_t s);
 template <typename T>
 void launch_residual64(const Geo& g, const double* phi, const double* rho, const double* eps64,

@@ -238,7 +238,7 @@ __device__ __forceinline__ df df_from(double v) {
     const float2 p = split_to_float2(v);      // the casts' result, without the FP64 pipe
     return {p.x, p.y};
 }
-__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double df_to(df a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
 __device__ __forceinline__ df as_df(float2 v) { return df{v.x, v.y}; }
 
 // (s, c): a compensated pair (value s + c) summed across the warp in place (Knuth two-sum per step)
@@ -543,10 +543,12 @@ __device__ __forceinline__ Tile make_tile_ez(const Geo& g) {
 }
 
 __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb, CoordTabs ct,
-                                                      double* eps64, double* pe64, float* eps32) {
+                                                      double* eps64, double* pe64, float* eps32,
+                                                      double* plane_max) {
     __shared__ int eai[ECAP][2];                 // (atom, image) of each surviving image
     __shared__ int cn[EB][NS];
     __shared__ df cf[EB][NS];
+    __shared__ unsigned long long pmax[EZ];      // the tile's max of eps - 1 per plane (bits of a double >= 0)
     __shared__ int ne;
     const Tile t = make_tile_ez(g);
     int tx, ty, tz;
@@ -564,6 +566,7 @@ __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParam
     const float dq = tb.s_dqf, qlo = tb.s_qlof;
     const float r0f = p.r0f, iwf = p.iwf;
     if (threadIdx.x == 0) ne = 0;
+    if (threadIdx.x < EZ) pmax[threadIdx.x] = 0ull;
     __syncthreads();
     for (int a0 = 0; a0 < at.n; a0 += ACHS) {
         const int na = min(ACHS, at.n - a0);
@@ -639,8 +642,16 @@ __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParam
             const double e = 1.0 + pe;
             eps64[idx] = e;
             if (pe64) pe64[idx] = pe;
-            if (eps32) eps32[idx] = (float)e;
+            if (eps32) eps32[idx] = split_to_float2(e).x;          // the rounded float, by integer instructions
+            if (plane_max) atomicMax(&pmax[tz + 4 * r], (unsigned long long)__double_as_longlong(e - 1.0));
         }
+    }
+    // the per-plane maxima of eps - 1 (the dry-plane test): nonnegative doubles
+    // order as their bit patterns, so the maxima are integer atomics
+    if (plane_max) {
+        __syncthreads();
+        if (threadIdx.x < EZ && t.k0 + (int)threadIdx.x < g.nz)
+            atomicMax(reinterpret_cast<unsigned long long*>(plane_max + t.k0 + threadIdx.x), pmax[threadIdx.x]);
     }
 }
 
@@ -667,6 +678,35 @@ __device__ __forceinline__ double force_weight(const Geo& g, const double* phi, 
     return ((ax * ax + bx * bx) * g.c2x + (ay * ay + by * by) * g.c2y + (az * az + bz * bz) * g.c2z) * pv;
 }
 
+// The same weight in df64 on the FP32 pipe, from phi as float pairs (a face
+// difference of two pairs keeps the pair representation's 2^-48 of phi; the
+// FP64 version spends about twenty FP64-pipe instructions per point). Returns -W.
+__device__ __forceinline__ df neg_force_weight_df(const Geo& g, const float2* phid, const double* wext, double pv,
+                                                  int i, int j, int k, long c, df c2x, df c2y, df c2z) {
+    if ((__double_as_longlong(pv) & 0x7fffffffffffffffll) == 0) return df{0.f, 0.f};
+    const df pvd = df_from(pv);
+    df W;
+    if (wext) {
+        W = df_mul(df_from(wext[c]), pvd);
+    } else {
+        const long pl = plane_of(g.nx, g.ny);
+        const long xp = c + (i == g.nx - 1 ? 1 - g.nx : 1), xm = c - (i == 0 ? 1 - g.nx : 1);
+        const long yp = c + (j == g.ny - 1 ? (1 - g.ny) * (long)g.nx : g.nx);
+        const long ym = c - (j == 0 ? (1 - g.ny) * (long)g.nx : g.nx);
+        const long zp = c + (k == g.nz - 1 ? (1 - g.nz) * pl : pl);
+        const long zm = c - (k == 0 ? (1 - g.nz) * pl : pl);
+        const df p0 = as_df(phid[c]), np0 = df{-p0.hi, -p0.lo};
+        auto sq2 = [&](long up, long dn) {
+            const df a = df_add(as_df(phid[up]), np0);
+            const float2 d = phid[dn];
+            const df b = df_add(p0, df{-d.x, -d.y});
+            return df_add(df_mul(a, a), df_mul(b, b));
+        };
+        W = df_mul(df_add(df_add(df_mul(sq2(xp, xm), c2x), df_mul(sq2(yp, ym), c2y)), df_mul(sq2(zp, zm), c2z)), pvd);
+    }
+    return df{-W.hi, -W.lo};
+}
+
 // ----------------------------------------------------------------- eps force, tabulated (df64)
 // The same sum as k_forces_eps with h = s'/(s d) from the packed table in df64
 // arithmetic, on 32 x 4 x 16 tiles. One warp per (tile, atom image): it
@@ -677,7 +717,7 @@ __device__ __forceinline__ double force_weight(const Geo& g, const double* phi, 
 constexpr int ECAPF = 384;              // image list capacity of the force kernel
 
 __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielParams p, SwTables tb, CoordTabs ct,
-                                                       const double* phi, const double* wext, const double* pe64,
+                                                       const float2* phid, const double* wext, const double* pe64,
                                                        double* S) {
     __shared__ df Ws[TX * TY * EZ];              // index tx + TX (ty + TY z)
     __shared__ df eres[ECAPF][3];                // each image's sum, converted to FP64 by a full warp
@@ -703,15 +743,18 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
     }
     __syncthreads();
     if (ne == 0) return;
-    for (int q = threadIdx.x; q < TX * TY * EZ; q += TT) {
-        const int tx = q % TX, ty = (q / TX) % TY, tz = q / (TX * TY);
-        const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
-        double W = 0.0;
-        if (i < g.nx && j < g.ny && k < g.nz) {
-            const long c = i + (long)g.nx * (j + (long)g.ny * k);
-            W = force_weight(g, phi, wext, pe64[c], i, j, k, c);
+    {
+        const df c2x = df_from(g.c2x), c2y = df_from(g.c2y), c2z = df_from(g.c2z);
+        for (int q = threadIdx.x; q < TX * TY * EZ; q += TT) {
+            const int tx = q % TX, ty = (q / TX) % TY, tz = q / (TX * TY);
+            const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+            df w = df{0.f, 0.f};
+            if (i < g.nx && j < g.ny && k < g.nz) {
+                const long c = i + (long)g.nx * (j + (long)g.ny * k);
+                w = neg_force_weight_df(g, phid, wext, pe64[c], i, j, k, c, c2x, c2y, c2z);
+            }
+            Ws[q] = w;         // sign of c = -W h folded in
         }
-        Ws[q] = df_from(-W);   // sign of c = -W h folded in
     }
     const float rc2f = p.rc2f;
     const float dq = tb.h_dqf, qlo = tb.h_qlof;
@@ -764,9 +807,9 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
                         const float dx = wd[warp][tx].hi, dy = wd[warp][TX + ty].hi, dz = wd[warp][TX + TY + tz].hi;
                         const float qq = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         if (!(qq < rc2f)) continue;
-                        const float d_ = sqrtf(qq);
-                        const float uf = (d_ - r0f) * iwf;
-                        ratio.hi = spf_norm * expf(-uf * uf) / d_;
+                        const float rs = rsqrtf(qq);          // 1/d
+                        const float uf = (qq * rs - r0f) * iwf;
+                        ratio.hi = spf_norm * exp2f(-1.44269504f * uf * uf) * rs;   // s'/d = spn exp(-u^2)/d
                         ratio.lo = 0.f;
                         const df c = df_mul(Ws[tx + TX * (ty + TY * tz)], ratio);
                         df_acc(sx, cx, c, wd[warp][tx]);
@@ -1328,10 +1371,15 @@ void launch_coord_tables(const Geo& g, Atoms at, double qlo, double inv_dq, cons
             g, at, qlo, inv_dq, ct);
 }
 
-void launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct, double* eps64,
-                      double* pe64, float* eps32, cudaStream_t s) {
-    if (tb.s32) k_build_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, ct, eps64, pe64, eps32);
-    else k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
+bool launch_build_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct, double* eps64,
+                      double* pe64, float* eps32, double* plane_max, cudaStream_t s) {
+    if (tb.s32) {
+        cudaMemsetAsync(plane_max, 0, sizeof(double) * g.nz, s);
+        k_build_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, ct, eps64, pe64, eps32, plane_max);
+        return true;
+    }
+    k_build_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, eps64, pe64, eps32);
+    return false;
 }
 
 size_t gauss_tabs_bytes(int n_atoms, int nmax) {
@@ -1386,15 +1434,16 @@ void launch_energy(const Geo& g, const double* rho, const double* phi, const dou
 }
 
 void launch_forces_eps(const Geo& g, Atoms at, DielParams p, const SwTables& tb, const CoordTabs& ct,
-                       const double* phi, const double* wext, const double* pe64, double* S, cudaStream_t s) {
-    if (tb.h32) k_forces_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, ct, phi, wext, pe64, S);
+                       const double* phi, const float2* phid, const double* wext, const double* pe64, double* S,
+                       cudaStream_t s) {
+    if (tb.h32) k_forces_eps_tab<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, tb, ct, phid, wext, pe64, S);
     else k_forces_eps<<<tile_grid(g), TT, 0, s>>>(g, at, p, tb, phi, wext, pe64, S);
 }
 
 void launch_forces_rho(const Geo& g, const GaussTabs& gt, const double* phi, float2* phid, double* T,
                        cudaStream_t s) {
     if (gt.G <= 0) return;
-    launch_to_df((long)g.nx * g.ny * g.nz, phi, 1.0, phid, s);
+    if (phi) launch_to_df((long)g.nx * g.ny * g.nz, phi, 1.0, phid, s);
     k_forces_rho<<<gt.G * kRhoChunks, kRhoThreads, 0, s>>>(g, gt, phid, T);
 }
 

@@ -1232,7 +1232,22 @@ __global__ void k_update_phid(long n2, float4* __restrict__ phid, const float2* 
 __global__ void k_from_df(long n, const float2* __restrict__ src, double* __restrict__ dst) {
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         const float2 v = src[t];
-        dst[t] = (double)v.x + (double)v.y;
+        dst[t] = f32_to_f64(v.x) + f32_to_f64(v.y);
+    }
+}
+
+// the same with the gauge: phi = (hi + lo) - mean, mean = scale * sum_slot[0]; the
+// pair less the mean's pair in df64 on the FP32 pipe, then one FP64 addition (the
+// two floats converted by their bits), instead of a conversion pass and a
+// read-modify-write pass over the FP64 field
+__global__ void k_from_df_gauge(long n, const float2* __restrict__ src, const double* sum_slot, double scale,
+                                double* __restrict__ dst) {
+    const float2 m = split_to_float2(sum_slot[0] * scale);
+    const d2 nm{-m.x, -m.y};
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const float2 v = src[t];
+        const d2 r = d2_add({v.x, v.y}, nm);
+        dst[t] = f32_to_f64(r.hi) + f32_to_f64(r.lo);
     }
 }
 
@@ -1854,6 +1869,10 @@ void launch_update_phid(long n, float2* phid, const float* e, cudaStream_t s) {
 }
 void launch_from_df(long n, const float2* src, double* dst, cudaStream_t s) {
     k_from_df<<<grid_for(n, 256), 256, 0, s>>>(n, src, dst);
+}
+void launch_from_df_gauge(long n, const float2* src, const double* sum_slot, double scale, double* dst,
+                          cudaStream_t s) {
+    k_from_df_gauge<<<grid_for(n, 256), 256, 0, s>>>(n, src, sum_slot, scale, dst);
 }
 
 void launch_residual_df(const Geo& g, const float2* phid, const float2* bd, const float2* epsd, float* r_out,
