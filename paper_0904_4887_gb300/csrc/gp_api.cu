@@ -425,16 +425,21 @@ void coarse_coeffs(gp_ctx* c, Hier<T>& H) {
 
 // ------------------------------------------------------------ V-cycle and PCG
 // nu fused red-black sweeps of the finest level, colour `first` first; the
-// result ends in u (ping-pong through H.tmp)
+// result ends in u (ping-pong through H.tmp). from_zero: u starts at 0 (the
+// pre-smoothing of a V-cycle): the first sweep then reads no u where the
+// kernel allows it, and u is cleared first where it does not.
 template <typename T>
-void smooth_fine(gp_ctx* c, Hier<T>& H, T* u, const T* f, int nu, int first) {
-    if (nu <= 0) return;
+void smooth_fine(gp_ctx* c, Hier<T>& H, T* u, const T* f, int nu, int first, bool from_zero = false) {
     const LV<T>& V = H.lv[0];
+    if (nu <= 0) {
+        if (from_zero) GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
+        return;
+    }
     if (sizeof(T) == 8) {
         // FP64 is bound by the FP64 pipe: the two-launch sweep issues no redundant work
         ProfScope ps(c, GP_PROF_SMOOTH0, 2 * nu);
         for (int it = 0; it < nu; ++it) {
-            launch_rbgs<T>(V, u, f, first, c->s);
+            launch_rbgs<T>(V, u, f, first, c->s, from_zero && it == 0);
             launch_rbgs<T>(V, u, f, 1 - first, c->s);
         }
         return;
@@ -443,8 +448,16 @@ void smooth_fine(gp_ctx* c, Hier<T>& H, T* u, const T* f, int nu, int first) {
     T* b = H.tmp;
     {
         ProfScope ps(c, GP_PROF_SMOOTH0, nu);
+        const int shape = H.sweep_shape < 0 ? 0 : H.sweep_shape;
         for (int it = 0; it < nu; ++it) {
-            launch_rb_sweep<T>(V, a, f, b, first, c->s, H.sweep_shape < 0 ? 0 : H.sweep_shape, c->dstatus + 1);
+            if (it == 0 && from_zero) {
+                if (!launch_rb_sweep<T>(V, nullptr, f, b, first, c->s, shape, c->dstatus + 1)) {
+                    GP_CUDA(cudaMemsetAsync(lbase(V, a), 0, level_bytes(V), c->s));
+                    launch_rb_sweep<T>(V, a, f, b, first, c->s, shape, c->dstatus + 1);
+                }
+            } else {
+                launch_rb_sweep<T>(V, a, f, b, first, c->s, shape, c->dstatus + 1);
+            }
             T* t = a; a = b; b = t;
         }
     }
@@ -473,8 +486,7 @@ void vcycle(gp_ctx* c, Hier<T>& H, T* u0, const T* f0) {
         T* u = l == 0 ? u0 : H.u[l];
         const T* f = l == 0 ? f0 : H.f[l];
         if (l == 0) {
-            GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
-            smooth_fine(c, H, u, f, c->prm.nu1, 0);
+            smooth_fine(c, H, u, f, c->prm.nu1, 0, true);
         } else if (pre_sweeps(l) == 0) {
             GP_CUDA(cudaMemsetAsync(lbase(V, u), 0, level_bytes(V), c->s));
         } else {

@@ -300,8 +300,10 @@ void rb_sweep_init();
 // polls per mbarrier wait of the whole-row smoother's main loop (< 0: the default);
 // gp_create sets it from GP_TEST_SWEEP_WAIT_POLLS, which only tests use
 void rb_sweep_set_wait_polls(int polls);
-// err: device flag set to 1 if a TMA wait of the row-tile kernel expired (may be null)
-template <typename T> void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first,
+// err: device flag set to 1 if a TMA wait of the row-tile kernel expired (may be null).
+// u_old null: the sweep starts from u = 0, which only the warp-specialised row shapes
+// do; for the others nothing is launched and the call returns false.
+template <typename T> bool launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first,
                                            cudaStream_t s, int shape, int* err = nullptr);
 template <typename T> int rb_sweep_autotune(const LV<T>& L, const T* u_old, const T* f, T* u_new, cudaStream_t s);
 // the shape actually used for a requested one (row tiles fall back to 0 where unavailable)

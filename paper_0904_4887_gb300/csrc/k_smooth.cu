@@ -524,6 +524,9 @@ __global__ void __maxnreg__((ws_max_regs<NPX, SY, K>()))
     const int qb = z0 - 2;
     const int T = z1 + 2 - qb;                       // planes qb .. z1+1; iterations 0 .. T-2
     const int tid = threadIdx.x;
+    // u_old == null: the sweep starts from u = 0 (the first sweep of a V-cycle):
+    // the u ring is zeroed once here and only eps is copied
+    const bool zu = u_old == nullptr;
 
     if (tid == 0) {
         bad = 0;
@@ -531,6 +534,8 @@ __global__ void __maxnreg__((ws_max_regs<NPX, SY, K>()))
         for (int k = 0; k < NRW; ++k) mbar_init(&R.rdy[k], NWC);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    if (zu)
+        for (int x = tid; x < NSW * RU * NPX; x += blockDim.x) (&R.u[0][0][0])[x] = make_float2(0.f, 0.f);
     __syncthreads();
 
     if (tid >= NC) {
@@ -555,7 +560,7 @@ __global__ void __maxnreg__((ws_max_regs<NPX, SY, K>()))
                     (&R.e[slot][0][0])[x] = make_float2(1.f, 1.f);
                 }
             __syncwarp();
-            const unsigned bytes = has_ue ? 2u * RU * ROWB : 0u;
+            const unsigned bytes = has_ue ? (zu ? 1u : 2u) * RU * ROWB : 0u;
             if (lane == 0) {
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 mbar_arrive_tx(&R.full[slot], bytes);
@@ -563,7 +568,7 @@ __global__ void __maxnreg__((ws_max_regs<NPX, SY, K>()))
             __syncwarp();
             const long base = (long)kg * pl;
             if (has_ue)
-                for (int r = lane; r < 2 * RU; r += 32) {
+                for (int r = zu ? RU + lane : lane; r < 2 * RU; r += 32) {
                     const int rr = r < RU ? r : r - RU;
                     const long off = base + (long)wrap_idx(j0 - 2 + rr, ny) * nx;
                     if (r < RU) bulk_g2s(&R.u[slot][rr][0], u_old + off, ROWB, &R.full[slot]);
@@ -843,6 +848,7 @@ bool rows_dispatch(int sy_id, int npx, const LV<float>& L, const float* u_old, c
         }
         return false;
     }
+    if (!attr && !u_old) return false;              // only the warp-specialised shapes start from zero
     switch (npx) {
 #define GP_NPX_CASE(N) \
     case N: return rows_dispatch_npx<N>(sy_id, L, u_old, f, u_new, first, s, attr, err);
@@ -877,15 +883,18 @@ void sweep_shape(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first
     k_rb_sweep<T, SX, SY><<<grid, NT, sm, s>>>(L, u_old, f, u_new, first, sz);
 }
 
+// false when nothing was launched: u_old null (start from zero) on a shape that
+// cannot do that
 template <typename T>
-void sweep_dispatch(int shape, const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s,
+bool sweep_dispatch(int shape, const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s,
                     bool attr, int* err = nullptr) {
     if constexpr (sizeof(T) == 4) {
         if (shape >= kSweepShapes) {
-            if (rows_dispatch(shape - kSweepShapes, L.nx / 2, L, u_old, f, u_new, first, s, attr, err)) return;
+            if (rows_dispatch(shape - kSweepShapes, L.nx / 2, L, u_old, f, u_new, first, s, attr, err)) return true;
             shape = 0;
         }
     }
+    if (!attr && !u_old) return false;
     switch (shape) {
 #define GP_CASE(I, X, Y) \
     case I: sweep_shape<T, X, Y>(L, u_old, f, u_new, first, s, attr); break;
@@ -893,6 +902,7 @@ void sweep_dispatch(int shape, const LV<T>& L, const T* u_old, const T* f, T* u_
 #undef GP_CASE
         default: sweep_shape<T, 64, 8>(L, u_old, f, u_new, first, s, attr); break;
     }
+    return true;
 }
 
 }  // namespace
@@ -916,9 +926,9 @@ void rb_sweep_init() {
 }
 
 template <typename T>
-void launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s, int shape,
+bool launch_rb_sweep(const LV<T>& L, const T* u_old, const T* f, T* u_new, int first, cudaStream_t s, int shape,
                      int* err) {
-    sweep_dispatch<T>(shape, L, u_old, f, u_new, first, s, false, err);
+    return sweep_dispatch<T>(shape, L, u_old, f, u_new, first, s, false, err);
 }
 
 // Time every tile shape on this level (three sweeps each, CUDA events on the
@@ -963,9 +973,9 @@ int rb_sweep_resolve(const LV<T>& L, int shape) {
 
 template int rb_sweep_resolve<float>(const LV<float>&, int);
 template int rb_sweep_resolve<double>(const LV<double>&, int);
-template void launch_rb_sweep<float>(const LV<float>&, const float*, const float*, float*, int, cudaStream_t, int,
+template bool launch_rb_sweep<float>(const LV<float>&, const float*, const float*, float*, int, cudaStream_t, int,
                                      int*);
-template void launch_rb_sweep<double>(const LV<double>&, const double*, const double*, double*, int, cudaStream_t,
+template bool launch_rb_sweep<double>(const LV<double>&, const double*, const double*, double*, int, cudaStream_t,
                                       int, int*);
 template int rb_sweep_autotune<float>(const LV<float>&, const float*, const float*, float*, cudaStream_t);
 template int rb_sweep_autotune<double>(const LV<double>&, const double*, const double*, double*, cudaStream_t);
