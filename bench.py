@@ -174,18 +174,16 @@ def make_inputs(w, frames, seed=0):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def roofline_for(kind, prof, n0, hbm, hbm_src, prec_bytes, zero_start_frac=0.0):
-    """Achieved vs peak for the kernel group `kind` from the live CUDA-event profile.
-    zero_start_frac: the share of the FP32 sweeps that start from u = 0 and read no u
-    (12 B/pt instead of 16)."""
+def roofline_for(kind, prof, n0, hbm, hbm_src, prec_bytes):
+    """Achieved vs peak for the kernel group `kind` from the live CUDA-event profile."""
     p = prof[kind]
     if p["launches"] == 0 or p["ms"] <= 0:
         return None
     per_launch_s = p["ms"] / 1e3 / p["launches"]
     if kind == "smooth0":
-        # FP32: one launch = one fused red-black sweep, 16 B/pt (read u, f, eps; write u),
-        # 12 B/pt for a sweep from u = 0; FP64: one launch = one colour of a sweep, half of 32 B/pt
-        bytes_per_launch = (16.0 - 4.0 * zero_start_frac) * n0
+        # FP32: one launch = one fused red-black sweep, 16 B/pt (read u, f, eps; write u);
+        # FP64: one launch = one colour of a sweep, half of 32 B/pt
+        bytes_per_launch = 16.0 * n0
         achieved = bytes_per_launch / per_launch_s / 1e9
         out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                "peak_source": hbm_src,
@@ -317,13 +315,14 @@ def gpu_arm(args, rank, world):
                     11: "k_rb_sweep_ws<%d, 16, 2>" % npx, 12: "k_rb_sweep_ws<%d, 14, 4>" % npx,
                     13: "k_rb_sweep_ws<%d, 14, 2>" % npx, 14: "k_rb_sweep_ws<%d, 12, 2>" % npx,
                     }.get(stats.sweep_shape, "k_rb_sweep")
-    # the first pre-smoothing sweep of each V-cycle starts from u = 0 on the warp-specialised
-    # shapes (7 and up) and reads no u: 12 of its 16 B/pt
-    prm = solver.params
-    zfrac = (1.0 / (prm.nu1 + prm.nu2)) if (args.precision == 1 and stats.sweep_shape >= 7 and prm.nu1 >= 1) else 0.0
-    smooth = roofline_for("smooth0", prof, n0, hbm, hbm_src, prec_bytes, zfrac)
-    if smooth is not None:
-        smooth["zero_start_share"] = zfrac
+    # the smoother's roofline covers its ordinary sweeps (16 B/pt); the first sweep of each
+    # V-cycle starts from u = 0, reads no u (12 B/pt) and is timed in a group of its own
+    smooth = roofline_for("smooth0", prof, n0, hbm, hbm_src, prec_bytes)
+    if smooth is not None and args.precision == 1 and prof.get("smooth0_zero", {}).get("launches"):
+        z = prof["smooth0_zero"]
+        z_s = z["ms"] / 1e3 / z["launches"]
+        smooth["from_zero"] = {"avg_launch_ms": z_s * 1e3, "algorithmic_bytes_per_launch": 12.0 * n0,
+                               "achieved": 12.0 * n0 / z_s / 1e9, "unit": "GB/s"}
         smooth["kernel"] = shape_kernel + " (finest level, fused red-black sweep)"
         smooth["traffic"] = sweep_traffic(shape_kernel, w.name) if args.precision == 1 else None
     # the roofline object is the finest-level smoother's: the kernel with the largest share of the

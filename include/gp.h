@@ -369,7 +369,8 @@ enum {
     GP_PROF_MISC = 11,       /* reductions, gauge, atom wrapping */
     GP_PROF_UPDATE64 = 12,   /* FP64 phi update */
     GP_PROF_ENERGY = 13,     /* energy reductions */
-    GP_PROF_KINDS = 14
+    GP_PROF_SMOOTH0_ZERO = 14, /* the first finest-level sweep of a V-cycle, from u = 0 (reads no u) */
+    GP_PROF_KINDS = 15
 };
 
 /* Enable (1) or disable (0) CUDA-event timing of kernel groups on this

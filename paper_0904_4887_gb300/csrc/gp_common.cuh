@@ -256,7 +256,10 @@ void launch_forces_finish(const double* S, const double* T, int n, double ce, do
 void launch_finalize(const double* partial, int nparts, int ncomp, double* out, cudaStream_t s);
 void launch_rho_stats(long n, const double* rho, double* partial, cudaStream_t s);
 // df64 (hi, lo FP32 pair) copies and the df64 full-box residual of the mixed-precision path
-void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStream_t s);
+// dst = the pairs of scale * src; nonzero (may be null): set to 1 if src has a nonzero
+// value (it is not cleared here); hi_out (may be null): the leading floats
+void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStream_t s, int* nonzero = nullptr,
+                  float* hi_out = nullptr);
 void launch_residual_df(const Geo& g, const float2* phid, const float2* bd, const float2* epsd, float* r_out,
                         double* partial, cudaStream_t s);
 // phid += e (n even, 16-byte aligned); phi = hi + lo

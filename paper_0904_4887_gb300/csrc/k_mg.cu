@@ -1109,12 +1109,22 @@ __device__ __forceinline__ d2 d2_ld(const float2* p, long i) {
 }
 
 // dst = (hi, lo) split of scale * src
-__global__ void k_to_df(long n, const double* __restrict__ src, double scale, float2* __restrict__ dst) {
+// optionally: *nonzero |= 1 if any value is nonzero (not +-0), and hi_out = the
+// leading floats (the value rounded to FP32)
+__global__ void k_to_df(long n, const double* __restrict__ src, double scale, float2* __restrict__ dst,
+                        int* nonzero, float* __restrict__ hi_out) {
     // the split by integer instructions (split_to_float2): one FP64 multiply per
     // value where scale != 1 instead of five FP64-pipe instructions
     const bool one = scale == 1.0;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
-        dst[t] = split_to_float2(one ? src[t] : scale * src[t]);
+    bool nz = false;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const double v = src[t];
+        nz |= (__double_as_longlong(v) << 1) != 0;
+        const float2 p = split_to_float2(one ? v : scale * v);
+        dst[t] = p;
+        if (hi_out) hi_out[t] = p.x;
+    }
+    if (nonzero && __any_sync(0xffffffffu, nz) && (threadIdx.x & 31) == 0) atomicOr(nonzero, 1);
 }
 
 // r = b - A phi on the periodic full box (cell eps, face means), in df64;
@@ -1236,18 +1246,15 @@ __global__ void k_from_df(long n, const float2* __restrict__ src, double* __rest
     }
 }
 
-// the same with the gauge: phi = (hi + lo) - mean, mean = scale * sum_slot[0]; the
-// pair less the mean's pair in df64 on the FP32 pipe, then one FP64 addition (the
-// two floats converted by their bits), instead of a conversion pass and a
-// read-modify-write pass over the FP64 field
+// the same with the gauge: phi = (hi + lo) - mean, mean = scale * sum_slot[0], in
+// FP64 (two additions; the floats converted by their bits), in one pass instead of
+// a conversion pass and a read-modify-write pass over the FP64 field
 __global__ void k_from_df_gauge(long n, const float2* __restrict__ src, const double* sum_slot, double scale,
                                 double* __restrict__ dst) {
-    const float2 m = split_to_float2(sum_slot[0] * scale);
-    const d2 nm{-m.x, -m.y};
+    const double m = sum_slot[0] * scale;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         const float2 v = src[t];
-        const d2 r = d2_add({v.x, v.y}, nm);
-        dst[t] = f32_to_f64(r.hi) + f32_to_f64(r.lo);
+        dst[t] = (f32_to_f64(v.x) + f32_to_f64(v.y)) - m;
     }
 }
 
@@ -1860,8 +1867,9 @@ void launch_residual64(const Geo& g, const double* phi, const double* rho, const
                        double* partial, cudaStream_t s) {
     k_residual64<T><<<kReduceBlocks, kReduceThreads, 0, s>>>(g, phi, rho, eps64, r_out, partial);
 }
-void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStream_t s) {
-    k_to_df<<<grid_for(n, 256), 256, 0, s>>>(n, src, scale, dst);
+void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStream_t s, int* nonzero,
+                  float* hi_out) {
+    k_to_df<<<grid_for(n, 256), 256, 0, s>>>(n, src, scale, dst, nonzero, hi_out);
 }
 void launch_update_phid(long n, float2* phid, const float* e, cudaStream_t s) {
     k_update_phid<<<grid_for(n / 2, 256), 256, 0, s>>>(n / 2, reinterpret_cast<float4*>(phid),

@@ -81,7 +81,7 @@ _SIGNATURES = {
 }
 
 PROF_KINDS = ["eps", "rho", "forces_eps", "forces_rho", "res64", "smooth0", "mg_fine", "mg_coarse", "krylov",
-              "fft", "setup", "misc", "update64", "energy"]
+              "fft", "setup", "misc", "update64", "energy", "smooth0_zero"]
 
 
 def gp_launch_count():

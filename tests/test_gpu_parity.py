@@ -544,3 +544,27 @@ def test_graph_captured_warm_start_frames():
     rho_o = O.charge_density(grid, cell, traj[3], at.Z, at.sigma_core, at.sigma_cloud)
     ref, _ = O.solve(rho_o, eps, h, tol=1e-14)
     assert _rel(phi.cpu().numpy(), ref) < 1e-7
+
+
+def test_checked_loop_starts_from_the_callers_phi(small_cases):
+    """The outer loop of the mixed solve starts from the phi it is given. From
+    zero its first residual is b itself (recorded as 1, not evaluated); from a
+    nonzero phi (the answer to a looser tolerance) the first residual is
+    evaluated, equals the residual that solve ended with, and the solve goes on
+    to the oracle's answer."""
+    GPSolver = _gpu()
+    (at, h, eps, rho), grid, cell = small_cases[0]
+    s = GPSolver(grid, cell, precision=1)
+    s.set_atoms(_t(at.pos))
+    rho_t = _t(rho)
+    phi = s.zeros()
+    s.solve(rho_t, phi, tol=1e-6)
+    st = s.stats()
+    assert st.history[0] == 1.0 and st.residual <= 1e-6
+    r1 = st.residual
+    s.solve(rho_t, phi, tol=1e-10)
+    st = s.stats()
+    assert abs(st.history[0] - r1) <= 0.05 * r1          # the gauge shift leaves the residual alone
+    assert st.residual <= 1e-10
+    ref, _ = O.solve(rho, eps, h, tol=1e-14)
+    assert _rel(phi.cpu().numpy(), ref) < 1e-8
