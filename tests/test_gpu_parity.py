@@ -568,3 +568,24 @@ def test_checked_loop_starts_from_the_callers_phi(small_cases):
     assert st.residual <= 1e-10
     ref, _ = O.solve(rho, eps, h, tol=1e-14)
     assert _rel(phi.cpu().numpy(), ref) < 1e-8
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_forces_of_every_atom_on_a_mid_size_grid(precision):
+    """Both force terms on 64x64x128 in a 16 x 16 x 32 A cell (18 atoms, the
+    cut-off sphere well inside the cell) against the oracle's gradient for
+    every atom, on the library's own phi, with rho moving and held fixed."""
+    GPSolver = _gpu()
+    grid, cell = (64, 64, 128), (16.0, 16.0, 32.0)
+    at = W.slab_atoms(cell, 3, 2, seed=7)
+    gauss = _t(_gauss(at))
+    s = GPSolver(grid, cell, precision=precision)
+    pos = _t(at.pos)
+    s.set_atoms(pos)
+    rho = s.build_rho(pos, gauss)
+    phi = s.solve(rho, tol=1e-10)
+    _, _, F = s.energy_forces(phi, rho, gauss)
+    Ge, Gr = O.energy_gradient(phi.cpu().numpy(), grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud)
+    assert _rel(F.cpu().numpy(), -(Ge + Gr)) < 1e-9
+    _, _, Fe = s.energy_forces(phi, rho, None)
+    assert _rel(Fe.cpu().numpy(), -Ge) < 1e-9
