@@ -262,9 +262,8 @@ void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStre
                   float* hi_out = nullptr);
 void launch_residual_df(const Geo& g, const float2* phid, const float2* bd, const float2* epsd, float* r_out,
                         double* partial, cudaStream_t s);
-// phid += e (n even, 16-byte aligned); phi = hi + lo
+// phid += e (n even, 16-byte aligned)
 void launch_update_phid(long n, float2* phid, const float* e, cudaStream_t s);
-void launch_from_df(long n, const float2* src, double* dst, cudaStream_t s);
 // dst = src - scale * sum_slot[0] (pairs to doubles, the mean taken off)
 void launch_from_df_gauge(long n, const float2* src, const double* sum_slot, double scale, double* dst,
                           cudaStream_t s);

@@ -1227,8 +1227,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_residual_df4(Geo g, const fl
     if (threadIdx.x == 0) partial[2 * blockIdx.x + 1] = sum;
 }
 
-// phid += e (df64 + FP32, 16-byte accesses: two points per float4) and its inverse,
-// phi = hi + lo in FP64, for the mixed-precision full-box loop that keeps phi as pairs
+// phid += e (df64 + FP32, 16-byte accesses: two points per float4), for the
+// mixed-precision full-box loop that keeps phi as pairs
 __global__ void k_update_phid(long n2, float4* __restrict__ phid, const float2* __restrict__ e) {
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n2; t += (long)gridDim.x * blockDim.x) {
         const float4 p = phid[t];
@@ -1239,16 +1239,9 @@ __global__ void k_update_phid(long n2, float4* __restrict__ phid, const float2* 
     }
 }
 
-__global__ void k_from_df(long n, const float2* __restrict__ src, double* __restrict__ dst) {
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        const float2 v = src[t];
-        dst[t] = f32_to_f64(v.x) + f32_to_f64(v.y);
-    }
-}
-
-// the same with the gauge: phi = (hi + lo) - mean, mean = scale * sum_slot[0], in
-// FP64 (two additions; the floats converted by their bits), in one pass instead of
-// a conversion pass and a read-modify-write pass over the FP64 field
+// phi = (hi + lo) - mean, mean = scale * sum_slot[0], in FP64 (two additions; the
+// floats converted by their bits): the pairs back to doubles and the gauge in one
+// pass instead of a conversion pass and a read-modify-write pass over the FP64 field
 __global__ void k_from_df_gauge(long n, const float2* __restrict__ src, const double* sum_slot, double scale,
                                 double* __restrict__ dst) {
     const double m = sum_slot[0] * scale;
@@ -1874,9 +1867,6 @@ void launch_to_df(long n, const double* src, double scale, float2* dst, cudaStre
 void launch_update_phid(long n, float2* phid, const float* e, cudaStream_t s) {
     k_update_phid<<<grid_for(n / 2, 256), 256, 0, s>>>(n / 2, reinterpret_cast<float4*>(phid),
                                                        reinterpret_cast<const float2*>(e));
-}
-void launch_from_df(long n, const float2* src, double* dst, cudaStream_t s) {
-    k_from_df<<<grid_for(n, 256), 256, 0, s>>>(n, src, dst);
 }
 void launch_from_df_gauge(long n, const float2* src, const double* sum_slot, double scale, double* dst,
                           cudaStream_t s) {
