@@ -565,11 +565,25 @@ __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParam
     const float reach = p.reachf + kMargin;
     const float dq = tb.s_dqf, qlo = tb.s_qlof;
     const float r0f = p.r0f, iwf = p.iwf;
+    // how many atom images reach the tile: when the list holds them all (the usual
+    // case), one pass collects them and one flush processes them, instead of a
+    // barrier pair per chunk of ACHS atoms
     if (threadIdx.x == 0) ne = 0;
     if (threadIdx.x < EZ) pmax[threadIdx.x] = 0ull;
     __syncthreads();
-    for (int a0 = 0; a0 < at.n; a0 += ACHS) {
-        const int na = min(ACHS, at.n - a0);
+    for (int q = threadIdx.x; q < at.n * 27; q += TT) {
+        float fx, fy, fz;
+        image32(at.w32, q / 27, q % 27, g, fx, fy, fz);
+        if (box_d2(t, fx, fy, fz) < reach * reach) atomicAdd(&ne, 1);
+    }
+    __syncthreads();
+    const int chunk = ne <= ECAP ? max(at.n, 1) : ACHS;
+    const int flush_at = ECAP - chunk * 27;
+    __syncthreads();
+    if (threadIdx.x == 0) ne = 0;
+    __syncthreads();
+    for (int a0 = 0; a0 < at.n; a0 += chunk) {
+        const int na = min(chunk, at.n - a0);
         for (int q = threadIdx.x; q < na * 27; q += TT) {
             const int a = a0 + q / 27, im = q % 27;
             float fx, fy, fz;
@@ -582,7 +596,7 @@ __global__ void __launch_bounds__(TT) k_build_eps_tab(Geo g, Atoms at, DielParam
         }
         __syncthreads();
         const int m = ne;
-        if (m > ECAP - ACHS * 27 || a0 + ACHS >= at.n) {
+        if (m > flush_at || a0 + chunk >= at.n) {
             for (int e0 = 0; e0 < m; e0 += EB) {
                 const int ms = min(EB, m - e0);
                 for (int r = threadIdx.x; r < ms * NS; r += TT) {
@@ -760,11 +774,15 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
     const float dq = tb.h_dqf, qlo = tb.h_qlof;
     const float r0f = p.r0f, iwf = p.iwf, spf_norm = p.spnf;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the count above sizes the passes: when the list holds every image, one pass
+    // collects them and one flush processes them
+    const int chunk = ne <= ECAPF ? max(at.n, 1) : ACHS;
+    const int flush_at = ECAPF - chunk * 27;
     __syncthreads();
     if (threadIdx.x == 0) ne = 0;
     __syncthreads();
-    for (int a0 = 0; a0 < at.n; a0 += ACHS) {
-        const int na = min(ACHS, at.n - a0);
+    for (int a0 = 0; a0 < at.n; a0 += chunk) {
+        const int na = min(chunk, at.n - a0);
         for (int q = threadIdx.x; q < na * 27; q += TT) {
             const int a = a0 + q / 27, im = q % 27;
             float fx, fy, fz;
@@ -777,7 +795,7 @@ __global__ void __launch_bounds__(TT) k_forces_eps_tab(Geo g, Atoms at, DielPara
         }
         __syncthreads();
         const int m = ne;
-        if (m > ECAPF - ACHS * 27 || a0 + ACHS >= at.n) {
+        if (m > flush_at || a0 + chunk >= at.n) {
             for (int e = warp; e < m; e += TT / 32) {
                 for (int c = lane; c < NS; c += 32) {
                     // grid index of this column / row / plane, clamped on ragged tiles (never read there)
