@@ -192,6 +192,10 @@ struct gp_ctx {
     CoordTabs ct_s{}, ct_h{};      // views: s(d) coordinates (build), h(d) coordinates and displacements (force)
     void* gtab = nullptr;          // periodized Gaussian factor tables (GaussTabs)
     size_t gtab_cap = 0;           // bytes
+    void* gmtab = nullptr;         // displacement and exponential tables of the df64 Eq. 9 kernels (GammaTabs)
+    size_t gmtab_cap = 0;          // bytes
+    GammaTabs gmt{};
+    bool gm_df = false;            // the df64 Eq. 9 kernels serve this dielectric (else the FP64 ones)
     SwTables sw{};
 
     // solver state
@@ -1569,6 +1573,34 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             dp.mz = (int)std::ceil(dp.rcut / c->g.lz);
             c->stats.gamma_cutoff = dp.rcut;
         }
+        // the df64 Eq. 9 kernels stage exp(-n) rows up to the radius (and exp(+n) rows up
+        // to the saturation distance of Eq. 19): radii beyond their rows take the FP64 kernels
+        c->gm_df = false;
+        if (p.kind != 0 && n_atoms > 0) {
+            const int m = std::max(dp.mx, std::max(dp.my, dp.mz));
+            const int kt1 = (int)std::floor(dp.rcut + 0.01) + 2;
+            double rvmax = 0.0;
+            for (int a = 0; a < n_atoms; ++a) rvmax = std::max(rvmax, c->rvdw_host[a]);
+            const int kg = p.kind == 2 ? (int)std::floor(rvmax + dp.esat + 0.01) + 2 : 1;
+            const long nimg = (long)(2 * dp.mx + 1) * (2 * dp.my + 1) * (2 * dp.mz + 1);
+            if (kt1 <= kGT1 && kg <= kGT1 && nimg * n_atoms < (1L << 30)) {
+                const int nmax = std::max(c->g.nx, std::max(c->g.ny, c->g.nz));
+                const size_t need = gamma_tabs_bytes(n_atoms, m, nmax);
+                if (need > c->gmtab_cap) {
+                    if (c->gmtab) cudaFree(c->gmtab);
+                    c->gmtab = nullptr;
+                    c->gmtab_cap = 0;
+                    if (cudaMalloc(&c->gmtab, need) != cudaSuccess) throw Err{GP_ERR_OOM, "cudaMalloc failed"};
+                    c->gmtab_cap = need;
+                }
+                c->gmt = gamma_tabs_view(c->gmtab, n_atoms, m, nmax);
+                c->gmt.kt1 = kt1;
+                c->gmt.kg = kg;
+                ProfScope ps(c, GP_PROF_EPS, 1);
+                launch_gamma_tables(c->g, at, dp, c->rvdw, c->gmt, c->s);
+                c->gm_df = true;
+            }
+        }
         c->dp = dp;
         // switching-function tables for these r0, w (when the tabulated range is away from d = 0)
         SwTables tb{};
@@ -1618,7 +1650,10 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
         {
             ProfScope ps(c, GP_PROF_EPS, 1);
             // pe64 holds the per-point factor of d eps/d R: eps - 1 (kind 0) or d eps/d gamma (kinds 1, 2)
-            if (p.kind != 0) launch_build_eps_gamma(c->g, at, dp, c->rvdw, c->eps64, c->pe64, c->eps32, c->s);
+            if (p.kind != 0 && c->gm_df)
+                launch_build_eps_gamma_df(c->g, at, dp, c->gmt, c->eps64, c->pe64, c->eps32, c->s);
+            else if (p.kind != 0)
+                launch_build_eps_gamma(c->g, at, dp, c->rvdw, c->eps64, c->pe64, c->eps32, c->s);
             else have_pmax = launch_build_eps(c->g, at, dp, tb, c->ct_s, c->eps64, c->pe64, c->eps32, c->plane_max, c->s);
         }
         c->epsd_ok = false;
@@ -1769,7 +1804,10 @@ gp_status gp_energy_forces(gp_ctx* c, const double* phi_dev, const double* rho_d
                 // phi as float pairs, once, for both force kernels
                 ProfScope ps(c, GP_PROF_FORCES_EPS, 2);
                 launch_to_df(c->n, phi_dev, 1.0, c->rho_phid, c->s);
-                if (c->prm.kind != 0)
+                if (c->prm.kind != 0 && c->gm_df)
+                    launch_forces_eps_gamma_df(c->g, at, dp, c->gmt, c->rho_phid, nullptr, c->pe64, c->forces_S,
+                                               c->s);
+                else if (c->prm.kind != 0)
                     launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, nullptr, c->pe64, c->forces_S, c->s);
                 else
                     launch_forces_eps(c->g, at, dp, c->sw, c->ct_h, phi_dev, c->rho_phid, nullptr, c->pe64,
@@ -1916,7 +1954,9 @@ gp_status gp_energy_forces6(gp_ctx* c, const double* phi_dev, double mu, const d
             const DielParams dp = c->dp;
             {
                 ProfScope ps(c, GP_PROF_FORCES_EPS, 1);
-                if (c->prm.kind != 0)
+                if (c->prm.kind != 0 && c->gm_df)
+                    launch_forces_eps_gamma_df(c->g, at, dp, c->gmt, nullptr, c->f6_w, c->pe64, c->forces_S, c->s);
+                else if (c->prm.kind != 0)
                     launch_forces_eps_gamma(c->g, at, dp, c->rvdw, phi_dev, c->f6_w, c->pe64, c->forces_S, c->s);
                 else
                     launch_forces_eps(c->g, at, dp, c->sw, c->ct_h, phi_dev, nullptr, c->f6_w, c->pe64,
@@ -2055,6 +2095,7 @@ void gp_destroy(gp_ctx* c) {
     if (c->atoms) cudaFree(c->atoms);
     if (c->atoms32) cudaFree(c->atoms32);
     if (c->gtab) cudaFree(c->gtab);
+    if (c->gmtab) cudaFree(c->gmtab);
     if (c->rvdw) cudaFree(c->rvdw);
     if (c->ratoms) cudaFree(c->ratoms);
     if (c->ratoms32) cudaFree(c->ratoms32);

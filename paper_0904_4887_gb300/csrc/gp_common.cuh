@@ -220,6 +220,37 @@ void launch_build_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* 
                             float* eps32, cudaStream_t s);
 void launch_forces_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, const double* phi,
                              const double* wext, const double* fe64, double* S, cudaStream_t s);
+// The same two sums in df64 on the FP32 pipe, from tables built once per set of atoms.
+// Per atom: exp(rvdw) and exp(-rvdw) as float pairs, (rvdw + esat)^2 in FP32 (a growing
+// Eq. 19 term whose squared distance reaches it saturates the point), and kzl, the
+// first grid plane k with k hz >= z of the atom in the cell when the atom belongs to
+// Eq. 19's lower layer (kind 2, z <= zlim), else 0: planes k < kzl lie below it.
+struct GAtom {
+    float2 a, b;
+    float qsat;
+    int kzl;
+};
+constexpr int kGT1 = 56;        // exp(-+n) rows the df64 kernels stage per atom: distances below kGT1 - 2 A
+struct GammaTabs {
+    float2* d;      // [n_atoms][2m + 1][3][nmax]: i h - (w_a + n L) for image digit n in [-m, m], as a pair
+    float2* t1;     // exp(-n), n < kGT1
+    float2* t2;     // exp(-j/256), j < 256
+    float2* u1;     // exp(+n), n < kGT1
+    float2* u2;     // exp(+j/256), j < 256
+    GAtom* at;      // [n_atoms]
+    int m, nmax;
+    int kt1;        // rows of exp(-n) a decaying term can use: floor(rcut) + 2
+    int kg;         // rows of exp(+n) a growing term can use before it saturates
+};
+size_t gamma_tabs_bytes(int n_atoms, int m, int nmax);
+GammaTabs gamma_tabs_view(void* base, int n_atoms, int m, int nmax);
+void launch_gamma_tables(const Geo& g, Atoms at, DielParams p, const double* rvdw, const GammaTabs& gt,
+                         cudaStream_t s);
+void launch_build_eps_gamma_df(const Geo& g, Atoms at, DielParams p, const GammaTabs& gt, double* eps64,
+                               double* fe64, float* eps32, cudaStream_t s);
+// phid: phi as float pairs (read unless wext is given)
+void launch_forces_eps_gamma_df(const Geo& g, Atoms at, DielParams p, const GammaTabs& gt, const float2* phid,
+                                const double* wext, const double* fe64, double* S, cudaStream_t s);
 // Periodized 1D Gaussian factor tables (k_fields.cu), Gaussian ge = 2 atom + {0 core, 1 cloud}
 struct GaussTabs {
     double* val;    // [G][3][nmax] X, Y, Z factors summed over the images -L, 0, +L

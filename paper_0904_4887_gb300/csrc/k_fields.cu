@@ -1096,6 +1096,519 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma(Geo g, Atoms at, DielPa
         }
 }
 
+// ----------------------------------------------------------------- eps, Eq. 9-10 and Eq. 19 in df64
+// The sums of k_build_eps_gamma and k_forces_eps_gamma with every (point, atom
+// image) pair in df64 on the FP32 pipe, on 32 x 4 x 16 tiles. A pair costs a
+// squared distance from the per-atom displacement tables (FP64 differences kept
+// as float pairs, so no pair needs an FP64 instruction), its df square root, and
+// the exponential by a table-driven method (Tang, ACM TOMS 15, 1989): with
+// k = rint(256 d) and r = d - k/256, |r| <= 1/512,
+//   exp(-d) = exp(-floor(k/256)) exp(-(k mod 256)/256) exp(-r),
+// the first factor from a row staged per atom image (already times the atom's
+// exp(rvdw)), the second from a 256-entry table, both as float pairs, and exp(-r)
+// from its Taylor series to r^5 (the remainder is below 3e-19), whose
+// 1 - r + r^2/2 is formed in df and the rest (below 1.3e-9) in FP32. A growing
+// Eq. 19 term exp(d - rvdw) takes the same steps with exp(+n), exp(+j/256) and
+// the series of exp(+r). A pair's error is a few units of 2^-48 relative to its
+// distance and its term.
+constexpr int GCAP = 3072;              // image list capacity (build)
+constexpr int GCAPF = 2048;             // image list capacity (force)
+constexpr int GB = 32;                  // atom images staged at a time (build)
+
+__device__ __forceinline__ long gtab_index(const GammaTabs& gt, int a, int n, int axis, int i) {
+    return (((long)a * (2 * gt.m + 1) + n + gt.m) * 3 + axis) * gt.nmax + i;
+}
+
+// exp(-x) (kNeg) or exp(+x) of x >= 0 given as df, times the staged row
+// row[n] = c exp(-+n) of the term's factor c; tab[j] = exp(-+j/256); n returns
+// the row used (the integer part of x, to within 1/512)
+template <bool kNeg>
+__device__ __forceinline__ df exp_tab(df x, const df* row, const df* tab, int& n) {
+    const int k = __float2int_rn(x.hi * 256.f);
+    n = min(k >> 8, kGT1 - 1);
+    const float rh = fmaf((float)k, -0.00390625f, x.hi);   // exact: |rh| <= 1/512 on x.hi's grid
+    const float s = rh + x.lo;                               // r = s + rl exactly (two-sum)
+    const float bb = s - rh;
+    const float rl = (rh - (s - bb)) + (x.lo - bb);
+    const float r2 = s * s;
+    const float r2e = fmaf(s, s, -r2) + 2.f * s * rl;       // r^2 = r2 + r2e
+    const float h = 0.5f * r2;
+    float u, ue, c;
+    if constexpr (kNeg) {
+        u = h - s;                                           // |s| >= |h|: ue is the exact error
+        ue = (h - (u + s)) - rl;
+        c = r2 * s * fmaf(s, fmaf(s, -1.f / 120.f, 1.f / 24.f), -1.f / 6.f);
+    } else {
+        u = h + s;
+        ue = (h - (u - s)) + rl;
+        c = r2 * s * fmaf(s, fmaf(s, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f);
+    }
+    const float lo = (ue + 0.5f * r2e) + c;
+    const float ph = 1.f + u;
+    const float pl = (u - (ph - 1.f)) + lo;
+    return df_mul(df_mul(row[n], tab[k & 255]), df{ph, pl});
+}
+
+// sqrt(q) as df for q.hi > 0 (a Newton step on the FP32 estimate, then the df
+// correction); y returns 1/sqrt(q.hi) to about 2^-23
+__device__ __forceinline__ df df_sqrt(df q, float& y) {
+    const float y0 = rsqrtf(q.hi);
+    const float s0 = q.hi * y0;
+    const float s = fmaf(fmaf(-s0, s0, q.hi), 0.5f * y0, s0);
+    y = y0 * fmaf(-0.5f * q.hi * y0, y0, 1.5f);
+    const float e = fmaf(-s, s, q.hi) + q.lo;
+    return df_quick(s, 0.5f * e * y);
+}
+
+// 1/d as df from d and an estimate y of 1/d.hi (one Newton step)
+__device__ __forceinline__ df df_recip(df d, float y) {
+    const float p = d.hi * y;
+    const float pe = fmaf(d.hi, y, -p);
+    const float del = ((1.f - p) - pe) - d.lo * y;
+    return df_quick(y, y * del);
+}
+
+// (s, c) += v as a df sum, renormalised after every term so that c stays below
+// half an ulp of s: a term far below s still lands in c with c's relative
+// precision (an unrenormalised error term grows with the terms it absorbs, and
+// terms below its half ulp are lost, all in one direction)
+__device__ __forceinline__ void df_add_to(float& s, float& c, df v) {
+    const float t = s + v.hi;
+    const float z = t - s;
+    float e = (s - (t - z)) + (v.hi - z);
+    e += c + v.lo;
+    s = t + e;
+    c = e - (s - t);
+}
+
+// A point's terms span 1 down to 1e-17: those from rows below kNear (d < ~10 A,
+// a few dozen per point) go into an FP64 sum, the rest (at most ~1e-3 of gamma)
+// into a df sum of their own, whose half ulp then sits far below any term that
+// matters. One df sum for all of them lost the terms beyond ~35 A (4e-12 of gamma).
+constexpr int kNear = 10;
+__device__ __forceinline__ void gamma_acc(double& D, float& F, float& G, df v, int n) {
+    if (n < kNear) D += f32_to_f64(v.hi) + f32_to_f64(v.lo);
+    else df_add_to(F, G, v);
+}
+
+// Appends, in order, the candidates q in [q0, q1) with keep(q) to list (when not
+// null) and returns their number. Every thread of the block calls it: thread t
+// tests a contiguous run, and an exclusive scan of the runs' counts places each
+// survivor, so the list (and every sum taken over it) does not depend on timing.
+template <typename Keep>
+__device__ int block_compact(int q0, int q1, Keep keep, int* list, int* scratch) {
+    const int per = (q1 - q0 + TT - 1) / TT;
+    const int b = q0 + (int)threadIdx.x * per, e = min(b + per, q1);
+    int c = 0;
+    for (int q = b; q < e; ++q) c += keep(q) ? 1 : 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();                        // scratch is free
+    if (lane == 31) scratch[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int v = lane < TT / 32 ? scratch[lane] : 0;
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane < TT / 32) scratch[lane] = inc - v;
+        if (lane == 31) scratch[TT / 32] = inc;
+    }
+    __syncthreads();
+    if (list) {
+        int off = scratch[w] + x - c;
+        for (int q = b; q < e; ++q)
+            if (keep(q)) list[off++] = q;
+    }
+    const int total = scratch[TT / 32];
+    __syncthreads();                        // the list is complete and every thread has the total
+    return total;
+}
+
+// column / row / plane c of the staged tile (c < NS): axis and grid index, clamped
+// on ragged tiles (the clamped values are never read: those points do not exist)
+__device__ __forceinline__ void staged_line(const Tile& t, const Geo& g, int c, int& axis, int& gi) {
+    if (c < TX) { axis = 0; gi = min(t.i0 + c, g.nx - 1); }
+    else if (c < TX + TY) { axis = 1; gi = min(t.j0 + c - TX, g.ny - 1); }
+    else { axis = 2; gi = min(t.k0 + c - TX - TY, g.nz - 1); }
+}
+
+// displacement of line (axis, gi) from the nearest image of atom a (digit -1, 0 or +1:
+// the atom and the point both lie in the cell)
+__device__ __forceinline__ df nearest_disp(const GammaTabs& gt, int a, int axis, int gi) {
+    df best = as_df(__ldg(gt.d + gtab_index(gt, a, 0, axis, gi)));
+    const df dm = as_df(__ldg(gt.d + gtab_index(gt, a, -1, axis, gi)));
+    const df dp = as_df(__ldg(gt.d + gtab_index(gt, a, 1, axis, gi)));
+    if (fabsf(dm.hi) < fabsf(best.hi)) best = dm;
+    if (fabsf(dp.hi) < fabsf(best.hi)) best = dp;
+    return best;
+}
+
+// image digit of image `im` along `axis`
+__device__ __forceinline__ int image_digit(const DielParams& p, int im, int axis) {
+    const int nxi = 2 * p.mx + 1, nyi = 2 * p.my + 1;
+    return axis == 0 ? im % nxi - p.mx : (axis == 1 ? (im / nxi) % nyi - p.my : im / (nxi * nyi) - p.mz);
+}
+
+// One table entry per thread: displacements (FP64, kept as float pairs), the
+// exponential tables, and the per-atom constants (kzl by FP64 comparisons of
+// k hz with z, the same test as the FP64 kernels').
+__global__ void k_gamma_tables(Geo g, Atoms at, DielParams p, const double* rvdw, GammaTabs gt) {
+    const int ND = 2 * gt.m + 1;
+    const long nd = (long)at.n * ND * 3 * gt.nmax;
+    const long total = nd + 2 * (kGT1 + 256) + at.n;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+        if (q < nd) {
+            const int i = (int)(q % gt.nmax);
+            const long r = q / gt.nmax;
+            const int axis = (int)(r % 3), n = (int)((r / 3) % ND) - gt.m, a = (int)(r / (3 * ND));
+            const int nax = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+            const double h = axis == 0 ? g.hx : (axis == 1 ? g.hy : g.hz);
+            const double L = axis == 0 ? g.lx : (axis == 1 ? g.ly : g.lz);
+            const double c = at.w64[3 * a + axis] + n * L;      // the FP64 kernels' image centre
+            gt.d[q] = i < nax ? split_to_float2(i * h - c) : make_float2(0.f, 0.f);
+            continue;
+        }
+        long r = q - nd;
+        if (r < kGT1) { gt.t1[r] = split_to_float2(exp(-(double)r)); continue; }
+        r -= kGT1;
+        if (r < 256) { gt.t2[r] = split_to_float2(exp(-(double)r / 256.0)); continue; }
+        r -= 256;
+        if (r < kGT1) { gt.u1[r] = split_to_float2(exp((double)r)); continue; }
+        r -= kGT1;
+        if (r < 256) { gt.u2[r] = split_to_float2(exp((double)r / 256.0)); continue; }
+        r -= 256;
+        const int a = (int)r;
+        const double rv = rvdw[a], za = at.w64[3 * a + 2];
+        GAtom ga;
+        ga.a = split_to_float2(exp(rv));
+        ga.b = split_to_float2(exp(-rv));
+        ga.qsat = (float)((rv + p.esat) * (rv + p.esat));
+        int kz = 0;
+        if (p.kind == 2 && za <= p.zlim) {
+            while (kz < g.nz && kz * g.hz < za) ++kz;           // planes k < kz have k hz < za
+        }
+        ga.kzl = kz;
+        gt.at[a] = ga;
+    }
+}
+
+__global__ void __launch_bounds__(TT) k_build_eps_gamma_df(Geo g, Atoms at, DielParams p, GammaTabs gt,
+                                                           double* eps64, double* fe64, float* eps32) {
+    __shared__ int elist[GCAP];
+    __shared__ df sx2[GB][TX];
+    __shared__ df sy2[GB][TY];
+    __shared__ df sz2[GB][EZ];
+    __shared__ df srow[GB][kGT1];
+    __shared__ df stab[256];
+    __shared__ int skz[GB];
+    __shared__ float sqs[GB];
+    __shared__ int scratch[TT / 32 + 1];
+    const Tile t = make_tile_ez(g);
+    int tx, ty, tz;
+    compact_point(threadIdx.x >> 5, threadIdx.x & 31, tx, ty, tz);
+    const int i = t.i0 + tx, j = t.j0 + ty;
+    bool valid[4], sat[4];
+    double D[4];
+    float F[4], G[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        valid[r] = i < g.nx && j < g.ny && t.k0 + tz + 4 * r < g.nz;
+        sat[r] = false;
+        D[r] = 0.0;
+        F[r] = 0.f;
+        G[r] = 0.f;
+    }
+    const bool eq19 = p.kind == 2;
+    if (eq19) {
+        // the growing terms first (each lower atom's nearest image, no cut-off): a
+        // point that saturates needs no decaying sum
+        for (int q = threadIdx.x; q < 256; q += TT) stab[q] = as_df(__ldg(gt.u2 + q));
+        const int ns = NS + gt.kg;
+        for (int a0 = 0; a0 < at.n; a0 += GCAP) {
+            const int nl =
+                block_compact(a0, min(a0 + GCAP, at.n), [&](int a) { return gt.at[a].kzl > t.k0; }, elist, scratch);
+            for (int e0 = 0; e0 < nl; e0 += GB) {
+                const int ms = min(GB, nl - e0);
+                for (int r = threadIdx.x; r < ms * ns; r += TT) {
+                    const int e = r / ns, c = r % ns;
+                    const int a = elist[e0 + e];
+                    if (c < NS) {
+                        int axis, gi;
+                        staged_line(t, g, c, axis, gi);
+                        const df dd = nearest_disp(gt, a, axis, gi);
+                        const df sq = df_mul(dd, dd);
+                        if (c < TX) sx2[e][c] = sq;
+                        else if (c < TX + TY) sy2[e][c - TX] = sq;
+                        else sz2[e][c - TX - TY] = sq;
+                    } else {
+                        const int n = c - NS;
+                        srow[e][n] = df_mul(as_df(gt.at[a].b), as_df(__ldg(gt.u1 + n)));
+                        if (n == 0) {
+                            skz[e] = gt.at[a].kzl;
+                            sqs[e] = gt.at[a].qsat;
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int e = 0; e < ms; ++e) {
+                    const df xy = df_add(sx2[e][tx], sy2[e][ty]);
+                    const int kz = skz[e];
+                    const float qs = sqs[e];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int zz = tz + 4 * r;
+                        if (!valid[r] || sat[r] || t.k0 + zz >= kz) continue;
+                        const df q = df_add(xy, sz2[e][zz]);
+                        if (!(q.hi < qs)) {                             // exp(d - rvdw) >= exp(esat)
+                            sat[r] = true;
+                            continue;
+                        }
+                        float y;
+                        int n;
+                        const df d = q.hi > 0.f ? df_sqrt(q, y) : df{0.f, 0.f};
+                        const df v = exp_tab<false>(d, srow[e], stab, n);
+                        gamma_acc(D[r], F[r], G[r], v, 0);          // exp(d - rvdw) > exp(-rvdw): near
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    // the decaying terms over every atom image within rcut
+    for (int q = threadIdx.x; q < 256; q += TT) stab[q] = as_df(__ldg(gt.t2 + q));
+    const int nxi = 2 * p.mx + 1, nyi = 2 * p.my + 1, nimg = nxi * nyi * (2 * p.mz + 1);
+    const int nq = at.n * nimg;
+    const float reach = p.rcutf + kMargin, rc2f = p.rc2f;
+    auto keep = [&](int q) {
+        float fx, fy, fz;
+        gimage32(at.w32, q / nimg, q % nimg, g, p, fx, fy, fz);
+        return box_d2(t, fx, fy, fz) < reach * reach;
+    };
+    const int total = block_compact(0, nq, keep, nullptr, scratch);
+    const int win = total <= GCAP ? nq : GCAP;       // GCAP candidates never overflow the list
+    const int ns = NS + gt.kt1;
+    for (int w0 = 0; w0 < nq; w0 += win) {
+        const int m = block_compact(w0, min(w0 + win, nq), keep, elist, scratch);
+        for (int e0 = 0; e0 < m; e0 += GB) {
+            const int ms = min(GB, m - e0);
+            for (int r = threadIdx.x; r < ms * ns; r += TT) {
+                const int e = r / ns, c = r % ns;
+                const int q = elist[e0 + e];
+                const int a = q / nimg, im = q % nimg;
+                if (c < NS) {
+                    int axis, gi;
+                    staged_line(t, g, c, axis, gi);
+                    const df dd = as_df(__ldg(gt.d + gtab_index(gt, a, image_digit(p, im, axis), axis, gi)));
+                    const df sq = df_mul(dd, dd);
+                    if (c < TX) sx2[e][c] = sq;
+                    else if (c < TX + TY) sy2[e][c - TX] = sq;
+                    else sz2[e][c - TX - TY] = sq;
+                } else {
+                    const int n = c - NS;
+                    srow[e][n] = df_mul(as_df(gt.at[a].a), as_df(__ldg(gt.t1 + n)));
+                    if (n == 0) skz[e] = eq19 ? gt.at[a].kzl : 0;
+                }
+            }
+            __syncthreads();
+            for (int e = 0; e < ms; ++e) {
+                const df xy = df_add(sx2[e][tx], sy2[e][ty]);
+                if (!(xy.hi < rc2f)) continue;                      // beyond rcut for every plane
+                const int kz = skz[e];                              // below a lower atom: its growing term instead
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int zz = tz + 4 * r;
+                    if (!valid[r] || sat[r] || t.k0 + zz < kz) continue;
+                    const df q = df_add(xy, sz2[e][zz]);
+                    if (!(q.hi < rc2f)) continue;
+                    float y;
+                    int n;
+                    const df d = q.hi > 0.f ? df_sqrt(q, y) : df{0.f, 0.f};
+                    const df v = exp_tab<true>(d, srow[e], stab, n);
+                    gamma_acc(D[r], F[r], G[r], v, n);
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (!valid[r]) continue;
+        const long idx = i + (long)g.nx * (j + (long)g.ny * (t.k0 + tz + 4 * r));
+        double e = p.eps0, fe = 0.0;
+        if (sat[r]) {
+            e = 1.0;
+        } else {
+            const double gam = D[r] + (f32_to_f64(F[r]) + f32_to_f64(G[r]));
+            if (gam > 0.0) {
+                const double gb = exp(p.beta2 * log(gam));         // gamma^(2 beta)
+                const double den = 1.0 + gb;
+                e = 1.0 + (p.eps0 - 1.0) / den;
+                fe = -(p.eps0 - 1.0) * p.beta2 * gb / (gam * den * den);
+            }
+        }
+        eps64[idx] = e;
+        if (fe64) fe64[idx] = fe;
+        if (eps32) eps32[idx] = split_to_float2(e).x;
+    }
+}
+
+// S_a as k_forces_eps_gamma computes it. The tile's image list is in candidate
+// order, so each atom's images are adjacent; every warp takes a contiguous share of
+// it, one image at a time over the tile's 2048 points (compensated FP32 sums of df
+// products), and turns its sums into FP64 atomics only when the atom changes.
+__global__ void __launch_bounds__(TT) k_forces_eps_gamma_df(Geo g, Atoms at, DielParams p, GammaTabs gt,
+                                                            const float2* phid, const double* wext,
+                                                            const double* fe64, double* S) {
+    __shared__ df Ws[TX * TY * EZ];              // W (d eps/d gamma), index tx + TX (ty + TY z)
+    __shared__ int elist[GCAPF];
+    __shared__ df wd[TT / 32][NS];               // a warp's image: displacements of the staged lines
+    __shared__ df wq[TT / 32][NS];               // and their squares
+    __shared__ df wrow[TT / 32][kGT1];
+    __shared__ df stab[256];
+    __shared__ int scratch[TT / 32 + 1];
+    const Tile t = make_tile_ez(g);
+    const bool eq19 = p.kind == 2;
+    int any = 0;
+    {
+        const df c2x = df_from(g.c2x), c2y = df_from(g.c2y), c2z = df_from(g.c2z);
+        for (int q = threadIdx.x; q < TX * TY * EZ; q += TT) {
+            const int tx = q % TX, ty = (q / TX) % TY, tz = q / (TX * TY);
+            const int i = t.i0 + tx, j = t.j0 + ty, k = t.k0 + tz;
+            df w = df{0.f, 0.f};
+            if (i < g.nx && j < g.ny && k < g.nz) {
+                const long c = i + (long)g.nx * (j + (long)g.ny * k);
+                const df nw = neg_force_weight_df(g, phid, wext, fe64[c], i, j, k, c, c2x, c2y, c2z);
+                w = df{-nw.hi, -nw.lo};
+            }
+            Ws[q] = w;
+            any |= w.hi != 0.f;
+        }
+    }
+    if (__syncthreads_or(any) == 0) return;      // d eps/d gamma = 0 on the whole tile
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float rc2f = p.rc2f;
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+    // the warp's sums for atom a into S: lanes 0, 1, 2 take x, y, z (one FP64 add each)
+    auto flush = [&](int a) {
+        warp_sum_df(sx, cx); warp_sum_df(sy, cy); warp_sum_df(sz, cz);
+        const float hi = lane == 0 ? sx : (lane == 1 ? sy : sz);
+        const float lo = lane == 0 ? cx : (lane == 1 ? cy : cz);
+        if (lane < 3) {
+            const double v = f32_to_f64(hi) + f32_to_f64(lo);
+            if (v != 0.0) atomicAdd(&S[3 * a + lane], v);
+        }
+        sx = cx = sy = cy = sz = cz = 0.f;
+    };
+    // one image (displacements in wd, squares in wq, factor row in wrow) over the
+    // tile's points: a decaying term at the planes k >= kz within rcut, a growing
+    // term (grow) at the planes k < kz
+    auto pairs = [&](int kz, bool grow) {
+        for (int b = 0; b < 16; ++b) {
+            int tx, ty, tz;
+            compact_point(b, lane, tx, ty, tz);
+            if (t.i0 + tx >= g.nx || t.j0 + ty >= g.ny) continue;
+            const df xy = df_add(wq[warp][tx], wq[warp][TX + ty]);
+            if (!grow && !(xy.hi < rc2f)) continue;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int zz = tz + 4 * r;
+                const int k = t.k0 + zz;
+                if (k >= g.nz || (grow ? k >= kz : k < kz)) continue;
+                const df W = Ws[tx + TX * (ty + TY * zz)];
+                if (W.hi == 0.f) continue;                          // also every saturated point
+                const df q = df_add(xy, wq[warp][TX + TY + zz]);
+                if (!(q.hi > 0.f) || (!grow && !(q.hi < rc2f))) continue;
+                float y;
+                const df d = df_sqrt(q, y);
+                df c;
+                int n;
+                if (grow) {
+                    c = df_mul(df_mul(W, exp_tab<false>(d, wrow[warp], stab, n)), df_recip(d, y));
+                    c = df{-c.hi, -c.lo};
+                } else {
+                    c = df_mul(df_mul(W, exp_tab<true>(d, wrow[warp], stab, n)), df_recip(d, y));
+                }
+                df_acc(sx, cx, c, wd[warp][tx]);
+                df_acc(sy, cy, c, wd[warp][TX + ty]);
+                df_acc(sz, cz, c, wd[warp][TX + TY + zz]);
+            }
+        }
+    };
+    // decaying terms
+    for (int q = threadIdx.x; q < 256; q += TT) stab[q] = as_df(__ldg(gt.t2 + q));
+    const int nxi = 2 * p.mx + 1, nyi = 2 * p.my + 1, nimg = nxi * nyi * (2 * p.mz + 1);
+    const int nq = at.n * nimg;
+    const float reach = p.rcutf + kMargin;
+    auto keep = [&](int q) {
+        float fx, fy, fz;
+        gimage32(at.w32, q / nimg, q % nimg, g, p, fx, fy, fz);
+        return box_d2(t, fx, fy, fz) < reach * reach;
+    };
+    const int total = block_compact(0, nq, keep, nullptr, scratch);
+    const int win = total <= GCAPF ? nq : GCAPF;
+    for (int w0 = 0; w0 < nq; w0 += win) {
+        const int m = block_compact(w0, min(w0 + win, nq), keep, elist, scratch);
+        const int e1 = (int)(((long)(warp + 1) * m) / (TT / 32));
+        int cur = -1;
+        for (int e = (int)(((long)warp * m) / (TT / 32)); e < e1; ++e) {
+            const int q = elist[e];
+            const int a = q / nimg, im = q % nimg;
+            if (a != cur) {
+                if (cur >= 0) flush(cur);
+                cur = a;
+            }
+            __syncwarp();
+            for (int c = lane; c < NS; c += 32) {
+                int axis, gi;
+                staged_line(t, g, c, axis, gi);
+                const df dd = as_df(__ldg(gt.d + gtab_index(gt, a, image_digit(p, im, axis), axis, gi)));
+                wd[warp][c] = dd;
+                wq[warp][c] = df_mul(dd, dd);
+            }
+            const df A = as_df(gt.at[a].a);
+            for (int n = lane; n < gt.kt1; n += 32) wrow[warp][n] = df_mul(A, as_df(__ldg(gt.t1 + n)));
+            __syncwarp();
+            pairs(eq19 ? gt.at[a].kzl : 0, false);
+        }
+        if (cur >= 0) flush(cur);
+        __syncthreads();                          // the list is read; the next window rebuilds it
+    }
+    if (!eq19) return;
+    // growing terms: each lower atom's nearest image at the points below it
+    __syncthreads();
+    for (int q = threadIdx.x; q < 256; q += TT) stab[q] = as_df(__ldg(gt.u2 + q));
+    for (int a0 = 0; a0 < at.n; a0 += GCAPF) {
+        const int nl =
+            block_compact(a0, min(a0 + GCAPF, at.n), [&](int a) { return gt.at[a].kzl > t.k0; }, elist, scratch);
+        for (int e = warp; e < nl; e += TT / 32) {
+            const int a = elist[e];
+            __syncwarp();
+            for (int c = lane; c < NS; c += 32) {
+                int axis, gi;
+                staged_line(t, g, c, axis, gi);
+                const df dd = nearest_disp(gt, a, axis, gi);
+                wd[warp][c] = dd;
+                wq[warp][c] = df_mul(dd, dd);
+            }
+            const df B = as_df(gt.at[a].b);
+            for (int n = lane; n < gt.kg; n += 32) wrow[warp][n] = df_mul(B, as_df(__ldg(gt.u1 + n)));
+            __syncwarp();
+            pairs(gt.at[a].kzl, true);
+            flush(a);
+        }
+        __syncthreads();                          // the list is read; the next window rebuilds it
+    }
+}
+
 // ----------------------------------------------------------------- dry planes
 __global__ void k_plane_max(Geo g, const double* eps64, double* out) {
     __shared__ double red[256];
@@ -1440,6 +1953,42 @@ void launch_build_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* 
 void launch_forces_eps_gamma(const Geo& g, Atoms at, DielParams p, const double* rvdw, const double* phi,
                              const double* wext, const double* fe64, double* S, cudaStream_t s) {
     k_forces_eps_gamma<<<tile_grid(g), TT, 0, s>>>(g, at, p, rvdw, phi, wext, fe64, S);
+}
+
+size_t gamma_tabs_bytes(int n_atoms, int m, int nmax) {
+    const size_t n = (size_t)(n_atoms > 0 ? n_atoms : 1);
+    return (n * (2 * m + 1) * 3 * nmax + 2 * (kGT1 + 256)) * sizeof(float2) + n * sizeof(GAtom) + 256;
+}
+
+GammaTabs gamma_tabs_view(void* base, int n_atoms, int m, int nmax) {
+    const size_t n = (size_t)(n_atoms > 0 ? n_atoms : 1);
+    GammaTabs gt{};
+    gt.m = m;
+    gt.nmax = nmax;
+    gt.d = static_cast<float2*>(base);
+    gt.t1 = gt.d + n * (2 * m + 1) * 3 * nmax;
+    gt.t2 = gt.t1 + kGT1;
+    gt.u1 = gt.t2 + 256;
+    gt.u2 = gt.u1 + kGT1;
+    gt.at = reinterpret_cast<GAtom*>(gt.u2 + 256);
+    return gt;
+}
+
+void launch_gamma_tables(const Geo& g, Atoms at, DielParams p, const double* rvdw, const GammaTabs& gt,
+                         cudaStream_t s) {
+    const long total = (long)at.n * (2 * gt.m + 1) * 3 * gt.nmax + 2 * (kGT1 + 256) + at.n;
+    k_gamma_tables<<<(int)((total + 255) / 256 < 152L * 16 ? (total + 255) / 256 : 152L * 16), 256, 0, s>>>(
+        g, at, p, rvdw, gt);
+}
+
+void launch_build_eps_gamma_df(const Geo& g, Atoms at, DielParams p, const GammaTabs& gt, double* eps64,
+                               double* fe64, float* eps32, cudaStream_t s) {
+    k_build_eps_gamma_df<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, gt, eps64, fe64, eps32);
+}
+
+void launch_forces_eps_gamma_df(const Geo& g, Atoms at, DielParams p, const GammaTabs& gt, const float2* phid,
+                                const double* wext, const double* fe64, double* S, cudaStream_t s) {
+    k_forces_eps_gamma_df<<<tile_grid_ez(g), TT, 0, s>>>(g, at, p, gt, phid, wext, fe64, S);
 }
 
 void launch_plane_max(const Geo& g, const double* eps64, double* out, cudaStream_t s) {

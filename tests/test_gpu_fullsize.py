@@ -191,3 +191,29 @@ def test_md_128x128x256_frames_full_size():
     _check_fields(w.grid, w.cell, last, e, r)
     _check_solution(w.grid, w.cell, p, r, e, 1e-8, s.stats().residual, E, E2, 1e-6, floor=1e-12)
     _check_forces(w.grid, w.cell, last, p, F.cpu().numpy(), W.fd_atom_indices(len(at.Z), 2, seed=3), 1e-9)
+
+
+def test_gamma_dielectric_192x192x384_sampled():
+    """Eq. 9-10 on the 192x192x384 slab: 288 atoms, every image within the
+    tail-bounded radius (about 41 A, so 75 images per atom). eps at seeded grid
+    points against the oracle's evaluation at those points, then a mixed solve to
+    1e-8 measured with the oracle's own residual."""
+    GPSolver = _gpu()
+    w = W.WORKLOADS["mixed_192x192x384"]
+    at = W.workload_atoms(w)
+    rv = W.vdw_radii(at.Z)
+    p = O.GammaParams()
+    s = GPSolver(w.grid, w.cell, precision=1, levels=w.levels, kind=1, beta=p.beta)
+    s.set_atoms(_t(at.pos), radii=_t(rv))
+    assert abs(s.stats().gamma_cutoff - O.gamma_cutoff(w.cell, rv, p.tail)) < 1e-5
+    e = s.eps().cpu().numpy()
+    flat, pts = _sample(w.grid, w.cell, at.pos)
+    ref = O.dielectric_gamma_points(pts, w.cell, at.pos, rv, p)
+    assert np.max(np.abs(e.ravel()[flat] - ref)) < 1e-13 * np.max(ref)
+    pos, gauss = _t(at.pos), _t(_gauss(at))
+    rho = s.build_rho(pos, gauss)
+    phi = s.solve(rho, tol=1e-8)
+    E, E2, F = s.energy_forces(phi, rho, gauss)
+    assert np.all(np.isfinite(F.cpu().numpy()))
+    _check_solution(w.grid, w.cell, phi.cpu().numpy(), rho.cpu().numpy(), e, 1e-8, s.stats().residual, E, E2,
+                    1e-6, floor=1e-12)

@@ -335,6 +335,35 @@ def test_gamma_tail_parameter_moves_the_radius():
     assert _rel(s.eps().cpu().numpy(), O.dielectric_gamma(grid, cell, at.pos, rv, p)) < 1e-13
 
 
+def test_gamma_fp64_kernels_beyond_the_staged_rows():
+    """A tail bound so small that the radius passes the rows the df64 kernels
+    stage (54 A) takes the FP64 kernels; eps and both force terms still follow
+    the oracle at that radius."""
+    GPSolver = _gpu()
+    grid, cell = (16, 8, 24), (7.0, 6.5, 12.0)
+    at = W.slab_atoms(cell, 1, 2, seed=0)
+    rv = _radii(at.Z)
+    p = O.GammaParams(tail=1e-30)
+    s = GPSolver(grid, cell, precision=0, kind=1, beta=p.beta, gamma_tail=p.tail)
+    s.set_atoms(_t(at.pos), radii=_t(rv))
+    assert s.stats().gamma_cutoff > 60.0
+    assert _rel(s.eps().cpu().numpy(), O.dielectric_gamma(grid, cell, at.pos, rv, p)) < 1e-13
+
+
+def test_gamma_dielectric_is_reproducible():
+    """The df64 kernels sum each point's terms in a fixed order (the tile's image
+    list is built by a scan, not by atomics): building eps twice gives the same bits."""
+    GPSolver = _gpu()
+    grid, cell = (32, 32, 48), (10.0, 10.0, 15.0)
+    at, _, _, _ = _case(grid, cell, 2, 3, seed=2)
+    rv = _t(_radii(at.Z))
+    s = GPSolver(grid, cell, precision=0, kind=1)
+    s.set_atoms(_t(at.pos), radii=rv)
+    e1 = s.eps().clone()
+    s.set_atoms(_t(at.pos), radii=rv)
+    assert torch.equal(e1, s.eps())
+
+
 def test_gamma_energy_and_forces_match_oracle():
     """Eq. 9-10 dielectric: solve, energy and both force terms against the oracle (Eq. 11 with
     the derived Eq. 12 sign)."""
