@@ -229,6 +229,7 @@ struct GAtom {
     float2 a, b;
     float qsat;
     int kzl;
+    float l2a;      // rvdw log2(e): exp(rvdw - d) = 2^(l2a - d log2(e)) for the FP32 far pairs
 };
 constexpr int kGT1 = 56;        // exp(-+n) rows the df64 kernels stage per atom: distances below kGT1 - 2 A
 struct GammaTabs {

@@ -1160,6 +1160,24 @@ __device__ __forceinline__ df df_sqrt(df q, float& y) {
     return df_quick(s, 0.5f * e * y);
 }
 
+// Far pairs in FP32. d = sqrt(q) to about an ulp, y = 1/d to about 2^-23 (a
+// Newton step on each hardware estimate)
+__device__ __forceinline__ float sqrt_f32(float q, float& y) {
+    const float y0 = rsqrtf(q);
+    const float s0 = q * y0;
+    y = y0 * fmaf(-0.5f * q * y0, y0, 1.5f);
+    return fmaf(fmaf(-s0, s0, q), 0.5f * y0, s0);
+}
+
+// exp(rvdw - d) = 2^(l2a - d log2(e)) of a far pair by the hardware base-2
+// exponential (relative error about 2^-22); with d from an FP32 squared distance
+// and the FP32 argument the term carries a relative error of a few 1e-6 at 40 A
+__device__ __forceinline__ float exp_far(float d, float l2a) {
+    float v;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(v) : "f"(fmaf(d, -1.44269504f, l2a)));
+    return v;
+}
+
 // 1/d as df from d and an estimate y of 1/d.hi (one Newton step)
 __device__ __forceinline__ df df_recip(df d, float y) {
     const float p = d.hi * y;
@@ -1185,7 +1203,11 @@ __device__ __forceinline__ void df_add_to(float& s, float& c, df v) {
 // a few dozen per point) go into an FP64 sum, the rest (at most ~1e-3 of gamma)
 // into a df sum of their own, whose half ulp then sits far below any term that
 // matters. One df sum for all of them lost the terms beyond ~35 A (4e-12 of gamma).
+// Beyond kFarEps (26 A) a term is below ~1e-9 of one at contact and the terms
+// there sum to a few 1e-9 of gamma, so FP32 (a few 1e-6 relative) leaves below
+// ~1e-14: those pairs skip the df work.
 constexpr int kNear = 10;
+constexpr float kFarEps2 = 26.f * 26.f;
 __device__ __forceinline__ void gamma_acc(double& D, float& F, float& G, df v, int n) {
     if (n < kNear) D += f32_to_f64(v.hi) + f32_to_f64(v.lo);
     else df_add_to(F, G, v);
@@ -1292,6 +1314,7 @@ __global__ void k_gamma_tables(Geo g, Atoms at, DielParams p, const double* rvdw
         ga.a = split_to_float2(exp(rv));
         ga.b = split_to_float2(exp(-rv));
         ga.qsat = (float)((rv + p.esat) * (rv + p.esat));
+        ga.l2a = (float)(rv * 1.4426950408889634);
         int kz = 0;
         if (p.kind == 2 && za <= p.zlim) {
             while (kz < g.nz && kz * g.hz < za) ++kz;           // planes k < kz have k hz < za
@@ -1301,7 +1324,7 @@ __global__ void k_gamma_tables(Geo g, Atoms at, DielParams p, const double* rvdw
     }
 }
 
-__global__ void __launch_bounds__(TT) k_build_eps_gamma_df(Geo g, Atoms at, DielParams p, GammaTabs gt,
+__global__ void __launch_bounds__(TT, 2) k_build_eps_gamma_df(Geo g, Atoms at, DielParams p, GammaTabs gt,
                                                            double* eps64, double* fe64, float* eps32) {
     __shared__ int elist[GCAP];
     __shared__ df sx2[GB][TX];
@@ -1318,7 +1341,7 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma_df(Geo g, Atoms at, Diel
     const int i = t.i0 + tx, j = t.j0 + ty;
     bool valid[4], sat[4];
     double D[4];
-    float F[4], G[4];
+    float F[4], G[4], H[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         valid[r] = i < g.nx && j < g.ny && t.k0 + tz + 4 * r < g.nz;
@@ -1326,6 +1349,7 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma_df(Geo g, Atoms at, Diel
         D[r] = 0.0;
         F[r] = 0.f;
         G[r] = 0.f;
+        H[r] = 0.f;
     }
     const bool eq19 = p.kind == 2;
     if (eq19) {
@@ -1415,7 +1439,10 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma_df(Geo g, Atoms at, Diel
                 } else {
                     const int n = c - NS;
                     srow[e][n] = df_mul(as_df(gt.at[a].a), as_df(__ldg(gt.t1 + n)));
-                    if (n == 0) skz[e] = eq19 ? gt.at[a].kzl : 0;
+                    if (n == 0) {
+                        skz[e] = eq19 ? gt.at[a].kzl : 0;
+                        sqs[e] = gt.at[a].l2a;
+                    }
                 }
             }
             __syncthreads();
@@ -1423,10 +1450,18 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma_df(Geo g, Atoms at, Diel
                 const df xy = df_add(sx2[e][tx], sy2[e][ty]);
                 if (!(xy.hi < rc2f)) continue;                      // beyond rcut for every plane
                 const int kz = skz[e];                              // below a lower atom: its growing term instead
+                const float l2a = sqs[e];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int zz = tz + 4 * r;
                     if (!valid[r] || sat[r] || t.k0 + zz < kz) continue;
+                    const float qf = xy.hi + sz2[e][zz].hi;
+                    if (qf >= kFarEps2) {
+                        if (!(qf < rc2f)) continue;
+                        float y;
+                        H[r] += exp_far(sqrt_f32(qf, y), l2a);      // at most a few 1e-9 of gamma in all
+                        continue;
+                    }
                     const df q = df_add(xy, sz2[e][zz]);
                     if (!(q.hi < rc2f)) continue;
                     float y;
@@ -1447,7 +1482,7 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma_df(Geo g, Atoms at, Diel
         if (sat[r]) {
             e = 1.0;
         } else {
-            const double gam = D[r] + (f32_to_f64(F[r]) + f32_to_f64(G[r]));
+            const double gam = D[r] + (f32_to_f64(F[r]) + (f32_to_f64(G[r]) + f32_to_f64(H[r])));
             if (gam > 0.0) {
                 const double gb = exp(p.beta2 * log(gam));         // gamma^(2 beta)
                 const double den = 1.0 + gb;
@@ -1460,6 +1495,11 @@ __global__ void __launch_bounds__(TT) k_build_eps_gamma_df(Geo g, Atoms at, Diel
         if (eps32) eps32[idx] = split_to_float2(e).x;
     }
 }
+
+// Beyond kFarF (18 A) a pair's force term is below ~1e-7 of one at contact and the
+// terms there sum to below ~1e-5 of an atom's force, so FP32 (a few 1e-6 relative)
+// leaves below ~1e-11 of it.
+constexpr float kFarF2 = 18.f * 18.f;
 
 // S_a as k_forces_eps_gamma computes it. The tile's image list is in candidate
 // order, so each atom's images are adjacent; every warp takes a contiguous share of
@@ -1477,6 +1517,7 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma_df(Geo g, Atoms at, Die
     __shared__ int scratch[TT / 32 + 1];
     const Tile t = make_tile_ez(g);
     const bool eq19 = p.kind == 2;
+    float l2a = 0.f;                             // the current image's rvdw log2(e)
     int any = 0;
     {
         const df c2x = df_from(g.c2x), c2y = df_from(g.c2y), c2z = df_from(g.c2z);
@@ -1497,8 +1538,11 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma_df(Geo g, Atoms at, Die
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float rc2f = p.rc2f;
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f;          // pairs beyond kFarF, summed in FP32
     // the warp's sums for atom a into S: lanes 0, 1, 2 take x, y, z (one FP64 add each)
     auto flush = [&](int a) {
+        df_add_to(sx, cx, df{fx, 0.f}); df_add_to(sy, cy, df{fy, 0.f}); df_add_to(sz, cz, df{fz, 0.f});
+        fx = fy = fz = 0.f;
         warp_sum_df(sx, cx); warp_sum_df(sy, cy); warp_sum_df(sz, cz);
         const float hi = lane == 0 ? sx : (lane == 1 ? sy : sz);
         const float lo = lane == 0 ? cx : (lane == 1 ? cy : cz);
@@ -1525,6 +1569,18 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma_df(Geo g, Atoms at, Die
                 if (k >= g.nz || (grow ? k >= kz : k < kz)) continue;
                 const df W = Ws[tx + TX * (ty + TY * zz)];
                 if (W.hi == 0.f) continue;                          // also every saturated point
+                if (!grow) {
+                    const float qf = xy.hi + wq[warp][TX + TY + zz].hi;
+                    if (qf >= kFarF2) {
+                        if (!(qf < rc2f)) continue;
+                        float y;
+                        const float c = W.hi * exp_far(sqrt_f32(qf, y), l2a) * y;
+                        fx = fmaf(c, wd[warp][tx].hi, fx);
+                        fy = fmaf(c, wd[warp][TX + ty].hi, fy);
+                        fz = fmaf(c, wd[warp][TX + TY + zz].hi, fz);
+                        continue;
+                    }
+                }
                 const df q = df_add(xy, wq[warp][TX + TY + zz]);
                 if (!(q.hi > 0.f) || (!grow && !(q.hi < rc2f))) continue;
                 float y;
@@ -1575,6 +1631,7 @@ __global__ void __launch_bounds__(TT) k_forces_eps_gamma_df(Geo g, Atoms at, Die
                 wq[warp][c] = df_mul(dd, dd);
             }
             const df A = as_df(gt.at[a].a);
+            l2a = gt.at[a].l2a;
             for (int n = lane; n < gt.kt1; n += 32) wrow[warp][n] = df_mul(A, as_df(__ldg(gt.t1 + n)));
             __syncwarp();
             pairs(eq19 ? gt.at[a].kzl : 0, false);
