@@ -217,3 +217,44 @@ def test_gamma_dielectric_192x192x384_sampled():
     assert np.all(np.isfinite(F.cpu().numpy()))
     _check_solution(w.grid, w.cell, phi.cpu().numpy(), rho.cpu().numpy(), e, 1e-8, s.stats().residual, E, E2,
                     1e-6, floor=1e-12)
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_gamma_forces_192x192x384_central_differences(kind):
+    """Eq. 9-10 (kind 1) and Eq. 19 (kind 2, the lowest layer excluding the solvent
+    below it) on the 192x192x384 slab: the solvent force of 3 seeded atoms against
+    central differences (h = 1e-4 A) of the library's own variational energy
+    2E - E' with rho frozen, every evaluation an FP64 solve to 1e-13 on the GPU;
+    within 1e-6 of the largest component."""
+    GPSolver = _gpu()
+    w = W.WORKLOADS["mixed_192x192x384"]
+    at = W.workload_atoms(w)
+    rv = _t(W.vdw_radii(at.Z))
+    zlim = W.lower_layer_zlim(at, w) if kind == 2 else 0.0
+    s = GPSolver(w.grid, w.cell, precision=0, levels=w.levels, kind=kind, zlim=zlim)
+    s.set_atoms(_t(at.pos), radii=rv)
+    rho = s.build_rho(_t(at.pos), _t(_gauss(at)))
+
+    def J(q):
+        s.set_atoms(_t(q), radii=rv)
+        phi = s.solve(rho, tol=1e-13)
+        E, E2, _ = s.energy_forces(phi, rho, None, forces=False)
+        return 2.0 * E - E2
+
+    s.set_atoms(_t(at.pos), radii=rv)
+    phi = s.solve(rho, tol=1e-13)
+    _, _, F = s.energy_forces(phi, rho, None)
+    F = F.cpu().numpy()
+    assert np.all(np.isfinite(F))
+    sel = W.fd_atom_indices(len(at.Z), 3, seed=7 + kind)
+    d = 1e-4
+    fd = np.zeros((len(sel), 3))
+    for t_, a in enumerate(sel):
+        for c in range(3):
+            pp = at.pos.copy(); pp[a, c] += d
+            pm = at.pos.copy(); pm[a, c] -= d
+            fd[t_, c] = -(J(pp) - J(pm)) / (2 * d)
+    scale = np.max(np.abs(fd))
+    assert scale > 1e-3
+    err = np.max(np.abs(fd - F[sel])) / scale
+    assert err < 1e-6, err
