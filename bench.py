@@ -395,6 +395,53 @@ def gpu_arm(args, rank, world):
             # residual and phi update switch from df64 (FP32 pairs) to FP64
             tight = time_variant(args.precision, args.split, "the headline solver at tol 1e-10", tol=1e-10)
 
+    # the same step with the paper's own dielectrics: Eq. 9-10 (kind 1) and Eq. 19
+    # (kind 2, the lowest layer excluding the solvent below it), eps from every atom
+    # image within the tail-bounded radius, on the same frames and solver settings
+    def time_dielectric(kind):
+        zl = W.lower_layer_zlim(at, w) if kind == 2 else 0.0
+        sv = P.GPSolver(w.grid, w.cell, precision=args.precision, split=0, levels=w.levels,
+                        sweep_shape=args.sweep_shape, n_dirichlet=n_dir, kind=kind, gamma_tail=args.gamma_tail,
+                        zlim=zl)
+        rv = torch.tensor(W.vdw_radii(at.Z), dtype=torch.float64, device=dev)
+
+        def stepk(pos):
+            sv.set_atoms(pos, radii=rv)
+            sv.build_rho(pos, gauss, out=rho)
+            phi.zero_()
+            sv.ctx.gp_solve(rho, phi, args.tol, check=True)
+            sv.ctx.gp_energy_forces(phi, rho, gauss, F)
+
+        stepk(frames[0])
+        torch.cuda.synchronize()
+        ncmp = max(1, min(args.steps, 3))
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for i in range(ncmp):
+            stepk(frames[args.warmup + i])
+        c1.record(stream)
+        torch.cuda.synchronize()
+        sst = sv.stats()
+        sv.ctx.gp_profile(True)
+        for i in range(ncmp):
+            stepk(frames[args.warmup + i])
+        torch.cuda.synchronize()
+        pv = sv.ctx.gp_get_profile()
+        sv.ctx.gp_profile(False)
+        out = {"dielectric": {1: "Eq. 9-10", 2: "Eq. 19 (z_lim %.3f A)" % zl}[kind],
+               "value": ncmp / (c0.elapsed_time(c1) / 1e3), "unit": "steps/s", "steps": ncmp,
+               "gamma_cutoff_A": sst.gamma_cutoff, "tol": args.tol,
+               "outer_iterations": sst.outer_iterations, "vcycles": sst.vcycles,
+               "eps_ms": pv["eps"]["ms"] / ncmp, "forces_eps_ms": pv["forces_eps"]["ms"] / ncmp,
+               "step": "set_dielectric + build_rho + solve (cold) + energy_forces"}
+        del sv
+        return out
+
+    dielectrics = None
+    if not args.no_dielectrics and world == 1:
+        dielectrics = {"eq9_10": time_dielectric(1), "eq19": time_dielectric(2)}
+
     # end to end through the public API with host buffers: every step copies its
     # inputs in from pinned memory and its result (phi, forces; E comes back with
     # the call) out to pinned memory, as a serving loop would: the copy-back of
@@ -472,7 +519,8 @@ def gpu_arm(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof, "smoother": smooth, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk, "fp64_fullbox": comparator, "split_scheme": split_variant, "tol_1e-10": tight,
-        "md": md, "oracle_full_step": oracle_full, "phases": phases, "dominant_kernel_group": dominant,
+        "md": md, "oracle_full_step": oracle_full, "dielectrics": dielectrics, "phases": phases,
+        "dominant_kernel_group": dominant,
     }
     return line
 
@@ -935,6 +983,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-dielectrics", action="store_true",
+                    help="skip the steps with the paper's Eq. 9-10 and Eq. 19 dielectrics")
     ap.add_argument("--mode", default="step", choices=["step", "md", "residual6", "solve6", "oracle"])
     ap.add_argument("--oracle-workers", type=int, nargs="+", default=[1, 0],
                     help="--mode oracle: process counts to time the complete step with (0 = every host core)")
