@@ -1572,6 +1572,10 @@ gp_status gp_set_dielectric(gp_ctx* c, const double* atoms_dev, int n_atoms, con
             dp.my = (int)std::ceil(dp.rcut / c->g.ly);
             dp.mz = (int)std::ceil(dp.rcut / c->g.lz);
             c->stats.gamma_cutoff = dp.rcut;
+            if (n_atoms > 0) {
+                const double r32 = gamma_cutoff(c->g, se, 1e-7);
+                dp.far2f = (float)(r32 * r32);
+            }
         }
         // the df64 Eq. 9 kernels stage exp(-n) rows up to the radius (and exp(+n) rows up
         // to the saturation distance of Eq. 19): radii beyond their rows take the FP64 kernels

@@ -94,6 +94,9 @@ struct DielParams {
     // FP32 copies for the culling and the FP32 branches, made on the host: a kernel that
     // converted them per thread would spend FP64-pipe instructions on it (and may redo them)
     float rcutf, rc2f, reachf, tinyf, r0f, iwf, spnf;
+    // kinds 1, 2: squared radius beyond which the df64 dielectric kernel takes a pair in
+    // FP32 (the host puts it where the proven tail bound on gamma falls to 1e-7)
+    float far2f;
 };
 
 // (hi, lo) = (RN_float(x), RN_float(x - hi)): the float pair of a double, as the
@@ -172,6 +175,7 @@ inline DielParams make_diel(double eps0, double r0, double w, double rcut, int k
     p.r0f = (float)r0;
     p.iwf = (float)p.iw;
     p.spnf = (float)p.sp_norm;
+    p.far2f = 3.0e38f;
     return p;
 }
 

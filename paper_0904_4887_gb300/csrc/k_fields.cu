@@ -1203,13 +1203,16 @@ __device__ __forceinline__ void df_add_to(float& s, float& c, df v) {
 // a few dozen per point) go into an FP64 sum, the rest (at most ~1e-3 of gamma)
 // into a df sum of their own, whose half ulp then sits far below any term that
 // matters. One df sum for all of them lost the terms beyond ~35 A (4e-12 of gamma).
-// Beyond kFarEps (26 A) a term is below ~1e-9 of one at contact and the terms
-// there sum to a few 1e-9 of gamma, so FP32 (a few 1e-6 relative) leaves below
-// ~1e-14: those pairs skip the df work.
+// Beyond the radius where the proven tail bound on gamma falls to 1e-7 (p.far2f,
+// about 27 A here) a term is evaluated in FP32 (a few 1e-6 relative, a few 1e-7 of
+// it in one direction) and added to the same df sum: an FP32 sum of those terms
+// instead lost the ones below its half ulp in a dense 10 x 10 x 15 A cell, where
+// they are thousands per point (1.5e-13 of eps).
 constexpr int kNear = 10;
-constexpr float kFarEps2 = 26.f * 26.f;
 __device__ __forceinline__ void gamma_acc(double& D, float& F, float& G, df v, int n) {
-    if (n < kNear) D += f32_to_f64(v.hi) + f32_to_f64(v.lo);
+    // the casts run on the FP64 pipe, idle otherwise here: two issue slots instead
+    // of the twenty-odd integer instructions of f32_to_f64
+    if (n < kNear) D += (double)v.hi + (double)v.lo;
     else df_add_to(F, G, v);
 }
 
@@ -1341,7 +1344,7 @@ __global__ void __launch_bounds__(TT, 2) k_build_eps_gamma_df(Geo g, Atoms at, D
     const int i = t.i0 + tx, j = t.j0 + ty;
     bool valid[4], sat[4];
     double D[4];
-    float F[4], G[4], H[4];
+    float F[4], G[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         valid[r] = i < g.nx && j < g.ny && t.k0 + tz + 4 * r < g.nz;
@@ -1349,7 +1352,6 @@ __global__ void __launch_bounds__(TT, 2) k_build_eps_gamma_df(Geo g, Atoms at, D
         D[r] = 0.0;
         F[r] = 0.f;
         G[r] = 0.f;
-        H[r] = 0.f;
     }
     const bool eq19 = p.kind == 2;
     if (eq19) {
@@ -1411,7 +1413,7 @@ __global__ void __launch_bounds__(TT, 2) k_build_eps_gamma_df(Geo g, Atoms at, D
     for (int q = threadIdx.x; q < 256; q += TT) stab[q] = as_df(__ldg(gt.t2 + q));
     const int nxi = 2 * p.mx + 1, nyi = 2 * p.my + 1, nimg = nxi * nyi * (2 * p.mz + 1);
     const int nq = at.n * nimg;
-    const float reach = p.rcutf + kMargin, rc2f = p.rc2f;
+    const float reach = p.rcutf + kMargin, rc2f = p.rc2f, far2f = p.far2f;
     auto keep = [&](int q) {
         float fx, fy, fz;
         gimage32(at.w32, q / nimg, q % nimg, g, p, fx, fy, fz);
@@ -1456,10 +1458,10 @@ __global__ void __launch_bounds__(TT, 2) k_build_eps_gamma_df(Geo g, Atoms at, D
                     const int zz = tz + 4 * r;
                     if (!valid[r] || sat[r] || t.k0 + zz < kz) continue;
                     const float qf = xy.hi + sz2[e][zz].hi;
-                    if (qf >= kFarEps2) {
+                    if (qf >= far2f) {
                         if (!(qf < rc2f)) continue;
                         float y;
-                        H[r] += exp_far(sqrt_f32(qf, y), l2a);      // at most a few 1e-9 of gamma in all
+                        df_add_to(F[r], G[r], df{exp_far(sqrt_f32(qf, y), l2a), 0.f});
                         continue;
                     }
                     const df q = df_add(xy, sz2[e][zz]);
@@ -1482,7 +1484,7 @@ __global__ void __launch_bounds__(TT, 2) k_build_eps_gamma_df(Geo g, Atoms at, D
         if (sat[r]) {
             e = 1.0;
         } else {
-            const double gam = D[r] + (f32_to_f64(F[r]) + (f32_to_f64(G[r]) + f32_to_f64(H[r])));
+            const double gam = D[r] + (f32_to_f64(F[r]) + f32_to_f64(G[r]));
             if (gam > 0.0) {
                 const double gb = exp(p.beta2 * log(gam));         // gamma^(2 beta)
                 const double den = 1.0 + gb;

@@ -364,6 +364,28 @@ def test_gamma_dielectric_is_reproducible():
     assert torch.equal(e1, s.eps())
 
 
+def test_gamma_image_lists_longer_than_a_tile_holds():
+    """A 10 x 10 x 15 A cell with 54 atoms: 847 images per atom within the 41.7 A
+    radius, about 11,000 reaching each tile, more than the image list of either
+    df64 kernel holds, so both take their candidates in windows. eps and both force
+    terms still follow the oracle."""
+    GPSolver = _gpu()
+    grid, cell = (16, 16, 24), (10.0, 10.0, 15.0)
+    at = W.slab_atoms(cell, 3, 3, seed=4)
+    rv = _radii(at.Z)
+    p = O.GammaParams()
+    eps = O.dielectric_gamma(grid, cell, at.pos, rv, p)
+    s = GPSolver(grid, cell, precision=0, kind=1, beta=p.beta)
+    s.set_atoms(_t(at.pos), radii=_t(rv))
+    assert _rel(s.eps().cpu().numpy(), eps) < 1e-13
+    rho = O.charge_density(grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud)
+    phi = s.solve(_t(rho), tol=1e-13)
+    pn = phi.cpu().numpy()
+    _, _, F = s.energy_forces(phi, _t(rho), _t(_gauss(at)))
+    Ge, Gr = O.energy_gradient(pn, grid, cell, at.pos, at.Z, at.sigma_core, at.sigma_cloud, p=p, rvdw=rv)
+    assert _rel(F.cpu().numpy(), -(Ge + Gr)) < 1e-10
+
+
 def test_gamma_energy_and_forces_match_oracle():
     """Eq. 9-10 dielectric: solve, energy and both force terms against the oracle (Eq. 11 with
     the derived Eq. 12 sign)."""
