@@ -1203,14 +1203,14 @@ __device__ __forceinline__ void df_add_to(float& s, float& c, df v) {
 // a few dozen per point) go into an FP64 sum, the rest (at most ~1e-3 of gamma)
 // into a df sum of their own, whose half ulp then sits far below any term that
 // matters. One df sum for all of them lost the terms beyond ~35 A (4e-12 of gamma).
-// Beyond the radius where the proven tail bound on gamma falls to 1e-7 (p.far2f,
-// about 27 A here) a term is evaluated in FP32 (a few 1e-6 relative, a few 1e-7 of
+// Beyond the radius where the proven tail bound on gamma falls to 1e-7 (p.far2f;
+// 26.8 A for 288 atoms in a 26 x 26 x 52 A cell) a term is evaluated in FP32 (a few 1e-6 relative, a few 1e-7 of
 // it in one direction) and added to the same df sum: an FP32 sum of those terms
 // instead lost the ones below its half ulp in a dense 10 x 10 x 15 A cell, where
 // they are thousands per point (1.5e-13 of eps).
 constexpr int kNear = 10;
 __device__ __forceinline__ void gamma_acc(double& D, float& F, float& G, df v, int n) {
-    // the casts run on the FP64 pipe, idle otherwise here: two issue slots instead
+    // the casts run on the FP64 pipe, otherwise idle in this kernel: two issue slots instead
     // of the twenty-odd integer instructions of f32_to_f64
     if (n < kNear) D += (double)v.hi + (double)v.lo;
     else df_add_to(F, G, v);
